@@ -1,0 +1,351 @@
+"""Benchmark: cells solved per second to ||d||/||f|| < 1e-10 on the 512^3
+periodic Gaussian-blob workload (FMG + V(1,1) cycles; FP32 multigrid inside
+FP64 defect correction), one solve per step, on one GB300 per rank.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun each rank solves its own grid (the solve
+does not shard: replicas), and value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cells solved/s to ||r||/||f||<1e-10 (512^3)"
+UNIT = "cells/s"
+TOL = 1e-10
+SEED = 20230227
+
+# Algorithmic bytes per finest cell of one launch of each kernel class, by
+# the width w of the level precision (see the design notes): the least data
+# that launch must move.
+def algorithmic_bytes_per_cell(kernel: str, w: int) -> float:
+    return {
+        "sor": 2.0 * w,                 # read u, read f (own colour), write u (own colour)
+        "defect_restrict": 2.0 * w + w / 8.0,
+        "prolong": 2.0 * w + w / 8.0,   # read u, coarse e; write u
+        "fmg_prolong": w + w / 8.0,
+        "defect_norm": 16.0,            # FP64 u, f
+        "outer_residual": 20.0,         # FP64 u, f -> FP32 r
+        "correct": 20.0,                # FP64 u, FP32 e -> FP64 u
+        "source": 16.0,                 # FP64 rho -> FP64 f
+    }[kernel]
+
+
+FP32_CLASSES = {"sor", "defect_restrict", "prolong", "fmg_prolong"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def src_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2302_13903_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel: str, prec: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    sha = src_sha()
+    best = None
+    for line in open(p):
+        f = line.split()
+        if len(f) != 6 or f[0].startswith("#"):
+            continue
+        k, pr, nn, cells_captured, bytes_per_launch, s = f
+        if k == kernel and pr == prec and s == sha:
+            scale = n ** 3 / float(cells_captured)  # traffic grows with the cells of a launch
+            best = float(bytes_per_launch) * scale
+    return best
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_solve_timed(n: int, threads: int):
+    import oracle
+    from paper_2302_13903_gb300 import inputs
+    oracle.build()
+    oracle.set_num_threads(threads)
+    rho = inputs.gaussian_blobs(n, 64, seed=SEED)
+    t = time.perf_counter()
+    r = oracle.solve(rho, 1.0 / n, oracle.PERIODIC, tol=TOL, four_pi_G=1.0)
+    dt = time.perf_counter() - t
+    assert r.ok, r.hist
+    return dt, len(r.hist)
+
+
+def cpu_baseline(n_sample: int):
+    threads = os.cpu_count() or 1
+    dt, cycles = oracle_solve_timed(n_sample, threads)
+    return {"value": n_sample ** 3 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one oracle solve of the same recipe at {n_sample}^3 (64 blobs, seed {SEED}), "
+                      f"FMG + V(1,1) to 1e-10 ({cycles} residual checks), {dt:.2f} s wall"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    n_sample = args.cpu_n
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_solve_timed(n_sample, threads)
+    times = []
+    for _ in range(args.steps):
+        dt, cycles = oracle_solve_timed(n_sample, threads)
+        times.append(dt)
+    tot = sum(times)
+    value = n_sample ** 3 * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{n_sample}^3 periodic Gaussian blobs (64, seed {SEED}), FP64 "
+                               f"FMG + V(1,1) to 1e-10 on the host cores (bounded sample of the "
+                               f"512^3 workload)", "n": n_sample, "bc": "periodic", "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n_sample}^3 instance of the same recipe, one solve per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64-path solves (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-n", type=int, default=256, help="oracle sample size")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2302_13903_gb300 as mg
+    from paper_2302_13903_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.n
+    prec = mg.MIXED if args.prec == "mixed" else mg.FP64
+    stream = torch.cuda.Stream()
+    rho = inputs.gaussian_blobs(n, 64, seed=SEED, device="cuda")
+    phi = torch.zeros_like(rho)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    solver = mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=prec)
+    hist = None
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            _, hist, st = solver.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+            assert st == 0, (st, hist)
+    cycles = len(hist)
+    solver.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, hist, st = solver.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+        assert st == 0, (st, hist)
+        launches += solver.last_launches
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ws * n ** 3 / (ms_per_step * 1e-3)
+    ktimes = solver.kernel_times()
+    solver.set_timing(False)
+
+    # roofline of the dominant kernel class (finest-level launches)
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    tot_ms, nl = ktimes[dom]
+    w = 4 if (prec == mg.MIXED and dom in FP32_CLASSES) else 8
+    alg = algorithmic_bytes_per_cell(dom, w) * n ** 3
+    achieved = alg / (tot_ms / nl * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    prec_tag = "f32" if w == 4 else "f64"
+    traffic = ncu_traffic(dom, prec_tag, n)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom}_{prec_tag}",
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg}
+
+    # end to end through the host API: pinned host rho/phi, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        rho_h = rho.cpu().pin_memory()
+        phi_h = torch.zeros_like(rho_h).pin_memory()
+        solver.solve_host(rho_h, 1.0, TOL, phi=phi_h, stream=stream)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            _, _, st = solver.solve_host(rho_h, 1.0, TOL, phi=phi_h, stream=stream)
+            assert st == 0
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        nbytes = n ** 3 * 8
+        e2e = {"value": ws * n ** 3 * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * cycles}
+        del rho_h, phi_h
+
+    # the plain FP64 GPU path on the same workload, for comparison
+    fp64 = None
+    if args.fp64_steps > 0 and prec == mg.MIXED:
+        solver.close()
+        s64 = mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.FP64)
+        _, h64, st = s64.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.fp64_steps):
+            _, h64, st = s64.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / args.fp64_steps
+        fp64 = {"value": n ** 3 / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
+                "cycles": len(h64), "status": st}
+        s64.close()
+    else:
+        solver.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and ws == 1:
+        cpu = cpu_baseline(args.cpu_n)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == mg.MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"{n}^3 periodic unit cube, 64 Gaussian blobs (seed {SEED}, "
+                                   f"sigma 0.02-0.08, lognormal amplitudes), mean removed; "
+                                   f"FMG + V(1,1) RB-SOR to ||d||/||f|| < 1e-10; "
+                                   + ("FP32 multigrid inside FP64 defect correction"
+                                      if prec == mg.MIXED else "FP64"),
+                       "n": n, "bc": "periodic", "prec": args.prec, "tol": TOL,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (1 GiB per FP64 field), no flush"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "residual_checks_per_solve": cycles,
+            "final_ratio": float(hist[-1]),
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items() if v[1]},
+            "fp64_path": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * mg.h -- C ABI of the GB300 geometric-multigrid Poisson solver.
+ *
+ * The library solves the discrete Poisson equation of self-gravity
+ *     (sum of the six face neighbours - 6 phi_ijk) / h^2 = 4 pi G rho_ijk
+ * (Tomida & Stone 2023, Sec. 2.1, Eqs. poisson and discretized2) on a uniform
+ * Cartesian grid of nx*ny*nz cells with spacing h, by full multigrid
+ * (Algorithm 2) followed by V(M,N) cycles (Algorithm 1) with a red-black SOR
+ * smoother (Sec. 2.3.2, Eqs. rbsor1-rbsor2), volume-average restriction and
+ * trilinear prolongation (Sec. 2.3.1), until the volume-weighted RMS defect
+ * (Sec. 2.3.7, Eq. threshold) divided by the RMS of the source falls below
+ * a tolerance.
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are contiguous, z-major: element (i, j, k) of an nx*ny*nz field
+ *    is at index (k*ny + j)*nx + i (x fastest).  Cell (i, j, k) has its centre
+ *    at ((i + 1/2 - nx/2) h, (j + 1/2 - ny/2) h, (k + 1/2 - nz/2) h): the
+ *    domain is centred on the origin.
+ *  - Pointers whose name ends in _dev are device pointers on the current CUDA
+ *    device; other pointers are host pointers.  The caller owns every array
+ *    it passes; the library never frees or keeps them past the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *    is issued on that stream in order; entry points that return values to
+ *    host memory synchronise that stream before returning.
+ *  - Every entry point returns an mg_status and never aborts the process.
+ *    mg_status_str() names a status; mg_last_error() gives the message of the
+ *    last failure of a context (or of the process, for NULL).
+ *  - Red cells are those with (i + j + k) even (0-based); red is updated first
+ *    (Sec. 2.2, Eqs. rbgs1-rbgs2).
+ */
+#ifndef MG_GB300_H
+#define MG_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_ARG = 1,           /* invalid argument (sizes, kinds, null pointers)     */
+  MG_ERR_OOM = 2,           /* device or host allocation failed / over budget     */
+  MG_ERR_CUDA = 3,          /* a CUDA call failed; see mg_last_error()            */
+  MG_ERR_NOT_CONVERGED = 4, /* tolerance not met within max_cycles or it stalled  */
+  MG_ERR_DIVERGED = 5,      /* NaN/Inf, or the defect grew tenfold                */
+  MG_ERR_TIMEOUT = 6,       /* a bounded device wait ran out                      */
+  MG_ERR_BUSY = 7           /* the resource is in use (server full)               */
+} mg_status;
+
+/* Boundary kinds (Sec. 2.3.6).  Periodic and zero-gradient ghosts copy cell
+ * centres; fixed and open ghosts are 2 b - (adjacent active cell), so that the
+ * value on the domain surface equals b (a constant for FIXED, the multipole
+ * potential of App. A for OPEN).  Coarse correction levels use the
+ * homogeneous counterpart (periodic, zero fixed, zero gradient). */
+typedef enum { MG_BC_PERIODIC = 0, MG_BC_FIXED = 1, MG_BC_ZEROGRAD = 2, MG_BC_OPEN = 3 } mg_bc;
+
+/* Arithmetic of a solve.  FP64: every step in double.  MIXED: an FP64
+ * defect-correction loop (outer residual, correction update, source,
+ * multipole moments and boundary values in double) around FP32 multigrid
+ * solves of the correction equation. */
+typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
+
+typedef struct {
+  int prec;           /* mg_precision; default MG_FP64                             */
+  int mode_fmg;       /* 1: FMG start (Algorithm 2); 0: MGI, phi_dev holds the      */
+                      /*    initial guess (Sec. 2.3.7).  Default 1                  */
+  int pre, post;      /* V(M,N) smoothing steps, each in {0,1,2}; default 1, 1      */
+  double omega;       /* SOR over-relaxation (Sec. 2.3.2); default 1.15             */
+  int max_cycles;     /* V-cycles (FP64) or outer iterations (MIXED); default 50    */
+  double fixed_value; /* b for MG_BC_FIXED; default 0                               */
+  int lmax;           /* multipole order for MG_BC_OPEN, 0..4 (App. A); default 4   */
+  int use_com;        /* 1: expansion about the centre of mass (default); 0: origin */
+  double origin[3];   /* expansion origin when use_com = 0                          */
+  double stall_ratio; /* stop when d_n > stall_ratio * d_{n-1} twice; default 0.9   */
+  int inner_fmg;      /* MIXED: start each inner FP32 solve with FMG (default 1)    */
+  int inner_cycles;   /* MIXED: FP32 V-cycles per outer iteration after the start;  */
+                      /*    default 3                                               */
+  int reserved[8];    /* must be zero                                               */
+} mg_opts;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Fill *opts with the defaults listed above. */
+void mg_opts_init(mg_opts *opts);
+
+/* Create a solver for an nx*ny*nz grid of spacing dx with boundary kind bc.
+ * Each dimension must be a power of two >= 2; this version requires
+ * nx == ny == nz (the coarsest level is then one cell, Sec. 2.3.2).  The
+ * level hierarchy (N_l = N / 2^(L-1-l), L = log2 N + 1 levels, Sec. 3.2.1) and
+ * all scratch are allocated on the current device here.  opts may be NULL
+ * for defaults; it is copied.  On success *ctx owns the device memory until
+ * mg_destroy.  Errors: MG_ERR_ARG (sizes, kinds, options), MG_ERR_OOM,
+ * MG_ERR_CUDA. */
+mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts *opts,
+                    mg_ctx **ctx);
+
+/* Solve for phi given rho: f = four_pi_G * rho; for periodic and
+ * zero-gradient grids the mean of f is removed and the returned phi has zero
+ * mean (Sec. 2.3.6); for open grids phi -> 0 at infinity.  rho_dev and
+ * phi_dev are FP64 nx*ny*nz device arrays; phi_dev is the initial guess in
+ * MGI mode and is overwritten with the result.  Iteration stops when
+ * ||d||/||f|| < tol (RMS norms over the finest level, Eq. threshold); tol = 0
+ * iterates until the reduction stalls (Sec. 2.3.7).
+ * hist (host, capacity hist_cap >= 1) receives ||d||/||f|| after the FMG
+ * sweep (FP64) or after the first outer iteration (MIXED), then after each
+ * further V-cycle / outer iteration; *n_hist is the count written.
+ * Returns MG_OK, MG_ERR_NOT_CONVERGED (phi still holds the last iterate),
+ * MG_ERR_DIVERGED, MG_ERR_ARG, MG_ERR_CUDA.  Synchronises `stream`. */
+mg_status mg_solve(mg_ctx *ctx, const double *rho_dev, double four_pi_G, double tol,
+                   double *phi_dev, double *hist, int hist_cap, int *n_hist, void *stream);
+
+/* Same as mg_solve with rho and phi in HOST memory (phi read as the initial
+ * guess in MGI mode): the host-to-device copy of rho (and phi), the solve and
+ * the device-to-host copy of phi all run on `stream` inside the call. */
+mg_status mg_solve_host(mg_ctx *ctx, const double *rho, double four_pi_G, double tol,
+                        double *phi, double *hist, int hist_cap, int *n_hist, void *stream);
+
+/* Release the context and its device memory.  NULL is accepted. */
+mg_status mg_destroy(mg_ctx *ctx);
+
+/* Bytes of device memory the context holds. */
+size_t mg_ctx_device_bytes(const mg_ctx *ctx);
+
+/* Number of kernel launches issued by the last mg_solve / mg_solve_host of
+ * this context. */
+long long mg_ctx_last_launches(const mg_ctx *ctx);
+
+/* Kernel classes for per-kernel timing of finest-level launches. */
+typedef enum {
+  MG_K_SOR = 0,             /* one colour of the smoother                         */
+  MG_K_DEFECT_RESTRICT = 1, /* fused defect + restriction                         */
+  MG_K_PROLONG = 2,         /* trilinear prolongation + correction                */
+  MG_K_FMG_PROLONG = 3,     /* FMG prolongation I'                                */
+  MG_K_DEFECT_NORM = 4,     /* FP64 defect norm of the stopping test              */
+  MG_K_OUTER_RESIDUAL = 5,  /* MIXED: FP64 residual -> FP32                       */
+  MG_K_CORRECT = 6,         /* MIXED: FP64 correction update                      */
+  MG_K_SOURCE = 7,          /* f = 4 pi G rho and its sums                         */
+  MG_K_COUNT = 8
+} mg_kernel;
+
+/* Enable (on = 1) or disable per-kernel timing: every finest-level launch of
+ * a later solve is bracketed by CUDA events on the solve's stream and its
+ * duration added to its class.  Enabling resets the totals. */
+mg_status mg_ctx_set_timing(mg_ctx *ctx, int on);
+
+/* Total milliseconds and launch count of kernel class k since timing was
+ * enabled. */
+mg_status mg_ctx_kernel_time(const mg_ctx *ctx, int k, double *total_ms, long long *launches);
+
+const char *mg_status_str(mg_status s);
+const char *mg_last_error(const mg_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Single-step operators on one level, for testing each kernel on its own.
+ * u_dev, f_dev, d_dev are nx*ny*nz device arrays of the precision `prec`
+ * (MG_FP64: double, MG_MIXED: float).  bc and bc_value as above; for
+ * MG_BC_OPEN, faces_dev holds the boundary value at every face point of the
+ * level: faces 0..5 (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) in turn, face 0/1
+ * indexed [k][j] with k, j in 0..nz+1, 0..ny+1 (index 0 and n+1 are the
+ * extended points used by edge and corner ghosts), faces 2/3 [k][i], faces
+ * 4/5 [j][i]; it is always FP64.  Edge and corner ghosts apply the face rule
+ * along x, then y, then z.  Each returns after the work is queued on stream.
+ * ---------------------------------------------------------------------- */
+
+/* `steps` SMOOTH applications (Eqs. rbsor1-rbsor2): colours 0 = red then
+ * black per step, 1 = red half-sweep only, 2 = black half-sweep only. */
+mg_status mg_op_smooth(int prec, int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
+                       const double *faces_dev, double omega, int steps, int colours,
+                       void *u_dev, const void *f_dev, void *stream);
+
+/* d = f - L_h u (Eq. defect). */
+mg_status mg_op_defect(int prec, int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
+                       const double *faces_dev, const void *u_dev, const void *f_dev,
+                       void *d_dev, void *stream);
+
+/* Fused defect + restriction: fc = I_l^{l-1}(f - L_h u) on the
+ * (nx/2)*(ny/2)*(nz/2) coarse grid (Algorithm 1, steps 2-3). */
+mg_status mg_op_defect_restrict(int prec, int nx, int ny, int nz, double h, mg_bc bc,
+                                double bc_value, const double *faces_dev, const void *u_dev,
+                                const void *f_dev, void *fc_dev, void *stream);
+
+/* uc = I_l^{l-1} uf: mean of each 2x2x2 block (Eq. restriction); nx, ny, nz
+ * are the fine sizes. */
+mg_status mg_op_restrict(int prec, int nx, int ny, int nz, const void *uf_dev, void *uc_dev,
+                         void *stream);
+
+/* Prolongation of the coarse (nx/2)*(ny/2)*(nz/2) array uc to the fine grid,
+ * with coarse ghosts from (bc, bc_value, coarse faces_dev):
+ * high_order = 0: trilinear (Eq. trilinear); 1: FMG operator I' (weights
+ * 5/32, 30/32, -3/32).  add = 1: uf += I uc (correction); 0: uf = I uc. */
+mg_status mg_op_prolong(int prec, int nx, int ny, int nz, mg_bc bc, double bc_value,
+                        const double *coarse_faces_dev, int high_order, int add,
+                        const void *uc_dev, void *uf_dev, void *stream);
+
+/* COARSEST (Sec. 2.3.2) on a 1x1x1 level from a zero guess: the 1-cell
+ * equation solved exactly with its ghosts; 0 for periodic / zero gradient. */
+mg_status mg_op_coarsest(int prec, double h, mg_bc bc, double bc_value, const double *faces_dev,
+                         const void *f_dev, void *u_dev, void *stream);
+
+/* Multipole moments of rho_dev (FP64, nx*ny*nz, spacing h) for App. A:
+ * Q_host receives (lmax+1)^2 moments ordered l*l + (m + l) (25 slots are
+ * written, zero above lmax); origin_host is the expansion origin on input
+ * (use_com = 0) or receives the centre of mass (use_com = 1; kept as given
+ * when the total mass is 0).  Synchronises `stream`. */
+mg_status mg_op_multipole_moments(int nx, int ny, int nz, double h, const double *rho_dev,
+                                  int lmax, int use_com, double *origin_host, double *Q_host,
+                                  void *stream);
+
+/* Multipole boundary potential -G sum Q_lm sqrt(4 pi/(2l+1)) Y_lm / r^(l+1)
+ * (App. A) at every face point of an nx*ny*nz level of spacing h, in the
+ * faces layout described above.  Q_host and origin_host as returned by
+ * mg_op_multipole_moments. */
+mg_status mg_op_open_faces(int nx, int ny, int nz, double h, const double *Q_host, int lmax,
+                           double G, const double *origin_host, double *faces_dev, void *stream);
+
+/* Number of doubles in a faces array of an nx*ny*nz level. */
+size_t mg_faces_count(int nx, int ny, int nz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_GB300_H */

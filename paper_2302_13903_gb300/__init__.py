@@ -1,0 +1,318 @@
+"""GB300 geometric-multigrid Poisson solver (Tomida & Stone 2023, Sec. 2-3).
+
+Thin ctypes binding over the C ABI declared in ``include/mg.h``.  Every step
+of a solve runs in the CUDA library ``_build/libmg_gb300.so``; this module only
+marshals arguments (torch tensors give device pointers and streams).  There
+is no CPU fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+PERIODIC, FIXED, ZEROGRAD, OPEN = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+STATUS = {0: "MG_OK", 1: "MG_ERR_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR_CUDA",
+          4: "MG_ERR_NOT_CONVERGED", 5: "MG_ERR_DIVERGED", 6: "MG_ERR_TIMEOUT", 7: "MG_ERR_BUSY"}
+
+# Every symbol include/mg.h declares (checked by the ABI test).
+EXPORTS = [
+    "mg_opts_init", "mg_create", "mg_solve", "mg_solve_host", "mg_destroy",
+    "mg_ctx_device_bytes", "mg_ctx_last_launches", "mg_status_str", "mg_last_error",
+    "mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict", "mg_op_prolong",
+    "mg_op_coarsest", "mg_op_multipole_moments", "mg_op_open_faces", "mg_faces_count",
+    "mg_ctx_set_timing", "mg_ctx_kernel_time",
+]
+KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
+           "correct", "source"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("prec", ctypes.c_int), ("mode_fmg", ctypes.c_int), ("pre", ctypes.c_int),
+        ("post", ctypes.c_int), ("omega", ctypes.c_double), ("max_cycles", ctypes.c_int),
+        ("fixed_value", ctypes.c_double), ("lmax", ctypes.c_int), ("use_com", ctypes.c_int),
+        ("origin", ctypes.c_double * 3), ("stall_ratio", ctypes.c_double),
+        ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+            L = ctypes.CDLL(_build.LIB)
+            i, d, p, sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+            L.mg_opts_init.argtypes = [ctypes.POINTER(Opts)]
+            L.mg_opts_init.restype = None
+            L.mg_create.argtypes = [i, i, i, d, i, ctypes.POINTER(Opts), ctypes.POINTER(p)]
+            L.mg_create.restype = i
+            L.mg_solve.argtypes = [p, p, d, d, p, p, i, ctypes.POINTER(i), p]
+            L.mg_solve.restype = i
+            L.mg_solve_host.argtypes = [p, p, d, d, p, p, i, ctypes.POINTER(i), p]
+            L.mg_solve_host.restype = i
+            L.mg_destroy.argtypes = [p]
+            L.mg_destroy.restype = i
+            L.mg_ctx_device_bytes.argtypes = [p]
+            L.mg_ctx_device_bytes.restype = sz
+            L.mg_ctx_last_launches.argtypes = [p]
+            L.mg_ctx_last_launches.restype = ctypes.c_longlong
+            L.mg_status_str.argtypes = [i]
+            L.mg_status_str.restype = ctypes.c_char_p
+            L.mg_last_error.argtypes = [p]
+            L.mg_last_error.restype = ctypes.c_char_p
+            L.mg_op_smooth.argtypes = [i, i, i, i, d, i, d, p, d, i, i, p, p, p]
+            L.mg_op_defect.argtypes = [i, i, i, i, d, i, d, p, p, p, p, p]
+            L.mg_op_defect_restrict.argtypes = [i, i, i, i, d, i, d, p, p, p, p, p]
+            L.mg_op_restrict.argtypes = [i, i, i, i, p, p, p]
+            L.mg_op_prolong.argtypes = [i, i, i, i, i, d, p, i, i, p, p, p]
+            L.mg_op_coarsest.argtypes = [i, d, i, d, p, p, p, p]
+            L.mg_op_multipole_moments.argtypes = [i, i, i, d, p, i, i, p, p, p]
+            L.mg_op_open_faces.argtypes = [i, i, i, d, p, i, d, p, p, p]
+            for name in ("mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict",
+                         "mg_op_prolong", "mg_op_coarsest", "mg_op_multipole_moments",
+                         "mg_op_open_faces"):
+                getattr(L, name).restype = i
+            L.mg_ctx_set_timing.argtypes = [p, i]
+            L.mg_ctx_set_timing.restype = i
+            L.mg_ctx_kernel_time.argtypes = [p, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+            L.mg_ctx_kernel_time.restype = i
+            L.mg_faces_count.argtypes = [i, i, i]
+            L.mg_faces_count.restype = sz
+            _lib = L
+    return _lib
+
+
+def last_error(ctx=None) -> str:
+    return lib().mg_last_error(ctx).decode()
+
+
+def _check(st, ctx=None):
+    if st != 0:
+        raise MGError(st, last_error(ctx))
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().mg_opts_init(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "origin":
+            o.origin[:] = list(v)
+        elif k == "prec" and isinstance(v, str):
+            o.prec = {"fp64": FP64, "mixed": MIXED}[v]
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, f"expected {dtype}, got {t.dtype}"
+    return t.data_ptr()
+
+
+class Solver:
+    """One grid configuration: ``mg_create`` on construction, ``mg_destroy`` on close."""
+
+    def __init__(self, n, dx, bc=PERIODIC, **opts):
+        self.n, self.dx, self.bc = n, dx, bc
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().mg_create(n, n, n, dx, bc, ctypes.byref(self.opts), ctypes.byref(h)))
+        self.ctx = h
+
+    def close(self):
+        if self.ctx:
+            lib().mg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def device_bytes(self):
+        return lib().mg_ctx_device_bytes(self.ctx)
+
+    @property
+    def last_launches(self):
+        return lib().mg_ctx_last_launches(self.ctx)
+
+    def set_timing(self, on=True):
+        _check(lib().mg_ctx_set_timing(self.ctx, int(on)), self.ctx)
+
+    def kernel_times(self):
+        """{kernel class: (total ms, launches)} of finest-level launches."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            ms, n = ctypes.c_double(0), ctypes.c_longlong(0)
+            _check(lib().mg_ctx_kernel_time(self.ctx, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    def solve(self, rho, four_pi_G=1.0, tol=1e-10, phi=None, stream=None, hist_cap=256,
+              raise_on_error=True):
+        """rho: CUDA float64 (n, n, n).  Returns (phi, hist, status)."""
+        import torch
+        if phi is None:
+            phi = torch.zeros_like(rho)
+        hist = np.zeros(hist_cap)
+        nh = ctypes.c_int(0)
+        st = lib().mg_solve(self.ctx, _dptr(rho, torch.float64), four_pi_G, tol,
+                            _dptr(phi, torch.float64), hist.ctypes.data_as(ctypes.c_void_p),
+                            hist_cap, ctypes.byref(nh), _stream_ptr(stream))
+        if raise_on_error and st not in (0, 4):
+            _check(st, self.ctx)
+        return phi, hist[: nh.value].copy(), st
+
+    def solve_host(self, rho, four_pi_G=1.0, tol=1e-10, phi=None, stream=None, hist_cap=256):
+        """rho, phi: host float64 arrays (numpy or pinned torch CPU tensors)."""
+        if phi is None:
+            phi = np.zeros_like(rho)
+        rp = rho.ctypes.data if isinstance(rho, np.ndarray) else rho.data_ptr()
+        pp = phi.ctypes.data if isinstance(phi, np.ndarray) else phi.data_ptr()
+        hist = np.zeros(hist_cap)
+        nh = ctypes.c_int(0)
+        st = lib().mg_solve_host(self.ctx, rp, four_pi_G, tol, pp,
+                                 hist.ctypes.data_as(ctypes.c_void_p), hist_cap,
+                                 ctypes.byref(nh), _stream_ptr(stream))
+        if st not in (0, 4):
+            _check(st, self.ctx)
+        return phi, hist[: nh.value].copy(), st
+
+
+def _prec_of(t):
+    import torch
+    return FP64 if t.dtype == torch.float64 else MIXED
+
+
+def _faces_ptr(faces):
+    import torch
+    return _dptr(faces, torch.float64) if faces is not None else None
+
+
+def op_smooth(u, f, h, bc=PERIODIC, bc_value=0.0, faces=None, omega=1.15, steps=1, colours=0,
+              stream=None):
+    nz, ny, nx = u.shape
+    _check(lib().mg_op_smooth(_prec_of(u), nx, ny, nz, h, bc, bc_value, _faces_ptr(faces), omega,
+                              steps, colours, _dptr(u, u.dtype), _dptr(f, u.dtype),
+                              _stream_ptr(stream)))
+    return u
+
+
+def op_defect(u, f, h, bc=PERIODIC, bc_value=0.0, faces=None, stream=None):
+    import torch
+    nz, ny, nx = u.shape
+    d = torch.empty_like(u)
+    _check(lib().mg_op_defect(_prec_of(u), nx, ny, nz, h, bc, bc_value, _faces_ptr(faces),
+                              _dptr(u, u.dtype), _dptr(f, u.dtype), _dptr(d), _stream_ptr(stream)))
+    return d
+
+
+def op_defect_restrict(u, f, h, bc=PERIODIC, bc_value=0.0, faces=None, stream=None):
+    import torch
+    nz, ny, nx = u.shape
+    fc = torch.empty((nz // 2, ny // 2, nx // 2), dtype=u.dtype, device=u.device)
+    _check(lib().mg_op_defect_restrict(_prec_of(u), nx, ny, nz, h, bc, bc_value, _faces_ptr(faces),
+                                       _dptr(u, u.dtype), _dptr(f, u.dtype), _dptr(fc),
+                                       _stream_ptr(stream)))
+    return fc
+
+
+def op_restrict(uf, stream=None):
+    import torch
+    nz, ny, nx = uf.shape
+    uc = torch.empty((nz // 2, ny // 2, nx // 2), dtype=uf.dtype, device=uf.device)
+    _check(lib().mg_op_restrict(_prec_of(uf), nx, ny, nz, _dptr(uf), _dptr(uc), _stream_ptr(stream)))
+    return uc
+
+
+def op_prolong(uc, bc=PERIODIC, bc_value=0.0, coarse_faces=None, high_order=False, add=False,
+               uf=None, stream=None):
+    import torch
+    nz, ny, nx = (2 * s for s in uc.shape)
+    if uf is None:
+        uf = torch.zeros((nz, ny, nx), dtype=uc.dtype, device=uc.device)
+    _check(lib().mg_op_prolong(_prec_of(uc), nx, ny, nz, bc, bc_value, _faces_ptr(coarse_faces),
+                               int(high_order), int(add), _dptr(uc, uc.dtype), _dptr(uf, uc.dtype),
+                               _stream_ptr(stream)))
+    return uf
+
+
+def op_coarsest(f, h, bc=PERIODIC, bc_value=0.0, faces=None, stream=None):
+    import torch
+    u = torch.zeros_like(f)
+    _check(lib().mg_op_coarsest(_prec_of(f), h, bc, bc_value, _faces_ptr(faces), _dptr(f), _dptr(u),
+                                _stream_ptr(stream)))
+    return u
+
+
+def op_multipole_moments(rho, h, lmax=4, use_com=True, origin=(0.0, 0.0, 0.0), stream=None):
+    import torch
+    nz, ny, nx = rho.shape
+    org = np.array(origin, dtype=np.float64)
+    Q = np.zeros(25)
+    _check(lib().mg_op_multipole_moments(nx, ny, nz, h, _dptr(rho, torch.float64), lmax,
+                                         int(use_com), org.ctypes.data_as(ctypes.c_void_p),
+                                         Q.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+    return Q, org
+
+
+def op_open_faces(n, h, Q, lmax, G, origin, device="cuda", stream=None):
+    import torch
+    cnt = lib().mg_faces_count(n, n, n)
+    faces = torch.empty(cnt, dtype=torch.float64, device=device)
+    Qa = np.ascontiguousarray(Q, dtype=np.float64)
+    org = np.ascontiguousarray(origin, dtype=np.float64)
+    _check(lib().mg_op_open_faces(n, n, n, h, Qa.ctypes.data_as(ctypes.c_void_p), lmax, G,
+                                  org.ctypes.data_as(ctypes.c_void_p), _dptr(faces),
+                                  _stream_ptr(stream)))
+    return faces
+
+
+def faces_count(nx, ny, nz):
+    return lib().mg_faces_count(nx, ny, nz)

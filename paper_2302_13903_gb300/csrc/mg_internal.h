@@ -1,0 +1,121 @@
+// mg_internal.h -- types and kernel launchers shared by the translation units
+// of the multigrid library.  Host-only header: kernels themselves live in the
+// .cu files; this declares what the solver driver may launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+namespace mg {
+
+enum BcKind : int { BC_PERIODIC = 0, BC_FIXED = 1, BC_ZEROGRAD = 2, BC_OPEN = 3 };
+
+// Cells per side of one level.
+struct Grid {
+  int nx, ny, nz;
+  __host__ __device__ long long cells() const { return (long long)nx * ny * nz; }
+};
+
+// Boundary rule of one level as a kernel sees it (Sec. 2.3.6).  OPEN uses the
+// level's face array (layout of mg.h); FIXED uses `value`; the homogeneous
+// counterpart of FIXED/OPEN is FIXED with value 0.
+struct Bc {
+  int kind;
+  double value;
+  const double* faces;
+};
+
+inline Bc homogeneous(const Bc& b) {
+  Bc h{b.kind, 0.0, nullptr};
+  if (b.kind == BC_FIXED || b.kind == BC_OPEN) h.kind = BC_FIXED;
+  return h;
+}
+
+inline size_t faces_count(const Grid& g) {
+  return 2 * (size_t)(g.ny + 2) * (g.nz + 2) + 2 * (size_t)(g.nx + 2) * (g.nz + 2) +
+         2 * (size_t)(g.nx + 2) * (g.ny + 2);
+}
+
+// Launch counter (per thread: a context is not thread-safe, so the driver
+// resets and reads it around one solve on one thread).
+extern thread_local long long g_launches;
+
+// Number of blocks used by the deterministic two-stage reductions for an
+// array of `n` elements; partial buffers need this many doubles.
+int reduce_blocks(long long n);
+constexpr int kMaxReduceBlocks = 1024;
+// Doubles in a context's partial-sum buffer (reductions and moment partials).
+constexpr int kPartials = 16384;
+
+// ---------------------------------------------------------------------------
+// Level kernels, T = float or double.  All return cudaGetLastError().
+
+template <typename T>
+cudaError_t launch_sor(T* u, const T* f, Grid g, double h, Bc bc, double omega, int colour,
+                       cudaStream_t s);
+// Red half-sweep from a zero initial value: writes red = (-omega h^2/6) f and
+// black = 0 (Algorithm 1, coarse levels start from 0).
+template <typename T>
+cudaError_t launch_sor_red_zero(T* u, const T* f, Grid g, double h, double omega,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_defect(const T* u, const T* f, T* d, Grid g, double h, Bc bc,
+                          double* partials, cudaStream_t s);
+template <typename T>
+cudaError_t launch_defect_restrict(const T* u, const T* f, T* fc, Grid g, double h, Bc bc,
+                                   cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(const T* uf, T* uc, Grid gf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong(const T* uc, T* uf, Grid gf, Bc bc_coarse, int high_order, int add,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarsest(const T* f, T* u, double h, Bc bc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fill(T* u, long long n, T v, cudaStream_t s);
+
+// FP64 source: f = four_pi_G * rho, partial sums of f into partials.
+cudaError_t launch_source(const double* rho, double* f, long long n, double four_pi_G,
+                          double* partials, cudaStream_t s);
+// a[i] -= sum(partials[0..nb)) / n  (removes the mean; the sum is formed on
+// the device in a fixed order).
+cudaError_t launch_subtract_mean(double* a, long long n, const double* partials, int nb,
+                                 cudaStream_t s);
+// Partial sums of a[i] (FP64) and of a[i]^2.
+template <typename T>
+cudaError_t launch_sum(const T* a, long long n, int squares, double* partials, cudaStream_t s);
+// out[0] = sum(partials[0..nb)) in a fixed order.
+cudaError_t launch_finish_sum(const double* partials, int nb, double* out, cudaStream_t s);
+
+// Mixed precision outer step (FP64 in, FP32 out): r32 = scale * (f - L_h u),
+// partial sums of (f - L_h u)^2 in FP64.
+cudaError_t launch_outer_residual(const double* u, const double* f, float* r32, Grid g, double h,
+                                  Bc bc, double scale, double* partials, cudaStream_t s);
+// u += inv_scale * e32 (FP64 correction update).
+cudaError_t launch_correct(double* u, const float* e32, long long n, double inv_scale,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Multipole boundary (App. A).
+
+// Upload the polynomial tables to this device's constant memory (once per
+// device; synchronous, so call it outside stream capture).
+cudaError_t prepare_multipole();
+// Raw moments sum rho x^a y^b z^c (a+b+c <= 4, 35 values) about the grid
+// centre, written as per-block partials [nb][35]; returns nb via *nb_out.
+cudaError_t launch_raw_moments(const double* rho, Grid g, double h, double* partials,
+                               int* nb_out, cudaStream_t s);
+// Reduce the partials and form Q_lm (25) and the origin on the device:
+// out[0..25) = Q, out[25..28) = origin, out[28] = total mass.
+cudaError_t launch_moments_finish(const double* partials, int nb, double h, int lmax,
+                                  int use_com, const double* origin_in, double* out,
+                                  cudaStream_t s);
+// Boundary values at every face point of a level from Q and the origin held
+// in `qo` (layout of launch_moments_finish's output).
+cudaError_t launch_open_faces(Grid g, double h, const double* qo, int lmax, double G,
+                              double* faces, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,790 @@
+// mg_solver.cu -- solver context, the FMG / V-cycle driver (FP64 and mixed
+// precision) and the C ABI of include/mg.h.
+//
+// The driver is host code that queues kernels on the caller's stream.  Device
+// data never comes back to the host except the norms the stopping test needs
+// (one 16-byte read per cycle).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+
+using mg::Bc;
+using mg::Grid;
+
+namespace {
+
+thread_local std::string g_err;  // last error of calls without a context
+
+constexpr int kMaxLevels = 16;
+
+}  // namespace
+
+struct mg_ctx {
+  int n = 0;            // cells per side of the finest level
+  int L = 0;            // number of levels; level L-1 is the finest
+  double h = 0.0;       // finest spacing
+  int bc_kind = 0;
+  mg_opts opts{};
+  int device = 0;
+  // FP64 hierarchy (u64[L-1] is the caller's phi during a solve).
+  double* u64[kMaxLevels] = {};
+  double* f64[kMaxLevels] = {};
+  double* faces[kMaxLevels] = {};  // open boundary values per level
+  // FP32 hierarchy (mixed precision).
+  float* u32[kMaxLevels] = {};
+  float* f32[kMaxLevels] = {};
+  double* partials = nullptr;  // reduction partials
+  double* scal = nullptr;      // device scalars: [0] |f|^2 sum, [1] |d|^2 sum, [2..31] multipole
+  double* pinned = nullptr;    // host mirror of scal
+  double* rho_dev_own = nullptr;  // buffers for mg_solve_host
+  double* phi_dev_own = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  long long last_launches = 0;
+  std::string err;
+  // Per-kernel timing of finest-level launches.
+  int timing = 0;
+  std::vector<cudaEvent_t> events;  // pool, used in start/stop pairs
+  std::vector<int> pending_class;   // class of each recorded pair in this solve
+  double kernel_ms[MG_K_COUNT] = {};
+  long long kernel_n[MG_K_COUNT] = {};
+};
+
+namespace {
+
+int level_n(const mg_ctx* c, int l) { return c->n >> (c->L - 1 - l); }
+double level_h(const mg_ctx* c, int l) { return c->h * (double)(1 << (c->L - 1 - l)); }
+Grid level_grid(const mg_ctx* c, int l) {
+  const int n = level_n(c, l);
+  return Grid{n, n, n};
+}
+
+bool is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+struct Fail {
+  mg_status st;
+};
+
+void check(mg_ctx* c, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    if (c) c->err = buf;
+    g_err = buf;
+    throw Fail{MG_ERR_CUDA};
+  }
+}
+
+void fail(mg_ctx* c, mg_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  g_err = msg;
+  throw Fail{st};
+}
+
+template <typename T>
+T* dalloc(mg_ctx* c, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, MG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(p);
+  c->bytes += count * sizeof(T);
+  return static_cast<T*>(p);
+}
+
+Bc physical_bc(const mg_ctx* c, int l) {
+  Bc b{c->bc_kind, c->opts.fixed_value, c->faces[l]};
+  return b;
+}
+
+// Brackets one finest-level launch with events when timing is on.
+struct KTimer {
+  mg_ctx* c;
+  int cls;
+  cudaStream_t s;
+  int slot = -1;
+  KTimer(mg_ctx* c_, int cls_, bool finest, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    if (!c->timing || !finest) return;
+    const size_t k = c->pending_class.size();
+    if (2 * k + 2 > c->events.size()) {
+      if (c->events.size() >= 8192) return;  // pool full: stop timing this solve
+      for (int q = 0; q < 256; ++q) {
+        cudaEvent_t e;
+        check(c, cudaEventCreate(&e), "cudaEventCreate");
+        c->events.push_back(e);
+      }
+    }
+    slot = (int)k;
+    c->pending_class.push_back(cls);
+    check(c, cudaEventRecord(c->events[2 * k], s), "cudaEventRecord");
+  }
+  ~KTimer() {
+    if (slot >= 0) cudaEventRecord(c->events[2 * slot + 1], s);
+  }
+};
+
+// After the solve's stream is synchronised: add the recorded durations.
+void collect_times(mg_ctx* c) {
+  for (size_t k = 0; k < c->pending_class.size(); ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->events[2 * k], c->events[2 * k + 1]) == cudaSuccess) {
+      c->kernel_ms[c->pending_class[k]] += ms;
+      c->kernel_n[c->pending_class[k]] += 1;
+    }
+  }
+  c->pending_class.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Cycles, templated on the level precision.
+
+template <typename T>
+struct Pyr {
+  T** u;
+  T** f;
+};
+
+template <typename T>
+Pyr<T> pyr(mg_ctx* c);
+template <>
+Pyr<double> pyr<double>(mg_ctx* c) { return {c->u64, c->f64}; }
+template <>
+Pyr<float> pyr<float>(mg_ctx* c) { return {c->u32, c->f32}; }
+
+template <typename T>
+void smooth_steps(mg_ctx* c, Pyr<T> P, int l, const Bc& bc, int steps, bool zero_guess,
+                  cudaStream_t s) {
+  const Grid g = level_grid(c, l);
+  const double h = level_h(c, l), om = c->opts.omega;
+  if (zero_guess && steps == 0) {
+    check(c, mg::launch_fill<T>(P.u[l], g.cells(), T(0), s), "fill");
+    return;
+  }
+  const bool fin = (l == c->L - 1);
+  for (int q = 0; q < steps; ++q) {
+    {
+      KTimer t(c, MG_K_SOR, fin, s);
+      if (q == 0 && zero_guess)
+        check(c, mg::launch_sor_red_zero<T>(P.u[l], P.f[l], g, h, om, s), "sor_red_zero");
+      else
+        check(c, mg::launch_sor<T>(P.u[l], P.f[l], g, h, bc, om, 0, s), "sor red");
+    }
+    KTimer t(c, MG_K_SOR, fin, s);
+    check(c, mg::launch_sor<T>(P.u[l], P.f[l], g, h, bc, om, 1, s), "sor black");
+  }
+}
+
+// Algorithm 1 on level l >= 1 with rule bc_top on level l and the homogeneous
+// rule `hom` below.  zero_guess: u_l enters as 0 (coarse corrections).
+template <typename T>
+void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool zero_guess,
+            cudaStream_t s) {
+  const Grid g = level_grid(c, l);
+  const double h = level_h(c, l);
+  const bool fin = (l == c->L - 1);
+  smooth_steps<T>(c, P, l, bc_top, c->opts.pre, zero_guess, s);                        // 1
+  {
+    KTimer t(c, MG_K_DEFECT_RESTRICT, fin, s);
+    check(c, mg::launch_defect_restrict<T>(P.u[l], P.f[l], P.f[l - 1], g, h, bc_top, s),  // 2-3
+          "defect_restrict");
+  }
+  if (l - 1 == 0)
+    check(c, mg::launch_coarsest<T>(P.f[0], P.u[0], level_h(c, 0), hom, s), "coarsest");  // 4.1
+  else
+    vcycle<T>(c, P, l - 1, hom, hom, true, s);                                         // 4.2
+  {
+    KTimer t(c, MG_K_PROLONG, fin, s);
+    check(c, mg::launch_prolong<T>(P.u[l - 1], P.u[l], g, hom, 0, 1, s), "prolong");    // 5-6
+  }
+  smooth_steps<T>(c, P, l, bc_top, c->opts.post, false, s);                            // 7
+}
+
+// Algorithm 2 with rule bcs[l] on every level.
+template <typename T>
+void fmg(mg_ctx* c, Pyr<T> P, const Bc* bcs, const Bc& hom, cudaStream_t s) {
+  for (int l = c->L - 1; l >= 1; --l)
+    check(c, mg::launch_restrict<T>(P.f[l], P.f[l - 1], level_grid(c, l), s), "restrict");
+  check(c, mg::launch_coarsest<T>(P.f[0], P.u[0], level_h(c, 0), bcs[0], s), "coarsest");
+  for (int l = 1; l < c->L; ++l) {
+    {
+      KTimer t(c, MG_K_FMG_PROLONG, l == c->L - 1, s);
+      check(c, mg::launch_prolong<T>(P.u[l - 1], P.u[l], level_grid(c, l), bcs[l - 1], 1, 0, s),
+            "fmg_prolong");
+    }
+    vcycle<T>(c, P, l, bcs[l], hom, false, s);
+  }
+}
+
+// Fixed-order sums of squares -> host.
+double read_scalar(mg_ctx* c, int slot, cudaStream_t s) {
+  check(c, cudaMemcpyAsync(c->pinned + slot, c->scal + slot, sizeof(double),
+                           cudaMemcpyDeviceToHost, s),
+        "read norm");
+  check(c, cudaStreamSynchronize(s), "sync");
+  return c->pinned[slot];
+}
+
+struct StopRule {
+  double tol, stall, d0 = -1.0, prev = -1.0;
+  int stalls = 0;
+  // Returns MG_OK to stop successfully, a failure status to stop, or -1 to go on.
+  int decide(double r, int cycles_done, int max_cycles, int n_hist, int hist_cap) {
+    if (d0 < 0) d0 = r;
+    if (std::isnan(r) || std::isinf(r) || r > 10.0 * d0) return MG_ERR_DIVERGED;
+    if (r < tol) return MG_OK;
+    if (stalls >= 2) return tol == 0.0 ? MG_OK : MG_ERR_NOT_CONVERGED;
+    if (cycles_done >= max_cycles || n_hist >= hist_cap) return MG_ERR_NOT_CONVERGED;
+    return -1;
+  }
+  void record(double r) {
+    if (prev >= 0) stalls = (r > stall * prev) ? stalls + 1 : 0;
+    prev = r;
+  }
+};
+
+// Source, mean removal, norm of f, and the open-boundary values.
+double prepare_source(mg_ctx* c, const double* rho, double four_pi_G, double* f_fin,
+                      bool all_levels_faces, cudaStream_t s) {
+  const int F = c->L - 1;
+  const Grid gf = level_grid(c, F);
+  const long long N = gf.cells();
+  const int nb = mg::reduce_blocks(N);
+  {
+    KTimer t(c, MG_K_SOURCE, true, s);
+    check(c, mg::launch_source(rho, f_fin, N, four_pi_G, c->partials, s), "source");
+  }
+  if (c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD)
+    check(c, mg::launch_subtract_mean(f_fin, N, c->partials, nb, s), "subtract_mean");
+  check(c, mg::launch_sum<double>(f_fin, N, 1, c->partials, s), "sum f^2");
+  check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 0, s), "finish f^2");
+  if (c->bc_kind == MG_BC_OPEN) {
+    int nbm = 0;
+    check(c, mg::launch_raw_moments(rho, gf, c->h, c->partials, &nbm, s), "moments");
+    check(c, mg::launch_moments_finish(c->partials, nbm, c->h, c->opts.lmax, c->opts.use_com,
+                                       c->opts.origin, c->scal + 2, s),
+          "moments_finish");
+    const double G = four_pi_G / (4.0 * 3.14159265358979323846);
+    for (int l = all_levels_faces ? 0 : F; l <= F; ++l)
+      check(c, mg::launch_open_faces(level_grid(c, l), level_h(c, l), c->scal + 2, c->opts.lmax,
+                                     G, c->faces[l], s),
+            "open_faces");
+  }
+  return std::sqrt(read_scalar(c, 0, s) / (double)N);
+}
+
+void remove_mean(mg_ctx* c, double* u, cudaStream_t s) {
+  if (c->bc_kind != MG_BC_PERIODIC && c->bc_kind != MG_BC_ZEROGRAD) return;
+  const long long N = level_grid(c, c->L - 1).cells();
+  check(c, mg::launch_sum<double>(u, N, 0, c->partials, s), "sum phi");
+  check(c, mg::launch_subtract_mean(u, N, c->partials, mg::reduce_blocks(N), s), "phi mean");
+}
+
+double defect_rms(mg_ctx* c, const double* u, const double* f, const Bc& bc, cudaStream_t s) {
+  const int F = c->L - 1;
+  const Grid g = level_grid(c, F);
+  const int nb = mg::reduce_blocks(g.cells());
+  {
+    KTimer t(c, MG_K_DEFECT_NORM, true, s);
+    check(c, mg::launch_defect<double>(u, f, nullptr, g, level_h(c, F), bc, c->partials, s),
+          "defect norm");
+  }
+  check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish d^2");
+  return std::sqrt(read_scalar(c, 1, s) / (double)g.cells());
+}
+
+mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
+                     double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
+  const int F = c->L - 1;
+  c->u64[F] = phi;
+  Pyr<double> P = pyr<double>(c);
+  double fnorm = prepare_source(c, rho, four_pi_G, c->f64[F], true, s);
+  Bc bcs[kMaxLevels];
+  for (int l = 0; l < c->L; ++l) bcs[l] = physical_bc(c, l);
+  const Bc hom = mg::homogeneous(bcs[F]);
+  if (c->opts.mode_fmg) fmg<double>(c, P, bcs, hom, s);
+  double dn = defect_rms(c, phi, c->f64[F], bcs[F], s);
+  if (fnorm == 0.0) fnorm = dn > 0.0 ? dn : 1.0;
+  StopRule rule{tol, c->opts.stall_ratio};
+  int n = 0, st = -1;
+  double r = dn / fnorm;
+  hist[n++] = r;
+  rule.record(r);
+  for (int cyc = 0;; ++cyc) {
+    st = rule.decide(r, cyc, c->opts.max_cycles, n, hist_cap);
+    if (st >= 0) break;
+    vcycle<double>(c, P, F, bcs[F], hom, false, s);
+    r = defect_rms(c, phi, c->f64[F], bcs[F], s) / fnorm;
+    hist[n++] = r;
+    rule.record(r);
+  }
+  remove_mean(c, phi, s);
+  *n_hist = n;
+  c->u64[F] = nullptr;
+  return (mg_status)st;
+}
+
+// FP32 multigrid solve of L e = r (homogeneous rule on every level) into
+// u32[L-1], with r already in f32[L-1].
+void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
+  const int F = c->L - 1;
+  Pyr<float> P = pyr<float>(c);
+  Bc bcs[kMaxLevels];
+  for (int l = 0; l < c->L; ++l) bcs[l] = hom;
+  if (c->opts.inner_fmg) {
+    fmg<float>(c, P, bcs, hom, s);
+  } else {
+    vcycle<float>(c, P, F, hom, hom, true, s);
+  }
+  for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, P, F, hom, hom, false, s);
+}
+
+mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
+                      double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
+  const int F = c->L - 1;
+  const Grid g = level_grid(c, F);
+  const long long N = g.cells();
+  const int nb = mg::reduce_blocks(N);
+  double* f = c->f64[F];
+  double fnorm = prepare_source(c, rho, four_pi_G, f, false, s);
+  const Bc bc = physical_bc(c, F);
+  const Bc hom = mg::homogeneous(bc);
+  if (c->opts.mode_fmg) check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
+  // r = f - L phi, scaled into FP32 so that its RMS is about 1.
+  double scale = fnorm > 0.0 ? 1.0 / fnorm : 1.0;
+  check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
+        "outer residual");
+  check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
+  double rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
+  if (fnorm == 0.0) {
+    fnorm = rn > 0.0 ? rn : 1.0;
+    scale = 1.0 / fnorm;
+    if (rn > 0.0) {
+      check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
+            "outer residual");
+    }
+  }
+  StopRule rule{tol, c->opts.stall_ratio};
+  int n = 0, st = -1;
+  for (int it = 0;; ++it) {
+    if (rn == 0.0) {  // exact already (zero source with a homogeneous rule)
+      hist[n++] = 0.0;
+      st = MG_OK;
+      break;
+    }
+    inner_solve(c, hom, s);
+    {
+      KTimer t(c, MG_K_CORRECT, true, s);
+      check(c, mg::launch_correct(phi, c->u32[F], N, 1.0 / scale, s), "correct");
+    }
+    scale = 1.0 / rn;  // the next residual is scaled by the current one's size
+    {
+      KTimer t(c, MG_K_OUTER_RESIDUAL, true, s);
+      check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
+            "outer residual");
+    }
+    check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
+    rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
+    const double r = rn / fnorm;
+    hist[n++] = r;
+    rule.record(r);
+    st = rule.decide(r, it + 1, c->opts.max_cycles, n, hist_cap);
+    if (st >= 0) break;
+  }
+  remove_mean(c, phi, s);
+  *n_hist = n;
+  return (mg_status)st;
+}
+
+mg_status validate_opts(const mg_opts& o) {
+  if (o.prec != MG_FP64 && o.prec != MG_MIXED) return MG_ERR_ARG;
+  if (o.pre < 0 || o.pre > 2 || o.post < 0 || o.post > 2 || o.pre + o.post == 0) return MG_ERR_ARG;
+  if (!(o.omega > 0.0 && o.omega < 2.0)) return MG_ERR_ARG;
+  if (o.max_cycles < 0 || o.lmax < 0 || o.lmax > 4) return MG_ERR_ARG;
+  if (o.inner_cycles < 0 || o.inner_cycles > 64) return MG_ERR_ARG;
+  if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
+  for (int r : o.reserved)
+    if (r != 0) return MG_ERR_ARG;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_opts_init(mg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->prec = MG_FP64;
+  o->mode_fmg = 1;
+  o->pre = 1;
+  o->post = 1;
+  o->omega = 1.15;
+  o->max_cycles = 50;
+  o->fixed_value = 0.0;
+  o->lmax = 4;
+  o->use_com = 1;
+  o->stall_ratio = 0.9;
+  o->inner_fmg = 1;
+  o->inner_cycles = 3;
+}
+
+const char* mg_status_str(mg_status s) {
+  switch (s) {
+    case MG_OK: return "MG_OK";
+    case MG_ERR_ARG: return "MG_ERR_ARG";
+    case MG_ERR_OOM: return "MG_ERR_OOM";
+    case MG_ERR_CUDA: return "MG_ERR_CUDA";
+    case MG_ERR_NOT_CONVERGED: return "MG_ERR_NOT_CONVERGED";
+    case MG_ERR_DIVERGED: return "MG_ERR_DIVERGED";
+    case MG_ERR_TIMEOUT: return "MG_ERR_TIMEOUT";
+    case MG_ERR_BUSY: return "MG_ERR_BUSY";
+  }
+  return "MG_ERR_UNKNOWN";
+}
+
+const char* mg_last_error(const mg_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+size_t mg_ctx_device_bytes(const mg_ctx* c) { return c ? c->bytes : 0; }
+
+long long mg_ctx_last_launches(const mg_ctx* c) { return c ? c->last_launches : 0; }
+
+mg_status mg_ctx_set_timing(mg_ctx* c, int on) {
+  if (!c) return MG_ERR_ARG;
+  c->timing = on ? 1 : 0;
+  for (int k = 0; k < MG_K_COUNT; ++k) {
+    c->kernel_ms[k] = 0.0;
+    c->kernel_n[k] = 0;
+  }
+  return MG_OK;
+}
+
+mg_status mg_ctx_kernel_time(const mg_ctx* c, int k, double* total_ms, long long* launches) {
+  if (!c || k < 0 || k >= MG_K_COUNT || !total_ms || !launches) return MG_ERR_ARG;
+  *total_ms = c->kernel_ms[k];
+  *launches = c->kernel_n[k];
+  return MG_OK;
+}
+
+mg_status mg_destroy(mg_ctx* c) {
+  if (!c) return MG_OK;
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+  return MG_OK;
+}
+
+mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* opts,
+                    mg_ctx** out) {
+  if (!out) {
+    g_err = "mg_create: ctx is NULL";
+    return MG_ERR_ARG;
+  }
+  *out = nullptr;
+  mg_opts o;
+  if (opts) o = *opts;
+  else mg_opts_init(&o);
+  if (!is_pow2(nx) || nx < 2 || nx != ny || nx != nz || !(dx > 0.0) || (int)bc < 0 ||
+      (int)bc > 3 || validate_opts(o) != MG_OK) {
+    g_err = "mg_create: invalid argument (cubic power-of-two grid >= 2, dx > 0, bc, opts)";
+    return MG_ERR_ARG;
+  }
+  mg_ctx* c = new mg_ctx;
+  try {
+    c->n = nx;
+    c->h = dx;
+    c->bc_kind = (int)bc;
+    c->opts = o;
+    int L = 1;
+    while ((nx >> (L - 1)) > 1) ++L;
+    if (L > kMaxLevels) fail(c, MG_ERR_ARG, "mg_create: grid too large");
+    c->L = L;
+    check(c, cudaGetDevice(&c->device), "cudaGetDevice");
+    if (bc == MG_BC_OPEN) check(c, mg::prepare_multipole(), "multipole tables");
+    const int F = L - 1;
+    for (int l = 0; l < L; ++l) {
+      const long long cells = level_grid(c, l).cells();
+      if (o.prec == MG_FP64) {
+        if (l < F) c->u64[l] = dalloc<double>(c, cells);
+        c->f64[l] = dalloc<double>(c, cells);
+        if (bc == MG_BC_OPEN) c->faces[l] = dalloc<double>(c, mg::faces_count(level_grid(c, l)));
+      } else {
+        c->u32[l] = dalloc<float>(c, cells);
+        c->f32[l] = dalloc<float>(c, cells);
+      }
+    }
+    if (o.prec == MG_MIXED) {
+      c->f64[F] = dalloc<double>(c, level_grid(c, F).cells());
+      if (bc == MG_BC_OPEN) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
+    }
+    c->partials = dalloc<double>(c, mg::kPartials);
+    c->scal = dalloc<double>(c, 64);
+    check(c, cudaMallocHost(&c->pinned, 64 * sizeof(double)), "cudaMallocHost");
+  } catch (const Fail& f) {
+    mg_destroy(c);
+    return f.st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
+                   double* hist, int hist_cap, int* n_hist, void* stream) {
+  if (!c) {
+    g_err = "mg_solve: ctx is NULL";
+    return MG_ERR_ARG;
+  }
+  if (!rho || !phi || !hist || hist_cap < 1 || !n_hist || !(tol >= 0.0) ||
+      !std::isfinite(four_pi_G)) {
+    c->err = "mg_solve: invalid argument";
+    return MG_ERR_ARG;
+  }
+  *n_hist = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  mg::g_launches = 0;
+  mg_status st;
+  try {
+    check(c, cudaSetDevice(c->device), "cudaSetDevice");
+    if (c->opts.prec == MG_FP64)
+      st = solve_fp64(c, rho, four_pi_G, tol, phi, hist, hist_cap, n_hist, s);
+    else
+      st = solve_mixed(c, rho, four_pi_G, tol, phi, hist, hist_cap, n_hist, s);
+    check(c, cudaStreamSynchronize(s), "sync");
+    collect_times(c);
+  } catch (const Fail& f) {
+    st = f.st;
+    cudaStreamSynchronize(s);
+    c->pending_class.clear();
+  }
+  c->last_launches = mg::g_launches;
+  return st;
+}
+
+mg_status mg_solve_host(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
+                        double* hist, int hist_cap, int* n_hist, void* stream) {
+  if (!c || !rho || !phi) {
+    g_err = "mg_solve_host: invalid argument";
+    return MG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)level_grid(c, c->L - 1).cells() * sizeof(double);
+  try {
+    check(c, cudaSetDevice(c->device), "cudaSetDevice");
+    if (!c->rho_dev_own) c->rho_dev_own = dalloc<double>(c, bytes / sizeof(double));
+    if (!c->phi_dev_own) c->phi_dev_own = dalloc<double>(c, bytes / sizeof(double));
+    check(c, cudaMemcpyAsync(c->rho_dev_own, rho, bytes, cudaMemcpyHostToDevice, s), "H2D rho");
+    if (!c->opts.mode_fmg)
+      check(c, cudaMemcpyAsync(c->phi_dev_own, phi, bytes, cudaMemcpyHostToDevice, s), "H2D phi");
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  mg_status st =
+      mg_solve(c, c->rho_dev_own, four_pi_G, tol, c->phi_dev_own, hist, hist_cap, n_hist, stream);
+  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+  try {
+    check(c, cudaMemcpyAsync(phi, c->phi_dev_own, bytes, cudaMemcpyDeviceToHost, s), "D2H phi");
+    check(c, cudaStreamSynchronize(s), "sync");
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// Single-step operators.
+
+size_t mg_faces_count(int nx, int ny, int nz) { return mg::faces_count(Grid{nx, ny, nz}); }
+
+}  // extern "C"
+
+namespace {
+
+bool op_args_ok(int prec, int nx, int ny, int nz, int bc, const double* faces) {
+  if (prec != MG_FP64 && prec != MG_MIXED) return false;
+  if (nx < 1 || ny < 1 || nz < 1 || bc < 0 || bc > 3) return false;
+  if (bc == MG_BC_OPEN && !faces) return false;
+  return true;
+}
+
+mg_status op_result(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MG_OK;
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return MG_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t do_smooth(int nx, int ny, int nz, double h, Bc bc, double omega, int steps,
+                      int colours, void* u, const void* f, cudaStream_t s) {
+  const Grid g{nx, ny, nz};
+  for (int q = 0; q < steps; ++q) {
+    if (colours == 0 || colours == 1) {
+      cudaError_t e = mg::launch_sor<T>((T*)u, (const T*)f, g, h, bc, omega, 0, s);
+      if (e != cudaSuccess) return e;
+    }
+    if (colours == 0 || colours == 2) {
+      cudaError_t e = mg::launch_sor<T>((T*)u, (const T*)f, g, h, bc, omega, 1, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_op_smooth(int prec, int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
+                       const double* faces, double omega, int steps, int colours, void* u,
+                       const void* f, void* stream) {
+  if (!op_args_ok(prec, nx, ny, nz, bc, faces) || !u || !f || nx % 2 || steps < 0 ||
+      colours < 0 || colours > 2) {
+    g_err = "mg_op_smooth: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, bc_value, faces};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == MG_FP64 ? do_smooth<double>(nx, ny, nz, h, b, omega, steps, colours, u, f, s)
+                                  : do_smooth<float>(nx, ny, nz, h, b, omega, steps, colours, u, f, s);
+  return op_result(e, "smooth");
+}
+
+mg_status mg_op_defect(int prec, int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
+                       const double* faces, const void* u, const void* f, void* d, void* stream) {
+  if (!op_args_ok(prec, nx, ny, nz, bc, faces) || !u || !f || !d) {
+    g_err = "mg_op_defect: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, bc_value, faces};
+  const Grid g{nx, ny, nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e =
+      prec == MG_FP64
+          ? mg::launch_defect<double>((const double*)u, (const double*)f, (double*)d, g, h, b, nullptr, s)
+          : mg::launch_defect<float>((const float*)u, (const float*)f, (float*)d, g, h, b, nullptr, s);
+  return op_result(e, "defect");
+}
+
+mg_status mg_op_defect_restrict(int prec, int nx, int ny, int nz, double h, mg_bc bc,
+                                double bc_value, const double* faces, const void* u, const void* f,
+                                void* fc, void* stream) {
+  if (!op_args_ok(prec, nx, ny, nz, bc, faces) || !u || !f || !fc || nx % 2 || ny % 2 || nz % 2) {
+    g_err = "mg_op_defect_restrict: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, bc_value, faces};
+  const Grid g{nx, ny, nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == MG_FP64
+                      ? mg::launch_defect_restrict<double>((const double*)u, (const double*)f,
+                                                           (double*)fc, g, h, b, s)
+                      : mg::launch_defect_restrict<float>((const float*)u, (const float*)f,
+                                                          (float*)fc, g, h, b, s);
+  return op_result(e, "defect_restrict");
+}
+
+mg_status mg_op_restrict(int prec, int nx, int ny, int nz, const void* uf, void* uc, void* stream) {
+  if ((prec != MG_FP64 && prec != MG_MIXED) || nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 ||
+      nz % 2 || !uf || !uc) {
+    g_err = "mg_op_restrict: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Grid g{nx, ny, nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == MG_FP64 ? mg::launch_restrict<double>((const double*)uf, (double*)uc, g, s)
+                                  : mg::launch_restrict<float>((const float*)uf, (float*)uc, g, s);
+  return op_result(e, "restrict");
+}
+
+mg_status mg_op_prolong(int prec, int nx, int ny, int nz, mg_bc bc, double bc_value,
+                        const double* coarse_faces, int high_order, int add, const void* uc,
+                        void* uf, void* stream) {
+  if (!op_args_ok(prec, nx, ny, nz, bc, coarse_faces) || nx % 2 || ny % 2 || nz % 2 || !uc || !uf) {
+    g_err = "mg_op_prolong: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, bc_value, coarse_faces};
+  const Grid g{nx, ny, nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == MG_FP64
+                      ? mg::launch_prolong<double>((const double*)uc, (double*)uf, g, b, high_order,
+                                                   add, s)
+                      : mg::launch_prolong<float>((const float*)uc, (float*)uf, g, b, high_order,
+                                                  add, s);
+  return op_result(e, "prolong");
+}
+
+mg_status mg_op_coarsest(int prec, double h, mg_bc bc, double bc_value, const double* faces,
+                         const void* f, void* u, void* stream) {
+  if (!op_args_ok(prec, 1, 1, 1, bc, faces) || !f || !u) {
+    g_err = "mg_op_coarsest: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, bc_value, faces};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == MG_FP64 ? mg::launch_coarsest<double>((const double*)f, (double*)u, h, b, s)
+                                  : mg::launch_coarsest<float>((const float*)f, (float*)u, h, b, s);
+  return op_result(e, "coarsest");
+}
+
+mg_status mg_op_multipole_moments(int nx, int ny, int nz, double h, const double* rho, int lmax,
+                                  int use_com, double* origin, double* Q, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || !rho || !origin || !Q || lmax < 0 || lmax > 4) {
+    g_err = "mg_op_multipole_moments: invalid argument";
+    return MG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* buf = nullptr;
+  double* host = nullptr;
+  cudaError_t e = mg::prepare_multipole();
+  if (e == cudaSuccess) e = cudaMallocAsync(&buf, (mg::kPartials + 64) * sizeof(double), s);
+  if (e != cudaSuccess) return op_result(e, "multipole_moments");
+  int nb = 0;
+  e = mg::launch_raw_moments(rho, Grid{nx, ny, nz}, h, buf, &nb, s);
+  if (e == cudaSuccess)
+    e = mg::launch_moments_finish(buf, nb, h, lmax, use_com, origin, buf + mg::kPartials, s);
+  if (e == cudaSuccess) e = cudaMallocHost(&host, 32 * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, buf + mg::kPartials, 29 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    std::memcpy(Q, host, 25 * sizeof(double));
+    std::memcpy(origin, host + 25, 3 * sizeof(double));
+  }
+  cudaFreeAsync(buf, s);
+  cudaStreamSynchronize(s);
+  if (host) cudaFreeHost(host);
+  return op_result(e, "multipole_moments");
+}
+
+mg_status mg_op_open_faces(int nx, int ny, int nz, double h, const double* Q, int lmax, double G,
+                           const double* origin, double* faces, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || !Q || !origin || !faces || lmax < 0 || lmax > 4) {
+    g_err = "mg_op_open_faces: invalid argument";
+    return MG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* qo = nullptr;
+  cudaError_t e = mg::prepare_multipole();
+  if (e == cudaSuccess) e = cudaMallocAsync(&qo, 32 * sizeof(double), s);
+  if (e != cudaSuccess) return op_result(e, "open_faces");
+  double tmp[28];
+  std::memcpy(tmp, Q, 25 * sizeof(double));
+  std::memcpy(tmp + 25, origin, 3 * sizeof(double));
+  e = cudaMemcpyAsync(qo, tmp, 28 * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = mg::launch_open_faces(Grid{nx, ny, nz}, h, qo, lmax, G, faces, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // tmp is on the stack
+  cudaFreeAsync(qo, s);
+  return op_result(e, "open_faces");
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/mg.h declares.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import paper_2302_13903_gb300 as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(mg_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = mg.lib()
+    declared = declared_functions()
+    assert declared, "no declarations found"
+    assert declared == set(mg.EXPORTS), declared ^ set(mg.EXPORTS)
+    for name in declared:
+        assert hasattr(L, name), name
+    raw = ctypes.CDLL(mg.library_path())
+    for name in declared:
+        getattr(raw, name)
+
+
+def test_built_for_sm_103a_only():
+    assert mg._build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(mg.library_path())
+
+
+def test_default_options_layout():
+    o = mg.default_opts()
+    assert (o.prec, o.mode_fmg, o.pre, o.post) == (0, 1, 1, 1)
+    assert o.omega == 1.15 and o.max_cycles == 50 and o.lmax == 4 and o.use_com == 1
+    assert o.stall_ratio == 0.9 and o.inner_fmg == 1 and o.inner_cycles == 3
+    assert list(o.reserved) == [0] * 8
+
+
+def test_status_strings_and_faces_count():
+    L = mg.lib()
+    for code, name in mg.STATUS.items():
+        assert L.mg_status_str(code).decode() == name
+    n = 8
+    assert L.mg_faces_count(n, n, n) == 6 * (n + 2) ** 2
+    assert L.mg_faces_count(4, 8, 2) == 2 * 10 * 4 + 2 * 6 * 4 + 2 * 6 * 10
+
+
+def test_argument_validation_needs_no_gpu():
+    L = mg.lib()
+    h = ctypes.c_void_p()
+    o = mg.default_opts()
+    for args in [(12, 12, 12, 0.1, 0), (8, 8, 4, 0.1, 0), (8, 8, 8, -1.0, 0), (8, 8, 8, 0.1, 7),
+                 (1, 1, 1, 0.1, 0)]:
+        assert L.mg_create(*args, ctypes.byref(o), ctypes.byref(h)) == 1
+        assert not h.value
+    bad = mg.default_opts(pre=3)
+    assert L.mg_create(8, 8, 8, 0.1, 0, ctypes.byref(bad), ctypes.byref(h)) == 1
+    bad = mg.default_opts(omega=2.5)
+    assert L.mg_create(8, 8, 8, 0.1, 0, ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert L.mg_solve(None, None, 1.0, 1e-10, None, None, 1, None, None) == 1
+    assert L.mg_destroy(None) == 0
+    assert L.mg_op_smooth(0, 8, 8, 8, 0.1, 3, 0.0, None, 1.15, 1, 0, None, None, None) == 1

@@ -1,0 +1,186 @@
+"""Whole-solve parity through the C ABI against the oracle.
+
+FP64 path: the same schedule (FMG + k V-cycles) on both sides agrees to
+e_max = max|phi_gpu - phi_ref| / max|phi_ref| <= 1e-11 at every k, and the
+solve to tolerance agrees with the oracle's converged solution to 1e-11.
+Mixed path (FP32 multigrid inside FP64 defect correction): the solution at
+||d||/||f|| < 1e-10 agrees with the oracle's converged FP64 solution to 1e-9.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import paper_2302_13903_gb300 as mg
+from paper_2302_13903_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BCS = [mg.PERIODIC, mg.FIXED, mg.ZEROGRAD, mg.OPEN]
+NO_STALL = 1e300
+
+
+def emax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def source(n, bc, seed=5):
+    if bc == mg.OPEN:
+        rho = inputs.uniform_sphere(n, 0.25, 4)
+        return rho * (1.0 + 0.2 * np.random.default_rng(seed).random(rho.shape)), 4 * math.pi
+    return inputs.gaussian_blobs(n, 8, seed=seed, periodic=(bc == mg.PERIODIC)), 1.0
+
+
+def gpu_solve(rho, bc, four_pi_G, tol, prec=mg.FP64, **opts):
+    n = rho.shape[0]
+    with mg.Solver(n, 1.0 / n, bc, prec=prec, fixed_value=0.25 if bc == mg.FIXED else 0.0,
+                   **opts) as s:
+        phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), four_pi_G, tol)
+        return phi.cpu().numpy(), hist, st, s.last_launches
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("n", [8, 32])
+def test_fp64_same_schedule_matches_oracle(bc, n):
+    rho, fpg = source(n, bc)
+    for k in (0, 1, 3):
+        ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0, four_pi_G=fpg,
+                        tol=0.0, max_cycles=k, stall_ratio=NO_STALL)
+        phi, hist, st, _ = gpu_solve(rho, bc, fpg, 0.0, max_cycles=k, stall_ratio=NO_STALL)
+        assert len(hist) == len(ref.hist) == k + 1
+        assert st == ref.status
+        assert emax(phi, ref.phi) <= 1e-11, (k, emax(phi, ref.phi))
+        assert np.allclose(hist, ref.hist, rtol=1e-6, atol=1e-14)
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_fp64_to_tolerance_matches_oracle(bc):
+    """Same stopping rule on both sides: the same cycles and the same phi."""
+    n = 32
+    rho, fpg = source(n, bc, seed=8)
+    ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0, four_pi_G=fpg,
+                    tol=1e-10)
+    phi, hist, st, launches = gpu_solve(rho, bc, fpg, 1e-10)
+    assert st == 0 and hist[-1] < 1e-10 and launches > 0
+    assert len(hist) == len(ref.hist)
+    assert emax(phi, ref.phi) <= 1e-11
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_fp64_converged_matches_converged_oracle(bc):
+    """Iterating until the reduction stalls (tol = 0) on both sides reaches the
+    discrete solution: the two agree to 1e-11 whatever the cycle counts."""
+    n = 32
+    rho, fpg = source(n, bc, seed=8)
+    ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0, four_pi_G=fpg,
+                    tol=0.0, max_cycles=80)
+    phi, hist, st, _ = gpu_solve(rho, bc, fpg, 0.0, max_cycles=80)
+    assert st == 0 and ref.ok
+    assert emax(phi, ref.phi) <= 1e-11
+
+
+def test_fp64_sinusoid_64_exact_discrete_solution():
+    """The 64^3 periodic sinusoid: FMG + V(1,1) to 1e-10 reaches the exact
+    discrete solution phi*_h = -h^2 f / (12 sin^2(pi h))."""
+    n = 64
+    h = 1.0 / n
+    rho = inputs.sinusoid(n)
+    phi, hist, st, _ = gpu_solve(rho, mg.PERIODIC, 1.0, 1e-10)
+    exact = -h * h * rho / (12 * math.sin(math.pi * h) ** 2)
+    assert st == 0 and len(hist) <= 16
+    assert emax(phi, exact) < 1e-9
+    ref = orc.solve(rho, h, mg.PERIODIC, tol=1e-10)
+    assert len(ref.hist) == len(hist)
+    assert emax(phi, ref.phi) <= 1e-11
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("n", [16, 64])
+def test_mixed_matches_converged_oracle(bc, n):
+    rho, fpg = source(n, bc, seed=9)
+    ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0, four_pi_G=fpg,
+                    tol=0.0, max_cycles=80)
+    phi, hist, st, _ = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED)
+    assert st == 0, (st, hist)
+    assert hist[-1] < 1e-10
+    assert emax(phi, ref.phi) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
+def test_mgi_initial_guess(prec):
+    n = 16
+    rho, _ = source(n, mg.PERIODIC, seed=2)
+    ref = orc.solve(rho, 1.0 / n, mg.PERIODIC, tol=0.0, max_cycles=80)
+    guess = ref.phi + 1e-3 * np.random.default_rng(1).standard_normal(ref.phi.shape)
+    tol = 0.0 if prec == mg.FP64 else 1e-10
+    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=prec, mode_fmg=0, max_cycles=80) as s:
+        phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), 1.0, tol,
+                                phi=torch.from_numpy(guess).cuda())
+    assert st == 0
+    assert emax(phi.cpu().numpy(), ref.phi) <= (1e-11 if prec == mg.FP64 else 1e-9)
+    if prec == mg.FP64:  # same schedule as the oracle from the same guess
+        ref2 = orc.solve(rho, 1.0 / n, mg.PERIODIC, tol=1e-10, fmg=False, phi0=guess)
+        with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=prec, mode_fmg=0) as s:
+            phi2, hist2, st2 = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-10,
+                                       phi=torch.from_numpy(guess).cuda())
+        assert len(hist2) == len(ref2.hist)
+        assert emax(phi2.cpu().numpy(), ref2.phi) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
+@pytest.mark.parametrize("n", [2, 4])
+def test_smallest_grids(prec, n):
+    for bc in BCS:
+        rho, fpg = source(n, bc, seed=3) if bc != mg.OPEN else (np.ones((n, n, n)), 4 * math.pi)
+        ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0,
+                        four_pi_G=fpg, tol=0.0, max_cycles=80)
+        phi, hist, st, _ = gpu_solve(rho, bc, fpg, 0.0 if prec == mg.FP64 else 1e-12, prec=prec,
+                                     max_cycles=80)
+        assert st == 0, (bc, st, hist)
+        assert emax(phi, ref.phi) <= (1e-11 if prec == mg.FP64 else 1e-9)
+
+
+@pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
+def test_zero_source(prec):
+    n = 8
+    for bc in (mg.PERIODIC, mg.ZEROGRAD, mg.FIXED):
+        phi, hist, st, _ = gpu_solve(np.zeros((n, n, n)), bc, 1.0, 1e-10, prec=prec)
+        assert st == 0
+        if bc == mg.FIXED:  # phi = b everywhere (to the tolerance of the solve)
+            assert np.abs(phi - 0.25).max() < 1e-9 * 0.25
+        else:
+            assert np.abs(phi).max() == 0.0
+
+
+def test_solve_host_matches_device():
+    n = 32
+    rho, _ = source(n, mg.PERIODIC, seed=4)
+    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED) as s:
+        pd, hd, _ = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-10)
+        ph, hh, st = s.solve_host(rho.copy(), 1.0, 1e-10)
+    assert st == 0
+    assert np.array_equal(pd.cpu().numpy(), ph)
+    assert np.array_equal(hd, hh)
+
+
+def test_deterministic_repeat():
+    n = 32
+    rho, _ = source(n, mg.FIXED, seed=12)
+    a = gpu_solve(rho, mg.FIXED, 1.0, 1e-10)
+    b = gpu_solve(rho, mg.FIXED, 1.0, 1e-10)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_invalid_arguments_on_gpu():
+    with mg.Solver(8, 1.0 / 8) as s:
+        rho = torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda")
+        L = mg.lib()
+        import ctypes
+        nh = ctypes.c_int(0)
+        hist = np.zeros(4)
+        assert L.mg_solve(s.ctx, rho.data_ptr(), 1.0, -1.0, rho.data_ptr(),
+                          hist.ctypes.data, 4, ctypes.byref(nh), None) == 1
+        assert L.mg_solve(s.ctx, None, 1.0, 1e-10, rho.data_ptr(), hist.ctypes.data, 4,
+                          ctypes.byref(nh), None) == 1
