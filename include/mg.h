@@ -214,6 +214,28 @@ mg_status mg_op_multipole_moments(int nx, int ny, int nz, double h, const double
 mg_status mg_op_open_faces(int nx, int ny, int nz, double h, const double *Q_host, int lmax,
                            double G, const double *origin_host, double *faces_dev, void *stream);
 
+/* Same result as mg_op_multipole_moments, for callers that cannot allocate
+ * device memory -- for instance a host application whose device memory is
+ * all reserved by its own pool allocator and that forbids allocations by
+ * plugins, or code that must not meet an out-of-memory failure or the
+ * allocator's latency mid-step.  The paper has no counterpart: this entry
+ * point exists only for such callers.
+ * It allocates nothing (no cudaMalloc, cudaFree or other allocating call):
+ * its scratch is one fixed device array of 8192 * 35 + 32 doubles (2.24 MiB)
+ * that every device which loads the library holds until the process exits.
+ * Limit: ny * nz <= 262144 rows (32 rows per partial block, 8192 blocks);
+ * larger grids are rejected with MG_ERR_ARG and a message on stderr (use
+ * mg_op_multipole_moments for them).  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress and loads the polynomial
+ * tables into constant memory, with that device current; make that first call
+ * before any stream capture.  Every call uses the same array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (on different
+ * streams, or from several host threads) race and must be serialised by the
+ * caller.  Synchronises `stream`. */
+mg_status mg_op_multipole_moments_noalloc(int nx, int ny, int nz, double h, const double *rho_dev,
+                                          int lmax, int use_com, double *origin_host,
+                                          double *Q_host, void *stream);
+
 /* Number of doubles in a faces array of an nx*ny*nz level. */
 size_t mg_faces_count(int nx, int ny, int nz);
 

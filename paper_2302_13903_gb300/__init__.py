@@ -26,7 +26,7 @@ EXPORTS = [
     "mg_ctx_device_bytes", "mg_ctx_last_launches", "mg_status_str", "mg_last_error",
     "mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict", "mg_op_prolong",
     "mg_op_coarsest", "mg_op_multipole_moments", "mg_op_open_faces", "mg_faces_count",
-    "mg_ctx_set_timing", "mg_ctx_kernel_time",
+    "mg_ctx_set_timing", "mg_ctx_kernel_time", "mg_op_multipole_moments_noalloc",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
            "correct", "source"]
@@ -94,6 +94,8 @@ def lib():
             L.mg_op_coarsest.argtypes = [i, d, i, d, p, p, p, p]
             L.mg_op_multipole_moments.argtypes = [i, i, i, d, p, i, i, p, p, p]
             L.mg_op_open_faces.argtypes = [i, i, i, d, p, i, d, p, p, p]
+            L.mg_op_multipole_moments_noalloc.argtypes = [i, i, i, d, p, i, i, p, p, p]
+            L.mg_op_multipole_moments_noalloc.restype = i
             for name in ("mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict",
                          "mg_op_prolong", "mg_op_coarsest", "mg_op_multipole_moments",
                          "mg_op_open_faces"):

@@ -108,6 +108,10 @@ cudaError_t prepare_multipole();
 // centre, written as per-block partials [nb][35]; returns nb via *nb_out.
 cudaError_t launch_raw_moments(const double* rho, Grid g, double h, double* partials,
                                int* nb_out, cudaStream_t s);
+// The same kernel on exactly nb blocks of 8 warps (one warp per row, rows
+// strided over the nb * 8 warps); partials need nb * 35 doubles.
+cudaError_t launch_raw_moments_blocks(const double* rho, Grid g, double h, double* partials,
+                                      int nb, cudaStream_t s);
 // Reduce the partials and form Q_lm (25) and the origin on the device:
 // out[0..25) = Q, out[25..28) = origin, out[28] = total mass.
 cudaError_t launch_moments_finish(const double* partials, int nb, double h, int lmax,

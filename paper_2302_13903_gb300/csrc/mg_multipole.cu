@@ -319,6 +319,15 @@ cudaError_t launch_raw_moments(const double* rho, Grid g, double h, double* part
   return cudaGetLastError();
 }
 
+cudaError_t launch_raw_moments_blocks(const double* rho, Grid g, double h, double* partials,
+                                     int nb, cudaStream_t s) {
+  cudaError_t e = upload_tables();
+  if (e != cudaSuccess) return e;
+  ++g_launches;
+  k_raw_moments<<<nb, kThreads, 0, s>>>(rho, g, h, partials);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_moments_finish(const double* partials, int nb, double h, int lmax, int use_com,
                                   const double* origin_in, double* out, cudaStream_t s) {
   cudaError_t e = upload_tables();
