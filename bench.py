@@ -41,10 +41,12 @@ def algorithmic_bytes_per_cell(kernel: str, w: int) -> float:
         "outer_residual": 20.0,         # FP64 u, f -> FP32 r
         "correct": 20.0,                # FP64 u, FP32 e -> FP64 u
         "source": 16.0,                 # FP64 rho -> FP64 f
+        "fused_down": 3.0 * w + w / 8.0,  # read u, f; write u, coarse f
+        "fused_up": 3.0 * w + w / 8.0,    # read u, coarse e, f; write u
     }[kernel]
 
 
-FP32_CLASSES = {"sor", "defect_restrict", "prolong", "fmg_prolong"}
+FP32_CLASSES = {"sor", "defect_restrict", "prolong", "fmg_prolong", "fused_down", "fused_up"}
 
 
 def peaks():

@@ -73,7 +73,8 @@ typedef struct {
   int use_com;        /* 1: expansion about the centre of mass (default); 0: origin */
   double origin[3];   /* expansion origin when use_com = 0                          */
   double stall_ratio; /* stop when d_n > stall_ratio * d_{n-1} twice; default 0.9   */
-  int inner_fmg;      /* MIXED: start each inner FP32 solve with FMG (default 1)    */
+  int inner_fmg;      /* MIXED: start each inner FP32 solve with FMG (default 0:    */
+                      /*    V-cycles from a zero correction)                         */
   int inner_cycles;   /* MIXED: FP32 V-cycles per outer iteration after the start;  */
                       /*    default 3                                               */
   int reserved[8];    /* must be zero                                               */
@@ -136,7 +137,9 @@ typedef enum {
   MG_K_OUTER_RESIDUAL = 5,  /* MIXED: FP64 residual -> FP32                       */
   MG_K_CORRECT = 6,         /* MIXED: FP64 correction update                      */
   MG_K_SOURCE = 7,          /* f = 4 pi G rho and its sums                         */
-  MG_K_COUNT = 8
+  MG_K_FUSED_DOWN = 8,      /* FP32 fused SMOOTH + defect + restriction           */
+  MG_K_FUSED_UP = 9,        /* FP32 fused prolongation + correction + SMOOTH      */
+  MG_K_COUNT = 10
 } mg_kernel;
 
 /* Enable (on = 1) or disable per-kernel timing: every finest-level launch of
@@ -197,6 +200,21 @@ mg_status mg_op_prolong(int prec, int nx, int ny, int nz, mg_bc bc, double bc_va
  * equation solved exactly with its ghosts; 0 for periodic / zero gradient. */
 mg_status mg_op_coarsest(int prec, double h, mg_bc bc, double bc_value, const double *faces_dev,
                          const void *f_dev, void *u_dev, void *stream);
+
+/* Fused FP32 legs of a V-cycle (Algorithm 1) on one level with a homogeneous
+ * rule (bc = MG_BC_PERIODIC, MG_BC_FIXED meaning zero fixed, or
+ * MG_BC_ZEROGRAD).  u_in and u_out are distinct float arrays.
+ * down: u_out = SMOOTH(u_in, or 0 if zero_guess), then fc = I_l^{l-1}(f - L u_out)
+ *       on the (nx/2)*(ny/2)*(nz/2) grid (steps 1-3).
+ * up:   u_out = SMOOTH(u_in + I_{l-1}^l ec), ec on the coarse grid (steps 5-7).
+ * Levels the fused kernels do not cover (narrower than 32 cells) run the
+ * per-step kernels instead, with the same result. */
+mg_status mg_op_vcycle_down(int nx, int ny, int nz, double h, mg_bc bc, double omega,
+                            int zero_guess, const float *u_in_dev, float *u_out_dev,
+                            const float *f_dev, float *fc_dev, void *stream);
+mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double omega,
+                          const float *u_in_dev, float *u_out_dev, const float *f_dev,
+                          const float *ec_dev, void *stream);
 
 /* Multipole moments of rho_dev (FP64, nx*ny*nz, spacing h) for App. A:
  * Q_host receives (lmax+1)^2 moments ordered l*l + (m + l) (25 slots are

@@ -27,9 +27,10 @@ EXPORTS = [
     "mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict", "mg_op_prolong",
     "mg_op_coarsest", "mg_op_multipole_moments", "mg_op_open_faces", "mg_faces_count",
     "mg_ctx_set_timing", "mg_ctx_kernel_time", "mg_op_multipole_moments_noalloc",
+    "mg_op_vcycle_down", "mg_op_vcycle_up",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
-           "correct", "source"]
+           "correct", "source", "fused_down", "fused_up"]
 
 
 class Opts(ctypes.Structure):
@@ -94,6 +95,10 @@ def lib():
             L.mg_op_coarsest.argtypes = [i, d, i, d, p, p, p, p]
             L.mg_op_multipole_moments.argtypes = [i, i, i, d, p, i, i, p, p, p]
             L.mg_op_open_faces.argtypes = [i, i, i, d, p, i, d, p, p, p]
+            L.mg_op_vcycle_down.argtypes = [i, i, i, d, i, d, i, p, p, p, p, p]
+            L.mg_op_vcycle_down.restype = i
+            L.mg_op_vcycle_up.argtypes = [i, i, i, d, i, d, p, p, p, p, p]
+            L.mg_op_vcycle_up.restype = i
             L.mg_op_multipole_moments_noalloc.argtypes = [i, i, i, d, p, i, i, p, p, p]
             L.mg_op_multipole_moments_noalloc.restype = i
             for name in ("mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict",
@@ -291,6 +296,29 @@ def op_coarsest(f, h, bc=PERIODIC, bc_value=0.0, faces=None, stream=None):
     _check(lib().mg_op_coarsest(_prec_of(f), h, bc, bc_value, _faces_ptr(faces), _dptr(f), _dptr(u),
                                 _stream_ptr(stream)))
     return u
+
+
+def op_vcycle_down(u, f, h, bc=PERIODIC, omega=1.15, zero_guess=False, stream=None):
+    """Fused down-leg on an FP32 level: returns (u_out, fc)."""
+    import torch
+    nz, ny, nx = f.shape
+    uo = torch.empty_like(f)
+    fc = torch.empty((nz // 2, ny // 2, nx // 2), dtype=f.dtype, device=f.device)
+    _check(lib().mg_op_vcycle_down(nx, ny, nz, h, bc, omega, int(zero_guess),
+                                   None if zero_guess else _dptr(u, torch.float32), _dptr(uo),
+                                   _dptr(f, torch.float32), _dptr(fc), _stream_ptr(stream)))
+    return uo, fc
+
+
+def op_vcycle_up(u, f, ec, h, bc=PERIODIC, omega=1.15, stream=None):
+    """Fused up-leg on an FP32 level: returns u_out."""
+    import torch
+    nz, ny, nx = f.shape
+    uo = torch.empty_like(f)
+    _check(lib().mg_op_vcycle_up(nx, ny, nz, h, bc, omega, _dptr(u, torch.float32), _dptr(uo),
+                                 _dptr(f, torch.float32), _dptr(ec, torch.float32),
+                                 _stream_ptr(stream)))
+    return uo
 
 
 def op_multipole_moments(rho, h, lmax=4, use_com=True, origin=(0.0, 0.0, 0.0), stream=None):

@@ -81,9 +81,9 @@ cudaError_t launch_fill(T* u, long long n, T v, cudaStream_t s);
 cudaError_t launch_source(const double* rho, double* f, long long n, double four_pi_G,
                           double* partials, cudaStream_t s);
 // a[i] -= sum(partials[0..nb)) / n  (removes the mean; the sum is formed on
-// the device in a fixed order).
+// the device in a fixed order into *total_slot, a device scalar).
 cudaError_t launch_subtract_mean(double* a, long long n, const double* partials, int nb,
-                                 cudaStream_t s);
+                                 double* total_slot, cudaStream_t s);
 // Partial sums of a[i] (FP64) and of a[i]^2.
 template <typename T>
 cudaError_t launch_sum(const T* a, long long n, int squares, double* partials, cudaStream_t s);
@@ -94,9 +94,41 @@ cudaError_t launch_finish_sum(const double* partials, int nb, double* out, cudaS
 // partial sums of (f - L_h u)^2 in FP64.
 cudaError_t launch_outer_residual(const double* u, const double* f, float* r32, Grid g, double h,
                                   Bc bc, double scale, double* partials, cudaStream_t s);
+// b = (float)(scale * a).
+cudaError_t launch_scale_to_f32(const double* a, float* b, long long n, double scale,
+                               cudaStream_t s);
 // u += inv_scale * e32 (FP64 correction update).
 cudaError_t launch_correct(double* u, const float* e32, long long n, double inv_scale,
                            cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Single-CTA bottom solver for the levels of at most 16^3 cells (levels
+// 0 .. kBottomLevels-1): u, f, n, h, bc indexed by level (bc may be null when
+// fmg is false).  fmg = false: one V-cycle on levels top .. 0 of the
+// correction (u[top] starts at 0, f[top] holds the restricted defect);
+// fmg = true: Algorithm 2 up to level `top` from f[top].
+constexpr int kBottomLevels = 5;
+template <typename T>
+cudaError_t launch_bottom(T* const* u, T* const* f, const int* n, const double* h, const Bc* bc,
+                          Bc hom, double omega, int pre, int post, int top, bool fmg,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Fused FP32 V-cycle legs (homogeneous rules only).  Each reads u_in and
+// writes u_out (distinct buffers).
+
+// Whether the fused kernels handle this level (width >= 32, homogeneous rule).
+bool fused_ok(Grid g, const Bc& bc);
+// One SMOOTH step from u_in (or 0) then fc = restriction of f - L u (Algorithm
+// 1, steps 1-3).
+cudaError_t launch_fused_down(const float* u_in, float* u_out, const float* f, float* fc, Grid g,
+                              double h, Bc bc, double omega, bool zero_guess, cudaStream_t s);
+// u_in + trilinear(ec), then one SMOOTH step (Algorithm 1, steps 5-7).
+cudaError_t launch_fused_up(const float* u_in, float* u_out, const float* f, const float* ec,
+                            Grid g, double h, Bc bc, double omega, cudaStream_t s);
+// One SMOOTH step.
+cudaError_t launch_fused_smooth(const float* u_in, float* u_out, const float* f, Grid g, double h,
+                                Bc bc, double omega, bool zero_guess, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Multipole boundary (App. A).

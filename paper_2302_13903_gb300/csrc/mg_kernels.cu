@@ -9,12 +9,13 @@
 // prolongations) the face rule is applied along x, then y, then z.
 //
 // These are the straightforward kernels: one thread per output cell (or per
-// coarse cell for the fused defect + restriction), grid-stride loops, and
-// deterministic two-stage reductions.
+// coarse cell for the fused defect + restriction), grid-stride loops over the
+// bodies in mg_device.cuh, and deterministic two-stage reductions.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "mg_device.cuh"
 #include "mg_internal.h"
 
 namespace mg {
@@ -24,73 +25,6 @@ thread_local long long g_launches = 0;
 namespace {
 
 constexpr int kThreads = 256;
-
-__host__ __device__ inline size_t at(const Grid& g, int i, int j, int k) {
-  return ((size_t)k * (size_t)g.ny + (size_t)j) * (size_t)g.nx + (size_t)i;
-}
-
-// Value on a face point; `a`, `b` are padded tangential indices (0..n+1).
-__device__ inline double face_value(const Bc& bc, const Grid& g, int face, int a, int b) {
-  if (bc.kind == BC_FIXED) return bc.value;
-  size_t off;
-  size_t fx = (size_t)(g.ny + 2) * (g.nz + 2), fy = (size_t)(g.nx + 2) * (g.nz + 2),
-         fz = (size_t)(g.nx + 2) * (g.ny + 2);
-  if (face < 2) off = face * fx + (size_t)b * (g.ny + 2) + a;
-  else if (face < 4) off = 2 * fx + (face - 2) * fy + (size_t)b * (g.nx + 2) + a;
-  else off = 2 * fx + 2 * fy + (face - 4) * fz + (size_t)b * (g.nx + 2) + a;
-  return bc.faces[off];
-}
-
-// Value at (i, j, k) where at least one index is -1 or n: the rule along z is
-// the outermost, then y, then x (so the x rule acts on the stored value).
-template <typename T>
-__device__ __noinline__ T ghost(const T* __restrict__ u, int i, int j, int k, const Grid g,
-                                const Bc bc) {
-  const bool affine = (bc.kind == BC_FIXED || bc.kind == BC_OPEN);
-  const bool wrap = (bc.kind == BC_PERIODIC);
-  int i2 = i, j2 = j, k2 = k;
-  T az = 1, cz = 0, ay = 1, cy = 0, ax = 1, cx = 0;
-  if ((unsigned)k >= (unsigned)g.nz) {
-    const int hi = k >= g.nz;
-    k2 = wrap ? (hi ? 0 : g.nz - 1) : (hi ? g.nz - 1 : 0);
-    if (affine) { az = -1; cz = (T)(2.0 * face_value(bc, g, 4 + hi, i + 1, j + 1)); }
-  }
-  if ((unsigned)j >= (unsigned)g.ny) {
-    const int hi = j >= g.ny;
-    j2 = wrap ? (hi ? 0 : g.ny - 1) : (hi ? g.ny - 1 : 0);
-    if (affine) { ay = -1; cy = (T)(2.0 * face_value(bc, g, 2 + hi, i + 1, k2 + 1)); }
-  }
-  if ((unsigned)i >= (unsigned)g.nx) {
-    const int hi = i >= g.nx;
-    i2 = wrap ? (hi ? 0 : g.nx - 1) : (hi ? g.nx - 1 : 0);
-    if (affine) { ax = -1; cx = (T)(2.0 * face_value(bc, g, 0 + hi, j2 + 1, k2 + 1)); }
-  }
-  T v = u[at(g, i2, j2, k2)];
-  v = ax * v + cx;
-  v = ay * v + cy;
-  v = az * v + cz;
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T fetch(const T* __restrict__ u, int i, int j, int k, const Grid& g,
-                                   const Bc& bc) {
-  if ((unsigned)i < (unsigned)g.nx && (unsigned)j < (unsigned)g.ny && (unsigned)k < (unsigned)g.nz)
-    return u[at(g, i, j, k)];
-  return ghost(u, i, j, k, g, bc);
-}
-
-// Sum of the six face neighbours of (i, j, k), in the order x-, x+, y-, y+, z-, z+.
-template <typename T>
-__device__ __forceinline__ T neighbour_sum(const T* __restrict__ u, int i, int j, int k,
-                                           const Grid& g, const Bc& bc) {
-  if (i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1 && k > 0 && k < g.nz - 1) {
-    const size_t c = at(g, i, j, k), sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
-    return u[c - 1] + u[c + 1] + u[c - sy] + u[c + sy] + u[c - sz] + u[c + sz];
-  }
-  return fetch(u, i - 1, j, k, g, bc) + fetch(u, i + 1, j, k, g, bc) + fetch(u, i, j - 1, k, g, bc) +
-         fetch(u, i, j + 1, k, g, bc) + fetch(u, i, j, k - 1, g, bc) + fetch(u, i, j, k + 1, g, bc);
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -121,40 +55,6 @@ int grid_for(long long work) {
 }
 
 // ---------------------------------------------------------------------------
-// SMOOTH: one colour of red-black SOR (Eqs. rbsor1-rbsor2),
-// u <- (1 - omega) u + (omega / 6) sum_nb + (-omega h^2 / 6) f.
-
-template <typename T>
-__global__ void k_sor(T* __restrict__ u, const T* __restrict__ f, Grid g, Bc bc, T cu, T cs,
-                      T cf, int colour) {
-  const int hx = g.nx >> 1;
-  const long long total = (long long)hx * g.ny * g.nz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(t % hx);
-    const long long r = t / hx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const int i = 2 * m + ((j + k + colour) & 1);
-    const size_t c = at(g, i, j, k);
-    const T s = neighbour_sum(u, i, j, k, g, bc);
-    u[c] = cu * u[c] + cs * s + cf * f[c];
-  }
-}
-
-// Red half-sweep from u = 0: every neighbour is 0 (and so is every ghost of
-// the homogeneous rule), so red cells become cf * f; black cells are zeroed.
-template <typename T>
-__global__ void k_sor_red_zero(T* __restrict__ u, const T* __restrict__ f, Grid g, T cf) {
-  const long long total = g.cells();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % g.nx);
-    const long long r = t / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    u[t] = ((i + j + k) & 1) ? T(0) : cf * f[t];
-  }
-}
-
 // d = f - (sum_nb - 6u) / h^2; optional store and partial sums of d^2.
 template <typename T>
 __global__ void k_defect(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ d,
@@ -166,7 +66,7 @@ __global__ void k_defect(const T* __restrict__ u, const T* __restrict__ f, T* __
     const int i = (int)(t % g.nx);
     const long long r = t / g.nx;
     const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const T s = neighbour_sum(u, i, j, k, g, bc);
+    const T s = dev::neighbour_sum(u, i, j, k, g, bc);
     const T dv = f[t] - (s - T(6) * u[t]) * inv_h2;
     if (d) d[t] = dv;
     acc += (double)dv * (double)dv;
@@ -177,133 +77,40 @@ __global__ void k_defect(const T* __restrict__ u, const T* __restrict__ f, T* __
   }
 }
 
-// Defect of the eight children of each coarse cell, averaged (Algorithm 1,
-// steps 2-3 with Eq. restriction).
 template <typename T>
-__global__ void k_defect_restrict(const T* __restrict__ u, const T* __restrict__ f,
-                                  T* __restrict__ fc, Grid g, Bc bc, T inv_h2) {
-  const Grid gc{g.nx / 2, g.ny / 2, g.nz / 2};
-  const long long total = gc.cells();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(t % gc.nx);
-    const long long r = t / gc.nx;
-    const int J = (int)(r % gc.ny), K = (int)(r / gc.ny);
-    T acc = 0;
-    for (int c = 0; c < 2; ++c)
-      for (int b = 0; b < 2; ++b)
-        for (int a = 0; a < 2; ++a) {
-          const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
-          const size_t q = at(g, i, j, k);
-          const T s = neighbour_sum(u, i, j, k, g, bc);
-          acc += f[q] - (s - T(6) * u[q]) * inv_h2;
-        }
-    fc[t] = acc * T(0.125);
-  }
+__global__ void k_sor(T* u, const T* f, Grid g, Bc bc, T cu, T cs, T cf, int colour) {
+  dev::sor_range(u, f, g, bc, cu, cs, cf, colour, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x);
 }
 
 template <typename T>
-__global__ void k_restrict(const T* __restrict__ uf, T* __restrict__ uc, Grid gf) {
-  const Grid gc{gf.nx / 2, gf.ny / 2, gf.nz / 2};
-  const long long total = gc.cells();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(t % gc.nx);
-    const long long r = t / gc.nx;
-    const int J = (int)(r % gc.ny), K = (int)(r / gc.ny);
-    T acc = 0;
-    for (int c = 0; c < 2; ++c)
-      for (int b = 0; b < 2; ++b)
-        for (int a = 0; a < 2; ++a) acc += uf[at(gf, 2 * I + a, 2 * J + b, 2 * K + c)];
-    uc[t] = acc * T(0.125);
-  }
+__global__ void k_sor_red_zero(T* u, const T* f, Grid g, T cf) {
+  dev::sor_red_zero_range(u, f, g, cf, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                          (long long)gridDim.x * blockDim.x);
 }
 
-// Prolongation, one thread per coarse cell writing its 2x2x2 children.  The
-// 27 coarse values around the parent (ghosts from the coarse rule) are
-// interpolated along x, then y, then z with the 1-D weights of the fine
-// parity: trilinear (Eq. trilinear) takes 1/4, 3/4 of the parents I-1, I for
-// an even (lower) child and 3/4, 1/4 of I, I+1 for an odd one; the FMG
-// operator I' takes 5/32, 30/32, -3/32 of I-1, I, I+1 (even) and the mirror
-// (odd).
-template <typename T, bool HIGH>
-__device__ __forceinline__ void interp1(const T a, const T b, const T c, T& even, T& odd) {
-  if (!HIGH) {
-    even = T(0.25) * a + T(0.75) * b;
-    odd = T(0.75) * b + T(0.25) * c;
-  } else {
-    even = T(5.0 / 32.0) * a + T(30.0 / 32.0) * b + T(-3.0 / 32.0) * c;
-    odd = T(-3.0 / 32.0) * a + T(30.0 / 32.0) * b + T(5.0 / 32.0) * c;
-  }
+template <typename T>
+__global__ void k_defect_restrict(const T* u, const T* f, T* fc, Grid g, Bc bc, T inv_h2) {
+  dev::defect_restrict_range(u, f, fc, g, bc, inv_h2,
+                             blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                             (long long)gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__global__ void k_restrict(const T* uf, T* uc, Grid gf) {
+  dev::restrict_range(uf, uc, gf, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                      (long long)gridDim.x * blockDim.x);
 }
 
 template <typename T, bool HIGH>
-__global__ void k_prolong(const T* __restrict__ uc, T* __restrict__ uf, Grid gf, Bc bc, int add) {
-  const Grid gc{gf.nx / 2, gf.ny / 2, gf.nz / 2};
-  const long long total = gc.cells();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(t % gc.nx);
-    const long long r = t / gc.nx;
-    const int J = (int)(r % gc.ny), K = (int)(r / gc.ny);
-    T c[3][3][3];
-    if (I > 0 && I < gc.nx - 1 && J > 0 && J < gc.ny - 1 && K > 0 && K < gc.nz - 1) {
-      const size_t sy = (size_t)gc.nx, sz = (size_t)gc.nx * gc.ny, o = at(gc, I, J, K);
-#pragma unroll
-      for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-          for (int cx = 0; cx < 3; ++cx)
-            c[cz][cy][cx] = uc[o + (cz - 1) * sz + (cy - 1) * sy + (cx - 1)];
-    } else {
-#pragma unroll
-      for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-          for (int cx = 0; cx < 3; ++cx)
-            c[cz][cy][cx] = fetch(uc, I + cx - 1, J + cy - 1, K + cz - 1, gc, bc);
-    }
-    T vx[3][3][2];  // [cz][cy][x parity]
-#pragma unroll
-    for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-      for (int cy = 0; cy < 3; ++cy)
-        interp1<T, HIGH>(c[cz][cy][0], c[cz][cy][1], c[cz][cy][2], vx[cz][cy][0], vx[cz][cy][1]);
-    T vy[3][2][2];  // [cz][y parity][x parity]
-#pragma unroll
-    for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-      for (int px = 0; px < 2; ++px)
-        interp1<T, HIGH>(vx[cz][0][px], vx[cz][1][px], vx[cz][2][px], vy[cz][0][px], vy[cz][1][px]);
-#pragma unroll
-    for (int py = 0; py < 2; ++py)
-#pragma unroll
-      for (int px = 0; px < 2; ++px) {
-        T lo, hi;
-        interp1<T, HIGH>(vy[0][py][px], vy[1][py][px], vy[2][py][px], lo, hi);
-        const size_t q0 = at(gf, 2 * I + px, 2 * J + py, 2 * K);
-        const size_t q1 = q0 + (size_t)gf.nx * gf.ny;
-        uf[q0] = add ? uf[q0] + lo : lo;
-        uf[q1] = add ? uf[q1] + hi : hi;
-      }
-  }
+__global__ void k_prolong(const T* uc, T* uf, Grid gf, Bc bc, int add) {
+  dev::prolong_range<T, HIGH>(uc, uf, gf, bc, add, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                              (long long)gridDim.x * blockDim.x);
 }
 
-// COARSEST on a single cell: the six ghosts are 2 b_face - u (fixed / open)
-// or u itself (periodic / zero gradient, singular: 0).
 template <typename T>
-__global__ void k_coarsest(const T* __restrict__ f, T* __restrict__ u, double h, Bc bc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (bc.kind == BC_PERIODIC || bc.kind == BC_ZEROGRAD) {
-    u[0] = T(0);
-    return;
-  }
-  const Grid g{1, 1, 1};
-  double sb = 0.0;
-  for (int face = 0; face < 6; ++face) sb += face_value(bc, g, face, 1, 1);
-  u[0] = (T)((2.0 * sb - h * h * (double)f[0]) / 12.0);
+__global__ void k_coarsest(const T* f, T* u, double h, Bc bc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) dev::coarsest_one(f, u, h, bc);
 }
 
 template <typename T>
@@ -346,16 +153,9 @@ __global__ void k_finish_sum(const double* __restrict__ partials, int nb, double
   if (threadIdx.x == 0) out[0] = b;
 }
 
-// a -= total / n, the total being the fixed-order sum of the partials.
-__global__ void k_subtract_mean(double* __restrict__ a, long long n,
-                                const double* __restrict__ partials, int nb) {
-  __shared__ double mean;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int q = 0; q < nb; ++q) s += partials[q];
-    mean = s / (double)n;
-  }
-  __syncthreads();
+// a -= total[0] / n (the total was formed on the device in a fixed order).
+__global__ void k_subtract_mean(double* __restrict__ a, long long n, const double* __restrict__ total) {
+  const double mean = total[0] / (double)n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
     a[t] -= mean;
@@ -371,13 +171,20 @@ __global__ void k_outer_residual(const double* __restrict__ u, const double* __r
     const int i = (int)(t % g.nx);
     const long long r = t / g.nx;
     const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const double s = neighbour_sum(u, i, j, k, g, bc);
+    const double s = dev::neighbour_sum(u, i, j, k, g, bc);
     const double d = f[t] - (s - 6.0 * u[t]) * inv_h2;
     r32[t] = (float)(d * scale);
     acc += d * d;
   }
   const double b = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+__global__ void k_scale_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n,
+                               double scale) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    b[t] = (float)(scale * a[t]);
 }
 
 __global__ void k_correct(double* __restrict__ u, const float* __restrict__ e, long long n,
@@ -473,9 +280,11 @@ cudaError_t launch_source(const double* rho, double* f, long long n, double four
 }
 
 cudaError_t launch_subtract_mean(double* a, long long n, const double* partials, int nb,
-                                 cudaStream_t s) {
+                                 double* total_slot, cudaStream_t s) {
   ++g_launches;
-  k_subtract_mean<<<grid_for(n), kThreads, 0, s>>>(a, n, partials, nb);
+  k_finish_sum<<<1, kThreads, 0, s>>>(partials, nb, total_slot);
+  ++g_launches;
+  k_subtract_mean<<<grid_for(n), kThreads, 0, s>>>(a, n, total_slot);
   return cudaGetLastError();
 }
 
@@ -497,6 +306,13 @@ cudaError_t launch_outer_residual(const double* u, const double* f, float* r32, 
   ++g_launches;
   k_outer_residual<<<reduce_blocks(g.cells()), kThreads, 0, s>>>(u, f, r32, g, bc, 1.0 / (h * h),
                                                                  scale, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_to_f32(const double* a, float* b, long long n, double scale,
+                               cudaStream_t s) {
+  ++g_launches;
+  k_scale_to_f32<<<grid_for(n), kThreads, 0, s>>>(a, b, n, scale);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/mg.h"
@@ -38,8 +40,10 @@ struct mg_ctx {
   double* u64[kMaxLevels] = {};
   double* f64[kMaxLevels] = {};
   double* faces[kMaxLevels] = {};  // open boundary values per level
-  // FP32 hierarchy (mixed precision).
+  // FP32 hierarchy (mixed precision); u32b is the second buffer of levels the
+  // fused kernels handle (they read one buffer and write the other).
   float* u32[kMaxLevels] = {};
+  float* u32b[kMaxLevels] = {};
   float* f32[kMaxLevels] = {};
   double* partials = nullptr;  // reduction partials
   double* scal = nullptr;      // device scalars: [0] |f|^2 sum, [1] |d|^2 sum, [2..31] multipole
@@ -148,6 +152,27 @@ void collect_times(mg_ctx* c) {
 // ---------------------------------------------------------------------------
 // Cycles, templated on the level precision.
 
+// Highest level index the single-CTA bottom solver covers (<= 16^3 cells).
+int bottom_top(const mg_ctx* c) {
+  int t = 0;
+  while (t + 1 < c->L && t + 1 < mg::kBottomLevels) ++t;
+  return t;
+}
+
+template <typename T>
+void launch_bottom_levels(mg_ctx* c, T** u, T** f, int top, const Bc* bcs, const Bc& hom, bool fmg,
+                          cudaStream_t s) {
+  int n[mg::kBottomLevels];
+  double h[mg::kBottomLevels];
+  for (int l = 0; l <= top; ++l) {
+    n[l] = level_n(c, l);
+    h[l] = level_h(c, l);
+  }
+  check(c, mg::launch_bottom<T>(u, f, n, h, bcs, hom, c->opts.omega, c->opts.pre, c->opts.post,
+                                top, fmg, s),
+        "bottom");
+}
+
 template <typename T>
 struct Pyr {
   T** u;
@@ -188,9 +213,77 @@ void smooth_steps(mg_ctx* c, Pyr<T> P, int l, const Bc& bc, int steps, bool zero
 // rule `hom` below.  zero_guess: u_l enters as 0 (coarse corrections).
 template <typename T>
 void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool zero_guess,
+            cudaStream_t s);
+
+// The same cycle on an FP32 level handled by the fused kernels: one kernel
+// per leg, ping-ponging between the level's two buffers.
+void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_guess,
+                  cudaStream_t s) {
+  const Grid g = level_grid(c, l);
+  const double h = level_h(c, l), om = c->opts.omega;
+  const bool fin = (l == c->L - 1);
+  auto swap_level = [&]() { std::swap(c->u32[l], c->u32b[l]); };
+  const int pre = c->opts.pre, post = c->opts.post;
+  bool zg = zero_guess;
+  for (int q = 0; q + 1 < pre; ++q) {  // extra pre-smoothing steps of V(2,.)
+    KTimer t(c, MG_K_SOR, fin, s);
+    check(c, mg::launch_fused_smooth(c->u32[l], c->u32b[l], c->f32[l], g, h, bc_top, om, zg, s),
+          "fused smooth");
+    swap_level();
+    zg = false;
+  }
+  if (pre >= 1) {  // 1-3
+    KTimer t(c, MG_K_FUSED_DOWN, fin, s);
+    check(c, mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
+                                   om, zg, s),
+          "fused down");
+    swap_level();
+  } else {
+    if (zg) check(c, mg::launch_fill<float>(c->u32[l], g.cells(), 0.f, s), "fill");
+    KTimer t(c, MG_K_DEFECT_RESTRICT, fin, s);
+    check(c, mg::launch_defect_restrict<float>(c->u32[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
+                                               s),
+          "defect_restrict");
+  }
+  Pyr<float> P = pyr<float>(c);
+  if (l - 1 == 0)
+    check(c, mg::launch_coarsest<float>(P.f[0], P.u[0], level_h(c, 0), hom, s), "coarsest");
+  else if (l - 1 <= bottom_top(c))
+    launch_bottom_levels<float>(c, P.u, P.f, l - 1, nullptr, hom, false, s);
+  else
+    vcycle<float>(c, P, l - 1, hom, hom, true, s);
+  if (post >= 1) {  // 5-7
+    {
+      KTimer t(c, MG_K_FUSED_UP, fin, s);
+      check(c, mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc_top,
+                                   om, s),
+            "fused up");
+      swap_level();
+    }
+    for (int q = 1; q < post; ++q) {
+      KTimer t(c, MG_K_SOR, fin, s);
+      check(c, mg::launch_fused_smooth(c->u32[l], c->u32b[l], c->f32[l], g, h, bc_top, om, false,
+                                       s),
+            "fused smooth");
+      swap_level();
+    }
+  } else {
+    KTimer t(c, MG_K_PROLONG, fin, s);
+    check(c, mg::launch_prolong<float>(c->u32[l - 1], c->u32[l], g, hom, 0, 1, s), "prolong");
+  }
+}
+
+template <typename T>
+void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool zero_guess,
             cudaStream_t s) {
   const Grid g = level_grid(c, l);
   const double h = level_h(c, l);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->u32b[l] && mg::fused_ok(g, bc_top)) {
+      vcycle_fused(c, l, bc_top, hom, zero_guess, s);
+      return;
+    }
+  }
   const bool fin = (l == c->L - 1);
   smooth_steps<T>(c, P, l, bc_top, c->opts.pre, zero_guess, s);                        // 1
   {
@@ -200,6 +293,8 @@ void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool ze
   }
   if (l - 1 == 0)
     check(c, mg::launch_coarsest<T>(P.f[0], P.u[0], level_h(c, 0), hom, s), "coarsest");  // 4.1
+  else if (l - 1 <= bottom_top(c))
+    launch_bottom_levels<T>(c, P.u, P.f, l - 1, nullptr, hom, false, s);                 // 4.2
   else
     vcycle<T>(c, P, l - 1, hom, hom, true, s);                                         // 4.2
   {
@@ -212,10 +307,11 @@ void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool ze
 // Algorithm 2 with rule bcs[l] on every level.
 template <typename T>
 void fmg(mg_ctx* c, Pyr<T> P, const Bc* bcs, const Bc& hom, cudaStream_t s) {
-  for (int l = c->L - 1; l >= 1; --l)
+  const int lb = bottom_top(c);
+  for (int l = c->L - 1; l > lb; --l)
     check(c, mg::launch_restrict<T>(P.f[l], P.f[l - 1], level_grid(c, l), s), "restrict");
-  check(c, mg::launch_coarsest<T>(P.f[0], P.u[0], level_h(c, 0), bcs[0], s), "coarsest");
-  for (int l = 1; l < c->L; ++l) {
+  launch_bottom_levels<T>(c, P.u, P.f, lb, bcs, hom, true, s);  // levels 0 .. lb
+  for (int l = lb + 1; l < c->L; ++l) {
     {
       KTimer t(c, MG_K_FMG_PROLONG, l == c->L - 1, s);
       check(c, mg::launch_prolong<T>(P.u[l - 1], P.u[l], level_grid(c, l), bcs[l - 1], 1, 0, s),
@@ -264,7 +360,7 @@ double prepare_source(mg_ctx* c, const double* rho, double four_pi_G, double* f_
     check(c, mg::launch_source(rho, f_fin, N, four_pi_G, c->partials, s), "source");
   }
   if (c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD)
-    check(c, mg::launch_subtract_mean(f_fin, N, c->partials, nb, s), "subtract_mean");
+    check(c, mg::launch_subtract_mean(f_fin, N, c->partials, nb, c->scal + 40, s), "subtract_mean");
   check(c, mg::launch_sum<double>(f_fin, N, 1, c->partials, s), "sum f^2");
   check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 0, s), "finish f^2");
   if (c->bc_kind == MG_BC_OPEN) {
@@ -286,7 +382,8 @@ void remove_mean(mg_ctx* c, double* u, cudaStream_t s) {
   if (c->bc_kind != MG_BC_PERIODIC && c->bc_kind != MG_BC_ZEROGRAD) return;
   const long long N = level_grid(c, c->L - 1).cells();
   check(c, mg::launch_sum<double>(u, N, 0, c->partials, s), "sum phi");
-  check(c, mg::launch_subtract_mean(u, N, c->partials, mg::reduce_blocks(N), s), "phi mean");
+  check(c, mg::launch_subtract_mean(u, N, c->partials, mg::reduce_blocks(N), c->scal + 40, s),
+        "phi mean");
 }
 
 double defect_rms(mg_ctx* c, const double* u, const double* f, const Bc& bc, cudaStream_t s) {
@@ -359,12 +456,21 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   const Bc bc = physical_bc(c, F);
   const Bc hom = mg::homogeneous(bc);
   if (c->opts.mode_fmg) check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
-  // r = f - L phi, scaled into FP32 so that its RMS is about 1.
+  // r = f - L phi, scaled into FP32 so that its RMS is about 1.  From phi = 0
+  // with a rule whose boundary values are 0, L phi = 0 and r = f exactly.
   double scale = fnorm > 0.0 ? 1.0 / fnorm : 1.0;
-  check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
-        "outer residual");
-  check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
-  double rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
+  const bool zero_values = bc.kind == mg::BC_PERIODIC || bc.kind == mg::BC_ZEROGRAD ||
+                           (bc.kind == mg::BC_FIXED && bc.value == 0.0);
+  double rn;
+  if (c->opts.mode_fmg && zero_values) {
+    check(c, mg::launch_scale_to_f32(f, c->f32[F], N, scale, s), "r = f");
+    rn = fnorm;
+  } else {
+    check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
+          "outer residual");
+    check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
+    rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
+  }
   if (fnorm == 0.0) {
     fnorm = rn > 0.0 ? rn : 1.0;
     scale = 1.0 / fnorm;
@@ -434,7 +540,7 @@ void mg_opts_init(mg_opts* o) {
   o->lmax = 4;
   o->use_com = 1;
   o->stall_ratio = 0.9;
-  o->inner_fmg = 1;
+  o->inner_fmg = 0;
   o->inner_cycles = 3;
 }
 
@@ -521,6 +627,8 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
       } else {
         c->u32[l] = dalloc<float>(c, cells);
         c->f32[l] = dalloc<float>(c, cells);
+        if (mg::fused_ok(level_grid(c, l), mg::homogeneous(Bc{(int)bc, 0.0, nullptr})))
+          c->u32b[l] = dalloc<float>(c, cells);
       }
     }
     if (o.prec == MG_MIXED) {
@@ -734,6 +842,55 @@ mg_status mg_op_coarsest(int prec, double h, mg_bc bc, double bc_value, const do
   cudaError_t e = prec == MG_FP64 ? mg::launch_coarsest<double>((const double*)f, (double*)u, h, b, s)
                                   : mg::launch_coarsest<float>((const float*)f, (float*)u, h, b, s);
   return op_result(e, "coarsest");
+}
+
+mg_status mg_op_vcycle_down(int nx, int ny, int nz, double h, mg_bc bc, double omega,
+                            int zero_guess, const float* u_in, float* u_out, const float* f,
+                            float* fc, void* stream) {
+  if (!op_args_ok(MG_MIXED, nx, ny, nz, bc, nullptr) || bc == MG_BC_OPEN || nx < 2 || ny < 2 ||
+      nz < 2 || nx % 2 || ny % 2 || nz % 2 || (!u_in && !zero_guess) || !u_out || !f || !fc ||
+      u_in == u_out) {
+    g_err = "mg_op_vcycle_down: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, 0.0, nullptr};
+  const Grid g{nx, ny, nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (mg::fused_ok(g, b)) {
+    e = mg::launch_fused_down(u_in, u_out, f, fc, g, h, b, omega, zero_guess != 0, s);
+  } else {
+    e = zero_guess ? mg::launch_sor_red_zero<float>(u_out, f, g, h, omega, s)
+                   : cudaMemcpyAsync(u_out, u_in, sizeof(float) * g.cells(),
+                                     cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && !zero_guess) e = mg::launch_sor<float>(u_out, f, g, h, b, omega, 0, s);
+    if (e == cudaSuccess) e = mg::launch_sor<float>(u_out, f, g, h, b, omega, 1, s);
+    if (e == cudaSuccess) e = mg::launch_defect_restrict<float>(u_out, f, fc, g, h, b, s);
+  }
+  return op_result(e, "vcycle_down");
+}
+
+mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double omega,
+                          const float* u_in, float* u_out, const float* f, const float* ec,
+                          void* stream) {
+  if (!op_args_ok(MG_MIXED, nx, ny, nz, bc, nullptr) || bc == MG_BC_OPEN || nx < 2 || ny < 2 ||
+      nz < 2 || nx % 2 || ny % 2 || nz % 2 || !u_in || !u_out || !f || !ec || u_in == u_out) {
+    g_err = "mg_op_vcycle_up: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, 0.0, nullptr};
+  const Grid g{nx, ny, nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (mg::fused_ok(g, b)) {
+    e = mg::launch_fused_up(u_in, u_out, f, ec, g, h, b, omega, s);
+  } else {
+    e = cudaMemcpyAsync(u_out, u_in, sizeof(float) * g.cells(), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = mg::launch_prolong<float>(ec, u_out, g, b, 0, 1, s);
+    if (e == cudaSuccess) e = mg::launch_sor<float>(u_out, f, g, h, b, omega, 0, s);
+    if (e == cudaSuccess) e = mg::launch_sor<float>(u_out, f, g, h, b, omega, 1, s);
+  }
+  return op_result(e, "vcycle_up");
 }
 
 mg_status mg_op_multipole_moments(int nx, int ny, int nz, double h, const double* rho, int lmax,

@@ -40,7 +40,7 @@ def test_default_options_layout():
     o = mg.default_opts()
     assert (o.prec, o.mode_fmg, o.pre, o.post) == (0, 1, 1, 1)
     assert o.omega == 1.15 and o.max_cycles == 50 and o.lmax == 4 and o.use_com == 1
-    assert o.stall_ratio == 0.9 and o.inner_fmg == 1 and o.inner_cycles == 3
+    assert o.stall_ratio == 0.9 and o.inner_fmg == 0 and o.inner_cycles == 3
     assert list(o.reserved) == [0] * 8
 
 

@@ -108,6 +108,20 @@ def test_mixed_matches_converged_oracle(bc, n):
     assert emax(phi, ref.phi) <= 1e-9
 
 
+@pytest.mark.parametrize("inner_fmg,inner_cycles", [(1, 1), (1, 3), (0, 1), (0, 5)])
+@pytest.mark.parametrize("bc", [mg.PERIODIC, mg.ZEROGRAD])
+def test_mixed_inner_schedules(inner_fmg, inner_cycles, bc):
+    """Every inner schedule of the FP32 solves converges to the same FP64
+    solution (the outer FP64 loop decides the accuracy)."""
+    n = 64
+    rho, fpg = source(n, bc, seed=21)
+    ref = orc.solve(rho, 1.0 / n, bc, four_pi_G=fpg, tol=0.0, max_cycles=80)
+    phi, hist, st, _ = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED, inner_fmg=inner_fmg,
+                                 inner_cycles=inner_cycles)
+    assert st == 0 and hist[-1] < 1e-10
+    assert emax(phi, ref.phi) <= 1e-9
+
+
 @pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
 def test_mgi_initial_guess(prec):
     n = 16
