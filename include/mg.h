@@ -77,7 +77,11 @@ typedef struct {
                       /*    V-cycles from a zero correction)                         */
   int inner_cycles;   /* MIXED: FP32 V-cycles per outer iteration after the start;  */
                       /*    default 3                                               */
-  int reserved[8];    /* must be zero                                               */
+  int outer_fixed;    /* MIXED: 1 (default): from the second outer iteration on,    */
+                      /*    phi and h^2 f are held as 64-bit integers scaled by 2^S  */
+                      /*    and the outer residual is exact integer arithmetic,     */
+                      /*    rounded once to FP32; 0: FP64 residual and update        */
+  int reserved[7];    /* must be zero                                               */
 } mg_opts;
 
 typedef struct mg_ctx mg_ctx;

@@ -131,6 +131,31 @@ cudaError_t launch_fused_smooth(const float* u_in, float* u_out, const float* f,
                                 Bc bc, double omega, bool zero_guess, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Exact 64-bit fixed-point outer residual (mg_fixed.cu).
+
+// out[0] = max |a| (deterministic two-stage reduction through partials).
+template <typename T>
+cudaError_t launch_absmax(const T* a, long long n, double* partials, double* out, cudaStream_t s);
+// In place: double -> round(a * c) as int64.  out = q * c as doubles (out
+// may alias q).
+cudaError_t launch_f64_to_fx(double* a, long long n, double c, cudaStream_t s);
+cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, double c,
+                             cudaStream_t s);
+// PHI += round(e * c); *flag |= 1 if |PHI| passes 2^60.
+cudaError_t launch_fx_correct(long long* phi, const float* e, long long n, float c, int* flag,
+                              cudaStream_t s);
+// Fused outer step: PHI_out = PHI_in + round(e * c) (e may be null), then
+// r32 = (F - (sum_nb PHI_out - 6 PHI_out)) * factor exactly in integers, one
+// partial sum of r32^2 per block (count in *nb_out, at most nb_max).
+// Requires nx % 32 == 0 and ny % 16 == 0 (fx_step_ok).
+bool fx_step_ok(Grid g);
+int fx_step_blocks(Grid g);
+cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const float* e, float c,
+                           const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
+                           float factor, double* partials, int nb_max, int* flag, int* nb_out,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Multipole boundary (App. A).
 
 // Upload the polynomial tables to this device's constant memory (once per

@@ -46,6 +46,9 @@ struct mg_ctx {
   float* u32b[kMaxLevels] = {};
   float* f32[kMaxLevels] = {};
   double* partials = nullptr;  // reduction partials
+  int* iflag = nullptr;        // device flag (fixed-point overflow)
+  long long* fxbuf = nullptr;  // second integer buffer of the fixed-point outer loop
+  int partials_cap = 0;        // doubles in `partials`
   double* scal = nullptr;      // device scalars: [0] |f|^2 sum, [1] |d|^2 sum, [2..31] multipole
   double* pinned = nullptr;    // host mirror of scal
   double* rho_dev_own = nullptr;  // buffers for mg_solve_host
@@ -481,6 +484,12 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   }
   StopRule rule{tol, c->opts.stall_ratio};
   int n = 0, st = -1;
+  const bool fx = c->opts.outer_fixed != 0 && c->fxbuf != nullptr;
+  double two_S = 1.0;  // 2^S of the fixed-point representation
+  bool in_fx = false;  // phi and f hold integers
+  long long* cur = reinterpret_cast<long long*>(phi);  // integer phi (in phi's own storage)
+  long long* alt = c->fxbuf;
+  const long long* FX = reinterpret_cast<const long long*>(f);
   for (int it = 0;; ++it) {
     if (rn == 0.0) {  // exact already (zero source with a homogeneous rule)
       hist[n++] = 0.0;
@@ -488,23 +497,77 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       break;
     }
     inner_solve(c, hom, s);
-    {
-      KTimer t(c, MG_K_CORRECT, true, s);
-      check(c, mg::launch_correct(phi, c->u32[F], N, 1.0 / scale, s), "correct");
-    }
+    const double old_scale = scale;
     scale = 1.0 / rn;  // the next residual is scaled by the current one's size
-    {
+    if (!fx) {
+      {
+        KTimer t(c, MG_K_CORRECT, true, s);
+        check(c, mg::launch_correct(phi, c->u32[F], N, 1.0 / old_scale, s), "correct");
+      }
       KTimer t(c, MG_K_OUTER_RESIDUAL, true, s);
       check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
             "outer residual");
+      check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
+      rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
+    } else {
+      if (it == 0) {
+        // S such that |phi| < 2^55 and |h^2 f| < 2^58 on the integer grid;
+        // phi after this step is at most max|phi_0| + max|e| / scale.
+        check(c, mg::launch_absmax<float>(c->u32[F], N, c->partials, c->scal + 50, s), "max |e|");
+        check(c, mg::launch_absmax<double>(f, N, c->partials, c->scal + 51, s), "max |f|");
+        if (!c->opts.mode_fmg)
+          check(c, mg::launch_absmax<double>(phi, N, c->partials, c->scal + 52, s), "max |phi|");
+        else
+          check(c, cudaMemsetAsync(c->scal + 52, 0, sizeof(double), s), "zero");
+        check(c, cudaMemcpyAsync(c->pinned + 50, c->scal + 50, 3 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s),
+              "read max");
+        check(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), s), "clear flag");
+        check(c, cudaStreamSynchronize(s), "sync");
+        const double mphi = c->pinned[52] + c->pinned[50] / old_scale;
+        const double mf = c->pinned[51] * c->h * c->h;
+        double lim = 0.0;
+        if (mphi > 0.0) lim = std::ldexp(1.0, 55) / mphi;
+        if (mf > 0.0 && (lim == 0.0 || std::ldexp(1.0, 58) / mf < lim))
+          lim = std::ldexp(1.0, 58) / mf;
+        if (lim == 0.0) lim = std::ldexp(1.0, 55);
+        int e2 = 0;
+        std::frexp(lim, &e2);
+        two_S = std::ldexp(1.0, e2 - 1);  // largest power of two <= lim
+        check(c, mg::launch_f64_to_fx(f, N, c->h * c->h * two_S, s), "h^2 f -> fixed point");
+        check(c, mg::launch_f64_to_fx(phi, N, two_S, s), "phi -> fixed point");
+        in_fx = true;
+      }
+      int nbs = 0;
+      {
+        KTimer t(c, MG_K_OUTER_RESIDUAL, true, s);
+        check(c, mg::launch_fx_step(cur, alt, c->u32[F], (float)(two_S / old_scale), FX,
+                                    c->f32[F], g, bc, two_S,
+                                    (float)(scale / (c->h * c->h * two_S)), c->partials,
+                                    c->partials_cap, c->iflag, &nbs, s),
+              "fixed-point step");
+      }
+      std::swap(cur, alt);
+      check(c, mg::launch_finish_sum(c->partials, nbs, c->scal + 1, s), "finish r^2");
+      rn = std::sqrt(read_scalar(c, 1, s) / (double)N) / scale;
     }
-    check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
-    rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
     const double r = rn / fnorm;
     hist[n++] = r;
     rule.record(r);
     st = rule.decide(r, it + 1, c->opts.max_cycles, n, hist_cap);
     if (st >= 0) break;
+  }
+  if (in_fx) {
+    check(c, mg::launch_fx_to_f64(cur, phi, N, 1.0 / two_S, s), "fixed point -> phi");
+    int flag = 0;
+    check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s),
+          "read flag");
+    check(c, cudaStreamSynchronize(s), "sync");
+    std::memcpy(&flag, c->pinned + 60, sizeof(int));
+    if (flag) {
+      c->err = "fixed-point outer loop: |phi| passed 2^60 (the solve diverged)";
+      st = MG_ERR_DIVERGED;
+    }
   }
   remove_mean(c, phi, s);
   *n_hist = n;
@@ -517,6 +580,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (!(o.omega > 0.0 && o.omega < 2.0)) return MG_ERR_ARG;
   if (o.max_cycles < 0 || o.lmax < 0 || o.lmax > 4) return MG_ERR_ARG;
   if (o.inner_cycles < 0 || o.inner_cycles > 64) return MG_ERR_ARG;
+  if (o.outer_fixed != 0 && o.outer_fixed != 1) return MG_ERR_ARG;
   if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;
@@ -542,6 +606,7 @@ void mg_opts_init(mg_opts* o) {
   o->stall_ratio = 0.9;
   o->inner_fmg = 0;
   o->inner_cycles = 3;
+  o->outer_fixed = 1;
 }
 
 const char* mg_status_str(mg_status s) {
@@ -635,8 +700,15 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
       c->f64[F] = dalloc<double>(c, level_grid(c, F).cells());
       if (bc == MG_BC_OPEN) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
     }
-    c->partials = dalloc<double>(c, mg::kPartials);
+    c->partials_cap = mg::kPartials;
+    if (o.prec == MG_MIXED && o.outer_fixed && mg::fx_step_ok(level_grid(c, F))) {
+      c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
+      const int nb = mg::fx_step_blocks(level_grid(c, F));
+      if (nb > c->partials_cap) c->partials_cap = nb;
+    }
+    c->partials = dalloc<double>(c, c->partials_cap);
     c->scal = dalloc<double>(c, 64);
+    c->iflag = dalloc<int>(c, 4);
     check(c, cudaMallocHost(&c->pinned, 64 * sizeof(double)), "cudaMallocHost");
   } catch (const Fail& f) {
     mg_destroy(c);

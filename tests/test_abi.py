@@ -3,6 +3,7 @@ entry point include/mg.h declares.  No compute call is made here."""
 import ctypes
 import os
 import re
+import subprocess
 
 import paper_2302_13903_gb300 as mg
 
@@ -41,7 +42,24 @@ def test_default_options_layout():
     assert (o.prec, o.mode_fmg, o.pre, o.post) == (0, 1, 1, 1)
     assert o.omega == 1.15 and o.max_cycles == 50 and o.lmax == 4 and o.use_com == 1
     assert o.stall_ratio == 0.9 and o.inner_fmg == 0 and o.inner_cycles == 3
-    assert list(o.reserved) == [0] * 8
+    assert o.outer_fixed == 1
+    assert list(o.reserved) == [0] * 7
+
+
+def test_opts_layout_matches_the_c_header(tmp_path):
+    """The ctypes mirror of mg_opts has the C compiler's size and offsets."""
+    fields = [f for f, _ in mg.Opts._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mg.h"\nint main(void){\n'
+                   + 'printf("%zu\\n", sizeof(mg_opts));\n'
+                   + "".join(f'printf("%zu\\n", offsetof(mg_opts, {f}));\n' for f in fields)
+                   + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(mg.Opts)
+    assert out[1:] == [getattr(mg.Opts, f).offset for f in fields]
 
 
 def test_status_strings_and_faces_count():

@@ -3,7 +3,8 @@
 FP64 path: the same schedule (FMG + k V-cycles) on both sides agrees to
 e_max = max|phi_gpu - phi_ref| / max|phi_ref| <= 1e-11 at every k, and the
 solve to tolerance agrees with the oracle's converged solution to 1e-11.
-Mixed path (FP32 multigrid inside FP64 defect correction): the solution at
+Mixed path (FP32 multigrid inside an FP64-accurate defect correction, with
+the outer residual in FP64 or exact 64-bit fixed point): the solution at
 ||d||/||f|| < 1e-10 agrees with the oracle's converged FP64 solution to 1e-9.
 """
 import math
@@ -96,13 +97,16 @@ def test_fp64_sinusoid_64_exact_discrete_solution():
     assert emax(phi, ref.phi) <= 1e-11
 
 
+@pytest.mark.parametrize("outer_fixed", [1, 0])
 @pytest.mark.parametrize("bc", BCS)
 @pytest.mark.parametrize("n", [16, 64])
-def test_mixed_matches_converged_oracle(bc, n):
+def test_mixed_matches_converged_oracle(bc, n, outer_fixed):
+    """Both outer loops -- the exact 64-bit fixed-point residual (default) and
+    the FP64 one -- reach the oracle's converged FP64 solution."""
     rho, fpg = source(n, bc, seed=9)
     ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0, four_pi_G=fpg,
                     tol=0.0, max_cycles=80)
-    phi, hist, st, _ = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED)
+    phi, hist, st, _ = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED, outer_fixed=outer_fixed)
     assert st == 0, (st, hist)
     assert hist[-1] < 1e-10
     assert emax(phi, ref.phi) <= 1e-9
