@@ -100,6 +100,13 @@ void mg_opts_init(mg_opts *opts);
 mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts *opts,
                     mg_ctx **ctx);
 
+/* Device bytes mg_create would allocate for this grid and these options
+ * (the level hierarchy and scratch, as requested from cudaMalloc; the
+ * allocator's rounding is not included).  Allocates nothing.  Errors:
+ * MG_ERR_ARG as mg_create. */
+mg_status mg_required_bytes(int nx, int ny, int nz, mg_bc bc, const mg_opts *opts,
+                            size_t *bytes);
+
 /* Solve for phi given rho: f = four_pi_G * rho; for periodic and
  * zero-gradient grids the mean of f is removed and the returned phi has zero
  * mean (Sec. 2.3.6); for open grids phi -> 0 at infinity.  rho_dev and
@@ -258,8 +265,127 @@ mg_status mg_op_multipole_moments_noalloc(int nx, int ny, int nz, double h, cons
                                           int lmax, int use_com, double *origin_host,
                                           double *Q_host, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solve: many independent grids in one persistent launch.
+ * ---------------------------------------------------------------------- */
+typedef struct mg_batch mg_batch;
+
+/* Create a batch of n grids: grid g has dims[3g..3g+2] cells (cubic, a power
+ * of two from 2 to 1024), spacing dx[g], rule bcs[g] (periodic, fixed or zero
+ * gradient; fixed_values[g] is b for a fixed rule, NULL means 0).  Every grid
+ * is solved by the mixed-precision method (an FP64 defect-correction loop --
+ * source, residual, correction and norms in FP64 -- around FP32 V(1,1)
+ * cycles): opts->prec must be MG_MIXED, pre = post = 1, mode_fmg = 1 (phi
+ * starts at 0), inner_fmg = 0; max_cycles (outer iterations, <= 64) and
+ * inner_cycles (V-cycles per outer iteration) are shared.  All level storage
+ * is allocated here.  Errors: MG_ERR_ARG, MG_ERR_OOM. */
+mg_status mg_batch_create(int n, const int *dims, const double *dx, const mg_bc *bcs,
+                          const double *fixed_values, const mg_opts *opts, mg_batch **batch);
+
+/* Solve every grid: rho_dev[g], phi_dev[g] are the FP64 device arrays of grid
+ * g, four_pi_G[g] and tol[g] its constants (host arrays of n).  One persistent
+ * cooperative kernel runs every phase of every grid; the first call captures
+ * the upload of the per-grid arguments, the kernel and the download of the
+ * results as a CUDA graph (so make it outside any capture of your own) and
+ * later calls replay it; each grid stops by the
+ * rule of mg_solve (Sec. 2.3.7).  hist (host, n * hist_cap, may be NULL)
+ * receives each grid's ||d||/||f|| after every outer iteration, n_hist[g] the
+ * count, status[g] its result.  Returns MG_OK when every grid converged, else
+ * the first failing grid's status, MG_ERR_TIMEOUT if a grid-wide barrier wait
+ * ran out (about 2 s), MG_ERR_CUDA.  Synchronises `stream`. */
+mg_status mg_batch_solve(mg_batch *batch, const double *const *rho_dev, const double *four_pi_G,
+                         const double *tol, double *const *phi_dev, double *hist, int hist_cap,
+                         int *n_hist, mg_status *status, void *stream);
+
+mg_status mg_batch_destroy(mg_batch *batch);
+
+/* Total cells of the finest levels of the batch. */
+long long mg_batch_cells(const mg_batch *batch);
+
+/* 1 when the solve runs as a captured CUDA graph (captured on the first
+ * mg_batch_solve and replayed after), 0 when it is launched directly. */
+int mg_batch_graph(const mg_batch *batch);
+
+const char *mg_batch_last_error(const mg_batch *batch);
+
 /* Number of doubles in a faces array of an nx*ny*nz level. */
 size_t mg_faces_count(int nx, int ny, int nz);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop.  Requests (solves of any supported size and boundary rule)
+ * are submitted one at a time and return a ticket at once.  `slots` worker
+ * threads, each with its own CUDA stream, take queued requests in arrival
+ * order as soon as a slot is free and the request's level hierarchy is
+ * resident and idle or fits in the HBM budget (idle hierarchies of other
+ * sizes are evicted least recently used first); a later request may pass a
+ * waiting one up to 64 times, then the waiting one holds the next free slot.
+ * Hierarchies stay resident between requests of the same key (cells, dx,
+ * rule, fixed value, lmax).  Requests on different slots run concurrently on
+ * the device; each result equals the result of the same request alone.  The
+ * server is internally synchronised: any thread may submit, poll and wait.
+ * --------------------------------------------------------------------------- */
+typedef struct mg_server mg_server;
+
+typedef struct {
+  int nx, ny, nz;        /* cubic power of two >= 2 */
+  double dx;             /* cell width */
+  mg_bc bc;
+  double fixed_value;    /* boundary value b of MG_BC_FIXED */
+  int lmax;              /* multipole order 0..4 of MG_BC_OPEN */
+  const double *rho;     /* FP64 device array, nx*ny*nz, caller-owned */
+  double four_pi_G;
+  double tol;            /* ||d||/||f|| target of this request */
+  double *phi;           /* FP64 device array written with the result */
+} mg_request;
+
+typedef struct {
+  int done;              /* 0 while queued or running */
+  mg_status status;      /* the solve's status (as mg_solve) once done */
+  int n_hist;            /* entries written to hist */
+  int reserved;
+  double queue_ms;       /* submission -> a slot took it */
+  double solve_ms;       /* slot took it -> result in phi (stream synchronised) */
+  double total_ms;       /* submission -> result: the request's latency */
+} mg_result;
+
+typedef struct {
+  long long submitted, completed, rejected, evictions, created, cells_completed;
+  size_t budget_bytes, resident_bytes, peak_bytes; /* hierarchy bytes as mg_required_bytes */
+  int queued, running, slots, resident;
+} mg_server_stats;
+
+/* Start a server on the current device: hbm_budget_bytes bounds the bytes of
+ * all resident hierarchies together (mg_required_bytes of each); slots
+ * (1..64) worker threads; at most max_queue (>= 1) requests wait at a time.
+ * opts (NULL: defaults) apply to every request except lmax and fixed_value,
+ * which come with each request.  Errors: MG_ERR_ARG. */
+mg_status mg_server_create(size_t hbm_budget_bytes, int slots, int max_queue,
+                           const mg_opts *opts, mg_server **server);
+
+/* Queue one request; *ticket names it.  rho and phi must stay valid and phi
+ * untouched by the caller until the request is done.  Errors: MG_ERR_ARG
+ * (invalid request), MG_ERR_OOM (its hierarchy alone exceeds the budget),
+ * MG_ERR_BUSY (the queue is full; nothing was queued). */
+mg_status mg_server_submit(mg_server *server, const mg_request *request, long long *ticket);
+
+/* State of a ticket without waiting.  Once it reports done = 1 the ticket
+ * is retired (a later poll returns MG_ERR_ARG).  hist (host, hist_cap
+ * entries, may be NULL) receives the residual history as mg_solve's. */
+mg_status mg_server_poll(mg_server *server, long long ticket, mg_result *result, double *hist,
+                         int hist_cap);
+
+/* Wait up to timeout_s seconds for a ticket; retires it when done.  Returns
+ * MG_ERR_TIMEOUT (ticket kept, result->done = 0) when time ran out. */
+mg_status mg_server_wait(mg_server *server, long long ticket, double timeout_s,
+                         mg_result *result, double *hist, int hist_cap);
+
+mg_status mg_server_get_stats(mg_server *server, mg_server_stats *stats);
+
+/* Finish every queued and running request, free all hierarchies, stop the
+ * workers. */
+mg_status mg_server_destroy(mg_server *server);
+
+const char *mg_server_last_error(const mg_server *server);
 
 #ifdef __cplusplus
 }

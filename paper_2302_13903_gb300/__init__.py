@@ -28,6 +28,10 @@ EXPORTS = [
     "mg_op_coarsest", "mg_op_multipole_moments", "mg_op_open_faces", "mg_faces_count",
     "mg_ctx_set_timing", "mg_ctx_kernel_time", "mg_op_multipole_moments_noalloc",
     "mg_op_vcycle_down", "mg_op_vcycle_up",
+    "mg_batch_create", "mg_batch_solve", "mg_batch_destroy", "mg_batch_cells",
+    "mg_batch_last_error", "mg_batch_graph", "mg_required_bytes",
+    "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
+    "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
            "correct", "source", "fused_down", "fused_up"]
@@ -42,6 +46,37 @@ class Opts(ctypes.Structure):
         ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("outer_fixed", ctypes.c_int), ("reserved", ctypes.c_int * 7),
     ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_double),
+        ("bc", ctypes.c_int), ("fixed_value", ctypes.c_double), ("lmax", ctypes.c_int),
+        ("rho", ctypes.c_void_p), ("four_pi_G", ctypes.c_double), ("tol", ctypes.c_double),
+        ("phi", ctypes.c_void_p),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("done", ctypes.c_int), ("status", ctypes.c_int), ("n_hist", ctypes.c_int),
+        ("reserved", ctypes.c_int), ("queue_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+        ("total_ms", ctypes.c_double),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+        ("rejected", ctypes.c_longlong), ("evictions", ctypes.c_longlong),
+        ("created", ctypes.c_longlong), ("cells_completed", ctypes.c_longlong),
+        ("budget_bytes", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t),
+        ("peak_bytes", ctypes.c_size_t), ("queued", ctypes.c_int), ("running", ctypes.c_int),
+        ("slots", ctypes.c_int), ("resident", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class MGError(RuntimeError):
@@ -109,8 +144,37 @@ def lib():
             L.mg_ctx_set_timing.restype = i
             L.mg_ctx_kernel_time.argtypes = [p, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
             L.mg_ctx_kernel_time.restype = i
+            L.mg_batch_create.argtypes = [i, p, p, p, p, ctypes.POINTER(Opts), ctypes.POINTER(p)]
+            L.mg_batch_create.restype = i
+            L.mg_batch_solve.argtypes = [p, p, p, p, p, p, i, p, p, p]
+            L.mg_batch_solve.restype = i
+            L.mg_batch_destroy.argtypes = [p]
+            L.mg_batch_destroy.restype = i
+            L.mg_batch_cells.argtypes = [p]
+            L.mg_batch_cells.restype = ctypes.c_longlong
+            L.mg_batch_graph.argtypes = [p]
+            L.mg_batch_graph.restype = i
+            L.mg_batch_last_error.argtypes = [p]
+            L.mg_batch_last_error.restype = ctypes.c_char_p
             L.mg_faces_count.argtypes = [i, i, i]
             L.mg_faces_count.restype = sz
+            L.mg_required_bytes.argtypes = [i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+            L.mg_required_bytes.restype = i
+            L.mg_server_create.argtypes = [sz, i, i, ctypes.POINTER(Opts), ctypes.POINTER(p)]
+            L.mg_server_create.restype = i
+            L.mg_server_submit.argtypes = [p, ctypes.POINTER(Request),
+                                           ctypes.POINTER(ctypes.c_longlong)]
+            L.mg_server_submit.restype = i
+            L.mg_server_poll.argtypes = [p, ctypes.c_longlong, ctypes.POINTER(Result), p, i]
+            L.mg_server_poll.restype = i
+            L.mg_server_wait.argtypes = [p, ctypes.c_longlong, d, ctypes.POINTER(Result), p, i]
+            L.mg_server_wait.restype = i
+            L.mg_server_get_stats.argtypes = [p, ctypes.POINTER(ServerStats)]
+            L.mg_server_get_stats.restype = i
+            L.mg_server_destroy.argtypes = [p]
+            L.mg_server_destroy.restype = i
+            L.mg_server_last_error.argtypes = [p]
+            L.mg_server_last_error.restype = ctypes.c_char_p
             _lib = L
     return _lib
 
@@ -346,3 +410,142 @@ def op_open_faces(n, h, Q, lmax, G, origin, device="cuda", stream=None):
 
 def faces_count(nx, ny, nz):
     return lib().mg_faces_count(nx, ny, nz)
+
+
+class Batch:
+    """Many independent grids solved by one persistent launch (mg_batch_*)."""
+
+    def __init__(self, sizes, dxs, bcs, fixed_values=None, **opts):
+        self.n = len(sizes)
+        opts.setdefault("prec", MIXED)
+        opts.setdefault("max_cycles", 12)  # outer iterations unrolled into the phase list
+        self.opts = default_opts(**opts)
+        dims = np.repeat(np.asarray(sizes, dtype=np.int32), 3)
+        dx = np.ascontiguousarray(dxs, dtype=np.float64)
+        bc = np.ascontiguousarray(bcs, dtype=np.int32)
+        fv = None if fixed_values is None else np.ascontiguousarray(fixed_values, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = lib().mg_batch_create(self.n, dims.ctypes.data, dx.ctypes.data, bc.ctypes.data,
+                                   None if fv is None else fv.ctypes.data, ctypes.byref(self.opts),
+                                   ctypes.byref(h))
+        if st != 0:
+            raise MGError(st, lib().mg_batch_last_error(None).decode())
+        self.ptr = h
+        self.sizes = list(sizes)
+
+    @property
+    def cells(self):
+        return lib().mg_batch_cells(self.ptr)
+
+    @property
+    def graph(self):
+        return bool(lib().mg_batch_graph(self.ptr))
+
+    def solve(self, rhos, phis, four_pi_G=1.0, tol=1e-10, hist_cap=64, stream=None):
+        """rhos, phis: lists of CUDA float64 tensors.  Returns (status, hists, statuses)."""
+        import torch
+        n = self.n
+        rp = np.array([_dptr(r, torch.float64) for r in rhos], dtype=np.uint64)
+        pp = np.array([_dptr(q, torch.float64) for q in phis], dtype=np.uint64)
+        fpg = np.broadcast_to(np.asarray(four_pi_G, dtype=np.float64), (n,)).copy()
+        tl = np.broadcast_to(np.asarray(tol, dtype=np.float64), (n,)).copy()
+        hist = np.zeros((n, hist_cap))
+        nh = np.zeros(n, dtype=np.int32)
+        sts = np.zeros(n, dtype=np.int32)
+        st = lib().mg_batch_solve(self.ptr, rp.ctypes.data, fpg.ctypes.data, tl.ctypes.data,
+                                  pp.ctypes.data, hist.ctypes.data, hist_cap, nh.ctypes.data,
+                                  sts.ctypes.data, _stream_ptr(stream))
+        if st in (3, 6):
+            raise MGError(st, lib().mg_batch_last_error(self.ptr).decode())
+        return st, [hist[g, : nh[g]].copy() for g in range(n)], sts
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().mg_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def required_bytes(n, bc=PERIODIC, **opts) -> int:
+    """Device bytes ``mg_create`` allocates for an n^3 grid (mg_required_bytes)."""
+    o = default_opts(**opts)
+    b = ctypes.c_size_t(0)
+    _check(lib().mg_required_bytes(n, n, n, bc, ctypes.byref(o), ctypes.byref(b)))
+    return b.value
+
+
+class Server:
+    """The serving loop (mg_server_*): submit solves, poll or wait for them."""
+
+    def __init__(self, budget_bytes, slots=4, max_queue=1024, **opts):
+        opts.setdefault("prec", MIXED)
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        st = lib().mg_server_create(int(budget_bytes), slots, max_queue, ctypes.byref(self.opts),
+                                    ctypes.byref(h))
+        if st != 0:
+            raise MGError(st, lib().mg_server_last_error(None).decode())
+        self.ptr = h
+
+    def submit(self, rho, phi, dx=None, bc=PERIODIC, four_pi_G=1.0, tol=1e-10, lmax=4,
+               fixed_value=0.0):
+        """rho, phi: CUDA float64 (n, n, n) tensors kept alive until done.
+        Returns the ticket, or raises MGError (MG_ERR_BUSY when the queue is full)."""
+        import torch
+        n = rho.shape[0]
+        q = Request(n, n, n, 1.0 / n if dx is None else dx, bc, fixed_value, lmax,
+                    _dptr(rho, torch.float64), four_pi_G, tol, _dptr(phi, torch.float64))
+        t = ctypes.c_longlong(0)
+        st = lib().mg_server_submit(self.ptr, ctypes.byref(q), ctypes.byref(t))
+        if st != 0:
+            raise MGError(st, lib().mg_server_last_error(self.ptr).decode())
+        return t.value
+
+    def _result(self, fn, ticket, *extra, hist_cap=64):
+        r = Result()
+        hist = np.zeros(hist_cap)
+        st = fn(self.ptr, ticket, *extra, ctypes.byref(r), hist.ctypes.data, hist_cap)
+        if st not in (0, 6):
+            raise MGError(st, lib().mg_server_last_error(self.ptr).decode())
+        return r, hist[: r.n_hist].copy()
+
+    def poll(self, ticket):
+        """(Result, hist); the ticket is retired once Result.done is 1."""
+        return self._result(lib().mg_server_poll, ticket)
+
+    def wait(self, ticket, timeout=60.0):
+        """Block until done (or the timeout: Result.done stays 0)."""
+        return self._result(lib().mg_server_wait, ticket, float(timeout))
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().mg_server_get_stats(self.ptr, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().mg_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

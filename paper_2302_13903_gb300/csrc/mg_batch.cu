@@ -1,0 +1,742 @@
+// mg_batch.cu -- many independent grids solved by one persistent launch.
+//
+// Each grid is solved by the mixed-precision method of the single-grid path:
+// an FP64 outer defect-correction loop (source, residual, correction and
+// norms in FP64) around FP32 V(1,1) cycles on the correction equation
+// (Algorithm 1 with the homogeneous rule on every level).  All grids advance
+// together through a fixed list of phases; a phase is a set of independent
+// work items (a tile of one grid's level, a chunk of one grid's finest level,
+// or one whole grid) that the CTAs of a persistent cooperative kernel take
+// from an atomic counter.  Phases are separated by a grid-wide barrier whose
+// waits are bounded in time (on expiry the kernel records an error and every
+// CTA returns).  Per grid, the stopping rule of the single-grid solve
+// (||d||/||f|| < tol, stall, divergence, max_cycles) is applied after every
+// outer iteration; a stopped grid's items become empty.
+//
+// Work items by phase:
+//   source: f = 4 pi G rho, mean removal, ||f||     (chunks of 32768 cells)
+//   first residual r = f - L(0), FP32 copy           (chunks)
+//   per V-cycle: down legs on levels >= 64^3 (fused tiles), one CTA per grid
+//     for the levels <= 32^3 (whole coarse cycle), up legs on levels >= 64^3
+//   correction phi += e / scale, FP64 residual + norm (chunks), stopping rule
+//     (one item per grid)
+//   at the end: <phi> = 0 for periodic and zero-gradient grids (chunks)
+// Partial sums live in per-chunk slots and are added in chunk order, so every
+// result is independent of which CTA ran which item.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_bottom.cuh"
+#include "mg_device.cuh"
+#include "mg_fused.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+namespace batch {
+
+constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4>::NT;  // 216
+constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4>::SMEM;
+constexpr int kMaxL = 16;
+constexpr int kChunk = 32768;   // cells per chunk item
+constexpr int kFusedMinN = 64;  // levels of at least 64^3 use the fused tiles
+constexpr int kCz = 32;         // z-chunk of fused tiles
+constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct GridDev {
+  int n, L, bc;
+  double h, bcval, fpg, tol;
+  const double* rho;
+  double* phi;
+  double* f64;
+  float* u32[kMaxL];
+  float* u32b[kMaxL];
+  float* f32[kMaxL];
+  int chunk0, nchunk;  // this grid's chunk items (same layout in every chunk phase)
+  // state
+  double mean, fnorm, rn, scale, prev, d0;
+  int stalls, active, status, nh, cycles;
+};
+
+enum PhaseType : int {
+  PH_SRC = 0,      // chunk: f = fpg rho, partial sum f
+  PH_MEANFIN,      // grid: mean (periodic / zero gradient)
+  PH_SRC2,         // chunk: f -= mean, partial sum f^2
+  PH_NORMFIN,      // grid: ||f||
+  PH_R0,           // chunk: r = f - L(0) in FP64 -> r32 = r / ||f||, partial sum r^2
+  PH_R0FIN,        // grid: rn
+  PH_DOWN,         // tile: fused down leg on level size `n`
+  PH_BOTTOM,       // grid: levels <= 32^3 of one V-cycle
+  PH_UP,           // tile: fused up leg on level size `n`
+  PH_CORR,         // chunk: phi += e / scale
+  PH_RESID,        // chunk: FP64 residual -> r32, partial sum r^2
+  PH_FIN,          // grid: stopping rule, history
+  PH_PSUM,         // chunk: partial sum phi
+  PH_PMEAN,        // grid: mean of phi
+  PH_PSUB          // chunk: phi -= mean
+};
+
+struct Phase {
+  int type;
+  int n;       // level size (DOWN / UP)
+  int first;   // first item in the item list
+  int count;   // items
+  int cycle;   // inner cycle index within the outer iteration (DOWN / BOTTOM)
+};
+
+struct Item {
+  int grid, a, b, c;
+};
+
+struct Ctl {
+  const Phase* phases;
+  const Item* items;
+  GridDev* grids;
+  double* part;        // one slot per chunk
+  double* hist;        // [ngrids][hist_cap]
+  unsigned* counters;  // one per phase
+  unsigned* bar_count;
+  unsigned* bar_gen;
+  int* err;
+  int* active_left;    // grids still active, after each FIN phase (index = phase)
+  int nphases, ngrids, hist_cap;
+  double omega;
+  int max_cycles, inner_zero;
+  double stall_ratio;
+};
+
+__device__ bool grid_barrier(const Ctl& c) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = c.bar_gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(c.bar_count, 1u) == gridDim.x - 1) {
+      *c.bar_count = 0;
+      __threadfence();
+      atomicAdd(c.bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (clock64() - t0 > kBarrierCycles) {
+          atomicOr(c.err, 1);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)c.err) == 0;
+}
+
+__device__ __forceinline__ int level_of(const GridDev& g, int n) {
+  int l = g.L - 1, m = g.n;
+  while (m > n) {
+    m >>= 1;
+    --l;
+  }
+  return l;
+}
+
+__device__ __forceinline__ Bc phys_bc(const GridDev& g) { return Bc{g.bc, g.bcval, nullptr}; }
+__device__ __forceinline__ Bc hom_bc(const GridDev& g) {
+  return Bc{g.bc == BC_FIXED ? BC_FIXED : g.bc, 0.0, nullptr};
+}
+
+// Sum over the CTA in thread order (the block is not a whole number of
+// warps); the result is valid in thread 0.
+__device__ double block_sum(double v) {
+  __shared__ double ws[kThreads];
+  ws[threadIdx.x] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)blockDim.x; ++q) r += ws[q];
+  __syncthreads();
+  return r;
+}
+
+// One chunk of the finest level: cells [c * kChunk, min(N, (c + 1) kChunk)).
+template <int TYPE>
+__device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
+  const Grid gr{g.n, g.n, g.n};
+  const long long N = gr.cells();
+  const long long lo = (long long)chunk * kChunk, hi = min(N, lo + kChunk);
+  const int F = g.L - 1;
+  double acc = 0.0;
+  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (TYPE == PH_SRC) {
+      const double v = g.fpg * g.rho[t];
+      g.f64[t] = v;
+      acc += v;
+    } else if (TYPE == PH_SRC2) {
+      const double v = g.f64[t] - g.mean;
+      g.f64[t] = v;
+      acc += v * v;
+    } else if (TYPE == PH_CORR) {
+      g.phi[t] += (double)g.u32[F][t] / g.scale;
+    } else if (TYPE == PH_PSUM) {
+      acc += g.phi[t];
+    } else if (TYPE == PH_PSUB) {
+      g.phi[t] -= g.mean;
+    } else {  // PH_R0 (phi = 0) and PH_RESID
+      const int i = (int)(t % gr.nx);
+      const long long r = t / gr.nx;
+      const int j = (int)(r % gr.ny), k = (int)(r / gr.ny);
+      double d;
+      if (TYPE == PH_R0) {
+        g.phi[t] = 0.0;
+        // L_h(0) is nonzero only through the fixed value's ghosts (2 b each)
+        int faces = 0;
+        if (g.bc == BC_FIXED) faces = (i == 0) + (i == gr.nx - 1) + (j == 0) + (j == gr.ny - 1) +
+                                      (k == 0) + (k == gr.nz - 1);
+        d = g.f64[t] - (faces * 2.0 * g.bcval) / (g.h * g.h);
+      } else {
+        const double s = dev::neighbour_sum(g.phi, i, j, k, gr, phys_bc(g));
+        d = g.f64[t] - (s - 6.0 * g.phi[t]) / (g.h * g.h);
+      }
+      const double sc = TYPE == PH_R0 ? 1.0 / g.fnorm : 1.0 / g.rn;
+      g.f32[F][t] = (float)(d * sc);
+      acc += d * d;
+    }
+  }
+  if (TYPE == PH_SRC || TYPE == PH_SRC2 || TYPE == PH_R0 || TYPE == PH_RESID || TYPE == PH_PSUM) {
+    const double b = block_sum(acc);
+    if (threadIdx.x == 0) c.part[g.chunk0 + chunk] = b;
+  }
+}
+
+__device__ double chunk_total(const Ctl& c, const GridDev& g) {
+  double s = 0.0;
+  for (int q = 0; q < g.nchunk; ++q) s += c.part[g.chunk0 + q];
+  return s;
+}
+
+// Stopping rule of the single-grid solve, after one outer iteration.
+__device__ void fin_item(const Ctl& c, GridDev& g, int gi) {
+  const double N = (double)g.n * g.n * g.n;
+  const double rn = sqrt(chunk_total(c, g) / N);
+  const double r = rn / g.fnorm;
+  g.scale = 1.0 / g.rn;  // the scale the residual just written used
+  g.rn = rn;
+  if (g.nh < c.hist_cap) c.hist[(size_t)gi * c.hist_cap + g.nh] = r;
+  g.nh++;
+  g.cycles++;
+  if (g.prev >= 0.0) g.stalls = (r > c.stall_ratio * g.prev) ? g.stalls + 1 : 0;
+  g.prev = r;
+  if (g.d0 < 0.0) g.d0 = r;
+  int st = -1;
+  if (isnan(r) || isinf(r) || r > 10.0 * g.d0) st = MG_ERR_DIVERGED;
+  else if (r < g.tol) st = MG_OK;
+  else if (g.stalls >= 2) st = g.tol == 0.0 ? MG_OK : MG_ERR_NOT_CONVERGED;
+  else if (g.cycles >= c.max_cycles || g.nh >= c.hist_cap) st = MG_ERR_NOT_CONVERGED;
+  if (st >= 0) {
+    g.status = st;
+    g.active = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_batch(Ctl c) {
+  extern __shared__ float4 smem[];
+  for (int ph = 0; ph < c.nphases; ++ph) {
+    const Phase P = c.phases[ph];
+    __shared__ int s_item;
+    for (;;) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(&c.counters[ph], 1u);
+      __syncthreads();
+      const int it = s_item;
+      __syncthreads();
+      if (it >= P.count) break;
+      const Item I = c.items[P.first + it];
+      GridDev& g = c.grids[I.grid];
+      const bool run = (P.type >= PH_PSUM) || g.active;
+      if (!run) continue;
+      switch (P.type) {
+        case PH_SRC: chunk_item<PH_SRC>(c, g, I.a); break;
+        case PH_SRC2: chunk_item<PH_SRC2>(c, g, I.a); break;
+        case PH_R0: chunk_item<PH_R0>(c, g, I.a); break;
+        case PH_CORR: chunk_item<PH_CORR>(c, g, I.a); break;
+        case PH_RESID: chunk_item<PH_RESID>(c, g, I.a); break;
+        case PH_PSUM: chunk_item<PH_PSUM>(c, g, I.a); break;
+        case PH_PSUB: chunk_item<PH_PSUB>(c, g, I.a); break;
+        case PH_MEANFIN:
+          if (threadIdx.x == 0)
+            g.mean = (g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD)
+                         ? chunk_total(c, g) / ((double)g.n * g.n * g.n)
+                         : 0.0;
+          break;
+        case PH_PMEAN:
+          if (threadIdx.x == 0)
+            g.mean = (g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD)
+                         ? chunk_total(c, g) / ((double)g.n * g.n * g.n)
+                         : 0.0;
+          break;
+        case PH_NORMFIN:
+          if (threadIdx.x == 0) {
+            g.fnorm = sqrt(chunk_total(c, g) / ((double)g.n * g.n * g.n));
+            if (g.fnorm == 0.0) g.fnorm = 1.0;  // r = f - L(0) decides below
+          }
+          break;
+        case PH_R0FIN:
+          if (threadIdx.x == 0) {
+            g.rn = sqrt(chunk_total(c, g) / ((double)g.n * g.n * g.n));
+            g.scale = 1.0 / g.fnorm;  // r32 = r / ||f||
+            if (g.rn == 0.0) {  // phi = 0 is exact
+              g.active = 0;
+              g.status = MG_OK;
+              if (c.hist_cap > 0) c.hist[(size_t)I.grid * c.hist_cap] = 0.0;
+              g.nh = 1;
+            }
+          }
+          break;
+        case PH_FIN:
+          if (threadIdx.x == 0) {
+            fin_item(c, g, I.grid);
+            if (g.active) atomicAdd(&c.active_left[ph], 1);
+          }
+          break;
+        case PH_BOTTOM: {
+          bottom::BottomArgs<float> a;
+          const int top = level_of(g, min(g.n, 32));
+          for (int l = 0; l < kBottomLevels; ++l) {
+            const bool used = l <= top;
+            a.u[l] = used ? g.u32[l] : nullptr;
+            a.f[l] = used ? g.f32[l] : nullptr;
+            a.n[l] = used ? (g.n >> (g.L - 1 - l)) : 0;
+            a.h[l] = used ? g.h * (double)(1 << (g.L - 1 - l)) : 0.0;
+            a.bc[l] = hom_bc(g);
+          }
+          a.hom = hom_bc(g);
+          a.omega = c.omega;
+          a.pre = 1;
+          a.post = 1;
+          a.top = top;
+          a.fmg = 0;
+          const bool zg = (top < g.L - 1) || (P.cycle == 0 && c.inner_zero);
+          bottom::vcycle(a, top, a.hom, zg);
+          break;
+        }
+        case PH_DOWN:
+        case PH_UP: {
+          const int l = level_of(g, P.n);
+          const double hl = g.h * (double)(1 << (g.L - 1 - l));
+          fused::FusedParams fp;
+          fp.nx = fp.ny = fp.nz = P.n;
+          fp.s = g.bc == BC_ZEROGRAD ? 1.f : -1.f;
+          fp.cu = (float)(1.0 - c.omega);
+          fp.cs = (float)(c.omega / 6.0);
+          fp.cf = (float)(-c.omega * hl * hl / 6.0);
+          fp.inv_h2 = (float)(1.0 / (hl * hl));
+          fp.cz = kCz < P.n ? kCz : P.n;
+          const bool per = g.bc == BC_PERIODIC;
+          if (P.type == PH_DOWN) {
+            const bool zg = (l < g.L - 1) || (P.cycle == 0 && c.inner_zero);
+            if (zg) {
+              if (per)
+                fused::fused_tile<fused::kDown, true, true, 64, 16, 4, true>(
+                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+              else
+                fused::fused_tile<fused::kDown, true, false, 64, 16, 4, true>(
+                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+            } else {
+              if (per)
+                fused::fused_tile<fused::kDown, false, true, 64, 16, 4, true>(
+                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+              else
+                fused::fused_tile<fused::kDown, false, false, 64, 16, 4, true>(
+                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+            }
+          } else {
+            if (per)
+              fused::fused_tile<fused::kUp, false, true, 64, 16, 4, true>(
+                  g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
+            else
+              fused::fused_tile<fused::kUp, false, false, 64, 16, 4, true>(
+                  g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
+          }
+          break;
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(c)) return;
+    if (P.type == PH_FIN && *((volatile int*)&c.active_left[ph]) == 0) {
+      // every grid has stopped: go to the final mean removal
+      int q = ph + 1;
+      while (q < c.nphases && c.phases[q].type < PH_PSUM) ++q;
+      ph = q - 1;
+    }
+  }
+}
+
+}  // namespace batch
+}  // namespace mg
+
+using namespace mg;
+using namespace mg::batch;
+
+struct mg_batch {
+  int ngrids = 0;
+  mg_opts opts{};
+  int device = 0;
+  std::vector<GridDev> host_grids;  // pointers and sizes (state fields reset per solve)
+  GridDev* d_grids = nullptr;
+  GridDev* h_grids = nullptr;  // pinned staging
+  Phase* d_phases = nullptr;
+  Item* d_items = nullptr;
+  double* d_part = nullptr;
+  double* d_hist = nullptr;
+  double* h_hist = nullptr;  // pinned
+  unsigned* d_counters = nullptr;
+  unsigned* d_bar = nullptr;
+  int* d_err = nullptr;
+  int* d_active = nullptr;
+  int* h_err = nullptr;
+  int nphases = 0, nitems = 0, nchunks = 0, hist_cap = 64;
+  int blocks = 0;
+  long long cells = 0;
+  // the per-solve work captured once as a CUDA graph and replayed
+  bool graph_tried = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_err;
+
+bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+
+template <typename T>
+T* balloc(mg_batch* b, size_t count) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  b->allocs.push_back(p);
+  b->bytes += count * sizeof(T);
+  return static_cast<T*>(p);
+}
+
+void free_batch(mg_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (void* p : b->allocs) cudaFree(p);
+  if (b->h_grids) cudaFreeHost(b->h_grids);
+  if (b->h_hist) cudaFreeHost(b->h_hist);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  delete b;
+}
+
+// The phase list: source, first residual, max_cycles outer iterations of
+// (inner_cycles V-cycles, correction, residual, stopping rule), mean removal.
+void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& items) {
+  const int G = b->ngrids;
+  auto add_chunk_phase = [&](int type) {
+    Phase p{type, 0, (int)items.size(), 0, 0};
+    for (int g = 0; g < G; ++g)
+      for (int q = 0; q < b->host_grids[g].nchunk; ++q) items.push_back(Item{g, q, 0, 0});
+    p.count = (int)items.size() - p.first;
+    phases.push_back(p);
+  };
+  auto add_grid_phase = [&](int type, int cycle) {
+    Phase p{type, 0, (int)items.size(), 0, cycle};
+    for (int g = 0; g < G; ++g) items.push_back(Item{g, 0, 0, 0});
+    p.count = G;
+    phases.push_back(p);
+  };
+  int nmax = 0;
+  for (const GridDev& g : b->host_grids) nmax = std::max(nmax, g.n);
+  auto add_tile_phase = [&](int type, int n, int cycle) {
+    Phase p{type, n, (int)items.size(), 0, cycle};
+    // largest tiles first: grids in the order given, tiles of this level
+    for (int g = 0; g < G; ++g) {
+      if (b->host_grids[g].n < n) continue;
+      const int cz = std::min(kCz, n);
+      for (int z = 0; z < n / cz; ++z)
+        for (int y = 0; y < n / 16; ++y)
+          for (int x = 0; x < n / 64; ++x) items.push_back(Item{g, x, y, z});
+    }
+    p.count = (int)items.size() - p.first;
+    if (p.count > 0) phases.push_back(p);
+  };
+  add_chunk_phase(PH_SRC);
+  add_grid_phase(PH_MEANFIN, 0);
+  add_chunk_phase(PH_SRC2);
+  add_grid_phase(PH_NORMFIN, 0);
+  add_chunk_phase(PH_R0);
+  add_grid_phase(PH_R0FIN, 0);
+  const int inner = std::max(1, b->opts.inner_cycles);
+  for (int o = 0; o < b->opts.max_cycles; ++o) {
+    for (int k = 0; k < inner; ++k) {
+      for (int n = nmax; n >= kFusedMinN; n >>= 1) add_tile_phase(PH_DOWN, n, k);
+      add_grid_phase(PH_BOTTOM, k);
+      for (int n = kFusedMinN; n <= nmax; n <<= 1) add_tile_phase(PH_UP, n, k);
+    }
+    add_chunk_phase(PH_CORR);
+    add_chunk_phase(PH_RESID);
+    add_grid_phase(PH_FIN, 0);
+  }
+  add_chunk_phase(PH_PSUM);
+  add_grid_phase(PH_PMEAN, 0);
+  add_chunk_phase(PH_PSUB);
+}
+
+// The device work of one solve, in stream order.
+cudaError_t enqueue_solve(mg_batch* b, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(b->d_grids, b->h_grids, sizeof(GridDev) * b->ngrids,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned) * b->nphases, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_active, 0, sizeof(int) * b->nphases, s);
+  Ctl c;
+  c.phases = b->d_phases;
+  c.items = b->d_items;
+  c.grids = b->d_grids;
+  c.part = b->d_part;
+  c.hist = b->d_hist;
+  c.counters = b->d_counters;
+  c.bar_count = b->d_bar;
+  c.bar_gen = b->d_bar + 1;
+  c.err = b->d_err;
+  c.active_left = b->d_active;
+  c.nphases = b->nphases;
+  c.ngrids = b->ngrids;
+  c.hist_cap = b->hist_cap;
+  c.omega = b->opts.omega;
+  c.max_cycles = b->opts.max_cycles;
+  c.inner_zero = b->opts.inner_fmg ? 0 : 1;
+  c.stall_ratio = b->opts.stall_ratio;
+  if (e == cudaSuccess) {
+    void* args[] = {&c};
+    e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->blocks), dim3(kThreads), args,
+                                    kSmem, s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_grids, b->d_grids, sizeof(GridDev) * b->ngrids,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_hist, b->d_hist, sizeof(double) * b->ngrids * b->hist_cap,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc* bcs,
+                          const double* fixed_values, const mg_opts* opts, mg_batch** out) {
+  if (!out || n < 1 || !dims || !dx || !bcs) {
+    g_batch_err = "mg_batch_create: invalid argument";
+    return MG_ERR_ARG;
+  }
+  *out = nullptr;
+  mg_opts o;
+  if (opts) o = *opts;
+  else mg_opts_init(&o);
+  if (o.prec != MG_MIXED || o.pre != 1 || o.post != 1 || !o.mode_fmg || o.inner_fmg ||
+      o.max_cycles < 1 || o.max_cycles > 64 || o.inner_cycles < 1 || o.inner_cycles > 16) {
+    g_batch_err = "mg_batch_create: the batched solve runs MG_MIXED, V(1,1), FMG mode, inner "
+                  "V-cycles from a zero correction (inner_fmg = 0), 1..64 outer iterations";
+    return MG_ERR_ARG;
+  }
+  for (int g = 0; g < n; ++g) {
+    const int nx = dims[3 * g], ny = dims[3 * g + 1], nz = dims[3 * g + 2];
+    if (!pow2(nx) || nx != ny || nx != nz || nx > 1024 || !(dx[g] > 0.0) ||
+        (bcs[g] != MG_BC_PERIODIC && bcs[g] != MG_BC_FIXED && bcs[g] != MG_BC_ZEROGRAD)) {
+      g_batch_err = "mg_batch_create: grids must be cubic powers of two 2..1024 with a "
+                    "periodic, fixed or zero-gradient rule";
+      return MG_ERR_ARG;
+    }
+  }
+  mg_batch* b = new mg_batch;
+  b->ngrids = n;
+  b->opts = o;
+  cudaGetDevice(&b->device);
+  b->host_grids.resize(n);
+  int chunk0 = 0;
+  bool ok = true;
+  for (int g = 0; g < n && ok; ++g) {
+    GridDev& d = b->host_grids[g];
+    std::memset(&d, 0, sizeof d);
+    d.n = dims[3 * g];
+    int L = 1;
+    while ((d.n >> (L - 1)) > 1) ++L;
+    d.L = L;
+    d.bc = (int)bcs[g];
+    d.h = dx[g];
+    d.bcval = (bcs[g] == MG_BC_FIXED && fixed_values) ? fixed_values[g] : 0.0;
+    const long long N = (long long)d.n * d.n * d.n;
+    b->cells += N;
+    d.f64 = balloc<double>(b, N);
+    ok = ok && d.f64;
+    for (int l = 0; l < L && ok; ++l) {
+      const long long c = 1LL << (3 * l);
+      d.u32[l] = balloc<float>(b, c);
+      d.f32[l] = balloc<float>(b, c);
+      ok = ok && d.u32[l] && d.f32[l];
+      if ((1 << l) >= kFusedMinN) {
+        d.u32b[l] = balloc<float>(b, c);
+        ok = ok && d.u32b[l];
+      }
+    }
+    d.chunk0 = chunk0;
+    d.nchunk = (int)((N + kChunk - 1) / kChunk);
+    chunk0 += d.nchunk;
+  }
+  b->nchunks = chunk0;
+  std::vector<Phase> phases;
+  std::vector<Item> items;
+  if (ok) build_phases(b, phases, items);
+  b->nphases = (int)phases.size();
+  b->nitems = (int)items.size();
+  if (ok) {
+    b->d_grids = balloc<GridDev>(b, n);
+    b->d_phases = balloc<Phase>(b, phases.size());
+    b->d_items = balloc<Item>(b, items.size());
+    b->d_part = balloc<double>(b, b->nchunks);
+    b->d_hist = balloc<double>(b, (size_t)n * b->hist_cap);
+    b->d_counters = balloc<unsigned>(b, b->nphases);
+    b->d_bar = balloc<unsigned>(b, 2);
+    b->d_err = balloc<int>(b, 1);
+    b->d_active = balloc<int>(b, b->nphases);
+    ok = b->d_grids && b->d_phases && b->d_items && b->d_part && b->d_hist && b->d_counters &&
+         b->d_bar && b->d_err && b->d_active;
+  }
+  if (ok) {
+    ok = cudaMallocHost(&b->h_grids, sizeof(GridDev) * n) == cudaSuccess &&
+         cudaMallocHost(&b->h_hist, sizeof(double) * n * b->hist_cap) == cudaSuccess &&
+         cudaMallocHost(&b->h_err, sizeof(int) * 4) == cudaSuccess;
+  }
+  if (ok) {
+    ok = cudaMemcpy(b->d_phases, phases.data(), sizeof(Phase) * phases.size(),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem) ==
+             cudaSuccess;
+  }
+  int per_sm = 0, sms = 0;
+  if (ok) {
+    ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreads, kSmem) ==
+             cudaSuccess &&
+         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
+         per_sm > 0;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    g_batch_err = "mg_batch_create: device allocation or set-up failed";
+    free_batch(b);
+    return MG_ERR_OOM;
+  }
+  b->blocks = per_sm * sms;
+  *out = b;
+  return MG_OK;
+}
+
+mg_status mg_batch_solve(mg_batch* b, const double* const* rho, const double* four_pi_G,
+                         const double* tol, double* const* phi, double* hist, int hist_cap,
+                         int* n_hist, mg_status* status, void* stream) {
+  if (!b || !rho || !four_pi_G || !tol || !phi) {
+    g_batch_err = "mg_batch_solve: invalid argument";
+    return MG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int g = 0; g < b->ngrids; ++g) {
+    if (!rho[g] || !phi[g] || !(tol[g] >= 0.0)) {
+      g_batch_err = "mg_batch_solve: invalid per-grid argument";
+      return MG_ERR_ARG;
+    }
+    GridDev d = b->host_grids[g];
+    d.rho = rho[g];
+    d.phi = phi[g];
+    d.fpg = four_pi_G[g];
+    d.tol = tol[g];
+    d.mean = 0.0;
+    d.fnorm = d.rn = 0.0;
+    d.scale = 1.0;
+    d.prev = -1.0;
+    d.d0 = -1.0;
+    d.stalls = 0;
+    d.active = 1;
+    d.status = MG_ERR_NOT_CONVERGED;
+    d.nh = 0;
+    d.cycles = 0;
+    b->h_grids[g] = d;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->graph_tried) {
+    // Capture the whole solve (upload of the per-grid arguments, counter
+    // resets, the persistent kernel, download of the results) once.
+    b->graph_tried = true;
+    cudaError_t ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      const cudaError_t ee = enqueue_solve(b, b->cap);
+      cudaGraph_t gph = nullptr;
+      ce = cudaStreamEndCapture(b->cap, &gph);
+      if (ee == cudaSuccess && ce == cudaSuccess && gph) {
+        b->graph = gph;
+        if (cudaGraphInstantiate(&b->exec, gph, 0) != cudaSuccess) b->exec = nullptr;
+      } else if (gph) {
+        cudaGraphDestroy(gph);
+      }
+    }
+    cudaGetLastError();  // a failed capture leaves the direct launch path
+  }
+  ++g_launches;
+  if (b->exec) e = cudaGraphLaunch(b->exec, s);
+  else e = enqueue_solve(b, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    b->err = std::string("mg_batch_solve: ") + cudaGetErrorString(e);
+    g_batch_err = b->err;
+    return MG_ERR_CUDA;
+  }
+  if (*b->h_err) {
+    b->err = "mg_batch_solve: a grid-wide barrier timed out";
+    g_batch_err = b->err;
+    return MG_ERR_TIMEOUT;
+  }
+  mg_status worst = MG_OK;
+  for (int g = 0; g < b->ngrids; ++g) {
+    const GridDev& d = b->h_grids[g];
+    const int nh = std::min(d.nh, std::min(hist_cap, b->hist_cap));
+    if (hist && hist_cap > 0)
+      for (int q = 0; q < nh; ++q) hist[(size_t)g * hist_cap + q] = b->h_hist[(size_t)g * b->hist_cap + q];
+    if (n_hist) n_hist[g] = nh;
+    if (status) status[g] = (mg_status)d.status;
+    if (d.status != MG_OK && worst == MG_OK) worst = (mg_status)d.status;
+  }
+  return worst;
+}
+
+mg_status mg_batch_destroy(mg_batch* b) {
+  if (b) free_batch(b);
+  return MG_OK;
+}
+
+long long mg_batch_cells(const mg_batch* b) { return b ? b->cells : 0; }
+
+int mg_batch_graph(const mg_batch* b) { return b && b->exec ? 1 : 0; }
+
+const char* mg_batch_last_error(const mg_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,495 @@
+// mg_fused.cuh -- the fused z-marching FP32 V-cycle-leg programs (device code
+// shared by the standalone kernels of mg_fused.cu and the batched solver).
+//
+// One kernel per leg of Algorithm 1 on an FP32 level with a homogeneous rule
+// (periodic, zero fixed or zero gradient -- the rules of the correction
+// equation):
+//   down:  [u = 0 or u_in] -> SMOOTH (red, then black) -> d = f - L u ->
+//          f_{l-1} = I_l^{l-1} d                          (steps 1-3)
+//   up:    u_in + I_{l-1}^l e_{l-1} -> SMOOTH             (steps 5-7)
+//   plain: one SMOOTH step (extra steps of V(2,.) / V(.,2) cycles)
+//
+// A CTA owns a TX x TY tile of (x, y) columns and marches along z through a
+// chunk of planes.  Each thread owns a 4 x 2 patch (four consecutive x cells
+// of an even row and of the odd row after it) and keeps its patch of the last
+// few planes in registers; neighbours in other threads' patches come from a
+// shared-memory copy of the plane.  Per plane step the pipeline is:
+//   copy plane q+2 of u and plane q+1 of f into shared memory (cp.async),
+//   red half-step on plane q-1, black half-step on plane q-2, write plane q-2,
+//   defect of plane q-3 and, every second plane, its 2x2x2 restriction.
+// One __syncthreads separates plane steps.  Because the patch spans an even
+// and an odd row and the z-loop is unrolled by four, the colour of every cell
+// is known at compile time; the two cells of one colour in a row are updated
+// together with packed FP32x2 arithmetic.
+//
+// Kernels read u_in and write u_out (different buffers): neighbouring tiles
+// recompute this tile's border cells as their halo (a ring of 2 cells around
+// the smoothed region, 3 when the defect follows; 4 in x to keep 16-byte
+// alignment, 4 in y to keep row pairs) and must see the values from before
+// the step.
+//
+// Boundaries: periodic halo cells are real cells at wrapped indices and are
+// updated like any other; for the non-periodic rules a neighbour outside the
+// level is s * (the cell itself), s = -1 (zero fixed) or +1 (zero gradient) --
+// the ghost value of Sec. 2.3.6 at the moment it is read.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "mg_internal.h"
+
+namespace mg {
+namespace fused {
+
+struct FusedParams {
+  int nx, ny, nz;
+  float s;           // -1 zero fixed, +1 zero gradient (non-periodic rules)
+  float cu, cs, cf;  // SOR: u <- cu u + cs sum_nb + cf f
+  float inv_h2;
+  int cz;            // planes per CTA (multiple of 8, or nz)
+};
+
+enum Mode : int { kPlain = 0, kDown = 1, kUp = 2 };
+
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// ---------------------------------------------------------------------------
+// Packed helpers.  A row of four cells is kept as e = (c0, c2), o = (c1, c3).
+
+struct Row {
+  float2 e, o;
+};
+struct Patch {
+  Row a, b;  // a: even row, b: odd row
+};
+
+__device__ __forceinline__ Row unpack(const float4 v) {
+  return Row{make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+__device__ __forceinline__ float4 pack(const Row r) { return make_float4(r.e.x, r.o.x, r.e.y, r.o.y); }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ Patch zero_patch() {
+  const float2 z = make_float2(0.f, 0.f);
+  return Patch{Row{z, z}, Row{z, z}};
+}
+
+// u <- cu u + cs (xm + xp + ym + yp + zm + zp) + cf f on two cells at once.
+__device__ __forceinline__ float2 sor2(float2 self, float2 xm, float2 xp, float2 ym, float2 yp,
+                                       float2 zm, float2 zp, float2 f, const FusedParams& p) {
+  const float2 sum = add2(add2(add2(xm, xp), add2(ym, yp)), add2(zm, zp));
+  float2 t = __fmul2_rn(make_float2(p.cf, p.cf), f);
+  t = __ffma2_rn(make_float2(p.cu, p.cu), self, t);
+  return __ffma2_rn(make_float2(p.cs, p.cs), sum, t);
+}
+
+// d = f - (sum_nb - 6 u) / h^2 on two cells at once.
+__device__ __forceinline__ float2 defect2(float2 self, float2 xm, float2 xp, float2 ym, float2 yp,
+                                          float2 zm, float2 zp, float2 f, const FusedParams& p) {
+  const float2 sum = add2(add2(add2(xm, xp), add2(ym, yp)), add2(zm, zp));
+  const float2 lap = __ffma2_rn(make_float2(-6.f, -6.f), self, sum);
+  return __ffma2_rn(make_float2(-p.inv_h2, -p.inv_h2), lap, f);
+}
+
+// Boundary flags of a thread's patch for the non-periodic rules.
+struct Flags {
+  bool xlo, xhi, ylo, yhi;
+};
+
+__device__ __forceinline__ float2 sub_if(bool flag, float s, float2 self, float2 v) {
+  return flag ? make_float2(s * self.x, s * self.y) : v;
+}
+
+template <bool E>
+__device__ __forceinline__ float2 part(const Row& r) {
+  return E ? r.e : r.o;
+}
+template <bool E>
+__device__ __forceinline__ float2 part4(const float4& v) {
+  return E ? f2(v.x, v.z) : f2(v.y, v.w);
+}
+template <bool E>
+__device__ __forceinline__ void set_part(Row& r, float2 v) {
+  if (E) r.e = v;
+  else r.o = v;
+}
+
+// x neighbours of one row's e cells (E) or o cells (!E); `side` is the
+// neighbouring thread's float4 of the same row (left for e, right for o).
+template <bool PER, bool E>
+__device__ __forceinline__ void x_nb(const Row& r, const float4& side, float2 self, float2& xm,
+                                     float2& xp, const FusedParams& p, const Flags& fl) {
+  if (E) {
+    xm = f2(side.w, r.o.x);
+    xp = r.o;
+    if (!PER && fl.xlo) xm.x = p.s * self.x;
+  } else {
+    xm = r.e;
+    xp = f2(r.e.y, side.x);
+    if (!PER && fl.xhi) xp.y = p.s * self.y;
+  }
+}
+
+// One SOR half-step on the patch: row a updates its e cells if AE (else o),
+// row b the cells of the other parity (the same colour one row down).  S: the
+// shared copy of this plane; zm, zp: the patch in the planes below / above.
+template <bool PER, bool AE>
+__device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S, int ia, int ib,
+                                          int offL, int offR, int offU, int offD, const Patch& zm,
+                                          const Patch& zp, const Patch& f, const FusedParams& p,
+                                          const Flags& fl, bool zlo, bool zhi) {
+  constexpr bool BE = !AE;
+  {
+    const float4 above = S[ia + offU];
+    const float4 side = S[ia + (AE ? offL : offR)];
+    const float2 self = part<AE>(u.a);
+    float2 xm, xp;
+    x_nb<PER, AE>(u.a, side, self, xm, xp, p, fl);
+    float2 ym = part4<AE>(above), yp = part<AE>(u.b);
+    float2 zmv = part<AE>(zm.a), zpv = part<AE>(zp.a);
+    if (!PER) {
+      ym = sub_if(fl.ylo, p.s, self, ym);
+      zmv = sub_if(zlo, p.s, self, zmv);
+      zpv = sub_if(zhi, p.s, self, zpv);
+    }
+    set_part<AE>(u.a, sor2(self, xm, xp, ym, yp, zmv, zpv, part<AE>(f.a), p));
+  }
+  {
+    const float4 below = S[ib + offD];
+    const float4 side = S[ib + (BE ? offL : offR)];
+    const float2 self = part<BE>(u.b);
+    float2 xm, xp;
+    x_nb<PER, BE>(u.b, side, self, xm, xp, p, fl);
+    float2 ym = part<BE>(u.a), yp = part4<BE>(below);
+    float2 zmv = part<BE>(zm.b), zpv = part<BE>(zp.b);
+    if (!PER) {
+      yp = sub_if(fl.yhi, p.s, self, yp);
+      zmv = sub_if(zlo, p.s, self, zmv);
+      zpv = sub_if(zhi, p.s, self, zpv);
+    }
+    set_part<BE>(u.b, sor2(self, xm, xp, ym, yp, zmv, zpv, part<BE>(f.b), p));
+  }
+}
+
+// Defect of one row's e or o cells.
+template <bool PER, bool E, bool ROWB>
+__device__ __forceinline__ float2 defect_part(const Row& r, const Row& other, const float4& yout4,
+                                              const float4& side, const Row& rzm, const Row& rzp,
+                                              const Row& rf, const FusedParams& p,
+                                              const Flags& fl, bool zlo, bool zhi) {
+  const float2 self = part<E>(r);
+  float2 xm, xp;
+  x_nb<PER, E>(r, side, self, xm, xp, p, fl);
+  float2 yout = part4<E>(yout4), yin = part<E>(other);
+  float2 zmv = part<E>(rzm), zpv = part<E>(rzp);
+  if (!PER) {
+    yout = sub_if(ROWB ? fl.yhi : fl.ylo, p.s, self, yout);
+    zmv = sub_if(zlo, p.s, self, zmv);
+    zpv = sub_if(zhi, p.s, self, zpv);
+  }
+  return ROWB ? defect2(self, xm, xp, yin, yout, zmv, zpv, part<E>(rf), p)
+              : defect2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p);
+}
+
+// Defect of the whole patch (interior threads only); returns the sums over
+// both rows of (d(4m) + d(4m+1), d(4m+2) + d(4m+3)): the two coarse cells in x.
+template <bool PER>
+__device__ __forceinline__ float2 defect_patch(const Patch& u, const float4* __restrict__ S,
+                                               int ia, int ib, int RT, const Patch& zm,
+                                               const Patch& zp, const Patch& f,
+                                               const FusedParams& p, const Flags& fl, bool zlo,
+                                               bool zhi) {
+  const float4 above = S[ia - RT], below = S[ib + RT];
+  const float4 la = S[ia - 1], ra = S[ia + 1], lb = S[ib - 1], rb = S[ib + 1];
+  const float2 dae = defect_part<PER, true, false>(u.a, u.b, above, la, zm.a, zp.a, f.a, p, fl, zlo, zhi);
+  const float2 dao = defect_part<PER, false, false>(u.a, u.b, above, ra, zm.a, zp.a, f.a, p, fl, zlo, zhi);
+  const float2 dbe = defect_part<PER, true, true>(u.b, u.a, below, lb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
+  const float2 dbo = defect_part<PER, false, true>(u.b, u.a, below, rb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
+  return add2(add2(dae, dao), add2(dbe, dbo));
+}
+
+// Asynchronous 16-byte global -> shared copy; src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// (x, y) part of the trilinear prolongation of coarse plane K at the patch:
+// rows gyA (even: coarse rows Y-1, Y) and gyA+1 (odd: Y, Y+1), Y = gyA/2;
+// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.
+// COH: the coarse values may have been written earlier in the same launch by
+// another CTA (the batched solver), so read them through L2 (ld.global.cg)
+// rather than the read-only path.
+template <bool PER, bool COH = false>
+__device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const FusedParams& p,
+                                           int gx4, int gyA, int K) {
+  const int cnx = p.nx >> 1, cny = p.ny >> 1;
+  const int X0 = gx4 >> 1, Y = gyA >> 1;
+  float xr[3][4];
+#pragma unroll
+  for (int yy = 0; yy < 3; ++yy) {
+    const int Yc = Y - 1 + yy;
+    int Yi = Yc;
+    float sy = 1.f;
+    if (Yc < 0 || Yc >= cny) {
+      if (PER) Yi = wrap(Yc, cny);
+      else { Yi = Yc < 0 ? 0 : cny - 1; sy = p.s; }
+    }
+    const float* rowp = ec + ((size_t)K * cny + Yi) * cnx;
+    float c[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int Xc = X0 - 1 + a;
+      float v;
+      const float* src;
+      float sx = 1.f;
+      if (Xc < 0 || Xc >= cnx) {
+        if (PER) src = rowp + wrap(Xc, cnx);
+        else { src = rowp + (Xc < 0 ? 0 : cnx - 1); sx = p.s; }
+      } else {
+        src = rowp + Xc;
+      }
+      v = sx * (COH ? __ldcg(src) : __ldg(src));
+      c[a] = sy * v;
+    }
+    xr[yy][0] = 0.25f * c[0] + 0.75f * c[1];
+    xr[yy][1] = 0.75f * c[1] + 0.25f * c[2];
+    xr[yy][2] = 0.25f * c[1] + 0.75f * c[2];
+    xr[yy][3] = 0.75f * c[2] + 0.25f * c[3];
+  }
+  Patch P;
+  P.a.e = f2(0.25f * xr[0][0] + 0.75f * xr[1][0], 0.25f * xr[0][2] + 0.75f * xr[1][2]);
+  P.a.o = f2(0.25f * xr[0][1] + 0.75f * xr[1][1], 0.25f * xr[0][3] + 0.75f * xr[1][3]);
+  P.b.e = f2(0.75f * xr[1][0] + 0.25f * xr[2][0], 0.75f * xr[1][2] + 0.25f * xr[2][2]);
+  P.b.o = f2(0.75f * xr[1][1] + 0.25f * xr[2][1], 0.75f * xr[1][3] + 0.25f * xr[2][3]);
+  return P;
+}
+
+// HYO > 0 overrides the rows of halo (so that every mode can share one block
+// size in the batched solver).
+template <int MODE, int TX, int TY, int HYO = 0>
+struct Shape {
+  static constexpr int HZ = (MODE == kDown) ? 3 : 2;  // planes of halo in z
+  static constexpr int HY = HYO > 0 ? HYO : ((MODE == kDown) ? 4 : 2);  // rows of halo in y (even)
+  static constexpr int RT = (TX + 8) / 4;              // float4 columns per row
+  static constexpr int RR = TY + 2 * HY;               // rows
+  static constexpr int RP = RR / 2;                    // row pairs
+  static constexpr int NT = RT * RP;                   // threads
+  static constexpr int PL = RT * RR;                   // float4 per shared plane
+  static constexpr int NU = 4, NF = 4, NRED = 2, NFIN = (MODE == kDown) ? 2 : 0;
+  static constexpr size_t SMEM = (size_t)(NU + NF + NRED + NFIN) * PL * 16;
+};
+
+// The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
+// Shape::SMEM bytes; threads tid >= Shape::NT of a larger CTA take part in
+// the barriers only.
+template <int MODE, bool ZERO, bool PER, int TX, int TY, int HYO = 0, bool COH = false>
+__device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, const float* f,
+                                           const float* ec, float* fc,
+                                           const FusedParams& p, int bx, int by, int bz,
+                                           float4* smem) {
+  using S_ = Shape<MODE, TX, TY, HYO>;
+  constexpr int HZ = S_::HZ, HY = S_::HY, RT = S_::RT, RP = S_::RP, PL = S_::PL;
+  float4* s_u = smem;                     // [4][PL] planes of u (async copies)
+  float4* s_f = s_u + S_::NU * PL;        // [4][PL] planes of f (async copies)
+  float4* s_red = s_f + S_::NF * PL;      // [2][PL] red-updated planes
+  float4* s_fin = s_red + S_::NRED * PL;  // [2][PL] final planes (down leg)
+
+  const int tid = threadIdx.x < S_::NT ? threadIdx.x : 0;  // spare threads mirror thread 0
+  const bool act = threadIdx.x < S_::NT;
+  const int tr = tid % RT, tp = tid / RT;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int z0 = bz * p.cz;
+  const int z1 = min(z0 + p.cz, p.nz);
+  const int gx4 = x0 - 4 + 4 * tr;   // x of the patch's first cell (may be outside)
+  const int gyA = y0 - HY + 2 * tp;  // even row of the patch (may be outside)
+  const bool in_col = (gx4 >= 0 && gx4 < p.nx) && (gyA >= 0 && gyA < p.ny);
+  const int gx4w = PER ? wrap(gx4, p.nx) : gx4;
+  const int gyAw = PER ? wrap(gyA, p.ny) : gyA;
+  const bool col_ok = PER || in_col;  // the patch holds real cells
+  Flags fl;
+  fl.xlo = !PER && gx4 == 0;
+  fl.xhi = !PER && gx4 + 3 == p.nx - 1;
+  fl.ylo = !PER && gyA == 0;
+  fl.yhi = !PER && gyA + 1 == p.ny - 1;
+  const bool out = tr >= 1 && tr <= TX / 4 && tp >= HY / 2 && tp < HY / 2 + TY / 2;
+  const size_t plane = (size_t)p.nx * p.ny;
+  const size_t offA = col_ok ? (size_t)gyAw * p.nx + gx4w : 0;
+  const size_t offB = col_ok ? offA + (size_t)p.nx : 0;
+  const int ia = (2 * tp) * RT + tr, ib = ia + RT;  // shared indices of rows a, b
+  const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
+  const int offU = tp > 0 ? -RT : 0, offD = tp < RP - 1 ? RT : 0;
+  const int q_first = z0 - HZ, q_last = z1 - 1 + HZ;
+
+  auto issue = [&](int qu) {
+    if (act && qu <= q_last) {
+      if (!ZERO) {
+        const bool in = col_ok && (PER || (qu >= 0 && qu < p.nz));
+        const size_t o = (size_t)(PER ? wrap(qu, p.nz) : (in ? qu : 0)) * plane;
+        float4* d = &s_u[(qu & 3) * PL];
+        cp_async16(&d[ia], u_in + o + offA, in ? 16 : 0);
+        cp_async16(&d[ib], u_in + o + offB, in ? 16 : 0);
+      }
+      const int qf = qu - 1;
+      const bool inf = col_ok && (PER || (qf >= 0 && qf < p.nz));
+      const size_t o = (size_t)(PER ? wrap(qf, p.nz) : (inf ? qf : 0)) * plane;
+      float4* d = &s_f[(qf & 3) * PL];
+      cp_async16(&d[ia], f + o + offA, inf ? 16 : 0);
+      cp_async16(&d[ib], f + o + offB, inf ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+
+  Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
+  float2 acc = make_float2(0.f, 0.f);
+  int ka = -1000000, kb = -1000000;  // coarse planes of the cached (x, y) interpolations
+  Patch Pa = r1, Pb = r1;
+
+  // One plane step.  J = (q - q_first) mod 4 fixes the ring slots and the
+  // colours at compile time: q_first = z0 - HZ with z0 a multiple of 8.
+  auto step = [&](auto Jc, int q) {
+    constexpr int J = decltype(Jc)::value;
+    constexpr int QP = ((J - HZ) % 4 + 4) % 4;  // q mod 4
+    constexpr int SL_U = QP, SL_UM1 = (QP + 3) % 4, SL_FM1 = (QP + 3) % 4;
+    constexpr int ZP_RED = (QP + 3) % 2;  // parity of plane q-1
+    constexpr int ZP_BLK = (QP + 2) % 2;  // parity of plane q-2
+    constexpr int ZP_DEF = (QP + 1) % 2;  // parity of plane q-3
+    cp_async_wait<1>();  // this thread's copies of plane q have landed
+    __syncthreads();     // ... and everyone's; the previous step is finished
+    issue(q + 2);
+    // [A] plane q of u (old values), plus the prolonged correction (up leg)
+    Patch r0 = zero_patch();
+    if (!ZERO) {
+      r0.a = unpack(s_u[SL_U * PL + ia]);
+      r0.b = unpack(s_u[SL_U * PL + ib]);
+    }
+    if (MODE == kUp) {
+      if (col_ok && (PER || (q >= 0 && q < p.nz))) {
+        const int qw = PER ? wrap(q, p.nz) : q;
+        const int cnz = p.nz >> 1;
+        const int K = qw >> 1;
+        int Kn = (qw & 1) ? K + 1 : K - 1;
+        float wn = 0.25f;
+        if (Kn < 0 || Kn >= cnz) {
+          if (PER) Kn = wrap(Kn, cnz);
+          else { Kn = Kn < 0 ? 0 : cnz - 1; wn *= p.s; }
+        }
+        Patch PK, PN;
+        if (K == kb) PK = Pb;
+        else if (K == ka) PK = Pa;
+        else { PK = xy_interp<PER, COH>(ec, p, gx4w, gyAw, K); ka = kb; Pa = Pb; kb = K; Pb = PK; }
+        if (Kn == kb) PN = Pb;
+        else if (Kn == ka) PN = Pa;
+        else { PN = xy_interp<PER, COH>(ec, p, gx4w, gyAw, Kn); ka = kb; Pa = Pb; kb = Kn; Pb = PN; }
+        const float2 w0 = make_float2(0.75f, 0.75f), w1 = make_float2(wn, wn);
+        r0.a.e = __ffma2_rn(w1, PN.a.e, __ffma2_rn(w0, PK.a.e, r0.a.e));
+        r0.a.o = __ffma2_rn(w1, PN.a.o, __ffma2_rn(w0, PK.a.o, r0.a.o));
+        r0.b.e = __ffma2_rn(w1, PN.b.e, __ffma2_rn(w0, PK.b.e, r0.b.e));
+        r0.b.o = __ffma2_rn(w1, PN.b.o, __ffma2_rn(w0, PK.b.o, r0.b.o));
+      }
+      if (act) {
+        s_u[SL_U * PL + ia] = pack(r0.a);  // the neighbours read corrected values
+        s_u[SL_U * PL + ib] = pack(r0.b);
+      }
+    }
+    Patch f1;
+    f1.a = unpack(s_f[SL_FM1 * PL + ia]);
+    f1.b = unpack(s_f[SL_FM1 * PL + ib]);
+    // [B] red half-step on plane q-1: the red cells of the even row are its
+    // e cells when the plane is even
+    {
+      const int pz = q - 1;
+      const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+      if (q > q_first) {
+        if (ZERO) {
+          // every neighbour of a red cell is still 0
+          const float2 cf2 = make_float2(p.cf, p.cf);
+          if (ZP_RED == 0) {
+            r1.a.e = __fmul2_rn(cf2, f1.a.e);
+            r1.b.o = __fmul2_rn(cf2, f1.b.o);
+          } else {
+            r1.a.o = __fmul2_rn(cf2, f1.a.o);
+            r1.b.e = __fmul2_rn(cf2, f1.b.e);
+          }
+        } else {
+          sor_patch<PER, ZP_RED == 0>(r1, &s_u[SL_UM1 * PL], ia, ib, offL, offR, offU, offD, r2,
+                                      r0, f1, p, fl, zlo, zhi);
+        }
+      }
+      if (act) {
+        s_red[ZP_RED * PL + ia] = pack(r1.a);
+        s_red[ZP_RED * PL + ib] = pack(r1.b);
+      }
+    }
+    // [C] black half-step on plane q-2 (red values of planes q-3 .. q-1)
+    {
+      const int pz = q - 2;
+      const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+      if (q > q_first + 1)
+        sor_patch<PER, ZP_BLK != 0>(r2, &s_red[ZP_BLK * PL], ia, ib, offL, offR, offU, offD, r3,
+                                    r1, f2p, p, fl, zlo, zhi);
+      if (MODE == kDown && act) {
+        s_fin[ZP_BLK * PL + ia] = pack(r2.a);
+        s_fin[ZP_BLK * PL + ib] = pack(r2.b);
+      }
+      if (act && out && pz >= z0 && pz < z1) {
+        *reinterpret_cast<float4*>(u_out + (size_t)pz * plane + offA) = pack(r2.a);
+        *reinterpret_cast<float4*>(u_out + (size_t)pz * plane + offB) = pack(r2.b);
+      }
+    }
+    // [D] defect of plane q-3 and its 2x2x2 restriction
+    if (MODE == kDown) {
+      const int pz = q - 3;
+      if (act && pz >= z0 && pz < z1 && out) {
+        const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+        const float2 s2 = defect_patch<PER>(r3, &s_fin[ZP_DEF * PL], ia, ib, RT, r4, r2, f3p, p,
+                                            fl, zlo, zhi);
+        if (ZP_DEF == 0) {
+          acc = s2;
+        } else {
+          acc = add2(acc, s2);
+          const int cnx = p.nx >> 1, cny = p.ny >> 1;
+          const int X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
+          *reinterpret_cast<float2*>(fc + ((size_t)Zc * cny + Yc) * cnx + X) =
+              __fmul2_rn(make_float2(0.125f, 0.125f), acc);
+        }
+      }
+    }
+    r4 = r3; r3 = r2; r2 = r1; r1 = r0;
+    f3p = f2p; f2p = f1;
+  };
+
+  issue(q_first);
+  issue(q_first + 1);
+  for (int q = q_first; q <= q_last; q += 4) {
+    step(std::integral_constant<int, 0>{}, q);
+    if (q + 1 > q_last) break;
+    step(std::integral_constant<int, 1>{}, q + 1);
+    if (q + 2 > q_last) break;
+    step(std::integral_constant<int, 2>{}, q + 2);
+    if (q + 3 > q_last) break;
+    step(std::integral_constant<int, 3>{}, q + 3);
+  }
+  cp_async_wait<0>();
+}
+
+template <int MODE, bool ZERO, bool PER, int TX, int TY>
+__global__ void __launch_bounds__(Shape<MODE, TX, TY>::NT)
+    k_fused(const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
+            const float* __restrict__ ec, float* __restrict__ fc, FusedParams p) {
+  extern __shared__ float4 smem[];
+  fused_tile<MODE, ZERO, PER, TX, TY>(u_in, u_out, f, ec, fc, p, blockIdx.x, blockIdx.y, blockIdx.z,
+                                      smem);
+}
+
+}  // namespace fused
+}  // namespace mg

@@ -107,7 +107,8 @@ cudaError_t launch_correct(double* u, const float* e32, long long n, double inv_
 // fmg is false).  fmg = false: one V-cycle on levels top .. 0 of the
 // correction (u[top] starts at 0, f[top] holds the restricted defect);
 // fmg = true: Algorithm 2 up to level `top` from f[top].
-constexpr int kBottomLevels = 5;
+constexpr int kBottomLevels = 6;  // arrays of the bottom programs (levels up to 32^3)
+constexpr int kBottomTopN = 16;   // the single-grid driver hands levels <= 16^3 to one CTA
 template <typename T>
 cudaError_t launch_bottom(T* const* u, T* const* f, const int* n, const double* h, const Bc* bc,
                           Bc hom, double omega, int pre, int post, int top, bool fmg,

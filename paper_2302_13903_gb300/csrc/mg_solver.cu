@@ -55,6 +55,7 @@ struct mg_ctx {
   double* phi_dev_own = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
+  bool dry = false;  // count the bytes of the hierarchy without allocating
   long long last_launches = 0;
   std::string err;
   // Per-kernel timing of finest-level launches.
@@ -98,6 +99,10 @@ void fail(mg_ctx* c, mg_status st, const std::string& msg) {
 
 template <typename T>
 T* dalloc(mg_ctx* c, size_t count) {
+  if (c->dry) {
+    c->bytes += count * sizeof(T);
+    return nullptr;
+  }
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, count * sizeof(T));
   if (e != cudaSuccess) {
@@ -107,6 +112,40 @@ T* dalloc(mg_ctx* c, size_t count) {
   c->allocs.push_back(p);
   c->bytes += count * sizeof(T);
   return static_cast<T*>(p);
+}
+
+// The device arrays of a context (counted only, when c->dry).
+void alloc_hierarchy(mg_ctx* c) {
+  const mg_bc bc = (mg_bc)c->bc_kind;
+  const mg_opts& o = c->opts;
+  const int L = c->L;
+  const int F = L - 1;
+  for (int l = 0; l < L; ++l) {
+    const long long cells = level_grid(c, l).cells();
+    if (o.prec == MG_FP64) {
+      if (l < F) c->u64[l] = dalloc<double>(c, cells);
+      c->f64[l] = dalloc<double>(c, cells);
+      if (bc == MG_BC_OPEN) c->faces[l] = dalloc<double>(c, mg::faces_count(level_grid(c, l)));
+    } else {
+      c->u32[l] = dalloc<float>(c, cells);
+      c->f32[l] = dalloc<float>(c, cells);
+      if (mg::fused_ok(level_grid(c, l), mg::homogeneous(Bc{(int)bc, 0.0, nullptr})))
+        c->u32b[l] = dalloc<float>(c, cells);
+    }
+  }
+  if (o.prec == MG_MIXED) {
+    c->f64[F] = dalloc<double>(c, level_grid(c, F).cells());
+    if (bc == MG_BC_OPEN) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
+  }
+  c->partials_cap = mg::kPartials;
+  if (o.prec == MG_MIXED && o.outer_fixed && mg::fx_step_ok(level_grid(c, F))) {
+    c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
+    const int nb = mg::fx_step_blocks(level_grid(c, F));
+    if (nb > c->partials_cap) c->partials_cap = nb;
+  }
+  c->partials = dalloc<double>(c, c->partials_cap);
+  c->scal = dalloc<double>(c, 64);
+  c->iflag = dalloc<int>(c, 4);
 }
 
 Bc physical_bc(const mg_ctx* c, int l) {
@@ -158,7 +197,7 @@ void collect_times(mg_ctx* c) {
 // Highest level index the single-CTA bottom solver covers (<= 16^3 cells).
 int bottom_top(const mg_ctx* c) {
   int t = 0;
-  while (t + 1 < c->L && t + 1 < mg::kBottomLevels) ++t;
+  while (t + 1 < c->L && t + 1 < mg::kBottomLevels && level_n(c, t + 1) <= mg::kBottomTopN) ++t;
   return t;
 }
 
@@ -682,39 +721,39 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
     c->L = L;
     check(c, cudaGetDevice(&c->device), "cudaGetDevice");
     if (bc == MG_BC_OPEN) check(c, mg::prepare_multipole(), "multipole tables");
-    const int F = L - 1;
-    for (int l = 0; l < L; ++l) {
-      const long long cells = level_grid(c, l).cells();
-      if (o.prec == MG_FP64) {
-        if (l < F) c->u64[l] = dalloc<double>(c, cells);
-        c->f64[l] = dalloc<double>(c, cells);
-        if (bc == MG_BC_OPEN) c->faces[l] = dalloc<double>(c, mg::faces_count(level_grid(c, l)));
-      } else {
-        c->u32[l] = dalloc<float>(c, cells);
-        c->f32[l] = dalloc<float>(c, cells);
-        if (mg::fused_ok(level_grid(c, l), mg::homogeneous(Bc{(int)bc, 0.0, nullptr})))
-          c->u32b[l] = dalloc<float>(c, cells);
-      }
-    }
-    if (o.prec == MG_MIXED) {
-      c->f64[F] = dalloc<double>(c, level_grid(c, F).cells());
-      if (bc == MG_BC_OPEN) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
-    }
-    c->partials_cap = mg::kPartials;
-    if (o.prec == MG_MIXED && o.outer_fixed && mg::fx_step_ok(level_grid(c, F))) {
-      c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
-      const int nb = mg::fx_step_blocks(level_grid(c, F));
-      if (nb > c->partials_cap) c->partials_cap = nb;
-    }
-    c->partials = dalloc<double>(c, c->partials_cap);
-    c->scal = dalloc<double>(c, 64);
-    c->iflag = dalloc<int>(c, 4);
+    alloc_hierarchy(c);
     check(c, cudaMallocHost(&c->pinned, 64 * sizeof(double)), "cudaMallocHost");
   } catch (const Fail& f) {
     mg_destroy(c);
     return f.st;
   }
   *out = c;
+  return MG_OK;
+}
+
+mg_status mg_required_bytes(int nx, int ny, int nz, mg_bc bc, const mg_opts* opts,
+                            size_t* bytes) {
+  if (!bytes) return MG_ERR_ARG;
+  *bytes = 0;
+  mg_opts o;
+  if (opts) o = *opts;
+  else mg_opts_init(&o);
+  if (!is_pow2(nx) || nx < 2 || nx != ny || nx != nz || (int)bc < 0 || (int)bc > 3 ||
+      validate_opts(o) != MG_OK) {
+    g_err = "mg_required_bytes: invalid argument";
+    return MG_ERR_ARG;
+  }
+  mg_ctx c;
+  c.dry = true;
+  c.n = nx;
+  c.h = 1.0;
+  c.bc_kind = (int)bc;
+  c.opts = o;
+  c.L = 1;
+  while ((nx >> (c.L - 1)) > 1) ++c.L;
+  if (c.L > kMaxLevels) return MG_ERR_ARG;
+  alloc_hierarchy(&c);
+  *bytes = c.bytes;
   return MG_OK;
 }
 

@@ -5,6 +5,8 @@ import os
 import re
 import subprocess
 
+import pytest
+
 import paper_2302_13903_gb300 as mg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -46,20 +48,58 @@ def test_default_options_layout():
     assert list(o.reserved) == [0] * 7
 
 
-def test_opts_layout_matches_the_c_header(tmp_path):
-    """The ctypes mirror of mg_opts has the C compiler's size and offsets."""
-    fields = [f for f, _ in mg.Opts._fields_]
+@pytest.mark.parametrize("py,c", [(mg.Opts, "mg_opts"), (mg.Request, "mg_request"),
+                                  (mg.Result, "mg_result"), (mg.ServerStats, "mg_server_stats")])
+def test_struct_layout_matches_the_c_header(tmp_path, py, c):
+    """Each ctypes mirror has the C compiler's size and offsets."""
+    fields = [f for f, _ in py._fields_]
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mg.h"\nint main(void){\n'
-                   + 'printf("%zu\\n", sizeof(mg_opts));\n'
-                   + "".join(f'printf("%zu\\n", offsetof(mg_opts, {f}));\n' for f in fields)
+                   + f'printf("%zu\\n", sizeof({c}));\n'
+                   + "".join(f'printf("%zu\\n", offsetof({c}, {f}));\n' for f in fields)
                    + "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
-    assert out[0] == ctypes.sizeof(mg.Opts)
-    assert out[1:] == [getattr(mg.Opts, f).offset for f in fields]
+    assert out[0] == ctypes.sizeof(py)
+    assert out[1:] == [getattr(py, f).offset for f in fields]
+
+
+def test_required_bytes_counts_the_hierarchy():
+    """mg_required_bytes needs no device: FP64 keeps phi/f pyramids (the finest
+    phi is the caller's), MIXED keeps FP32 pyramids plus FP64 f and the
+    fixed-point buffer on the finest level."""
+    n = 128
+    fine = n ** 3
+    pyramid = sum(8 ** l for l in range(8))  # 1^3 .. 128^3
+    b64 = mg.required_bytes(n, mg.PERIODIC, prec=mg.FP64)
+    assert 8 * (pyramid + pyramid - fine) <= b64 <= 8 * (2 * pyramid - fine) + 2 ** 20
+    bmx = mg.required_bytes(n, mg.PERIODIC, prec=mg.MIXED)
+    # u32 + f32 everywhere, a second u32 on the fused levels (32..128), f64 + int64 finest
+    lo = 4 * 2 * pyramid + 4 * (fine + fine // 8 + fine // 64) + 16 * fine
+    assert lo <= bmx <= lo + 2 ** 20
+    assert mg.required_bytes(n, mg.OPEN, prec=mg.MIXED) > bmx  # boundary faces
+    assert mg.required_bytes(2 * n, mg.PERIODIC, prec=mg.MIXED) > 7.9 * bmx
+    L = mg.lib()
+    b = ctypes.c_size_t(0)
+    o = mg.default_opts()
+    assert L.mg_required_bytes(12, 12, 12, 0, ctypes.byref(o), ctypes.byref(b)) == 1
+    assert L.mg_required_bytes(8, 8, 8, 0, ctypes.byref(o), None) == 1
+
+
+def test_server_argument_validation_needs_no_gpu():
+    L = mg.lib()
+    h = ctypes.c_void_p()
+    o = mg.default_opts(prec=mg.MIXED)
+    assert L.mg_server_create(0, 2, 8, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert L.mg_server_create(1 << 30, 0, 8, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert L.mg_server_create(1 << 30, 2, 0, ctypes.byref(o), ctypes.byref(h)) == 1
+    bad = mg.default_opts(pre=5)
+    assert L.mg_server_create(1 << 30, 2, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert not h.value
+    assert L.mg_server_submit(None, None, None) == 1
+    assert L.mg_server_destroy(None) == 0
 
 
 def test_status_strings_and_faces_count():

@@ -1,0 +1,110 @@
+"""Serving loop: requests of different sizes and rules run concurrently on
+resident hierarchies under an HBM budget, and every result equals the same
+request solved alone (bit for bit: each solve is deterministic and a
+hierarchy serves one request at a time)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import paper_2302_13903_gb300 as mg
+from paper_2302_13903_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+MIX = [(64, mg.PERIODIC, 0, 1e-10), (32, mg.OPEN, 4, 1e-8), (128, mg.FIXED, 0, 1e-9),
+       (32, mg.ZEROGRAD, 0, 1e-10), (128, mg.OPEN, 2, 1e-10), (64, mg.FIXED, 0, 1e-6),
+       (16, mg.PERIODIC, 0, 1e-10), (128, mg.PERIODIC, 0, 1e-7), (64, mg.ZEROGRAD, 0, 1e-10),
+       (64, mg.OPEN, 0, 1e-9), (32, mg.FIXED, 0, 1e-10), (128, mg.ZEROGRAD, 0, 1e-8)]
+
+
+def sources(mix, seed=11):
+    return [inputs.serving_source(dict(n=n, bc=bc, seed=seed + k, n_blobs=1 + k % 8), "cuda")
+            for k, (n, bc, _, _) in enumerate(mix)]
+
+
+def solve_alone(rho, n, bc, lmax, tol):
+    with mg.Server(1 << 34, slots=1, max_queue=4) as s:
+        phi = torch.zeros_like(rho)
+        res, hist = s.wait(s.submit(rho, phi, bc=bc, tol=tol, lmax=lmax), 120)
+        assert res.done and res.status in (0, 4)
+    return phi, hist
+
+
+def test_server_mix_equals_alone():
+    rhos = sources(MIX)
+    alone = [solve_alone(r, n, bc, lmax, tol) for r, (n, bc, lmax, tol) in zip(rhos, MIX)]
+    with mg.Server(1 << 34, slots=4, max_queue=64) as s:
+        phis = [torch.full_like(r, float("nan")) for r in rhos]
+        tickets = [s.submit(r, p, bc=bc, tol=tol, lmax=lmax)
+                   for r, p, (n, bc, lmax, tol) in zip(rhos, phis, MIX)]
+        results = [s.wait(t, 120) for t in tickets]
+        st = s.stats()
+    assert st["completed"] == len(MIX) and st["rejected"] == 0
+    for k, ((res, hist), (pa, ha)) in enumerate(zip(results, alone)):
+        assert res.done and res.status == 0, (k, res.status)
+        assert hist[-1] < MIX[k][3]
+        assert 0.0 <= res.queue_ms <= res.total_ms and res.solve_ms > 0.0
+        assert torch.equal(phis[k], pa), k
+        assert np.array_equal(hist, ha), k
+
+
+def test_server_open_request_matches_oracle():
+    n, bc, lmax, tol = 32, mg.OPEN, 4, 1e-10
+    rho = inputs.serving_source(dict(n=n, bc=bc, seed=5, n_blobs=3))
+    ref = orc.solve(rho, 1.0 / n, bc, lmax=lmax, tol=0.0, max_cycles=80)
+    with mg.Server(1 << 32, slots=2) as s:
+        rd = torch.from_numpy(rho).cuda()
+        phi = torch.zeros_like(rd)
+        res, hist = s.wait(s.submit(rd, phi, bc=bc, tol=tol, lmax=lmax), 120)
+    assert res.status == 0 and hist[-1] < tol
+    err = float(np.abs(phi.cpu().numpy() - ref.phi).max() / np.abs(ref.phi).max())
+    assert err <= 1e-9, err
+
+
+def test_server_budget_evicts_and_results_stay_equal():
+    mix = [(128, mg.PERIODIC, 0, 1e-10), (64, mg.FIXED, 0, 1e-10), (128, mg.ZEROGRAD, 0, 1e-10),
+           (32, mg.OPEN, 3, 1e-10), (64, mg.PERIODIC, 0, 1e-10), (128, mg.FIXED, 0, 1e-10),
+           (64, mg.FIXED, 0, 1e-10), (128, mg.PERIODIC, 0, 1e-10)]
+    need = {(n, bc, lmax): mg.required_bytes(n, bc, prec=mg.MIXED, lmax=lmax)
+            for n, bc, lmax, _ in mix}
+    budget = int(1.2 * max(need.values()) + need[(64, mg.FIXED, 0)])
+    rhos = sources(mix, seed=40)
+    alone = [solve_alone(r, n, bc, lmax, tol)[0] for r, (n, bc, lmax, tol) in zip(rhos, mix)]
+    with mg.Server(budget, slots=3, max_queue=64) as s:
+        phis = [torch.zeros_like(r) for r in rhos]
+        tickets = [s.submit(r, p, bc=bc, tol=tol, lmax=lmax)
+                   for r, p, (n, bc, lmax, tol) in zip(rhos, phis, mix)]
+        results = [s.wait(t, 120)[0] for t in tickets]
+        st = s.stats()
+    assert all(r.done and r.status == 0 for r in results)
+    assert st["peak_bytes"] <= budget and st["evictions"] > 0
+    for k in range(len(mix)):
+        assert torch.equal(phis[k], alone[k]), k
+
+
+def test_server_refusals_and_ticket_lifecycle():
+    rho = inputs.serving_source(dict(n=128, bc=mg.PERIODIC, seed=1, n_blobs=2), "cuda")
+    small = mg.required_bytes(32, mg.PERIODIC, prec=mg.MIXED)
+    with mg.Server(small + 1, slots=1, max_queue=2) as s:
+        with pytest.raises(mg.MGError) as e:  # its hierarchy alone exceeds the budget
+            s.submit(rho, torch.zeros_like(rho), tol=1e-10)
+        assert e.value.status == 2
+        assert s.stats()["rejected"] == 1
+    with mg.Server(1 << 33, slots=1, max_queue=1) as s:
+        phis = [torch.zeros_like(rho) for _ in range(6)]
+        taken, busy = [], 0
+        for p in phis:  # one runs, one waits, the rest find the queue full
+            try:
+                taken.append((s.submit(rho, p, tol=1e-10), p))
+            except mg.MGError as err:
+                assert err.status == 7
+                busy += 1
+        assert busy >= 1 and len(taken) >= 1
+        assert s.stats()["rejected"] == busy
+        done = [s.wait(t, 120)[0] for t, _ in taken]
+        assert all(r.done and r.status == 0 for r in done)
+        with pytest.raises(mg.MGError):  # retired once reported done
+            s.poll(taken[0][0])
+        for _, p in taken[1:]:
+            assert torch.equal(p, taken[0][1])
