@@ -31,14 +31,16 @@ SEED = 20230227
 # Algorithmic bytes per finest cell of one launch of each kernel class, by
 # the width w of the level precision (see the design notes): the least data
 # that launch must move.
-def algorithmic_bytes_per_cell(kernel: str, w: int) -> float:
+def algorithmic_bytes_per_cell(kernel: str, w: int, fixed_point: bool = True) -> float:
     return {
         "sor": 2.0 * w,                 # read u, read f (own colour), write u (own colour)
         "defect_restrict": 2.0 * w + w / 8.0,
         "prolong": 2.0 * w + w / 8.0,   # read u, coarse e; write u
         "fmg_prolong": w + w / 8.0,
         "defect_norm": 16.0,            # FP64 u, f
-        "outer_residual": 20.0,         # FP64 u, f -> FP32 r
+        # fixed-point outer step: int64 phi, F and FP32 e in; int64 phi, FP32 r out;
+        # the plain FP64 residual: FP64 u, f in, FP32 r out
+        "outer_residual": 32.0 if fixed_point else 20.0,
         "correct": 20.0,                # FP64 u, FP32 e -> FP64 u
         "source": 16.0,                 # FP64 rho -> FP64 f
         "fused_down": 3.0 * w + w / 8.0,  # read u, f; write u, coarse f
@@ -188,6 +190,66 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, ws, rank, stream):
+    """512 grids of {16,32,64,128}^3 (Zipf weights), mixed rules, one persistent
+    graph-captured launch per solve; under torchrun each rank takes its LPT share."""
+    import torch
+
+    import paper_2302_13903_gb300 as mg
+    from paper_2302_13903_gb300 import inputs
+    from paper_2302_13903_gb300.sharding import max_over_ranks, partition_lpt
+    specs = inputs.batch_specs(512)
+    share = partition_lpt([s["n"] ** 3 for s in specs], ws)[rank]
+    mine = [specs[i] for i in share]
+    sizes = [s["n"] for s in mine]
+    rhos = [inputs.batch_source(s, device="cuda") for s in mine]
+    phis = [torch.zeros_like(r) for r in rhos]
+    with mg.Batch(sizes, [1.0 / n for n in sizes], [s["bc"] for s in mine]) as b:
+        for _ in range(max(args.warmup, 3)):
+            st, hists, sts = b.solve(rhos, phis, 1.0, TOL, stream=stream)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.batch_steps):
+            st, hists, sts = b.solve(rhos, phis, 1.0, TOL, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(a.elapsed_time(e) / args.batch_steps)
+        cells = b.cells
+        graph = b.graph
+    total = sum(s["n"] ** 3 for s in specs)
+    return {"grids": len(specs), "cells": total, "ms_per_solve": ms,
+            "value": total / (ms * 1e-3), "unit": UNIT, "graph": graph,
+            "converged": int(sum(1 for x in sts if x == 0)), "of": len(sts),
+            "max_outer_iterations": max(len(h) for h in hists), "rank_cells": cells,
+            "workload": "512 grids, sizes {16,32,64,128}^3 with Zipf 1/rank weights, rules "
+                        "periodic / fixed 0 / zero gradient, 1-8 Gaussian blobs each; FP32 "
+                        "multigrid inside FP64 defect correction to 1e-10; one persistent "
+                        "cooperative launch captured as a CUDA graph"}
+
+
+def run_serving(args):
+    """Poisson arrivals of 32^3-256^3 requests with mixed rules (open with
+    lmax 0-4), tol log-uniform in [1e-10, 1e-6], HBM budget half of free memory."""
+    import torch
+
+    import paper_2302_13903_gb300 as mg
+    from paper_2302_13903_gb300 import inputs, serving
+    free, _ = torch.cuda.mem_get_info()
+    pool = serving.SourcePool()
+    out = []
+    with mg.Server(free // 2, slots=8, max_queue=128) as srv:
+        serving.run_stream(srv, inputs.serving_stream(200, 0.5, seed=1), pool)  # warm hierarchies
+        for rate in (100, 300, 1000, 3000, 5000):
+            stream = inputs.serving_stream(rate, args.serve_seconds)
+            rec, busy, wall = serving.run_stream(srv, stream, pool)
+            out.append(serving.summarize(rec, busy, wall, rate, args.serve_seconds))
+        stats = srv.stats()
+    return {"rates": out, "slots": 8, "max_queue": 128, "budget_bytes": stats["budget_bytes"],
+            "peak_resident_bytes": stats["peak_bytes"], "evictions": stats["evictions"],
+            "latency": "submission to result in the caller's phi (server clock)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,6 +262,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-n", type=int, default=256, help="oracle sample size")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--batch-steps", type=int, default=3, help="timed batched solves (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds of arrivals per serving rate (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -229,6 +295,9 @@ def main():
             torch.distributed.barrier()
 
     solver = mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=prec)
+    if not args.no_tune:
+        solver.autotune(stream)
+    tiles = solver.tile_configs()
     hist = None
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -316,6 +385,9 @@ def main():
     else:
         solver.close()
 
+    batched = run_batched(args, ws, rank, stream) if args.batch_steps > 0 else None
+    serving = run_serving(args) if args.serve_seconds > 0 and ws == 1 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
         cpu = cpu_baseline(args.cpu_n)
@@ -333,6 +405,8 @@ def main():
                                       if prec == mg.MIXED else "FP64"),
                        "n": n, "bc": "periodic", "prec": args.prec, "tol": TOL,
                        "parallelism": f"replicas x{ws}",
+                       "tile_configs": {k: {str(l): list(v) for l, v in d.items()}
+                                        for k, d in tiles.items() if d},
                        "l2": "inputs larger than L2 (1 GiB per FP64 field), no flush"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -343,6 +417,8 @@ def main():
             "final_ratio": float(hist[-1]),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items() if v[1]},
             "fp64_path": fp64,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -306,10 +306,36 @@ long long mg_batch_cells(const mg_batch *batch);
  * mg_batch_solve and replayed after), 0 when it is launched directly. */
 int mg_batch_graph(const mg_batch *batch);
 
+/* Device time of the last mg_batch_solve by phase kind, in milliseconds
+ * (from the GPU's global timer at each grid-wide barrier): ms_by_type[k] for
+ * k < n_types in the order source, mean, source-2, norm, first residual,
+ * first-residual norm, fused down leg, bottom levels, fused up leg,
+ * correction, residual, stopping rule, phi sum, phi mean, phi mean
+ * removal.  Synchronises the device.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
+mg_status mg_batch_phase_ms(mg_batch *batch, double *ms_by_type, int n_types);
+
 const char *mg_batch_last_error(const mg_batch *batch);
 
 /* Number of doubles in a faces array of an nx*ny*nz level. */
 size_t mg_faces_count(int nx, int ny, int nz);
+
+/* Autotune the launch shapes of this context's hot kernels on `stream`: for
+ * every level the fused FP32 legs run on (tile width 32 or 64 cells,
+ * 8..64 z-planes per CTA) and for the fixed-point outer step (4..64 planes),
+ * each candidate is timed with CUDA events on the context's own buffers and
+ * the fastest kept.  Choices are shared by every context of the same shape
+ * in the process (so they give identical bits) and, when the environment
+ * variable MG_TUNE_CACHE names a file, read from and appended to it.  Results
+ * do not depend on the shapes except for the rounding order of the residual
+ * norm.  Overwrites the context's scratch only; synchronises `stream`.
+ * Errors: MG_ERR_ARG, MG_ERR_CUDA. */
+mg_status mg_ctx_autotune(mg_ctx *ctx, void *stream);
+
+/* The shape chosen for a kernel class on a level (MG_K_FUSED_DOWN,
+ * MG_K_FUSED_UP, MG_K_SOR for extra fused smoothing steps, MG_K_OUTER_RESIDUAL
+ * for the fixed-point step on the finest level); 0 means the built-in
+ * choice. */
+mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, int *cz);
 
 /* ---------------------------------------------------------------------------
  * Serving loop.  Requests (solves of any supported size and boundary rule)

@@ -29,7 +29,8 @@ EXPORTS = [
     "mg_ctx_set_timing", "mg_ctx_kernel_time", "mg_op_multipole_moments_noalloc",
     "mg_op_vcycle_down", "mg_op_vcycle_up",
     "mg_batch_create", "mg_batch_solve", "mg_batch_destroy", "mg_batch_cells",
-    "mg_batch_last_error", "mg_batch_graph", "mg_required_bytes",
+    "mg_batch_last_error", "mg_batch_graph", "mg_required_bytes", "mg_ctx_autotune",
+    "mg_ctx_tile_config", "mg_batch_phase_ms",
     "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
     "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error",
 ]
@@ -152,12 +153,18 @@ def lib():
             L.mg_batch_destroy.restype = i
             L.mg_batch_cells.argtypes = [p]
             L.mg_batch_cells.restype = ctypes.c_longlong
+            L.mg_batch_phase_ms.argtypes = [p, p, i]
+            L.mg_batch_phase_ms.restype = i
             L.mg_batch_graph.argtypes = [p]
             L.mg_batch_graph.restype = i
             L.mg_batch_last_error.argtypes = [p]
             L.mg_batch_last_error.restype = ctypes.c_char_p
             L.mg_faces_count.argtypes = [i, i, i]
             L.mg_faces_count.restype = sz
+            L.mg_ctx_autotune.argtypes = [p, p]
+            L.mg_ctx_autotune.restype = i
+            L.mg_ctx_tile_config.argtypes = [p, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            L.mg_ctx_tile_config.restype = i
             L.mg_required_bytes.argtypes = [i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
             L.mg_required_bytes.restype = i
             L.mg_server_create.argtypes = [sz, i, i, ctypes.POINTER(Opts), ctypes.POINTER(p)]
@@ -255,6 +262,26 @@ class Solver:
 
     def set_timing(self, on=True):
         _check(lib().mg_ctx_set_timing(self.ctx, int(on)), self.ctx)
+
+    def autotune(self, stream=None):
+        """Time the candidate launch shapes of the hot kernels and keep the fastest."""
+        _check(lib().mg_ctx_autotune(self.ctx, _stream_ptr(stream)), self.ctx)
+
+    def tile_configs(self):
+        """{"fused_down" | "fused_up" | "sor" | "outer_residual": {level: (tx, cz)}} (0: built-in)."""
+        out = {}
+        levels = self.n.bit_length()
+        for name in ("fused_down", "fused_up", "sor", "outer_residual"):
+            k = KERNELS.index(name)
+            per = {}
+            for l in range(levels):
+                tx, cz = ctypes.c_int(0), ctypes.c_int(0)
+                _check(lib().mg_ctx_tile_config(self.ctx, l, k, ctypes.byref(tx), ctypes.byref(cz)),
+                       self.ctx)
+                if tx.value or cz.value:
+                    per[l] = (tx.value, cz.value)
+            out[name] = per
+        return out
 
     def kernel_times(self):
         """{kernel class: (total ms, launches)} of finest-level launches."""
@@ -440,6 +467,17 @@ class Batch:
     @property
     def graph(self):
         return bool(lib().mg_batch_graph(self.ptr))
+
+    PHASES = ["source", "mean", "source2", "norm", "r0", "r0_norm", "down", "bottom", "up",
+              "correct", "residual", "stop_rule", "phi_sum", "phi_mean", "phi_sub"]
+
+    def phase_ms(self):
+        """{phase kind: device ms} of the last solve."""
+        out = np.zeros(len(self.PHASES))
+        st = lib().mg_batch_phase_ms(self.ptr, out.ctypes.data, len(out))
+        if st != 0:
+            raise MGError(st, lib().mg_batch_last_error(self.ptr).decode())
+        return dict(zip(self.PHASES, out.tolist()))
 
     def solve(self, rhos, phis, four_pi_G=1.0, tol=1e-10, hist_cap=64, stream=None):
         """rhos, phis: lists of CUDA float64 tensors.  Returns (status, hists, statuses)."""

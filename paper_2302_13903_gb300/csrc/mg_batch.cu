@@ -45,7 +45,7 @@ constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4>::NT;  // 216
 constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4>::SMEM;
 constexpr int kMaxL = 16;
 constexpr int kChunk = 32768;   // cells per chunk item
-constexpr int kFusedMinN = 64;  // levels of at least 64^3 use the fused tiles
+constexpr int kFusedMinN = 32;  // levels of at least 32^3 use the fused tiles
 constexpr int kCz = 32;         // z-chunk of fused tiles
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -105,6 +105,7 @@ struct Ctl {
   unsigned* bar_gen;
   int* err;
   int* active_left;    // grids still active, after each FIN phase (index = phase)
+  unsigned long long* ptime;  // [nphases + 1]: end of each phase, [nphases] = start (ns)
   int nphases, ngrids, hist_cap;
   double omega;
   int max_cycles, inner_zero;
@@ -137,6 +138,12 @@ __device__ bool grid_barrier(const Ctl& c) {
   return *((volatile int*)c.err) == 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ int level_of(const GridDev& g, int n) {
   int l = g.L - 1, m = g.n;
   while (m > n) {
@@ -165,46 +172,56 @@ __device__ double block_sum(double v) {
 }
 
 // One chunk of the finest level: cells [c * kChunk, min(N, (c + 1) kChunk)).
+// The grid's fields are read once into registers (the loop's stores could
+// otherwise alias them).
 template <int TYPE>
 __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
-  const Grid gr{g.n, g.n, g.n};
-  const long long N = gr.cells();
-  const long long lo = (long long)chunk * kChunk, hi = min(N, lo + kChunk);
+  const int n = g.n;
+  const Grid gr{n, n, n};
+  const int N = n * n * n;  // <= 1024^3 = 2^30
+  const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
   const int F = g.L - 1;
+  double* __restrict__ phi = g.phi;
+  double* __restrict__ f64 = g.f64;
+  const double* __restrict__ rho = g.rho;
+  float* __restrict__ r32 = g.f32[F];
+  const float* __restrict__ e32 = g.u32[F];
+  const double fpg = g.fpg, mean = g.mean, inv_scale = 1.0 / g.scale, h = g.h;
+  const double inv_h2 = 1.0 / (h * h), bcval = g.bcval;
+  const int bc = g.bc;
+  const double sc = TYPE == PH_R0 ? 1.0 / g.fnorm : 1.0 / g.rn;
   double acc = 0.0;
-  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+  for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) {
     if (TYPE == PH_SRC) {
-      const double v = g.fpg * g.rho[t];
-      g.f64[t] = v;
+      const double v = fpg * rho[t];
+      f64[t] = v;
       acc += v;
     } else if (TYPE == PH_SRC2) {
-      const double v = g.f64[t] - g.mean;
-      g.f64[t] = v;
+      const double v = f64[t] - mean;
+      f64[t] = v;
       acc += v * v;
     } else if (TYPE == PH_CORR) {
-      g.phi[t] += (double)g.u32[F][t] / g.scale;
+      phi[t] += (double)e32[t] * inv_scale;
     } else if (TYPE == PH_PSUM) {
-      acc += g.phi[t];
+      acc += phi[t];
     } else if (TYPE == PH_PSUB) {
-      g.phi[t] -= g.mean;
+      phi[t] -= mean;
     } else {  // PH_R0 (phi = 0) and PH_RESID
-      const int i = (int)(t % gr.nx);
-      const long long r = t / gr.nx;
-      const int j = (int)(r % gr.ny), k = (int)(r / gr.ny);
+      const int i = t % n, r = t / n;
+      const int j = r % n, k = r / n;
       double d;
       if (TYPE == PH_R0) {
-        g.phi[t] = 0.0;
+        phi[t] = 0.0;
         // L_h(0) is nonzero only through the fixed value's ghosts (2 b each)
         int faces = 0;
-        if (g.bc == BC_FIXED) faces = (i == 0) + (i == gr.nx - 1) + (j == 0) + (j == gr.ny - 1) +
-                                      (k == 0) + (k == gr.nz - 1);
-        d = g.f64[t] - (faces * 2.0 * g.bcval) / (g.h * g.h);
+        if (bc == BC_FIXED)
+          faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
+        d = f64[t] - (faces * 2.0 * bcval) * inv_h2;
       } else {
-        const double s = dev::neighbour_sum(g.phi, i, j, k, gr, phys_bc(g));
-        d = g.f64[t] - (s - 6.0 * g.phi[t]) / (g.h * g.h);
+        const double s = dev::neighbour_sum(phi, i, j, k, gr, Bc{bc, bcval, nullptr});
+        d = f64[t] - (s - 6.0 * phi[t]) * inv_h2;
       }
-      const double sc = TYPE == PH_R0 ? 1.0 / g.fnorm : 1.0 / g.rn;
-      g.f32[F][t] = (float)(d * sc);
+      r32[t] = (float)(d * sc);
       acc += d * d;
     }
   }
@@ -244,8 +261,43 @@ __device__ void fin_item(const Ctl& c, GridDev& g, int gi) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_batch(Ctl c) {
+// One tile item of a fused leg on level l: tiles TX x 16 cells, the chunk's
+// planes; the down leg starts from zero on coarse levels and, when asked, on
+// the finest.
+template <int TX>
+__device__ __forceinline__ void tile_leg(bool down, bool per, const GridDev& g, int l,
+                                         bool zero_finest, const fused::FusedParams& fp,
+                                         const Item& I, float4* smem) {
+  if (down) {
+    const bool zg = (l < g.L - 1) || zero_finest;
+    if (zg) {
+      if (per)
+        fused::fused_tile<fused::kDown, true, true, TX, 16, 4, true>(
+            g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+      else
+        fused::fused_tile<fused::kDown, true, false, TX, 16, 4, true>(
+            g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+    } else {
+      if (per)
+        fused::fused_tile<fused::kDown, false, true, TX, 16, 4, true>(
+            g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+      else
+        fused::fused_tile<fused::kDown, false, false, TX, 16, 4, true>(
+            g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
+    }
+  } else {
+    if (per)
+      fused::fused_tile<fused::kUp, false, true, TX, 16, 4, true>(
+          g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
+    else
+      fused::fused_tile<fused::kUp, false, false, TX, 16, 4, true>(
+          g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
   extern __shared__ float4 smem[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) c.ptime[c.nphases] = global_ns();
   for (int ph = 0; ph < c.nphases; ++ph) {
     const Phase P = c.phases[ph];
     __shared__ int s_item;
@@ -305,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch(Ctl c) {
           break;
         case PH_BOTTOM: {
           bottom::BottomArgs<float> a;
-          const int top = level_of(g, min(g.n, 32));
+          const int top = level_of(g, min(g.n, kFusedMinN / 2));
           for (int l = 0; l < kBottomLevels; ++l) {
             const bool used = l <= top;
             a.u[l] = used ? g.u32[l] : nullptr;
@@ -337,37 +389,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch(Ctl c) {
           fp.inv_h2 = (float)(1.0 / (hl * hl));
           fp.cz = kCz < P.n ? kCz : P.n;
           const bool per = g.bc == BC_PERIODIC;
-          if (P.type == PH_DOWN) {
-            const bool zg = (l < g.L - 1) || (P.cycle == 0 && c.inner_zero);
-            if (zg) {
-              if (per)
-                fused::fused_tile<fused::kDown, true, true, 64, 16, 4, true>(
-                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
-              else
-                fused::fused_tile<fused::kDown, true, false, 64, 16, 4, true>(
-                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
-            } else {
-              if (per)
-                fused::fused_tile<fused::kDown, false, true, 64, 16, 4, true>(
-                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
-              else
-                fused::fused_tile<fused::kDown, false, false, 64, 16, 4, true>(
-                    g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
-            }
-          } else {
-            if (per)
-              fused::fused_tile<fused::kUp, false, true, 64, 16, 4, true>(
-                  g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
-            else
-              fused::fused_tile<fused::kUp, false, false, 64, 16, 4, true>(
-                  g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
-          }
+          if (P.n >= 64)
+            tile_leg<64>(P.type == PH_DOWN, per, g, l, P.cycle == 0 && c.inner_zero, fp, I, smem);
+          else
+            tile_leg<32>(P.type == PH_DOWN, per, g, l, P.cycle == 0 && c.inner_zero, fp, I, smem);
           break;
         }
       }
       __syncthreads();
     }
     if (!grid_barrier(c)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.ptime[ph] = global_ns();
     if (P.type == PH_FIN && *((volatile int*)&c.active_left[ph]) == 0) {
       // every grid has stopped: go to the final mean removal
       int q = ph + 1;
@@ -399,6 +431,8 @@ struct mg_batch {
   unsigned* d_bar = nullptr;
   int* d_err = nullptr;
   int* d_active = nullptr;
+  unsigned long long* d_ptime = nullptr;
+  std::vector<Phase> host_phases;
   int* h_err = nullptr;
   int nphases = 0, nitems = 0, nchunks = 0, hist_cap = 64;
   int blocks = 0;
@@ -466,10 +500,10 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
     // largest tiles first: grids in the order given, tiles of this level
     for (int g = 0; g < G; ++g) {
       if (b->host_grids[g].n < n) continue;
-      const int cz = std::min(kCz, n);
+      const int cz = std::min(kCz, n), tx = n >= 64 ? 64 : 32;
       for (int z = 0; z < n / cz; ++z)
         for (int y = 0; y < n / 16; ++y)
-          for (int x = 0; x < n / 64; ++x) items.push_back(Item{g, x, y, z});
+          for (int x = 0; x < n / tx; ++x) items.push_back(Item{g, x, y, z});
     }
     p.count = (int)items.size() - p.first;
     if (p.count > 0) phases.push_back(p);
@@ -504,6 +538,8 @@ cudaError_t enqueue_solve(mg_batch* b, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_active, 0, sizeof(int) * b->nphases, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(b->d_ptime, 0, sizeof(unsigned long long) * (b->nphases + 1), s);
   Ctl c;
   c.phases = b->d_phases;
   c.items = b->d_items;
@@ -515,6 +551,7 @@ cudaError_t enqueue_solve(mg_batch* b, cudaStream_t s) {
   c.bar_gen = b->d_bar + 1;
   c.err = b->d_err;
   c.active_left = b->d_active;
+  c.ptime = b->d_ptime;
   c.nphases = b->nphases;
   c.ngrids = b->ngrids;
   c.hist_cap = b->hist_cap;
@@ -617,8 +654,10 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
     b->d_bar = balloc<unsigned>(b, 2);
     b->d_err = balloc<int>(b, 1);
     b->d_active = balloc<int>(b, b->nphases);
+    b->d_ptime = balloc<unsigned long long>(b, b->nphases + 1);
     ok = b->d_grids && b->d_phases && b->d_items && b->d_part && b->d_hist && b->d_counters &&
-         b->d_bar && b->d_err && b->d_active;
+         b->d_bar && b->d_err && b->d_active && b->d_ptime;
+    b->host_phases = phases;
   }
   if (ok) {
     ok = cudaMallocHost(&b->h_grids, sizeof(GridDev) * n) == cudaSuccess &&
@@ -736,6 +775,25 @@ mg_status mg_batch_destroy(mg_batch* b) {
 long long mg_batch_cells(const mg_batch* b) { return b ? b->cells : 0; }
 
 int mg_batch_graph(const mg_batch* b) { return b && b->exec ? 1 : 0; }
+
+mg_status mg_batch_phase_ms(mg_batch* b, double* ms_by_type, int n_types) {
+  if (!b || !ms_by_type || n_types < 1) return MG_ERR_ARG;
+  std::vector<unsigned long long> t((size_t)b->nphases + 1);
+  if (cudaMemcpy(t.data(), b->d_ptime, sizeof(unsigned long long) * t.size(),
+                 cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  for (int k = 0; k < n_types; ++k) ms_by_type[k] = 0.0;
+  unsigned long long last = t[(size_t)b->nphases];
+  for (int ph = 0; ph < b->nphases; ++ph) {
+    if (!t[(size_t)ph] || !last) continue;  // skipped after every grid stopped
+    const int ty = b->host_phases[(size_t)ph].type;
+    if (ty < n_types) ms_by_type[ty] += (double)(t[(size_t)ph] - last) * 1e-6;
+    last = t[(size_t)ph];
+  }
+  return MG_OK;
+}
 
 const char* mg_batch_last_error(const mg_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
 

@@ -250,28 +250,37 @@ cudaError_t launch_fx_correct(long long* phi, const float* e, long long n, float
 
 bool fx_step_ok(Grid g) { return g.nx % FX_TX == 0 && g.ny % FX_TY == 0; }
 
-int fx_step_blocks(Grid g) {
+// Planes per CTA: the given cz, else the largest of 64 .. 4 that still
+// gives four CTAs per SM.
+int fx_step_cz(Grid g, int cz) {
   const long long cols = (long long)(g.nx / FX_TX) * (g.ny / FX_TY);
-  int cz = 64;
-  while (cz > 4 && cols * ((g.nz + cz - 1) / cz) < 4 * 152) cz /= 2;
-  if (cz > g.nz) cz = g.nz;
-  return (int)(cols * ((g.nz + cz - 1) / cz));
+  if (cz <= 0) {
+    cz = 64;
+    while (cz > kFxMinCz && cols * ((g.nz + cz - 1) / cz) < 4 * 152) cz /= 2;
+  }
+  return cz > g.nz ? g.nz : cz;
+}
+
+// Blocks of a launch with `cz` planes per CTA; cz = 0: the most any allowed
+// cz (>= kFxMinCz) gives, to size the partial sums.
+int fx_step_blocks(Grid g, int cz) {
+  const long long cols = (long long)(g.nx / FX_TX) * (g.ny / FX_TY);
+  const int z = cz > 0 ? fx_step_cz(g, cz) : (g.nz < kFxMinCz ? g.nz : kFxMinCz);
+  return (int)(cols * ((g.nz + z - 1) / z));
 }
 
 cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const float* e, float c,
                            const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
                            float factor, double* partials, int nb_max, int* flag, int* nb_out,
-                           cudaStream_t s) {
+                           cudaStream_t s, int cz_req) {
   // The ghost 2 b - phi on the fixed-point grid: 2 b 2^S rounded once.
   FxBc b;
   b.kind = bc.kind;
   b.c2 = 2.0 * two_pow_S;
   b.b2 = bc.kind == BC_FIXED ? (long long)std::llrint(bc.value * b.c2) : 0;
   b.faces = bc.faces;
-  const long long cols = (long long)(g.nx / FX_TX) * (g.ny / FX_TY);
-  int cz = 64;
-  while (cz > 4 && cols * ((g.nz + cz - 1) / cz) < 4 * 152) cz /= 2;
-  if (cz > g.nz) cz = g.nz;
+  if (cz_req != 0 && cz_req < kFxMinCz) return cudaErrorInvalidValue;
+  const int cz = fx_step_cz(g, cz_req);
   dim3 grid(g.nx / FX_TX, g.ny / FX_TY, (g.nz + cz - 1) / cz);
   const int nb = (int)(grid.x * grid.y * grid.z);
   if (nb > nb_max) return cudaErrorInvalidValue;

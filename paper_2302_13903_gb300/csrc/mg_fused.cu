@@ -31,16 +31,18 @@ cudaError_t launch_t(const float* ui, float* uo, const float* f, const float* ec
   return cudaGetLastError();
 }
 
-// Tiles: 64 x 16 for levels >= 64 cells wide, 32 x 16 for 32.  The z-chunk is
-// the largest of 64, 32, 16, 8 planes that still gives two CTAs per SM.
+// Built-in shape: tiles of 64 x 16 for levels >= 64 cells wide, 32 x 16 for
+// 32; the z-chunk is the largest of 64, 32, 16, 8 planes that still gives two
+// CTAs per SM.  A nonzero cfg field (checked by fused_cfg_ok) replaces it.
 template <int MODE, bool ZERO, bool PER>
 cudaError_t dispatch_t(const float* ui, float* uo, const float* f, const float* ec, float* fc,
-                       FusedParams p, cudaStream_t s) {
+                       FusedParams p, TileCfg cfg, cudaStream_t s) {
   const long long sms = 152;
-  const int tx = p.nx >= 64 ? 64 : 32, ty = 16;
+  const int tx = cfg.tx ? cfg.tx : (p.nx >= 64 ? 64 : 32), ty = 16;
   const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
   int cz = 64;
   while (cz > 8 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
+  if (cfg.cz) cz = cfg.cz;
   p.cz = cz < p.nz ? cz : p.nz;
   if (tx == 64) return launch_t<MODE, ZERO, PER, 64, 16>(ui, uo, f, ec, fc, p, s);
   return launch_t<MODE, ZERO, PER, 32, 16>(ui, uo, f, ec, fc, p, s);
@@ -48,9 +50,9 @@ cudaError_t dispatch_t(const float* ui, float* uo, const float* f, const float* 
 
 template <int MODE, bool ZERO>
 cudaError_t dispatch(const float* ui, float* uo, const float* f, const float* ec, float* fc,
-                     FusedParams p, bool periodic, cudaStream_t s) {
-  return periodic ? dispatch_t<MODE, ZERO, true>(ui, uo, f, ec, fc, p, s)
-                  : dispatch_t<MODE, ZERO, false>(ui, uo, f, ec, fc, p, s);
+                     FusedParams p, bool periodic, TileCfg cfg, cudaStream_t s) {
+  return periodic ? dispatch_t<MODE, ZERO, true>(ui, uo, f, ec, fc, p, cfg, s)
+                  : dispatch_t<MODE, ZERO, false>(ui, uo, f, ec, fc, p, cfg, s);
 }
 
 FusedParams params(Grid g, double h, const Bc& bc, double omega) {
@@ -83,26 +85,38 @@ bool fused_ok(Grid g, const Bc& bc) {
          g.nz % 8 == 0 && (g.nx < 64 || g.nx % 64 == 0);
 }
 
+bool fused_cfg_ok(Grid g, TileCfg cfg) {
+  const bool tx_ok = cfg.tx == 0 || (cfg.tx == 32 && g.nx % 32 == 0) ||
+                     (cfg.tx == 64 && g.nx % 64 == 0);
+  const bool cz_ok = cfg.cz == 0 || (cfg.cz >= 8 && cfg.cz % 8 == 0 && cfg.cz <= 1024);
+  return tx_ok && cz_ok;
+}
+
 cudaError_t launch_fused_down(const float* u_in, float* u_out, const float* f, float* fc, Grid g,
-                              double h, Bc bc, double omega, bool zero_guess, cudaStream_t s) {
+                              double h, Bc bc, double omega, bool zero_guess, cudaStream_t s,
+                              TileCfg cfg) {
+  if (!fused_cfg_ok(g, cfg)) return cudaErrorInvalidValue;
   const FusedParams p = params(g, h, bc, omega);
   const bool per = bc.kind == BC_PERIODIC;
-  return zero_guess ? dispatch<kDown, true>(u_in, u_out, f, nullptr, fc, p, per, s)
-                    : dispatch<kDown, false>(u_in, u_out, f, nullptr, fc, p, per, s);
+  return zero_guess ? dispatch<kDown, true>(u_in, u_out, f, nullptr, fc, p, per, cfg, s)
+                    : dispatch<kDown, false>(u_in, u_out, f, nullptr, fc, p, per, cfg, s);
 }
 
 cudaError_t launch_fused_up(const float* u_in, float* u_out, const float* f, const float* ec,
-                            Grid g, double h, Bc bc, double omega, cudaStream_t s) {
+                            Grid g, double h, Bc bc, double omega, cudaStream_t s, TileCfg cfg) {
+  if (!fused_cfg_ok(g, cfg)) return cudaErrorInvalidValue;
   return dispatch<kUp, false>(u_in, u_out, f, ec, nullptr, params(g, h, bc, omega),
-                              bc.kind == BC_PERIODIC, s);
+                              bc.kind == BC_PERIODIC, cfg, s);
 }
 
 cudaError_t launch_fused_smooth(const float* u_in, float* u_out, const float* f, Grid g, double h,
-                                Bc bc, double omega, bool zero_guess, cudaStream_t s) {
+                                Bc bc, double omega, bool zero_guess, cudaStream_t s,
+                                TileCfg cfg) {
+  if (!fused_cfg_ok(g, cfg)) return cudaErrorInvalidValue;
   const FusedParams p = params(g, h, bc, omega);
   const bool per = bc.kind == BC_PERIODIC;
-  return zero_guess ? dispatch<kPlain, true>(u_in, u_out, f, nullptr, nullptr, p, per, s)
-                    : dispatch<kPlain, false>(u_in, u_out, f, nullptr, nullptr, p, per, s);
+  return zero_guess ? dispatch<kPlain, true>(u_in, u_out, f, nullptr, nullptr, p, per, cfg, s)
+                    : dispatch<kPlain, false>(u_in, u_out, f, nullptr, nullptr, p, per, cfg, s);
 }
 
 }  // namespace mg

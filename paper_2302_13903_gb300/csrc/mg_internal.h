@@ -118,18 +118,30 @@ cudaError_t launch_bottom(T* const* u, T* const* f, const int* n, const double* 
 // Fused FP32 V-cycle legs (homogeneous rules only).  Each reads u_in and
 // writes u_out (distinct buffers).
 
+// Launch shape of a z-marching kernel: tile width in cells (fused kernels:
+// 32 or 64) and z-planes per CTA.  A zero field takes the built-in choice.
+struct TileCfg {
+  int tx = 0;
+  int cz = 0;
+};
+
 // Whether the fused kernels handle this level (width >= 32, homogeneous rule).
 bool fused_ok(Grid g, const Bc& bc);
+// Whether cfg is a shape the fused kernels can run on g (zeros allowed).
+bool fused_cfg_ok(Grid g, TileCfg cfg);
 // One SMOOTH step from u_in (or 0) then fc = restriction of f - L u (Algorithm
 // 1, steps 1-3).
 cudaError_t launch_fused_down(const float* u_in, float* u_out, const float* f, float* fc, Grid g,
-                              double h, Bc bc, double omega, bool zero_guess, cudaStream_t s);
+                              double h, Bc bc, double omega, bool zero_guess, cudaStream_t s,
+                              TileCfg cfg = TileCfg{});
 // u_in + trilinear(ec), then one SMOOTH step (Algorithm 1, steps 5-7).
 cudaError_t launch_fused_up(const float* u_in, float* u_out, const float* f, const float* ec,
-                            Grid g, double h, Bc bc, double omega, cudaStream_t s);
+                            Grid g, double h, Bc bc, double omega, cudaStream_t s,
+                            TileCfg cfg = TileCfg{});
 // One SMOOTH step.
 cudaError_t launch_fused_smooth(const float* u_in, float* u_out, const float* f, Grid g, double h,
-                                Bc bc, double omega, bool zero_guess, cudaStream_t s);
+                                Bc bc, double omega, bool zero_guess, cudaStream_t s,
+                                TileCfg cfg = TileCfg{});
 
 // ---------------------------------------------------------------------------
 // Exact 64-bit fixed-point outer residual (mg_fixed.cu).
@@ -149,12 +161,16 @@ cudaError_t launch_fx_correct(long long* phi, const float* e, long long n, float
 // r32 = (F - (sum_nb PHI_out - 6 PHI_out)) * factor exactly in integers, one
 // partial sum of r32^2 per block (count in *nb_out, at most nb_max).
 // Requires nx % 32 == 0 and ny % 16 == 0 (fx_step_ok).
+// cz = 0 takes the built-in planes per CTA; fx_step_blocks(g, 0) bounds the
+// block count of every cz >= kFxMinCz.
+constexpr int kFxMinCz = 4;
 bool fx_step_ok(Grid g);
-int fx_step_blocks(Grid g);
+int fx_step_cz(Grid g, int cz);
+int fx_step_blocks(Grid g, int cz);
 cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const float* e, float c,
                            const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
                            float factor, double* partials, int nb_max, int* flag, int* nb_out,
-                           cudaStream_t s);
+                           cudaStream_t s, int cz = 0);
 
 // ---------------------------------------------------------------------------
 // Multipole boundary (App. A).

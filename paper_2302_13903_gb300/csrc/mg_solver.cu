@@ -8,8 +8,11 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -64,6 +67,10 @@ struct mg_ctx {
   std::vector<int> pending_class;   // class of each recorded pair in this solve
   double kernel_ms[MG_K_COUNT] = {};
   long long kernel_n[MG_K_COUNT] = {};
+  // Launch shapes of the fused legs per level and of the fixed-point outer
+  // step (zeros: built-in choice), set by mg_ctx_autotune.
+  mg::TileCfg cfg_down[kMaxLevels] = {}, cfg_up[kMaxLevels] = {}, cfg_smooth[kMaxLevels] = {};
+  int fx_cz = 0;
 };
 
 namespace {
@@ -140,7 +147,7 @@ void alloc_hierarchy(mg_ctx* c) {
   c->partials_cap = mg::kPartials;
   if (o.prec == MG_MIXED && o.outer_fixed && mg::fx_step_ok(level_grid(c, F))) {
     c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
-    const int nb = mg::fx_step_blocks(level_grid(c, F));
+    const int nb = mg::fx_step_blocks(level_grid(c, F), 0);
     if (nb > c->partials_cap) c->partials_cap = nb;
   }
   c->partials = dalloc<double>(c, c->partials_cap);
@@ -269,7 +276,8 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
   bool zg = zero_guess;
   for (int q = 0; q + 1 < pre; ++q) {  // extra pre-smoothing steps of V(2,.)
     KTimer t(c, MG_K_SOR, fin, s);
-    check(c, mg::launch_fused_smooth(c->u32[l], c->u32b[l], c->f32[l], g, h, bc_top, om, zg, s),
+    check(c, mg::launch_fused_smooth(c->u32[l], c->u32b[l], c->f32[l], g, h, bc_top, om, zg, s,
+                                     c->cfg_smooth[l]),
           "fused smooth");
     swap_level();
     zg = false;
@@ -277,7 +285,7 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
   if (pre >= 1) {  // 1-3
     KTimer t(c, MG_K_FUSED_DOWN, fin, s);
     check(c, mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
-                                   om, zg, s),
+                                   om, zg, s, c->cfg_down[l]),
           "fused down");
     swap_level();
   } else {
@@ -298,14 +306,14 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
     {
       KTimer t(c, MG_K_FUSED_UP, fin, s);
       check(c, mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc_top,
-                                   om, s),
+                                   om, s, c->cfg_up[l]),
             "fused up");
       swap_level();
     }
     for (int q = 1; q < post; ++q) {
       KTimer t(c, MG_K_SOR, fin, s);
       check(c, mg::launch_fused_smooth(c->u32[l], c->u32b[l], c->f32[l], g, h, bc_top, om, false,
-                                       s),
+                                       s, c->cfg_smooth[l]),
             "fused smooth");
       swap_level();
     }
@@ -583,7 +591,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
         check(c, mg::launch_fx_step(cur, alt, c->u32[F], (float)(two_S / old_scale), FX,
                                     c->f32[F], g, bc, two_S,
                                     (float)(scale / (c->h * c->h * two_S)), c->partials,
-                                    c->partials_cap, c->iflag, &nbs, s),
+                                    c->partials_cap, c->iflag, &nbs, s, c->fx_cz),
               "fixed-point step");
       }
       std::swap(cur, alt);
@@ -624,6 +632,163 @@ mg_status validate_opts(const mg_opts& o) {
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;
   return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of launch shapes.  Each candidate runs on the context's own
+// buffers (contents irrelevant: the kernels' cost does not depend on the
+// values) a few times between CUDA events on the solve's stream; the fastest
+// wins.  Results are kept per process, keyed by device and problem shape, so
+// every context of that shape launches identically (and gives identical
+// bits); with MG_TUNE_CACHE naming a file they also persist across runs.
+enum TuneKind { TUNE_DOWN = 0, TUNE_UP = 1, TUNE_SMOOTH = 2, TUNE_FX = 3 };
+
+struct TuneKey {
+  int sms, major, minor, kind, n, periodic;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(sms, major, minor, kind, n, periodic) <
+           std::tie(o.sms, o.major, o.minor, o.kind, o.n, o.periodic);
+  }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, mg::TileCfg> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("MG_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return;
+  TuneKey k;
+  mg::TileCfg v;
+  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d", &k.sms, &k.major, &k.minor, &k.kind, &k.n,
+                     &k.periodic, &v.tx, &v.cz) == 8)
+    g_tune[k] = v;
+  std::fclose(fp);
+}
+
+void tune_store_locked(const TuneKey& k, mg::TileCfg v) {
+  g_tune[k] = v;
+  const char* path = std::getenv("MG_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = std::fopen(path, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%d %d %d %d %d %d %d %d\n", k.sms, k.major, k.minor, k.kind, k.n, k.periodic,
+               v.tx, v.cz);
+  std::fclose(fp);
+}
+
+// Milliseconds of `reps` launches of `run` after two untimed ones.
+template <typename Run>
+float time_launches(mg_ctx* c, cudaStream_t s, int reps, Run run) {
+  for (int q = 0; q < 2; ++q) check(c, run(), "autotune launch");
+  cudaEvent_t a, b;
+  check(c, cudaEventCreate(&a), "cudaEventCreate");
+  check(c, cudaEventCreate(&b), "cudaEventCreate");
+  check(c, cudaEventRecord(a, s), "record");
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < reps && e == cudaSuccess; ++q) e = run();
+  check(c, e, "autotune launch");
+  check(c, cudaEventRecord(b, s), "record");
+  check(c, cudaEventSynchronize(b), "sync");
+  float ms = 0.f;
+  check(c, cudaEventElapsedTime(&ms, a, b), "elapsed");
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+void autotune(mg_ctx* c, cudaStream_t s) {
+  cudaDeviceProp prop;
+  check(c, cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
+  const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr});
+  const int periodic = c->bc_kind == MG_BC_PERIODIC ? 1 : 0;
+  const double om = c->opts.omega;
+  const int F = c->L - 1;
+  const int reps = 5;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  if (c->opts.prec == MG_MIXED) {
+    for (int l = 1; l <= F; ++l) {
+      const Grid g = level_grid(c, l);
+      if (!c->u32b[l] || !mg::fused_ok(g, hom)) continue;
+      for (int z : {0, 1, 2}) {  // zero-fill the level's buffers once
+        float* buf = z == 0 ? c->u32[l] : z == 1 ? c->u32b[l] : c->f32[l];
+        check(c, cudaMemsetAsync(buf, 0, sizeof(float) * g.cells(), s), "zero");
+      }
+      check(c, cudaMemsetAsync(c->u32[l - 1], 0, sizeof(float) * level_grid(c, l - 1).cells(), s),
+            "zero");
+      const double h = level_h(c, l);
+      for (int kind : {TUNE_DOWN, TUNE_UP, TUNE_SMOOTH}) {
+        if (kind == TUNE_SMOOTH && c->opts.pre < 2 && c->opts.post < 2) continue;
+        const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, kind, g.nx, periodic};
+        mg::TileCfg best;
+        auto hit = g_tune.find(key);
+        if (hit != g_tune.end()) {
+          best = hit->second;
+        } else {
+          float best_ms = 1e30f;
+          for (int tx : {32, 64}) {
+            for (int cz : {8, 16, 32, 64}) {
+              const mg::TileCfg cand{tx, cz};
+              if (cz > g.nz || !mg::fused_cfg_ok(g, cand)) continue;
+              const float ms = time_launches(c, s, reps, [&]() {
+                if (kind == TUNE_DOWN)
+                  return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g,
+                                               h, hom, om, false, s, cand);
+                if (kind == TUNE_UP)
+                  return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h,
+                                             hom, om, s, cand);
+                return mg::launch_fused_smooth(c->u32[l], c->u32b[l], c->f32[l], g, h, hom, om,
+                                               false, s, cand);
+              });
+              if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+              }
+            }
+          }
+          tune_store_locked(key, best);
+        }
+        (kind == TUNE_DOWN ? c->cfg_down : kind == TUNE_UP ? c->cfg_up : c->cfg_smooth)[l] = best;
+      }
+    }
+  }
+  const Grid g = level_grid(c, F);
+  if (c->fxbuf) {
+    const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, TUNE_FX, g.nx, periodic};
+    auto hit = g_tune.find(key);
+    if (hit != g_tune.end()) {
+      c->fx_cz = hit->second.cz;
+    } else {
+      // phi_in and F both read the zeroed FP64 source buffer (as integers),
+      // phi_out is the second integer buffer.
+      long long* q = reinterpret_cast<long long*>(c->f64[F]);
+      check(c, cudaMemsetAsync(q, 0, sizeof(long long) * g.cells(), s), "zero");
+      check(c, cudaMemsetAsync(c->u32[F], 0, sizeof(float) * g.cells(), s), "zero");
+      float best_ms = 1e30f;
+      int best = 0;
+      for (int cz : {4, 8, 16, 32, 64}) {
+        if (cz > g.nz) continue;
+        int nb = 0;
+        const float ms = time_launches(c, s, reps, [&]() {
+          return mg::launch_fx_step(q, c->fxbuf, c->u32[F], 1.f, q, c->f32[F], g, hom, 1.0, 1.f,
+                                    c->partials, c->partials_cap, c->iflag, &nb, s, cz);
+        });
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = cz;
+        }
+      }
+      check(c, cudaMemsetAsync(c->iflag, 0, sizeof(int) * 4, s), "clear flag");
+      tune_store_locked(key, mg::TileCfg{0, best});
+      c->fx_cz = best;
+    }
+  }
+  check(c, cudaStreamSynchronize(s), "sync");
 }
 
 }  // namespace
@@ -675,6 +840,31 @@ mg_status mg_ctx_set_timing(mg_ctx* c, int on) {
     c->kernel_ms[k] = 0.0;
     c->kernel_n[k] = 0;
   }
+  return MG_OK;
+}
+
+mg_status mg_ctx_autotune(mg_ctx* c, void* stream) {
+  if (!c) return MG_ERR_ARG;
+  try {
+    check(c, cudaSetDevice(c->device), "cudaSetDevice");
+    autotune(c, (cudaStream_t)stream);
+  } catch (const Fail& f) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    return f.st;
+  }
+  return MG_OK;
+}
+
+mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, int* cz) {
+  if (!c || !tx || !cz || level < 0 || level >= c->L) return MG_ERR_ARG;
+  mg::TileCfg v;
+  if (kernel == MG_K_FUSED_DOWN) v = c->cfg_down[level];
+  else if (kernel == MG_K_FUSED_UP) v = c->cfg_up[level];
+  else if (kernel == MG_K_SOR) v = c->cfg_smooth[level];
+  else if (kernel == MG_K_OUTER_RESIDUAL) v = mg::TileCfg{0, level == c->L - 1 ? c->fx_cz : 0};
+  else return MG_ERR_ARG;
+  *tx = v.tx;
+  *cz = v.cz;
   return MG_OK;
 }
 

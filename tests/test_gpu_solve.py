@@ -202,3 +202,32 @@ def test_invalid_arguments_on_gpu():
                           hist.ctypes.data, 4, ctypes.byref(nh), None) == 1
         assert L.mg_solve(s.ctx, None, 1.0, 1e-10, rho.data_ptr(), hist.ctypes.data, 4,
                           ctypes.byref(nh), None) == 1
+
+
+@pytest.mark.parametrize("bc,n", [(mg.PERIODIC, 128), (mg.FIXED, 64), (mg.ZEROGRAD, 32)])
+def test_autotuned_shapes_keep_the_result(bc, n):
+    """The tuner only changes launch shapes: the same phi bits (the fixed-point
+    outer loop is exact), the residual history up to its summation order (each
+    thread of the outer step sums at most 64 squares in FP32 before the FP64
+    block sum, so a relative 64 * 2^-24 bounds the change), and a second
+    context of the same shape takes the same shapes."""
+    rho, fpg = source(n, bc, seed=21)
+    rd = torch.from_numpy(rho).cuda()
+    with mg.Solver(n, 1.0 / n, bc, prec=mg.MIXED) as s:
+        p0, h0, st0 = s.solve(rd, fpg, 1e-10)
+        s.autotune()
+        cfg = s.tile_configs()
+        p1, h1, st1 = s.solve(rd, fpg, 1e-10)
+    assert st0 == st1 == 0
+    fused_levels = [l for l in range(n.bit_length()) if (n >> (n.bit_length() - 1 - l)) >= 32]
+    assert sorted(cfg["fused_down"]) == sorted(cfg["fused_up"]) == fused_levels
+    for l, (tx, cz) in list(cfg["fused_down"].items()) + list(cfg["fused_up"].items()):
+        width = n >> (n.bit_length() - 1 - l)
+        assert tx in (32, 64) and width % tx == 0 and cz in (8, 16, 32, 64) and cz <= width
+    assert list(cfg["outer_residual"]) == [n.bit_length() - 1]
+    assert cfg["outer_residual"][n.bit_length() - 1][1] in (4, 8, 16, 32, 64)
+    assert torch.equal(p0, p1)
+    assert len(h0) == len(h1) and np.allclose(h0, h1, rtol=64 * 2.0 ** -24, atol=0)
+    with mg.Solver(n, 1.0 / n, bc, prec=mg.MIXED) as s2:
+        s2.autotune()
+        assert s2.tile_configs() == cfg
