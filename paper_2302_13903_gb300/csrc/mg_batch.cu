@@ -191,6 +191,8 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
   const int bc = g.bc;
   const double sc = TYPE == PH_R0 ? 1.0 / g.fnorm : 1.0 / g.rn;
   double acc = 0.0;
+  // unrolled so that each thread has several independent loads in flight
+#pragma unroll 4
   for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) {
     if (TYPE == PH_SRC) {
       const double v = fpg * rho[t];
