@@ -74,19 +74,97 @@ __global__ void k_finish_max(const double* __restrict__ partials, int nb, double
   if (threadIdx.x == 0) out[0] = m;
 }
 
-// In place: the double a[t] becomes the integer round(a[t] * c).
-__global__ void k_f64_to_fx(double* a, long long n, double c) {
+// In place: the double a[t] becomes the integer round((a[t] - mu) * c).
+__global__ void k_f64_to_fx(double* a, long long n, double mu, double c) {
   long long* q = reinterpret_cast<long long*>(a);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    q[t] = __double2ll_rn(a[t] * c);
+    q[t] = __double2ll_rn((a[t] - mu) * c);
 }
 
-// out[t] = q[t] * c as a double (out may alias q).
-__global__ void k_fx_to_f64(const long long* q, double* out, long long n, double c) {
+// out[t] = q[t] * c - m as a double (out may alias q), with m = total[0] * cm
+// when total is given (the mean of the integers, from their device sum).
+__global__ void k_fx_to_f64(const long long* q, double* out, long long n, double c,
+                            const double* __restrict__ total, double cm) {
+  const double m = total ? total[0] * cm : 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    out[t] = __ll2double_rn(q[t]) * c;
+    out[t] = __ll2double_rn(q[t]) * c - m;
+}
+
+// |x| as an unsigned integer: for non-negative doubles (and floats) the order
+// of the bit patterns is the order of the values, so maxima need no FP64 work.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+
+// Per-block partial sums of rho (sum[]) and maxima of |rho| (mx[], as the
+// double whose bits are the largest |rho| pattern); two cells per step.
+__global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
+                            double* __restrict__ sum, double* __restrict__ mx) {
+  double acc = 0.0;
+  unsigned long long m = 0;
+#pragma unroll 4
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double2 r = rho[t];
+    acc += r.x + r.y;
+    const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
+    m = a > m ? a : m;
+    m = b > m ? b : m;
+  }
+  const double bs = block_reduce<false>(acc);
+  const double bm = block_reduce<true>(__longlong_as_double((long long)m));
+  if (threadIdx.x == 0) {
+    sum[blockIdx.x] = bs;
+    mx[blockIdx.x] = bm;
+  }
+}
+
+// r32 = (a rho - b) rounded to FP32 (a = 4 pi G scale, b = mean scale);
+// per-block partial sums of r32^2 (FP32 per thread) and maxima of |r32|.
+__global__ void k_rho_to_r32(const double2* __restrict__ rho, float2* __restrict__ r32,
+                             long long n2, double a, double b, double* __restrict__ sum,
+                             double* __restrict__ mx) {
+  float acc = 0.f, m = 0.f;
+#pragma unroll 4
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double2 r = rho[t];
+    const float x = (float)fma(a, r.x, -b), y = (float)fma(a, r.y, -b);
+    r32[t] = make_float2(x, y);
+    acc = fmaf(x, x, fmaf(y, y, acc));
+    m = fmaxf(m, fmaxf(fabsf(x), fabsf(y)));
+  }
+  const double bs = block_reduce<false>((double)acc);
+  const double bm = block_reduce<true>((double)m);
+  if (threadIdx.x == 0) {
+    sum[blockIdx.x] = bs;
+    mx[blockIdx.x] = bm;
+  }
+}
+
+// In place into the integer array q: round(a rho - b) (the fixed-point h^2 f).
+__global__ void k_rho_to_fx(const double* __restrict__ rho, long long* __restrict__ q, long long n,
+                            double a, double b) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    q[t] = __double2ll_rn(fma(a, rho[t], -b));
+}
+
+__global__ void k_finish_sum_max(const double* __restrict__ sum, const double* __restrict__ mx,
+                                 int nb, double* __restrict__ out) {
+  double a = 0.0, m = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    a += sum[t];
+    m = fmax(m, mx[t]);
+  }
+  a = block_reduce<false>(a);
+  m = block_reduce<true>(m);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = m;
+  }
 }
 
 // PHI += round(e * c) (the FP32 correction on the fixed-point grid); flags a
@@ -111,13 +189,19 @@ struct FxBc {
 };
 
 // One outer step on the integer grid, fused and z-marching:
-//   PHI' = PHI_in + round(e * c)          (the pending FP32 correction; e may be null)
+//   PHI' = PHI_in + round(e * c)          (the pending FP32 correction; e may be
+//                                           null; ZERO_IN: PHI_in is all zero)
 //   R    = F - (sum_nb PHI' - 6 PHI')      (exact)
-//   r32  = R * factor, partial sums of r32^2, PHI_out = PHI' (a different buffer:
-//   neighbouring tiles read PHI_in as their halo).
-// A 32 x 16 tile of columns marches through a chunk of planes with a ring of
-// three corrected planes (halo of one cell) in shared memory.
+//   r32  = R * factor, partial sums of r32^2 (and of PHI' when psum is given),
+//   PHI_out = PHI' (a different buffer: neighbouring tiles read PHI_in as
+//   their halo and correct it themselves).
+// A 32 x 16 tile of columns marches up a chunk of planes.  Each thread keeps
+// PHI' of its own column at planes z-1, z, z+1 in registers (the z
+// neighbours); the x / y neighbours come from the current plane in shared
+// memory (double-buffered, one barrier per plane), whose 100 halo cells the
+// first 100 threads load and correct.
 constexpr int FX_TX = 32, FX_TY = 16, FX_W = FX_TX + 2, FX_H = FX_TY + 2;
+constexpr int FX_HALO = 2 * FX_W + 2 * FX_TY;  // 100
 
 __device__ __forceinline__ long long fx_face_ghost(const FxBc& bc, const Grid& g, long long self,
                                                    int i, int j, int k, int axis, int hi) {
@@ -135,82 +219,152 @@ __device__ __forceinline__ long long fx_face_ghost(const FxBc& bc, const Grid& g
   return b2 - self;
 }
 
+// PHI' at flat offset o.
+template <bool ZERO_IN>
+__device__ __forceinline__ long long fx_corrected(const long long* __restrict__ phi_in,
+                                                  const float* __restrict__ e, float c,
+                                                  size_t o) {
+  long long v = ZERO_IN ? 0 : phi_in[o];
+  if (e) v += __float2ll_rn(e[o] * c);
+  return v;
+}
+
+template <bool PER, bool ZERO_IN>
 __global__ void __launch_bounds__(FX_TX* FX_TY)
     k_fx_step(const long long* __restrict__ phi_in, long long* __restrict__ phi_out,
               const float* __restrict__ e, float c, const long long* __restrict__ F,
               float* __restrict__ r32, Grid g, FxBc bc, float factor, int cz,
-              double* __restrict__ partials, int* __restrict__ flag) {
-  __shared__ long long P[3][FX_H][FX_W];
-  const bool per = bc.kind == BC_PERIODIC;
+              double* __restrict__ partials, long long* __restrict__ psum,
+              int* __restrict__ flag) {
+  __shared__ long long P[2][FX_H][FX_W];
   const int tx = threadIdx.x % FX_TX, ty = threadIdx.x / FX_TX;
   const int x0 = blockIdx.x * FX_TX, y0 = blockIdx.y * FX_TY, z0 = blockIdx.z * cz;
   const int z1 = min(z0 + cz, g.nz);
-  const int i = x0 + tx, j = y0 + ty;  // this thread's interior column
+  const int i = x0 + tx, j = y0 + ty;  // this thread's column
   const size_t plane = (size_t)g.nx * g.ny;
+  const size_t col = (size_t)j * g.nx + i;
+  // the halo cell this thread loads (threads < FX_HALO): rows -1 and 16 over
+  // the full width, columns -1 and 32 over the tile's rows
+  int ha = 0, hb = 0;
+  const bool halo = threadIdx.x < FX_HALO;
+  if (halo) {
+    const int h = threadIdx.x;
+    if (h < FX_W) { ha = h; hb = 0; }
+    else if (h < 2 * FX_W) { ha = h - FX_W; hb = FX_H - 1; }
+    else if (h < 2 * FX_W + FX_TY) { ha = 0; hb = h - 2 * FX_W + 1; }
+    else { ha = FX_W - 1; hb = h - 2 * FX_W - FX_TY + 1; }
+  }
+  int hx = x0 - 1 + ha, hy = y0 - 1 + hb;
+  bool h_in = halo;
+  if (PER) {
+    hx = hx < 0 ? hx + g.nx : (hx >= g.nx ? hx - g.nx : hx);
+    hy = hy < 0 ? hy + g.ny : (hy >= g.ny ? hy - g.ny : hy);
+  } else {
+    h_in = h_in && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
+  }
+  const size_t hcol = (size_t)hy * g.nx + hx;
+  auto wrapz = [&](int q) { return q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q); };
+  auto own = [&](int q) -> long long {  // PHI' of this column at plane q (0 outside)
+    if (!PER && (q < 0 || q >= g.nz)) return 0;
+    return fx_corrected<ZERO_IN>(phi_in, e, c, (size_t)(PER ? wrapz(q) : q) * plane + col);
+  };
+  auto halo_at = [&](int q) -> long long {  // PHI' of this thread's halo cell at plane q
+    return h_in ? fx_corrected<ZERO_IN>(phi_in, e, c, (size_t)q * plane + hcol) : 0;
+  };
+  // every load of a plane is issued one plane ahead of its use
+  long long zm = own(z0 - 1), self = own(z0), hcur = halo_at(z0);
   float acc = 0.f;
+  long long sum_hi = 0, sum_lo = 0;  // exact sum of PHI' = hi 2^32 + lo
   bool bad = false;
-  for (int q = z0 - 1; q <= z1; ++q) {
-    const int slot = (q - z0 + 1) % 3;
-    __syncthreads();  // the slot being refilled was read two planes ago
-    const bool q_in = per || (q >= 0 && q < g.nz);
-    const int qw = per ? (q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q)) : q;
-    for (int idx = threadIdx.x; idx < FX_W * FX_H; idx += blockDim.x) {
-      const int a = idx % FX_W, b = idx / FX_W;
-      int gx = x0 - 1 + a, gy = y0 - 1 + b;
-      long long v = 0;
-      bool in = q_in;
-      if (per) {
-        gx = gx < 0 ? gx + g.nx : (gx >= g.nx ? gx - g.nx : gx);
-        gy = gy < 0 ? gy + g.ny : (gy >= g.ny ? gy - g.ny : gy);
-      } else {
-        in = in && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
-      }
-      if (in) {
-        const size_t o = (size_t)qw * plane + (size_t)gy * g.nx + gx;
-        v = phi_in[o];
-        if (e) v += __float2ll_rn(e[o] * c);
-        // the owner of an interior cell of this tile stores it
-        if (a >= 1 && a <= FX_TX && b >= 1 && b <= FX_TY && q >= z0 && q < z1) {
-          phi_out[o] = v;
-          bad |= (v > (1LL << 60)) || (v < -(1LL << 60));
-        }
-      }
-      P[slot][b][a] = v;
-    }
+  for (int z = z0; z < z1; ++z) {
+    const size_t o = (size_t)z * plane + col;
+    const long long Fo = F[o];
+    const long long zp = own(z + 1);
+    const long long hnext = z + 1 < z1 ? halo_at(z + 1) : 0;
+    const int buf = (z - z0) & 1;
+    P[buf][ty + 1][tx + 1] = self;
+    if (halo) P[buf][hb][ha] = hcur;
+    phi_out[o] = self;
+    sum_hi += self >> 32;
+    sum_lo += self & 0xffffffffLL;
+    bad |= (self > (1LL << 60)) || (self < -(1LL << 60));
     __syncthreads();
-    const int pz = q - 1;  // residual of the plane below, now that q is in
-    if (pz >= z0 && pz < z1) {
-      const int sm = (slot + 1) % 3, s0 = (slot + 2) % 3;  // planes pz-1, pz
-      const long long self = P[s0][ty + 1][tx + 1];
-      long long xm = P[s0][ty + 1][tx], xp = P[s0][ty + 1][tx + 2];
-      long long ym = P[s0][ty][tx + 1], yp = P[s0][ty + 2][tx + 1];
-      long long zm = P[sm][ty + 1][tx + 1], zp = P[slot][ty + 1][tx + 1];
-      if (!per) {
-        if (i == 0) xm = fx_face_ghost(bc, g, self, i, j, pz, 0, 0);
-        if (i == g.nx - 1) xp = fx_face_ghost(bc, g, self, i, j, pz, 0, 1);
-        if (j == 0) ym = fx_face_ghost(bc, g, self, i, j, pz, 1, 0);
-        if (j == g.ny - 1) yp = fx_face_ghost(bc, g, self, i, j, pz, 1, 1);
-        if (pz == 0) zm = fx_face_ghost(bc, g, self, i, j, pz, 2, 0);
-        if (pz == g.nz - 1) zp = fx_face_ghost(bc, g, self, i, j, pz, 2, 1);
-      }
-      const size_t o = (size_t)pz * plane + (size_t)j * g.nx + i;
-      const long long R = F[o] - (((xm + xp) + (ym + yp)) + (zm + zp) - 6 * self);
-      const float r = __ll2float_rn(R) * factor;
-      r32[o] = r;
-      acc = fmaf(r, r, acc);
+    long long xm = P[buf][ty + 1][tx], xp = P[buf][ty + 1][tx + 2];
+    long long ym = P[buf][ty][tx + 1], yp = P[buf][ty + 2][tx + 1];
+    long long zmv = zm, zpv = zp;
+    if (!PER) {
+      if (i == 0) xm = fx_face_ghost(bc, g, self, i, j, z, 0, 0);
+      if (i == g.nx - 1) xp = fx_face_ghost(bc, g, self, i, j, z, 0, 1);
+      if (j == 0) ym = fx_face_ghost(bc, g, self, i, j, z, 1, 0);
+      if (j == g.ny - 1) yp = fx_face_ghost(bc, g, self, i, j, z, 1, 1);
+      if (z == 0) zmv = fx_face_ghost(bc, g, self, i, j, z, 2, 0);
+      if (z == g.nz - 1) zpv = fx_face_ghost(bc, g, self, i, j, z, 2, 1);
     }
+    const long long R = Fo - (((xm + xp) + (ym + yp)) + (zmv + zpv) - 6 * self);
+    const float r = __ll2float_rn(R) * factor;
+    r32[o] = r;
+    acc = fmaf(r, r, acc);
+    zm = self;
+    self = zp;
+    hcur = hnext;
+    // the next plane writes the other buffer; this one is rewritten two planes
+    // on, after every thread has passed the next barrier
   }
   if (bad) atomicOr(flag, 1);
-  // deterministic block sum, then one partial per block (blocks in launch order)
+  // deterministic block sums, then one partial per block (blocks in launch
+  // order); the sums of PHI' stay exact integers, so their total does not
+  // depend on the blocking
   __shared__ double ws[FX_TX * FX_TY / 32];
-  double v = warp_sum((double)acc);
+  __shared__ long long wh[FX_TX * FX_TY / 32], wl[FX_TX * FX_TY / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) ws[w] = v;
+  const double v = warp_sum((double)acc);
+  if (psum) {
+    for (int o = 16; o > 0; o >>= 1) {
+      sum_hi += __shfl_down_sync(0xffffffffu, sum_hi, o);
+      sum_lo += __shfl_down_sync(0xffffffffu, sum_lo, o);
+    }
+  }
+  if (lane == 0) {
+    ws[w] = v;
+    wh[w] = sum_hi;
+    wl[w] = sum_lo;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < FX_TX * FX_TY / 32; ++q) t += ws[q];
-    partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+    long long th = 0, tl = 0;
+    for (int q = 0; q < FX_TX * FX_TY / 32; ++q) {
+      t += ws[q];
+      th += wh[q];
+      tl += wl[q];
+    }
+    const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    partials[b] = t;
+    if (psum) {
+      psum[2 * b] = th;
+      psum[2 * b + 1] = tl;
+    }
+  }
+}
+
+// out[0] = the total of the (hi, lo) pairs as a double, summed exactly.
+__global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb,
+                                double* __restrict__ out) {
+  __shared__ long long sh[kThreads], sl[kThreads];
+  long long h = 0, l = 0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    h += psum[2 * t];
+    l += psum[2 * t + 1];
+  }
+  sh[threadIdx.x] = h;
+  sl[threadIdx.x] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)blockDim.x; ++q) {
+      h += sh[q];
+      l += sl[q];
+    }
+    out[0] = (double)h * 4294967296.0 + (double)l;
   }
 }
 
@@ -228,16 +382,48 @@ cudaError_t launch_absmax(const T* a, long long n, double* partials, double* out
 template cudaError_t launch_absmax<double>(const double*, long long, double*, double*, cudaStream_t);
 template cudaError_t launch_absmax<float>(const float*, long long, double*, double*, cudaStream_t);
 
-cudaError_t launch_f64_to_fx(double* a, long long n, double c, cudaStream_t s) {
+cudaError_t launch_f64_to_fx(double* a, long long n, double mu, double c, cudaStream_t s) {
   ++g_launches;
-  k_f64_to_fx<<<grid_for(n), kThreads, 0, s>>>(a, n, c);
+  k_f64_to_fx<<<grid_for(n), kThreads, 0, s>>>(a, n, mu, c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, double c,
+                             const double* total, double cm, cudaStream_t s) {
+  ++g_launches;
+  k_fx_to_f64<<<grid_for(n), kThreads, 0, s>>>(q, out, n, c, total, cm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, double* out,
+                             cudaStream_t s) {
+  if (n % 2) return cudaErrorInvalidValue;
+  const int nb = reduce_blocks(n / 2);
+  ++g_launches;
+  k_rho_stats<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(rho), n / 2, partials,
+                                      partials + nb);
+  ++g_launches;
+  k_finish_sum_max<<<1, kThreads, 0, s>>>(partials, partials + nb, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_to_r32(const double* rho, float* r32, long long n, double a, double b,
+                              double* partials, double* out, cudaStream_t s) {
+  if (n % 2) return cudaErrorInvalidValue;
+  const int nb = reduce_blocks(n / 2);
+  ++g_launches;
+  k_rho_to_r32<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(rho),
+                                       reinterpret_cast<float2*>(r32), n / 2, a, b, partials,
+                                       partials + nb);
+  ++g_launches;
+  k_finish_sum_max<<<1, kThreads, 0, s>>>(partials, partials + nb, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_to_fx(const double* rho, long long* q, long long n, double a, double b,
                              cudaStream_t s) {
   ++g_launches;
-  k_fx_to_f64<<<grid_for(n), kThreads, 0, s>>>(q, out, n, c);
+  k_rho_to_fx<<<grid_for(n), kThreads, 0, s>>>(rho, q, n, a, b);
   return cudaGetLastError();
 }
 
@@ -272,7 +458,7 @@ int fx_step_blocks(Grid g, int cz) {
 cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const float* e, float c,
                            const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
                            float factor, double* partials, int nb_max, int* flag, int* nb_out,
-                           cudaStream_t s, int cz_req) {
+                           cudaStream_t s, int cz_req, long long* psum) {
   // The ghost 2 b - phi on the fixed-point grid: 2 b 2^S rounded once.
   FxBc b;
   b.kind = bc.kind;
@@ -286,8 +472,25 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   if (nb > nb_max) return cudaErrorInvalidValue;
   *nb_out = nb;
   ++g_launches;
-  k_fx_step<<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b, factor, cz,
-                                           partials, flag);
+  const bool per = bc.kind == BC_PERIODIC, zero_in = phi_in == nullptr;
+  if (per && zero_in)
+    k_fx_step<true, true><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
+                                                         factor, cz, partials, psum, flag);
+  else if (per)
+    k_fx_step<true, false><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
+                                                          factor, cz, partials, psum, flag);
+  else if (zero_in)
+    k_fx_step<false, true><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
+                                                          factor, cz, partials, psum, flag);
+  else
+    k_fx_step<false, false><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
+                                                           factor, cz, partials, psum, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_fx_sum(const long long* psum, int nb, double* out, cudaStream_t s) {
+  ++g_launches;
+  k_finish_fx_sum<<<1, kThreads, 0, s>>>(psum, nb, out);
   return cudaGetLastError();
 }
 

@@ -149,17 +149,29 @@ cudaError_t launch_fused_smooth(const float* u_in, float* u_out, const float* f,
 // out[0] = max |a| (deterministic two-stage reduction through partials).
 template <typename T>
 cudaError_t launch_absmax(const T* a, long long n, double* partials, double* out, cudaStream_t s);
-// In place: double -> round(a * c) as int64.  out = q * c as doubles (out
-// may alias q).
-cudaError_t launch_f64_to_fx(double* a, long long n, double c, cudaStream_t s);
+// In place: double -> round((a - mu) * c) as int64.  out = q * c - m as
+// doubles (out may alias q), m = total[0] * cm when total is given.
+cudaError_t launch_f64_to_fx(double* a, long long n, double mu, double c, cudaStream_t s);
 cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, double c,
+                             const double* total, double cm, cudaStream_t s);
+// out[0] = sum rho, out[1] = max |rho| (n even; partials holds 2
+// reduce_blocks(n / 2) doubles); reads rho only.
+cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, double* out,
+                             cudaStream_t s);
+// r32 = fl32(a rho - b); out[0] = sum r32^2, out[1] = max |r32|.
+cudaError_t launch_rho_to_r32(const double* rho, float* r32, long long n, double a, double b,
+                              double* partials, double* out, cudaStream_t s);
+// q = round(a rho - b) as int64.
+cudaError_t launch_rho_to_fx(const double* rho, long long* q, long long n, double a, double b,
                              cudaStream_t s);
 // PHI += round(e * c); *flag |= 1 if |PHI| passes 2^60.
 cudaError_t launch_fx_correct(long long* phi, const float* e, long long n, float c, int* flag,
                               cudaStream_t s);
-// Fused outer step: PHI_out = PHI_in + round(e * c) (e may be null), then
-// r32 = (F - (sum_nb PHI_out - 6 PHI_out)) * factor exactly in integers, one
-// partial sum of r32^2 per block (count in *nb_out, at most nb_max).
+// Fused outer step: PHI_out = PHI_in + round(e * c) (e may be null; phi_in
+// null means PHI_in = 0), then r32 = (F - (sum_nb PHI_out - 6 PHI_out)) *
+// factor exactly in integers, one partial sum of r32^2 per block in partials
+// (count in *nb_out, at most nb_max) and, when psum is given, the exact sum of
+// PHI_out per block as a (hi 2^32, lo) pair of integers (2 nb_max entries).
 // Requires nx % 32 == 0 and ny % 16 == 0 (fx_step_ok).
 // cz = 0 takes the built-in planes per CTA; fx_step_blocks(g, 0) bounds the
 // block count of every cz >= kFxMinCz.
@@ -170,7 +182,9 @@ int fx_step_blocks(Grid g, int cz);
 cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const float* e, float c,
                            const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
                            float factor, double* partials, int nb_max, int* flag, int* nb_out,
-                           cudaStream_t s, int cz = 0);
+                           cudaStream_t s, int cz = 0, long long* psum = nullptr);
+// out[0] = sum over nb blocks of the pairs launch_fx_step wrote, as a double.
+cudaError_t launch_finish_fx_sum(const long long* psum, int nb, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Multipole boundary (App. A).

@@ -150,7 +150,8 @@ void alloc_hierarchy(mg_ctx* c) {
     const int nb = mg::fx_step_blocks(level_grid(c, F), 0);
     if (nb > c->partials_cap) c->partials_cap = nb;
   }
-  c->partials = dalloc<double>(c, c->partials_cap);
+  // partials, then room for two integers per block of the fixed-point step
+  c->partials = dalloc<double>(c, 3 * (size_t)c->partials_cap);
   c->scal = dalloc<double>(c, 64);
   c->iflag = dalloc<int>(c, 4);
 }
@@ -502,40 +503,80 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   const long long N = g.cells();
   const int nb = mg::reduce_blocks(N);
   double* f = c->f64[F];
-  double fnorm = prepare_source(c, rho, four_pi_G, f, false, s);
   const Bc bc = physical_bc(c, F);
   const Bc hom = mg::homogeneous(bc);
-  if (c->opts.mode_fmg) check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
-  // r = f - L phi, scaled into FP32 so that its RMS is about 1.  From phi = 0
-  // with a rule whose boundary values are 0, L phi = 0 and r = f exactly.
-  double scale = fnorm > 0.0 ? 1.0 / fnorm : 1.0;
+  const bool fx = c->opts.outer_fixed != 0 && c->fxbuf != nullptr;
+  const bool has_mean = c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD;
   const bool zero_values = bc.kind == mg::BC_PERIODIC || bc.kind == mg::BC_ZEROGRAD ||
                            (bc.kind == mg::BC_FIXED && bc.value == 0.0);
-  double rn;
-  if (c->opts.mode_fmg && zero_values) {
-    check(c, mg::launch_scale_to_f32(f, c->f32[F], N, scale, s), "r = f");
+  // From phi = 0 with a rule whose boundary values are 0, L phi = 0 and the
+  // first residual is f itself.  On that path (with the fixed-point outer
+  // loop) f is never stored as doubles: one pass over rho gives its sum (the
+  // mean of f) and maximum, a second writes r32 = (4 pi G rho - mean) * scale
+  // with its norm and maximum, and the integer h^2 f is formed from rho when
+  // the scale 2^S is known.  Few FP64 operations per cell: on this GPU they,
+  // not the bytes, would bound these passes.
+  const bool fast = fx && c->opts.mode_fmg && zero_values;
+  double mu = 0.0;     // mean of f (fast path: not subtracted in memory)
+  double mf = -1.0;    // max |f - mean| when known
+  double fnorm, scale, rn;
+  if (fast) {
+    {
+      KTimer t(c, MG_K_SOURCE, true, s);
+      check(c, mg::launch_rho_stats(rho, N, c->partials, c->scal + 0, s), "source stats");
+    }
+    check(c, cudaMemcpyAsync(c->pinned, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
+          "read source stats");
+    check(c, cudaStreamSynchronize(s), "sync");
+    mu = has_mean ? four_pi_G * (c->pinned[0] / (double)N) : 0.0;
+    const double bound = std::fabs(four_pi_G) * c->pinned[1] + std::fabs(mu);  // >= max|f - mean|
+    scale = bound > 0.0 ? 1.0 / bound : 1.0;
+    check(c, mg::launch_rho_to_r32(rho, c->f32[F], N, four_pi_G * scale, mu * scale, c->partials,
+                                   c->scal + 0, s),
+          "r = f - mean");
+    check(c, cudaMemcpyAsync(c->pinned, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
+          "read norm");
+    check(c, cudaStreamSynchronize(s), "sync");
+    fnorm = std::sqrt(c->pinned[0] / (double)N) / scale;
+    mf = c->pinned[1] / scale;
     rn = fnorm;
+    if (fnorm == 0.0) {
+      fnorm = 1.0;
+      check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
+    }
   } else {
-    check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
-          "outer residual");
-    check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
-    rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
-  }
-  if (fnorm == 0.0) {
-    fnorm = rn > 0.0 ? rn : 1.0;
-    scale = 1.0 / fnorm;
-    if (rn > 0.0) {
+    fnorm = prepare_source(c, rho, four_pi_G, f, false, s);
+    if (c->opts.mode_fmg) check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
+    // r = f - L phi, scaled into FP32 so that its RMS is about 1.
+    scale = fnorm > 0.0 ? 1.0 / fnorm : 1.0;
+    if (c->opts.mode_fmg && zero_values) {
+      check(c, mg::launch_scale_to_f32(f, c->f32[F], N, scale, s), "r = f");
+      rn = fnorm;
+    } else {
       check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
             "outer residual");
+      check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 1, s), "finish r^2");
+      rn = std::sqrt(read_scalar(c, 1, s) / (double)N);
+    }
+    if (fnorm == 0.0) {
+      fnorm = rn > 0.0 ? rn : 1.0;
+      scale = 1.0 / fnorm;
+      if (rn > 0.0) {
+        check(c, mg::launch_outer_residual(phi, f, c->f32[F], g, c->h, bc, scale, c->partials, s),
+              "outer residual");
+      }
     }
   }
   StopRule rule{tol, c->opts.stall_ratio};
   int n = 0, st = -1;
-  const bool fx = c->opts.outer_fixed != 0 && c->fxbuf != nullptr;
   double two_S = 1.0;  // 2^S of the fixed-point representation
   bool in_fx = false;  // phi and f hold integers
+  bool phi_zero = false;  // the integer phi is all zero (FMG start): not read
   long long* cur = reinterpret_cast<long long*>(phi);  // integer phi (in phi's own storage)
   long long* alt = c->fxbuf;
+  // per-block exact sums of the integer phi, (hi, lo) pairs
+  long long* psum = reinterpret_cast<long long*>(c->partials + c->partials_cap);
+  int nbs = 0;
   const long long* FX = reinterpret_cast<const long long*>(f);
   for (int it = 0;; ++it) {
     if (rn == 0.0) {  // exact already (zero source with a homogeneous rule)
@@ -561,8 +602,10 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
         // S such that |phi| < 2^55 and |h^2 f| < 2^58 on the integer grid;
         // phi after this step is at most max|phi_0| + max|e| / scale.
         check(c, mg::launch_absmax<float>(c->u32[F], N, c->partials, c->scal + 50, s), "max |e|");
-        check(c, mg::launch_absmax<double>(f, N, c->partials, c->scal + 51, s), "max |f|");
-        if (!c->opts.mode_fmg)
+        if (mf < 0.0)
+          check(c, mg::launch_absmax<double>(f, N, c->partials, c->scal + 51, s), "max |f|");
+        phi_zero = c->opts.mode_fmg != 0;
+        if (!phi_zero)
           check(c, mg::launch_absmax<double>(phi, N, c->partials, c->scal + 52, s), "max |phi|");
         else
           check(c, cudaMemsetAsync(c->scal + 52, 0, sizeof(double), s), "zero");
@@ -572,28 +615,35 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
         check(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), s), "clear flag");
         check(c, cudaStreamSynchronize(s), "sync");
         const double mphi = c->pinned[52] + c->pinned[50] / old_scale;
-        const double mf = c->pinned[51] * c->h * c->h;
+        const double mfh = (mf >= 0.0 ? mf : c->pinned[51]) * c->h * c->h;
         double lim = 0.0;
         if (mphi > 0.0) lim = std::ldexp(1.0, 55) / mphi;
-        if (mf > 0.0 && (lim == 0.0 || std::ldexp(1.0, 58) / mf < lim))
-          lim = std::ldexp(1.0, 58) / mf;
+        if (mfh > 0.0 && (lim == 0.0 || std::ldexp(1.0, 58) / mfh < lim))
+          lim = std::ldexp(1.0, 58) / mfh;
         if (lim == 0.0) lim = std::ldexp(1.0, 55);
         int e2 = 0;
         std::frexp(lim, &e2);
         two_S = std::ldexp(1.0, e2 - 1);  // largest power of two <= lim
-        check(c, mg::launch_f64_to_fx(f, N, c->h * c->h * two_S, s), "h^2 f -> fixed point");
-        check(c, mg::launch_f64_to_fx(phi, N, two_S, s), "phi -> fixed point");
+        const double c2 = c->h * c->h * two_S;
+        if (fast)
+          check(c, mg::launch_rho_to_fx(rho, reinterpret_cast<long long*>(f), N, four_pi_G * c2,
+                                        mu * c2, s),
+                "h^2 f -> fixed point");
+        else
+          check(c, mg::launch_f64_to_fx(f, N, 0.0, c2, s), "h^2 f -> fixed point");
+        if (!phi_zero) check(c, mg::launch_f64_to_fx(phi, N, 0.0, two_S, s), "phi -> fixed point");
         in_fx = true;
       }
-      int nbs = 0;
       {
         KTimer t(c, MG_K_OUTER_RESIDUAL, true, s);
-        check(c, mg::launch_fx_step(cur, alt, c->u32[F], (float)(two_S / old_scale), FX,
-                                    c->f32[F], g, bc, two_S,
+        check(c, mg::launch_fx_step(phi_zero ? nullptr : cur, alt, c->u32[F],
+                                    (float)(two_S / old_scale), FX, c->f32[F], g, bc, two_S,
                                     (float)(scale / (c->h * c->h * two_S)), c->partials,
-                                    c->partials_cap, c->iflag, &nbs, s, c->fx_cz),
+                                    c->partials_cap, c->iflag, &nbs, s, c->fx_cz,
+                                    has_mean ? psum : nullptr),
               "fixed-point step");
       }
+      phi_zero = false;
       std::swap(cur, alt);
       check(c, mg::launch_finish_sum(c->partials, nbs, c->scal + 1, s), "finish r^2");
       rn = std::sqrt(read_scalar(c, 1, s) / (double)N) / scale;
@@ -605,7 +655,15 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
     if (st >= 0) break;
   }
   if (in_fx) {
-    check(c, mg::launch_fx_to_f64(cur, phi, N, 1.0 / two_S, s), "fixed point -> phi");
+    // phi = PHI 2^-S, less its mean (periodic / zero gradient) from the last
+    // step's integer sums
+    const double* total = nullptr;
+    if (has_mean) {
+      check(c, mg::launch_finish_fx_sum(psum, nbs, c->scal + 56, s), "finish sum phi");
+      total = c->scal + 56;
+    }
+    check(c, mg::launch_fx_to_f64(cur, phi, N, 1.0 / two_S, total, 1.0 / (two_S * (double)N), s),
+          "fixed point -> phi");
     int flag = 0;
     check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s),
           "read flag");
@@ -615,8 +673,9 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       c->err = "fixed-point outer loop: |phi| passed 2^60 (the solve diverged)";
       st = MG_ERR_DIVERGED;
     }
+  } else {
+    remove_mean(c, phi, s);
   }
-  remove_mean(c, phi, s);
   *n_hist = n;
   return (mg_status)st;
 }
@@ -681,24 +740,30 @@ void tune_store_locked(const TuneKey& k, mg::TileCfg v) {
   std::fclose(fp);
 }
 
-// Milliseconds of `reps` launches of `run` after two untimed ones.
+// Milliseconds of `reps` launches of `run` after one untimed one; before each
+// timed launch the L2 cache is flushed by writing `flush` (when given), so
+// that every launch reads its inputs from HBM as inside a solve.
 template <typename Run>
-float time_launches(mg_ctx* c, cudaStream_t s, int reps, Run run) {
-  for (int q = 0; q < 2; ++q) check(c, run(), "autotune launch");
+float time_launches(mg_ctx* c, cudaStream_t s, int reps, void* flush, size_t flush_bytes,
+                    Run run) {
+  check(c, run(), "autotune launch");
   cudaEvent_t a, b;
   check(c, cudaEventCreate(&a), "cudaEventCreate");
   check(c, cudaEventCreate(&b), "cudaEventCreate");
-  check(c, cudaEventRecord(a, s), "record");
-  cudaError_t e = cudaSuccess;
-  for (int q = 0; q < reps && e == cudaSuccess; ++q) e = run();
-  check(c, e, "autotune launch");
-  check(c, cudaEventRecord(b, s), "record");
-  check(c, cudaEventSynchronize(b), "sync");
-  float ms = 0.f;
-  check(c, cudaEventElapsedTime(&ms, a, b), "elapsed");
+  float total = 0.f;
+  for (int q = 0; q < reps; ++q) {
+    if (flush) check(c, cudaMemsetAsync(flush, q & 1, flush_bytes, s), "flush L2");
+    check(c, cudaEventRecord(a, s), "record");
+    check(c, run(), "autotune launch");
+    check(c, cudaEventRecord(b, s), "record");
+    check(c, cudaEventSynchronize(b), "sync");
+    float ms = 0.f;
+    check(c, cudaEventElapsedTime(&ms, a, b), "elapsed");
+    total += ms;
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  return ms;
+  return total;
 }
 
 void autotune(mg_ctx* c, cudaStream_t s) {
@@ -711,6 +776,20 @@ void autotune(mg_ctx* c, cudaStream_t s) {
   const int reps = 5;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load_locked();
+  // a buffer twice the L2 size to flush it between timed launches (skipped
+  // if it cannot be had)
+  const size_t flush_bytes = 2 * (size_t)prop.l2CacheSize;
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
+  struct FreeFlush {
+    void* p;
+    ~FreeFlush() {
+      if (p) cudaFree(p);
+    }
+  } free_flush{flush};
   if (c->opts.prec == MG_MIXED) {
     for (int l = 1; l <= F; ++l) {
       const Grid g = level_grid(c, l);
@@ -735,7 +814,7 @@ void autotune(mg_ctx* c, cudaStream_t s) {
             for (int cz : {8, 16, 32, 64}) {
               const mg::TileCfg cand{tx, cz};
               if (cz > g.nz || !mg::fused_cfg_ok(g, cand)) continue;
-              const float ms = time_launches(c, s, reps, [&]() {
+              const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
                 if (kind == TUNE_DOWN)
                   return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g,
                                                h, hom, om, false, s, cand);
@@ -774,7 +853,7 @@ void autotune(mg_ctx* c, cudaStream_t s) {
       for (int cz : {4, 8, 16, 32, 64}) {
         if (cz > g.nz) continue;
         int nb = 0;
-        const float ms = time_launches(c, s, reps, [&]() {
+        const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
           return mg::launch_fx_step(q, c->fxbuf, c->u32[F], 1.f, q, c->f32[F], g, hom, 1.0, 1.f,
                                     c->partials, c->partials_cap, c->iflag, &nb, s, cz);
         });
