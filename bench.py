@@ -190,6 +190,42 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_open_sphere(args, stream):
+    """256^3 uniform sphere (R = 0.25, 10^3 sub-cells) on [-0.5, 0.5]^3 with open
+    boundaries (multipoles to l = 4 about the centre of mass), 4 pi G = 4 pi, to
+    1e-10 in FP64 and in mixed precision; error against the analytic potential."""
+    import numpy as np
+    import torch
+
+    import paper_2302_13903_gb300 as mg
+    from paper_2302_13903_gb300 import inputs
+    n = 256
+    rho_h = inputs.uniform_sphere(n, 0.25, 10)
+    exact = inputs.sphere_potential(n, 0.25, G=1.0)
+    rho = torch.from_numpy(rho_h).cuda()
+    phi = torch.zeros_like(rho)
+    out = {"workload": "256^3 uniform sphere R = 0.25 (cell-averaged, 10^3 sub-cells), open "
+                       "boundaries from multipoles to l = 4, 4 pi G = 4 pi, tol 1e-10"}
+    for name, prec in (("fp64", mg.FP64), ("mixed", mg.MIXED)):
+        with mg.Solver(n, 1.0 / n, mg.OPEN, prec=prec, lmax=4) as s:
+            for _ in range(2):
+                _, hist, st = s.solve(rho, 4 * math.pi, TOL, phi=phi, stream=stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.open_steps):
+                _, hist, st = s.solve(rho, 4 * math.pi, TOL, phi=phi, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / args.open_steps
+        p = phi.cpu().numpy()
+        out[name] = {"ms_per_solve": ms, "value": n ** 3 / (ms * 1e-3), "unit": UNIT,
+                     "status": st, "residual_checks": len(hist), "final_ratio": float(hist[-1]),
+                     "max_rel_error_vs_analytic": float(np.abs(p - exact).max() /
+                                                        np.abs(exact).max())}
+    return out
+
+
 def run_batched(args, ws, rank, stream):
     """512 grids of {16,32,64,128}^3 (Zipf weights), mixed rules, one persistent
     graph-captured launch per solve; under torchrun each rank takes its LPT share."""
@@ -266,6 +302,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3, help="timed batched solves (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of arrivals per serving rate (0: skip)")
+    ap.add_argument("--open-steps", type=int, default=3,
+                    help="timed solves of the 256^3 open-boundary sphere per precision (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -385,6 +423,7 @@ def main():
     else:
         solver.close()
 
+    open_sphere = run_open_sphere(args, stream) if args.open_steps > 0 else None
     batched = run_batched(args, ws, rank, stream) if args.batch_steps > 0 else None
     serving = run_serving(args) if args.serve_seconds > 0 and ws == 1 else None
 
@@ -417,6 +456,7 @@ def main():
             "final_ratio": float(hist[-1]),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items() if v[1]},
             "fp64_path": fp64,
+            "open_sphere": open_sphere,
             "batched": batched,
             "serving": serving,
         }

@@ -309,9 +309,10 @@ int mg_batch_graph(const mg_batch *batch);
 /* Device time of the last mg_batch_solve by phase kind, in milliseconds
  * (from the GPU's global timer at each grid-wide barrier): ms_by_type[k] for
  * k < n_types in the order source, mean, source-2, norm, first residual,
- * first-residual norm, fused down leg, bottom levels, fused up leg,
- * correction, residual, stopping rule, phi sum, phi mean, phi mean
- * removal.  Synchronises the device.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
+ * first-residual norm, fused down leg, bottom levels, fused up leg, max |e|,
+ * fixed-point scale, conversion to fixed point, correction, residual,
+ * stopping rule, phi sum, phi mean, phi conversion and mean removal.
+ * Synchronises the device.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
 mg_status mg_batch_phase_ms(mg_batch *batch, double *ms_by_type, int n_types);
 
 const char *mg_batch_last_error(const mg_batch *batch);

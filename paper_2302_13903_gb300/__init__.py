@@ -469,7 +469,8 @@ class Batch:
         return bool(lib().mg_batch_graph(self.ptr))
 
     PHASES = ["source", "mean", "source2", "norm", "r0", "r0_norm", "down", "bottom", "up",
-              "correct", "residual", "stop_rule", "phi_sum", "phi_mean", "phi_sub"]
+              "max_e", "set_fixed_point", "to_fixed_point", "correct", "residual", "stop_rule",
+              "phi_sum", "phi_mean", "phi_sub"]
 
     def phase_ms(self):
         """{phase kind: device ms} of the last solve."""

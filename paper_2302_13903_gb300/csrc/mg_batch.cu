@@ -62,6 +62,10 @@ struct GridDev {
   // state
   double mean, fnorm, rn, scale, prev, d0;
   int stalls, active, status, nh, cycles;
+  // fixed-point outer loop: phi and h^2 f as integers scaled by two_S
+  double maxf, two_S;
+  long long b2;  // FIXED: round(2 b 2^S), the integer ghost offset
+  int in_fx, fxbad;
 };
 
 enum PhaseType : int {
@@ -74,12 +78,15 @@ enum PhaseType : int {
   PH_DOWN,         // tile: fused down leg on level size `n`
   PH_BOTTOM,       // grid: levels <= 32^3 of one V-cycle
   PH_UP,           // tile: fused up leg on level size `n`
-  PH_CORR,         // chunk: phi += e / scale
-  PH_RESID,        // chunk: FP64 residual -> r32, partial sum r^2
+  PH_EMAX,         // chunk: max |e| (first outer iteration)
+  PH_SETFX,        // grid: the fixed-point scale 2^S
+  PH_TOFX,         // chunk: F = round(h^2 f 2^S), PHI = round(e 2^S / scale)
+  PH_FXCORR,       // chunk: PHI += round(e 2^S / scale)
+  PH_FXRES,        // chunk: exact integer residual -> r32, partial sum r32^2
   PH_FIN,          // grid: stopping rule, history
-  PH_PSUM,         // chunk: partial sum phi
+  PH_PSUM,         // chunk: partial sum phi (exact integer sum in fixed point)
   PH_PMEAN,        // grid: mean of phi
-  PH_PSUB          // chunk: phi -= mean
+  PH_PSUB          // chunk: phi = PHI 2^-S - mean (fixed point) or phi -= mean
 };
 
 struct Phase {
@@ -99,6 +106,8 @@ struct Ctl {
   const Item* items;
   GridDev* grids;
   double* part;        // one slot per chunk
+  double* part2;       // a second slot per chunk (maxima)
+  long long* ipart;    // two integer slots per chunk (exact sums of PHI: hi, lo)
   double* hist;        // [ngrids][hist_cap]
   unsigned* counters;  // one per phase
   unsigned* bar_count;
@@ -171,26 +180,71 @@ __device__ double block_sum(double v) {
   return r;
 }
 
+__device__ double block_max(double v) {
+  __shared__ double wm[kThreads];
+  wm[threadIdx.x] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)blockDim.x; ++q) r = fmax(r, wm[q]);
+  __syncthreads();
+  return r;
+}
+
+__device__ long long block_isum(long long v) {
+  __shared__ long long wi[kThreads];
+  wi[threadIdx.x] = v;
+  __syncthreads();
+  long long r = 0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)blockDim.x; ++q) r += wi[q];
+  __syncthreads();
+  return r;
+}
+
+// Integer neighbour of cell (i, j, k) along one axis on the fixed-point grid:
+// inside the level the cell itself, outside it the rule's ghost (periodic
+// wrap, zero gradient: the cell, fixed b: round(2 b 2^S) - the cell).
+__device__ __forceinline__ long long fx_nb(const long long* __restrict__ q, long long self,
+                                           int inside, long long o_in, long long o_wrap, int bc,
+                                           long long b2) {
+  if (inside) return q[o_in];
+  if (bc == BC_PERIODIC) return q[o_wrap];
+  return bc == BC_ZEROGRAD ? self : b2 - self;
+}
+
 // One chunk of the finest level: cells [c * kChunk, min(N, (c + 1) kChunk)).
 // The grid's fields are read once into registers (the loop's stores could
 // otherwise alias them).
 template <int TYPE>
 __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
-  const int n = g.n;
+  const int n = g.n, lg = g.L - 1;  // n = 2^lg
   const Grid gr{n, n, n};
   const int N = n * n * n;  // <= 1024^3 = 2^30
   const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
   const int F = g.L - 1;
   double* __restrict__ phi = g.phi;
   double* __restrict__ f64 = g.f64;
+  long long* __restrict__ PHI = reinterpret_cast<long long*>(g.phi);
+  long long* __restrict__ FX = reinterpret_cast<long long*>(g.f64);
   const double* __restrict__ rho = g.rho;
   float* __restrict__ r32 = g.f32[F];
   const float* __restrict__ e32 = g.u32[F];
-  const double fpg = g.fpg, mean = g.mean, inv_scale = 1.0 / g.scale, h = g.h;
+  const double fpg = g.fpg, mean = g.mean, h = g.h;
   const double inv_h2 = 1.0 / (h * h), bcval = g.bcval;
   const int bc = g.bc;
-  const double sc = TYPE == PH_R0 ? 1.0 / g.fnorm : 1.0 / g.rn;
-  double acc = 0.0;
+  const bool fx = g.in_fx != 0;
+  const double two_S = g.two_S;
+  const float ce = (float)(two_S / g.scale);  // e -> integer correction
+  const long long b2 = g.b2;
+  const double inv_fn = 1.0 / g.fnorm;
+  // r32 = r / rn_previous, r = R 2^-S / h^2
+  const float rfac = (float)(1.0 / (g.rn * h * h * two_S));
+  double acc = 0.0, mx = 0.0;
+  float af = 0.f;  // FP32 sum of r32^2 over at most 8 cells, then added to acc
+  int nf = 0;
+  long long s_hi = 0, s_lo = 0;
+  bool bad = false;
   // unrolled so that each thread has several independent loads in flight
 #pragma unroll 4
   for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) {
@@ -202,35 +256,103 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
       const double v = f64[t] - mean;
       f64[t] = v;
       acc += v * v;
-    } else if (TYPE == PH_CORR) {
-      phi[t] += (double)e32[t] * inv_scale;
-    } else if (TYPE == PH_PSUM) {
-      acc += phi[t];
-    } else if (TYPE == PH_PSUB) {
-      phi[t] -= mean;
-    } else {  // PH_R0 (phi = 0) and PH_RESID
-      const int i = t % n, r = t / n;
-      const int j = r % n, k = r / n;
-      double d;
-      if (TYPE == PH_R0) {
-        phi[t] = 0.0;
-        // L_h(0) is nonzero only through the fixed value's ghosts (2 b each)
-        int faces = 0;
-        if (bc == BC_FIXED)
-          faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
-        d = f64[t] - (faces * 2.0 * bcval) * inv_h2;
-      } else {
-        const double s = dev::neighbour_sum(phi, i, j, k, gr, Bc{bc, bcval, nullptr});
-        d = f64[t] - (s - 6.0 * phi[t]) * inv_h2;
-      }
-      r32[t] = (float)(d * sc);
+      mx = fmax(mx, fabs(v));
+    } else if (TYPE == PH_R0) {
+      const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
+      phi[t] = 0.0;
+      // L_h(0) is nonzero only through the fixed value's ghosts (2 b each)
+      int faces = 0;
+      if (bc == BC_FIXED)
+        faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
+      const double d = f64[t] - (faces * 2.0 * bcval) * inv_h2;
+      r32[t] = (float)(d * inv_fn);
       acc += d * d;
+    } else if (TYPE == PH_EMAX) {
+      mx = fmax(mx, (double)fabsf(e32[t]));
+    } else if (TYPE == PH_TOFX) {
+      FX[t] = __double2ll_rn(f64[t] * (h * h * two_S));
+      const long long v = __float2ll_rn(e32[t] * ce);
+      PHI[t] = v;
+      bad |= (v > (1LL << 60)) || (v < -(1LL << 60));
+    } else if (TYPE == PH_FXCORR) {
+      const long long v = PHI[t] + __float2ll_rn(e32[t] * ce);
+      PHI[t] = v;
+      bad |= (v > (1LL << 60)) || (v < -(1LL << 60));
+    } else if (TYPE == PH_FXRES) {
+      const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
+      const long long self = PHI[t];
+      const int sx = 1, sy = n, sz = n * n;
+      const long long xm = fx_nb(PHI, self, i > 0, t - sx, t + (n - 1) * sx, bc, b2);
+      const long long xp = fx_nb(PHI, self, i < n - 1, t + sx, t - (n - 1) * sx, bc, b2);
+      const long long ym = fx_nb(PHI, self, j > 0, t - sy, t + (n - 1) * sy, bc, b2);
+      const long long yp = fx_nb(PHI, self, j < n - 1, t + sy, t - (n - 1) * sy, bc, b2);
+      const long long zm = fx_nb(PHI, self, k > 0, t - sz, t + (long long)(n - 1) * sz, bc, b2);
+      const long long zp = fx_nb(PHI, self, k < n - 1, t + sz, t - (long long)(n - 1) * sz, bc, b2);
+      const long long R = FX[t] - (((xm + xp) + (ym + yp)) + (zm + zp) - 6 * self);
+      const float r = __ll2float_rn(R) * rfac;
+      r32[t] = r;
+      af = fmaf(r, r, af);
+      if (++nf == 8) {
+        acc += af;
+        af = 0.f;
+        nf = 0;
+      }
+    } else if (TYPE == PH_PSUM) {
+      if (fx) {
+        const long long v = PHI[t];
+        s_hi += v >> 32;
+        s_lo += v & 0xffffffffLL;
+      } else {
+        acc += phi[t];
+      }
+    } else if (TYPE == PH_PSUB) {
+      if (fx) phi[t] = (double)PHI[t] * (1.0 / two_S) - mean;
+      else phi[t] -= mean;
     }
   }
-  if (TYPE == PH_SRC || TYPE == PH_SRC2 || TYPE == PH_R0 || TYPE == PH_RESID || TYPE == PH_PSUM) {
+  if (TYPE == PH_FXRES) acc += af;
+  if (TYPE == PH_SRC || TYPE == PH_SRC2 || TYPE == PH_R0 || TYPE == PH_FXRES ||
+      (TYPE == PH_PSUM && !fx)) {
     const double b = block_sum(acc);
     if (threadIdx.x == 0) c.part[g.chunk0 + chunk] = b;
   }
+  if (TYPE == PH_SRC2 || TYPE == PH_EMAX) {
+    const double b = block_max(mx);
+    if (threadIdx.x == 0) c.part2[g.chunk0 + chunk] = b;
+  }
+  if (TYPE == PH_PSUM && fx) {
+    const long long bh = block_isum(s_hi), bl = block_isum(s_lo);
+    if (threadIdx.x == 0) {
+      c.ipart[2 * (g.chunk0 + chunk)] = bh;
+      c.ipart[2 * (g.chunk0 + chunk) + 1] = bl;
+    }
+  }
+  if (TYPE == PH_TOFX || TYPE == PH_FXCORR) {
+    if (bad) atomicOr(&g.fxbad, 1);
+  }
+}
+
+__device__ double chunk_max(const Ctl& c, const GridDev& g) {
+  double m = 0.0;
+  for (int q = 0; q < g.nchunk; ++q) m = fmax(m, c.part2[g.chunk0 + q]);
+  return m;
+}
+
+// The fixed-point scale of one grid after its first inner solve: 2^S the
+// largest power of two keeping |PHI| < 2^55 and |h^2 f 2^S| < 2^58.
+__device__ void setfx_item(const Ctl& c, GridDev& g) {
+  const double mphi = chunk_max(c, g) / g.scale;  // phi = e / scale after this step
+  const double mfh = g.maxf * g.h * g.h;
+  double lim = 0.0;
+  if (mphi > 0.0) lim = 36028797018963968.0 / mphi;                    // 2^55
+  if (mfh > 0.0 && (lim == 0.0 || 288230376151711744.0 / mfh < lim))  // 2^58
+    lim = 288230376151711744.0 / mfh;
+  if (lim == 0.0) lim = 36028797018963968.0;
+  int e2 = 0;
+  frexp(lim, &e2);
+  g.two_S = ldexp(1.0, e2 - 1);
+  g.b2 = g.bc == BC_FIXED ? __double2ll_rn(2.0 * g.bcval * g.two_S) : 0;
+  g.in_fx = 1;
 }
 
 __device__ double chunk_total(const Ctl& c, const GridDev& g) {
@@ -242,8 +364,10 @@ __device__ double chunk_total(const Ctl& c, const GridDev& g) {
 // Stopping rule of the single-grid solve, after one outer iteration.
 __device__ void fin_item(const Ctl& c, GridDev& g, int gi) {
   const double N = (double)g.n * g.n * g.n;
-  const double rn = sqrt(chunk_total(c, g) / N);
-  const double r = rn / g.fnorm;
+  // the residual pass summed the squares of r32 = r / rn_previous
+  const double rn = sqrt(chunk_total(c, g) / N) * g.rn;
+  double r = rn / g.fnorm;
+  if (g.fxbad) r = NAN;  // the integers passed 2^60: the solve diverged
   g.scale = 1.0 / g.rn;  // the scale the residual just written used
   g.rn = rn;
   if (g.nh < c.hist_cap) c.hist[(size_t)gi * c.hist_cap + g.nh] = r;
@@ -311,14 +435,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
       if (it >= P.count) break;
       const Item I = c.items[P.first + it];
       GridDev& g = c.grids[I.grid];
-      const bool run = (P.type >= PH_PSUM) || g.active;
+      const bool has_mean = g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD;
+      const bool run = P.type == PH_PSUM ? has_mean : (P.type > PH_PSUM || g.active);
       if (!run) continue;
       switch (P.type) {
         case PH_SRC: chunk_item<PH_SRC>(c, g, I.a); break;
         case PH_SRC2: chunk_item<PH_SRC2>(c, g, I.a); break;
         case PH_R0: chunk_item<PH_R0>(c, g, I.a); break;
-        case PH_CORR: chunk_item<PH_CORR>(c, g, I.a); break;
-        case PH_RESID: chunk_item<PH_RESID>(c, g, I.a); break;
+        case PH_EMAX: chunk_item<PH_EMAX>(c, g, I.a); break;
+        case PH_TOFX: chunk_item<PH_TOFX>(c, g, I.a); break;
+        case PH_FXCORR: chunk_item<PH_FXCORR>(c, g, I.a); break;
+        case PH_FXRES: chunk_item<PH_FXRES>(c, g, I.a); break;
+        case PH_SETFX:
+          if (threadIdx.x == 0) setfx_item(c, g);
+          break;
         case PH_PSUM: chunk_item<PH_PSUM>(c, g, I.a); break;
         case PH_PSUB: chunk_item<PH_PSUB>(c, g, I.a); break;
         case PH_MEANFIN:
@@ -328,13 +458,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
                          : 0.0;
           break;
         case PH_PMEAN:
-          if (threadIdx.x == 0)
-            g.mean = (g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD)
-                         ? chunk_total(c, g) / ((double)g.n * g.n * g.n)
-                         : 0.0;
+          if (threadIdx.x == 0) {
+            const double N = (double)g.n * g.n * g.n;
+            double m = 0.0;
+            if (g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD) {
+              if (g.in_fx) {  // exact integer total, independent of the chunking
+                long long th = 0, tl = 0;
+                for (int q = 0; q < g.nchunk; ++q) {
+                  th += c.ipart[2 * (g.chunk0 + q)];
+                  tl += c.ipart[2 * (g.chunk0 + q) + 1];
+                }
+                m = ((double)th * 4294967296.0 + (double)tl) / (N * g.two_S);
+              } else {
+                m = chunk_total(c, g) / N;
+              }
+            }
+            g.mean = m;
+          }
           break;
         case PH_NORMFIN:
           if (threadIdx.x == 0) {
+            g.maxf = chunk_max(c, g);
             g.fnorm = sqrt(chunk_total(c, g) / ((double)g.n * g.n * g.n));
             if (g.fnorm == 0.0) g.fnorm = 1.0;  // r = f - L(0) decides below
           }
@@ -427,6 +571,8 @@ struct mg_batch {
   Phase* d_phases = nullptr;
   Item* d_items = nullptr;
   double* d_part = nullptr;
+  double* d_part2 = nullptr;
+  long long* d_ipart = nullptr;
   double* d_hist = nullptr;
   double* h_hist = nullptr;  // pinned
   unsigned* d_counters = nullptr;
@@ -523,8 +669,14 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
       add_grid_phase(PH_BOTTOM, k);
       for (int n = kFusedMinN; n <= nmax; n <<= 1) add_tile_phase(PH_UP, n, k);
     }
-    add_chunk_phase(PH_CORR);
-    add_chunk_phase(PH_RESID);
+    if (o == 0) {
+      add_chunk_phase(PH_EMAX);
+      add_grid_phase(PH_SETFX, 0);
+      add_chunk_phase(PH_TOFX);
+    } else {
+      add_chunk_phase(PH_FXCORR);
+    }
+    add_chunk_phase(PH_FXRES);
     add_grid_phase(PH_FIN, 0);
   }
   add_chunk_phase(PH_PSUM);
@@ -547,6 +699,8 @@ cudaError_t enqueue_solve(mg_batch* b, cudaStream_t s) {
   c.items = b->d_items;
   c.grids = b->d_grids;
   c.part = b->d_part;
+  c.part2 = b->d_part2;
+  c.ipart = b->d_ipart;
   c.hist = b->d_hist;
   c.counters = b->d_counters;
   c.bar_count = b->d_bar;
@@ -651,13 +805,16 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
     b->d_phases = balloc<Phase>(b, phases.size());
     b->d_items = balloc<Item>(b, items.size());
     b->d_part = balloc<double>(b, b->nchunks);
+    b->d_part2 = balloc<double>(b, b->nchunks);
+    b->d_ipart = balloc<long long>(b, 2 * (size_t)b->nchunks);
     b->d_hist = balloc<double>(b, (size_t)n * b->hist_cap);
     b->d_counters = balloc<unsigned>(b, b->nphases);
     b->d_bar = balloc<unsigned>(b, 2);
     b->d_err = balloc<int>(b, 1);
     b->d_active = balloc<int>(b, b->nphases);
     b->d_ptime = balloc<unsigned long long>(b, b->nphases + 1);
-    ok = b->d_grids && b->d_phases && b->d_items && b->d_part && b->d_hist && b->d_counters &&
+    ok = b->d_grids && b->d_phases && b->d_items && b->d_part && b->d_part2 && b->d_ipart &&
+         b->d_hist && b->d_counters &&
          b->d_bar && b->d_err && b->d_active && b->d_ptime;
     b->host_phases = phases;
   }
@@ -720,6 +877,11 @@ mg_status mg_batch_solve(mg_batch* b, const double* const* rho, const double* fo
     d.status = MG_ERR_NOT_CONVERGED;
     d.nh = 0;
     d.cycles = 0;
+    d.maxf = 0.0;
+    d.two_S = 1.0;
+    d.b2 = 0;
+    d.in_fx = 0;
+    d.fxbad = 0;
     b->h_grids[g] = d;
   }
   cudaError_t e = cudaSuccess;

@@ -231,3 +231,24 @@ def test_autotuned_shapes_keep_the_result(bc, n):
     with mg.Solver(n, 1.0 / n, bc, prec=mg.MIXED) as s2:
         s2.autotune()
         assert s2.tile_configs() == cfg
+
+
+@pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
+def test_open_sphere_256_full_size(prec):
+    """The open-boundary workload at full size: a cell-averaged uniform sphere
+    (R = 0.25, 10^3 sub-cells) on [-0.5, 0.5]^3 at 256^3, multipoles to l = 4,
+    4 pi G = 4 pi, solved to 1e-10.  Against the oracle's converged solution
+    (FP64: 1e-11, mixed: 1e-9) and against the analytic potential, whose
+    error falls at second order from 128^3 (Sec. 4.2.1)."""
+    errs = {}
+    for n in (128, 256):
+        rho = inputs.uniform_sphere(n, 0.25, 10)
+        phi, hist, st, _ = gpu_solve(rho, mg.OPEN, 4 * math.pi, 1e-10, prec=prec)
+        assert st == 0 and hist[-1] < 1e-10
+        exact = inputs.sphere_potential(n, 0.25, G=1.0)
+        errs[n] = emax(phi, exact)
+        if n == 256:
+            ref = orc.solve(rho, 1.0 / n, mg.OPEN, four_pi_G=4 * math.pi, tol=0.0, max_cycles=40)
+            assert emax(phi, ref.phi) <= (1e-11 if prec == mg.FP64 else 1e-9)
+    assert errs[256] < 1e-3
+    assert 2.5 < errs[128] / errs[256] < 6.0
