@@ -67,6 +67,8 @@ def lib():
             L.orc_op_coarsest.argtypes = [i, i, i, d, i, d, p, p, p]
             L.orc_op_vcycle.restype = i
             L.orc_op_vcycle.argtypes = [i, i, i, d, i, d, d, i, i, i, p, p]
+            L.orc_op_gravity.argtypes = [i, i, i, d, i, d, p, p, p]
+            L.orc_op_gravity.restype = i
             L.orc_ylm.restype = d
             L.orc_ylm.argtypes = [i, i, d, d, d]
             L.orc_multipole_moments.restype = None
@@ -164,6 +166,16 @@ def prolong(uc, bc=PERIODIC, *, bc_value=0.0, coarse_faces=None, high_order=Fals
                               _ptr(uc), _ptr(out))
     assert st == 0
     return out
+
+
+def gravity(phi, h, bc=PERIODIC, *, bc_value=0.0, faces=None):
+    """Cell-centred acceleration (Sec. 3.2.3): array (3, nz, ny, nx) of g_x, g_y, g_z."""
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    g = np.zeros((3, nz, ny, nx))
+    fa = None if faces is None else _f64(faces)
+    assert lib().orc_op_gravity(nx, ny, nz, h, bc, bc_value, _ptr(fa), _ptr(phi), _ptr(g)) == 0
+    return g
 
 
 def coarsest(f, h, bc=PERIODIC, *, bc_value=0.0, faces=None):

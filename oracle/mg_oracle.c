@@ -6,7 +6,8 @@
  * the operators of Sec. 2.3.1, the coarsest-level solver of Sec. 2.3.2,
  * the V-cycle (Algorithm 1), full multigrid (Algorithm 2), the full
  * approximation scheme (Algorithm 3), the boundary rules of Sec. 2.3.6, the
- * stopping rule of Sec. 2.3.7 and the multipole boundary of App. A.
+ * stopping rule of Sec. 2.3.7, the multipole boundary of App. A and the
+ * cell-centred gravitational acceleration of Sec. 3.2.3.
  *
  * TEST INFRASTRUCTURE ONLY.  This is the correctness oracle for the CUDA
  * library.  It shares no code, header, table or helper with the CUDA path and
@@ -849,6 +850,38 @@ int orc_op_vcycle(int nx, int ny, int nz, double h, int bc_kind, double bc_value
   else multigrid(H.lev, H.nlev - 1, H.bcs, &H.bcs[H.nlev - 1], &hom, &o);
   store(F, F->u, u);
   hier_free(&H);
+  return ORC_OK;
+}
+
+/* Gravitational acceleration at cell centres (Sec. 3.2.3, the cell-centred
+ * source-term scheme): along each axis the two face-centred accelerations
+ * -(phi_{i+1} - phi_i) / h and -(phi_i - phi_{i-1}) / h are averaged; the
+ * neighbours outside the grid are ghosts from the boundary rule.  g holds the
+ * three (nz, ny, nx) arrays g_x, g_y, g_z one after the other. */
+int orc_op_gravity(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
+                   const double *faces, const double *phi, double *g) {
+  OneLevel o;
+  if (one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces) != ORC_OK) { one_free(&o); return ORC_ERR_OOM; }
+  load(&o.L, o.L.u, phi);
+  fill_ghosts(&o.L, o.L.u, &o.bc);
+  const double *u = o.L.u;
+  const size_t N = (size_t)nx * ny * nz;
+  for (int k = 1; k <= nz; ++k)
+    for (int j = 1; j <= ny; ++j)
+      for (int i = 1; i <= nx; ++i) {
+        const double c = u[pidx(nx, ny, i, j, k)];
+        const size_t t = ((size_t)(k - 1) * ny + (j - 1)) * nx + (i - 1);
+        const double xl = -(c - u[pidx(nx, ny, i - 1, j, k)]) / h;
+        const double xr = -(u[pidx(nx, ny, i + 1, j, k)] - c) / h;
+        const double yl = -(c - u[pidx(nx, ny, i, j - 1, k)]) / h;
+        const double yr = -(u[pidx(nx, ny, i, j + 1, k)] - c) / h;
+        const double zl = -(c - u[pidx(nx, ny, i, j, k - 1)]) / h;
+        const double zr = -(u[pidx(nx, ny, i, j, k + 1)] - c) / h;
+        g[t] = 0.5 * (xl + xr);
+        g[N + t] = 0.5 * (yl + yr);
+        g[2 * N + t] = 0.5 * (zl + zr);
+      }
+  one_free(&o);
   return ORC_OK;
 }
 

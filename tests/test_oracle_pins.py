@@ -433,3 +433,86 @@ def test_uniform_sphere_open_boundary_second_order(orc):
         errs.append(np.abs(r.phi - exact).max() / np.abs(exact).max())
     assert errs[0] < 5e-3
     assert 2.5 < errs[0] / errs[1] < 6.0
+
+
+# ---------------------------------------------------------------------------
+# Cell-centred gravitational acceleration (Sec. 3.2.3): the average of the two
+# face accelerations along each axis.
+
+def test_gravity_periodic_sinusoid_closed_form(orc):
+    """For phi = sin 2pi x sin 2pi y sin 2pi z at cell centres the average of the
+    two face differences is the central difference, whose value on a sine is
+    known in closed form: g_x = -(sin(2 pi h) / h) cos 2pi x sin 2pi y sin 2pi z."""
+    n = 16
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    s, c = np.sin(2 * np.pi * x), np.cos(2 * np.pi * x)
+    phi = s[:, None, None] * s[None, :, None] * s[None, None, :]
+    g = orc.gravity(phi, h, PERIODIC)
+    k = np.sin(2 * np.pi * h) / h
+    gx = -k * s[:, None, None] * s[None, :, None] * c[None, None, :]
+    gy = -k * s[:, None, None] * c[None, :, None] * s[None, None, :]
+    gz = -k * c[:, None, None] * s[None, :, None] * s[None, None, :]
+    for got, want in zip(g, (gx, gy, gz)):
+        assert np.abs(got - want).max() <= 1e-13 * k
+
+
+def test_gravity_zero_gradient_cosine_closed_form(orc):
+    """phi = cos(pi x) (x only): the zero-gradient ghost equals the mirrored
+    cosine, so g_x = sin(pi x) sin(pi h) / h holds up to the boundary cells;
+    g_y = g_z = 0."""
+    n = 8
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    phi = np.broadcast_to(np.cos(np.pi * x)[None, None, :], (n, n, n)).copy()
+    g = orc.gravity(phi, h, ZEROGRAD)
+    want = np.sin(np.pi * x) * np.sin(np.pi * h) / h
+    assert np.abs(g[0] - want[None, None, :]).max() <= 1e-13
+    assert np.abs(g[1]).max() == 0.0 and np.abs(g[2]).max() == 0.0
+
+
+def test_gravity_given_faces_linear_potential(orc):
+    """A linear potential with its own values on the faces (ghost = 2 b - cell,
+    applied x, then y, then z) is continued linearly into every ghost, so g is
+    the constant -(a, b, c) in every cell including edges and corners."""
+    n = 4
+    h = 1.0 / n
+    a, b, c, d = 0.7, -1.3, 2.1, 0.4
+    lin = lambda x, y, z: a * x + b * y + c * z + d
+    p = (np.arange(n + 2) - 0.5) * h  # padded index -> coordinate
+    faces = []
+    for face in range(6):
+        axis, hi = divmod(face, 2)
+        wall = 1.0 if hi else 0.0
+        if axis == 0:
+            A, B = np.meshgrid(p, p, indexing="xy")  # (k, j) grid, j fastest
+            vals = lin(wall, A, B)
+        elif axis == 1:
+            A, B = np.meshgrid(p, p, indexing="xy")  # (k, i)
+            vals = lin(A, wall, B)
+        else:
+            A, B = np.meshgrid(p, p, indexing="xy")  # (j, i)
+            vals = lin(A, B, wall)
+        faces.append(vals.ravel())
+    faces = np.concatenate(faces)
+    assert faces.size == orc.faces_size(n, n, n)
+    xc = (np.arange(n) + 0.5) * h
+    phi = lin(xc[None, None, :], xc[None, :, None], xc[:, None, None])
+    g = orc.gravity(phi, h, FACES, faces=faces)
+    for comp, want in zip(g, (-a, -b, -c)):
+        assert np.abs(comp - want).max() <= 1e-12
+
+
+def test_gravity_fixed_rule_boundary_cells(orc):
+    """Fixed value b: the ghost is 2 b - phi, so in the first cell the
+    left face acceleration is -(phi_0 - b) / (h / 2); check one cell by hand."""
+    n = 4
+    h = 1.0 / n
+    rng = np.random.default_rng(3)
+    phi = rng.standard_normal((n, n, n))
+    bval = 0.3
+    g = orc.gravity(phi, h, FIXED, bc_value=bval)
+    k, j = 2, 1
+    ghost = 2 * bval - phi[k, j, 0]
+    want = 0.5 * (-(phi[k, j, 0] - ghost) / h - (phi[k, j, 1] - phi[k, j, 0]) / h)
+    assert abs(g[0, k, j, 0] - want) <= 1e-14 * max(1.0, abs(want))
