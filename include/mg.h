@@ -100,6 +100,17 @@ void mg_opts_init(mg_opts *opts);
 mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts *opts,
                     mg_ctx **ctx);
 
+/* mg_solve, then the gravitational acceleration at cell centres (Sec. 3.2.3):
+ * per axis the average of the two face accelerations -(phi_{i+1} - phi_i)/h
+ * and -(phi_i - phi_{i-1})/h, neighbours outside the grid from the boundary
+ * rule.  g_dev (caller-owned, FP64, 3*nx*ny*nz) receives g_x, g_y, g_z one
+ * after the other, each (nz, ny, nx).  In the fixed-point mixed solve the
+ * acceleration is formed from the exact integer potential in the same pass
+ * that writes phi.  Other arguments, results and errors as mg_solve. */
+mg_status mg_solve_gravity(mg_ctx *ctx, const double *rho_dev, double four_pi_G, double tol,
+                           double *phi_dev, double *g_dev, double *hist, int hist_cap,
+                           int *n_hist, void *stream);
+
 /* Device bytes mg_create would allocate for this grid and these options
  * (the level hierarchy and scratch, as requested from cudaMalloc; the
  * allocator's rounding is not included).  Allocates nothing.  Errors:
@@ -150,7 +161,8 @@ typedef enum {
   MG_K_SOURCE = 7,          /* f = 4 pi G rho and its sums                         */
   MG_K_FUSED_DOWN = 8,      /* FP32 fused SMOOTH + defect + restriction           */
   MG_K_FUSED_UP = 9,        /* FP32 fused prolongation + correction + SMOOTH      */
-  MG_K_COUNT = 10
+  MG_K_GRAVITY = 10,        /* acceleration g = -grad phi (mg_solve_gravity)       */
+  MG_K_COUNT = 11
 } mg_kernel;
 
 /* Enable (on = 1) or disable per-kernel timing: every finest-level launch of
@@ -187,6 +199,12 @@ mg_status mg_op_smooth(int prec, int nx, int ny, int nz, double h, mg_bc bc, dou
 mg_status mg_op_defect(int prec, int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
                        const double *faces_dev, const void *u_dev, const void *f_dev,
                        void *d_dev, void *stream);
+
+/* Acceleration g = [g_x | g_y | g_z] (3 N doubles) of an FP64 potential at
+ * cell centres (Sec. 3.2.3), as in mg_solve_gravity. */
+mg_status mg_op_gravity(int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
+                        const double *faces_dev, const double *phi_dev, double *g_dev,
+                        void *stream);
 
 /* Fused defect + restriction: fc = I_l^{l-1}(f - L_h u) on the
  * (nx/2)*(ny/2)*(nz/2) coarse grid (Algorithm 1, steps 2-3). */

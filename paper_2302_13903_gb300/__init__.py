@@ -30,12 +30,12 @@ EXPORTS = [
     "mg_op_vcycle_down", "mg_op_vcycle_up",
     "mg_batch_create", "mg_batch_solve", "mg_batch_destroy", "mg_batch_cells",
     "mg_batch_last_error", "mg_batch_graph", "mg_required_bytes", "mg_ctx_autotune",
-    "mg_ctx_tile_config", "mg_batch_phase_ms",
+    "mg_ctx_tile_config", "mg_batch_phase_ms", "mg_solve_gravity", "mg_op_gravity",
     "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
     "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
-           "correct", "source", "fused_down", "fused_up"]
+           "correct", "source", "fused_down", "fused_up", "gravity"]
 
 
 class Opts(ctypes.Structure):
@@ -112,6 +112,10 @@ def lib():
             L.mg_solve.argtypes = [p, p, d, d, p, p, i, ctypes.POINTER(i), p]
             L.mg_solve.restype = i
             L.mg_solve_host.argtypes = [p, p, d, d, p, p, i, ctypes.POINTER(i), p]
+            L.mg_solve_gravity.argtypes = [p, p, d, d, p, p, p, i, ctypes.POINTER(i), p]
+            L.mg_solve_gravity.restype = i
+            L.mg_op_gravity.argtypes = [i, i, i, d, i, d, p, p, p, p]
+            L.mg_op_gravity.restype = i
             L.mg_solve_host.restype = i
             L.mg_destroy.argtypes = [p]
             L.mg_destroy.restype = i
@@ -307,6 +311,24 @@ class Solver:
             _check(st, self.ctx)
         return phi, hist[: nh.value].copy(), st
 
+    def solve_gravity(self, rho, four_pi_G=1.0, tol=1e-10, phi=None, g=None, stream=None,
+                      hist_cap=256):
+        """mg_solve_gravity: returns (phi, g, hist, status), g of shape (3, n, n, n)."""
+        import torch
+        if phi is None:
+            phi = torch.zeros_like(rho)
+        if g is None:
+            g = torch.empty((3,) + tuple(rho.shape), dtype=torch.float64, device=rho.device)
+        hist = np.zeros(hist_cap)
+        nh = ctypes.c_int(0)
+        st = lib().mg_solve_gravity(self.ctx, _dptr(rho, torch.float64), four_pi_G, tol,
+                                    _dptr(phi, torch.float64), _dptr(g, torch.float64),
+                                    hist.ctypes.data_as(ctypes.c_void_p), hist_cap,
+                                    ctypes.byref(nh), _stream_ptr(stream))
+        if st not in (0, 4):
+            _check(st, self.ctx)
+        return phi, g, hist[: nh.value].copy(), st
+
     def solve_host(self, rho, four_pi_G=1.0, tol=1e-10, phi=None, stream=None, hist_cap=256):
         """rho, phi: host float64 arrays (numpy or pinned torch CPU tensors)."""
         if phi is None:
@@ -331,6 +353,17 @@ def _prec_of(t):
 def _faces_ptr(faces):
     import torch
     return _dptr(faces, torch.float64) if faces is not None else None
+
+
+def op_gravity(phi, h, bc=PERIODIC, bc_value=0.0, faces=None, stream=None):
+    """mg_op_gravity: (3, nz, ny, nx) acceleration of a CUDA float64 potential."""
+    import torch
+    nz, ny, nx = phi.shape
+    g = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=phi.device)
+    _check(lib().mg_op_gravity(nx, ny, nz, h, bc, bc_value, _faces_ptr(faces),
+                               _dptr(phi, torch.float64), _dptr(g, torch.float64),
+                               _stream_ptr(stream)))
+    return g
 
 
 def op_smooth(u, f, h, bc=PERIODIC, bc_value=0.0, faces=None, omega=1.15, steps=1, colours=0,

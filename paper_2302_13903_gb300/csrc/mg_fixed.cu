@@ -219,6 +219,37 @@ __device__ __forceinline__ long long fx_face_ghost(const FxBc& bc, const Grid& g
   return b2 - self;
 }
 
+// The rule on the integer grid for the finishing pass.
+struct FxBcLite {
+  int kind;
+  long long b2;          // FIXED: round(2 b 2^S)
+  const double* faces;   // OPEN: face values, times c2 = 2^(S+1)
+  double c2;
+};
+
+// Integer neighbour along `axis` (side hi) of cell (i, j, k) holding `self`:
+// the stored value inside the grid, else the rule's ghost.
+__device__ __forceinline__ long long fx_nb_lite(const long long* __restrict__ q,
+                                                const FxBcLite& bc, const Grid& g,
+                                                long long self, bool inside, long long o, int i,
+                                                int j, int k, int axis, int hi) {
+  if (inside) return q[o];
+  if (bc.kind == BC_PERIODIC) {
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const long long t = ((long long)k * g.ny + j) * g.nx + i;
+    if (axis == 0) return q[hi ? t - (g.nx - 1) : t + (g.nx - 1)];
+    if (axis == 1) return q[hi ? t - (long long)(g.ny - 1) * sy : t + (long long)(g.ny - 1) * sy];
+    return q[hi ? t - (long long)(g.nz - 1) * sz : t + (long long)(g.nz - 1) * sz];
+  }
+  if (bc.kind == BC_ZEROGRAD) return self;
+  FxBc full;
+  full.kind = bc.kind;
+  full.b2 = bc.b2;
+  full.faces = bc.faces;
+  full.c2 = bc.c2;
+  return fx_face_ghost(full, g, self, i, j, k, axis, hi);
+}
+
 // PHI' at flat offset o.
 template <bool ZERO_IN>
 __device__ __forceinline__ long long fx_corrected(const long long* __restrict__ phi_in,
@@ -368,6 +399,36 @@ __global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb,
   }
 }
 
+// The last conversion of the fixed-point outer loop with the acceleration
+// (Sec. 3.2.3) fused in: phi = PHI 2^-S - m and, per axis, the average of the
+// two face accelerations, which on the integer grid is the exact difference
+// -(PHI_{i+1} - PHI_{i-1}) rounded once and scaled by 2^-S / (2 h).
+// Writes phi (as doubles, into a different buffer than q) and g = [gx|gy|gz].
+__global__ void k_fx_finish_gravity(const long long* __restrict__ q, double* __restrict__ phi,
+                                    double* __restrict__ g, Grid gr, FxBcLite bc, double c,
+                                    double cg, const double* __restrict__ total, double cm) {
+  const double m = total ? total[0] * cm : 0.0;
+  const long long N = gr.cells();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % gr.nx);
+    const long long r = t / gr.nx;
+    const int j = (int)(r % gr.ny), k = (int)(r / gr.ny);
+    const long long self = q[t];
+    phi[t] = __ll2double_rn(self) * c - m;
+    const long long sy = gr.nx, sz = (long long)gr.nx * gr.ny;
+    const long long xm = fx_nb_lite(q, bc, gr, self, i > 0, t - 1, i, j, k, 0, 0);
+    const long long xp = fx_nb_lite(q, bc, gr, self, i < gr.nx - 1, t + 1, i, j, k, 0, 1);
+    const long long ym = fx_nb_lite(q, bc, gr, self, j > 0, t - sy, i, j, k, 1, 0);
+    const long long yp = fx_nb_lite(q, bc, gr, self, j < gr.ny - 1, t + sy, i, j, k, 1, 1);
+    const long long zm = fx_nb_lite(q, bc, gr, self, k > 0, t - sz, i, j, k, 2, 0);
+    const long long zp = fx_nb_lite(q, bc, gr, self, k < gr.nz - 1, t + sz, i, j, k, 2, 1);
+    g[t] = -__ll2double_rn(xp - xm) * cg;
+    g[N + t] = -__ll2double_rn(yp - ym) * cg;
+    g[2 * N + t] = -__ll2double_rn(zp - zm) * cg;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -485,6 +546,20 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   else
     k_fx_step<false, false><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
                                                            factor, cz, partials, psum, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fx_finish_gravity(const long long* q, double* phi, double* g, Grid gr,
+                                     const Bc& bc, double h, double two_pow_S,
+                                     const double* total, double cm, cudaStream_t s) {
+  FxBcLite b;
+  b.kind = bc.kind;
+  b.c2 = 2.0 * two_pow_S;
+  b.b2 = bc.kind == BC_FIXED ? (long long)std::llrint(bc.value * b.c2) : 0;
+  b.faces = bc.faces;
+  ++g_launches;
+  k_fx_finish_gravity<<<grid_for(gr.cells()), kThreads, 0, s>>>(
+      q, phi, g, gr, b, 1.0 / two_pow_S, 1.0 / (2.0 * h * two_pow_S), total, cm);
   return cudaGetLastError();
 }
 

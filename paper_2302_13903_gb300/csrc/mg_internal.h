@@ -89,6 +89,8 @@ template <typename T>
 cudaError_t launch_sum(const T* a, long long n, int squares, double* partials, cudaStream_t s);
 // out[0] = sum(partials[0..nb)) in a fixed order.
 cudaError_t launch_finish_sum(const double* partials, int nb, double* out, cudaStream_t s);
+// g = -grad phi at cell centres (Sec. 3.2.3), g = [gx | gy | gz] (3 N doubles).
+cudaError_t launch_gravity(const double* u, double* g, Grid gr, double h, Bc bc, cudaStream_t s);
 
 // Mixed precision outer step (FP64 in, FP32 out): r32 = scale * (f - L_h u),
 // partial sums of (f - L_h u)^2 in FP64.
@@ -183,6 +185,12 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
                            const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
                            float factor, double* partials, int nb_max, int* flag, int* nb_out,
                            cudaStream_t s, int cz = 0, long long* psum = nullptr);
+// phi = q 2^-S - m (m = total[0] * cm when total is given; phi must not alias
+// q) and g = -grad phi at cell centres from the exact integer differences
+// (Sec. 3.2.3), g = [gx | gy | gz].
+cudaError_t launch_fx_finish_gravity(const long long* q, double* phi, double* g, Grid gr,
+                                     const Bc& bc, double h, double two_pow_S,
+                                     const double* total, double cm, cudaStream_t s);
 // out[0] = sum over nb blocks of the pairs launch_fx_step wrote, as a double.
 cudaError_t launch_finish_fx_sum(const long long* psum, int nb, double* out, cudaStream_t s);
 

@@ -194,6 +194,30 @@ __global__ void k_correct(double* __restrict__ u, const float* __restrict__ e, l
     u[t] += inv_scale * (double)e[t];
 }
 
+// g = -grad phi at cell centres (Sec. 3.2.3): per axis the average of the two
+// face accelerations -(phi_{i+1} - phi_i) / h and -(phi_i - phi_{i-1}) / h,
+// neighbours outside the level from the rule; g = [g_x | g_y | g_z].
+__global__ void k_gravity(const double* __restrict__ u, double* __restrict__ g, Grid gr, Bc bc,
+                          double h) {
+  const long long total = gr.cells();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % gr.nx);
+    const long long r = t / gr.nx;
+    const int j = (int)(r % gr.ny), k = (int)(r / gr.ny);
+    const double c = u[t];
+    const double xl = -(c - dev::fetch(u, i - 1, j, k, gr, bc)) / h;
+    const double xr = -(dev::fetch(u, i + 1, j, k, gr, bc) - c) / h;
+    const double yl = -(c - dev::fetch(u, i, j - 1, k, gr, bc)) / h;
+    const double yr = -(dev::fetch(u, i, j + 1, k, gr, bc) - c) / h;
+    const double zl = -(c - dev::fetch(u, i, j, k - 1, gr, bc)) / h;
+    const double zr = -(dev::fetch(u, i, j, k + 1, gr, bc) - c) / h;
+    g[t] = 0.5 * (xl + xr);
+    g[total + t] = 0.5 * (yl + yr);
+    g[2 * total + t] = 0.5 * (zl + zr);
+  }
+}
+
 }  // namespace
 
 int reduce_blocks(long long n) {
@@ -292,6 +316,12 @@ template <typename T>
 cudaError_t launch_sum(const T* a, long long n, int squares, double* partials, cudaStream_t s) {
   ++g_launches;
   k_sum<T><<<reduce_blocks(n), kThreads, 0, s>>>(a, n, squares, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gravity(const double* u, double* g, Grid gr, double h, Bc bc, cudaStream_t s) {
+  ++g_launches;
+  k_gravity<<<grid_for(gr.cells()), kThreads, 0, s>>>(u, g, gr, bc, h);
   return cudaGetLastError();
 }
 

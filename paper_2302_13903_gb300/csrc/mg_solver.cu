@@ -451,7 +451,7 @@ double defect_rms(mg_ctx* c, const double* u, const double* f, const Bc& bc, cud
 }
 
 mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
-                     double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
+                     double* gacc, double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
   const int F = c->L - 1;
   c->u64[F] = phi;
   Pyr<double> P = pyr<double>(c);
@@ -476,6 +476,10 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
     rule.record(r);
   }
   remove_mean(c, phi, s);
+  if (gacc) {
+    KTimer t(c, MG_K_GRAVITY, true, s);
+    check(c, mg::launch_gravity(phi, gacc, level_grid(c, F), c->h, bcs[F], s), "gravity");
+  }
   *n_hist = n;
   c->u64[F] = nullptr;
   return (mg_status)st;
@@ -497,7 +501,7 @@ void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
 }
 
 mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
-                      double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
+                      double* gacc, double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
   const int F = c->L - 1;
   const Grid g = level_grid(c, F);
   const long long N = g.cells();
@@ -662,8 +666,21 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       check(c, mg::launch_finish_fx_sum(psum, nbs, c->scal + 56, s), "finish sum phi");
       total = c->scal + 56;
     }
-    check(c, mg::launch_fx_to_f64(cur, phi, N, 1.0 / two_S, total, 1.0 / (two_S * (double)N), s),
-          "fixed point -> phi");
+    const double cm = 1.0 / (two_S * (double)N);
+    if (gacc) {
+      // phi and g from the integers in one pass; it reads neighbours, so it
+      // writes phi into the free integer buffer when the integers are in phi
+      const bool alias = cur == reinterpret_cast<long long*>(phi);
+      double* out = alias ? reinterpret_cast<double*>(alt) : phi;
+      KTimer t(c, MG_K_GRAVITY, true, s);
+      check(c, mg::launch_fx_finish_gravity(cur, out, gacc, g, bc, c->h, two_S, total, cm, s),
+            "fixed point -> phi, g");
+      if (alias)
+        check(c, cudaMemcpyAsync(phi, out, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
+              "copy phi");
+    } else {
+      check(c, mg::launch_fx_to_f64(cur, phi, N, 1.0 / two_S, total, cm, s), "fixed point -> phi");
+    }
     int flag = 0;
     check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s),
           "read flag");
@@ -675,6 +692,10 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
     }
   } else {
     remove_mean(c, phi, s);
+    if (gacc) {
+      KTimer t(c, MG_K_GRAVITY, true, s);
+      check(c, mg::launch_gravity(phi, gacc, g, c->h, bc, s), "gravity");
+    }
   }
   *n_hist = n;
   return (mg_status)st;
@@ -1028,6 +1049,11 @@ mg_status mg_required_bytes(int nx, int ny, int nz, mg_bc bc, const mg_opts* opt
 
 mg_status mg_solve(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
                    double* hist, int hist_cap, int* n_hist, void* stream) {
+  return mg_solve_gravity(c, rho, four_pi_G, tol, phi, nullptr, hist, hist_cap, n_hist, stream);
+}
+
+mg_status mg_solve_gravity(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
+                           double* g, double* hist, int hist_cap, int* n_hist, void* stream) {
   if (!c) {
     g_err = "mg_solve: ctx is NULL";
     return MG_ERR_ARG;
@@ -1044,9 +1070,9 @@ mg_status mg_solve(mg_ctx* c, const double* rho, double four_pi_G, double tol, d
   try {
     check(c, cudaSetDevice(c->device), "cudaSetDevice");
     if (c->opts.prec == MG_FP64)
-      st = solve_fp64(c, rho, four_pi_G, tol, phi, hist, hist_cap, n_hist, s);
+      st = solve_fp64(c, rho, four_pi_G, tol, phi, g, hist, hist_cap, n_hist, s);
     else
-      st = solve_mixed(c, rho, four_pi_G, tol, phi, hist, hist_cap, n_hist, s);
+      st = solve_mixed(c, rho, four_pi_G, tol, phi, g, hist, hist_cap, n_hist, s);
     check(c, cudaStreamSynchronize(s), "sync");
     collect_times(c);
   } catch (const Fail& f) {
@@ -1160,6 +1186,17 @@ mg_status mg_op_defect(int prec, int nx, int ny, int nz, double h, mg_bc bc, dou
           ? mg::launch_defect<double>((const double*)u, (const double*)f, (double*)d, g, h, b, nullptr, s)
           : mg::launch_defect<float>((const float*)u, (const float*)f, (float*)d, g, h, b, nullptr, s);
   return op_result(e, "defect");
+}
+
+mg_status mg_op_gravity(int nx, int ny, int nz, double h, mg_bc bc, double bc_value,
+                        const double* faces, const double* phi, double* g, void* stream) {
+  if (!op_args_ok(MG_FP64, nx, ny, nz, bc, faces) || !phi || !g || !(h > 0.0)) {
+    g_err = "mg_op_gravity: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const Bc b{(int)bc, bc_value, faces};
+  const Grid gr{nx, ny, nz};
+  return op_result(mg::launch_gravity(phi, g, gr, h, b, (cudaStream_t)stream), "gravity");
 }
 
 mg_status mg_op_defect_restrict(int prec, int nx, int ny, int nz, double h, mg_bc bc,
