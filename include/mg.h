@@ -81,7 +81,10 @@ typedef struct {
                       /*    phi and h^2 f are held as 64-bit integers scaled by 2^S  */
                       /*    and the outer residual is exact integer arithmetic,     */
                       /*    rounded once to FP32; 0: FP64 residual and update        */
-  int reserved[7];    /* must be zero                                               */
+  int fas;            /* FP64: 1 runs the full approximation scheme (Algorithm 3,   */
+                      /*    Sec. 2.3.5) in place of the correction scheme in every  */
+                      /*    V-cycle and in FMG; 0 (default) the correction scheme   */
+  int reserved[6];    /* must be zero                                               */
 } mg_opts;
 
 typedef struct mg_ctx mg_ctx;

@@ -239,9 +239,10 @@ __device__ __forceinline__ void prolong_range(const T* uc, T* uf, Grid gf, Bc bc
 // COARSEST on a single cell: the six ghosts are 2 b_face - u (fixed / open)
 // or u itself (periodic / zero gradient, singular: 0).
 template <typename T>
-__device__ __forceinline__ void coarsest_one(const T* f, T* u, double h, Bc bc) {
+__device__ __forceinline__ void coarsest_one(const T* f, T* u, double h, Bc bc,
+                                             bool keep = false) {
   if (bc.kind == BC_PERIODIC || bc.kind == BC_ZEROGRAD) {
-    u[0] = T(0);
+    if (!keep) u[0] = T(0);  // singular: any value solves it; keep the start (FAS) or 0
     return;
   }
   const Grid g{1, 1, 1};

@@ -73,7 +73,8 @@ template <typename T>
 cudaError_t launch_prolong(const T* uc, T* uf, Grid gf, Bc bc_coarse, int high_order, int add,
                            cudaStream_t s);
 template <typename T>
-cudaError_t launch_coarsest(const T* f, T* u, double h, Bc bc, cudaStream_t s);
+// keep: a singular 1-cell level keeps u's start value (FAS) instead of 0.
+cudaError_t launch_coarsest(const T* f, T* u, double h, Bc bc, cudaStream_t s, bool keep = false);
 template <typename T>
 cudaError_t launch_fill(T* u, long long n, T v, cudaStream_t s);
 
@@ -89,6 +90,10 @@ template <typename T>
 cudaError_t launch_sum(const T* a, long long n, int squares, double* partials, cudaStream_t s);
 // out[0] = sum(partials[0..nb)) in a fixed order.
 cudaError_t launch_finish_sum(const double* partials, int nb, double* out, cudaStream_t s);
+// FAS (Algorithm 3): f += L ur and u = ur (step 5); u -= ur (step 7).
+cudaError_t launch_fas_rhs(const double* ur, double* f, double* u, Grid g, double h, Bc bc,
+                           cudaStream_t s);
+cudaError_t launch_sub(double* u, const double* ur, long long n, cudaStream_t s);
 // g = -grad phi at cell centres (Sec. 3.2.3), g = [gx | gy | gz] (3 N doubles).
 cudaError_t launch_gravity(const double* u, double* g, Grid gr, double h, Bc bc, cudaStream_t s);
 

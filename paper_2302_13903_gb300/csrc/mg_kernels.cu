@@ -109,8 +109,8 @@ __global__ void k_prolong(const T* uc, T* uf, Grid gf, Bc bc, int add) {
 }
 
 template <typename T>
-__global__ void k_coarsest(const T* f, T* u, double h, Bc bc) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) dev::coarsest_one(f, u, h, bc);
+__global__ void k_coarsest(const T* f, T* u, double h, Bc bc, bool keep) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) dev::coarsest_one(f, u, h, bc, keep);
 }
 
 template <typename T>
@@ -192,6 +192,29 @@ __global__ void k_correct(double* __restrict__ u, const float* __restrict__ e, l
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
     u[t] += inv_scale * (double)e[t];
+}
+
+// Algorithm 3 step 5 on a coarse level: f += L ur (the restricted potential's
+// Laplacian with the level's own rule) and the start value u = ur.
+__global__ void k_fas_rhs(const double* __restrict__ ur, double* __restrict__ f,
+                          double* __restrict__ u, Grid g, Bc bc, double inv_h2) {
+  const long long total = g.cells();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const long long r = t / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const double s = dev::neighbour_sum(ur, i, j, k, g, bc);
+    f[t] += (s - 6.0 * ur[t]) * inv_h2;
+    u[t] = ur[t];
+  }
+}
+
+// Algorithm 3 step 7: u -= ur (the coarse-grid correction).
+__global__ void k_sub(double* __restrict__ u, const double* __restrict__ ur, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    u[t] -= ur[t];
 }
 
 // g = -grad phi at cell centres (Sec. 3.2.3): per axis the average of the two
@@ -283,9 +306,9 @@ cudaError_t launch_prolong(const T* uc, T* uf, Grid gf, Bc bc_coarse, int high_o
 }
 
 template <typename T>
-cudaError_t launch_coarsest(const T* f, T* u, double h, Bc bc, cudaStream_t s) {
+cudaError_t launch_coarsest(const T* f, T* u, double h, Bc bc, cudaStream_t s, bool keep) {
   ++g_launches;
-  k_coarsest<T><<<1, 32, 0, s>>>(f, u, h, bc);
+  k_coarsest<T><<<1, 32, 0, s>>>(f, u, h, bc, keep);
   return cudaGetLastError();
 }
 
@@ -316,6 +339,19 @@ template <typename T>
 cudaError_t launch_sum(const T* a, long long n, int squares, double* partials, cudaStream_t s) {
   ++g_launches;
   k_sum<T><<<reduce_blocks(n), kThreads, 0, s>>>(a, n, squares, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fas_rhs(const double* ur, double* f, double* u, Grid g, double h, Bc bc,
+                           cudaStream_t s) {
+  ++g_launches;
+  k_fas_rhs<<<grid_for(g.cells()), kThreads, 0, s>>>(ur, f, u, g, bc, 1.0 / (h * h));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(double* u, const double* ur, long long n, cudaStream_t s) {
+  ++g_launches;
+  k_sub<<<grid_for(n), kThreads, 0, s>>>(u, ur, n);
   return cudaGetLastError();
 }
 
@@ -362,7 +398,7 @@ cudaError_t launch_correct(double* u, const float* e32, long long n, double inv_
                                                  cudaStream_t);                                  \
   template cudaError_t launch_restrict<T>(const T*, T*, Grid, cudaStream_t);                     \
   template cudaError_t launch_prolong<T>(const T*, T*, Grid, Bc, int, int, cudaStream_t);        \
-  template cudaError_t launch_coarsest<T>(const T*, T*, double, Bc, cudaStream_t);               \
+  template cudaError_t launch_coarsest<T>(const T*, T*, double, Bc, cudaStream_t, bool);         \
   template cudaError_t launch_fill<T>(T*, long long, T, cudaStream_t);                           \
   template cudaError_t launch_sum<T>(const T*, long long, int, double*, cudaStream_t);
 

@@ -43,6 +43,7 @@ struct mg_ctx {
   double* u64[kMaxLevels] = {};
   double* f64[kMaxLevels] = {};
   double* faces[kMaxLevels] = {};  // open boundary values per level
+  double* ur64[kMaxLevels] = {};   // FAS: restricted potential per coarse level
   // FP32 hierarchy (mixed precision); u32b is the second buffer of levels the
   // fused kernels handle (they read one buffer and write the other).
   float* u32[kMaxLevels] = {};
@@ -131,6 +132,7 @@ void alloc_hierarchy(mg_ctx* c) {
     const long long cells = level_grid(c, l).cells();
     if (o.prec == MG_FP64) {
       if (l < F) c->u64[l] = dalloc<double>(c, cells);
+      if (l < F && o.fas) c->ur64[l] = dalloc<double>(c, cells);
       c->f64[l] = dalloc<double>(c, cells);
       if (bc == MG_BC_OPEN) c->faces[l] = dalloc<double>(c, mg::faces_count(level_grid(c, l)));
     } else {
@@ -372,6 +374,56 @@ void fmg(mg_ctx* c, Pyr<T> P, const Bc* bcs, const Bc& hom, cudaStream_t s) {
   }
 }
 
+// Algorithm 3 on level l >= 1 (FP64 path): every level solves the original
+// equation with its own physical rule (bcs[l]); the coarse-grid correction
+// psi - phi_bar is prolonged with the homogeneous rule.
+void vcycle_fas(mg_ctx* c, int l, const Bc* bcs, const Bc& hom, cudaStream_t s) {
+  Pyr<double> P = pyr<double>(c);
+  const Grid g = level_grid(c, l), gc = level_grid(c, l - 1);
+  const double h = level_h(c, l);
+  const bool fin = (l == c->L - 1);
+  smooth_steps<double>(c, P, l, bcs[l], c->opts.pre, false, s);                      // 1
+  {
+    KTimer t(c, MG_K_DEFECT_RESTRICT, fin, s);
+    check(c, mg::launch_defect_restrict<double>(P.u[l], P.f[l], P.f[l - 1], g, h, bcs[l], s),
+          "defect_restrict");                                                         // 2-3
+  }
+  check(c, mg::launch_restrict<double>(P.u[l], c->ur64[l - 1], g, s), "restrict phi");  // 4
+  check(c, mg::launch_fas_rhs(c->ur64[l - 1], P.f[l - 1], P.u[l - 1], gc, level_h(c, l - 1),
+                              bcs[l - 1], s),
+        "fas rhs");                                                                   // 5
+  if (l - 1 == 0)
+    check(c, mg::launch_coarsest<double>(P.f[0], P.u[0], level_h(c, 0), bcs[0], s, true),
+          "coarsest");                                                                // 6.1
+  else
+    vcycle_fas(c, l - 1, bcs, hom, s);                                                // 6.2
+  check(c, mg::launch_sub(P.u[l - 1], c->ur64[l - 1], gc.cells(), s), "fas correction");  // 7
+  {
+    KTimer t(c, MG_K_PROLONG, fin, s);
+    check(c, mg::launch_prolong<double>(P.u[l - 1], P.u[l], g, hom, 0, 1, s), "prolong");  // 8-9
+  }
+  smooth_steps<double>(c, P, l, bcs[l], c->opts.post, false, s);                     // 10
+}
+
+// Algorithm 2 with Algorithm 3 as the cycle, every level with its own rule.
+void fmg_fas(mg_ctx* c, const Bc* bcs, const Bc& hom, cudaStream_t s) {
+  Pyr<double> P = pyr<double>(c);
+  for (int l = c->L - 1; l > 0; --l)
+    check(c, mg::launch_restrict<double>(P.f[l], P.f[l - 1], level_grid(c, l), s), "restrict");
+  check(c, mg::launch_fill<double>(P.u[0], 1, 0.0, s), "fill");
+  check(c, mg::launch_coarsest<double>(P.f[0], P.u[0], level_h(c, 0), bcs[0], s, true),
+        "coarsest");
+  for (int l = 1; l < c->L; ++l) {
+    {
+      KTimer t(c, MG_K_FMG_PROLONG, l == c->L - 1, s);
+      check(c, mg::launch_prolong<double>(P.u[l - 1], P.u[l], level_grid(c, l), bcs[l - 1], 1, 0,
+                                          s),
+            "fmg_prolong");
+    }
+    vcycle_fas(c, l, bcs, hom, s);
+  }
+}
+
 // Fixed-order sums of squares -> host.
 double read_scalar(mg_ctx* c, int slot, cudaStream_t s) {
   check(c, cudaMemcpyAsync(c->pinned + slot, c->scal + slot, sizeof(double),
@@ -459,7 +511,11 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
   Bc bcs[kMaxLevels];
   for (int l = 0; l < c->L; ++l) bcs[l] = physical_bc(c, l);
   const Bc hom = mg::homogeneous(bcs[F]);
-  if (c->opts.mode_fmg) fmg<double>(c, P, bcs, hom, s);
+  const bool fas = c->opts.fas != 0;
+  if (c->opts.mode_fmg) {
+    if (fas) fmg_fas(c, bcs, hom, s);
+    else fmg<double>(c, P, bcs, hom, s);
+  }
   double dn = defect_rms(c, phi, c->f64[F], bcs[F], s);
   if (fnorm == 0.0) fnorm = dn > 0.0 ? dn : 1.0;
   StopRule rule{tol, c->opts.stall_ratio};
@@ -470,7 +526,8 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
   for (int cyc = 0;; ++cyc) {
     st = rule.decide(r, cyc, c->opts.max_cycles, n, hist_cap);
     if (st >= 0) break;
-    vcycle<double>(c, P, F, bcs[F], hom, false, s);
+    if (fas) vcycle_fas(c, F, bcs, hom, s);
+    else vcycle<double>(c, P, F, bcs[F], hom, false, s);
     r = defect_rms(c, phi, c->f64[F], bcs[F], s) / fnorm;
     hist[n++] = r;
     rule.record(r);
@@ -708,6 +765,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (o.max_cycles < 0 || o.lmax < 0 || o.lmax > 4) return MG_ERR_ARG;
   if (o.inner_cycles < 0 || o.inner_cycles > 64) return MG_ERR_ARG;
   if (o.outer_fixed != 0 && o.outer_fixed != 1) return MG_ERR_ARG;
+  if (o.fas != 0 && (o.fas != 1 || o.prec != MG_FP64)) return MG_ERR_ARG;
   if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;
@@ -911,6 +969,7 @@ void mg_opts_init(mg_opts* o) {
   o->inner_fmg = 0;
   o->inner_cycles = 3;
   o->outer_fixed = 1;
+  o->fas = 0;
 }
 
 const char* mg_status_str(mg_status s) {

@@ -44,8 +44,8 @@ def test_default_options_layout():
     assert (o.prec, o.mode_fmg, o.pre, o.post) == (0, 1, 1, 1)
     assert o.omega == 1.15 and o.max_cycles == 50 and o.lmax == 4 and o.use_com == 1
     assert o.stall_ratio == 0.9 and o.inner_fmg == 0 and o.inner_cycles == 3
-    assert o.outer_fixed == 1
-    assert list(o.reserved) == [0] * 7
+    assert o.outer_fixed == 1 and o.fas == 0
+    assert list(o.reserved) == [0] * 6
 
 
 @pytest.mark.parametrize("py,c", [(mg.Opts, "mg_opts"), (mg.Request, "mg_request"),

@@ -252,3 +252,35 @@ def test_open_sphere_256_full_size(prec):
             assert emax(phi, ref.phi) <= (1e-11 if prec == mg.FP64 else 1e-9)
     assert errs[256] < 1e-3
     assert 2.5 < errs[128] / errs[256] < 6.0
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_fas_same_schedule_matches_oracle(bc):
+    """Algorithm 3 (FAS, with FMG built on it) on the FP64 path: the same phi
+    as the oracle's FAS after the same number of cycles."""
+    n = 32
+    rho, fpg = source(n, bc, seed=14)
+    for k in (0, 2):
+        ref = orc.solve(rho, 1.0 / n, bc, bc_value=0.25 if bc == mg.FIXED else 0.0, four_pi_G=fpg,
+                        tol=0.0, max_cycles=k, stall_ratio=NO_STALL, cycle=orc.FAS)
+        phi, hist, st, _ = gpu_solve(rho, bc, fpg, 0.0, max_cycles=k, stall_ratio=NO_STALL, fas=1)
+        assert len(hist) == len(ref.hist) == k + 1
+        assert emax(phi, ref.phi) <= 1e-11, (k, emax(phi, ref.phi))
+        assert np.allclose(hist, ref.hist, rtol=1e-6, atol=1e-14)
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_fas_equals_correction_scheme(bc):
+    """On a uniform grid the two schemes are the same iteration (Sec. 2.3.5):
+    after the same cycles the potentials agree to rounding."""
+    n = 64
+    rho, fpg = source(n, bc, seed=15)
+    a = gpu_solve(rho, bc, fpg, 0.0, max_cycles=3, stall_ratio=NO_STALL, fas=1)
+    b = gpu_solve(rho, bc, fpg, 0.0, max_cycles=3, stall_ratio=NO_STALL, fas=0)
+    assert emax(a[0], b[0]) <= 1e-12
+    assert np.allclose(a[1], b[1], rtol=1e-8, atol=1e-15)
+
+
+def test_fas_needs_the_fp64_path():
+    with pytest.raises(mg.MGError):
+        mg.Solver(16, 1.0 / 16, mg.PERIODIC, prec=mg.MIXED, fas=1)
