@@ -516,3 +516,78 @@ def test_gravity_fixed_rule_boundary_cells(orc):
     ghost = 2 * bval - phi[k, j, 0]
     want = 0.5 * (-(phi[k, j, 0] - ghost) / h - (phi[k, j, 1] - phi[k, j, 0]) / h)
     assert abs(g[0, k, j, 0] - want) <= 1e-14 * max(1.0, abs(want))
+
+
+# ---------------------------------------------------------------------------
+# Non-cubic grids (the Jeans-wave box 1 x 0.5 x 0.5 of Sec. 4.3): levels are
+# halved until the shortest side has one cell, so the coarsest level has more
+# than one cell and COARSEST is N_0,max Gauss-Seidel sweeps (Sec. 2.3.2).
+
+def dense_system_box(nx, ny, nz, h, bc, b=0.0):
+    """(sum nb - 6u)/h^2 on an nx*ny*nz box with the ghost eliminated."""
+    N = nx * ny * nz
+    A = np.zeros((N, N))
+    g = np.zeros(N)
+    dims = (nx, ny, nz)
+    idx = lambda i, j, k: (k * ny + j) * nx + i
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                c = idx(i, j, k)
+                A[c, c] -= 6 / h ** 2
+                for axis in range(3):
+                    for side in (-1, 1):
+                        p = [i, j, k]
+                        p[axis] += side
+                        if 0 <= p[axis] < dims[axis]:
+                            A[c, idx(*p)] += 1 / h ** 2
+                        elif bc == PERIODIC:
+                            p[axis] %= dims[axis]
+                            A[c, idx(*p)] += 1 / h ** 2
+                        elif bc == ZEROGRAD:
+                            A[c, c] += 1 / h ** 2
+                        else:
+                            A[c, c] -= 1 / h ** 2
+                            g[c] += 2 * b / h ** 2
+    return A, g
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, FIXED, ZEROGRAD])
+@pytest.mark.parametrize("shape", [(8, 4, 4), (8, 8, 2), (4, 2, 2)])
+def test_non_cubic_converged_multigrid_equals_dense_solve(orc, bc, shape):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz + bc)
+    h = 1.0 / nx
+    rho = rng.standard_normal((nz, ny, nx))
+    b = 0.3 if bc == FIXED else 0.0
+    A, g = dense_system_box(nx, ny, nz, h, bc, b)
+    f = rho.ravel().copy()
+    if bc in (PERIODIC, ZEROGRAD):
+        f -= f.mean()
+        M = np.zeros((f.size + 1, f.size + 1))
+        M[:-1, :-1] = A
+        M[:-1, -1] = 1.0
+        M[-1, :-1] = 1.0
+        ref = np.linalg.solve(M, np.append(f - g, 0.0))[:-1]
+    else:
+        ref = np.linalg.solve(A, f - g)
+    r = orc.solve(rho, h, bc, bc_value=b, tol=0.0, max_cycles=80)
+    assert r.ok, (r.status, r.hist)
+    assert emax(r.phi.ravel(), ref) < 1e-12
+
+
+def test_jeans_box_periodic_mode_is_exact(orc):
+    """Periodic 1 x 0.5 x 0.5 box (32 x 16 x 16 cells): the mode
+    sin 2pi x sin 4pi y sin 4pi z is an eigenvector of the 7-point operator,
+    eigenvalue -(4/h^2)(sin^2(pi h) + 2 sin^2(2 pi h)); the converged solve
+    returns rho / lambda.  The coarsest level is 2 x 1 x 1."""
+    nx, ny, nz = 32, 16, 16
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(ny) + 0.5) * h
+    rho = (np.sin(4 * np.pi * y)[:, None, None] * np.sin(4 * np.pi * y)[None, :, None] *
+           np.sin(2 * np.pi * x)[None, None, :])
+    lam = -(4 / h ** 2) * (math.sin(math.pi * h) ** 2 + 2 * math.sin(2 * math.pi * h) ** 2)
+    r = orc.solve(rho, h, PERIODIC, tol=0.0, max_cycles=60)
+    assert r.ok and len(r.hist) < 60
+    assert emax(r.phi, rho / lam) < 1e-12
