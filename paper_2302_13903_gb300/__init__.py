@@ -233,10 +233,13 @@ class Solver:
     """One grid configuration: ``mg_create`` on construction, ``mg_destroy`` on close."""
 
     def __init__(self, n, dx, bc=PERIODIC, **opts):
-        self.n, self.dx, self.bc = n, dx, bc
+        """n: cells per side, or (nx, ny, nz) for a box (arrays are (nz, ny, nx))."""
+        dims = (n, n, n) if isinstance(n, int) else tuple(int(v) for v in n)
+        self.dims = dims
+        self.n, self.dx, self.bc = min(dims), dx, bc
         self.opts = default_opts(**opts)
         h = ctypes.c_void_p()
-        _check(lib().mg_create(n, n, n, dx, bc, ctypes.byref(self.opts), ctypes.byref(h)))
+        _check(lib().mg_create(*dims, dx, bc, ctypes.byref(self.opts), ctypes.byref(h)))
         self.ctx = h
 
     def close(self):

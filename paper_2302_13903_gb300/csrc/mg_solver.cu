@@ -6,6 +6,7 @@
 // (one 16-byte read per cycle).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -33,7 +34,8 @@ constexpr int kMaxLevels = 16;
 }  // namespace
 
 struct mg_ctx {
-  int n = 0;            // cells per side of the finest level
+  int n = 0;            // cells along x of the finest level (nx)
+  int ny = 0, nz = 0;   // cells along y and z (equal to n for cubic grids)
   int L = 0;            // number of levels; level L-1 is the finest
   double h = 0.0;       // finest spacing
   int bc_kind = 0;
@@ -79,11 +81,21 @@ namespace {
 int level_n(const mg_ctx* c, int l) { return c->n >> (c->L - 1 - l); }
 double level_h(const mg_ctx* c, int l) { return c->h * (double)(1 << (c->L - 1 - l)); }
 Grid level_grid(const mg_ctx* c, int l) {
-  const int n = level_n(c, l);
-  return Grid{n, n, n};
+  const int s = c->L - 1 - l;
+  return Grid{c->n >> s, c->ny >> s, c->nz >> s};
 }
+bool is_cubic(const mg_ctx* c) { return c->n == c->ny && c->n == c->nz; }
 
 bool is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+// Powers of two >= 2 on every axis; a non-cubic grid must have x as a
+// longest side (the red-black kernels pair cells along x, so the coarsest
+// level, where the shortest side has one cell, keeps at least two along x).
+bool dims_ok(int nx, int ny, int nz) {
+  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nx < 2 || ny < 2 || nz < 2) return false;
+  const bool cubic = nx == ny && nx == nz;
+  return cubic || (nx >= ny && nx >= nz);
+}
 
 struct Fail {
   mg_status st;
@@ -206,6 +218,7 @@ void collect_times(mg_ctx* c) {
 
 // Highest level index the single-CTA bottom solver covers (<= 16^3 cells).
 int bottom_top(const mg_ctx* c) {
+  if (!is_cubic(c)) return 0;  // the single-CTA bottom solver takes cubes only
   int t = 0;
   while (t + 1 < c->L && t + 1 < mg::kBottomLevels && level_n(c, t + 1) <= mg::kBottomTopN) ++t;
   return t;
@@ -223,6 +236,25 @@ void launch_bottom_levels(mg_ctx* c, T** u, T** f, int top, const Bc* bcs, const
   check(c, mg::launch_bottom<T>(u, f, n, h, bcs, hom, c->opts.omega, c->opts.pre, c->opts.post,
                                 top, fmg, s),
         "bottom");
+}
+
+// COARSEST on level 0 (Sec. 2.3.2): one cell is solved exactly; a level of
+// several cells (non-cubic grids) gets N_0,max red-black Gauss-Seidel sweeps
+// (omega = 1) from 0, or from its current value when `keep` (FAS).
+template <typename T>
+void coarsest_solve(mg_ctx* c, T* u0, const T* f0, const Bc& bc, bool keep, cudaStream_t s) {
+  const Grid g0 = level_grid(c, 0);
+  const double h0 = level_h(c, 0);
+  if (g0.cells() == 1) {
+    check(c, mg::launch_coarsest<T>(f0, u0, h0, bc, s, keep), "coarsest");
+    return;
+  }
+  if (!keep) check(c, mg::launch_fill<T>(u0, g0.cells(), T(0), s), "fill");
+  const int nmax = std::max(g0.nx, std::max(g0.ny, g0.nz));
+  for (int q = 0; q < nmax; ++q) {
+    check(c, mg::launch_sor<T>(u0, f0, g0, h0, bc, 1.0, 0, s), "coarsest red");
+    check(c, mg::launch_sor<T>(u0, f0, g0, h0, bc, 1.0, 1, s), "coarsest black");
+  }
 }
 
 template <typename T>
@@ -300,7 +332,7 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
   }
   Pyr<float> P = pyr<float>(c);
   if (l - 1 == 0)
-    check(c, mg::launch_coarsest<float>(P.f[0], P.u[0], level_h(c, 0), hom, s), "coarsest");
+    coarsest_solve<float>(c, P.u[0], P.f[0], hom, false, s);
   else if (l - 1 <= bottom_top(c))
     launch_bottom_levels<float>(c, P.u, P.f, l - 1, nullptr, hom, false, s);
   else
@@ -345,7 +377,7 @@ void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool ze
           "defect_restrict");
   }
   if (l - 1 == 0)
-    check(c, mg::launch_coarsest<T>(P.f[0], P.u[0], level_h(c, 0), hom, s), "coarsest");  // 4.1
+    coarsest_solve<T>(c, P.u[0], P.f[0], hom, false, s);                               // 4.1
   else if (l - 1 <= bottom_top(c))
     launch_bottom_levels<T>(c, P.u, P.f, l - 1, nullptr, hom, false, s);                 // 4.2
   else
@@ -363,7 +395,10 @@ void fmg(mg_ctx* c, Pyr<T> P, const Bc* bcs, const Bc& hom, cudaStream_t s) {
   const int lb = bottom_top(c);
   for (int l = c->L - 1; l > lb; --l)
     check(c, mg::launch_restrict<T>(P.f[l], P.f[l - 1], level_grid(c, l), s), "restrict");
-  launch_bottom_levels<T>(c, P.u, P.f, lb, bcs, hom, true, s);  // levels 0 .. lb
+  if (lb > 0 || level_grid(c, 0).cells() == 1)
+    launch_bottom_levels<T>(c, P.u, P.f, lb, bcs, hom, true, s);  // levels 0 .. lb
+  else
+    coarsest_solve<T>(c, P.u[0], P.f[0], bcs[0], false, s);
   for (int l = lb + 1; l < c->L; ++l) {
     {
       KTimer t(c, MG_K_FMG_PROLONG, l == c->L - 1, s);
@@ -393,8 +428,7 @@ void vcycle_fas(mg_ctx* c, int l, const Bc* bcs, const Bc& hom, cudaStream_t s) 
                               bcs[l - 1], s),
         "fas rhs");                                                                   // 5
   if (l - 1 == 0)
-    check(c, mg::launch_coarsest<double>(P.f[0], P.u[0], level_h(c, 0), bcs[0], s, true),
-          "coarsest");                                                                // 6.1
+    coarsest_solve<double>(c, P.u[0], P.f[0], bcs[0], true, s);                      // 6.1
   else
     vcycle_fas(c, l - 1, bcs, hom, s);                                                // 6.2
   check(c, mg::launch_sub(P.u[l - 1], c->ur64[l - 1], gc.cells(), s), "fas correction");  // 7
@@ -410,9 +444,7 @@ void fmg_fas(mg_ctx* c, const Bc* bcs, const Bc& hom, cudaStream_t s) {
   Pyr<double> P = pyr<double>(c);
   for (int l = c->L - 1; l > 0; --l)
     check(c, mg::launch_restrict<double>(P.f[l], P.f[l - 1], level_grid(c, l), s), "restrict");
-  check(c, mg::launch_fill<double>(P.u[0], 1, 0.0, s), "fill");
-  check(c, mg::launch_coarsest<double>(P.f[0], P.u[0], level_h(c, 0), bcs[0], s, true),
-        "coarsest");
+  coarsest_solve<double>(c, P.u[0], P.f[0], bcs[0], false, s);
   for (int l = 1; l < c->L; ++l) {
     {
       KTimer t(c, MG_K_FMG_PROLONG, l == c->L - 1, s);
@@ -782,10 +814,10 @@ mg_status validate_opts(const mg_opts& o) {
 enum TuneKind { TUNE_DOWN = 0, TUNE_UP = 1, TUNE_SMOOTH = 2, TUNE_FX = 3 };
 
 struct TuneKey {
-  int sms, major, minor, kind, n, periodic;
+  int sms, major, minor, kind, nx, ny, nz, periodic;
   bool operator<(const TuneKey& o) const {
-    return std::tie(sms, major, minor, kind, n, periodic) <
-           std::tie(o.sms, o.major, o.minor, o.kind, o.n, o.periodic);
+    return std::tie(sms, major, minor, kind, nx, ny, nz, periodic) <
+           std::tie(o.sms, o.major, o.minor, o.kind, o.nx, o.ny, o.nz, o.periodic);
   }
 };
 
@@ -802,8 +834,8 @@ void tune_load_locked() {
   if (!fp) return;
   TuneKey k;
   mg::TileCfg v;
-  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d", &k.sms, &k.major, &k.minor, &k.kind, &k.n,
-                     &k.periodic, &v.tx, &v.cz) == 8)
+  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d %d %d", &k.sms, &k.major, &k.minor, &k.kind,
+                     &k.nx, &k.ny, &k.nz, &k.periodic, &v.tx, &v.cz) == 10)
     g_tune[k] = v;
   std::fclose(fp);
 }
@@ -814,8 +846,8 @@ void tune_store_locked(const TuneKey& k, mg::TileCfg v) {
   if (!path || !*path) return;
   FILE* fp = std::fopen(path, "a");
   if (!fp) return;
-  std::fprintf(fp, "%d %d %d %d %d %d %d %d\n", k.sms, k.major, k.minor, k.kind, k.n, k.periodic,
-               v.tx, v.cz);
+  std::fprintf(fp, "%d %d %d %d %d %d %d %d %d %d\n", k.sms, k.major, k.minor, k.kind, k.nx, k.ny,
+               k.nz, k.periodic, v.tx, v.cz);
   std::fclose(fp);
 }
 
@@ -882,7 +914,8 @@ void autotune(mg_ctx* c, cudaStream_t s) {
       const double h = level_h(c, l);
       for (int kind : {TUNE_DOWN, TUNE_UP, TUNE_SMOOTH}) {
         if (kind == TUNE_SMOOTH && c->opts.pre < 2 && c->opts.post < 2) continue;
-        const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, kind, g.nx, periodic};
+        const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, kind, g.nx, g.ny, g.nz,
+                          periodic};
         mg::TileCfg best;
         auto hit = g_tune.find(key);
         if (hit != g_tune.end()) {
@@ -917,7 +950,8 @@ void autotune(mg_ctx* c, cudaStream_t s) {
   }
   const Grid g = level_grid(c, F);
   if (c->fxbuf) {
-    const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, TUNE_FX, g.nx, periodic};
+    const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, TUNE_FX, g.nx, g.ny, g.nz,
+                      periodic};
     auto hit = g_tune.find(key);
     if (hit != g_tune.end()) {
       c->fx_cz = hit->second.cz;
@@ -1053,19 +1087,23 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
   mg_opts o;
   if (opts) o = *opts;
   else mg_opts_init(&o);
-  if (!is_pow2(nx) || nx < 2 || nx != ny || nx != nz || !(dx > 0.0) || (int)bc < 0 ||
-      (int)bc > 3 || validate_opts(o) != MG_OK) {
-    g_err = "mg_create: invalid argument (cubic power-of-two grid >= 2, dx > 0, bc, opts)";
+  if (!dims_ok(nx, ny, nz) || !(dx > 0.0) || (int)bc < 0 || (int)bc > 3 ||
+      validate_opts(o) != MG_OK) {
+    g_err = "mg_create: invalid argument (powers of two >= 2 with nx the longest side, dx > 0, "
+            "bc, opts)";
     return MG_ERR_ARG;
   }
   mg_ctx* c = new mg_ctx;
   try {
     c->n = nx;
+    c->ny = ny;
+    c->nz = nz;
     c->h = dx;
     c->bc_kind = (int)bc;
     c->opts = o;
+    const int m = std::min(nx, std::min(ny, nz));
     int L = 1;
-    while ((nx >> (L - 1)) > 1) ++L;
+    while ((m >> (L - 1)) > 1) ++L;
     if (L > kMaxLevels) fail(c, MG_ERR_ARG, "mg_create: grid too large");
     c->L = L;
     check(c, cudaGetDevice(&c->device), "cudaGetDevice");
@@ -1087,19 +1125,21 @@ mg_status mg_required_bytes(int nx, int ny, int nz, mg_bc bc, const mg_opts* opt
   mg_opts o;
   if (opts) o = *opts;
   else mg_opts_init(&o);
-  if (!is_pow2(nx) || nx < 2 || nx != ny || nx != nz || (int)bc < 0 || (int)bc > 3 ||
-      validate_opts(o) != MG_OK) {
+  if (!dims_ok(nx, ny, nz) || (int)bc < 0 || (int)bc > 3 || validate_opts(o) != MG_OK) {
     g_err = "mg_required_bytes: invalid argument";
     return MG_ERR_ARG;
   }
   mg_ctx c;
   c.dry = true;
   c.n = nx;
+  c.ny = ny;
+  c.nz = nz;
   c.h = 1.0;
   c.bc_kind = (int)bc;
   c.opts = o;
   c.L = 1;
-  while ((nx >> (c.L - 1)) > 1) ++c.L;
+  const int m = std::min(nx, std::min(ny, nz));
+  while ((m >> (c.L - 1)) > 1) ++c.L;
   if (c.L > kMaxLevels) return MG_ERR_ARG;
   alloc_hierarchy(&c);
   *bytes = c.bytes;

@@ -115,7 +115,7 @@ def test_argument_validation_needs_no_gpu():
     L = mg.lib()
     h = ctypes.c_void_p()
     o = mg.default_opts()
-    for args in [(12, 12, 12, 0.1, 0), (8, 8, 4, 0.1, 0), (8, 8, 8, -1.0, 0), (8, 8, 8, 0.1, 7),
+    for args in [(12, 12, 12, 0.1, 0), (4, 8, 8, 0.1, 0), (8, 8, 8, -1.0, 0), (8, 8, 8, 0.1, 7),
                  (1, 1, 1, 0.1, 0)]:
         assert L.mg_create(*args, ctypes.byref(o), ctypes.byref(h)) == 1
         assert not h.value

@@ -284,3 +284,78 @@ def test_fas_equals_correction_scheme(bc):
 def test_fas_needs_the_fp64_path():
     with pytest.raises(mg.MGError):
         mg.Solver(16, 1.0 / 16, mg.PERIODIC, prec=mg.MIXED, fas=1)
+
+
+def box_source(shape, bc, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(ny) + 0.5) * h
+    z = (np.arange(nz) + 0.5) * h
+    rho = np.zeros((nz, ny, nx))
+    for _ in range(4):
+        c = rng.random(3) * np.array([nx, ny, nz]) * h
+        sig = 0.05 + 0.05 * rng.random()
+        rho += (np.exp(-((z - c[2]) ** 2) / (2 * sig ** 2))[:, None, None] *
+                np.exp(-((y - c[1]) ** 2) / (2 * sig ** 2))[None, :, None] *
+                np.exp(-((x - c[0]) ** 2) / (2 * sig ** 2))[None, None, :])
+    if bc in (mg.PERIODIC, mg.ZEROGRAD):
+        rho -= rho.mean()
+    return rho
+
+
+@pytest.mark.parametrize("bc", [mg.PERIODIC, mg.FIXED, mg.ZEROGRAD, mg.OPEN])
+@pytest.mark.parametrize("shape", [(16, 8, 8), (64, 32, 16), (32, 32, 8)])
+def test_non_cubic_fp64_same_schedule_matches_oracle(bc, shape):
+    """Boxes whose shortest side reaches one cell first: the coarsest level
+    has several cells and gets N_0,max Gauss-Seidel sweeps (Sec. 2.3.2)."""
+    nx, ny, nz = shape
+    rho = box_source(shape, bc, seed=nx + ny + nz + bc)
+    fpg = 1.0
+    b = 0.25 if bc == mg.FIXED else 0.0
+    for k in (0, 2):
+        ref = orc.solve(rho, 1.0 / nx, bc, bc_value=b, four_pi_G=fpg, tol=0.0, max_cycles=k,
+                        stall_ratio=NO_STALL)
+        with mg.Solver(shape, 1.0 / nx, bc, prec=mg.FP64, fixed_value=b, max_cycles=k,
+                       stall_ratio=NO_STALL) as s:
+            phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), fpg, 0.0)
+        assert len(hist) == len(ref.hist) == k + 1
+        assert emax(phi.cpu().numpy(), ref.phi) <= 1e-11, (k, emax(phi.cpu().numpy(), ref.phi))
+
+
+@pytest.mark.parametrize("bc", [mg.PERIODIC, mg.FIXED, mg.ZEROGRAD, mg.OPEN])
+def test_non_cubic_mixed_matches_converged_oracle(bc):
+    """The Jeans-wave box shape 1 x 0.5 x 0.5 at 128 x 64 x 64 (fused kernels on
+    the levels that allow them), mixed precision to 1e-10."""
+    shape = (128, 64, 64)
+    rho = box_source(shape, bc, seed=3 + bc)
+    b = 0.25 if bc == mg.FIXED else 0.0
+    ref = orc.solve(rho, 1.0 / 128, bc, bc_value=b, tol=0.0, max_cycles=60)
+    with mg.Solver(shape, 1.0 / 128, bc, prec=mg.MIXED, fixed_value=b) as s:
+        phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-10)
+    assert st == 0 and hist[-1] < 1e-10
+    assert emax(phi.cpu().numpy(), ref.phi) <= 1e-9
+
+
+def test_jeans_box_mode_exact_on_gpu():
+    """64 x 32 x 32 periodic box: sin 2pi x sin 4pi y sin 4pi z is an exact
+    eigenvector; the FP64 solve to 1e-12 returns rho / lambda."""
+    nx, ny, nz = 64, 32, 32
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(ny) + 0.5) * h
+    rho = (np.sin(4 * np.pi * y)[:, None, None] * np.sin(4 * np.pi * y)[None, :, None] *
+           np.sin(2 * np.pi * x)[None, None, :])
+    lam = -(4 / h ** 2) * (math.sin(math.pi * h) ** 2 + 2 * math.sin(2 * math.pi * h) ** 2)
+    with mg.Solver((nx, ny, nz), h, mg.PERIODIC, prec=mg.FP64) as s:
+        phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-12)
+    assert st == 0
+    assert emax(phi.cpu().numpy(), rho / lam) <= 1e-11
+
+
+def test_non_cubic_shape_rules():
+    with pytest.raises(mg.MGError):  # x must be a longest side
+        mg.Solver((8, 16, 16), 0.1, mg.PERIODIC)
+    with pytest.raises(mg.MGError):
+        mg.Solver((12, 8, 8), 0.1, mg.PERIODIC)
