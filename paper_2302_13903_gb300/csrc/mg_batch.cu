@@ -41,8 +41,8 @@
 namespace mg {
 namespace batch {
 
-constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4>::NT;  // 216
-constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4>::SMEM;
+constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4, false>::NT;  // 216
+constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4, false>::SMEM;
 constexpr int kMaxL = 16;
 constexpr int kChunk = 32768;   // cells per chunk item
 constexpr int kFusedMinN = 32;  // levels of at least 32^3 use the fused tiles
@@ -398,25 +398,25 @@ __device__ __forceinline__ void tile_leg(bool down, bool per, const GridDev& g, 
     const bool zg = (l < g.L - 1) || zero_finest;
     if (zg) {
       if (per)
-        fused::fused_tile<fused::kDown, true, true, TX, 16, 4, true>(
+        fused::fused_tile<fused::kDown, true, true, TX, 16, 4, true, false>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, true, false, TX, 16, 4, true>(
+        fused::fused_tile<fused::kDown, true, false, TX, 16, 4, true, false>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     } else {
       if (per)
-        fused::fused_tile<fused::kDown, false, true, TX, 16, 4, true>(
+        fused::fused_tile<fused::kDown, false, true, TX, 16, 4, true, false>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, false, false, TX, 16, 4, true>(
+        fused::fused_tile<fused::kDown, false, false, TX, 16, 4, true, false>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     }
   } else {
     if (per)
-      fused::fused_tile<fused::kUp, false, true, TX, 16, 4, true>(
+      fused::fused_tile<fused::kUp, false, true, TX, 16, 4, true, false>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
     else
-      fused::fused_tile<fused::kUp, false, false, TX, 16, 4, true>(
+      fused::fused_tile<fused::kUp, false, false, TX, 16, 4, true, false>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
   }
 }

@@ -197,11 +197,11 @@ __device__ __forceinline__ float2 defect_part(const Row& r, const Row& other, co
 // both rows of (d(4m) + d(4m+1), d(4m+2) + d(4m+3)): the two coarse cells in x.
 template <bool PER>
 __device__ __forceinline__ float2 defect_patch(const Patch& u, const float4* __restrict__ S,
-                                               int ia, int ib, int RT, const Patch& zm,
+                                               int ia, int ib, int RS, const Patch& zm,
                                                const Patch& zp, const Patch& f,
                                                const FusedParams& p, const Flags& fl, bool zlo,
                                                bool zhi) {
-  const float4 above = S[ia - RT], below = S[ib + RT];
+  const float4 above = S[ia - RS], below = S[ib + RS];
   const float4 la = S[ia - 1], ra = S[ia + 1], lb = S[ib - 1], rb = S[ib + 1];
   const float2 dae = defect_part<PER, true, false>(u.a, u.b, above, la, zm.a, zp.a, f.a, p, fl, zlo, zhi);
   const float2 dao = defect_part<PER, false, false>(u.a, u.b, above, ra, zm.a, zp.a, f.a, p, fl, zlo, zhi);
@@ -274,17 +274,29 @@ __device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const F
   return P;
 }
 
+// Row stride of a shared plane, in float4: the smallest RS >= RT with
+// 2 RS = RT (mod 8).  Thread t = tp RT + tr reads float4 2 tp RS + tr (+ a
+// constant), which is then t plus a multiple of 8 -- eight consecutive
+// threads hit eight different 16-byte bank groups (no bank conflicts).
+constexpr int row_stride(int rt) {
+  int r = rt;
+  while ((2 * r - rt) % 8 != 0) ++r;
+  return r;
+}
+
 // HYO > 0 overrides the rows of halo (so that every mode can share one block
-// size in the batched solver).
-template <int MODE, int TX, int TY, int HYO = 0>
+// size in the batched solver); PAD = false keeps rows unpadded (RS = RT), for
+// the batched solver, whose other phases want the shared memory as L1.
+template <int MODE, int TX, int TY, int HYO = 0, bool PAD = true>
 struct Shape {
   static constexpr int HZ = (MODE == kDown) ? 3 : 2;  // planes of halo in z
   static constexpr int HY = HYO > 0 ? HYO : ((MODE == kDown) ? 4 : 2);  // rows of halo in y (even)
   static constexpr int RT = (TX + 8) / 4;              // float4 columns per row
+  static constexpr int RS = PAD ? row_stride(RT) : RT;  // float4 between rows in shared memory
   static constexpr int RR = TY + 2 * HY;               // rows
   static constexpr int RP = RR / 2;                    // row pairs
   static constexpr int NT = RT * RP;                   // threads
-  static constexpr int PL = RT * RR;                   // float4 per shared plane
+  static constexpr int PL = RS * RR;                   // float4 per shared plane
   static constexpr int NU = 4, NF = 4, NRED = 2, NFIN = (MODE == kDown) ? 2 : 0;
   static constexpr size_t SMEM = (size_t)(NU + NF + NRED + NFIN) * PL * 16;
 };
@@ -292,13 +304,14 @@ struct Shape {
 // The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
 // Shape::SMEM bytes; threads tid >= Shape::NT of a larger CTA take part in
 // the barriers only.
-template <int MODE, bool ZERO, bool PER, int TX, int TY, int HYO = 0, bool COH = false>
+template <int MODE, bool ZERO, bool PER, int TX, int TY, int HYO = 0, bool COH = false,
+          bool PAD = true>
 __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, const float* f,
                                            const float* ec, float* fc,
                                            const FusedParams& p, int bx, int by, int bz,
                                            float4* smem) {
-  using S_ = Shape<MODE, TX, TY, HYO>;
-  constexpr int HZ = S_::HZ, HY = S_::HY, RT = S_::RT, RP = S_::RP, PL = S_::PL;
+  using S_ = Shape<MODE, TX, TY, HYO, PAD>;
+  constexpr int HZ = S_::HZ, HY = S_::HY, RT = S_::RT, RS = S_::RS, RP = S_::RP, PL = S_::PL;
   float4* s_u = smem;                     // [4][PL] planes of u (async copies)
   float4* s_f = s_u + S_::NU * PL;        // [4][PL] planes of f (async copies)
   float4* s_red = s_f + S_::NF * PL;      // [2][PL] red-updated planes
@@ -325,9 +338,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   const size_t plane = (size_t)p.nx * p.ny;
   const size_t offA = col_ok ? (size_t)gyAw * p.nx + gx4w : 0;
   const size_t offB = col_ok ? offA + (size_t)p.nx : 0;
-  const int ia = (2 * tp) * RT + tr, ib = ia + RT;  // shared indices of rows a, b
+  const int ia = (2 * tp) * RS + tr, ib = ia + RS;  // shared indices of rows a, b
   const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
-  const int offU = tp > 0 ? -RT : 0, offD = tp < RP - 1 ? RT : 0;
+  const int offU = tp > 0 ? -RS : 0, offD = tp < RP - 1 ? RS : 0;
   const int q_first = z0 - HZ, q_last = z1 - 1 + HZ;
 
   auto issue = [&](int qu) {
@@ -451,7 +464,7 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       const int pz = q - 3;
       if (act && pz >= z0 && pz < z1 && out) {
         const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
-        const float2 s2 = defect_patch<PER>(r3, &s_fin[ZP_DEF * PL], ia, ib, RT, r4, r2, f3p, p,
+        const float2 s2 = defect_patch<PER>(r3, &s_fin[ZP_DEF * PL], ia, ib, RS, r4, r2, f3p, p,
                                             fl, zlo, zhi);
         if (ZP_DEF == 0) {
           acc = s2;
