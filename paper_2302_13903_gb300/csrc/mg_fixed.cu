@@ -261,7 +261,7 @@ __device__ __forceinline__ long long fx_corrected(const long long* __restrict__ 
 }
 
 template <bool PER, bool ZERO_IN>
-__global__ void __launch_bounds__(FX_TX* FX_TY)
+__global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     k_fx_step(const long long* __restrict__ phi_in, long long* __restrict__ phi_out,
               const float* __restrict__ e, float c, const long long* __restrict__ F,
               float* __restrict__ r32, Grid g, FxBc bc, float factor, int cz,
