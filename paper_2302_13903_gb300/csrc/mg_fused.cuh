@@ -225,16 +225,23 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // (x, y) part of the trilinear prolongation of coarse plane K at the patch:
 // rows gyA (even: coarse rows Y-1, Y) and gyA+1 (odd: Y, Y+1), Y = gyA/2;
-// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.
+// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  Split in two so
+// that the loads of a plane can be issued a step before they are combined:
+// xy_load fetches the 3 x 4 coarse values (ghosts applied), xy_combine
+// weights them.
 // COH: the coarse values may have been written earlier in the same launch by
 // another CTA (the batched solver), so read them through L2 (ld.global.cg)
 // rather than the read-only path.
+struct Coarse12 {
+  float c[3][4];
+};
+
 template <bool PER, bool COH = false>
-__device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const FusedParams& p,
-                                           int gx4, int gyA, int K) {
+__device__ __forceinline__ Coarse12 xy_load(const float* __restrict__ ec, const FusedParams& p,
+                                            int gx4, int gyA, int K) {
   const int cnx = p.nx >> 1, cny = p.ny >> 1;
   const int X0 = gx4 >> 1, Y = gyA >> 1;
-  float xr[3][4];
+  Coarse12 r;
 #pragma unroll
   for (int yy = 0; yy < 3; ++yy) {
     const int Yc = Y - 1 + yy;
@@ -245,11 +252,9 @@ __device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const F
       else { Yi = Yc < 0 ? 0 : cny - 1; sy = p.s; }
     }
     const float* rowp = ec + ((size_t)K * cny + Yi) * cnx;
-    float c[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int Xc = X0 - 1 + a;
-      float v;
       const float* src;
       float sx = 1.f;
       if (Xc < 0 || Xc >= cnx) {
@@ -258,9 +263,17 @@ __device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const F
       } else {
         src = rowp + Xc;
       }
-      v = sx * (COH ? __ldcg(src) : __ldg(src));
-      c[a] = sy * v;
+      r.c[yy][a] = sy * (sx * (COH ? __ldcg(src) : __ldg(src)));
     }
+  }
+  return r;
+}
+
+__device__ __forceinline__ Patch xy_combine(const Coarse12& r) {
+  float xr[3][4];
+#pragma unroll
+  for (int yy = 0; yy < 3; ++yy) {
+    const float* c = r.c[yy];
     xr[yy][0] = 0.25f * c[0] + 0.75f * c[1];
     xr[yy][1] = 0.75f * c[1] + 0.25f * c[2];
     xr[yy][2] = 0.25f * c[1] + 0.75f * c[2];
@@ -272,6 +285,12 @@ __device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const F
   P.b.e = f2(0.75f * xr[1][0] + 0.25f * xr[2][0], 0.75f * xr[1][2] + 0.25f * xr[2][2]);
   P.b.o = f2(0.75f * xr[1][1] + 0.25f * xr[2][1], 0.75f * xr[1][3] + 0.25f * xr[2][3]);
   return P;
+}
+
+template <bool PER, bool COH = false>
+__device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const FusedParams& p,
+                                           int gx4, int gyA, int K) {
+  return xy_combine(xy_load<PER, COH>(ec, p, gx4, gyA, K));
 }
 
 // Row stride of a shared plane, in float4: the smallest RS >= RT with
@@ -366,6 +385,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   float2 acc = make_float2(0.f, 0.f);
   int ka = -1000000, kb = -1000000;  // coarse planes of the cached (x, y) interpolations
   Patch Pa = r1, Pb = r1;
+  int kpre = -1000000;  // coarse plane whose values were loaded a step ahead
+  Coarse12 pre;
 
   // One plane step.  J = (q - q_first) mod 4 fixes the ring slots and the
   // colours at compile time: q_first = z0 - HZ with z0 a multiple of 8.
@@ -399,10 +420,26 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         Patch PK, PN;
         if (K == kb) PK = Pb;
         else if (K == ka) PK = Pa;
-        else { PK = xy_interp<PER, COH>(ec, p, gx4w, gyAw, K); ka = kb; Pa = Pb; kb = K; Pb = PK; }
+        else {
+          PK = K == kpre ? xy_combine(pre) : xy_interp<PER, COH>(ec, p, gx4w, gyAw, K);
+          ka = kb; Pa = Pb; kb = K; Pb = PK;
+        }
         if (Kn == kb) PN = Pb;
         else if (Kn == ka) PN = Pa;
-        else { PN = xy_interp<PER, COH>(ec, p, gx4w, gyAw, Kn); ka = kb; Pa = Pb; kb = Kn; Pb = PN; }
+        else {
+          PN = Kn == kpre ? xy_combine(pre) : xy_interp<PER, COH>(ec, p, gx4w, gyAw, Kn);
+          ka = kb; Pa = Pb; kb = Kn; Pb = PN;
+        }
+        // an even plane 2K is followed by 2K+1, which needs coarse plane K+1:
+        // issue its loads now, to be combined in the next step
+        if ((QP & 1) == 0 && q + 1 <= q_last) {
+          int Kp = K + 1;
+          if (Kp >= cnz) Kp = PER ? Kp - cnz : cnz - 1;
+          if (Kp != kb && Kp != ka) {
+            pre = xy_load<PER, COH>(ec, p, gx4w, gyAw, Kp);
+            kpre = Kp;
+          }
+        }
         const float2 w0 = make_float2(0.75f, 0.75f), w1 = make_float2(wn, wn);
         r0.a.e = __ffma2_rn(w1, PN.a.e, __ffma2_rn(w0, PK.a.e, r0.a.e));
         r0.a.o = __ffma2_rn(w1, PN.a.o, __ffma2_rn(w0, PK.a.o, r0.a.o));
