@@ -12,6 +12,8 @@
 //           physical rule and the homogeneous rule below the top of a cycle.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "mg_bottom.cuh"
 #include "mg_device.cuh"
 #include "mg_internal.h"
@@ -25,23 +27,27 @@ using bottom::vcycle;
 
 template <typename T>
 __global__ void __launch_bounds__(kBottomThreads) k_bottom(BottomArgs<T> a) {
+  extern __shared__ double bottom_smem[];
+  T* sm = reinterpret_cast<T*>(bottom_smem);
   if (!a.fmg) {
-    vcycle(a, a.top, a.hom, true);
+    bottom::in_shared(a, sm, false, [&](const BottomArgs<T>& b) { vcycle(b, b.top, b.hom, true); });
     return;
   }
-  for (int l = a.top; l >= 1; --l) {
-    const Grid g{a.n[l], a.n[l], a.n[l]};
-    dev::restrict_range(a.f[l], a.f[l - 1], g, threadIdx.x, blockDim.x);
+  bottom::in_shared(a, sm, false, [&](const BottomArgs<T>& b) {
+    for (int l = b.top; l >= 1; --l) {
+      const Grid g{b.n[l], b.n[l], b.n[l]};
+      dev::restrict_range(b.f[l], b.f[l - 1], g, threadIdx.x, blockDim.x);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) dev::coarsest_one(b.f[0], b.u[0], b.h[0], b.bc[0]);
     __syncthreads();
-  }
-  if (threadIdx.x == 0) dev::coarsest_one(a.f[0], a.u[0], a.h[0], a.bc[0]);
-  __syncthreads();
-  for (int l = 1; l <= a.top; ++l) {
-    const Grid g{a.n[l], a.n[l], a.n[l]};
-    dev::prolong_range<T, true>(a.u[l - 1], a.u[l], g, a.bc[l - 1], 0, threadIdx.x, blockDim.x);
-    __syncthreads();
-    vcycle(a, l, a.bc[l], false);
-  }
+    for (int l = 1; l <= b.top; ++l) {
+      const Grid g{b.n[l], b.n[l], b.n[l]};
+      dev::prolong_range<T, true>(b.u[l - 1], b.u[l], g, b.bc[l - 1], 0, threadIdx.x, blockDim.x);
+      __syncthreads();
+      vcycle(b, l, b.bc[l], false);
+    }
+  });
 }
 
 }  // namespace
@@ -66,8 +72,20 @@ cudaError_t launch_bottom(T* const* u, T* const* f, const int* n, const double* 
   a.post = post;
   a.top = top;
   a.fmg = fmg ? 1 : 0;
+  const size_t smem = 2 * (size_t)bottom::cells_upto(a) * sizeof(T);
+  static std::atomic<int> configured[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !configured[dev].load()) {
+    // room for the largest case: levels up to 16^3 in FP64 (75 KB)
+    const cudaError_t e = cudaFuncSetAttribute(k_bottom<T>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(2 * 4681 * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    configured[dev].store(1);
+  }
   ++g_launches;
-  k_bottom<T><<<1, kBottomThreads, 0, s>>>(a);
+  k_bottom<T><<<1, kBottomThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -71,5 +71,40 @@ __device__ void vcycle(const BottomArgs<T>& a, int top, const Bc& bc_top, bool z
   }
 }
 
+// Cells of levels 0 .. top together.
+template <typename T>
+__host__ __device__ inline int cells_upto(const BottomArgs<T>& a) {
+  int total = 0;
+  for (int l = 0; l <= a.top; ++l) total += a.n[l] * a.n[l] * a.n[l];
+  return total;
+}
+
+// Runs `body` on copies of levels 0 .. top held in shared memory `smem` (room
+// for 2 cells_upto(a) values of T): the levels' f and u then have the latency
+// of shared memory, not of L2.  f[top] is copied in, and u[top] when its start
+// value is used (load_u); u[top] is copied back out.  Lower levels are
+// scratch of the cycle (their f comes from restriction, their u starts at 0).
+template <typename T, typename Body>
+__device__ void in_shared(const BottomArgs<T>& a, T* smem, bool load_u, Body body) {
+  BottomArgs<T> b = a;
+  const int total = cells_upto(a);
+  int off = 0;
+  for (int l = 0; l <= a.top; ++l) {
+    b.u[l] = smem + off;
+    b.f[l] = smem + total + off;
+    off += a.n[l] * a.n[l] * a.n[l];
+  }
+  const int top = a.top, ct = a.n[top] * a.n[top] * a.n[top];
+  for (int t = threadIdx.x; t < ct; t += blockDim.x) {
+    b.f[top][t] = a.f[top][t];
+    if (load_u) b.u[top][t] = a.u[top][t];
+  }
+  __syncthreads();
+  body(b);
+  __syncthreads();
+  for (int t = threadIdx.x; t < ct; t += blockDim.x) a.u[top][t] = b.u[top][t];
+  __syncthreads();
+}
+
 }  // namespace bottom
 }  // namespace mg

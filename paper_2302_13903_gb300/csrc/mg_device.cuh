@@ -70,6 +70,30 @@ __device__ __noinline__ T ghost(const T* u, int i, int j, int k, const Grid g,
   return v;
 }
 
+// (i, j, k) of flat index t in an nx * ny * (any) array: shifts when nx and ny
+// are powers of two (every level of a solve), divisions otherwise.
+struct Split {
+  int nx, ny, lx, lxy;
+  bool pow2;
+  __device__ __forceinline__ Split(int nx_, int ny_) : nx(nx_), ny(ny_) {
+    pow2 = (nx & (nx - 1)) == 0 && (ny & (ny - 1)) == 0;
+    lx = __ffs(nx) - 1;
+    lxy = lx + __ffs(ny) - 1;
+  }
+  __device__ __forceinline__ void operator()(long long t, int& i, int& j, int& k) const {
+    if (pow2) {
+      i = (int)(t & (nx - 1));
+      j = (int)((t >> lx) & (ny - 1));
+      k = (int)(t >> lxy);
+    } else {
+      i = (int)(t % nx);
+      const long long r = t / nx;
+      j = (int)(r % ny);
+      k = (int)(r / ny);
+    }
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ T fetch(const T* u, int i, int j, int k, const Grid& g,
                                    const Bc& bc) {
@@ -98,10 +122,10 @@ __device__ __forceinline__ void sor_range(T* u, const T* f, Grid g, Bc bc, T cu,
                                           int colour, long long t0, long long dt) {
   const int hx = g.nx >> 1;
   const long long total = (long long)hx * g.ny * g.nz;
+  const Split sp(hx, g.ny);
   for (long long t = t0; t < total; t += dt) {
-    const int m = (int)(t % hx);
-    const long long r = t / hx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    int m, j, k;
+    sp(t, m, j, k);
     const int i = 2 * m + ((j + k + colour) & 1);
     const size_t c = at(g, i, j, k);
     const T s = neighbour_sum(u, i, j, k, g, bc);
@@ -115,10 +139,10 @@ template <typename T>
 __device__ __forceinline__ void sor_red_zero_range(T* u, const T* f, Grid g, T cf, long long t0,
                                                    long long dt) {
   const long long total = g.cells();
+  const Split sp(g.nx, g.ny);
   for (long long t = t0; t < total; t += dt) {
-    const int i = (int)(t % g.nx);
-    const long long r = t / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    int i, j, k;
+    sp(t, i, j, k);
     u[t] = ((i + j + k) & 1) ? T(0) : cf * f[t];
   }
 }
@@ -130,10 +154,10 @@ __device__ __forceinline__ void defect_restrict_range(const T* u, const T* f, T*
                                                       T inv_h2, long long t0, long long dt) {
   const Grid gc{g.nx / 2, g.ny / 2, g.nz / 2};
   const long long total = gc.cells();
+  const Split sp(gc.nx, gc.ny);
   for (long long t = t0; t < total; t += dt) {
-    const int I = (int)(t % gc.nx);
-    const long long r = t / gc.nx;
-    const int J = (int)(r % gc.ny), K = (int)(r / gc.ny);
+    int I, J, K;
+    sp(t, I, J, K);
     T acc = 0;
     for (int c = 0; c < 2; ++c)
       for (int b = 0; b < 2; ++b)
@@ -152,10 +176,10 @@ __device__ __forceinline__ void restrict_range(const T* uf, T* uc, Grid gf, long
                                                long long dt) {
   const Grid gc{gf.nx / 2, gf.ny / 2, gf.nz / 2};
   const long long total = gc.cells();
+  const Split sp(gc.nx, gc.ny);
   for (long long t = t0; t < total; t += dt) {
-    const int I = (int)(t % gc.nx);
-    const long long r = t / gc.nx;
-    const int J = (int)(r % gc.ny), K = (int)(r / gc.ny);
+    int I, J, K;
+    sp(t, I, J, K);
     T acc = 0;
     for (int c = 0; c < 2; ++c)
       for (int b = 0; b < 2; ++b)
@@ -187,10 +211,10 @@ __device__ __forceinline__ void prolong_range(const T* uc, T* uf, Grid gf, Bc bc
                                               long long t0, long long dt) {
   const Grid gc{gf.nx / 2, gf.ny / 2, gf.nz / 2};
   const long long total = gc.cells();
+  const Split sp(gc.nx, gc.ny);
   for (long long t = t0; t < total; t += dt) {
-    const int I = (int)(t % gc.nx);
-    const long long r = t / gc.nx;
-    const int J = (int)(r % gc.ny), K = (int)(r / gc.ny);
+    int I, J, K;
+    sp(t, I, J, K);
     T c[3][3][3];
     if (I > 0 && I < gc.nx - 1 && J > 0 && J < gc.ny - 1 && K > 0 && K < gc.nz - 1) {
       const size_t sy = (size_t)gc.nx, sz = (size_t)gc.nx * gc.ny, o = at(gc, I, J, K);

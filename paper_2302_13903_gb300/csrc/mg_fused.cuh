@@ -431,8 +431,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
           ka = kb; Pa = Pb; kb = Kn; Pb = PN;
         }
         // an even plane 2K is followed by 2K+1, which needs coarse plane K+1:
-        // issue its loads now, to be combined in the next step
-        if ((QP & 1) == 0 && q + 1 <= q_last) {
+        // issue its loads now, to be combined in the next step (not in the
+        // batched solver, whose kernel has no registers to spare)
+        if (!COH && (QP & 1) == 0 && q + 1 <= q_last) {
           int Kp = K + 1;
           if (Kp >= cnz) Kp = PER ? Kp - cnz : cnz - 1;
           if (Kp != kb && Kp != ka) {
