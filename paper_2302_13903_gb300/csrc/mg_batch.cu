@@ -518,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
           a.post = 1;
           a.top = top;
           a.fmg = 0;
+          bottom::set_coefficients(a);
           const bool zg = (top < g.L - 1) || (P.cycle == 0 && c.inner_zero);
           bottom::vcycle(a, top, a.hom, zg);
           break;

@@ -72,6 +72,7 @@ cudaError_t launch_bottom(T* const* u, T* const* f, const int* n, const double* 
   a.post = post;
   a.top = top;
   a.fmg = fmg ? 1 : 0;
+  bottom::set_coefficients(a);
   const size_t smem = 2 * (size_t)bottom::cells_upto(a) * sizeof(T);
   static std::atomic<int> configured[64];
   int dev = 0;
