@@ -331,8 +331,9 @@ int mg_batch_graph(const mg_batch *batch);
  * (from the GPU's global timer at each grid-wide barrier): ms_by_type[k] for
  * k < n_types in the order source, mean, source-2, norm, first residual,
  * first-residual norm, fused down leg, bottom levels, fused up leg, max |e|,
- * fixed-point scale, conversion to fixed point, correction, residual,
- * stopping rule, phi sum, phi mean, phi conversion and mean removal.
+ * fixed-point scale, conversion to fixed point, outer step (correction and
+ * residual), stopping rule, phi sum, phi mean, phi conversion and mean
+ * removal.
  * Synchronises the device.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
 mg_status mg_batch_phase_ms(mg_batch *batch, double *ms_by_type, int n_types);
 

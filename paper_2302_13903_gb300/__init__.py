@@ -505,7 +505,7 @@ class Batch:
         return bool(lib().mg_batch_graph(self.ptr))
 
     PHASES = ["source", "mean", "source2", "norm", "r0", "r0_norm", "down", "bottom", "up",
-              "max_e", "set_fixed_point", "to_fixed_point", "correct", "residual", "stop_rule",
+              "max_e", "set_fixed_point", "to_fixed_point", "outer_step", "stop_rule",
               "phi_sum", "phi_mean", "phi_sub"]
 
     def phase_ms(self):

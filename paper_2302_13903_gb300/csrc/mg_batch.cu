@@ -66,6 +66,9 @@ struct GridDev {
   double maxf, two_S;
   long long b2;  // FIXED: round(2 b 2^S), the integer ghost offset
   int in_fx, fxbad;
+  long long* fx2;      // second integer buffer (the outer step writes the other one)
+  int cur;             // which buffer holds PHI: 0 phi's own storage, 1 fx2
+  int part0, ntile;    // this grid's tiles of the fixed-point step (partials in part3)
 };
 
 enum PhaseType : int {
@@ -80,9 +83,8 @@ enum PhaseType : int {
   PH_UP,           // tile: fused up leg on level size `n`
   PH_EMAX,         // chunk: max |e| (first outer iteration)
   PH_SETFX,        // grid: the fixed-point scale 2^S
-  PH_TOFX,         // chunk: F = round(h^2 f 2^S), PHI = round(e 2^S / scale)
-  PH_FXCORR,       // chunk: PHI += round(e 2^S / scale)
-  PH_FXRES,        // chunk: exact integer residual -> r32, partial sum r32^2
+  PH_TOFX,         // chunk: F = round(h^2 f 2^S)
+  PH_FXSTEP,       // tile: PHI' = PHI + round(e 2^S / scale), exact residual -> r32
   PH_FIN,          // grid: stopping rule, history
   PH_PSUM,         // chunk: partial sum phi (exact integer sum in fixed point)
   PH_PMEAN,        // grid: mean of phi
@@ -108,6 +110,7 @@ struct Ctl {
   double* part;        // one slot per chunk
   double* part2;       // a second slot per chunk (maxima)
   long long* ipart;    // two integer slots per chunk (exact sums of PHI: hi, lo)
+  double* part3;       // one slot per tile of the fixed-point step
   double* hist;        // [ngrids][hist_cap]
   unsigned* counters;  // one per phase
   unsigned* bar_count;
@@ -202,17 +205,6 @@ __device__ long long block_isum(long long v) {
   return r;
 }
 
-// Integer neighbour of cell (i, j, k) along one axis on the fixed-point grid:
-// inside the level the cell itself, outside it the rule's ghost (periodic
-// wrap, zero gradient: the cell, fixed b: round(2 b 2^S) - the cell).
-__device__ __forceinline__ long long fx_nb(const long long* __restrict__ q, long long self,
-                                           int inside, long long o_in, long long o_wrap, int bc,
-                                           long long b2) {
-  if (inside) return q[o_in];
-  if (bc == BC_PERIODIC) return q[o_wrap];
-  return bc == BC_ZEROGRAD ? self : b2 - self;
-}
-
 // One chunk of the finest level: cells [c * kChunk, min(N, (c + 1) kChunk)).
 // The grid's fields are read once into registers (the loop's stores could
 // otherwise alias them).
@@ -223,9 +215,10 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
   const int N = n * n * n;  // <= 1024^3 = 2^30
   const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
   const int F = g.L - 1;
-  double* __restrict__ phi = g.phi;
+  double* phi = g.phi;
   double* __restrict__ f64 = g.f64;
-  long long* __restrict__ PHI = reinterpret_cast<long long*>(g.phi);
+  // the integer potential: in phi's own storage or in the second buffer
+  const long long* PHI = g.cur ? g.fx2 : reinterpret_cast<const long long*>(g.phi);  // may be phi
   long long* __restrict__ FX = reinterpret_cast<long long*>(g.f64);
   const double* __restrict__ rho = g.rho;
   float* __restrict__ r32 = g.f32[F];
@@ -235,16 +228,9 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
   const int bc = g.bc;
   const bool fx = g.in_fx != 0;
   const double two_S = g.two_S;
-  const float ce = (float)(two_S / g.scale);  // e -> integer correction
-  const long long b2 = g.b2;
   const double inv_fn = 1.0 / g.fnorm;
-  // r32 = r / rn_previous, r = R 2^-S / h^2
-  const float rfac = (float)(1.0 / (g.rn * h * h * two_S));
   double acc = 0.0, mx = 0.0;
-  float af = 0.f;  // FP32 sum of r32^2 over at most 8 cells, then added to acc
-  int nf = 0;
   long long s_hi = 0, s_lo = 0;
-  bool bad = false;
   // unrolled so that each thread has several independent loads in flight
 #pragma unroll 4
   for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) {
@@ -271,32 +257,6 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
       mx = fmax(mx, (double)fabsf(e32[t]));
     } else if (TYPE == PH_TOFX) {
       FX[t] = __double2ll_rn(f64[t] * (h * h * two_S));
-      const long long v = __float2ll_rn(e32[t] * ce);
-      PHI[t] = v;
-      bad |= (v > (1LL << 60)) || (v < -(1LL << 60));
-    } else if (TYPE == PH_FXCORR) {
-      const long long v = PHI[t] + __float2ll_rn(e32[t] * ce);
-      PHI[t] = v;
-      bad |= (v > (1LL << 60)) || (v < -(1LL << 60));
-    } else if (TYPE == PH_FXRES) {
-      const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
-      const long long self = PHI[t];
-      const int sx = 1, sy = n, sz = n * n;
-      const long long xm = fx_nb(PHI, self, i > 0, t - sx, t + (n - 1) * sx, bc, b2);
-      const long long xp = fx_nb(PHI, self, i < n - 1, t + sx, t - (n - 1) * sx, bc, b2);
-      const long long ym = fx_nb(PHI, self, j > 0, t - sy, t + (n - 1) * sy, bc, b2);
-      const long long yp = fx_nb(PHI, self, j < n - 1, t + sy, t - (n - 1) * sy, bc, b2);
-      const long long zm = fx_nb(PHI, self, k > 0, t - sz, t + (long long)(n - 1) * sz, bc, b2);
-      const long long zp = fx_nb(PHI, self, k < n - 1, t + sz, t - (long long)(n - 1) * sz, bc, b2);
-      const long long R = FX[t] - (((xm + xp) + (ym + yp)) + (zm + zp) - 6 * self);
-      const float r = __ll2float_rn(R) * rfac;
-      r32[t] = r;
-      af = fmaf(r, r, af);
-      if (++nf == 8) {
-        acc += af;
-        af = 0.f;
-        nf = 0;
-      }
     } else if (TYPE == PH_PSUM) {
       if (fx) {
         const long long v = PHI[t];
@@ -310,9 +270,7 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
       else phi[t] -= mean;
     }
   }
-  if (TYPE == PH_FXRES) acc += af;
-  if (TYPE == PH_SRC || TYPE == PH_SRC2 || TYPE == PH_R0 || TYPE == PH_FXRES ||
-      (TYPE == PH_PSUM && !fx)) {
+  if (TYPE == PH_SRC || TYPE == PH_SRC2 || TYPE == PH_R0 || (TYPE == PH_PSUM && !fx)) {
     const double b = block_sum(acc);
     if (threadIdx.x == 0) c.part[g.chunk0 + chunk] = b;
   }
@@ -326,9 +284,6 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
       c.ipart[2 * (g.chunk0 + chunk)] = bh;
       c.ipart[2 * (g.chunk0 + chunk) + 1] = bl;
     }
-  }
-  if (TYPE == PH_TOFX || TYPE == PH_FXCORR) {
-    if (bad) atomicOr(&g.fxbad, 1);
   }
 }
 
@@ -361,11 +316,148 @@ __device__ double chunk_total(const Ctl& c, const GridDev& g) {
   return s;
 }
 
+// Tile sizes of the fixed-point step: TX x TY columns, FXCZ planes.
+__host__ __device__ inline int fx_tx(int n) { return n < 32 ? n : 32; }
+__host__ __device__ inline int fx_ty(int n) { return n < 16 ? n : 16; }
+__host__ __device__ inline int fx_cz(int n) { return n < 32 ? n : 32; }
+constexpr int kFxCols = 3;  // columns per thread (32 x 16 = 512 <= 3 x 216)
+
+// One tile of the fused outer step on the integer grid (z-marching, as the
+// single-grid kernel): PHI' = PHI + round(e 2^S / scale) (PHI = 0 on the
+// first step), R = F - (sum_nb PHI' - 6 PHI') exactly, r32 = R / (rn h^2 2^S)
+// with one partial sum of r32^2 per tile; PHI' goes to the other buffer.
+// Each thread owns up to three columns, keeping PHI' of planes z-1, z, z+1 in
+// registers; x / y neighbours come from the current plane in shared memory,
+// whose halo the first threads load and correct.
+__device__ void fx_tile_item(const Ctl& c, GridDev& g, const Item& I, bool zero_in,
+                             float4* smem) {
+  const int n = g.n, TX = fx_tx(n), TY = fx_ty(n), CZ = fx_cz(n);
+  const int W = TX + 2, H = TY + 2, cols = TX * TY, nhalo = 2 * W + 2 * TY;
+  const int x0 = I.a * TX, y0 = I.b * TY, z0 = I.c * CZ, z1 = z0 + CZ;
+  const int F = g.L - 1;
+  const bool per = g.bc == BC_PERIODIC;
+  const long long* __restrict__ pin =
+      g.cur ? g.fx2 : reinterpret_cast<const long long*>(g.phi);
+  long long* __restrict__ pout = g.cur ? reinterpret_cast<long long*>(g.phi) : g.fx2;
+  const long long* __restrict__ FX = reinterpret_cast<const long long*>(g.f64);
+  const float* __restrict__ e = g.u32[F];
+  float* __restrict__ r32 = g.f32[F];
+  const float ce = (float)(g.two_S / g.scale);
+  const float rfac = (float)(1.0 / (g.rn * g.h * g.h * g.two_S));
+  const long long b2 = g.b2;
+  const int bc = g.bc;
+  const size_t plane = (size_t)n * n;
+  long long* P = reinterpret_cast<long long*>(smem);  // [2][H][W]
+  auto corrected = [&](size_t o) -> long long {
+    long long v = zero_in ? 0 : pin[o];
+    return v + __float2ll_rn(e[o] * ce);
+  };
+  auto wrapq = [&](int q) { return q < 0 ? q + n : (q >= n ? q - n : q); };
+  // this thread's columns
+  int ci[kFxCols], cj[kFxCols];
+  bool cact[kFxCols];
+#pragma unroll
+  for (int q = 0; q < kFxCols; ++q) {
+    const int col = threadIdx.x + q * (int)blockDim.x;
+    cact[q] = col < cols;
+    ci[q] = x0 + (cact[q] ? col % TX : 0);
+    cj[q] = y0 + (cact[q] ? col / TX : 0);
+  }
+  // this thread's halo cell (rows -1 and TY over the full width, columns -1
+  // and TX over the tile's rows)
+  const bool halo = (int)threadIdx.x < nhalo;
+  int ha = 0, hb = 0;
+  if (halo) {
+    const int h = threadIdx.x;
+    if (h < W) { ha = h; hb = 0; }
+    else if (h < 2 * W) { ha = h - W; hb = H - 1; }
+    else if (h < 2 * W + TY) { ha = 0; hb = h - 2 * W + 1; }
+    else { ha = W - 1; hb = h - 2 * W - TY + 1; }
+  }
+  int hx = x0 - 1 + ha, hy = y0 - 1 + hb;
+  bool h_in = halo;
+  if (per) {
+    hx = wrapq(hx);
+    hy = wrapq(hy);
+  } else {
+    h_in = h_in && hx >= 0 && hx < n && hy >= 0 && hy < n;
+  }
+  const size_t hcol = (size_t)hy * n + hx;
+  auto own = [&](int q, int z) -> long long {
+    if (!cact[q]) return 0;
+    if (!per && (z < 0 || z >= n)) return 0;
+    return corrected((size_t)(per ? wrapq(z) : z) * plane + (size_t)cj[q] * n + ci[q]);
+  };
+  long long zm[kFxCols], self[kFxCols];
+#pragma unroll
+  for (int q = 0; q < kFxCols; ++q) {
+    zm[q] = own(q, z0 - 1);
+    self[q] = own(q, z0);
+  }
+  long long hcur = h_in ? corrected((size_t)z0 * plane + hcol) : 0;
+  float acc = 0.f;
+  bool bad = false;
+  for (int z = z0; z < z1; ++z) {
+    const int buf = (z - z0) & 1;
+    long long* Pb = P + (size_t)buf * H * W;
+    long long zp[kFxCols], Fo[kFxCols];
+#pragma unroll
+    for (int q = 0; q < kFxCols; ++q) {
+      zp[q] = own(q, z + 1);
+      Fo[q] = cact[q] ? FX[(size_t)z * plane + (size_t)cj[q] * n + ci[q]] : 0;
+    }
+    const long long hnext = (h_in && z + 1 < z1) ? corrected((size_t)(z + 1) * plane + hcol) : 0;
+#pragma unroll
+    for (int q = 0; q < kFxCols; ++q) {
+      if (!cact[q]) continue;
+      Pb[(cj[q] - y0 + 1) * W + (ci[q] - x0 + 1)] = self[q];
+      pout[(size_t)z * plane + (size_t)cj[q] * n + ci[q]] = self[q];
+      bad |= (self[q] > (1LL << 60)) || (self[q] < -(1LL << 60));
+    }
+    if (halo) Pb[hb * W + ha] = hcur;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kFxCols; ++q) {
+      if (!cact[q]) continue;
+      const int i = ci[q], j = cj[q], a = i - x0 + 1, b = j - y0 + 1;
+      const long long sv = self[q];
+      long long xm = Pb[b * W + a - 1], xp = Pb[b * W + a + 1];
+      long long ym = Pb[(b - 1) * W + a], yp = Pb[(b + 1) * W + a];
+      long long zmv = zm[q], zpv = zp[q];
+      if (!per) {
+        const long long gh = bc == BC_ZEROGRAD ? sv : b2 - sv;
+        if (i == 0) xm = gh;
+        if (i == n - 1) xp = gh;
+        if (j == 0) ym = gh;
+        if (j == n - 1) yp = gh;
+        if (z == 0) zmv = gh;
+        if (z == n - 1) zpv = gh;
+      }
+      const size_t o = (size_t)z * plane + (size_t)j * n + i;
+      const long long R = Fo[q] - (((xm + xp) + (ym + yp)) + (zmv + zpv) - 6 * sv);
+      const float r = __ll2float_rn(R) * rfac;
+      r32[o] = r;
+      acc = fmaf(r, r, acc);
+      zm[q] = sv;
+      self[q] = zp[q];
+    }
+    hcur = hnext;
+    // the next plane writes the other half of P; this one is rewritten two
+    // planes on, after every thread has passed the next barrier
+  }
+  if (bad) atomicOr(&g.fxbad, 1);
+  const double b = block_sum((double)acc);
+  if (threadIdx.x == 0) c.part3[g.part0 + (I.c * (n / TY) + I.b) * (n / TX) + I.a] = b;
+}
+
 // Stopping rule of the single-grid solve, after one outer iteration.
 __device__ void fin_item(const Ctl& c, GridDev& g, int gi) {
   const double N = (double)g.n * g.n * g.n;
-  // the residual pass summed the squares of r32 = r / rn_previous
-  const double rn = sqrt(chunk_total(c, g) / N) * g.rn;
+  // the outer step summed the squares of r32 = r / rn_previous, per tile
+  double tot = 0.0;
+  for (int q = 0; q < g.ntile; ++q) tot += c.part3[g.part0 + q];
+  const double rn = sqrt(tot / N) * g.rn;
+  g.cur ^= 1;  // the step wrote the other integer buffer
   double r = rn / g.fnorm;
   if (g.fxbad) r = NAN;  // the integers passed 2^60: the solve diverged
   g.scale = 1.0 / g.rn;  // the scale the residual just written used
@@ -444,10 +536,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
         case PH_R0: chunk_item<PH_R0>(c, g, I.a); break;
         case PH_EMAX: chunk_item<PH_EMAX>(c, g, I.a); break;
         case PH_TOFX: chunk_item<PH_TOFX>(c, g, I.a); break;
-        case PH_FXCORR: chunk_item<PH_FXCORR>(c, g, I.a); break;
-        case PH_FXRES: chunk_item<PH_FXRES>(c, g, I.a); break;
         case PH_SETFX:
           if (threadIdx.x == 0) setfx_item(c, g);
+          break;
+        case PH_FXSTEP:
+          fx_tile_item(c, g, I, P.cycle != 0, smem);
           break;
         case PH_PSUM: chunk_item<PH_PSUM>(c, g, I.a); break;
         case PH_PSUB: chunk_item<PH_PSUB>(c, g, I.a); break;
@@ -574,6 +667,7 @@ struct mg_batch {
   double* d_part = nullptr;
   double* d_part2 = nullptr;
   long long* d_ipart = nullptr;
+  double* d_part3 = nullptr;
   double* d_hist = nullptr;
   double* h_hist = nullptr;  // pinned
   unsigned* d_counters = nullptr;
@@ -583,7 +677,7 @@ struct mg_batch {
   unsigned long long* d_ptime = nullptr;
   std::vector<Phase> host_phases;
   int* h_err = nullptr;
-  int nphases = 0, nitems = 0, nchunks = 0, hist_cap = 64;
+  int nphases = 0, nitems = 0, nchunks = 0, ntiles = 0, hist_cap = 64;
   int blocks = 0;
   long long cells = 0;
   // the per-solve work captured once as a CUDA graph and replayed
@@ -657,6 +751,17 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
     p.count = (int)items.size() - p.first;
     if (p.count > 0) phases.push_back(p);
   };
+  auto add_fx_phase = [&](int zero_in) {
+    Phase p{PH_FXSTEP, 0, (int)items.size(), 0, zero_in};
+    for (int g = 0; g < G; ++g) {
+      const int n = b->host_grids[g].n, tx = fx_tx(n), ty = fx_ty(n), cz = fx_cz(n);
+      for (int z = 0; z < n / cz; ++z)
+        for (int y = 0; y < n / ty; ++y)
+          for (int x = 0; x < n / tx; ++x) items.push_back(Item{g, x, y, z});
+    }
+    p.count = (int)items.size() - p.first;
+    phases.push_back(p);
+  };
   add_chunk_phase(PH_SRC);
   add_grid_phase(PH_MEANFIN, 0);
   add_chunk_phase(PH_SRC2);
@@ -674,10 +779,8 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
       add_chunk_phase(PH_EMAX);
       add_grid_phase(PH_SETFX, 0);
       add_chunk_phase(PH_TOFX);
-    } else {
-      add_chunk_phase(PH_FXCORR);
     }
-    add_chunk_phase(PH_FXRES);
+    add_fx_phase(o == 0 ? 1 : 0);  // the first step starts from PHI = 0
     add_grid_phase(PH_FIN, 0);
   }
   add_chunk_phase(PH_PSUM);
@@ -702,6 +805,7 @@ cudaError_t enqueue_solve(mg_batch* b, cudaStream_t s) {
   c.part = b->d_part;
   c.part2 = b->d_part2;
   c.ipart = b->d_ipart;
+  c.part3 = b->d_part3;
   c.hist = b->d_hist;
   c.counters = b->d_counters;
   c.bar_count = b->d_bar;
@@ -765,7 +869,7 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
   b->opts = o;
   cudaGetDevice(&b->device);
   b->host_grids.resize(n);
-  int chunk0 = 0;
+  int chunk0 = 0, tile0 = 0;
   bool ok = true;
   for (int g = 0; g < n && ok; ++g) {
     GridDev& d = b->host_grids[g];
@@ -794,8 +898,14 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
     d.chunk0 = chunk0;
     d.nchunk = (int)((N + kChunk - 1) / kChunk);
     chunk0 += d.nchunk;
+    d.fx2 = balloc<long long>(b, N);
+    ok = ok && d.fx2;
+    d.part0 = tile0;
+    d.ntile = (d.n / fx_tx(d.n)) * (d.n / fx_ty(d.n)) * (d.n / fx_cz(d.n));
+    tile0 += d.ntile;
   }
   b->nchunks = chunk0;
+  b->ntiles = tile0;
   std::vector<Phase> phases;
   std::vector<Item> items;
   if (ok) build_phases(b, phases, items);
@@ -808,6 +918,7 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
     b->d_part = balloc<double>(b, b->nchunks);
     b->d_part2 = balloc<double>(b, b->nchunks);
     b->d_ipart = balloc<long long>(b, 2 * (size_t)b->nchunks);
+    b->d_part3 = balloc<double>(b, b->ntiles);
     b->d_hist = balloc<double>(b, (size_t)n * b->hist_cap);
     b->d_counters = balloc<unsigned>(b, b->nphases);
     b->d_bar = balloc<unsigned>(b, 2);
@@ -815,6 +926,7 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
     b->d_active = balloc<int>(b, b->nphases);
     b->d_ptime = balloc<unsigned long long>(b, b->nphases + 1);
     ok = b->d_grids && b->d_phases && b->d_items && b->d_part && b->d_part2 && b->d_ipart &&
+         b->d_part3 &&
          b->d_hist && b->d_counters &&
          b->d_bar && b->d_err && b->d_active && b->d_ptime;
     b->host_phases = phases;
@@ -883,6 +995,7 @@ mg_status mg_batch_solve(mg_batch* b, const double* const* rho, const double* fo
     d.b2 = 0;
     d.in_fx = 0;
     d.fxbad = 0;
+    d.cur = 0;
     b->h_grids[g] = d;
   }
   cudaError_t e = cudaSuccess;
