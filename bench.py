@@ -60,10 +60,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def src_sha() -> str:
+# Sources that define each kernel class (its device program and launcher, and
+# the headers they include); a traffic figure applies while these are unchanged.
+KERNEL_SOURCES = {
+    "fused_up": ["mg_fused.cuh", "mg_fused.cu", "mg_internal.h"],
+    "fused_down": ["mg_fused.cuh", "mg_fused.cu", "mg_internal.h"],
+    "outer_residual": ["mg_fixed.cu", "mg_device.cuh", "mg_internal.h"],
+}
+
+
+def src_sha(kernel: str = None) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2302_13903_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    names = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(d))
+    for fn in names:
         h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:12]
 
@@ -74,7 +84,7 @@ def ncu_traffic(kernel: str, prec: str, n: int):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    sha = src_sha()
+    sha = src_sha(kernel)
     best = None
     for line in open(p):
         f = line.split()

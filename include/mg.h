@@ -294,12 +294,13 @@ typedef struct mg_batch mg_batch;
 /* Create a batch of n grids: grid g has dims[3g..3g+2] cells (cubic, a power
  * of two from 2 to 1024), spacing dx[g], rule bcs[g] (periodic, fixed or zero
  * gradient; fixed_values[g] is b for a fixed rule, NULL means 0).  Every grid
- * is solved by the mixed-precision method (an FP64 defect-correction loop --
- * source, residual, correction and norms in FP64 -- around FP32 V(1,1)
- * cycles): opts->prec must be MG_MIXED, pre = post = 1, mode_fmg = 1 (phi
- * starts at 0), inner_fmg = 0; max_cycles (outer iterations, <= 64) and
- * inner_cycles (V-cycles per outer iteration) are shared.  All level storage
- * is allocated here.  Errors: MG_ERR_ARG, MG_ERR_OOM. */
+ * is solved by the mixed-precision method (a defect-correction loop whose
+ * source, norms and residual are FP64-accurate -- the residual exact in 64-bit
+ * fixed point, as in mg_solve -- around FP32 V(1,1) cycles): opts->prec must
+ * be MG_MIXED, pre = post = 1, mode_fmg = 1 (phi starts at 0), inner_fmg = 0;
+ * max_cycles (outer iterations, <= 64) and inner_cycles (V-cycles per outer
+ * iteration after the one from a zero correction, 0..16) are shared.  All
+ * level storage is allocated here.  Errors: MG_ERR_ARG, MG_ERR_OOM. */
 mg_status mg_batch_create(int n, const int *dims, const double *dx, const mg_bc *bcs,
                           const double *fixed_values, const mg_opts *opts, mg_batch **batch);
 

@@ -720,7 +720,7 @@ void free_batch(mg_batch* b) {
 }
 
 // The phase list: source, first residual, max_cycles outer iterations of
-// (inner_cycles V-cycles, correction, residual, stopping rule), mean removal.
+// (1 + inner_cycles V-cycles, outer step, stopping rule), mean removal.
 void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& items) {
   const int G = b->ngrids;
   auto add_chunk_phase = [&](int type) {
@@ -768,7 +768,8 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
   add_grid_phase(PH_NORMFIN, 0);
   add_chunk_phase(PH_R0);
   add_grid_phase(PH_R0FIN, 0);
-  const int inner = std::max(1, b->opts.inner_cycles);
+  // one V-cycle from a zero correction, then inner_cycles more (as mg_solve)
+  const int inner = 1 + b->opts.inner_cycles;
   for (int o = 0; o < b->opts.max_cycles; ++o) {
     for (int k = 0; k < inner; ++k) {
       for (int n = nmax; n >= kFusedMinN; n >>= 1) add_tile_phase(PH_DOWN, n, k);
@@ -850,7 +851,7 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
   if (opts) o = *opts;
   else mg_opts_init(&o);
   if (o.prec != MG_MIXED || o.pre != 1 || o.post != 1 || !o.mode_fmg || o.inner_fmg ||
-      o.max_cycles < 1 || o.max_cycles > 64 || o.inner_cycles < 1 || o.inner_cycles > 16) {
+      o.max_cycles < 1 || o.max_cycles > 64 || o.inner_cycles < 0 || o.inner_cycles > 16) {
     g_batch_err = "mg_batch_create: the batched solve runs MG_MIXED, V(1,1), FMG mode, inner "
                   "V-cycles from a zero correction (inner_fmg = 0), 1..64 outer iterations";
     return MG_ERR_ARG;
