@@ -344,8 +344,9 @@ const char *mg_batch_last_error(const mg_batch *batch);
 size_t mg_faces_count(int nx, int ny, int nz);
 
 /* Autotune the launch shapes of this context's hot kernels on `stream`: for
- * every level the fused FP32 legs run on (tile width 32 or 64 cells,
- * 8..64 z-planes per CTA) and for the fixed-point outer step (4..64 planes),
+ * every level the fused FP32 legs run on (tiles of 32 or 64 cells by 16 or 32
+ * rows, 8..64 z-planes per CTA) and for the fixed-point outer step (4..64
+ * planes),
  * each candidate is timed with CUDA events on the context's own buffers and
  * the fastest kept.  Choices are shared by every context of the same shape
  * in the process (so they give identical bits) and, when the environment
@@ -355,11 +356,13 @@ size_t mg_faces_count(int nx, int ny, int nz);
  * Errors: MG_ERR_ARG, MG_ERR_CUDA. */
 mg_status mg_ctx_autotune(mg_ctx *ctx, void *stream);
 
-/* The shape chosen for a kernel class on a level (MG_K_FUSED_DOWN,
+/* The shape (tile width tx, height ty, planes cz) chosen for a kernel class on
+ * a level (MG_K_FUSED_DOWN,
  * MG_K_FUSED_UP, MG_K_SOR for extra fused smoothing steps, MG_K_OUTER_RESIDUAL
  * for the fixed-point step on the finest level); 0 means the built-in
  * choice. */
-mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, int *cz);
+mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, int *ty,
+                             int *cz);
 
 /* ---------------------------------------------------------------------------
  * Serving loop.  Requests (solves of any supported size and boundary rule)

@@ -167,7 +167,8 @@ def lib():
             L.mg_faces_count.restype = sz
             L.mg_ctx_autotune.argtypes = [p, p]
             L.mg_ctx_autotune.restype = i
-            L.mg_ctx_tile_config.argtypes = [p, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            L.mg_ctx_tile_config.argtypes = [p, i, i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                             ctypes.POINTER(i)]
             L.mg_ctx_tile_config.restype = i
             L.mg_required_bytes.argtypes = [i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
             L.mg_required_bytes.restype = i
@@ -275,18 +276,19 @@ class Solver:
         _check(lib().mg_ctx_autotune(self.ctx, _stream_ptr(stream)), self.ctx)
 
     def tile_configs(self):
-        """{"fused_down" | "fused_up" | "sor" | "outer_residual": {level: (tx, cz)}} (0: built-in)."""
+        """{"fused_down" | "fused_up" | "sor" | "outer_residual": {level: (tx, ty, cz)}}
+        (0: built-in)."""
         out = {}
         levels = self.n.bit_length()
         for name in ("fused_down", "fused_up", "sor", "outer_residual"):
             k = KERNELS.index(name)
             per = {}
             for l in range(levels):
-                tx, cz = ctypes.c_int(0), ctypes.c_int(0)
-                _check(lib().mg_ctx_tile_config(self.ctx, l, k, ctypes.byref(tx), ctypes.byref(cz)),
-                       self.ctx)
-                if tx.value or cz.value:
-                    per[l] = (tx.value, cz.value)
+                tx, ty, cz = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+                _check(lib().mg_ctx_tile_config(self.ctx, l, k, ctypes.byref(tx), ctypes.byref(ty),
+                                                ctypes.byref(cz)), self.ctx)
+                if tx.value or ty.value or cz.value:
+                    per[l] = (tx.value, ty.value, cz.value)
             out[name] = per
         return out
 

@@ -32,18 +32,22 @@ cudaError_t launch_t(const float* ui, float* uo, const float* f, const float* ec
 }
 
 // Built-in shape: tiles of 64 x 16 for levels >= 64 cells wide, 32 x 16 for
-// 32; the z-chunk is the largest of 64, 32, 16, 8 planes that still gives two
+// 32 (32 rows when asked); the z-chunk is the largest of 64, 32, 16, 8 planes that still gives two
 // CTAs per SM.  A nonzero cfg field (checked by fused_cfg_ok) replaces it.
 template <int MODE, bool ZERO, bool PER>
 cudaError_t dispatch_t(const float* ui, float* uo, const float* f, const float* ec, float* fc,
                        FusedParams p, TileCfg cfg, cudaStream_t s) {
   const long long sms = 152;
-  const int tx = cfg.tx ? cfg.tx : (p.nx >= 64 ? 64 : 32), ty = 16;
+  const int tx = cfg.tx ? cfg.tx : (p.nx >= 64 ? 64 : 32), ty = cfg.ty ? cfg.ty : 16;
   const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
   int cz = 64;
   while (cz > 8 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
   if (cfg.cz) cz = cfg.cz;
   p.cz = cz < p.nz ? cz : p.nz;
+  if (ty == 32) {
+    if (tx == 64) return launch_t<MODE, ZERO, PER, 64, 32>(ui, uo, f, ec, fc, p, s);
+    return launch_t<MODE, ZERO, PER, 32, 32>(ui, uo, f, ec, fc, p, s);
+  }
   if (tx == 64) return launch_t<MODE, ZERO, PER, 64, 16>(ui, uo, f, ec, fc, p, s);
   return launch_t<MODE, ZERO, PER, 32, 16>(ui, uo, f, ec, fc, p, s);
 }
@@ -89,7 +93,8 @@ bool fused_cfg_ok(Grid g, TileCfg cfg) {
   const bool tx_ok = cfg.tx == 0 || (cfg.tx == 32 && g.nx % 32 == 0) ||
                      (cfg.tx == 64 && g.nx % 64 == 0);
   const bool cz_ok = cfg.cz == 0 || (cfg.cz >= 8 && cfg.cz % 8 == 0 && cfg.cz <= 1024);
-  return tx_ok && cz_ok;
+  const bool ty_ok = cfg.ty == 0 || cfg.ty == 16 || (cfg.ty == 32 && g.ny % 32 == 0);
+  return tx_ok && cz_ok && ty_ok;
 }
 
 cudaError_t launch_fused_down(const float* u_in, float* u_out, const float* f, float* fc, Grid g,

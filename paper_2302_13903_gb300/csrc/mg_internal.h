@@ -126,10 +126,12 @@ cudaError_t launch_bottom(T* const* u, T* const* f, const int* n, const double* 
 // writes u_out (distinct buffers).
 
 // Launch shape of a z-marching kernel: tile width in cells (fused kernels:
-// 32 or 64) and z-planes per CTA.  A zero field takes the built-in choice.
+// 32 or 64), z-planes per CTA and tile height (fused kernels: 16 or 32).  A
+// zero field takes the built-in choice.
 struct TileCfg {
   int tx = 0;
   int cz = 0;
+  int ty = 0;  // tile height in rows (16 or 32; 0: 16)
 };
 
 // Whether the fused kernels handle this level (width >= 32, homogeneous rule).

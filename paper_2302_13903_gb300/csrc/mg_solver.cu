@@ -834,8 +834,8 @@ void tune_load_locked() {
   if (!fp) return;
   TuneKey k;
   mg::TileCfg v;
-  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d %d %d", &k.sms, &k.major, &k.minor, &k.kind,
-                     &k.nx, &k.ny, &k.nz, &k.periodic, &v.tx, &v.cz) == 10)
+  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d %d %d %d", &k.sms, &k.major, &k.minor, &k.kind,
+                     &k.nx, &k.ny, &k.nz, &k.periodic, &v.tx, &v.cz, &v.ty) == 11)
     g_tune[k] = v;
   std::fclose(fp);
 }
@@ -846,8 +846,8 @@ void tune_store_locked(const TuneKey& k, mg::TileCfg v) {
   if (!path || !*path) return;
   FILE* fp = std::fopen(path, "a");
   if (!fp) return;
-  std::fprintf(fp, "%d %d %d %d %d %d %d %d %d %d\n", k.sms, k.major, k.minor, k.kind, k.nx, k.ny,
-               k.nz, k.periodic, v.tx, v.cz);
+  std::fprintf(fp, "%d %d %d %d %d %d %d %d %d %d %d\n", k.sms, k.major, k.minor, k.kind, k.nx,
+               k.ny, k.nz, k.periodic, v.tx, v.cz, v.ty);
   std::fclose(fp);
 }
 
@@ -922,9 +922,11 @@ void autotune(mg_ctx* c, cudaStream_t s) {
           best = hit->second;
         } else {
           float best_ms = 1e30f;
-          for (int tx : {32, 64}) {
-            for (int cz : {8, 16, 32, 64}) {
-              const mg::TileCfg cand{tx, cz};
+          for (int cand_i = 0; cand_i < 16; ++cand_i) {
+            {
+              const int tx = (cand_i & 1) ? 64 : 32, ty = (cand_i & 2) ? 32 : 16;
+              const int cz = 8 << (cand_i >> 2);  // 8, 16, 32, 64
+              const mg::TileCfg cand{tx, cz, ty};
               if (cz > g.nz || !mg::fused_cfg_ok(g, cand)) continue;
               const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
                 if (kind == TUNE_DOWN)
@@ -1048,8 +1050,8 @@ mg_status mg_ctx_autotune(mg_ctx* c, void* stream) {
   return MG_OK;
 }
 
-mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, int* cz) {
-  if (!c || !tx || !cz || level < 0 || level >= c->L) return MG_ERR_ARG;
+mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, int* ty, int* cz) {
+  if (!c || !tx || !ty || !cz || level < 0 || level >= c->L) return MG_ERR_ARG;
   mg::TileCfg v;
   if (kernel == MG_K_FUSED_DOWN) v = c->cfg_down[level];
   else if (kernel == MG_K_FUSED_UP) v = c->cfg_up[level];
@@ -1057,6 +1059,7 @@ mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, in
   else if (kernel == MG_K_OUTER_RESIDUAL) v = mg::TileCfg{0, level == c->L - 1 ? c->fx_cz : 0};
   else return MG_ERR_ARG;
   *tx = v.tx;
+  *ty = v.ty;
   *cz = v.cz;
   return MG_OK;
 }

@@ -221,11 +221,12 @@ def test_autotuned_shapes_keep_the_result(bc, n):
     assert st0 == st1 == 0
     fused_levels = [l for l in range(n.bit_length()) if (n >> (n.bit_length() - 1 - l)) >= 32]
     assert sorted(cfg["fused_down"]) == sorted(cfg["fused_up"]) == fused_levels
-    for l, (tx, cz) in list(cfg["fused_down"].items()) + list(cfg["fused_up"].items()):
+    for l, (tx, ty, cz) in list(cfg["fused_down"].items()) + list(cfg["fused_up"].items()):
         width = n >> (n.bit_length() - 1 - l)
         assert tx in (32, 64) and width % tx == 0 and cz in (8, 16, 32, 64) and cz <= width
+        assert ty in (16, 32) and width % ty == 0
     assert list(cfg["outer_residual"]) == [n.bit_length() - 1]
-    assert cfg["outer_residual"][n.bit_length() - 1][1] in (4, 8, 16, 32, 64)
+    assert cfg["outer_residual"][n.bit_length() - 1][2] in (4, 8, 16, 32, 64)
     assert torch.equal(p0, p1)
     assert len(h0) == len(h1) and np.allclose(h0, h1, rtol=64 * 2.0 ** -24, atol=0)
     with mg.Solver(n, 1.0 / n, bc, prec=mg.MIXED) as s2:
