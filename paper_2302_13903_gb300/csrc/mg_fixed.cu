@@ -12,6 +12,7 @@
 // is used once per cell per pass (the conversion), integer adds do the rest.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "mg_device.cuh"
@@ -260,6 +261,40 @@ __device__ __forceinline__ long long fx_corrected(const long long* __restrict__ 
   return v;
 }
 
+// Asynchronous global -> shared copies of 8 or 4 bytes (src_bytes 0 fills
+// zeros), and the wait for all but the newest N groups.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Per-thread staging ring of the fixed-point step: for each of FX_RING planes,
+// this thread's own PHI_in, e and F, and its halo cell's PHI_in and e.  Each
+// thread reads back only what it copied itself, so the ring needs no barrier.
+constexpr int FX_RING = 4;
+constexpr int FX_NT = FX_TX * FX_TY;
+struct FxRing {
+  long long p[FX_RING][FX_NT];
+  long long f[FX_RING][FX_NT];
+  float e[FX_RING][FX_NT];
+  long long hp[FX_RING][128];
+  float he[FX_RING][128];
+};
+constexpr size_t kFxSmem = sizeof(FxRing);
+
 template <bool PER, bool ZERO_IN>
 __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     k_fx_step(const long long* __restrict__ phi_in, long long* __restrict__ phi_out,
@@ -268,7 +303,10 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
               double* __restrict__ partials, long long* __restrict__ psum,
               int* __restrict__ flag) {
   __shared__ long long P[2][FX_H][FX_W];
-  const int tx = threadIdx.x % FX_TX, ty = threadIdx.x / FX_TX;
+  extern __shared__ long long fx_dyn[];
+  FxRing& ring = *reinterpret_cast<FxRing*>(fx_dyn);
+  const int tid = threadIdx.x;
+  const int tx = tid % FX_TX, ty = tid / FX_TX;
   const int x0 = blockIdx.x * FX_TX, y0 = blockIdx.y * FX_TY, z0 = blockIdx.z * cz;
   const int z1 = min(z0 + cz, g.nz);
   const int i = x0 + tx, j = y0 + ty;  // this thread's column
@@ -277,9 +315,9 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   // the halo cell this thread loads (threads < FX_HALO): rows -1 and 16 over
   // the full width, columns -1 and 32 over the tile's rows
   int ha = 0, hb = 0;
-  const bool halo = threadIdx.x < FX_HALO;
+  const bool halo = tid < FX_HALO;
   if (halo) {
-    const int h = threadIdx.x;
+    const int h = tid;
     if (h < FX_W) { ha = h; hb = 0; }
     else if (h < 2 * FX_W) { ha = h - FX_W; hb = FX_H - 1; }
     else if (h < 2 * FX_W + FX_TY) { ha = 0; hb = h - 2 * FX_W + 1; }
@@ -293,28 +331,55 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   } else {
     h_in = h_in && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
   }
-  const size_t hcol = (size_t)hy * g.nx + hx;
-  auto wrapz = [&](int q) { return q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q); };
-  auto own = [&](int q) -> long long {  // PHI' of this column at plane q (0 outside)
-    if (!PER && (q < 0 || q >= g.nz)) return 0;
-    return fx_corrected<ZERO_IN>(phi_in, e, c, (size_t)(PER ? wrapz(q) : q) * plane + col);
+  const size_t hcol = h_in ? (size_t)hy * g.nx + hx : 0;
+  auto slot = [&](int q) { return (q - z0 + 1) & (FX_RING - 1); };
+  // Copies for plane q: own PHI_in and e (z0-1 <= q <= z1; zeros outside a
+  // non-periodic grid), F (z0 <= q < z1), the halo cell (z0 <= q < z1).
+  auto issue = [&](int q) {
+    if (q <= z1) {
+      const int sl = slot(q);
+      const bool in = PER || (q >= 0 && q < g.nz);
+      const int qw = PER ? (q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q)) : (in ? q : 0);
+      const size_t o = (size_t)qw * plane + col;
+      if (!ZERO_IN) cp_async8(&ring.p[sl][tid], phi_in + o, in ? 8 : 0);
+      cp_async4(&ring.e[sl][tid], e + o, in ? 4 : 0);
+      if (q >= z0 && q < z1) {
+        cp_async8(&ring.f[sl][tid], F + (size_t)q * plane + col, 8);
+        if (halo) {
+          const size_t ho = (size_t)q * plane + hcol;
+          if (!ZERO_IN) cp_async8(&ring.hp[sl][tid], phi_in + ho, h_in ? 8 : 0);
+          cp_async4(&ring.he[sl][tid], e + ho, h_in ? 4 : 0);
+        }
+      }
+    }
+    cp_commit();
   };
-  auto halo_at = [&](int q) -> long long {  // PHI' of this thread's halo cell at plane q
-    return h_in ? fx_corrected<ZERO_IN>(phi_in, e, c, (size_t)q * plane + hcol) : 0;
+  auto own_at = [&](int q) -> long long {  // PHI' of this column at plane q
+    const int sl = slot(q);
+    const long long v = ZERO_IN ? 0 : ring.p[sl][tid];
+    return v + __float2ll_rn(ring.e[sl][tid] * c);
   };
-  // every load of a plane is issued one plane ahead of its use
-  long long zm = own(z0 - 1), self = own(z0), hcur = halo_at(z0);
+  issue(z0 - 1);
+  issue(z0);
+  issue(z0 + 1);
+  cp_wait<1>();  // planes z0 - 1 and z0 have landed
+  long long zm = own_at(z0 - 1), self = own_at(z0);
   float acc = 0.f;
   long long sum_hi = 0, sum_lo = 0;  // exact sum of PHI' = hi 2^32 + lo
   bool bad = false;
   for (int z = z0; z < z1; ++z) {
+    issue(z + 2);
+    cp_wait<1>();  // every plane up to z + 1 has landed
     const size_t o = (size_t)z * plane + col;
-    const long long Fo = F[o];
-    const long long zp = own(z + 1);
-    const long long hnext = z + 1 < z1 ? halo_at(z + 1) : 0;
+    const int sl = slot(z);
+    const long long Fo = ring.f[sl][tid];
+    const long long zp = own_at(z + 1);
     const int buf = (z - z0) & 1;
     P[buf][ty + 1][tx + 1] = self;
-    if (halo) P[buf][hb][ha] = hcur;
+    if (halo) {
+      const long long hv = (ZERO_IN ? 0 : ring.hp[sl][tid]) + __float2ll_rn(ring.he[sl][tid] * c);
+      P[buf][hb][ha] = h_in ? hv : 0;
+    }
     phi_out[o] = self;
     sum_hi += self >> 32;
     sum_lo += self & 0xffffffffLL;
@@ -337,10 +402,10 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     acc = fmaf(r, r, acc);
     zm = self;
     self = zp;
-    hcur = hnext;
-    // the next plane writes the other buffer; this one is rewritten two planes
-    // on, after every thread has passed the next barrier
+    // the next plane writes the other half of P; this one is rewritten two
+    // planes on, after every thread has passed the next barrier
   }
+  cp_wait<0>();
   if (bad) atomicOr(flag, 1);
   // deterministic block sums, then one partial per block (blocks in launch
   // order); the sums of PHI' stay exact integers, so their total does not
@@ -534,18 +599,22 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   *nb_out = nb;
   ++g_launches;
   const bool per = bc.kind == BC_PERIODIC, zero_in = phi_in == nullptr;
-  if (per && zero_in)
-    k_fx_step<true, true><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
-                                                         factor, cz, partials, psum, flag);
-  else if (per)
-    k_fx_step<true, false><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
-                                                          factor, cz, partials, psum, flag);
-  else if (zero_in)
-    k_fx_step<false, true><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
-                                                          factor, cz, partials, psum, flag);
-  else
-    k_fx_step<false, false><<<grid, FX_TX * FX_TY, 0, s>>>(phi_in, phi_out, e, c, F, r32, g, b,
-                                                           factor, cz, partials, psum, flag);
+  static std::atomic<int> configured[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !configured[dev].load()) {
+    for (auto kf : {k_fx_step<true, true>, k_fx_step<true, false>, k_fx_step<false, true>,
+                    k_fx_step<false, false>}) {
+      const cudaError_t e2 =
+          cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFxSmem);
+      if (e2 != cudaSuccess) return e2;
+    }
+    configured[dev].store(1);
+  }
+  auto kf = per ? (zero_in ? k_fx_step<true, true> : k_fx_step<true, false>)
+                : (zero_in ? k_fx_step<false, true> : k_fx_step<false, false>);
+  kf<<<grid, FX_TX * FX_TY, kFxSmem, s>>>(phi_in, phi_out, e, c, F, r32, g, b, factor, cz,
+                                          partials, psum, flag);
   return cudaGetLastError();
 }
 
