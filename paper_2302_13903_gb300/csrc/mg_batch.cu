@@ -329,6 +329,35 @@ constexpr int kFxCols = 3;  // columns per thread (32 x 16 = 512 <= 3 x 216)
 // Each thread owns up to three columns, keeping PHI' of planes z-1, z, z+1 in
 // registers; x / y neighbours come from the current plane in shared memory,
 // whose halo the first threads load and correct.
+// Asynchronous global -> shared copies of 8 or 4 bytes (src_bytes 0 fills
+// zeros) for the outer step's staging ring.
+__device__ __forceinline__ void ring_cp8(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void ring_cp4(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+
+// Staging ring of the outer step in the CTA's dynamic shared memory, after
+// the two halo planes: per plane, each thread's columns' PHI, F and e and its
+// halo cell's PHI and e.  A thread reads back only what it copied itself.
+constexpr int kRing = 4;
+constexpr size_t kPlaneBytes = 2 * 18 * 34 * sizeof(long long);  // [2][TY+2][TX+2], TX, TY <= 32, 16
+struct TileRing {
+  long long p[kRing][kFxCols][kThreads];
+  long long f[kRing][kFxCols][kThreads];
+  float e[kRing][kFxCols][kThreads];
+  long long hp[kRing][kThreads];
+  float he[kRing][kThreads];
+};
+static_assert(kPlaneBytes + sizeof(TileRing) <= kSmem, "outer-step ring exceeds the CTA's smem");
+
 __device__ void fx_tile_item(const Ctl& c, GridDev& g, const Item& I, bool zero_in,
                              float4* smem) {
   const int n = g.n, TX = fx_tx(n), TY = fx_ty(n), CZ = fx_cz(n);
@@ -336,39 +365,36 @@ __device__ void fx_tile_item(const Ctl& c, GridDev& g, const Item& I, bool zero_
   const int x0 = I.a * TX, y0 = I.b * TY, z0 = I.c * CZ, z1 = z0 + CZ;
   const int F = g.L - 1;
   const bool per = g.bc == BC_PERIODIC;
-  const long long* __restrict__ pin =
-      g.cur ? g.fx2 : reinterpret_cast<const long long*>(g.phi);
+  const long long* pin = g.cur ? g.fx2 : reinterpret_cast<const long long*>(g.phi);
   long long* __restrict__ pout = g.cur ? reinterpret_cast<long long*>(g.phi) : g.fx2;
-  const long long* __restrict__ FX = reinterpret_cast<const long long*>(g.f64);
-  const float* __restrict__ e = g.u32[F];
+  const long long* FX = reinterpret_cast<const long long*>(g.f64);
+  const float* e = g.u32[F];
   float* __restrict__ r32 = g.f32[F];
   const float ce = (float)(g.two_S / g.scale);
   const float rfac = (float)(1.0 / (g.rn * g.h * g.h * g.two_S));
   const long long b2 = g.b2;
   const int bc = g.bc;
+  const int tid = threadIdx.x;
   const size_t plane = (size_t)n * n;
   long long* P = reinterpret_cast<long long*>(smem);  // [2][H][W]
-  auto corrected = [&](size_t o) -> long long {
-    long long v = zero_in ? 0 : pin[o];
-    return v + __float2ll_rn(e[o] * ce);
-  };
+  TileRing& ring = *reinterpret_cast<TileRing*>(reinterpret_cast<char*>(smem) + kPlaneBytes);
   auto wrapq = [&](int q) { return q < 0 ? q + n : (q >= n ? q - n : q); };
   // this thread's columns
   int ci[kFxCols], cj[kFxCols];
   bool cact[kFxCols];
 #pragma unroll
   for (int q = 0; q < kFxCols; ++q) {
-    const int col = threadIdx.x + q * (int)blockDim.x;
+    const int col = tid + q * kThreads;
     cact[q] = col < cols;
     ci[q] = x0 + (cact[q] ? col % TX : 0);
     cj[q] = y0 + (cact[q] ? col / TX : 0);
   }
   // this thread's halo cell (rows -1 and TY over the full width, columns -1
   // and TX over the tile's rows)
-  const bool halo = (int)threadIdx.x < nhalo;
+  const bool halo = tid < nhalo;
   int ha = 0, hb = 0;
   if (halo) {
-    const int h = threadIdx.x;
+    const int h = tid;
     if (h < W) { ha = h; hb = 0; }
     else if (h < 2 * W) { ha = h - W; hb = H - 1; }
     else if (h < 2 * W + TY) { ha = 0; hb = h - 2 * W + 1; }
@@ -382,48 +408,76 @@ __device__ void fx_tile_item(const Ctl& c, GridDev& g, const Item& I, bool zero_
   } else {
     h_in = h_in && hx >= 0 && hx < n && hy >= 0 && hy < n;
   }
-  const size_t hcol = (size_t)hy * n + hx;
-  auto own = [&](int q, int z) -> long long {
-    if (!cact[q]) return 0;
-    if (!per && (z < 0 || z >= n)) return 0;
-    return corrected((size_t)(per ? wrapq(z) : z) * plane + (size_t)cj[q] * n + ci[q]);
+  const size_t hcol = h_in ? (size_t)hy * n + hx : 0;
+  auto slot = [&](int q) { return (q - z0 + 1) & (kRing - 1); };
+  // copies for plane q: the columns' PHI and e (z0-1 <= q <= z1, zeros outside
+  // a non-periodic grid), F and the halo cell (z0 <= q < z1)
+  auto issue = [&](int q) {
+    if (q <= z1) {
+      const int sl = slot(q);
+      const bool in = per || (q >= 0 && q < n);
+      const int qw = per ? wrapq(q) : (in ? q : 0);
+#pragma unroll
+      for (int k = 0; k < kFxCols; ++k) {
+        if (!cact[k]) continue;
+        const size_t o = (size_t)qw * plane + (size_t)cj[k] * n + ci[k];
+        if (!zero_in) ring_cp8(&ring.p[sl][k][tid], pin + o, in ? 8 : 0);
+        ring_cp4(&ring.e[sl][k][tid], e + o, in ? 4 : 0);
+        if (q >= z0 && q < z1)
+          ring_cp8(&ring.f[sl][k][tid], FX + (size_t)q * plane + (size_t)cj[k] * n + ci[k], 8);
+      }
+      if (halo && q >= z0 && q < z1) {
+        const size_t ho = (size_t)q * plane + hcol;
+        if (!zero_in) ring_cp8(&ring.hp[sl][tid], pin + ho, h_in ? 8 : 0);
+        ring_cp4(&ring.he[sl][tid], e + ho, h_in ? 4 : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
+  auto own_at = [&](int k, int q) -> long long {
+    const int sl = slot(q);
+    const long long v = zero_in ? 0 : ring.p[sl][k][tid];
+    return v + __float2ll_rn(ring.e[sl][k][tid] * ce);
+  };
+  issue(z0 - 1);
+  issue(z0);
+  issue(z0 + 1);
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // planes z0 - 1, z0 landed
   long long zm[kFxCols], self[kFxCols];
 #pragma unroll
-  for (int q = 0; q < kFxCols; ++q) {
-    zm[q] = own(q, z0 - 1);
-    self[q] = own(q, z0);
+  for (int k = 0; k < kFxCols; ++k) {
+    zm[k] = cact[k] ? own_at(k, z0 - 1) : 0;
+    self[k] = cact[k] ? own_at(k, z0) : 0;
   }
-  long long hcur = h_in ? corrected((size_t)z0 * plane + hcol) : 0;
   float acc = 0.f;
   bool bad = false;
   for (int z = z0; z < z1; ++z) {
+    issue(z + 2);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // every plane up to z + 1
+    const int sl = slot(z);
     const int buf = (z - z0) & 1;
     long long* Pb = P + (size_t)buf * H * W;
-    long long zp[kFxCols], Fo[kFxCols];
 #pragma unroll
-    for (int q = 0; q < kFxCols; ++q) {
-      zp[q] = own(q, z + 1);
-      Fo[q] = cact[q] ? FX[(size_t)z * plane + (size_t)cj[q] * n + ci[q]] : 0;
+    for (int k = 0; k < kFxCols; ++k) {
+      if (!cact[k]) continue;
+      Pb[(cj[k] - y0 + 1) * W + (ci[k] - x0 + 1)] = self[k];
+      pout[(size_t)z * plane + (size_t)cj[k] * n + ci[k]] = self[k];
+      bad |= (self[k] > (1LL << 60)) || (self[k] < -(1LL << 60));
     }
-    const long long hnext = (h_in && z + 1 < z1) ? corrected((size_t)(z + 1) * plane + hcol) : 0;
-#pragma unroll
-    for (int q = 0; q < kFxCols; ++q) {
-      if (!cact[q]) continue;
-      Pb[(cj[q] - y0 + 1) * W + (ci[q] - x0 + 1)] = self[q];
-      pout[(size_t)z * plane + (size_t)cj[q] * n + ci[q]] = self[q];
-      bad |= (self[q] > (1LL << 60)) || (self[q] < -(1LL << 60));
+    if (halo) {
+      const long long hv = (zero_in ? 0 : ring.hp[sl][tid]) + __float2ll_rn(ring.he[sl][tid] * ce);
+      Pb[hb * W + ha] = h_in ? hv : 0;
     }
-    if (halo) Pb[hb * W + ha] = hcur;
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kFxCols; ++q) {
-      if (!cact[q]) continue;
-      const int i = ci[q], j = cj[q], a = i - x0 + 1, b = j - y0 + 1;
-      const long long sv = self[q];
-      long long xm = Pb[b * W + a - 1], xp = Pb[b * W + a + 1];
-      long long ym = Pb[(b - 1) * W + a], yp = Pb[(b + 1) * W + a];
-      long long zmv = zm[q], zpv = zp[q];
+    for (int k = 0; k < kFxCols; ++k) {
+      if (!cact[k]) continue;
+      const int i = ci[k], j = cj[k], a = i - x0 + 1, bb = j - y0 + 1;
+      const long long sv = self[k];
+      const long long zp = own_at(k, z + 1);
+      long long xm = Pb[bb * W + a - 1], xp = Pb[bb * W + a + 1];
+      long long ym = Pb[(bb - 1) * W + a], yp = Pb[(bb + 1) * W + a];
+      long long zmv = zm[k], zpv = zp;
       if (!per) {
         const long long gh = bc == BC_ZEROGRAD ? sv : b2 - sv;
         if (i == 0) xm = gh;
@@ -434,17 +488,17 @@ __device__ void fx_tile_item(const Ctl& c, GridDev& g, const Item& I, bool zero_
         if (z == n - 1) zpv = gh;
       }
       const size_t o = (size_t)z * plane + (size_t)j * n + i;
-      const long long R = Fo[q] - (((xm + xp) + (ym + yp)) + (zmv + zpv) - 6 * sv);
+      const long long R = ring.f[sl][k][tid] - (((xm + xp) + (ym + yp)) + (zmv + zpv) - 6 * sv);
       const float r = __ll2float_rn(R) * rfac;
       r32[o] = r;
       acc = fmaf(r, r, acc);
-      zm[q] = sv;
-      self[q] = zp[q];
+      zm[k] = sv;
+      self[k] = zp;
     }
-    hcur = hnext;
     // the next plane writes the other half of P; this one is rewritten two
     // planes on, after every thread has passed the next barrier
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (bad) atomicOr(&g.fxbad, 1);
   const double b = block_sum((double)acc);
   if (threadIdx.x == 0) c.part3[g.part0 + (I.c * (n / TY) + I.b) * (n / TX) + I.a] = b;
