@@ -330,8 +330,8 @@ int mg_batch_graph(const mg_batch *batch);
 
 /* Device time of the last mg_batch_solve by phase kind, in milliseconds
  * (from the GPU's global timer at each grid-wide barrier): ms_by_type[k] for
- * k < n_types in the order source, mean, source-2, norm, first residual,
- * first-residual norm, fused down leg, bottom levels, fused up leg, max |e|,
+ * k < n_types in the order source, mean, first residual, norms of the
+ * source and first residual, fused down leg, bottom levels, fused up leg, max |e|,
  * fixed-point scale, conversion to fixed point, outer step (correction and
  * residual), stopping rule, phi sum, phi mean, phi conversion and mean
  * removal.

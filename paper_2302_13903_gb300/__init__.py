@@ -506,9 +506,9 @@ class Batch:
     def graph(self):
         return bool(lib().mg_batch_graph(self.ptr))
 
-    PHASES = ["source", "mean", "source2", "norm", "r0", "r0_norm", "down", "bottom", "up",
-              "max_e", "set_fixed_point", "to_fixed_point", "outer_step", "stop_rule",
-              "phi_sum", "phi_mean", "phi_sub"]
+    PHASES = ["source", "mean", "r0", "r0_norm", "down", "bottom", "up", "max_e",
+              "set_fixed_point", "to_fixed_point", "outer_step", "stop_rule", "phi_sum",
+              "phi_mean", "phi_sub"]
 
     def phase_ms(self):
         """{phase kind: device ms} of the last solve."""

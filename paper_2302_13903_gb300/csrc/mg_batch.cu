@@ -72,12 +72,10 @@ struct GridDev {
 };
 
 enum PhaseType : int {
-  PH_SRC = 0,      // chunk: f = fpg rho, partial sum f
-  PH_MEANFIN,      // grid: mean (periodic / zero gradient)
-  PH_SRC2,         // chunk: f -= mean, partial sum f^2
-  PH_NORMFIN,      // grid: ||f||
-  PH_R0,           // chunk: r = f - L(0) in FP64 -> r32 = r / ||f||, partial sum r^2
-  PH_R0FIN,        // grid: rn
+  PH_SRC = 0,      // chunk: partial sum and maximum of rho
+  PH_MEANFIN,      // grid: mean of f (periodic / zero gradient), the FP32 scale
+  PH_R0,           // chunk: r = f - mean - L(0) -> r32 (scaled), sums of (f - mean)^2, r^2
+  PH_R0FIN,        // grid: ||f||, rn
   PH_DOWN,         // tile: fused down leg on level size `n`
   PH_BOTTOM,       // grid: levels <= 32^3 of one V-cycle
   PH_UP,           // tile: fused up leg on level size `n`
@@ -216,7 +214,6 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
   const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
   const int F = g.L - 1;
   double* phi = g.phi;
-  double* __restrict__ f64 = g.f64;
   // the integer potential: in phi's own storage or in the second buffer
   const long long* PHI = g.cur ? g.fx2 : reinterpret_cast<const long long*>(g.phi);  // may be phi
   long long* __restrict__ FX = reinterpret_cast<long long*>(g.f64);
@@ -228,57 +225,74 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
   const int bc = g.bc;
   const bool fx = g.in_fx != 0;
   const double two_S = g.two_S;
-  const double inv_fn = 1.0 / g.fnorm;
   double acc = 0.0, mx = 0.0;
   long long s_hi = 0, s_lo = 0;
+  // unrolled so that each thread has several independent loads in flight
+  // f = 4 pi G rho is never stored: each pass forms what it needs from rho
+  const double sc = g.scale;  // r32 = (f - mean - L(0)) sc
+  const double a0 = fpg * sc, b0 = mean * sc;
+  const float bt = (float)(2.0 * bcval * inv_h2 * sc);  // one fixed-value ghost term, scaled
+  const double c2 = h * h * two_S;
+  float af = 0.f, ar = 0.f;  // FP32 sums over at most 8 cells, then added in FP64
+  double acc2 = 0.0;
+  int nf = 0;
+  unsigned long long mb = 0;  // largest |rho| bit pattern
   // unrolled so that each thread has several independent loads in flight
 #pragma unroll 4
   for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) {
     if (TYPE == PH_SRC) {
-      const double v = fpg * rho[t];
-      f64[t] = v;
+      const double v = rho[t];
       acc += v;
-    } else if (TYPE == PH_SRC2) {
-      const double v = f64[t] - mean;
-      f64[t] = v;
-      acc += v * v;
-      mx = fmax(mx, fabs(v));
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+      mb = bits > mb ? bits : mb;
     } else if (TYPE == PH_R0) {
-      const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
-      phi[t] = 0.0;
-      // L_h(0) is nonzero only through the fixed value's ghosts (2 b each)
-      int faces = 0;
-      if (bc == BC_FIXED)
-        faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
-      const double d = f64[t] - (faces * 2.0 * bcval) * inv_h2;
-      r32[t] = (float)(d * inv_fn);
-      acc += d * d;
+      const float x = (float)fma(a0, rho[t], -b0);  // (f - mean) sc
+      float xs = x;
+      if (bc == BC_FIXED && bcval != 0.0) {  // L_h(0): 2 b per fixed-value ghost
+        const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
+        const int faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
+        xs = x - (float)faces * bt;
+      }
+      r32[t] = xs;
+      af = fmaf(x, x, af);
+      ar = fmaf(xs, xs, ar);
+      if (++nf == 8) {
+        acc += af;
+        acc2 += ar;
+        af = ar = 0.f;
+        nf = 0;
+      }
     } else if (TYPE == PH_EMAX) {
       mx = fmax(mx, (double)fabsf(e32[t]));
     } else if (TYPE == PH_TOFX) {
-      FX[t] = __double2ll_rn(f64[t] * (h * h * two_S));
+      FX[t] = __double2ll_rn(fma(fpg * c2, rho[t], -mean * c2));
     } else if (TYPE == PH_PSUM) {
-      if (fx) {
-        const long long v = PHI[t];
-        s_hi += v >> 32;
-        s_lo += v & 0xffffffffLL;
-      } else {
-        acc += phi[t];
-      }
+      const long long v = PHI[t];
+      s_hi += v >> 32;
+      s_lo += v & 0xffffffffLL;
     } else if (TYPE == PH_PSUB) {
-      if (fx) phi[t] = (double)PHI[t] * (1.0 / two_S) - mean;
-      else phi[t] -= mean;
+      // a grid that never reached the fixed-point loop has phi = 0 exactly
+      phi[t] = fx ? (double)PHI[t] * (1.0 / two_S) - mean : 0.0;
     }
   }
-  if (TYPE == PH_SRC || TYPE == PH_SRC2 || TYPE == PH_R0 || (TYPE == PH_PSUM && !fx)) {
+  if (TYPE == PH_R0) {
+    acc += af;
+    acc2 += ar;
+  }
+  if (TYPE == PH_SRC || TYPE == PH_R0) {
     const double b = block_sum(acc);
     if (threadIdx.x == 0) c.part[g.chunk0 + chunk] = b;
   }
-  if (TYPE == PH_SRC2 || TYPE == PH_EMAX) {
+  if (TYPE == PH_R0) {
+    const double b = block_sum(acc2);
+    if (threadIdx.x == 0) c.part2[g.chunk0 + chunk] = b;
+  }
+  if (TYPE == PH_SRC) mx = __longlong_as_double((long long)mb);
+  if (TYPE == PH_SRC || TYPE == PH_EMAX) {
     const double b = block_max(mx);
     if (threadIdx.x == 0) c.part2[g.chunk0 + chunk] = b;
   }
-  if (TYPE == PH_PSUM && fx) {
+  if (TYPE == PH_PSUM) {
     const long long bh = block_isum(s_hi), bl = block_isum(s_lo);
     if (threadIdx.x == 0) {
       c.ipart[2 * (g.chunk0 + chunk)] = bh;
@@ -586,7 +600,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
       if (!run) continue;
       switch (P.type) {
         case PH_SRC: chunk_item<PH_SRC>(c, g, I.a); break;
-        case PH_SRC2: chunk_item<PH_SRC2>(c, g, I.a); break;
         case PH_R0: chunk_item<PH_R0>(c, g, I.a); break;
         case PH_EMAX: chunk_item<PH_EMAX>(c, g, I.a); break;
         case PH_TOFX: chunk_item<PH_TOFX>(c, g, I.a); break;
@@ -599,10 +612,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
         case PH_PSUM: chunk_item<PH_PSUM>(c, g, I.a); break;
         case PH_PSUB: chunk_item<PH_PSUB>(c, g, I.a); break;
         case PH_MEANFIN:
-          if (threadIdx.x == 0)
-            g.mean = (g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD)
-                         ? chunk_total(c, g) / ((double)g.n * g.n * g.n)
-                         : 0.0;
+          if (threadIdx.x == 0) {
+            const double N = (double)g.n * g.n * g.n;
+            g.mean = (g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD) ? g.fpg * (chunk_total(c, g) / N)
+                                                                  : 0.0;
+            // max |f - mean| <= |4 pi G| max |rho| + |mean|: the scale of r32 and of 2^S
+            g.maxf = fabs(g.fpg) * chunk_max(c, g) + fabs(g.mean);
+            g.scale = g.maxf > 0.0 ? 1.0 / g.maxf : 1.0;
+          }
           break;
         case PH_PMEAN:
           if (threadIdx.x == 0) {
@@ -616,24 +633,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
                   tl += c.ipart[2 * (g.chunk0 + q) + 1];
                 }
                 m = ((double)th * 4294967296.0 + (double)tl) / (N * g.two_S);
-              } else {
-                m = chunk_total(c, g) / N;
-              }
+              }  // otherwise phi = 0 exactly (the grid stopped at its first residual)
             }
             g.mean = m;
           }
           break;
-        case PH_NORMFIN:
-          if (threadIdx.x == 0) {
-            g.maxf = chunk_max(c, g);
-            g.fnorm = sqrt(chunk_total(c, g) / ((double)g.n * g.n * g.n));
-            if (g.fnorm == 0.0) g.fnorm = 1.0;  // r = f - L(0) decides below
-          }
-          break;
         case PH_R0FIN:
           if (threadIdx.x == 0) {
-            g.rn = sqrt(chunk_total(c, g) / ((double)g.n * g.n * g.n));
-            g.scale = 1.0 / g.fnorm;  // r32 = r / ||f||
+            const double N = (double)g.n * g.n * g.n;
+            double fs = 0.0, rs = 0.0;  // sums of ((f - mean) sc)^2 and (r0 sc)^2
+            for (int q = 0; q < g.nchunk; ++q) {
+              fs += c.part[g.chunk0 + q];
+              rs += c.part2[g.chunk0 + q];
+            }
+            g.fnorm = sqrt(fs / N) / g.scale;
+            g.rn = sqrt(rs / N) / g.scale;
+            if (g.fnorm == 0.0) g.fnorm = g.rn > 0.0 ? g.rn : 1.0;
             if (g.rn == 0.0) {  // phi = 0 is exact
               g.active = 0;
               g.status = MG_OK;
@@ -818,8 +833,6 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
   };
   add_chunk_phase(PH_SRC);
   add_grid_phase(PH_MEANFIN, 0);
-  add_chunk_phase(PH_SRC2);
-  add_grid_phase(PH_NORMFIN, 0);
   add_chunk_phase(PH_R0);
   add_grid_phase(PH_R0FIN, 0);
   // one V-cycle from a zero correction, then inner_cycles more (as mg_solve)
