@@ -65,10 +65,18 @@ struct Patch {
   Row a, b;  // a: even row, b: odd row
 };
 
+// A float4 of a shared plane holds four consecutive cells c0..c3, either in
+// the level's own order (planes copied from global memory) or, in planes this
+// kernel writes itself, in packed order (c0, c2, c1, c3) = (e, o), whose
+// colour pairs are adjacent registers after a load.
 __device__ __forceinline__ Row unpack(const float4 v) {
   return Row{make_float2(v.x, v.z), make_float2(v.y, v.w)};
 }
 __device__ __forceinline__ float4 pack(const Row r) { return make_float4(r.e.x, r.o.x, r.e.y, r.o.y); }
+__device__ __forceinline__ Row unpack_p(const float4 v) {
+  return Row{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ float4 pack_p(const Row r) { return make_float4(r.e.x, r.e.y, r.o.x, r.o.y); }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ Patch zero_patch() {
@@ -106,9 +114,11 @@ template <bool E>
 __device__ __forceinline__ float2 part(const Row& r) {
   return E ? r.e : r.o;
 }
-template <bool E>
+// The e (E) or o cells of a shared float4 in natural (PKD = false) or packed
+// order.  c0 is .x and c3 is .w in both orders.
+template <bool E, bool PKD>
 __device__ __forceinline__ float2 part4(const float4& v) {
-  return E ? f2(v.x, v.z) : f2(v.y, v.w);
+  return PKD ? (E ? f2(v.x, v.y) : f2(v.z, v.w)) : (E ? f2(v.x, v.z) : f2(v.y, v.w));
 }
 template <bool E>
 __device__ __forceinline__ void set_part(Row& r, float2 v) {
@@ -135,7 +145,7 @@ __device__ __forceinline__ void x_nb(const Row& r, const float4& side, float2 se
 // One SOR half-step on the patch: row a updates its e cells if AE (else o),
 // row b the cells of the other parity (the same colour one row down).  S: the
 // shared copy of this plane; zm, zp: the patch in the planes below / above.
-template <bool PER, bool AE>
+template <bool PER, bool AE, bool PKD>
 __device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S, int ia, int ib,
                                           int offL, int offR, int offU, int offD, const Patch& zm,
                                           const Patch& zp, const Patch& f, const FusedParams& p,
@@ -147,7 +157,7 @@ __device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S
     const float2 self = part<AE>(u.a);
     float2 xm, xp;
     x_nb<PER, AE>(u.a, side, self, xm, xp, p, fl);
-    float2 ym = part4<AE>(above), yp = part<AE>(u.b);
+    float2 ym = part4<AE, PKD>(above), yp = part<AE>(u.b);
     float2 zmv = part<AE>(zm.a), zpv = part<AE>(zp.a);
     if (!PER) {
       ym = sub_if(fl.ylo, p.s, self, ym);
@@ -162,7 +172,7 @@ __device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S
     const float2 self = part<BE>(u.b);
     float2 xm, xp;
     x_nb<PER, BE>(u.b, side, self, xm, xp, p, fl);
-    float2 ym = part<BE>(u.a), yp = part4<BE>(below);
+    float2 ym = part<BE>(u.a), yp = part4<BE, PKD>(below);
     float2 zmv = part<BE>(zm.b), zpv = part<BE>(zp.b);
     if (!PER) {
       yp = sub_if(fl.yhi, p.s, self, yp);
@@ -182,7 +192,7 @@ __device__ __forceinline__ float2 defect_part(const Row& r, const Row& other, co
   const float2 self = part<E>(r);
   float2 xm, xp;
   x_nb<PER, E>(r, side, self, xm, xp, p, fl);
-  float2 yout = part4<E>(yout4), yin = part<E>(other);
+  float2 yout = part4<E, true>(yout4), yin = part<E>(other);
   float2 zmv = part<E>(rzm), zpv = part<E>(rzp);
   if (!PER) {
     yout = sub_if(ROWB ? fl.yhi : fl.ylo, p.s, self, yout);
@@ -193,8 +203,8 @@ __device__ __forceinline__ float2 defect_part(const Row& r, const Row& other, co
               : defect2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p);
 }
 
-// Defect of the whole patch (interior threads only); returns the sums over
-// both rows of (d(4m) + d(4m+1), d(4m+2) + d(4m+3)): the two coarse cells in x.
+// Defect of the whole patch (interior threads only; S in packed order);
+// returns the sums over both rows of (d(4m) + d(4m+1), d(4m+2) + d(4m+3)): the two coarse cells in x.
 template <bool PER>
 __device__ __forceinline__ float2 defect_patch(const Patch& u, const float4* __restrict__ S,
                                                int ia, int ib, int RS, const Patch& zm,
@@ -223,12 +233,13 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// (x, y) part of the trilinear prolongation of coarse plane K at the patch:
+// (x, y) part of the trilinear prolongation of one coarse plane at a patch:
 // rows gyA (even: coarse rows Y-1, Y) and gyA+1 (odd: Y, Y+1), Y = gyA/2;
-// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  Split in two so
-// that the loads of a plane can be issued a step before they are combined:
-// xy_load fetches the 3 x 4 coarse values (ghosts applied), xy_combine
-// weights them.
+// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  The 3 x 4
+// coarse columns are resolved once per thread (CoarseIdx: wrapped indices,
+// or edge indices with the ghost sign s for the non-periodic rules), so a
+// plane costs twelve loads (xy_load) and the weighting (xy_combine).  Patches
+// outside the level get clamped, in-bounds indices; their values are unused.
 // COH: the coarse values may have been written earlier in the same launch by
 // another CTA (the batched solver), so read them through L2 (ld.global.cg)
 // rather than the read-only path.
@@ -236,34 +247,59 @@ struct Coarse12 {
   float c[3][4];
 };
 
-template <bool PER, bool COH = false>
-__device__ __forceinline__ Coarse12 xy_load(const float* __restrict__ ec, const FusedParams& p,
-                                            int gx4, int gyA, int K) {
+template <bool PER>
+struct CoarseIdx {
+  int col[4];  // coarse x
+  int row[3];  // coarse y * cnx
+  float sx[4], sy[3];  // ghost signs (non-periodic rules; 1 inside)
+};
+
+template <bool PER>
+__device__ __forceinline__ CoarseIdx<PER> coarse_idx(const FusedParams& p, int gx4, int gyA) {
   const int cnx = p.nx >> 1, cny = p.ny >> 1;
   const int X0 = gx4 >> 1, Y = gyA >> 1;
-  Coarse12 r;
+  CoarseIdx<PER> ci;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int Xc = X0 - 1 + a;
+    ci.sx[a] = 1.f;
+    if (PER) ci.col[a] = wrap(Xc, cnx);
+    else if (Xc < 0) { ci.col[a] = 0; ci.sx[a] = p.s; }
+    else if (Xc >= cnx) { ci.col[a] = cnx - 1; ci.sx[a] = p.s; }
+    else ci.col[a] = Xc;
+  }
 #pragma unroll
   for (int yy = 0; yy < 3; ++yy) {
     const int Yc = Y - 1 + yy;
     int Yi = Yc;
-    float sy = 1.f;
-    if (Yc < 0 || Yc >= cny) {
-      if (PER) Yi = wrap(Yc, cny);
-      else { Yi = Yc < 0 ? 0 : cny - 1; sy = p.s; }
-    }
-    const float* rowp = ec + ((size_t)K * cny + Yi) * cnx;
+    ci.sy[yy] = 1.f;
+    if (PER) Yi = wrap(Yc, cny);
+    else if (Yc < 0) { Yi = 0; ci.sy[yy] = p.s; }
+    else if (Yc >= cny) { Yi = cny - 1; ci.sy[yy] = p.s; }
+    ci.row[yy] = Yi * cnx;
+  }
+  return ci;
+}
+
+// The 3 x 4 coarse values of coarse plane Kc (any index from -2 to cnz + 1:
+// wrapped, or clamped with the ghost sign), ghosts applied.
+template <bool PER, bool COH>
+__device__ __forceinline__ Coarse12 xy_load(const float* __restrict__ ec, const FusedParams& p,
+                                            const CoarseIdx<PER>& ci, int Kc) {
+  const int cnz = p.nz >> 1;
+  float sz = 1.f;
+  if (PER) Kc = wrap(Kc, cnz);
+  else if (Kc < 0) { Kc = 0; sz = p.s; }
+  else if (Kc >= cnz) { Kc = cnz - 1; sz = p.s; }
+  const float* base = ec + (size_t)Kc * (size_t)((p.nx >> 1) * (p.ny >> 1));
+  Coarse12 r;
+#pragma unroll
+  for (int yy = 0; yy < 3; ++yy) {
+    const float* rowp = base + ci.row[yy];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const int Xc = X0 - 1 + a;
-      const float* src;
-      float sx = 1.f;
-      if (Xc < 0 || Xc >= cnx) {
-        if (PER) src = rowp + wrap(Xc, cnx);
-        else { src = rowp + (Xc < 0 ? 0 : cnx - 1); sx = p.s; }
-      } else {
-        src = rowp + Xc;
-      }
-      r.c[yy][a] = sy * (sx * (COH ? __ldcg(src) : __ldg(src)));
+      const float v = COH ? __ldcg(rowp + ci.col[a]) : __ldg(rowp + ci.col[a]);
+      r.c[yy][a] = PER ? v : sz * (ci.sy[yy] * (ci.sx[a] * v));
     }
   }
   return r;
@@ -285,12 +321,6 @@ __device__ __forceinline__ Patch xy_combine(const Coarse12& r) {
   P.b.e = f2(0.75f * xr[1][0] + 0.25f * xr[2][0], 0.75f * xr[1][2] + 0.25f * xr[2][2]);
   P.b.o = f2(0.75f * xr[1][1] + 0.25f * xr[2][1], 0.75f * xr[1][3] + 0.25f * xr[2][3]);
   return P;
-}
-
-template <bool PER, bool COH = false>
-__device__ __forceinline__ Patch xy_interp(const float* __restrict__ ec, const FusedParams& p,
-                                           int gx4, int gyA, int K) {
-  return xy_combine(xy_load<PER, COH>(ec, p, gx4, gyA, K));
 }
 
 // Row stride of a shared plane, in float4: the smallest RS >= RT with
@@ -355,38 +385,55 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   fl.yhi = !PER && gyA + 1 == p.ny - 1;
   const bool out = tr >= 1 && tr <= TX / 4 && tp >= HY / 2 && tp < HY / 2 + TY / 2;
   const size_t plane = (size_t)p.nx * p.ny;
-  const size_t offA = col_ok ? (size_t)gyAw * p.nx + gx4w : 0;
-  const size_t offB = col_ok ? offA + (size_t)p.nx : 0;
+  const size_t offA = col_ok ? (size_t)gyAw * p.nx + gx4w : 0;  // row a; row b is nx further
   const int ia = (2 * tp) * RS + tr, ib = ia + RS;  // shared indices of rows a, b
   const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
   const int offU = tp > 0 ? -RS : 0, offD = tp < RP - 1 ? RS : 0;
   const int q_first = z0 - HZ, q_last = z1 - 1 + HZ;
 
-  auto issue = [&](int qu) {
+  // Copies of plane qu of u into ring slot SU and plane qu - 1 of f into
+  // slot SF (the slots are compile-time: qu mod 4 is fixed by the step).
+  auto issue = [&](auto SUc, auto SFc, int qu) {
+    constexpr int SU = decltype(SUc)::value, SF = decltype(SFc)::value;
     if (act && qu <= q_last) {
       if (!ZERO) {
         const bool in = col_ok && (PER || (qu >= 0 && qu < p.nz));
-        const size_t o = (size_t)(PER ? wrap(qu, p.nz) : (in ? qu : 0)) * plane;
-        float4* d = &s_u[(qu & 3) * PL];
-        cp_async16(&d[ia], u_in + o + offA, in ? 16 : 0);
-        cp_async16(&d[ib], u_in + o + offB, in ? 16 : 0);
+        const int w = PER ? wrap(qu, p.nz) : (in ? qu : 0);
+        const float* src = u_in + (size_t)w * plane + offA;
+        float4* d = &s_u[SU * PL];
+        cp_async16(&d[ia], src, in ? 16 : 0);
+        cp_async16(&d[ib], src + p.nx, in ? 16 : 0);
       }
       const int qf = qu - 1;
       const bool inf = col_ok && (PER || (qf >= 0 && qf < p.nz));
-      const size_t o = (size_t)(PER ? wrap(qf, p.nz) : (inf ? qf : 0)) * plane;
-      float4* d = &s_f[(qf & 3) * PL];
-      cp_async16(&d[ia], f + o + offA, inf ? 16 : 0);
-      cp_async16(&d[ib], f + o + offB, inf ? 16 : 0);
+      const int w = PER ? wrap(qf, p.nz) : (inf ? qf : 0);
+      const float* src = f + (size_t)w * plane + offA;
+      float4* d = &s_f[SF * PL];
+      cp_async16(&d[ia], src, inf ? 16 : 0);
+      cp_async16(&d[ib], src + p.nx, inf ? 16 : 0);
     }
     cp_async_commit();
   };
 
   Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
   float2 acc = make_float2(0.f, 0.f);
-  int ka = -1000000, kb = -1000000;  // coarse planes of the cached (x, y) interpolations
-  Patch Pa = r1, Pb = r1;
-  int kpre = -1000000;  // coarse plane whose values were loaded a step ahead
+  // Up leg: the (x, y)-interpolated coarse planes K-1, K, K+1 around fine
+  // planes 2K, 2K+1 live in W[0] (even K) and W[1] (odd K); fine plane 2K
+  // takes 3/4 of plane K and 1/4 of plane K-1, fine plane 2K+1 3/4 of K and
+  // 1/4 of K+1.  The loads of plane K+1 are issued at fine plane 2K and
+  // combined at 2K+1 (in the batched solver, which has no registers to
+  // spare, loaded and combined at 2K+1).
+  constexpr bool PF = !COH;
+  Patch W[2];
   Coarse12 pre;
+  CoarseIdx<PER> ci;
+  if (MODE == kUp) {
+    ci = coarse_idx<PER>(p, gx4, gyA);
+    // q_first = z0 - 2 with z0 a multiple of 8: K0 = q_first / 2 is odd
+    const int K0 = q_first >> 1;
+    W[0] = xy_combine(xy_load<PER, COH>(ec, p, ci, K0 - 1));
+    W[1] = xy_combine(xy_load<PER, COH>(ec, p, ci, K0));
+  }
 
   // One plane step.  J = (q - q_first) mod 4 fixes the ring slots and the
   // colours at compile time: q_first = z0 - HZ with z0 a multiple of 8.
@@ -397,9 +444,11 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     constexpr int ZP_RED = (QP + 3) % 2;  // parity of plane q-1
     constexpr int ZP_BLK = (QP + 2) % 2;  // parity of plane q-2
     constexpr int ZP_DEF = (QP + 1) % 2;  // parity of plane q-3
+    constexpr bool PKU = MODE == kUp;     // the u planes hold corrected values, packed
     cp_async_wait<1>();  // this thread's copies of plane q have landed
     __syncthreads();     // ... and everyone's; the previous step is finished
-    issue(q + 2);
+    issue(std::integral_constant<int, (QP + 2) % 4>{}, std::integral_constant<int, (QP + 1) % 4>{},
+          q + 2);
     // [A] plane q of u (old values), plus the prolonged correction (up leg)
     Patch r0 = zero_patch();
     if (!ZERO) {
@@ -407,49 +456,22 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       r0.b = unpack(s_u[SL_U * PL + ib]);
     }
     if (MODE == kUp) {
+      constexpr int KP = (QP >> 1) & 1;  // parity of K = floor(q / 2)
+      const int K = q >> 1;
+      if (QP & 1) W[1 - KP] = xy_combine(PF ? pre : xy_load<PER, COH>(ec, p, ci, K + 1));
       if (col_ok && (PER || (q >= 0 && q < p.nz))) {
-        const int qw = PER ? wrap(q, p.nz) : q;
-        const int cnz = p.nz >> 1;
-        const int K = qw >> 1;
-        int Kn = (qw & 1) ? K + 1 : K - 1;
-        float wn = 0.25f;
-        if (Kn < 0 || Kn >= cnz) {
-          if (PER) Kn = wrap(Kn, cnz);
-          else { Kn = Kn < 0 ? 0 : cnz - 1; wn *= p.s; }
-        }
-        Patch PK, PN;
-        if (K == kb) PK = Pb;
-        else if (K == ka) PK = Pa;
-        else {
-          PK = K == kpre ? xy_combine(pre) : xy_interp<PER, COH>(ec, p, gx4w, gyAw, K);
-          ka = kb; Pa = Pb; kb = K; Pb = PK;
-        }
-        if (Kn == kb) PN = Pb;
-        else if (Kn == ka) PN = Pa;
-        else {
-          PN = Kn == kpre ? xy_combine(pre) : xy_interp<PER, COH>(ec, p, gx4w, gyAw, Kn);
-          ka = kb; Pa = Pb; kb = Kn; Pb = PN;
-        }
-        // an even plane 2K is followed by 2K+1, which needs coarse plane K+1:
-        // issue its loads now, to be combined in the next step (not in the
-        // batched solver, whose kernel has no registers to spare)
-        if (!COH && (QP & 1) == 0 && q + 1 <= q_last) {
-          int Kp = K + 1;
-          if (Kp >= cnz) Kp = PER ? Kp - cnz : cnz - 1;
-          if (Kp != kb && Kp != ka) {
-            pre = xy_load<PER, COH>(ec, p, gx4w, gyAw, Kp);
-            kpre = Kp;
-          }
-        }
-        const float2 w0 = make_float2(0.75f, 0.75f), w1 = make_float2(wn, wn);
+        const float2 w0 = make_float2(0.75f, 0.75f), w1 = make_float2(0.25f, 0.25f);
+        const Patch& PK = W[KP];
+        const Patch& PN = W[1 - KP];
         r0.a.e = __ffma2_rn(w1, PN.a.e, __ffma2_rn(w0, PK.a.e, r0.a.e));
         r0.a.o = __ffma2_rn(w1, PN.a.o, __ffma2_rn(w0, PK.a.o, r0.a.o));
         r0.b.e = __ffma2_rn(w1, PN.b.e, __ffma2_rn(w0, PK.b.e, r0.b.e));
         r0.b.o = __ffma2_rn(w1, PN.b.o, __ffma2_rn(w0, PK.b.o, r0.b.o));
       }
+      if (PF && !(QP & 1)) pre = xy_load<PER, COH>(ec, p, ci, K + 1);
       if (act) {
-        s_u[SL_U * PL + ia] = pack(r0.a);  // the neighbours read corrected values
-        s_u[SL_U * PL + ib] = pack(r0.b);
+        s_u[SL_U * PL + ia] = pack_p(r0.a);  // the neighbours read corrected values
+        s_u[SL_U * PL + ib] = pack_p(r0.b);
       }
     }
     Patch f1;
@@ -472,13 +494,13 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
             r1.b.e = __fmul2_rn(cf2, f1.b.e);
           }
         } else {
-          sor_patch<PER, ZP_RED == 0>(r1, &s_u[SL_UM1 * PL], ia, ib, offL, offR, offU, offD, r2,
-                                      r0, f1, p, fl, zlo, zhi);
+          sor_patch<PER, ZP_RED == 0, PKU>(r1, &s_u[SL_UM1 * PL], ia, ib, offL, offR, offU, offD,
+                                           r2, r0, f1, p, fl, zlo, zhi);
         }
       }
       if (act) {
-        s_red[ZP_RED * PL + ia] = pack(r1.a);
-        s_red[ZP_RED * PL + ib] = pack(r1.b);
+        s_red[ZP_RED * PL + ia] = pack_p(r1.a);
+        s_red[ZP_RED * PL + ib] = pack_p(r1.b);
       }
     }
     // [C] black half-step on plane q-2 (red values of planes q-3 .. q-1)
@@ -486,15 +508,16 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       const int pz = q - 2;
       const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
       if (q > q_first + 1)
-        sor_patch<PER, ZP_BLK != 0>(r2, &s_red[ZP_BLK * PL], ia, ib, offL, offR, offU, offD, r3,
-                                    r1, f2p, p, fl, zlo, zhi);
+        sor_patch<PER, ZP_BLK != 0, true>(r2, &s_red[ZP_BLK * PL], ia, ib, offL, offR, offU, offD,
+                                          r3, r1, f2p, p, fl, zlo, zhi);
       if (MODE == kDown && act) {
-        s_fin[ZP_BLK * PL + ia] = pack(r2.a);
-        s_fin[ZP_BLK * PL + ib] = pack(r2.b);
+        s_fin[ZP_BLK * PL + ia] = pack_p(r2.a);
+        s_fin[ZP_BLK * PL + ib] = pack_p(r2.b);
       }
       if (act && out && pz >= z0 && pz < z1) {
-        *reinterpret_cast<float4*>(u_out + (size_t)pz * plane + offA) = pack(r2.a);
-        *reinterpret_cast<float4*>(u_out + (size_t)pz * plane + offB) = pack(r2.b);
+        float* dst = u_out + (size_t)pz * plane + offA;
+        *reinterpret_cast<float4*>(dst) = pack(r2.a);
+        *reinterpret_cast<float4*>(dst + p.nx) = pack(r2.b);
       }
     }
     // [D] defect of plane q-3 and its 2x2x2 restriction
@@ -519,8 +542,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     f3p = f2p; f2p = f1;
   };
 
-  issue(q_first);
-  issue(q_first + 1);
+  constexpr int Q0 = ((-HZ) % 4 + 4) % 4;  // q_first mod 4
+  issue(std::integral_constant<int, Q0>{}, std::integral_constant<int, (Q0 + 3) % 4>{}, q_first);
+  issue(std::integral_constant<int, (Q0 + 1) % 4>{}, std::integral_constant<int, Q0>{},
+        q_first + 1);
   for (int q = q_first; q <= q_last; q += 4) {
     step(std::integral_constant<int, 0>{}, q);
     if (q + 1 > q_last) break;
@@ -533,8 +558,18 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   cp_async_wait<0>();
 }
 
+// Register caps.  The register file is split among the four schedulers, so
+// two 7-warp CTAs (down leg, 16-row tiles) fit on an SM at <= 128 registers;
+// the 6-warp up leg fits two at any cap up to 168 and runs fastest at 112
+// (three, at <= 96, spill and run slower).  The 32-row tiles take one CTA
+// per SM (their shared memory alone decides).
+template <int MODE, int TY>
+constexpr int fused_max_regs() {
+  return TY == 16 ? (MODE == kUp ? 112 : 128) : 168;
+}
+
 template <int MODE, bool ZERO, bool PER, int TX, int TY>
-__global__ void __launch_bounds__(Shape<MODE, TX, TY>::NT)
+__global__ void __maxnreg__((fused_max_regs<MODE, TY>()))
     k_fused(const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
             const float* __restrict__ ec, float* __restrict__ fc, FusedParams p) {
   extern __shared__ float4 smem[];
