@@ -43,6 +43,9 @@ namespace batch {
 
 constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4, false>::NT;  // 216
 constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4, false>::SMEM;
+static_assert(fused::Shape<fused::kUp, 64, 16, 4, false>::SMEM <= kSmem &&
+                  fused::Shape<fused::kUp, 32, 16, 4, false>::SMEM <= kSmem,
+              "an up-leg tile needs more shared memory than the CTA has");
 constexpr int kMaxL = 16;
 constexpr int kChunk = 32768;   // cells per chunk item
 constexpr int kFusedMinN = 32;  // levels of at least 32^3 use the fused tiles
@@ -558,25 +561,25 @@ __device__ __forceinline__ void tile_leg(bool down, bool per, const GridDev& g, 
     const bool zg = (l < g.L - 1) || zero_finest;
     if (zg) {
       if (per)
-        fused::fused_tile<fused::kDown, true, true, TX, 16, 4, true, false>(
+        fused::fused_tile<fused::kDown, true, true, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, true, false, TX, 16, 4, true, false>(
+        fused::fused_tile<fused::kDown, true, false, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     } else {
       if (per)
-        fused::fused_tile<fused::kDown, false, true, TX, 16, 4, true, false>(
+        fused::fused_tile<fused::kDown, false, true, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, false, false, TX, 16, 4, true, false>(
+        fused::fused_tile<fused::kDown, false, false, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     }
   } else {
     if (per)
-      fused::fused_tile<fused::kUp, false, true, TX, 16, 4, true, false>(
+      fused::fused_tile<fused::kUp, false, true, TX, 16, 4, false, kThreads>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
     else
-      fused::fused_tile<fused::kUp, false, false, TX, 16, 4, true, false>(
+      fused::fused_tile<fused::kUp, false, false, TX, 16, 4, false, kThreads>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
   }
 }

@@ -84,9 +84,10 @@ using fused::params;
 bool fused_ok(Grid g, const Bc& bc) {
   const bool hom = bc.kind == BC_PERIODIC || bc.kind == BC_ZEROGRAD ||
                    (bc.kind == BC_FIXED && bc.value == 0.0);
-  // widths the 64- or 32-wide tiles divide, rows in 16s, planes in chunks of 8
+  // widths the 64- or 32-wide tiles divide, rows in 16s, planes in chunks of 8;
+  // element offsets of 32 bits
   return hom && g.nx >= 32 && g.ny >= 32 && g.nz >= 32 && g.nx % 32 == 0 && g.ny % 16 == 0 &&
-         g.nz % 8 == 0 && (g.nx < 64 || g.nx % 64 == 0);
+         g.nz % 8 == 0 && (g.nx < 64 || g.nx % 64 == 0) && g.cells() < (1LL << 32);
 }
 
 bool fused_cfg_ok(Grid g, TileCfg cfg) {

@@ -235,72 +235,64 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // (x, y) part of the trilinear prolongation of one coarse plane at a patch:
 // rows gyA (even: coarse rows Y-1, Y) and gyA+1 (odd: Y, Y+1), Y = gyA/2;
-// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  The 3 x 4
-// coarse columns are resolved once per thread (CoarseIdx: wrapped indices,
-// or edge indices with the ghost sign s for the non-periodic rules), so a
-// plane costs twelve loads (xy_load) and the weighting (xy_combine).  Patches
-// outside the level get clamped, in-bounds indices; their values are unused.
-// COH: the coarse values may have been written earlier in the same launch by
-// another CTA (the batched solver), so read them through L2 (ld.global.cg)
-// rather than the read-only path.
+// four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  The up leg
+// stages the coarse cells under its tile in shared memory, one plane at a
+// time: CX columns from x0/2 - 4 and CY rows from y0/2 - HY/2 - 1, wrapped
+// (periodic) or zero-filled outside the level.  A thread's 3 x 4 block then
+// starts at tile row tp, column 1 + 2 tr; for the non-periodic rules its
+// indices are clamped to the level's edge cells and carry the ghost sign s
+// (CoarseIdx).  Patches outside the level read clamped indices; their values
+// are unused.
 struct Coarse12 {
   float c[3][4];
 };
 
 template <bool PER>
 struct CoarseIdx {
-  int col[4];  // coarse x
-  int row[3];  // coarse y * cnx
-  float sx[4], sy[3];  // ghost signs (non-periodic rules; 1 inside)
+  int col[4];  // tile column (non-periodic rules)
+  int row[3];  // tile row
+  float sx[4], sy[3];  // ghost signs (1 inside)
 };
 
 template <bool PER>
-__device__ __forceinline__ CoarseIdx<PER> coarse_idx(const FusedParams& p, int gx4, int gyA) {
+__device__ __forceinline__ CoarseIdx<PER> coarse_idx(const FusedParams& p, int gx4, int gyA,
+                                                     int cx0, int cy0) {
   const int cnx = p.nx >> 1, cny = p.ny >> 1;
   const int X0 = gx4 >> 1, Y = gyA >> 1;
   CoarseIdx<PER> ci;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int Xc = X0 - 1 + a;
-    ci.sx[a] = 1.f;
-    if (PER) ci.col[a] = wrap(Xc, cnx);
-    else if (Xc < 0) { ci.col[a] = 0; ci.sx[a] = p.s; }
-    else if (Xc >= cnx) { ci.col[a] = cnx - 1; ci.sx[a] = p.s; }
-    else ci.col[a] = Xc;
+    ci.sx[a] = (Xc < 0 || Xc >= cnx) ? p.s : 1.f;
+    ci.col[a] = (Xc < 0 ? 0 : (Xc >= cnx ? cnx - 1 : Xc)) - cx0;
   }
 #pragma unroll
   for (int yy = 0; yy < 3; ++yy) {
     const int Yc = Y - 1 + yy;
-    int Yi = Yc;
-    ci.sy[yy] = 1.f;
-    if (PER) Yi = wrap(Yc, cny);
-    else if (Yc < 0) { Yi = 0; ci.sy[yy] = p.s; }
-    else if (Yc >= cny) { Yi = cny - 1; ci.sy[yy] = p.s; }
-    ci.row[yy] = Yi * cnx;
+    ci.sy[yy] = (Yc < 0 || Yc >= cny) ? p.s : 1.f;
+    ci.row[yy] = (Yc < 0 ? 0 : (Yc >= cny ? cny - 1 : Yc)) - cy0;
   }
   return ci;
 }
 
-// The 3 x 4 coarse values of coarse plane Kc (any index from -2 to cnz + 1:
-// wrapped, or clamped with the ghost sign), ghosts applied.
-template <bool PER, bool COH>
-__device__ __forceinline__ Coarse12 xy_load(const float* __restrict__ ec, const FusedParams& p,
-                                            const CoarseIdx<PER>& ci, int Kc) {
-  const int cnz = p.nz >> 1;
-  float sz = 1.f;
-  if (PER) Kc = wrap(Kc, cnz);
-  else if (Kc < 0) { Kc = 0; sz = p.s; }
-  else if (Kc >= cnz) { Kc = cnz - 1; sz = p.s; }
-  const float* base = ec + (size_t)Kc * (size_t)((p.nx >> 1) * (p.ny >> 1));
+// The 3 x 4 coarse values of a staged plane S (sz: the ghost sign of a plane
+// outside a non-periodic level), ghosts applied.
+template <bool PER, int CX>
+__device__ __forceinline__ Coarse12 xy_read(const float* S, const CoarseIdx<PER>& ci, int tr,
+                                            int tp, float sz) {
   Coarse12 r;
+  if (PER) {
+    const float* b = S + tp * CX + 1 + 2 * tr;
 #pragma unroll
-  for (int yy = 0; yy < 3; ++yy) {
-    const float* rowp = base + ci.row[yy];
+    for (int yy = 0; yy < 3; ++yy)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float v = COH ? __ldcg(rowp + ci.col[a]) : __ldg(rowp + ci.col[a]);
-      r.c[yy][a] = PER ? v : sz * (ci.sy[yy] * (ci.sx[a] * v));
-    }
+      for (int a = 0; a < 4; ++a) r.c[yy][a] = b[yy * CX + a];
+  } else {
+#pragma unroll
+    for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        r.c[yy][a] = sz * (ci.sy[yy] * (ci.sx[a] * S[ci.row[yy] * CX + ci.col[a]]));
   }
   return r;
 }
@@ -347,14 +339,19 @@ struct Shape {
   static constexpr int NT = RT * RP;                   // threads
   static constexpr int PL = RS * RR;                   // float4 per shared plane
   static constexpr int NU = 4, NF = 4, NRED = 2, NFIN = (MODE == kDown) ? 2 : 0;
-  static constexpr size_t SMEM = (size_t)(NU + NF + NRED + NFIN) * PL * 16;
+  static constexpr int CX = TX / 2 + 8;  // coarse tile columns (up leg)
+  static constexpr int CY = RP + 2;      // coarse tile rows
+  static constexpr int NC = (MODE == kUp) ? 2 * CX * CY : 0;  // floats of the two coarse slots
+  static constexpr size_t SMEM = (size_t)(NU + NF + NRED + NFIN) * PL * 16 + (size_t)NC * 4;
 };
 
 // The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
-// Shape::SMEM bytes; threads tid >= Shape::NT of a larger CTA take part in
-// the barriers only.
-template <int MODE, bool ZERO, bool PER, int TX, int TY, int HYO = 0, bool COH = false,
-          bool PAD = true>
+// Shape::SMEM bytes.  NTB: the CTA's size when it is larger than Shape::NT
+// (0: exactly NT); threads tid >= Shape::NT of a larger CTA take part in the
+// barriers only.  Element offsets are 32-bit: levels have fewer than 2^32
+// cells (fused_ok).
+template <int MODE, bool ZERO, bool PER, int TX, int TY, int HYO = 0, bool PAD = true,
+          int NTB = 0>
 __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, const float* f,
                                            const float* ec, float* fc,
                                            const FusedParams& p, int bx, int by, int bz,
@@ -365,9 +362,11 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   float4* s_f = s_u + S_::NU * PL;        // [4][PL] planes of f (async copies)
   float4* s_red = s_f + S_::NF * PL;      // [2][PL] red-updated planes
   float4* s_fin = s_red + S_::NRED * PL;  // [2][PL] final planes (down leg)
+  float* s_c = reinterpret_cast<float*>(s_fin + S_::NFIN * PL);  // [2][CY][CX] coarse (up leg)
 
-  const int tid = threadIdx.x < S_::NT ? threadIdx.x : 0;  // spare threads mirror thread 0
-  const bool act = threadIdx.x < S_::NT;
+  constexpr bool SPARE = NTB > S_::NT;  // the CTA has threads without a patch
+  const int tid = (!SPARE || threadIdx.x < S_::NT) ? threadIdx.x : 0;  // spare: mirror thread 0
+  const bool act = !SPARE || threadIdx.x < S_::NT;
   const int tr = tid % RT, tp = tid / RT;
   const int x0 = bx * TX, y0 = by * TY;
   const int z0 = bz * p.cz;
@@ -384,8 +383,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   fl.ylo = !PER && gyA == 0;
   fl.yhi = !PER && gyA + 1 == p.ny - 1;
   const bool out = tr >= 1 && tr <= TX / 4 && tp >= HY / 2 && tp < HY / 2 + TY / 2;
-  const size_t plane = (size_t)p.nx * p.ny;
-  const size_t offA = col_ok ? (size_t)gyAw * p.nx + gx4w : 0;  // row a; row b is nx further
+  const unsigned plane = (unsigned)p.nx * (unsigned)p.ny;
+  const unsigned offA = col_ok ? (unsigned)gyAw * p.nx + gx4w : 0u;  // row a; row b is nx further
   const int ia = (2 * tp) * RS + tr, ib = ia + RS;  // shared indices of rows a, b
   const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
   const int offU = tp > 0 ? -RS : 0, offD = tp < RP - 1 ? RS : 0;
@@ -398,21 +397,43 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     if (act && qu <= q_last) {
       if (!ZERO) {
         const bool in = col_ok && (PER || (qu >= 0 && qu < p.nz));
-        const int w = PER ? wrap(qu, p.nz) : (in ? qu : 0);
-        const float* src = u_in + (size_t)w * plane + offA;
+        const unsigned o = (unsigned)(PER ? wrap(qu, p.nz) : (in ? qu : 0)) * plane + offA;
         float4* d = &s_u[SU * PL];
-        cp_async16(&d[ia], src, in ? 16 : 0);
-        cp_async16(&d[ib], src + p.nx, in ? 16 : 0);
+        cp_async16(&d[ia], u_in + o, in ? 16 : 0);
+        cp_async16(&d[ib], u_in + (o + p.nx), in ? 16 : 0);
       }
       const int qf = qu - 1;
       const bool inf = col_ok && (PER || (qf >= 0 && qf < p.nz));
-      const int w = PER ? wrap(qf, p.nz) : (inf ? qf : 0);
-      const float* src = f + (size_t)w * plane + offA;
+      const unsigned o = (unsigned)(PER ? wrap(qf, p.nz) : (inf ? qf : 0)) * plane + offA;
       float4* d = &s_f[SF * PL];
-      cp_async16(&d[ia], src, inf ? 16 : 0);
-      cp_async16(&d[ib], src + p.nx, inf ? 16 : 0);
+      cp_async16(&d[ia], f + o, inf ? 16 : 0);
+      cp_async16(&d[ib], f + (o + p.nx), inf ? 16 : 0);
     }
-    cp_async_commit();
+  };
+
+  // Up leg: copy coarse plane Kc (any index from -2 to cnz + 1) into slot SL.
+  const int cx0 = (x0 >> 1) - 4, cy0 = (y0 >> 1) - HY / 2 - 1;
+  auto copy_coarse = [&](auto SLc, int Kc) {
+    constexpr int SL = decltype(SLc)::value, CW = S_::CX / 4;  // float4 per tile row
+    const int cnx = p.nx >> 1, cny = p.ny >> 1, cnz = p.nz >> 1;
+    const int t = threadIdx.x;
+    if (t < CW * S_::CY) {
+      const int i = t / CW, j = t - i * CW;
+      int X = cx0 + 4 * j, Y = cy0 + i, K = Kc;
+      bool in = true;
+      if (PER) {
+        X = wrap(X, cnx); Y = wrap(Y, cny); K = wrap(K, cnz);
+      } else {
+        in = X >= 0 && X < cnx && Y >= 0 && Y < cny;
+        K = K < 0 ? 0 : (K >= cnz ? cnz - 1 : K);
+        if (!in) { X = 0; Y = 0; }
+      }
+      cp_async16(s_c + SL * S_::CX * S_::CY + i * S_::CX + 4 * j,
+                 ec + (((unsigned)K * cny + Y) * cnx + X), in ? 16 : 0);
+    }
+  };
+  auto plane_sign = [&](int Kc) {
+    return (!PER && (Kc < 0 || Kc >= (p.nz >> 1))) ? p.s : 1.f;
   };
 
   Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
@@ -420,19 +441,24 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   // Up leg: the (x, y)-interpolated coarse planes K-1, K, K+1 around fine
   // planes 2K, 2K+1 live in W[0] (even K) and W[1] (odd K); fine plane 2K
   // takes 3/4 of plane K and 1/4 of plane K-1, fine plane 2K+1 3/4 of K and
-  // 1/4 of K+1.  The loads of plane K+1 are issued at fine plane 2K and
-  // combined at 2K+1 (in the batched solver, which has no registers to
-  // spare, loaded and combined at 2K+1).
-  constexpr bool PF = !COH;
+  // 1/4 of K+1.  Coarse plane K+1 is combined at fine plane 2K+1 from shared
+  // slot (K+1) mod 2, whose copy was issued two steps earlier; plane K+2 is
+  // then copied into slot K mod 2.
   Patch W[2];
-  Coarse12 pre;
   CoarseIdx<PER> ci;
   if (MODE == kUp) {
-    ci = coarse_idx<PER>(p, gx4, gyA);
+    if (!PER) ci = coarse_idx<PER>(p, gx4, gyA, cx0, cy0);
     // q_first = z0 - 2 with z0 a multiple of 8: K0 = q_first / 2 is odd
     const int K0 = q_first >> 1;
-    W[0] = xy_combine(xy_load<PER, COH>(ec, p, ci, K0 - 1));
-    W[1] = xy_combine(xy_load<PER, COH>(ec, p, ci, K0));
+    copy_coarse(std::integral_constant<int, 0>{}, K0 - 1);
+    copy_coarse(std::integral_constant<int, 1>{}, K0);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    W[0] = xy_combine(xy_read<PER, S_::CX>(s_c, ci, tr, tp, plane_sign(K0 - 1)));
+    W[1] = xy_combine(xy_read<PER, S_::CX>(s_c + S_::CX * S_::CY, ci, tr, tp, plane_sign(K0)));
+    __syncthreads();
+    copy_coarse(std::integral_constant<int, 0>{}, K0 + 1);  // committed with plane q_first
   }
 
   // One plane step.  J = (q - q_first) mod 4 fixes the ring slots and the
@@ -449,6 +475,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     __syncthreads();     // ... and everyone's; the previous step is finished
     issue(std::integral_constant<int, (QP + 2) % 4>{}, std::integral_constant<int, (QP + 1) % 4>{},
           q + 2);
+    if (MODE == kUp && (QP & 1) && q + 2 <= q_last)  // q = 2K+1: plane K+2 into slot K mod 2
+      copy_coarse(std::integral_constant<int, (QP >> 1) & 1>{}, (q >> 1) + 2);
+    cp_async_commit();
     // [A] plane q of u (old values), plus the prolonged correction (up leg)
     Patch r0 = zero_patch();
     if (!ZERO) {
@@ -458,7 +487,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     if (MODE == kUp) {
       constexpr int KP = (QP >> 1) & 1;  // parity of K = floor(q / 2)
       const int K = q >> 1;
-      if (QP & 1) W[1 - KP] = xy_combine(PF ? pre : xy_load<PER, COH>(ec, p, ci, K + 1));
+      if (QP & 1)
+        W[1 - KP] = xy_combine(xy_read<PER, S_::CX>(s_c + (1 - KP) * S_::CX * S_::CY, ci, tr, tp,
+                                                     plane_sign(K + 1)));
       if (col_ok && (PER || (q >= 0 && q < p.nz))) {
         const float2 w0 = make_float2(0.75f, 0.75f), w1 = make_float2(0.25f, 0.25f);
         const Patch& PK = W[KP];
@@ -468,7 +499,6 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         r0.b.e = __ffma2_rn(w1, PN.b.e, __ffma2_rn(w0, PK.b.e, r0.b.e));
         r0.b.o = __ffma2_rn(w1, PN.b.o, __ffma2_rn(w0, PK.b.o, r0.b.o));
       }
-      if (PF && !(QP & 1)) pre = xy_load<PER, COH>(ec, p, ci, K + 1);
       if (act) {
         s_u[SL_U * PL + ia] = pack_p(r0.a);  // the neighbours read corrected values
         s_u[SL_U * PL + ib] = pack_p(r0.b);
@@ -515,9 +545,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         s_fin[ZP_BLK * PL + ib] = pack_p(r2.b);
       }
       if (act && out && pz >= z0 && pz < z1) {
-        float* dst = u_out + (size_t)pz * plane + offA;
-        *reinterpret_cast<float4*>(dst) = pack(r2.a);
-        *reinterpret_cast<float4*>(dst + p.nx) = pack(r2.b);
+        const unsigned o = (unsigned)pz * plane + offA;
+        *reinterpret_cast<float4*>(u_out + o) = pack(r2.a);
+        *reinterpret_cast<float4*>(u_out + (o + p.nx)) = pack(r2.b);
       }
     }
     // [D] defect of plane q-3 and its 2x2x2 restriction
@@ -531,9 +561,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
           acc = s2;
         } else {
           acc = add2(acc, s2);
-          const int cnx = p.nx >> 1, cny = p.ny >> 1;
-          const int X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
-          *reinterpret_cast<float2*>(fc + ((size_t)Zc * cny + Yc) * cnx + X) =
+          const unsigned cnx = (unsigned)p.nx >> 1, cny = (unsigned)p.ny >> 1;
+          const unsigned X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
+          *reinterpret_cast<float2*>(fc + ((Zc * cny + Yc) * cnx + X)) =
               __fmul2_rn(make_float2(0.125f, 0.125f), acc);
         }
       }
@@ -544,8 +574,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
 
   constexpr int Q0 = ((-HZ) % 4 + 4) % 4;  // q_first mod 4
   issue(std::integral_constant<int, Q0>{}, std::integral_constant<int, (Q0 + 3) % 4>{}, q_first);
+  cp_async_commit();
   issue(std::integral_constant<int, (Q0 + 1) % 4>{}, std::integral_constant<int, Q0>{},
         q_first + 1);
+  cp_async_commit();
   for (int q = q_first; q <= q_last; q += 4) {
     step(std::integral_constant<int, 0>{}, q);
     if (q + 1 > q_last) break;
@@ -559,13 +591,12 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
 }
 
 // Register caps.  The register file is split among the four schedulers, so
-// two 7-warp CTAs (down leg, 16-row tiles) fit on an SM at <= 128 registers;
-// the 6-warp up leg fits two at any cap up to 168 and runs fastest at 112
-// (three, at <= 96, spill and run slower).  The 32-row tiles take one CTA
-// per SM (their shared memory alone decides).
+// two 7-warp CTAs (down leg, 16-row tiles) fit on an SM at <= 128 registers
+// and three 6-warp CTAs (up leg) at <= 96; the 32-row tiles take one CTA per
+// SM (their shared memory alone decides).
 template <int MODE, int TY>
 constexpr int fused_max_regs() {
-  return TY == 16 ? (MODE == kUp ? 112 : 128) : 168;
+  return TY == 16 ? (MODE == kUp ? 96 : 128) : 168;
 }
 
 template <int MODE, bool ZERO, bool PER, int TX, int TY>
