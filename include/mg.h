@@ -203,6 +203,16 @@ mg_status mg_op_defect(int prec, int nx, int ny, int nz, double h, mg_bc bc, dou
                        const double *faces_dev, const void *u_dev, const void *f_dev,
                        void *d_dev, void *stream);
 
+/* The exact conversions of the fixed-point outer loop (binary64 / binary32 to
+ * and from 64-bit integers, round to nearest with ties to even, computed in
+ * integer arithmetic), applied elementwise to n device values: kind 0 double
+ * -> int64, 1 int64 -> double, 2 double -> float, 3 float -> int64, 4 int64
+ * -> float.  in_dev and out_dev hold n elements of the kind's input and output
+ * types and must not overlap.  Results are the correctly rounded values (the
+ * IEEE 754 conversion); out-of-range inputs saturate.  Errors: MG_ERR_ARG for
+ * a bad kind, n < 0 or a null pointer with n > 0. */
+mg_status mg_op_convert(int kind, long long n, const void *in_dev, void *out_dev, void *stream);
+
 /* Acceleration g = [g_x | g_y | g_z] (3 N doubles) of an FP64 potential at
  * cell centres (Sec. 3.2.3), as in mg_solve_gravity. */
 mg_status mg_op_gravity(int nx, int ny, int nz, double h, mg_bc bc, double bc_value,

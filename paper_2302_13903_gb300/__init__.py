@@ -32,7 +32,7 @@ EXPORTS = [
     "mg_batch_last_error", "mg_batch_graph", "mg_required_bytes", "mg_ctx_autotune",
     "mg_ctx_tile_config", "mg_batch_phase_ms", "mg_solve_gravity", "mg_op_gravity",
     "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
-    "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error",
+    "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error", "mg_op_convert",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
            "correct", "source", "fused_down", "fused_up", "gravity"]
@@ -116,6 +116,8 @@ def lib():
             L.mg_solve_gravity.restype = i
             L.mg_op_gravity.argtypes = [i, i, i, d, i, d, p, p, p, p]
             L.mg_op_gravity.restype = i
+            L.mg_op_convert.argtypes = [i, ctypes.c_longlong, p, p, p]
+            L.mg_op_convert.restype = i
             L.mg_solve_host.restype = i
             L.mg_destroy.argtypes = [p]
             L.mg_destroy.restype = i
@@ -358,6 +360,23 @@ def _prec_of(t):
 def _faces_ptr(faces):
     import torch
     return _dptr(faces, torch.float64) if faces is not None else None
+
+
+# mg_op_convert kinds: (input dtype, output dtype)
+CONVERT_KINDS = {0: ("float64", "int64"), 1: ("int64", "float64"), 2: ("float64", "float32"),
+                 3: ("float32", "int64"), 4: ("int64", "float32")}
+
+
+def op_convert(kind, x, stream=None):
+    """mg_op_convert: the fixed-point loop's exact conversion `kind` of a CUDA tensor."""
+    import torch
+    src, dst = CONVERT_KINDS[kind]
+    if x.dtype != getattr(torch, src) or not x.is_contiguous():
+        raise TypeError(f"kind {kind} converts contiguous {src} tensors")
+    out = torch.empty(x.shape, dtype=getattr(torch, dst), device=x.device)
+    _check(lib().mg_op_convert(kind, x.numel(), ctypes.c_void_p(x.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def op_gravity(phi, h, bc=PERIODIC, bc_value=0.0, faces=None, stream=None):

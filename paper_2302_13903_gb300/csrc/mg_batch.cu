@@ -34,6 +34,7 @@
 
 #include "../../include/mg.h"
 #include "mg_bottom.cuh"
+#include "mg_convert.cuh"
 #include "mg_device.cuh"
 #include "mg_fused.cuh"
 #include "mg_internal.h"
@@ -249,7 +250,7 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
       const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
       mb = bits > mb ? bits : mb;
     } else if (TYPE == PH_R0) {
-      const float x = (float)fma(a0, rho[t], -b0);  // (f - mean) sc
+      const float x = cvt::d2f_rn(fma(a0, rho[t], -b0));  // (f - mean) sc
       float xs = x;
       if (bc == BC_FIXED && bcval != 0.0) {  // L_h(0): 2 b per fixed-value ghost
         const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
@@ -268,14 +269,14 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
     } else if (TYPE == PH_EMAX) {
       mx = fmax(mx, (double)fabsf(e32[t]));
     } else if (TYPE == PH_TOFX) {
-      FX[t] = __double2ll_rn(fma(fpg * c2, rho[t], -mean * c2));
+      FX[t] = cvt::d2ll_rn(fma(fpg * c2, rho[t], -mean * c2));
     } else if (TYPE == PH_PSUM) {
       const long long v = PHI[t];
       s_hi += v >> 32;
       s_lo += v & 0xffffffffLL;
     } else if (TYPE == PH_PSUB) {
       // a grid that never reached the fixed-point loop has phi = 0 exactly
-      phi[t] = fx ? (double)PHI[t] * (1.0 / two_S) - mean : 0.0;
+      phi[t] = fx ? cvt::ll2d_rn(PHI[t]) * (1.0 / two_S) - mean : 0.0;
     }
   }
   if (TYPE == PH_R0) {

@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 
+#include "mg_convert.cuh"
 #include "mg_device.cuh"
 #include "mg_internal.h"
 
@@ -80,7 +81,7 @@ __global__ void k_f64_to_fx(double* a, long long n, double mu, double c) {
   long long* q = reinterpret_cast<long long*>(a);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    q[t] = __double2ll_rn((a[t] - mu) * c);
+    q[t] = cvt::d2ll_rn((a[t] - mu) * c);
 }
 
 // out[t] = q[t] * c - m as a double (out may alias q), with m = total[0] * cm
@@ -90,7 +91,7 @@ __global__ void k_fx_to_f64(const long long* q, double* out, long long n, double
   const double m = total ? total[0] * cm : 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    out[t] = __ll2double_rn(q[t]) * c - m;
+    out[t] = cvt::ll2d_rn(q[t]) * c - m;
 }
 
 // |x| as an unsigned integer: for non-negative doubles (and floats) the order
@@ -103,18 +104,30 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 // double whose bits are the largest |rho| pattern); two cells per step.
 __global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
                             double* __restrict__ sum, double* __restrict__ mx) {
-  double acc = 0.0;
+  // four independent sums per thread, so that consecutive adds do not wait
+  // on one another
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   unsigned long long m = 0;
-#pragma unroll 4
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
-       t += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < n2; t += 4 * stride) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 r = rho[t + k * stride];
+      acc[k] += r.x + r.y;
+      const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
+      m = a > m ? a : m;
+      m = b > m ? b : m;
+    }
+  }
+  for (; t < n2; t += stride) {
     const double2 r = rho[t];
-    acc += r.x + r.y;
+    acc[0] += r.x + r.y;
     const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
     m = a > m ? a : m;
     m = b > m ? b : m;
   }
-  const double bs = block_reduce<false>(acc);
+  const double bs = block_reduce<false>((acc[0] + acc[1]) + (acc[2] + acc[3]));
   const double bm = block_reduce<true>(__longlong_as_double((long long)m));
   if (threadIdx.x == 0) {
     sum[blockIdx.x] = bs;
@@ -132,7 +145,7 @@ __global__ void k_rho_to_r32(const double2* __restrict__ rho, float2* __restrict
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 r = rho[t];
-    const float x = (float)fma(a, r.x, -b), y = (float)fma(a, r.y, -b);
+    const float x = cvt::d2f_rn(fma(a, r.x, -b)), y = cvt::d2f_rn(fma(a, r.y, -b));
     r32[t] = make_float2(x, y);
     acc = fmaf(x, x, fmaf(y, y, acc));
     m = fmaxf(m, fmaxf(fabsf(x), fabsf(y)));
@@ -150,7 +163,7 @@ __global__ void k_rho_to_fx(const double* __restrict__ rho, long long* __restric
                             double a, double b) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    q[t] = __double2ll_rn(fma(a, rho[t], -b));
+    q[t] = cvt::d2ll_rn(fma(a, rho[t], -b));
 }
 
 __global__ void k_finish_sum_max(const double* __restrict__ sum, const double* __restrict__ mx,
@@ -480,7 +493,7 @@ __global__ void k_fx_finish_gravity(const long long* __restrict__ q, double* __r
     const long long r = t / gr.nx;
     const int j = (int)(r % gr.ny), k = (int)(r / gr.ny);
     const long long self = q[t];
-    phi[t] = __ll2double_rn(self) * c - m;
+    phi[t] = cvt::ll2d_rn(self) * c - m;
     const long long sy = gr.nx, sz = (long long)gr.nx * gr.ny;
     const long long xm = fx_nb_lite(q, bc, gr, self, i > 0, t - 1, i, j, k, 0, 0);
     const long long xp = fx_nb_lite(q, bc, gr, self, i < gr.nx - 1, t + 1, i, j, k, 0, 1);
@@ -488,9 +501,9 @@ __global__ void k_fx_finish_gravity(const long long* __restrict__ q, double* __r
     const long long yp = fx_nb_lite(q, bc, gr, self, j < gr.ny - 1, t + sy, i, j, k, 1, 1);
     const long long zm = fx_nb_lite(q, bc, gr, self, k > 0, t - sz, i, j, k, 2, 0);
     const long long zp = fx_nb_lite(q, bc, gr, self, k < gr.nz - 1, t + sz, i, j, k, 2, 1);
-    g[t] = -__ll2double_rn(xp - xm) * cg;
-    g[N + t] = -__ll2double_rn(yp - ym) * cg;
-    g[2 * N + t] = -__ll2double_rn(zp - zm) * cg;
+    g[t] = -cvt::ll2d_rn(xp - xm) * cg;
+    g[N + t] = -cvt::ll2d_rn(yp - ym) * cg;
+    g[2 * N + t] = -cvt::ll2d_rn(zp - zm) * cg;
   }
 }
 
@@ -518,6 +531,32 @@ cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, doubl
                              const double* total, double cm, cudaStream_t s) {
   ++g_launches;
   k_fx_to_f64<<<grid_for(n), kThreads, 0, s>>>(q, out, n, c, total, cm);
+  return cudaGetLastError();
+}
+
+template <int KIND>
+__global__ void k_convert(const void* __restrict__ in, void* __restrict__ out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (KIND == 0) static_cast<long long*>(out)[t] = cvt::d2ll_rn(static_cast<const double*>(in)[t]);
+    if (KIND == 1) static_cast<double*>(out)[t] = cvt::ll2d_rn(static_cast<const long long*>(in)[t]);
+    if (KIND == 2) static_cast<float*>(out)[t] = cvt::d2f_rn(static_cast<const double*>(in)[t]);
+    if (KIND == 3) static_cast<long long*>(out)[t] = cvt::f2ll_rn(static_cast<const float*>(in)[t]);
+    if (KIND == 4) static_cast<float*>(out)[t] = cvt::ll2f_rn(static_cast<const long long*>(in)[t]);
+  }
+}
+
+cudaError_t launch_convert(int kind, long long n, const void* in, void* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  ++g_launches;
+  switch (kind) {
+    case 0: k_convert<0><<<grid_for(n), kThreads, 0, s>>>(in, out, n); break;
+    case 1: k_convert<1><<<grid_for(n), kThreads, 0, s>>>(in, out, n); break;
+    case 2: k_convert<2><<<grid_for(n), kThreads, 0, s>>>(in, out, n); break;
+    case 3: k_convert<3><<<grid_for(n), kThreads, 0, s>>>(in, out, n); break;
+    case 4: k_convert<4><<<grid_for(n), kThreads, 0, s>>>(in, out, n); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -1412,6 +1412,14 @@ mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double ome
   return op_result(e, "vcycle_up");
 }
 
+mg_status mg_op_convert(int kind, long long n, const void* in, void* out, void* stream) {
+  if (kind < 0 || kind > 4 || n < 0 || (n > 0 && (!in || !out))) {
+    g_err = "mg_op_convert: invalid argument";
+    return MG_ERR_ARG;
+  }
+  return op_result(mg::launch_convert(kind, n, in, out, (cudaStream_t)stream), "convert");
+}
+
 mg_status mg_op_multipole_moments(int nx, int ny, int nz, double h, const double* rho, int lmax,
                                   int use_com, double* origin, double* Q, void* stream) {
   if (nx < 1 || ny < 1 || nz < 1 || !rho || !origin || !Q || lmax < 0 || lmax > 4) {

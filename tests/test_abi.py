@@ -126,3 +126,9 @@ def test_argument_validation_needs_no_gpu():
     assert L.mg_solve(None, None, 1.0, 1e-10, None, None, 1, None, None) == 1
     assert L.mg_destroy(None) == 0
     assert L.mg_op_smooth(0, 8, 8, 8, 0.1, 3, 0.0, None, 1.15, 1, 0, None, None, None) == 1
+    # mg_op_convert: a kind outside 0..4, a negative count, null arrays
+    assert L.mg_op_convert(5, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None) == 1
+    assert L.mg_op_convert(-1, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None) == 1
+    assert L.mg_op_convert(0, -1, ctypes.c_void_p(8), ctypes.c_void_p(8), None) == 1
+    assert L.mg_op_convert(2, 4, None, ctypes.c_void_p(8), None) == 1
+    assert L.mg_op_convert(4, 0, None, None, None) == 0  # nothing to do, no launch
