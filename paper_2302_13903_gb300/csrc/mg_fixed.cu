@@ -100,34 +100,81 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
 }
 
+// Exact sum of a thread's doubles in integer arithmetic: A (two's-complement
+// 128-bit, hi:lo) counts units of 2^B, with B = 60 below the binary exponent
+// of the largest significand unit seen so far.  A double m 2^k (m < 2^53) adds
+// m 2^(k - B) < 2^113, so a thread may add up to 2^14 values without
+// overflow; bits below 2^B (2^-112 of the largest value, and values below
+// 2^-1022) are dropped.  No FP64 arithmetic per value: that pipe, not memory,
+// would bound the pass.
+struct ExactSum {
+  unsigned long long lo = 0;
+  long long hi = 0;
+  int B = -100000;  // no value yet
+};
+
+__device__ __forceinline__ void exact_add(ExactSum& a, double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0) return;
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const int k = e - 1075;  // x = +-m 2^k
+  if (k - a.B > 60) {  // a new largest exponent: A >>= d (arithmetic), B += d
+    const int d = k - 60 - a.B;
+    if (d >= 128) {
+      a.lo = (unsigned long long)(a.hi >> 63);
+      a.hi >>= 63;
+    } else if (d >= 64) {
+      a.lo = (unsigned long long)(a.hi >> (d - 64));
+      a.hi >>= 63;
+    } else {
+      a.lo = (a.lo >> d) | ((unsigned long long)a.hi << (64 - d));
+      a.hi >>= d;
+    }
+    a.B = k - 60;
+  }
+  const int sh = k - a.B;  // <= 60
+  unsigned long long tlo = 0, thi = 0;
+  if (sh >= 0) {
+    tlo = m << sh;
+    thi = sh > 11 ? m >> (64 - sh) : 0;  // m < 2^53: bits reach the high word from sh = 12
+  } else if (sh > -64) {
+    tlo = m >> -sh;
+  }
+  if (u >> 63) {
+    const unsigned long long lo = a.lo - tlo;
+    a.hi = a.hi - (long long)thi - (lo > a.lo ? 1 : 0);
+    a.lo = lo;
+  } else {
+    const unsigned long long lo = a.lo + tlo;
+    a.hi = a.hi + (long long)thi + (lo < tlo ? 1 : 0);
+    a.lo = lo;
+  }
+}
+
+// The thread's sum as a double (rounded in the conversions of its two words).
+__device__ __forceinline__ double exact_value(const ExactSum& a) {
+  if (a.B == -100000) return 0.0;
+  return ldexp(fma((double)a.hi, 18446744073709551616.0, __ull2double_rn(a.lo)), a.B);
+}
+
 // Per-block partial sums of rho (sum[]) and maxima of |rho| (mx[], as the
 // double whose bits are the largest |rho| pattern); two cells per step.
 __global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
                             double* __restrict__ sum, double* __restrict__ mx) {
-  // four independent sums per thread, so that consecutive adds do not wait
-  // on one another
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  ExactSum acc;
   unsigned long long m = 0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (; t + 3 * stride < n2; t += 4 * stride) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const double2 r = rho[t + k * stride];
-      acc[k] += r.x + r.y;
-      const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
-      m = a > m ? a : m;
-      m = b > m ? b : m;
-    }
-  }
-  for (; t < n2; t += stride) {
+#pragma unroll 4
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
+       t += (long long)gridDim.x * blockDim.x) {
     const double2 r = rho[t];
-    acc[0] += r.x + r.y;
+    exact_add(acc, r.x);
+    exact_add(acc, r.y);
     const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
     m = a > m ? a : m;
     m = b > m ? b : m;
   }
-  const double bs = block_reduce<false>((acc[0] + acc[1]) + (acc[2] + acc[3]));
+  const double bs = block_reduce<false>(exact_value(acc));
   const double bm = block_reduce<true>(__longlong_as_double((long long)m));
   if (threadIdx.x == 0) {
     sum[blockIdx.x] = bs;
@@ -135,17 +182,21 @@ __global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
   }
 }
 
-// r32 = (a rho - b) rounded to FP32 (a = 4 pi G scale, b = mean scale);
-// per-block partial sums of r32^2 (FP32 per thread) and maxima of |r32|.
+// r32 = a rho - b in FP32 arithmetic (a = 4 pi G scale, b = mean scale, so
+// |a rho|, |b| <= 1 + |b| and the error is a few FP32 ulps of 1: this is only
+// the right-hand side of the first FP32 inner solve, whose exact residual the
+// fixed-point step recomputes); per-block partial sums of r32^2 (FP32 per
+// thread) and maxima of |r32|.  No FP64 arithmetic: rho reaches FP32 by the
+// integer conversion.
 __global__ void k_rho_to_r32(const double2* __restrict__ rho, float2* __restrict__ r32,
-                             long long n2, double a, double b, double* __restrict__ sum,
+                             long long n2, float a, float b, double* __restrict__ sum,
                              double* __restrict__ mx) {
   float acc = 0.f, m = 0.f;
 #pragma unroll 4
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 r = rho[t];
-    const float x = cvt::d2f_rn(fma(a, r.x, -b)), y = cvt::d2f_rn(fma(a, r.y, -b));
+    const float x = fmaf(a, cvt::d2f_rn(r.x), -b), y = fmaf(a, cvt::d2f_rn(r.y), -b);
     r32[t] = make_float2(x, y);
     acc = fmaf(x, x, fmaf(y, y, acc));
     m = fmaxf(m, fmaxf(fabsf(x), fabsf(y)));
@@ -564,6 +615,8 @@ cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, d
                              cudaStream_t s) {
   if (n % 2) return cudaErrorInvalidValue;
   const int nb = reduce_blocks(n / 2);
+  // at most 2^14 values per thread in the exact sums (2^32 cells, 34 GB of rho)
+  if (n > (long long)nb * kThreads * 16384) return cudaErrorInvalidValue;
   ++g_launches;
   k_rho_stats<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(rho), n / 2, partials,
                                       partials + nb);
@@ -578,8 +631,8 @@ cudaError_t launch_rho_to_r32(const double* rho, float* r32, long long n, double
   const int nb = reduce_blocks(n / 2);
   ++g_launches;
   k_rho_to_r32<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(rho),
-                                       reinterpret_cast<float2*>(r32), n / 2, a, b, partials,
-                                       partials + nb);
+                                       reinterpret_cast<float2*>(r32), n / 2, (float)a, (float)b,
+                                       partials, partials + nb);
   ++g_launches;
   k_finish_sum_max<<<1, kThreads, 0, s>>>(partials, partials + nb, nb, out);
   return cudaGetLastError();
