@@ -56,6 +56,20 @@ __device__ __forceinline__ double ll2d_rn(long long v) {
   return __longlong_as_double((long long)((s << 63) + ((uint64_t)(p + 1022) << 52) + q));
 }
 
+// int64 v times 2^-S -> binary64: the exponent of ll2d_rn(v) lowered by S,
+// which is exact while the result stays a normal number (|S| well inside the
+// exponent range); otherwise a rounded scale in FP64.
+__device__ __forceinline__ double ll2d_pow2_rn(long long v, int S) {
+  if (v == 0) return 0.0;
+  const uint64_t s = (uint64_t)v >> 63;
+  const uint64_t a = s ? 0 - (uint64_t)v : (uint64_t)v;
+  const int p = 63 - __clzll((long long)a);
+  const int E = p + 1023 - S;  // biased exponent of the result
+  if (E < 1 || E > 2046) return ldexp(ll2d_rn(v), -S);
+  const uint64_t q = p <= 52 ? (a << (52 - p)) : shr_rne(a, p - 52);
+  return __longlong_as_double((long long)((s << 63) + ((uint64_t)(E - 1) << 52) + q));
+}
+
 // binary64 -> binary32, subnormal results included.
 __device__ __forceinline__ float d2f_rn(double x) {
   const uint64_t u = (uint64_t)__double_as_longlong(x);

@@ -84,14 +84,14 @@ __global__ void k_f64_to_fx(double* a, long long n, double mu, double c) {
     q[t] = cvt::d2ll_rn((a[t] - mu) * c);
 }
 
-// out[t] = q[t] * c - m as a double (out may alias q), with m = total[0] * cm
-// when total is given (the mean of the integers, from their device sum).
-__global__ void k_fx_to_f64(const long long* q, double* out, long long n, double c,
-                            const double* __restrict__ total, double cm) {
-  const double m = total ? total[0] * cm : 0.0;
+// out[t] = (q[t] - M) 2^-S as a double (out may alias q), M = *mean (the
+// integers' rounded mean) when given, else 0.  Integer arithmetic only.
+__global__ void k_fx_to_f64(const long long* q, double* out, long long n, int S,
+                            const long long* __restrict__ mean) {
+  const long long M = mean ? mean[0] : 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    out[t] = cvt::ll2d_rn(q[t]) * c - m;
+    out[t] = cvt::ll2d_pow2_rn(q[t] - M, S);
 }
 
 // |x| as an unsigned integer: for non-negative doubles (and floats) the order
@@ -508,7 +508,11 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
 }
 
 // out[0] = the total of the (hi, lo) pairs as a double, summed exactly.
-__global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb,
+// The integers' sum from the per-block (hi, lo) partials (value = hi 2^32 +
+// lo) and their mean rounded to an integer, exactly: N = 2^log2n cells, so the
+// mean is the 128-bit sum shifted right with rounding (ties up).  out[0]: the
+// sum as a double; out[1]: the mean's bits as a long long.
+__global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb, int log2n,
                                 double* __restrict__ out) {
   __shared__ long long sh[kThreads], sl[kThreads];
   long long h = 0, l = 0;
@@ -525,6 +529,22 @@ __global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb,
       l += sl[q];
     }
     out[0] = (double)h * 4294967296.0 + (double)l;
+    // 128-bit sum: h 2^32 + l
+    const long long shi = h >> 32;
+    const unsigned long long t = (unsigned long long)h << 32;
+    unsigned long long slo = t + (unsigned long long)l;
+    long long sh2 = shi + (l < 0 ? -1 : 0) + (slo < t ? 1 : 0);
+    // + 2^(log2n - 1), then an arithmetic shift right by log2n (0 <= log2n < 64)
+    long long mean = 0;
+    if (log2n == 0) {
+      mean = (long long)slo;
+    } else {
+      const unsigned long long half = 1ULL << (log2n - 1);
+      const unsigned long long lo2 = slo + half;
+      sh2 += lo2 < slo ? 1 : 0;
+      mean = (long long)((lo2 >> log2n) | ((unsigned long long)sh2 << (64 - log2n)));
+    }
+    reinterpret_cast<long long*>(out)[1] = mean;
   }
 }
 
@@ -534,17 +554,17 @@ __global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb,
 // -(PHI_{i+1} - PHI_{i-1}) rounded once and scaled by 2^-S / (2 h).
 // Writes phi (as doubles, into a different buffer than q) and g = [gx|gy|gz].
 __global__ void k_fx_finish_gravity(const long long* __restrict__ q, double* __restrict__ phi,
-                                    double* __restrict__ g, Grid gr, FxBcLite bc, double c,
-                                    double cg, const double* __restrict__ total, double cm) {
-  const double m = total ? total[0] * cm : 0.0;
+                                    double* __restrict__ g, Grid gr, FxBcLite bc, int S,
+                                    double cg, const long long* __restrict__ mean) {
+  const long long M = mean ? mean[0] : 0;
   const long long N = gr.cells();
+  const dev::Split sp(gr.nx, gr.ny);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
        t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % gr.nx);
-    const long long r = t / gr.nx;
-    const int j = (int)(r % gr.ny), k = (int)(r / gr.ny);
+    int i, j, k;
+    sp(t, i, j, k);
     const long long self = q[t];
-    phi[t] = cvt::ll2d_rn(self) * c - m;
+    phi[t] = cvt::ll2d_pow2_rn(self - M, S);
     const long long sy = gr.nx, sz = (long long)gr.nx * gr.ny;
     const long long xm = fx_nb_lite(q, bc, gr, self, i > 0, t - 1, i, j, k, 0, 0);
     const long long xp = fx_nb_lite(q, bc, gr, self, i < gr.nx - 1, t + 1, i, j, k, 0, 1);
@@ -578,10 +598,10 @@ cudaError_t launch_f64_to_fx(double* a, long long n, double mu, double c, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, double c,
-                             const double* total, double cm, cudaStream_t s) {
+cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, int S,
+                             const long long* mean, cudaStream_t s) {
   ++g_launches;
-  k_fx_to_f64<<<grid_for(n), kThreads, 0, s>>>(q, out, n, c, total, cm);
+  k_fx_to_f64<<<grid_for(n), kThreads, 0, s>>>(q, out, n, S, mean);
   return cudaGetLastError();
 }
 
@@ -711,8 +731,9 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
 }
 
 cudaError_t launch_fx_finish_gravity(const long long* q, double* phi, double* g, Grid gr,
-                                     const Bc& bc, double h, double two_pow_S,
-                                     const double* total, double cm, cudaStream_t s) {
+                                     const Bc& bc, double h, int S, const long long* mean,
+                                     cudaStream_t s) {
+  const double two_pow_S = std::ldexp(1.0, S);
   FxBcLite b;
   b.kind = bc.kind;
   b.c2 = 2.0 * two_pow_S;
@@ -720,13 +741,17 @@ cudaError_t launch_fx_finish_gravity(const long long* q, double* phi, double* g,
   b.faces = bc.faces;
   ++g_launches;
   k_fx_finish_gravity<<<grid_for(gr.cells()), kThreads, 0, s>>>(
-      q, phi, g, gr, b, 1.0 / two_pow_S, 1.0 / (2.0 * h * two_pow_S), total, cm);
+      q, phi, g, gr, b, S, 1.0 / (2.0 * h * two_pow_S), mean);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_fx_sum(const long long* psum, int nb, double* out, cudaStream_t s) {
+cudaError_t launch_finish_fx_sum(const long long* psum, int nb, long long n, double* out,
+                                 cudaStream_t s) {
+  int log2n = 0;
+  while ((1LL << log2n) < n) ++log2n;
+  if ((1LL << log2n) != n) return cudaErrorInvalidValue;  // levels have 2^k cells
   ++g_launches;
-  k_finish_fx_sum<<<1, kThreads, 0, s>>>(psum, nb, out);
+  k_finish_fx_sum<<<1, kThreads, 0, s>>>(psum, nb, log2n, out);
   return cudaGetLastError();
 }
 

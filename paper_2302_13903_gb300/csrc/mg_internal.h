@@ -161,8 +161,9 @@ cudaError_t launch_absmax(const T* a, long long n, double* partials, double* out
 // In place: double -> round((a - mu) * c) as int64.  out = q * c - m as
 // doubles (out may alias q), m = total[0] * cm when total is given.
 cudaError_t launch_f64_to_fx(double* a, long long n, double mu, double c, cudaStream_t s);
-cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, double c,
-                             const double* total, double cm, cudaStream_t s);
+// out[t] = (q[t] - *mean) 2^-S (mean may be null: 0); out may alias q.
+cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, int S,
+                             const long long* mean, cudaStream_t s);
 // out[0] = sum rho, out[1] = max |rho| (n even; partials holds 2
 // reduce_blocks(n / 2) doubles); reads rho only.
 cudaError_t launch_convert(int kind, long long n, const void* in, void* out, cudaStream_t s);
@@ -197,10 +198,12 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
 // q) and g = -grad phi at cell centres from the exact integer differences
 // (Sec. 3.2.3), g = [gx | gy | gz].
 cudaError_t launch_fx_finish_gravity(const long long* q, double* phi, double* g, Grid gr,
-                                     const Bc& bc, double h, double two_pow_S,
-                                     const double* total, double cm, cudaStream_t s);
-// out[0] = sum over nb blocks of the pairs launch_fx_step wrote, as a double.
-cudaError_t launch_finish_fx_sum(const long long* psum, int nb, double* out, cudaStream_t s);
+                                     const Bc& bc, double h, int S, const long long* mean,
+                                     cudaStream_t s);
+// out[0] = sum over nb blocks of the pairs launch_fx_step wrote, as a double;
+// out[1] (as a long long) = that sum over n = 2^k cells, rounded to an integer.
+cudaError_t launch_finish_fx_sum(const long long* psum, int nb, long long n, double* out,
+                                 cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Multipole boundary (App. A).

@@ -663,6 +663,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   StopRule rule{tol, c->opts.stall_ratio};
   int n = 0, st = -1;
   double two_S = 1.0;  // 2^S of the fixed-point representation
+  int S = 0;
   bool in_fx = false;  // phi and f hold integers
   bool phi_zero = false;  // the integer phi is all zero (FMG start): not read
   long long* cur = reinterpret_cast<long long*>(phi);  // integer phi (in phi's own storage)
@@ -716,7 +717,8 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
         if (lim == 0.0) lim = std::ldexp(1.0, 55);
         int e2 = 0;
         std::frexp(lim, &e2);
-        two_S = std::ldexp(1.0, e2 - 1);  // largest power of two <= lim
+        S = e2 - 1;
+        two_S = std::ldexp(1.0, S);  // largest power of two <= lim
         const double c2 = c->h * c->h * two_S;
         if (fast)
           check(c, mg::launch_rho_to_fx(rho, reinterpret_cast<long long*>(f), N, four_pi_G * c2,
@@ -748,27 +750,26 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
     if (st >= 0) break;
   }
   if (in_fx) {
-    // phi = PHI 2^-S, less its mean (periodic / zero gradient) from the last
-    // step's integer sums
-    const double* total = nullptr;
+    // phi = (PHI - M) 2^-S, M the integers' mean (periodic / zero gradient)
+    // rounded to an integer, from the last step's exact integer sums
+    const long long* mean = nullptr;
     if (has_mean) {
-      check(c, mg::launch_finish_fx_sum(psum, nbs, c->scal + 56, s), "finish sum phi");
-      total = c->scal + 56;
+      check(c, mg::launch_finish_fx_sum(psum, nbs, N, c->scal + 56, s), "finish sum phi");
+      mean = reinterpret_cast<const long long*>(c->scal + 57);
     }
-    const double cm = 1.0 / (two_S * (double)N);
     if (gacc) {
       // phi and g from the integers in one pass; it reads neighbours, so it
       // writes phi into the free integer buffer when the integers are in phi
       const bool alias = cur == reinterpret_cast<long long*>(phi);
       double* out = alias ? reinterpret_cast<double*>(alt) : phi;
       KTimer t(c, MG_K_GRAVITY, true, s);
-      check(c, mg::launch_fx_finish_gravity(cur, out, gacc, g, bc, c->h, two_S, total, cm, s),
+      check(c, mg::launch_fx_finish_gravity(cur, out, gacc, g, bc, c->h, S, mean, s),
             "fixed point -> phi, g");
       if (alias)
         check(c, cudaMemcpyAsync(phi, out, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
               "copy phi");
     } else {
-      check(c, mg::launch_fx_to_f64(cur, phi, N, 1.0 / two_S, total, cm, s), "fixed point -> phi");
+      check(c, mg::launch_fx_to_f64(cur, phi, N, S, mean, s), "fixed point -> phi");
     }
     int flag = 0;
     check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s),
