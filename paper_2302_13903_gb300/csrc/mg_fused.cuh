@@ -84,13 +84,22 @@ __device__ __forceinline__ Patch zero_patch() {
   return Patch{Row{z, z}, Row{z, z}};
 }
 
-// u <- cu u + cs (xm + xp + ym + yp + zm + zp) + cf f on two cells at once.
+// u <- cu u + cs (xm + xp + ym + yp + zm + zp) + cf f on two cells at once;
+// `sum` receives the neighbour sum.
 __device__ __forceinline__ float2 sor2(float2 self, float2 xm, float2 xp, float2 ym, float2 yp,
-                                       float2 zm, float2 zp, float2 f, const FusedParams& p) {
-  const float2 sum = add2(add2(add2(xm, xp), add2(ym, yp)), add2(zm, zp));
+                                       float2 zm, float2 zp, float2 f, const FusedParams& p,
+                                       float2& sum) {
+  sum = add2(add2(add2(xm, xp), add2(ym, yp)), add2(zm, zp));
   float2 t = __fmul2_rn(make_float2(p.cf, p.cf), f);
   t = __ffma2_rn(make_float2(p.cu, p.cu), self, t);
   return __ffma2_rn(make_float2(p.cs, p.cs), sum, t);
+}
+
+// d = f - (sum - 6 u) / h^2 from a neighbour sum.
+__device__ __forceinline__ float2 defect_from_sum(float2 self, float2 sum, float2 f,
+                                                  const FusedParams& p) {
+  const float2 lap = __ffma2_rn(make_float2(-6.f, -6.f), self, sum);
+  return __ffma2_rn(make_float2(-p.inv_h2, -p.inv_h2), lap, f);
 }
 
 // d = f - (sum_nb - 6 u) / h^2 on two cells at once.
@@ -145,11 +154,18 @@ __device__ __forceinline__ void x_nb(const Row& r, const float4& side, float2 se
 // One SOR half-step on the patch: row a updates its e cells if AE (else o),
 // row b the cells of the other parity (the same colour one row down).  S: the
 // shared copy of this plane; zm, zp: the patch in the planes below / above.
-template <bool PER, bool AE, bool PKD>
+// DEF (black half-step, periodic rule): dsum receives the updated cells'
+// defects, summed over both rows (the coarse x pair of the restriction).  The
+// neighbours of a black cell are red and keep their values after this
+// half-step, so the defect from the update's own neighbour sum is the defect
+// of the finished sweep, bit for bit.  (With ghosts s u the neighbour sum
+// changes with u itself, so the non-periodic rules do not use this.)
+template <bool PER, bool AE, bool PKD, bool DEF = false>
 __device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S, int ia, int ib,
                                           int offL, int offR, int offU, int offD, const Patch& zm,
                                           const Patch& zp, const Patch& f, const FusedParams& p,
-                                          const Flags& fl, bool zlo, bool zhi) {
+                                          const Flags& fl, bool zlo, bool zhi,
+                                          float2* dsum = nullptr) {
   constexpr bool BE = !AE;
   {
     const float4 above = S[ia + offU];
@@ -164,7 +180,10 @@ __device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S
       zmv = sub_if(zlo, p.s, self, zmv);
       zpv = sub_if(zhi, p.s, self, zpv);
     }
-    set_part<AE>(u.a, sor2(self, xm, xp, ym, yp, zmv, zpv, part<AE>(f.a), p));
+    float2 sum;
+    const float2 un = sor2(self, xm, xp, ym, yp, zmv, zpv, part<AE>(f.a), p, sum);
+    set_part<AE>(u.a, un);
+    if (DEF) *dsum = defect_from_sum(un, sum, part<AE>(f.a), p);
   }
   {
     const float4 below = S[ib + offD];
@@ -179,7 +198,10 @@ __device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S
       zmv = sub_if(zlo, p.s, self, zmv);
       zpv = sub_if(zhi, p.s, self, zpv);
     }
-    set_part<BE>(u.b, sor2(self, xm, xp, ym, yp, zmv, zpv, part<BE>(f.b), p));
+    float2 sum;
+    const float2 un = sor2(self, xm, xp, ym, yp, zmv, zpv, part<BE>(f.b), p, sum);
+    set_part<BE>(u.b, un);
+    if (DEF) *dsum = add2(*dsum, defect_from_sum(un, sum, part<BE>(f.b), p));
   }
 }
 
@@ -218,6 +240,20 @@ __device__ __forceinline__ float2 defect_patch(const Patch& u, const float4* __r
   const float2 dbe = defect_part<PER, true, true>(u.b, u.a, below, lb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
   const float2 dbo = defect_part<PER, false, true>(u.b, u.a, below, rb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
   return add2(add2(dae, dao), add2(dbe, dbo));
+}
+
+// Defect of the red cells of a patch (row a's e cells if AE, row b's of the
+// other parity), summed over both rows: the red half of defect_patch.
+template <bool PER, bool AE>
+__device__ __forceinline__ float2 defect_red(const Patch& u, const float4* __restrict__ S, int ia,
+                                             int ib, int RS, const Patch& zm, const Patch& zp,
+                                             const Patch& f, const FusedParams& p,
+                                             const Flags& fl, bool zlo, bool zhi) {
+  const float4 above = S[ia - RS], below = S[ib + RS];
+  const float4 sa = S[ia + (AE ? -1 : 1)], sb = S[ib + (AE ? 1 : -1)];
+  const float2 da = defect_part<PER, AE, false>(u.a, u.b, above, sa, zm.a, zp.a, f.a, p, fl, zlo, zhi);
+  const float2 db = defect_part<PER, !AE, true>(u.b, u.a, below, sb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
+  return add2(da, db);
 }
 
 // Asynchronous 16-byte global -> shared copy; src_bytes = 0 fills zeros.
@@ -438,6 +474,11 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
 
   Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
   float2 acc = make_float2(0.f, 0.f);
+  // down leg, periodic rule: black defects come from the black half-step
+  // (sor_patch DEF), red ones from the defect pass; accz holds the coarse
+  // planes' sums by parity
+  constexpr bool SPLIT = MODE == kDown && PER;
+  float2 accz[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   // Up leg: the (x, y)-interpolated coarse planes K-1, K, K+1 around fine
   // planes 2K, 2K+1 live in W[0] (even K) and W[1] (odd K); fine plane 2K
   // takes 3/4 of plane K and 1/4 of plane K-1, fine plane 2K+1 3/4 of K and
@@ -537,9 +578,16 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     {
       const int pz = q - 2;
       const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+      float2 dblk = make_float2(0.f, 0.f);
       if (q > q_first + 1)
-        sor_patch<PER, ZP_BLK != 0, true>(r2, &s_red[ZP_BLK * PL], ia, ib, offL, offR, offU, offD,
-                                          r3, r1, f2p, p, fl, zlo, zhi);
+        sor_patch<PER, ZP_BLK != 0, true, SPLIT>(r2, &s_red[ZP_BLK * PL], ia, ib, offL, offR, offU,
+                                                 offD, r3, r1, f2p, p, fl, zlo, zhi, &dblk);
+      if (SPLIT && act && out && pz >= z0 && pz < z1) {
+        // black defects of plane q-2 open (even plane) or join its coarse plane's sum
+        constexpr int ZA = ((QP + 2) % 4) >> 1;  // parity of the coarse plane (q-2)/2
+        if ((QP + 2) % 2 == 0) accz[ZA] = dblk;
+        else accz[ZA] = add2(accz[ZA], dblk);
+      }
       if (MODE == kDown && act) {
         s_fin[ZP_BLK * PL + ia] = pack_p(r2.a);
         s_fin[ZP_BLK * PL + ib] = pack_p(r2.b);
@@ -550,8 +598,23 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         *reinterpret_cast<float4*>(u_out + (o + p.nx)) = pack(r2.b);
       }
     }
-    // [D] defect of plane q-3 and its 2x2x2 restriction
-    if (MODE == kDown) {
+    // [D] defect of plane q-3 (its red cells only when SPLIT) and its 2x2x2
+    // restriction
+    if (MODE == kDown && SPLIT) {
+      const int pz = q - 3;
+      if (act && pz >= z0 && pz < z1 && out) {
+        constexpr int ZA = ((QP + 1) % 4) >> 1;  // parity of the coarse plane (q-3)/2
+        accz[ZA] = add2(accz[ZA], defect_red<PER, ZP_DEF == 0>(r3, &s_fin[ZP_DEF * PL], ia, ib, RS,
+                                                               r4, r2, f3p, p, fl, false, false));
+        if (ZP_DEF != 0) {
+          const unsigned cnx = (unsigned)p.nx >> 1, cny = (unsigned)p.ny >> 1;
+          const unsigned X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
+          *reinterpret_cast<float2*>(fc + ((Zc * cny + Yc) * cnx + X)) =
+              __fmul2_rn(make_float2(0.125f, 0.125f), accz[ZA]);
+        }
+      }
+    }
+    if (MODE == kDown && !SPLIT) {
       const int pz = q - 3;
       if (act && pz >= z0 && pz < z1 && out) {
         const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
