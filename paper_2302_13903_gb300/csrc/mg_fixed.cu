@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   const int x0 = blockIdx.x * FX_TX, y0 = blockIdx.y * FX_TY, z0 = blockIdx.z * cz;
   const int z1 = min(z0 + cz, g.nz);
   const int i = x0 + tx, j = y0 + ty;  // this thread's column
-  const size_t plane = (size_t)g.nx * g.ny;
-  const size_t col = (size_t)j * g.nx + i;
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;  // 32-bit offsets (fx_step_ok)
+  const unsigned col = (unsigned)j * g.nx + i;
   // the halo cell this thread loads (threads < FX_HALO): rows -1 and 16 over
   // the full width, columns -1 and 32 over the tile's rows
   int ha = 0, hb = 0;
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   } else {
     h_in = h_in && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
   }
-  const size_t hcol = h_in ? (size_t)hy * g.nx + hx : 0;
+  const unsigned hcol = h_in ? (unsigned)hy * g.nx + hx : 0u;
   auto slot = [&](int q) { return (q - z0 + 1) & (FX_RING - 1); };
   // Copies for plane q: own PHI_in and e (z0-1 <= q <= z1; zeros outside a
   // non-periodic grid), F (z0 <= q < z1), the halo cell (z0 <= q < z1).
@@ -404,13 +404,13 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
       const int sl = slot(q);
       const bool in = PER || (q >= 0 && q < g.nz);
       const int qw = PER ? (q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q)) : (in ? q : 0);
-      const size_t o = (size_t)qw * plane + col;
+      const unsigned o = (unsigned)qw * plane + col;
       if (!ZERO_IN) cp_async8(&ring.p[sl][tid], phi_in + o, in ? 8 : 0);
       cp_async4(&ring.e[sl][tid], e + o, in ? 4 : 0);
       if (q >= z0 && q < z1) {
-        cp_async8(&ring.f[sl][tid], F + (size_t)q * plane + col, 8);
+        cp_async8(&ring.f[sl][tid], F + ((unsigned)q * plane + col), 8);
         if (halo) {
-          const size_t ho = (size_t)q * plane + hcol;
+          const unsigned ho = (unsigned)q * plane + hcol;
           if (!ZERO_IN) cp_async8(&ring.hp[sl][tid], phi_in + ho, h_in ? 8 : 0);
           cp_async4(&ring.he[sl][tid], e + ho, h_in ? 4 : 0);
         }
@@ -429,12 +429,14 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   cp_wait<1>();  // planes z0 - 1 and z0 have landed
   long long zm = own_at(z0 - 1), self = own_at(z0);
   float acc = 0.f;
-  long long sum_hi = 0, sum_lo = 0;  // exact sum of PHI' = hi 2^32 + lo
+  // exact sum of this column's PHI' (|PHI'| <= 2^60 and at most 64 planes per
+  // CTA, so no overflow); split into hi 2^32 + lo for the block sums
+  long long csum = 0;
   bool bad = false;
   for (int z = z0; z < z1; ++z) {
     issue(z + 2);
     cp_wait<1>();  // every plane up to z + 1 has landed
-    const size_t o = (size_t)z * plane + col;
+    const unsigned o = (unsigned)z * plane + col;
     const int sl = slot(z);
     const long long Fo = ring.f[sl][tid];
     const long long zp = own_at(z + 1);
@@ -445,9 +447,8 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
       P[buf][hb][ha] = h_in ? hv : 0;
     }
     phi_out[o] = self;
-    sum_hi += self >> 32;
-    sum_lo += self & 0xffffffffLL;
-    bad |= (self > (1LL << 60)) || (self < -(1LL << 60));
+    csum += self;
+    bad |= (unsigned long long)(self + (1LL << 60)) > (2ULL << 60);  // |PHI'| > 2^60
     __syncthreads();
     long long xm = P[buf][ty + 1][tx], xp = P[buf][ty + 1][tx + 2];
     long long ym = P[buf][ty][tx + 1], yp = P[buf][ty + 2][tx + 1];
@@ -478,6 +479,7 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   __shared__ long long wh[FX_TX * FX_TY / 32], wl[FX_TX * FX_TY / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double v = warp_sum((double)acc);
+  long long sum_hi = csum >> 32, sum_lo = csum & 0xffffffffLL;
   if (psum) {
     for (int o = 16; o > 0; o >>= 1) {
       sum_hi += __shfl_down_sync(0xffffffffu, sum_hi, o);
@@ -672,16 +674,21 @@ cudaError_t launch_fx_correct(long long* phi, const float* e, long long n, float
   return cudaGetLastError();
 }
 
-bool fx_step_ok(Grid g) { return g.nx % FX_TX == 0 && g.ny % FX_TY == 0; }
+// 32-bit element offsets: fewer than 2^32 cells
+bool fx_step_ok(Grid g) {
+  return g.nx % FX_TX == 0 && g.ny % FX_TY == 0 && g.cells() < (1LL << 32);
+}
 
 // Planes per CTA: the given cz, else the largest of 64 .. 4 that still
-// gives four CTAs per SM.
+// gives four CTAs per SM; at most 128 (a thread's exact sum of its column's
+// integers, each below 2^55, must stay below 2^63).
 int fx_step_cz(Grid g, int cz) {
   const long long cols = (long long)(g.nx / FX_TX) * (g.ny / FX_TY);
   if (cz <= 0) {
     cz = 64;
     while (cz > kFxMinCz && cols * ((g.nz + cz - 1) / cz) < 4 * 152) cz /= 2;
   }
+  if (cz > 128) cz = 128;
   return cz > g.nz ? g.nz : cz;
 }
 
