@@ -14,6 +14,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 
 #include "mg_convert.cuh"
 #include "mg_device.cuh"
@@ -396,12 +397,12 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     h_in = h_in && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
   }
   const unsigned hcol = h_in ? (unsigned)hy * g.nx + hx : 0u;
-  auto slot = [&](int q) { return (q - z0 + 1) & (FX_RING - 1); };
-  // Copies for plane q: own PHI_in and e (z0-1 <= q <= z1; zeros outside a
-  // non-periodic grid), F (z0 <= q < z1), the halo cell (z0 <= q < z1).
-  auto issue = [&](int q) {
+  // Ring slot of plane q is (q - z0 + 1) mod 4; the z-march below is unrolled
+  // by four, so every slot (and the plane buffer of P) is a compile-time
+  // constant.
+  auto issue = [&](auto SLc, int q) {
+    constexpr int sl = decltype(SLc)::value;
     if (q <= z1) {
-      const int sl = slot(q);
       const bool in = PER || (q >= 0 && q < g.nz);
       const int qw = PER ? (q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q)) : (in ? q : 0);
       const unsigned o = (unsigned)qw * plane + col;
@@ -418,29 +419,33 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     }
     cp_commit();
   };
-  auto own_at = [&](int q) -> long long {  // PHI' of this column at plane q
-    const int sl = slot(q);
+  auto own_at = [&](auto SLc) -> long long {  // PHI' of this column in slot SL
+    constexpr int sl = decltype(SLc)::value;
     const long long v = ZERO_IN ? 0 : ring.p[sl][tid];
     return v + __float2ll_rn(ring.e[sl][tid] * c);
   };
-  issue(z0 - 1);
-  issue(z0);
-  issue(z0 + 1);
+  using I0 = std::integral_constant<int, 0>;
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  issue(I0{}, z0 - 1);
+  issue(I1{}, z0);
+  issue(I2{}, z0 + 1);
   cp_wait<1>();  // planes z0 - 1 and z0 have landed
-  long long zm = own_at(z0 - 1), self = own_at(z0);
+  long long zm = own_at(I0{}), self = own_at(I1{});
   float acc = 0.f;
-  // exact sum of this column's PHI' (|PHI'| <= 2^60 and at most 64 planes per
+  // exact sum of this column's PHI' (|PHI'| <= 2^60 and at most 128 planes per
   // CTA, so no overflow); split into hi 2^32 + lo for the block sums
   long long csum = 0;
   bool bad = false;
-  for (int z = z0; z < z1; ++z) {
-    issue(z + 2);
+  // plane z = z0 + J (mod 4): its slot is J + 1, z + 1's is J + 2, z + 2's J + 3
+  auto step = [&](auto Jc, int z) {
+    constexpr int J = decltype(Jc)::value;
+    issue(std::integral_constant<int, (J + 3) & 3>{}, z + 2);
     cp_wait<1>();  // every plane up to z + 1 has landed
+    constexpr int sl = (J + 1) & 3, buf = J & 1;
     const unsigned o = (unsigned)z * plane + col;
-    const int sl = slot(z);
     const long long Fo = ring.f[sl][tid];
-    const long long zp = own_at(z + 1);
-    const int buf = (z - z0) & 1;
+    const long long zp = own_at(std::integral_constant<int, (J + 2) & 3>{});
     P[buf][ty + 1][tx + 1] = self;
     if (halo) {
       const long long hv = (ZERO_IN ? 0 : ring.hp[sl][tid]) + __float2ll_rn(ring.he[sl][tid] * c);
@@ -469,6 +474,15 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     self = zp;
     // the next plane writes the other half of P; this one is rewritten two
     // planes on, after every thread has passed the next barrier
+  };
+  for (int z = z0; z < z1; z += 4) {
+    step(I0{}, z);
+    if (z + 1 >= z1) break;
+    step(I1{}, z + 1);
+    if (z + 2 >= z1) break;
+    step(I2{}, z + 2);
+    if (z + 3 >= z1) break;
+    step(std::integral_constant<int, 3>{}, z + 3);
   }
   cp_wait<0>();
   if (bad) atomicOr(flag, 1);
