@@ -74,6 +74,12 @@ struct mg_ctx {
   // step (zeros: built-in choice), set by mg_ctx_autotune.
   mg::TileCfg cfg_down[kMaxLevels] = {}, cfg_up[kMaxLevels] = {}, cfg_smooth[kMaxLevels] = {};
   int fx_cz = 0;
+  // The mixed path's inner FP32 solve (the same launches on the same buffers
+  // every outer iteration) as a CUDA graph, captured on its second run and
+  // replayed from then on; dropped when the launch shapes change.
+  cudaGraphExec_t inner_exec = nullptr;
+  long long inner_launches = 0;  // kernels in the graph
+  int inner_runs = 0;
 };
 
 namespace {
@@ -576,7 +582,7 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
 
 // FP32 multigrid solve of L e = r (homogeneous rule on every level) into
 // u32[L-1], with r already in f32[L-1].
-void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
+void inner_solve_launches(mg_ctx* c, const Bc& hom, cudaStream_t s) {
   const int F = c->L - 1;
   Pyr<float> P = pyr<float>(c);
   Bc bcs[kMaxLevels];
@@ -587,6 +593,52 @@ void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
     vcycle<float>(c, P, F, hom, hom, true, s);
   }
   for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, P, F, hom, hom, false, s);
+}
+
+void drop_inner_graph(mg_ctx* c) {
+  if (c->inner_exec) cudaGraphExecDestroy(c->inner_exec);
+  c->inner_exec = nullptr;
+  c->inner_runs = 0;
+}
+
+// The inner solve, from its second run on as one CUDA graph launch (not while
+// per-kernel timing is on, on the legacy default stream, or inside a capture
+// the caller started).  The launches are the same every outer iteration: the
+// same kernels, shapes and buffers.
+void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
+  if (c->inner_exec && !c->timing) {
+    check(c, cudaGraphLaunch(c->inner_exec, s), "inner solve graph");
+    mg::g_launches += c->inner_launches;
+    return;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capture = !c->timing && c->inner_runs >= 1 && s != nullptr &&
+                       cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+                       cs == cudaStreamCaptureStatusNone;
+  ++c->inner_runs;
+  if (!capture) {
+    inner_solve_launches(c, hom, s);
+    return;
+  }
+  check(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+  const long long before = mg::g_launches;
+  cudaGraph_t graph = nullptr;
+  try {
+    inner_solve_launches(c, hom, s);
+  } catch (const Fail&) {
+    cudaStreamEndCapture(s, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  check(c, cudaStreamEndCapture(s, &graph), "end capture");
+  const cudaError_t e = cudaGraphInstantiate(&c->inner_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->inner_exec = nullptr;
+    check(c, e, "instantiate inner solve graph");
+  }
+  c->inner_launches = mg::g_launches - before;
+  check(c, cudaGraphLaunch(c->inner_exec, s), "inner solve graph");
 }
 
 mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
@@ -1043,6 +1095,7 @@ mg_status mg_ctx_autotune(mg_ctx* c, void* stream) {
   if (!c) return MG_ERR_ARG;
   try {
     check(c, cudaSetDevice(c->device), "cudaSetDevice");
+    drop_inner_graph(c);  // the launch shapes may change
     autotune(c, (cudaStream_t)stream);
   } catch (const Fail& f) {
     cudaStreamSynchronize((cudaStream_t)stream);
@@ -1074,6 +1127,7 @@ mg_status mg_ctx_kernel_time(const mg_ctx* c, int k, double* total_ms, long long
 
 mg_status mg_destroy(mg_ctx* c) {
   if (!c) return MG_OK;
+  drop_inner_graph(c);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
