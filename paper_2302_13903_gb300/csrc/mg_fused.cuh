@@ -135,86 +135,59 @@ __device__ __forceinline__ void set_part(Row& r, float2 v) {
   else r.o = v;
 }
 
-// x neighbours of one row's e cells (E) or o cells (!E); `side` is the
-// neighbouring thread's float4 of the same row (left for e, right for o).
+// x neighbours of one row's e cells (E) or o cells (!E); `sidev` is the
+// neighbouring thread's cell next to them: its c3 on the left for e, its c0 on
+// the right for o.
 template <bool PER, bool E>
-__device__ __forceinline__ void x_nb(const Row& r, const float4& side, float2 self, float2& xm,
+__device__ __forceinline__ void x_nb(const Row& r, float sidev, float2 self, float2& xm,
                                      float2& xp, const FusedParams& p, const Flags& fl) {
   if (E) {
-    xm = f2(side.w, r.o.x);
+    xm = f2(sidev, r.o.x);
     xp = r.o;
     if (!PER && fl.xlo) xm.x = p.s * self.x;
   } else {
     xm = r.e;
-    xp = f2(r.e.y, side.x);
+    xp = f2(r.e.y, sidev);
     if (!PER && fl.xhi) xp.y = p.s * self.y;
   }
 }
 
-// One SOR half-step on the patch: row a updates its e cells if AE (else o),
-// row b the cells of the other parity (the same colour one row down).  S: the
-// shared copy of this plane; zm, zp: the patch in the planes below / above.
-// DEF (black half-step, periodic rule): dsum receives the updated cells'
-// defects, summed over both rows (the coarse x pair of the restriction).  The
-// neighbours of a black cell are red and keep their values after this
-// half-step, so the defect from the update's own neighbour sum is the defect
-// of the finished sweep, bit for bit.  (With ghosts s u the neighbour sum
-// changes with u itself, so the non-periodic rules do not use this.)
-template <bool PER, bool AE, bool PKD, bool DEF = false>
-__device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S, int ia, int ib,
-                                          int offL, int offR, int offU, int offD, const Patch& zm,
-                                          const Patch& zp, const Patch& f, const FusedParams& p,
-                                          const Flags& fl, bool zlo, bool zhi,
-                                          float2* dsum = nullptr) {
-  constexpr bool BE = !AE;
-  {
-    const float4 above = S[ia + offU];
-    const float4 side = S[ia + (AE ? offL : offR)];
-    const float2 self = part<AE>(u.a);
-    float2 xm, xp;
-    x_nb<PER, AE>(u.a, side, self, xm, xp, p, fl);
-    float2 ym = part4<AE, PKD>(above), yp = part<AE>(u.b);
-    float2 zmv = part<AE>(zm.a), zpv = part<AE>(zp.a);
-    if (!PER) {
-      ym = sub_if(fl.ylo, p.s, self, ym);
-      zmv = sub_if(zlo, p.s, self, zmv);
-      zpv = sub_if(zhi, p.s, self, zpv);
-    }
-    float2 sum;
-    const float2 un = sor2(self, xm, xp, ym, yp, zmv, zpv, part<AE>(f.a), p, sum);
-    set_part<AE>(u.a, un);
-    if (DEF) *dsum = defect_from_sum(un, sum, part<AE>(f.a), p);
-  }
-  {
-    const float4 below = S[ib + offD];
-    const float4 side = S[ib + (BE ? offL : offR)];
-    const float2 self = part<BE>(u.b);
-    float2 xm, xp;
-    x_nb<PER, BE>(u.b, side, self, xm, xp, p, fl);
-    float2 ym = part<BE>(u.a), yp = part4<BE, PKD>(below);
-    float2 zmv = part<BE>(zm.b), zpv = part<BE>(zp.b);
-    if (!PER) {
-      yp = sub_if(fl.yhi, p.s, self, yp);
-      zmv = sub_if(zlo, p.s, self, zmv);
-      zpv = sub_if(zhi, p.s, self, zpv);
-    }
-    float2 sum;
-    const float2 un = sor2(self, xm, xp, ym, yp, zmv, zpv, part<BE>(f.b), p, sum);
-    set_part<BE>(u.b, un);
-    if (DEF) *dsum = add2(*dsum, defect_from_sum(un, sum, part<BE>(f.b), p));
-  }
-}
-
-// Defect of one row's e or o cells.
-template <bool PER, bool E, bool ROWB>
-__device__ __forceinline__ float2 defect_part(const Row& r, const Row& other, const float4& yout4,
-                                              const float4& side, const Row& rzm, const Row& rzp,
-                                              const Row& rf, const FusedParams& p,
-                                              const Flags& fl, bool zlo, bool zhi) {
+// SOR update of one row's E cells.  yout: their neighbours in the adjacent
+// row pair (the row above for row a, ROWB = false; below for row b); `other`:
+// the patch's other row; sidev as in x_nb.  DEF: *d receives the updated
+// cells' defects from the update's own neighbour sum.
+template <bool PER, bool E, bool ROWB, bool DEF>
+__device__ __forceinline__ void sor_row(Row& r, const Row& other, float2 yout, float sidev,
+                                        const Row& rzm, const Row& rzp, const Row& rf,
+                                        const FusedParams& p, const Flags& fl, bool zlo, bool zhi,
+                                        float2* d) {
   const float2 self = part<E>(r);
   float2 xm, xp;
-  x_nb<PER, E>(r, side, self, xm, xp, p, fl);
-  float2 yout = part4<E, true>(yout4), yin = part<E>(other);
+  x_nb<PER, E>(r, sidev, self, xm, xp, p, fl);
+  const float2 yin = part<E>(other);
+  float2 zmv = part<E>(rzm), zpv = part<E>(rzp);
+  if (!PER) {
+    yout = sub_if(ROWB ? fl.yhi : fl.ylo, p.s, self, yout);
+    zmv = sub_if(zlo, p.s, self, zmv);
+    zpv = sub_if(zhi, p.s, self, zpv);
+  }
+  float2 sum;
+  const float2 un = ROWB ? sor2(self, xm, xp, yin, yout, zmv, zpv, part<E>(rf), p, sum)
+                         : sor2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p, sum);
+  set_part<E>(r, un);
+  if (DEF) *d = defect_from_sum(un, sum, part<E>(rf), p);
+}
+
+// Defect of one row's E cells (arguments as in sor_row).
+template <bool PER, bool E, bool ROWB>
+__device__ __forceinline__ float2 defect_row(const Row& r, const Row& other, float2 yout,
+                                             float sidev, const Row& rzm, const Row& rzp,
+                                             const Row& rf, const FusedParams& p,
+                                             const Flags& fl, bool zlo, bool zhi) {
+  const float2 self = part<E>(r);
+  float2 xm, xp;
+  x_nb<PER, E>(r, sidev, self, xm, xp, p, fl);
+  const float2 yin = part<E>(other);
   float2 zmv = part<E>(rzm), zpv = part<E>(rzp);
   if (!PER) {
     yout = sub_if(ROWB ? fl.yhi : fl.ylo, p.s, self, yout);
@@ -223,6 +196,61 @@ __device__ __forceinline__ float2 defect_part(const Row& r, const Row& other, co
   }
   return ROWB ? defect2(self, xm, xp, yin, yout, zmv, zpv, part<E>(rf), p)
               : defect2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p);
+}
+
+// One SOR half-step on the patch: row a updates its e cells if AE (else o),
+// row b the cells of the other parity (the same colour one row down).  S: the
+// shared copy of this plane (float4 per thread and row, natural or packed
+// order); zm, zp: the patch in the planes below / above.  DEF: dsum receives
+// the updated cells' defects summed over both rows (sor_row).
+template <bool PER, bool AE, bool PKD, bool DEF = false>
+__device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S, int ia, int ib,
+                                          int offL, int offR, int offU, int offD, const Patch& zm,
+                                          const Patch& zp, const Patch& f, const FusedParams& p,
+                                          const Flags& fl, bool zlo, bool zhi,
+                                          float2* dsum = nullptr) {
+  constexpr bool BE = !AE;
+  float2 da, db;
+  {
+    const float4 above = S[ia + offU];
+    const float4 side = S[ia + (AE ? offL : offR)];
+    sor_row<PER, AE, false, DEF>(u.a, u.b, part4<AE, PKD>(above), AE ? side.w : side.x, zm.a,
+                                 zp.a, f.a, p, fl, zlo, zhi, &da);
+  }
+  {
+    const float4 below = S[ib + offD];
+    const float4 side = S[ib + (BE ? offL : offR)];
+    sor_row<PER, BE, true, DEF>(u.b, u.a, part4<BE, PKD>(below), BE ? side.w : side.x, zm.b,
+                                zp.b, f.b, p, fl, zlo, zhi, &db);
+  }
+  if (DEF) *dsum = add2(da, db);
+}
+
+// A pair plane holds, for every row of a plane and every thread, the two cells
+// of that row's patch of one colour (the colour whose values a later
+// half-step needs as neighbours) as a float2; rows are RS2 float2 apart.  A
+// cell's y neighbours in the adjacent rows have the same x, so the pair of the
+// adjacent row is exactly the yout of sor_row; the x neighbour across a patch
+// edge is the pair's .y (left thread, its c3) or .x (right thread, its c0).
+__device__ __forceinline__ float side_of(const float2* SP, int idx, int offL, int offR, bool e) {
+  const float* SF = reinterpret_cast<const float*>(SP);
+  return e ? SF[2 * (idx + offL) + 1] : SF[2 * (idx + offR)];
+}
+
+// sor_patch with the neighbours' colour in a pair plane (offsets in float2).
+template <bool PER, bool AE, bool DEF = false>
+__device__ __forceinline__ void sor_pairs(Patch& u, const float2* __restrict__ SP, int pa, int pb,
+                                          int offL, int offR, int offU, int offD, const Patch& zm,
+                                          const Patch& zp, const Patch& f, const FusedParams& p,
+                                          const Flags& fl, bool zlo, bool zhi,
+                                          float2* dsum = nullptr) {
+  constexpr bool BE = !AE;
+  float2 da, db;
+  sor_row<PER, AE, false, DEF>(u.a, u.b, SP[pa + offU], side_of(SP, pa, offL, offR, AE), zm.a,
+                               zp.a, f.a, p, fl, zlo, zhi, &da);
+  sor_row<PER, BE, true, DEF>(u.b, u.a, SP[pb + offD], side_of(SP, pb, offL, offR, BE), zm.b,
+                              zp.b, f.b, p, fl, zlo, zhi, &db);
+  if (DEF) *dsum = add2(da, db);
 }
 
 // Defect of the whole patch (interior threads only; S in packed order);
@@ -235,24 +263,29 @@ __device__ __forceinline__ float2 defect_patch(const Patch& u, const float4* __r
                                                bool zhi) {
   const float4 above = S[ia - RS], below = S[ib + RS];
   const float4 la = S[ia - 1], ra = S[ia + 1], lb = S[ib - 1], rb = S[ib + 1];
-  const float2 dae = defect_part<PER, true, false>(u.a, u.b, above, la, zm.a, zp.a, f.a, p, fl, zlo, zhi);
-  const float2 dao = defect_part<PER, false, false>(u.a, u.b, above, ra, zm.a, zp.a, f.a, p, fl, zlo, zhi);
-  const float2 dbe = defect_part<PER, true, true>(u.b, u.a, below, lb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
-  const float2 dbo = defect_part<PER, false, true>(u.b, u.a, below, rb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
+  const float2 dae = defect_row<PER, true, false>(u.a, u.b, part4<true, true>(above), la.w, zm.a,
+                                                  zp.a, f.a, p, fl, zlo, zhi);
+  const float2 dao = defect_row<PER, false, false>(u.a, u.b, part4<false, true>(above), ra.x,
+                                                   zm.a, zp.a, f.a, p, fl, zlo, zhi);
+  const float2 dbe = defect_row<PER, true, true>(u.b, u.a, part4<true, true>(below), lb.w, zm.b,
+                                                 zp.b, f.b, p, fl, zlo, zhi);
+  const float2 dbo = defect_row<PER, false, true>(u.b, u.a, part4<false, true>(below), rb.x,
+                                                  zm.b, zp.b, f.b, p, fl, zlo, zhi);
   return add2(add2(dae, dao), add2(dbe, dbo));
 }
 
 // Defect of the red cells of a patch (row a's e cells if AE, row b's of the
-// other parity), summed over both rows: the red half of defect_patch.
+// other parity) from a pair plane of the final black cells, summed over both
+// rows: the red half of defect_patch.
 template <bool PER, bool AE>
-__device__ __forceinline__ float2 defect_red(const Patch& u, const float4* __restrict__ S, int ia,
-                                             int ib, int RS, const Patch& zm, const Patch& zp,
+__device__ __forceinline__ float2 defect_red(const Patch& u, const float2* __restrict__ SP, int pa,
+                                             int pb, int RS2, const Patch& zm, const Patch& zp,
                                              const Patch& f, const FusedParams& p,
                                              const Flags& fl, bool zlo, bool zhi) {
-  const float4 above = S[ia - RS], below = S[ib + RS];
-  const float4 sa = S[ia + (AE ? -1 : 1)], sb = S[ib + (AE ? 1 : -1)];
-  const float2 da = defect_part<PER, AE, false>(u.a, u.b, above, sa, zm.a, zp.a, f.a, p, fl, zlo, zhi);
-  const float2 db = defect_part<PER, !AE, true>(u.b, u.a, below, sb, zm.b, zp.b, f.b, p, fl, zlo, zhi);
+  const float2 da = defect_row<PER, AE, false>(u.a, u.b, SP[pa - RS2], side_of(SP, pa, -1, 1, AE),
+                                               zm.a, zp.a, f.a, p, fl, zlo, zhi);
+  const float2 db = defect_row<PER, !AE, true>(u.b, u.a, SP[pb + RS2], side_of(SP, pb, -1, 1, !AE),
+                                               zm.b, zp.b, f.b, p, fl, zlo, zhi);
   return add2(da, db);
 }
 
@@ -361,6 +394,15 @@ constexpr int row_stride(int rt) {
   return r;
 }
 
+// Row stride of a pair plane, in float2: the smallest RS2 >= RT with
+// 2 RS2 = RT (mod 16), so that the 16 threads of a half-warp, reading float2
+// 2 tp RS2 + tr (+ a constant), hit 16 different 8-byte bank pairs.
+constexpr int pair_stride(int rt) {
+  int r = rt;
+  while ((2 * r - rt) % 16 != 0) ++r;
+  return r;
+}
+
 // HYO > 0 overrides the rows of halo (so that every mode can share one block
 // size in the batched solver); PAD = false keeps rows unpadded (RS = RT), for
 // the batched solver, whose other phases want the shared memory as L1.
@@ -374,11 +416,14 @@ struct Shape {
   static constexpr int RP = RR / 2;                    // row pairs
   static constexpr int NT = RT * RP;                   // threads
   static constexpr int PL = RS * RR;                   // float4 per shared plane
+  static constexpr int RS2 = PAD ? pair_stride(RT) : RT;  // float2 between rows of a pair plane
+  static constexpr int PL2 = RS2 * RR;                 // float2 per pair plane
   static constexpr int NU = 4, NF = 4, NRED = 2, NFIN = (MODE == kDown) ? 2 : 0;
   static constexpr int CX = TX / 2 + 8;  // coarse tile columns (up leg)
   static constexpr int CY = RP + 2;      // coarse tile rows
   static constexpr int NC = (MODE == kUp) ? 2 * CX * CY : 0;  // floats of the two coarse slots
-  static constexpr size_t SMEM = (size_t)(NU + NF + NRED + NFIN) * PL * 16 + (size_t)NC * 4;
+  static constexpr size_t SMEM =
+      (size_t)(NU + NF + NFIN) * PL * 16 + (size_t)NRED * PL2 * 8 + (size_t)NC * 4;
 };
 
 // The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
@@ -396,8 +441,12 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   constexpr int HZ = S_::HZ, HY = S_::HY, RT = S_::RT, RS = S_::RS, RP = S_::RP, PL = S_::PL;
   float4* s_u = smem;                     // [4][PL] planes of u (async copies)
   float4* s_f = s_u + S_::NU * PL;        // [4][PL] planes of f (async copies)
-  float4* s_red = s_f + S_::NF * PL;      // [2][PL] red-updated planes
-  float4* s_fin = s_red + S_::NRED * PL;  // [2][PL] final planes (down leg)
+  // [2][PL2] pair planes of the red cells after the red half-step
+  float2* s_red = reinterpret_cast<float2*>(s_f + S_::NF * PL);
+  // [2][PL] final planes (down leg), or [2][PL2] pair planes of their black
+  // cells when the defect pass needs only those (SPLIT)
+  float4* s_fin = reinterpret_cast<float4*>(s_red + S_::NRED * S_::PL2);
+  float2* s_finp = reinterpret_cast<float2*>(s_fin);
   float* s_c = reinterpret_cast<float*>(s_fin + S_::NFIN * PL);  // [2][CY][CX] coarse (up leg)
 
   constexpr bool SPARE = NTB > S_::NT;  // the CTA has threads without a patch
@@ -422,6 +471,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   const unsigned plane = (unsigned)p.nx * (unsigned)p.ny;
   const unsigned offA = col_ok ? (unsigned)gyAw * p.nx + gx4w : 0u;  // row a; row b is nx further
   const int ia = (2 * tp) * RS + tr, ib = ia + RS;  // shared indices of rows a, b
+  constexpr int RS2 = S_::RS2, PL2 = S_::PL2;
+  const int pa = (2 * tp) * RS2 + tr, pb = pa + RS2;  // their pair-plane indices
+  const int offU2 = tp > 0 ? -RS2 : 0, offD2 = tp < RP - 1 ? RS2 : 0;
   const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
   const int offU = tp > 0 ? -RS : 0, offD = tp < RP - 1 ? RS : 0;
   const int q_first = z0 - HZ, q_last = z1 - 1 + HZ;
@@ -569,9 +621,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
                                            r2, r0, f1, p, fl, zlo, zhi);
         }
       }
-      if (act) {
-        s_red[ZP_RED * PL + ia] = pack_p(r1.a);
-        s_red[ZP_RED * PL + ib] = pack_p(r1.b);
+      if (act) {  // the red cells: row a's e cells on an even plane, row b's o cells
+        s_red[ZP_RED * PL2 + pa] = part<ZP_RED == 0>(r1.a);
+        s_red[ZP_RED * PL2 + pb] = part<ZP_RED != 0>(r1.b);
       }
     }
     // [C] black half-step on plane q-2 (red values of planes q-3 .. q-1)
@@ -580,8 +632,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
       float2 dblk = make_float2(0.f, 0.f);
       if (q > q_first + 1)
-        sor_patch<PER, ZP_BLK != 0, true, SPLIT>(r2, &s_red[ZP_BLK * PL], ia, ib, offL, offR, offU,
-                                                 offD, r3, r1, f2p, p, fl, zlo, zhi, &dblk);
+        sor_pairs<PER, ZP_BLK != 0, SPLIT>(r2, &s_red[ZP_BLK * PL2], pa, pb, offL, offR, offU2,
+                                           offD2, r3, r1, f2p, p, fl, zlo, zhi, &dblk);
       if (SPLIT && act && out && pz >= z0 && pz < z1) {
         // black defects of plane q-2 open (even plane) or join its coarse plane's sum
         constexpr int ZA = ((QP + 2) % 4) >> 1;  // parity of the coarse plane (q-2)/2
@@ -589,8 +641,13 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         else accz[ZA] = add2(accz[ZA], dblk);
       }
       if (MODE == kDown && act) {
-        s_fin[ZP_BLK * PL + ia] = pack_p(r2.a);
-        s_fin[ZP_BLK * PL + ib] = pack_p(r2.b);
+        if (SPLIT) {  // the black cells: row a's o cells on an even plane, row b's e cells
+          s_finp[ZP_BLK * PL2 + pa] = part<ZP_BLK != 0>(r2.a);
+          s_finp[ZP_BLK * PL2 + pb] = part<ZP_BLK == 0>(r2.b);
+        } else {
+          s_fin[ZP_BLK * PL + ia] = pack_p(r2.a);
+          s_fin[ZP_BLK * PL + ib] = pack_p(r2.b);
+        }
       }
       if (act && out && pz >= z0 && pz < z1) {
         const unsigned o = (unsigned)pz * plane + offA;
@@ -604,8 +661,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       const int pz = q - 3;
       if (act && pz >= z0 && pz < z1 && out) {
         constexpr int ZA = ((QP + 1) % 4) >> 1;  // parity of the coarse plane (q-3)/2
-        accz[ZA] = add2(accz[ZA], defect_red<PER, ZP_DEF == 0>(r3, &s_fin[ZP_DEF * PL], ia, ib, RS,
-                                                               r4, r2, f3p, p, fl, false, false));
+        accz[ZA] = add2(accz[ZA], defect_red<PER, ZP_DEF == 0>(r3, &s_finp[ZP_DEF * PL2], pa, pb,
+                                                               RS2, r4, r2, f3p, p, fl, false,
+                                                               false));
         if (ZP_DEF != 0) {
           const unsigned cnx = (unsigned)p.nx >> 1, cny = (unsigned)p.ny >> 1;
           const unsigned X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
