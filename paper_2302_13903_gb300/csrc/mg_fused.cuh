@@ -198,34 +198,6 @@ __device__ __forceinline__ float2 defect_row(const Row& r, const Row& other, flo
               : defect2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p);
 }
 
-// One SOR half-step on the patch: row a updates its e cells if AE (else o),
-// row b the cells of the other parity (the same colour one row down).  S: the
-// shared copy of this plane (float4 per thread and row, natural or packed
-// order); zm, zp: the patch in the planes below / above.  DEF: dsum receives
-// the updated cells' defects summed over both rows (sor_row).
-template <bool PER, bool AE, bool PKD, bool DEF = false>
-__device__ __forceinline__ void sor_patch(Patch& u, const float4* __restrict__ S, int ia, int ib,
-                                          int offL, int offR, int offU, int offD, const Patch& zm,
-                                          const Patch& zp, const Patch& f, const FusedParams& p,
-                                          const Flags& fl, bool zlo, bool zhi,
-                                          float2* dsum = nullptr) {
-  constexpr bool BE = !AE;
-  float2 da, db;
-  {
-    const float4 above = S[ia + offU];
-    const float4 side = S[ia + (AE ? offL : offR)];
-    sor_row<PER, AE, false, DEF>(u.a, u.b, part4<AE, PKD>(above), AE ? side.w : side.x, zm.a,
-                                 zp.a, f.a, p, fl, zlo, zhi, &da);
-  }
-  {
-    const float4 below = S[ib + offD];
-    const float4 side = S[ib + (BE ? offL : offR)];
-    sor_row<PER, BE, true, DEF>(u.b, u.a, part4<BE, PKD>(below), BE ? side.w : side.x, zm.b,
-                                zp.b, f.b, p, fl, zlo, zhi, &db);
-  }
-  if (DEF) *dsum = add2(da, db);
-}
-
 // A pair plane holds, for every row of a plane and every thread, the two cells
 // of that row's patch of one colour (the colour whose values a later
 // half-step needs as neighbours) as a float2; rows are RS2 float2 apart.  A
@@ -237,7 +209,11 @@ __device__ __forceinline__ float side_of(const float2* SP, int idx, int offL, in
   return e ? SF[2 * (idx + offL) + 1] : SF[2 * (idx + offR)];
 }
 
-// sor_patch with the neighbours' colour in a pair plane (offsets in float2).
+// One SOR half-step on the patch: row a updates its e cells if AE (else o),
+// row b the cells of the other parity (the same colour one row down), with
+// the other colour's cells of this plane in the pair plane SP (offsets in
+// float2); zm, zp: the patch in the planes below / above.  DEF: dsum receives
+// the updated cells' defects summed over both rows (sor_row).
 template <bool PER, bool AE, bool DEF = false>
 __device__ __forceinline__ void sor_pairs(Patch& u, const float2* __restrict__ SP, int pa, int pb,
                                           int offL, int offR, int offU, int offD, const Patch& zm,
@@ -416,14 +392,15 @@ struct Shape {
   static constexpr int RP = RR / 2;                    // row pairs
   static constexpr int NT = RT * RP;                   // threads
   static constexpr int PL = RS * RR;                   // float4 per shared plane
-  static constexpr int RS2 = PAD ? pair_stride(RT) : RT;  // float2 between rows of a pair plane
+  static constexpr int RS2 = pair_stride(RT);          // float2 between rows of a pair plane
   static constexpr int PL2 = RS2 * RR;                 // float2 per pair plane
   static constexpr int NU = 4, NF = 4, NRED = 2, NFIN = (MODE == kDown) ? 2 : 0;
   static constexpr int CX = TX / 2 + 8;  // coarse tile columns (up leg)
   static constexpr int CY = RP + 2;      // coarse tile rows
   static constexpr int NC = (MODE == kUp) ? 2 * CX * CY : 0;  // floats of the two coarse slots
+  static constexpr int NUB = 2;  // pair planes of the u planes' black cells
   static constexpr size_t SMEM =
-      (size_t)(NU + NF + NFIN) * PL * 16 + (size_t)NRED * PL2 * 8 + (size_t)NC * 4;
+      (size_t)(NU + NF + NFIN) * PL * 16 + (size_t)(NRED + NUB) * PL2 * 8 + (size_t)NC * 4;
 };
 
 // The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
@@ -445,7 +422,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   float2* s_red = reinterpret_cast<float2*>(s_f + S_::NF * PL);
   // [2][PL] final planes (down leg), or [2][PL2] pair planes of their black
   // cells when the defect pass needs only those (SPLIT)
-  float4* s_fin = reinterpret_cast<float4*>(s_red + S_::NRED * S_::PL2);
+  // [2][PL2] pair planes of the black cells of u (with the correction, on the
+  // up leg) as loaded: the red half-step's neighbours
+  float2* s_ub = s_red + S_::NRED * S_::PL2;
+  float4* s_fin = reinterpret_cast<float4*>(s_ub + S_::NUB * S_::PL2);
   float2* s_finp = reinterpret_cast<float2*>(s_fin);
   float* s_c = reinterpret_cast<float*>(s_fin + S_::NFIN * PL);  // [2][CY][CX] coarse (up leg)
 
@@ -475,7 +455,6 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   const int pa = (2 * tp) * RS2 + tr, pb = pa + RS2;  // their pair-plane indices
   const int offU2 = tp > 0 ? -RS2 : 0, offD2 = tp < RP - 1 ? RS2 : 0;
   const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
-  const int offU = tp > 0 ? -RS : 0, offD = tp < RP - 1 ? RS : 0;
   const int q_first = z0 - HZ, q_last = z1 - 1 + HZ;
 
   // Copies of plane qu of u into ring slot SU and plane qu - 1 of f into
@@ -527,7 +506,7 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
   float2 acc = make_float2(0.f, 0.f);
   // down leg, periodic rule: black defects come from the black half-step
-  // (sor_patch DEF), red ones from the defect pass; accz holds the coarse
+  // (sor_pairs DEF), red ones from the defect pass; accz holds the coarse
   // planes' sums by parity
   constexpr bool SPLIT = MODE == kDown && PER;
   float2 accz[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -559,11 +538,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   auto step = [&](auto Jc, int q) {
     constexpr int J = decltype(Jc)::value;
     constexpr int QP = ((J - HZ) % 4 + 4) % 4;  // q mod 4
-    constexpr int SL_U = QP, SL_UM1 = (QP + 3) % 4, SL_FM1 = (QP + 3) % 4;
+    constexpr int SL_U = QP, SL_FM1 = (QP + 3) % 4;
     constexpr int ZP_RED = (QP + 3) % 2;  // parity of plane q-1
     constexpr int ZP_BLK = (QP + 2) % 2;  // parity of plane q-2
     constexpr int ZP_DEF = (QP + 1) % 2;  // parity of plane q-3
-    constexpr bool PKU = MODE == kUp;     // the u planes hold corrected values, packed
     cp_async_wait<1>();  // this thread's copies of plane q have landed
     __syncthreads();     // ... and everyone's; the previous step is finished
     issue(std::integral_constant<int, (QP + 2) % 4>{}, std::integral_constant<int, (QP + 1) % 4>{},
@@ -592,10 +570,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         r0.b.e = __ffma2_rn(w1, PN.b.e, __ffma2_rn(w0, PK.b.e, r0.b.e));
         r0.b.o = __ffma2_rn(w1, PN.b.o, __ffma2_rn(w0, PK.b.o, r0.b.o));
       }
-      if (act) {
-        s_u[SL_U * PL + ia] = pack_p(r0.a);  // the neighbours read corrected values
-        s_u[SL_U * PL + ib] = pack_p(r0.b);
-      }
+    }
+    if (!ZERO && act) {  // black cells of plane q: row a's o cells on an even plane, row b's e
+      s_ub[(QP & 1) * PL2 + pa] = part<(QP & 1) != 0>(r0.a);
+      s_ub[(QP & 1) * PL2 + pb] = part<(QP & 1) == 0>(r0.b);
     }
     Patch f1;
     f1.a = unpack(s_f[SL_FM1 * PL + ia]);
@@ -617,8 +595,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
             r1.b.e = __fmul2_rn(cf2, f1.b.e);
           }
         } else {
-          sor_patch<PER, ZP_RED == 0, PKU>(r1, &s_u[SL_UM1 * PL], ia, ib, offL, offR, offU, offD,
-                                           r2, r0, f1, p, fl, zlo, zhi);
+          sor_pairs<PER, ZP_RED == 0>(r1, &s_ub[ZP_RED * PL2], pa, pb, offL, offR, offU2, offD2,
+                                      r2, r0, f1, p, fl, zlo, zhi);
         }
       }
       if (act) {  // the red cells: row a's e cells on an even plane, row b's o cells
