@@ -419,10 +419,14 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     }
     cp_commit();
   };
-  auto own_at = [&](auto SLc) -> long long {  // PHI' of this column in slot SL
+  // PHI' of this column in slot SL.  The correction's rounding to an integer
+  // is done in integer arithmetic (exact, as the hardware's): with it and the
+  // residual's conversion both on the FP64 pipe, that pipe bounds the step,
+  // and with both in integer arithmetic, the issue rate does.
+  auto own_at = [&](auto SLc) -> long long {
     constexpr int sl = decltype(SLc)::value;
     const long long v = ZERO_IN ? 0 : ring.p[sl][tid];
-    return v + __float2ll_rn(ring.e[sl][tid] * c);
+    return v + cvt::f2ll_rn(ring.e[sl][tid] * c);
   };
   using I0 = std::integral_constant<int, 0>;
   using I1 = std::integral_constant<int, 1>;
