@@ -155,7 +155,8 @@ __device__ __forceinline__ void x_nb(const Row& r, float sidev, float2 self, flo
 // SOR update of one row's E cells.  yout: their neighbours in the adjacent
 // row pair (the row above for row a, ROWB = false; below for row b); `other`:
 // the patch's other row; sidev as in x_nb.  DEF: *d receives the updated
-// cells' defects from the update's own neighbour sum.
+// cells' defects from the update's own neighbour sum (plus, for the
+// non-periodic rules, the change of their ghost neighbours s u).
 template <bool PER, bool E, bool ROWB, bool DEF>
 __device__ __forceinline__ void sor_row(Row& r, const Row& other, float2 yout, float sidev,
                                         const Row& rzm, const Row& rzp, const Row& rf,
@@ -175,7 +176,19 @@ __device__ __forceinline__ void sor_row(Row& r, const Row& other, float2 yout, f
   const float2 un = ROWB ? sor2(self, xm, xp, yin, yout, zmv, zpv, part<E>(rf), p, sum)
                          : sor2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p, sum);
   set_part<E>(r, un);
-  if (DEF) *d = defect_from_sum(un, sum, part<E>(rf), p);
+  if (DEF) {
+    float2 dd = defect_from_sum(un, sum, part<E>(rf), p);
+    if (!PER) {
+      // each ghost neighbour s u moved with u: its share of the finished
+      // sweep's sum is s (un - self) more than the update used
+      const float base = (float)((ROWB ? fl.yhi : fl.ylo) + zlo + zhi);
+      const float k = -p.s * p.inv_h2;
+      const float2 kng = make_float2(k * (base + ((E && fl.xlo) ? 1.f : 0.f)),
+                                     k * (base + ((!E && fl.xhi) ? 1.f : 0.f)));
+      dd = __ffma2_rn(kng, add2(un, make_float2(-self.x, -self.y)), dd);
+    }
+    *d = dd;
+  }
 }
 
 // Defect of one row's E cells (arguments as in sor_row).
@@ -229,30 +242,9 @@ __device__ __forceinline__ void sor_pairs(Patch& u, const float2* __restrict__ S
   if (DEF) *dsum = add2(da, db);
 }
 
-// Defect of the whole patch (interior threads only; S in packed order);
-// returns the sums over both rows of (d(4m) + d(4m+1), d(4m+2) + d(4m+3)): the two coarse cells in x.
-template <bool PER>
-__device__ __forceinline__ float2 defect_patch(const Patch& u, const float4* __restrict__ S,
-                                               int ia, int ib, int RS, const Patch& zm,
-                                               const Patch& zp, const Patch& f,
-                                               const FusedParams& p, const Flags& fl, bool zlo,
-                                               bool zhi) {
-  const float4 above = S[ia - RS], below = S[ib + RS];
-  const float4 la = S[ia - 1], ra = S[ia + 1], lb = S[ib - 1], rb = S[ib + 1];
-  const float2 dae = defect_row<PER, true, false>(u.a, u.b, part4<true, true>(above), la.w, zm.a,
-                                                  zp.a, f.a, p, fl, zlo, zhi);
-  const float2 dao = defect_row<PER, false, false>(u.a, u.b, part4<false, true>(above), ra.x,
-                                                   zm.a, zp.a, f.a, p, fl, zlo, zhi);
-  const float2 dbe = defect_row<PER, true, true>(u.b, u.a, part4<true, true>(below), lb.w, zm.b,
-                                                 zp.b, f.b, p, fl, zlo, zhi);
-  const float2 dbo = defect_row<PER, false, true>(u.b, u.a, part4<false, true>(below), rb.x,
-                                                  zm.b, zp.b, f.b, p, fl, zlo, zhi);
-  return add2(add2(dae, dao), add2(dbe, dbo));
-}
-
 // Defect of the red cells of a patch (row a's e cells if AE, row b's of the
 // other parity) from a pair plane of the final black cells, summed over both
-// rows: the red half of defect_patch.
+// rows.
 template <bool PER, bool AE>
 __device__ __forceinline__ float2 defect_red(const Patch& u, const float2* __restrict__ SP, int pa,
                                              int pb, int RS2, const Patch& zm, const Patch& zp,
@@ -400,7 +392,7 @@ struct Shape {
   static constexpr int NC = (MODE == kUp) ? 2 * CX * CY : 0;  // floats of the two coarse slots
   static constexpr int NUB = 2;  // pair planes of the u planes' black cells
   static constexpr size_t SMEM =
-      (size_t)(NU + NF + NFIN) * PL * 16 + (size_t)(NRED + NUB) * PL2 * 8 + (size_t)NC * 4;
+      (size_t)(NU + NF) * PL * 16 + (size_t)(NRED + NUB + NFIN) * PL2 * 8 + (size_t)NC * 4;
 };
 
 // The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
@@ -420,14 +412,13 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   float4* s_f = s_u + S_::NU * PL;        // [4][PL] planes of f (async copies)
   // [2][PL2] pair planes of the red cells after the red half-step
   float2* s_red = reinterpret_cast<float2*>(s_f + S_::NF * PL);
-  // [2][PL] final planes (down leg), or [2][PL2] pair planes of their black
-  // cells when the defect pass needs only those (SPLIT)
   // [2][PL2] pair planes of the black cells of u (with the correction, on the
   // up leg) as loaded: the red half-step's neighbours
   float2* s_ub = s_red + S_::NRED * S_::PL2;
-  float4* s_fin = reinterpret_cast<float4*>(s_ub + S_::NUB * S_::PL2);
-  float2* s_finp = reinterpret_cast<float2*>(s_fin);
-  float* s_c = reinterpret_cast<float*>(s_fin + S_::NFIN * PL);  // [2][CY][CX] coarse (up leg)
+  // [2][PL2] pair planes of the final black cells (down leg): the red cells'
+  // defect neighbours
+  float2* s_finp = s_ub + S_::NUB * S_::PL2;
+  float* s_c = reinterpret_cast<float*>(s_finp + S_::NFIN * S_::PL2);  // [2][CY][CX] coarse (up)
 
   constexpr bool SPARE = NTB > S_::NT;  // the CTA has threads without a patch
   const int tid = (!SPARE || threadIdx.x < S_::NT) ? threadIdx.x : 0;  // spare: mirror thread 0
@@ -504,11 +495,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   };
 
   Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
-  float2 acc = make_float2(0.f, 0.f);
-  // down leg, periodic rule: black defects come from the black half-step
-  // (sor_pairs DEF), red ones from the defect pass; accz holds the coarse
-  // planes' sums by parity
-  constexpr bool SPLIT = MODE == kDown && PER;
+  // down leg: black defects come from the black half-step (sor_pairs DEF), red
+  // ones from the defect pass; accz holds the coarse planes' sums by parity
+  constexpr bool SPLIT = MODE == kDown;
   float2 accz[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   // Up leg: the (x, y)-interpolated coarse planes K-1, K, K+1 around fine
   // planes 2K, 2K+1 live in W[0] (even K) and W[1] (odd K); fine plane 2K
@@ -618,14 +607,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         if ((QP + 2) % 2 == 0) accz[ZA] = dblk;
         else accz[ZA] = add2(accz[ZA], dblk);
       }
-      if (MODE == kDown && act) {
-        if (SPLIT) {  // the black cells: row a's o cells on an even plane, row b's e cells
-          s_finp[ZP_BLK * PL2 + pa] = part<ZP_BLK != 0>(r2.a);
-          s_finp[ZP_BLK * PL2 + pb] = part<ZP_BLK == 0>(r2.b);
-        } else {
-          s_fin[ZP_BLK * PL + ia] = pack_p(r2.a);
-          s_fin[ZP_BLK * PL + ib] = pack_p(r2.b);
-        }
+      if (MODE == kDown && act) {  // black cells: row a's o cells on an even plane, row b's e
+        s_finp[ZP_BLK * PL2 + pa] = part<ZP_BLK != 0>(r2.a);
+        s_finp[ZP_BLK * PL2 + pb] = part<ZP_BLK == 0>(r2.b);
       }
       if (act && out && pz >= z0 && pz < z1) {
         const unsigned o = (unsigned)pz * plane + offA;
@@ -633,37 +617,20 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         *reinterpret_cast<float4*>(u_out + (o + p.nx)) = pack(r2.b);
       }
     }
-    // [D] defect of plane q-3 (its red cells only when SPLIT) and its 2x2x2
-    // restriction
-    if (MODE == kDown && SPLIT) {
+    // [D] defect of plane q-3's red cells (its black cells' came from [C]) and
+    // the 2x2x2 restriction
+    if (MODE == kDown) {
       const int pz = q - 3;
       if (act && pz >= z0 && pz < z1 && out) {
+        const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
         constexpr int ZA = ((QP + 1) % 4) >> 1;  // parity of the coarse plane (q-3)/2
         accz[ZA] = add2(accz[ZA], defect_red<PER, ZP_DEF == 0>(r3, &s_finp[ZP_DEF * PL2], pa, pb,
-                                                               RS2, r4, r2, f3p, p, fl, false,
-                                                               false));
+                                                               RS2, r4, r2, f3p, p, fl, zlo, zhi));
         if (ZP_DEF != 0) {
           const unsigned cnx = (unsigned)p.nx >> 1, cny = (unsigned)p.ny >> 1;
           const unsigned X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
           *reinterpret_cast<float2*>(fc + ((Zc * cny + Yc) * cnx + X)) =
               __fmul2_rn(make_float2(0.125f, 0.125f), accz[ZA]);
-        }
-      }
-    }
-    if (MODE == kDown && !SPLIT) {
-      const int pz = q - 3;
-      if (act && pz >= z0 && pz < z1 && out) {
-        const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
-        const float2 s2 = defect_patch<PER>(r3, &s_fin[ZP_DEF * PL], ia, ib, RS, r4, r2, f3p, p,
-                                            fl, zlo, zhi);
-        if (ZP_DEF == 0) {
-          acc = s2;
-        } else {
-          acc = add2(acc, s2);
-          const unsigned cnx = (unsigned)p.nx >> 1, cny = (unsigned)p.ny >> 1;
-          const unsigned X = gx4 >> 1, Yc = gyA >> 1, Zc = pz >> 1;
-          *reinterpret_cast<float2*>(fc + ((Zc * cny + Yc) * cnx + X)) =
-              __fmul2_rn(make_float2(0.125f, 0.125f), acc);
         }
       }
     }
