@@ -12,15 +12,21 @@
 // A CTA owns a TX x TY tile of (x, y) columns and marches along z through a
 // chunk of planes.  Each thread owns a 4 x 2 patch (four consecutive x cells
 // of an even row and of the odd row after it) and keeps its patch of the last
-// few planes in registers; neighbours in other threads' patches come from a
-// shared-memory copy of the plane.  Per plane step the pipeline is:
+// few planes in registers.  Per plane step the pipeline is:
 //   copy plane q+2 of u and plane q+1 of f into shared memory (cp.async),
-//   red half-step on plane q-1, black half-step on plane q-2, write plane q-2,
-//   defect of plane q-3 and, every second plane, its 2x2x2 restriction.
-// One __syncthreads separates plane steps.  Because the patch spans an even
-// and an odd row and the z-loop is unrolled by four, the colour of every cell
-// is known at compile time; the two cells of one colour in a row are updated
-// together with packed FP32x2 arithmetic.
+//   [A] load plane q of u (up leg: add the prolonged correction),
+//   [B] red half-step on plane q-1, [C] black half-step on plane q-2 (down
+//   leg: with the black cells' defects), write plane q-2,
+//   [D] down leg: the red cells' defect of plane q-3 and, every second plane,
+//   the 2x2x2 restriction.
+// A half-step needs of its own plane only the other colour's cells in the
+// neighbouring patches; they come from colour-pair planes in shared memory
+// (each thread's two cells of one colour per row, as a float2), written when
+// that colour was last updated: the black cells of u at [A], the red cells at
+// [B], the final black cells at [C].  One __syncthreads separates plane steps.
+// Because the patch spans an even and an odd row and the z-loop is unrolled by
+// four, the colour of every cell is known at compile time; the two cells of
+// one colour in a row are updated together with packed FP32x2 arithmetic.
 //
 // Kernels read u_in and write u_out (different buffers): neighbouring tiles
 // recompute this tile's border cells as their halo (a ring of 2 cells around
