@@ -263,11 +263,13 @@ def run_batched(args, ws, rank, stream):
         ms = max_over_ranks(a.elapsed_time(e) / args.batch_steps)
         cells = b.cells
         graph = b.graph
+        phases = {k: round(v, 3) for k, v in b.phase_ms().items() if v > 0}
     total = sum(s["n"] ** 3 for s in specs)
     return {"grids": len(specs), "cells": total, "ms_per_solve": ms,
             "value": total / (ms * 1e-3), "unit": UNIT, "graph": graph,
             "converged": int(sum(1 for x in sts if x == 0)), "of": len(sts),
             "max_outer_iterations": max(len(h) for h in hists), "rank_cells": cells,
+            "phase_ms": phases,
             "workload": "512 grids, sizes {16,32,64,128}^3 with Zipf 1/rank weights, rules "
                         "periodic / fixed 0 / zero gradient, 1-8 Gaussian blobs each; FP32 "
                         "multigrid inside FP64 defect correction to 1e-10; one persistent "

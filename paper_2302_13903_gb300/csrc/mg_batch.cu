@@ -172,39 +172,35 @@ __device__ __forceinline__ Bc hom_bc(const GridDev& g) {
   return Bc{g.bc == BC_FIXED ? BC_FIXED : g.bc, 0.0, nullptr};
 }
 
-// Sum over the CTA in thread order (the block is not a whole number of
-// warps); the result is valid in thread 0.
+// Reductions over the CTA (not a whole number of warps: the values are padded
+// with the operation's identity to whole warps in shared memory); warp 0's
+// lanes combine every 32nd value, then a shuffle tree.  A fixed order, so the
+// results do not depend on timing; valid in thread 0.
+constexpr int kPadThreads = (kThreads + 31) / 32 * 32;
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce_pad(T v, T identity, Op op) {
+  __shared__ T w[kPadThreads];
+  w[threadIdx.x] = v;
+  if (threadIdx.x < kPadThreads - (int)blockDim.x) w[blockDim.x + threadIdx.x] = identity;
+  __syncthreads();
+  T r = identity;
+  if (threadIdx.x < 32) {
+    for (int q = threadIdx.x; q < kPadThreads; q += 32) r = op(r, w[q]);
+    for (int o = 16; o > 0; o >>= 1) r = op(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  __syncthreads();
+  return r;
+}
+
 __device__ double block_sum(double v) {
-  __shared__ double ws[kThreads];
-  ws[threadIdx.x] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < (int)blockDim.x; ++q) r += ws[q];
-  __syncthreads();
-  return r;
+  return block_reduce_pad(v, 0.0, [](double a, double b) { return a + b; });
 }
-
 __device__ double block_max(double v) {
-  __shared__ double wm[kThreads];
-  wm[threadIdx.x] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < (int)blockDim.x; ++q) r = fmax(r, wm[q]);
-  __syncthreads();
-  return r;
+  return block_reduce_pad(v, 0.0, [](double a, double b) { return fmax(a, b); });
 }
-
 __device__ long long block_isum(long long v) {
-  __shared__ long long wi[kThreads];
-  wi[threadIdx.x] = v;
-  __syncthreads();
-  long long r = 0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < (int)blockDim.x; ++q) r += wi[q];
-  __syncthreads();
-  return r;
+  return block_reduce_pad(v, 0LL, [](long long a, long long b) { return a + b; });
 }
 
 // One chunk of the finest level: cells [c * kChunk, min(N, (c + 1) kChunk)).
@@ -241,42 +237,63 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
   double acc2 = 0.0;
   int nf = 0;
   unsigned long long mb = 0;  // largest |rho| bit pattern
-  // unrolled so that each thread has several independent loads in flight
-#pragma unroll 4
-  for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+  // two cells per step (16-byte loads) and the loop unrolled by eight, so that
+  // each thread keeps several independent loads in flight: the CTA is small
+  // (two per SM), and these passes are bound by memory latency
+  const double2* __restrict__ rho2 = reinterpret_cast<const double2*>(rho);
+  auto r0_cell = [&](int t, double v) {
+    const float x = cvt::d2f_rn(fma(a0, v, -b0));  // (f - mean) sc
+    float xs = x;
+    if (bc == BC_FIXED && bcval != 0.0) {  // L_h(0): 2 b per fixed-value ghost
+      const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
+      const int faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
+      xs = x - (float)faces * bt;
+    }
+    af = fmaf(x, x, af);
+    ar = fmaf(xs, xs, ar);
+    return xs;
+  };
+#pragma unroll 8
+  for (int t2 = (lo >> 1) + threadIdx.x; t2 < (hi >> 1); t2 += blockDim.x) {
+    const int t = 2 * t2;  // cells t, t + 1 (lo, hi and N are even)
     if (TYPE == PH_SRC) {
-      const double v = rho[t];
-      acc += v;
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
-      mb = bits > mb ? bits : mb;
+      const double2 v = rho2[t2];
+      acc += v.x + v.y;
+      const unsigned long long b0 = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffULL;
+      const unsigned long long b1 = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffULL;
+      mb = b0 > mb ? b0 : mb;
+      mb = b1 > mb ? b1 : mb;
     } else if (TYPE == PH_R0) {
-      const float x = cvt::d2f_rn(fma(a0, rho[t], -b0));  // (f - mean) sc
-      float xs = x;
-      if (bc == BC_FIXED && bcval != 0.0) {  // L_h(0): 2 b per fixed-value ghost
-        const int i = t & (n - 1), j = (t >> lg) & (n - 1), k = t >> (2 * lg);
-        const int faces = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) + (k == 0) + (k == n - 1);
-        xs = x - (float)faces * bt;
-      }
-      r32[t] = xs;
-      af = fmaf(x, x, af);
-      ar = fmaf(xs, xs, ar);
-      if (++nf == 8) {
+      const double2 v = rho2[t2];
+      const float x0 = r0_cell(t, v.x), x1 = r0_cell(t + 1, v.y);
+      reinterpret_cast<float2*>(r32)[t2] = make_float2(x0, x1);
+      if (++nf == 4) {  // FP32 sums over at most 8 cells, then added in FP64
         acc += af;
         acc2 += ar;
         af = ar = 0.f;
         nf = 0;
       }
     } else if (TYPE == PH_EMAX) {
-      mx = fmax(mx, (double)fabsf(e32[t]));
+      const float2 v = reinterpret_cast<const float2*>(e32)[t2];
+      mx = fmax(mx, (double)fmaxf(fabsf(v.x), fabsf(v.y)));
     } else if (TYPE == PH_TOFX) {
-      FX[t] = cvt::d2ll_rn(fma(fpg * c2, rho[t], -mean * c2));
+      const double2 v = rho2[t2];
+      const double a = fpg * c2, b = mean * c2;
+      reinterpret_cast<longlong2*>(FX)[t2] =
+          make_longlong2(cvt::d2ll_rn(fma(a, v.x, -b)), cvt::d2ll_rn(fma(a, v.y, -b)));
     } else if (TYPE == PH_PSUM) {
-      const long long v = PHI[t];
-      s_hi += v >> 32;
-      s_lo += v & 0xffffffffLL;
+      const longlong2 v = reinterpret_cast<const longlong2*>(PHI)[t2];
+      s_hi += (v.x >> 32) + (v.y >> 32);
+      s_lo += (v.x & 0xffffffffLL) + (v.y & 0xffffffffLL);
     } else if (TYPE == PH_PSUB) {
       // a grid that never reached the fixed-point loop has phi = 0 exactly
-      phi[t] = fx ? cvt::ll2d_rn(PHI[t]) * (1.0 / two_S) - mean : 0.0;
+      double2 out = make_double2(0.0, 0.0);
+      if (fx) {
+        const longlong2 v = reinterpret_cast<const longlong2*>(PHI)[t2];
+        out = make_double2(cvt::ll2d_rn(v.x) * (1.0 / two_S) - mean,
+                           cvt::ll2d_rn(v.y) * (1.0 / two_S) - mean);
+      }
+      reinterpret_cast<double2*>(phi)[t2] = out;
     }
   }
   if (TYPE == PH_R0) {

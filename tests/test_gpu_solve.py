@@ -191,6 +191,34 @@ def test_deterministic_repeat():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("bc,n", [(mg.PERIODIC, 64), (mg.ZEROGRAD, 32), (mg.OPEN, 32)])
+def test_inner_solve_graph_replay_gives_the_same_bits(bc, n):
+    """From its second run on the inner FP32 solve replays as a captured CUDA
+    graph; per-kernel timing keeps the launches one by one.  Both are the same
+    kernels on the same buffers, so phi, the history and the kernel count
+    agree exactly (and again after the tuner has dropped the graph)."""
+    rho, fpg = source(n, bc, seed=33)
+    rd = torch.from_numpy(rho).cuda()
+    stream = torch.cuda.Stream()
+    with mg.Solver(n, 1.0 / n, bc, prec=mg.MIXED) as s:
+        with torch.cuda.stream(stream):
+            s.solve(rd, fpg, 1e-10, stream=stream)  # first run: plain launches, graph captured
+            p_graph, h_graph, st = s.solve(rd, fpg, 1e-10, stream=stream)
+            n_graph = s.last_launches
+            s.set_timing(True)
+            p_plain, h_plain, st2 = s.solve(rd, fpg, 1e-10, stream=stream)
+            n_plain = s.last_launches
+            s.set_timing(False)
+            s.autotune(stream)
+            p_again, h_again, st3 = s.solve(rd, fpg, 1e-10, stream=stream)
+        stream.synchronize()
+    assert st == st2 == st3 == 0
+    assert torch.equal(p_graph, p_plain) and np.array_equal(h_graph, h_plain)
+    assert n_graph == n_plain > 0
+    assert len(h_again) == len(h_plain) and np.allclose(h_again, h_plain, rtol=64 * 2.0 ** -24)
+    assert torch.equal(p_again, p_plain)
+
+
 def test_invalid_arguments_on_gpu():
     with mg.Solver(8, 1.0 / 8) as s:
         rho = torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda")
