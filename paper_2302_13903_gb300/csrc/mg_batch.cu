@@ -68,6 +68,8 @@ struct GridDev {
   int stalls, active, status, nh, cycles;
   // fixed-point outer loop: phi and h^2 f as integers scaled by two_S
   double maxf, two_S;
+  int S;            // two_S = 2^S
+  long long imean;  // PHI's mean rounded to an integer (periodic / zero gradient), else 0
   long long b2;  // FIXED: round(2 b 2^S), the integer ghost offset
   int in_fx, fxbad;
   long long* fx2;      // second integer buffer (the outer step writes the other one)
@@ -288,10 +290,10 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
     } else if (TYPE == PH_PSUB) {
       // a grid that never reached the fixed-point loop has phi = 0 exactly
       double2 out = make_double2(0.0, 0.0);
-      if (fx) {
+      if (fx) {  // (PHI - M) 2^-S, M the rounded integer mean: integer arithmetic only
         const longlong2 v = reinterpret_cast<const longlong2*>(PHI)[t2];
-        out = make_double2(cvt::ll2d_rn(v.x) * (1.0 / two_S) - mean,
-                           cvt::ll2d_rn(v.y) * (1.0 / two_S) - mean);
+        out = make_double2(cvt::ll2d_pow2_rn(v.x - g.imean, g.S),
+                           cvt::ll2d_pow2_rn(v.y - g.imean, g.S));
       }
       reinterpret_cast<double2*>(phi)[t2] = out;
     }
@@ -340,6 +342,7 @@ __device__ void setfx_item(const Ctl& c, GridDev& g) {
   if (lim == 0.0) lim = 36028797018963968.0;
   int e2 = 0;
   frexp(lim, &e2);
+  g.S = e2 - 1;
   g.two_S = ldexp(1.0, e2 - 1);
   g.b2 = g.bc == BC_FIXED ? __double2ll_rn(2.0 * g.bcval * g.two_S) : 0;
   g.in_fx = 1;
@@ -654,6 +657,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
                   tl += c.ipart[2 * (g.chunk0 + q) + 1];
                 }
                 m = ((double)th * 4294967296.0 + (double)tl) / (N * g.two_S);
+                // the same mean as an integer, exactly: the 128-bit sum th 2^32 + tl
+                // over N = 2^(3 lg) cells, rounded (ties up)
+                const int k = 3 * (g.L - 1);
+                const unsigned long long t = (unsigned long long)th << 32;
+                unsigned long long lo = t + (unsigned long long)tl;
+                long long hi = (th >> 32) + (tl < 0 ? -1 : 0) + (lo < t ? 1 : 0);
+                if (k > 0) {
+                  const unsigned long long lo2 = lo + (1ULL << (k - 1));
+                  hi += lo2 < lo ? 1 : 0;
+                  g.imean = (long long)((lo2 >> k) | ((unsigned long long)hi << (64 - k)));
+                } else {
+                  g.imean = (long long)lo;
+                }
               }  // otherwise phi = 0 exactly (the grid stopped at its first residual)
             }
             g.mean = m;
@@ -1081,6 +1097,8 @@ mg_status mg_batch_solve(mg_batch* b, const double* const* rho, const double* fo
     d.cycles = 0;
     d.maxf = 0.0;
     d.two_S = 1.0;
+    d.S = 0;
+    d.imean = 0;
     d.b2 = 0;
     d.in_fx = 0;
     d.fxbad = 0;
