@@ -161,14 +161,18 @@ __device__ __forceinline__ double exact_value(const ExactSum& a) {
 
 // Per-block partial sums of rho (sum[]) and maxima of |rho| (mx[], as the
 // double whose bits are the largest |rho| pattern); two cells per step.
+// With `copy`, rho is read from host memory and each value is also stored
+// into copy (the device array the later passes read).
 __global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
-                            double* __restrict__ sum, double* __restrict__ mx) {
+                            double* __restrict__ sum, double* __restrict__ mx,
+                            double2* __restrict__ copy) {
   ExactSum acc;
   unsigned long long m = 0;
 #pragma unroll 4
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 r = rho[t];
+    if (copy) copy[t] = r;
     exact_add(acc, r.x);
     exact_add(acc, r.y);
     const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
@@ -659,7 +663,20 @@ cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, d
   if (n > (long long)nb * kThreads * 16384) return cudaErrorInvalidValue;
   ++g_launches;
   k_rho_stats<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(rho), n / 2, partials,
-                                      partials + nb);
+                                      partials + nb, nullptr);
+  ++g_launches;
+  k_finish_sum_max<<<1, kThreads, 0, s>>>(partials, partials + nb, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_stats_copy(const double* host_rho, double* dev, long long n,
+                                  double* partials, double* out, cudaStream_t s) {
+  if (n % 2) return cudaErrorInvalidValue;
+  const int nb = reduce_blocks(n / 2);
+  if (n > (long long)nb * kThreads * 16384) return cudaErrorInvalidValue;
+  ++g_launches;
+  k_rho_stats<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(host_rho), n / 2, partials,
+                                      partials + nb, reinterpret_cast<double2*>(dev));
   ++g_launches;
   k_finish_sum_max<<<1, kThreads, 0, s>>>(partials, partials + nb, nb, out);
   return cudaGetLastError();

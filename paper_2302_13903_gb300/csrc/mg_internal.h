@@ -167,6 +167,10 @@ cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, int S
 // out[0] = sum rho, out[1] = max |rho| (n even; partials holds 2
 // reduce_blocks(n / 2) doubles); reads rho only.
 cudaError_t launch_convert(int kind, long long n, const void* in, void* out, cudaStream_t s);
+// launch_rho_stats reading rho from (device-mapped) host memory and leaving
+// its copy in dev.
+cudaError_t launch_rho_stats_copy(const double* host_rho, double* dev, long long n,
+                                  double* partials, double* out, cudaStream_t s);
 cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, double* out,
                              cudaStream_t s);
 // r32 = fl32(a rho - b); out[0] = sum r32^2, out[1] = max |r32|.

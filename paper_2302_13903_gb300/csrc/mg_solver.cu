@@ -59,6 +59,12 @@ struct mg_ctx {
   double* pinned = nullptr;    // host mirror of scal
   double* rho_dev_own = nullptr;  // buffers for mg_solve_host
   double* phi_dev_own = nullptr;
+  // mg_solve_host with pinned host buffers: the first pass over rho reads it
+  // from host memory (and leaves the device copy), the last pass writes phi to
+  // host memory (host_phi_written then set); null otherwise
+  const double* host_rho = nullptr;
+  double* host_phi = nullptr;
+  bool host_phi_written = false;
   std::vector<void*> allocs;
   size_t bytes = 0;
   bool dry = false;  // count the bytes of the hierarchy without allocating
@@ -543,6 +549,10 @@ double defect_rms(mg_ctx* c, const double* u, const double* f, const Bc& bc, cud
 mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
                      double* gacc, double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
   const int F = c->L - 1;
+  if (c->host_rho)
+    check(c, cudaMemcpyAsync(const_cast<double*>(rho), c->host_rho,
+                             sizeof(double) * level_grid(c, F).cells(), cudaMemcpyHostToDevice, s),
+          "H2D rho");
   c->u64[F] = phi;
   Pyr<double> P = pyr<double>(c);
   double fnorm = prepare_source(c, rho, four_pi_G, c->f64[F], true, s);
@@ -662,13 +672,22 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   // the scale 2^S is known.  Few FP64 operations per cell: on this GPU they,
   // not the bytes, would bound these passes.
   const bool fast = fx && c->opts.mode_fmg && zero_values;
+  if (c->host_rho && !fast)
+    check(c, cudaMemcpyAsync(const_cast<double*>(rho), c->host_rho, sizeof(double) * N,
+                             cudaMemcpyHostToDevice, s),
+          "H2D rho");
   double mu = 0.0;     // mean of f (fast path: not subtracted in memory)
   double mf = -1.0;    // max |f - mean| when known
   double fnorm, scale, rn;
   if (fast) {
     {
       KTimer t(c, MG_K_SOURCE, true, s);
-      check(c, mg::launch_rho_stats(rho, N, c->partials, c->scal + 0, s), "source stats");
+      if (c->host_rho)  // rho arrives from host memory in this pass, which leaves the device copy
+        check(c, mg::launch_rho_stats_copy(c->host_rho, const_cast<double*>(rho), N, c->partials,
+                                           c->scal + 0, s),
+              "source stats");
+      else
+        check(c, mg::launch_rho_stats(rho, N, c->partials, c->scal + 0, s), "source stats");
     }
     check(c, cudaMemcpyAsync(c->pinned, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
           "read source stats");
@@ -821,7 +840,10 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
         check(c, cudaMemcpyAsync(phi, out, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
               "copy phi");
     } else {
-      check(c, mg::launch_fx_to_f64(cur, phi, N, S, mean, s), "fixed point -> phi");
+      // straight into the caller's pinned host phi when there is one
+      double* out = c->host_phi ? c->host_phi : phi;
+      check(c, mg::launch_fx_to_f64(cur, out, N, S, mean, s), "fixed point -> phi");
+      c->host_phi_written = c->host_phi != nullptr;
     }
     int flag = 0;
     check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s),
@@ -1241,6 +1263,17 @@ mg_status mg_solve_gravity(mg_ctx* c, const double* rho, double four_pi_G, doubl
   return st;
 }
 
+// Page-locked host memory that this device can address directly (unified
+// addressing maps it at the same address).
+static bool host_mapped(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky error of an unknown pointer
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 mg_status mg_solve_host(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
                         double* hist, int hist_cap, int* n_hist, void* stream) {
   if (!c || !rho || !phi) {
@@ -1253,17 +1286,29 @@ mg_status mg_solve_host(mg_ctx* c, const double* rho, double four_pi_G, double t
     check(c, cudaSetDevice(c->device), "cudaSetDevice");
     if (!c->rho_dev_own) c->rho_dev_own = dalloc<double>(c, bytes / sizeof(double));
     if (!c->phi_dev_own) c->phi_dev_own = dalloc<double>(c, bytes / sizeof(double));
-    check(c, cudaMemcpyAsync(c->rho_dev_own, rho, bytes, cudaMemcpyHostToDevice, s), "H2D rho");
+    // Pinned (page-locked, device-mapped) host buffers are read and written by
+    // the solve's first and last passes themselves; others go through copies.
+    const bool rho_pinned = host_mapped(rho), phi_pinned = host_mapped(phi);
+    if (!rho_pinned)
+      check(c, cudaMemcpyAsync(c->rho_dev_own, rho, bytes, cudaMemcpyHostToDevice, s), "H2D rho");
     if (!c->opts.mode_fmg)
       check(c, cudaMemcpyAsync(c->phi_dev_own, phi, bytes, cudaMemcpyHostToDevice, s), "H2D phi");
+    c->host_rho = rho_pinned ? rho : nullptr;
+    c->host_phi = phi_pinned ? phi : nullptr;
+    c->host_phi_written = false;
   } catch (const Fail& f) {
     return f.st;
   }
   mg_status st =
       mg_solve(c, c->rho_dev_own, four_pi_G, tol, c->phi_dev_own, hist, hist_cap, n_hist, stream);
+  const bool written = c->host_phi_written;
+  c->host_rho = nullptr;
+  c->host_phi = nullptr;
+  c->host_phi_written = false;
   if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
   try {
-    check(c, cudaMemcpyAsync(phi, c->phi_dev_own, bytes, cudaMemcpyDeviceToHost, s), "D2H phi");
+    if (!written)
+      check(c, cudaMemcpyAsync(phi, c->phi_dev_own, bytes, cudaMemcpyDeviceToHost, s), "D2H phi");
     check(c, cudaStreamSynchronize(s), "sync");
   } catch (const Fail& f) {
     return f.st;

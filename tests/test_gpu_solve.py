@@ -172,15 +172,25 @@ def test_zero_source(prec):
             assert np.abs(phi).max() == 0.0
 
 
-def test_solve_host_matches_device():
+@pytest.mark.parametrize("bc,prec", [(mg.PERIODIC, mg.MIXED), (mg.FIXED, mg.MIXED),
+                                     (mg.OPEN, mg.MIXED), (mg.PERIODIC, mg.FP64)])
+def test_solve_host_matches_device(bc, prec):
+    """Host buffers give the device solve's bits: pageable ones through copies,
+    pinned ones read by the first pass over rho and written by the last pass
+    (the mixed path's fixed-point conversion)."""
     n = 32
-    rho, _ = source(n, mg.PERIODIC, seed=4)
-    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED) as s:
-        pd, hd, _ = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-10)
-        ph, hh, st = s.solve_host(rho.copy(), 1.0, 1e-10)
-    assert st == 0
+    rho, fpg = source(n, bc, seed=4)
+    with mg.Solver(n, 1.0 / n, bc, prec=prec) as s:
+        pd, hd, _ = s.solve(torch.from_numpy(rho).cuda(), fpg, 1e-10)
+        ph, hh, st = s.solve_host(rho.copy(), fpg, 1e-10)
+        rp = torch.from_numpy(rho.copy()).pin_memory()
+        pp = torch.full_like(rp, float("nan")).pin_memory()
+        _, hp, st2 = s.solve_host(rp, fpg, 1e-10, phi=pp)
+    assert st == st2 == 0
     assert np.array_equal(pd.cpu().numpy(), ph)
     assert np.array_equal(hd, hh)
+    assert np.array_equal(pd.cpu().numpy(), pp.numpy())
+    assert np.array_equal(hd, hp)
 
 
 def test_deterministic_repeat():
