@@ -137,8 +137,12 @@ mg_status mg_solve(mg_ctx *ctx, const double *rho_dev, double four_pi_G, double 
                    double *phi_dev, double *hist, int hist_cap, int *n_hist, void *stream);
 
 /* Same as mg_solve with rho and phi in HOST memory (phi read as the initial
- * guess in MGI mode): the host-to-device copy of rho (and phi), the solve and
- * the device-to-host copy of phi all run on `stream` inside the call. */
+ * guess in MGI mode): the transfers and the solve all run on `stream` inside
+ * the call, and phi holds the result when it returns.  Page-locked buffers
+ * (cudaHostAlloc / cudaHostRegister, mapped for this device) are read and
+ * written in place by the solve's first pass over rho and its last pass over
+ * phi; other host memory goes through copies into device buffers the context
+ * keeps.  Same bits either way. */
 mg_status mg_solve_host(mg_ctx *ctx, const double *rho, double four_pi_G, double tol,
                         double *phi, double *hist, int hist_cap, int *n_hist, void *stream);
 
