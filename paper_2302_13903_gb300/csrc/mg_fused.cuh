@@ -71,18 +71,13 @@ struct Patch {
   Row a, b;  // a: even row, b: odd row
 };
 
-// A float4 of a shared plane holds four consecutive cells c0..c3, either in
-// the level's own order (planes copied from global memory) or, in planes this
-// kernel writes itself, in packed order (c0, c2, c1, c3) = (e, o), whose
-// colour pairs are adjacent registers after a load.
+// A float4 of a level (or of its copy in a shared plane) holds four
+// consecutive cells c0..c3; a Row keeps them as the colour pairs (c0, c2) and
+// (c1, c3).
 __device__ __forceinline__ Row unpack(const float4 v) {
   return Row{make_float2(v.x, v.z), make_float2(v.y, v.w)};
 }
 __device__ __forceinline__ float4 pack(const Row r) { return make_float4(r.e.x, r.o.x, r.e.y, r.o.y); }
-__device__ __forceinline__ Row unpack_p(const float4 v) {
-  return Row{make_float2(v.x, v.y), make_float2(v.z, v.w)};
-}
-__device__ __forceinline__ float4 pack_p(const Row r) { return make_float4(r.e.x, r.e.y, r.o.x, r.o.y); }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ Patch zero_patch() {
@@ -128,12 +123,6 @@ __device__ __forceinline__ float2 sub_if(bool flag, float s, float2 self, float2
 template <bool E>
 __device__ __forceinline__ float2 part(const Row& r) {
   return E ? r.e : r.o;
-}
-// The e (E) or o cells of a shared float4 in natural (PKD = false) or packed
-// order.  c0 is .x and c3 is .w in both orders.
-template <bool E, bool PKD>
-__device__ __forceinline__ float2 part4(const float4& v) {
-  return PKD ? (E ? f2(v.x, v.y) : f2(v.z, v.w)) : (E ? f2(v.x, v.z) : f2(v.y, v.w));
 }
 template <bool E>
 __device__ __forceinline__ void set_part(Row& r, float2 v) {
