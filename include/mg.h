@@ -84,7 +84,14 @@ typedef struct {
   int fas;            /* FP64: 1 runs the full approximation scheme (Algorithm 3,   */
                       /*    Sec. 2.3.5) in place of the correction scheme in every  */
                       /*    V-cycle and in FMG; 0 (default) the correction scheme   */
-  int reserved[6];    /* must be zero                                               */
+  int coarse_literal; /* 1: the coarse correction levels of a zero-gradient grid   */
+                      /*    take zero fixed values (Sec. 2.3.6 read word for word)  */
+                      /*    instead of the homogeneous zero-gradient rule; other    */
+                      /*    rules are unaffected.  Converges, but slowly (about     */
+                      /*    0.9 per V-cycle on 16^3-32^3 grids against 0.15), so    */
+                      /*    give stall_ratio >= 1 and room in max_cycles.  Not in    */
+                      /*    mg_batch_create.  Default 0                              */
+  int reserved[5];    /* must be zero                                               */
 } mg_opts;
 
 typedef struct mg_ctx mg_ctx;

@@ -53,7 +53,7 @@ def lib():
             L = ctypes.CDLL(_LIB_PATH)
             d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
             L.orc_solve.restype = i
-            L.orc_solve.argtypes = [i, i, i, d, i, d, p, i, i, p, d, i, i, i, i, i, d, d, d,
+            L.orc_solve.argtypes = [i, i, i, d, i, d, p, i, i, p, d, i, i, i, i, i, i, d, d, d,
                                     p, p, p, i, p, p, p]
             L.orc_op_smooth.restype = i
             L.orc_op_smooth.argtypes = [i, i, i, d, i, d, p, d, i, i, p, p]
@@ -66,7 +66,7 @@ def lib():
             L.orc_op_coarsest.restype = i
             L.orc_op_coarsest.argtypes = [i, i, i, d, i, d, p, p, p]
             L.orc_op_vcycle.restype = i
-            L.orc_op_vcycle.argtypes = [i, i, i, d, i, d, d, i, i, i, p, p]
+            L.orc_op_vcycle.argtypes = [i, i, i, d, i, d, d, i, i, i, i, p, p]
             L.orc_op_gravity.argtypes = [i, i, i, d, i, d, p, p, p]
             L.orc_op_gravity.restype = i
             L.orc_ylm.restype = d
@@ -107,8 +107,12 @@ class SolveResult:
 def solve(rho, h, bc=PERIODIC, *, bc_value=0.0, faces=None, lmax=4, use_com=True,
           origin=(0.0, 0.0, 0.0), omega=1.15, pre=1, post=1, fmg=True, cycle=CORRECTION,
           max_cycles=50, stall_ratio=0.9, tol=1e-10, four_pi_G=1.0, phi0=None,
-          hist_cap=256) -> SolveResult:
-    """FMG (or a given initial guess) then V-cycles to ||d||/||f|| < tol."""
+          hist_cap=256, coarse_literal=False) -> SolveResult:
+    """FMG (or a given initial guess) then V-cycles to ||d||/||f|| < tol.
+
+    coarse_literal: the coarse correction levels of a zero-gradient grid use
+    zero fixed values (Sec. 2.3.6 read word for word) instead of the
+    homogeneous zero-gradient rule."""
     rho = _f64(rho)
     nz, ny, nx = rho.shape
     phi = np.zeros_like(rho) if phi0 is None else _f64(phi0).copy()
@@ -119,7 +123,8 @@ def solve(rho, h, bc=PERIODIC, *, bc_value=0.0, faces=None, lmax=4, use_com=True
     Q = np.zeros(25)
     fa = None if faces is None else _f64(faces)
     st = lib().orc_solve(nx, ny, nz, h, bc, bc_value, _ptr(fa), lmax, int(use_com), _ptr(org),
-                         omega, pre, post, int(fmg), cycle, max_cycles, stall_ratio, tol,
+                         omega, pre, post, int(fmg), cycle, int(coarse_literal), max_cycles,
+                         stall_ratio, tol,
                          four_pi_G, _ptr(rho), _ptr(phi), _ptr(hist), hist_cap,
                          ctypes.byref(nh), _ptr(org_out), _ptr(Q))
     return SolveResult(phi, hist[: nh.value].copy(), st, org_out, Q)
@@ -187,12 +192,13 @@ def coarsest(f, h, bc=PERIODIC, *, bc_value=0.0, faces=None):
     return u
 
 
-def vcycle(u, f, h, bc=PERIODIC, *, bc_value=0.0, omega=1.15, pre=1, post=1, cycle=CORRECTION):
+def vcycle(u, f, h, bc=PERIODIC, *, bc_value=0.0, omega=1.15, pre=1, post=1, cycle=CORRECTION,
+           coarse_literal=False):
     u = _f64(u).copy()
     f = _f64(f)
     nz, ny, nx = u.shape
-    st = lib().orc_op_vcycle(nx, ny, nz, h, bc, bc_value, omega, pre, post, cycle, _ptr(u),
-                             _ptr(f))
+    st = lib().orc_op_vcycle(nx, ny, nz, h, bc, bc_value, omega, pre, post, cycle,
+                             int(coarse_literal), _ptr(u), _ptr(f))
     assert st == 0
     return u
 

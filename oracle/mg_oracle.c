@@ -154,6 +154,19 @@ static Bc homogeneous(const Bc *bc) {
   return z;
 }
 
+/* The rule of the coarse correction levels.  By default the homogeneous
+ * counterpart above; with `literal` set, Sec. 2.3.6 read word for word: zero
+ * fixed values on every coarse level unless the grid is periodic, so a
+ * zero-gradient grid's corrections get zero fixed values too. */
+static Bc correction_rule(const Bc *bc, int literal) {
+  Bc z = homogeneous(bc);
+  if (literal && z.kind == BC_ZEROGRAD) {
+    z.kind = BC_FIXED;
+    z.value = 0.0;
+  }
+  return z;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Smoother: red-black SOR, Eqs. (rbsor1)-(rbsor2), with omega (Sec. 2.3.2). */
 
@@ -624,7 +637,8 @@ static int hier_set_bc(Hier *H, int kind, double value, const double *Q, int lma
  * hist[n] after the n-th further V-cycle. */
 int orc_solve(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
               const double *given_faces, int lmax, int use_com, const double *origin_in,
-              double omega, int pre, int post, int mode_fmg, int cycle, int max_cycles,
+              double omega, int pre, int post, int mode_fmg, int cycle, int coarse_literal,
+              int max_cycles,
               double stall_ratio, double tol, double four_pi_G, const double *rho, double *phi,
               double *hist, int hist_cap, int *n_hist, double *origin_out, double *Q_out) {
   if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || h <= 0.0) return ORC_ERR_ARG;
@@ -646,7 +660,7 @@ int orc_solve(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
   if (Q_out) memcpy(Q_out, Q, sizeof Q);
   st = hier_set_bc(&H, bc_kind, bc_value, Q, lmax, four_pi_G / (4.0 * pi), origin, given_faces);
   if (st != ORC_OK) { hier_free(&H); return st; }
-  Bc hom = homogeneous(&H.bcs[0]);
+  Bc hom = correction_rule(&H.bcs[0], coarse_literal);
 
   /* f = 4 pi G rho */
   for (int k = 0; k < nz; ++k)
@@ -835,7 +849,8 @@ int orc_op_coarsest(int nx, int ny, int nz, double h, int bc_kind, double bc_val
 /* One V-cycle of Algorithm 1 (cycle = 0) or Algorithm 3 (cycle = 1) on the
  * finest level of an nx*ny*nz grid, given u and f (f is used as is). */
 int orc_op_vcycle(int nx, int ny, int nz, double h, int bc_kind, double bc_value, double omega,
-                  int pre, int post, int cycle, double *u, const double *f) {
+                  int pre, int post, int cycle, int coarse_literal, double *u,
+                  const double *f) {
   if (bc_kind == BC_OPEN || bc_kind == BC_FACES) return ORC_ERR_ARG;
   Hier H;
   int st = hier_build(&H, nx, ny, nz, h);
@@ -844,7 +859,7 @@ int orc_op_vcycle(int nx, int ny, int nz, double h, int bc_kind, double bc_value
   Level *F = &H.lev[H.nlev - 1];
   load(F, F->u, u);
   load(F, F->f, f);
-  Bc hom = homogeneous(&H.bcs[0]);
+  Bc hom = correction_rule(&H.bcs[0], coarse_literal);
   CycleOpts o = {omega, pre, post, cycle};
   if (H.nlev == 1) coarsest(F, &H.bcs[0]);
   else multigrid(H.lev, H.nlev - 1, H.bcs, &H.bcs[H.nlev - 1], &hom, &o);

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
         ("fixed_value", ctypes.c_double), ("lmax", ctypes.c_int), ("use_com", ctypes.c_int),
         ("origin", ctypes.c_double * 3), ("stall_ratio", ctypes.c_double),
         ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-        ("outer_fixed", ctypes.c_int), ("fas", ctypes.c_int), ("reserved", ctypes.c_int * 6),
+        ("outer_fixed", ctypes.c_int), ("fas", ctypes.c_int), ("coarse_literal", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 

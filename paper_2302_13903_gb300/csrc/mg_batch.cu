@@ -955,9 +955,11 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
   if (opts) o = *opts;
   else mg_opts_init(&o);
   if (o.prec != MG_MIXED || o.pre != 1 || o.post != 1 || !o.mode_fmg || o.inner_fmg ||
-      o.max_cycles < 1 || o.max_cycles > 64 || o.inner_cycles < 0 || o.inner_cycles > 16) {
+      o.max_cycles < 1 || o.max_cycles > 64 || o.inner_cycles < 0 || o.inner_cycles > 16 ||
+      o.coarse_literal) {
     g_batch_err = "mg_batch_create: the batched solve runs MG_MIXED, V(1,1), FMG mode, inner "
-                  "V-cycles from a zero correction (inner_fmg = 0), 1..64 outer iterations";
+                  "V-cycles from a zero correction (inner_fmg = 0), 1..64 outer iterations, "
+                  "homogeneous coarse rules (coarse_literal = 0)";
     return MG_ERR_ARG;
   }
   for (int g = 0; g < n; ++g) {

@@ -546,6 +546,15 @@ double defect_rms(mg_ctx* c, const double* u, const double* f, const Bc& bc, cud
   return std::sqrt(read_scalar(c, 1, s) / (double)g.cells());
 }
 
+// The rule of the coarse correction levels below a level with rule `top`:
+// its homogeneous counterpart, or with coarse_literal zero fixed values for a
+// zero-gradient rule too (Sec. 2.3.6 taken word for word).
+Bc correction_bc(const mg_ctx* c, const Bc& top) {
+  const Bc z = mg::homogeneous(top);
+  if (c->opts.coarse_literal && z.kind == mg::BC_ZEROGRAD) return Bc{mg::BC_FIXED, 0.0, nullptr};
+  return z;
+}
+
 mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
                      double* gacc, double* hist, int hist_cap, int* n_hist, cudaStream_t s) {
   const int F = c->L - 1;
@@ -558,7 +567,7 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
   double fnorm = prepare_source(c, rho, four_pi_G, c->f64[F], true, s);
   Bc bcs[kMaxLevels];
   for (int l = 0; l < c->L; ++l) bcs[l] = physical_bc(c, l);
-  const Bc hom = mg::homogeneous(bcs[F]);
+  const Bc hom = correction_bc(c, bcs[F]);
   const bool fas = c->opts.fas != 0;
   if (c->opts.mode_fmg) {
     if (fas) fmg_fas(c, bcs, hom, s);
@@ -590,19 +599,20 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
   return (mg_status)st;
 }
 
-// FP32 multigrid solve of L e = r (homogeneous rule on every level) into
-// u32[L-1], with r already in f32[L-1].
-void inner_solve_launches(mg_ctx* c, const Bc& hom, cudaStream_t s) {
+// FP32 multigrid solve of L e = r into u32[L-1], with r already in f32[L-1]:
+// rule `hom` (the homogeneous rule of the finest level) for e itself and in
+// FMG, `coarse` for the corrections of e on the levels below.
+void inner_solve_launches(mg_ctx* c, const Bc& hom, const Bc& coarse, cudaStream_t s) {
   const int F = c->L - 1;
   Pyr<float> P = pyr<float>(c);
   Bc bcs[kMaxLevels];
   for (int l = 0; l < c->L; ++l) bcs[l] = hom;
   if (c->opts.inner_fmg) {
-    fmg<float>(c, P, bcs, hom, s);
+    fmg<float>(c, P, bcs, coarse, s);
   } else {
-    vcycle<float>(c, P, F, hom, hom, true, s);
+    vcycle<float>(c, P, F, hom, coarse, true, s);
   }
-  for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, P, F, hom, hom, false, s);
+  for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, P, F, hom, coarse, false, s);
 }
 
 void drop_inner_graph(mg_ctx* c) {
@@ -615,7 +625,7 @@ void drop_inner_graph(mg_ctx* c) {
 // per-kernel timing is on, on the legacy default stream, or inside a capture
 // the caller started).  The launches are the same every outer iteration: the
 // same kernels, shapes and buffers.
-void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
+void inner_solve(mg_ctx* c, const Bc& hom, const Bc& coarse, cudaStream_t s) {
   if (c->inner_exec && !c->timing) {
     check(c, cudaGraphLaunch(c->inner_exec, s), "inner solve graph");
     mg::g_launches += c->inner_launches;
@@ -627,14 +637,14 @@ void inner_solve(mg_ctx* c, const Bc& hom, cudaStream_t s) {
                        cs == cudaStreamCaptureStatusNone;
   ++c->inner_runs;
   if (!capture) {
-    inner_solve_launches(c, hom, s);
+    inner_solve_launches(c, hom, coarse, s);
     return;
   }
   check(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   const long long before = mg::g_launches;
   cudaGraph_t graph = nullptr;
   try {
-    inner_solve_launches(c, hom, s);
+    inner_solve_launches(c, hom, coarse, s);
   } catch (const Fail&) {
     cudaStreamEndCapture(s, &graph);
     if (graph) cudaGraphDestroy(graph);
@@ -660,6 +670,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   double* f = c->f64[F];
   const Bc bc = physical_bc(c, F);
   const Bc hom = mg::homogeneous(bc);
+  const Bc coarse = correction_bc(c, bc);
   const bool fx = c->opts.outer_fixed != 0 && c->fxbuf != nullptr;
   const bool has_mean = c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD;
   const bool zero_values = bc.kind == mg::BC_PERIODIC || bc.kind == mg::BC_ZEROGRAD ||
@@ -749,7 +760,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       st = MG_OK;
       break;
     }
-    inner_solve(c, hom, s);
+    inner_solve(c, hom, coarse, s);
     const double old_scale = scale;
     scale = 1.0 / rn;  // the next residual is scaled by the current one's size
     if (!fx) {
@@ -873,6 +884,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (o.inner_cycles < 0 || o.inner_cycles > 64) return MG_ERR_ARG;
   if (o.outer_fixed != 0 && o.outer_fixed != 1) return MG_ERR_ARG;
   if (o.fas != 0 && (o.fas != 1 || o.prec != MG_FP64)) return MG_ERR_ARG;
+  if (o.coarse_literal != 0 && o.coarse_literal != 1) return MG_ERR_ARG;
   if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;

@@ -45,7 +45,8 @@ def test_default_options_layout():
     assert o.omega == 1.15 and o.max_cycles == 50 and o.lmax == 4 and o.use_com == 1
     assert o.stall_ratio == 0.9 and o.inner_fmg == 0 and o.inner_cycles == 3
     assert o.outer_fixed == 1 and o.fas == 0
-    assert list(o.reserved) == [0] * 6
+    assert o.coarse_literal == 0
+    assert list(o.reserved) == [0] * 5
 
 
 @pytest.mark.parametrize("py,c", [(mg.Opts, "mg_opts"), (mg.Request, "mg_request"),
@@ -123,6 +124,15 @@ def test_argument_validation_needs_no_gpu():
     assert L.mg_create(8, 8, 8, 0.1, 0, ctypes.byref(bad), ctypes.byref(h)) == 1
     bad = mg.default_opts(omega=2.5)
     assert L.mg_create(8, 8, 8, 0.1, 0, ctypes.byref(bad), ctypes.byref(h)) == 1
+    bad = mg.default_opts(coarse_literal=2)
+    assert L.mg_create(8, 8, 8, 0.1, 2, ctypes.byref(bad), ctypes.byref(h)) == 1
+    # the batched solve keeps the homogeneous coarse rules
+    lit = mg.default_opts(prec=mg.MIXED, coarse_literal=1)
+    dims = (ctypes.c_int * 3)(16, 16, 16)
+    dx = (ctypes.c_double * 1)(1.0 / 16)
+    bcs = (ctypes.c_int * 1)(mg.ZEROGRAD)
+    assert L.mg_batch_create(1, dims, dx, bcs, None, ctypes.byref(lit), ctypes.byref(h)) == 1
+    assert not h.value
     assert L.mg_solve(None, None, 1.0, 1e-10, None, None, 1, None, None) == 1
     assert L.mg_destroy(None) == 0
     assert L.mg_op_smooth(0, 8, 8, 8, 0.1, 3, 0.0, None, 1.15, 1, 0, None, None, None) == 1

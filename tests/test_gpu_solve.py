@@ -320,6 +320,46 @@ def test_fas_equals_correction_scheme(bc):
     assert np.allclose(a[1], b[1], rtol=1e-8, atol=1e-15)
 
 
+@pytest.mark.parametrize("fas", [0, 1])
+@pytest.mark.parametrize("n", [8, 32])
+def test_literal_coarse_rule_same_schedule_matches_oracle(n, fas):
+    """Zero fixed values on the coarse correction levels of a zero-gradient
+    grid (Sec. 2.3.6 taken word for word): the FP64 path, in the correction
+    scheme and in FAS, gives the oracle's phi after the same cycles."""
+    bc = mg.ZEROGRAD
+    rho, fpg = source(n, bc, seed=17)
+    for k in (0, 3):
+        ref = orc.solve(rho, 1.0 / n, bc, four_pi_G=fpg, tol=0.0, max_cycles=k,
+                        stall_ratio=NO_STALL, cycle=orc.FAS if fas else orc.CORRECTION,
+                        coarse_literal=True)
+        phi, hist, st, _ = gpu_solve(rho, bc, fpg, 0.0, max_cycles=k, stall_ratio=NO_STALL,
+                                     fas=fas, coarse_literal=1)
+        assert len(hist) == len(ref.hist) == k + 1
+        assert emax(phi, ref.phi) <= 1e-11, (k, emax(phi, ref.phi))
+        assert np.allclose(hist, ref.hist, rtol=1e-6, atol=1e-14)
+    hom = orc.solve(rho, 1.0 / n, bc, four_pi_G=fpg, tol=0.0, max_cycles=3, stall_ratio=NO_STALL,
+                    cycle=orc.FAS if fas else orc.CORRECTION)
+    assert emax(phi, hom.phi) > 1e-6  # the option took effect
+
+
+@pytest.mark.parametrize("outer_fixed", [1, 0])
+def test_mixed_literal_coarse_rule_reaches_the_converged_solution(outer_fixed):
+    """With zero fixed coarse corrections the FP32 inner solves contract
+    slowly, but the FP64-accurate outer loop still reaches the oracle's
+    converged solution (the coarse rule does not change the finest level's
+    discrete problem)."""
+    n, bc = 32, mg.ZEROGRAD
+    rho, fpg = source(n, bc, seed=18)
+    ref = orc.solve(rho, 1.0 / n, bc, four_pi_G=fpg, tol=0.0, max_cycles=80)
+    phi, hist, st, _ = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED, outer_fixed=outer_fixed,
+                                 coarse_literal=1, stall_ratio=1.0, max_cycles=250)
+    assert st == 0, (st, hist[-3:])
+    assert hist[-1] < 1e-10
+    assert emax(phi, ref.phi) <= 1e-9
+    default = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED, outer_fixed=outer_fixed)
+    assert len(default[1]) * 3 < len(hist)
+
+
 def test_fas_needs_the_fp64_path():
     with pytest.raises(mg.MGError):
         mg.Solver(16, 1.0 / 16, mg.PERIODIC, prec=mg.MIXED, fas=1)

@@ -245,6 +245,86 @@ def test_stall_stops_with_zero_tolerance(orc):
 
 
 # --------------------------------------------------------------------------
+# The coarse-level rule read word for word (Sec. 2.3.6: zero fixed values on
+# the coarse levels of the correction scheme unless the grid is periodic).  By
+# default a zero-gradient grid's corrections keep the zero-gradient rule; the
+# literal option gives them zero fixed values.
+
+def _vcycle_by_hand(orc, u, f, h, top, coarse):
+    """Algorithm 1 on a 4^3 grid (levels 4, 2, 1) from the oracle's pinned
+    single operators, rule `top` on the finest level and `coarse` below."""
+    u = orc.smooth(u, f, h, top)
+    fc = orc.restrict(orc.defect(u, f, h, top))
+    uc = orc.smooth(np.zeros_like(fc), fc, 2 * h, coarse)
+    fcc = orc.restrict(orc.defect(uc, fc, 2 * h, coarse))
+    uc = orc.prolong(orc.coarsest(fcc, 4 * h, coarse), coarse, add=True, uf=uc)
+    uc = orc.smooth(uc, fc, 2 * h, coarse)
+    u = orc.prolong(uc, coarse, add=True, uf=u)
+    return orc.smooth(u, f, h, top)
+
+
+def test_literal_coarse_rule_vcycle_is_algorithm_1_with_zero_fixed_corrections(orc):
+    rng = np.random.default_rng(31)
+    n, h = 4, 0.25
+    u0 = rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    f -= f.mean()
+    lit = orc.vcycle(u0, f, h, ZEROGRAD, coarse_literal=True)
+    assert np.array_equal(lit, _vcycle_by_hand(orc, u0, f, h, ZEROGRAD, FIXED))
+    hom = orc.vcycle(u0, f, h, ZEROGRAD)
+    assert np.array_equal(hom, _vcycle_by_hand(orc, u0, f, h, ZEROGRAD, ZEROGRAD))
+    assert np.abs(lit - hom).max() > 1e-3  # the option changes the zero-gradient cycle
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, FIXED])
+def test_literal_coarse_rule_leaves_other_rules_alone(orc, bc):
+    n = 16
+    rho = inputs.gaussian_blobs(n, 4, seed=2, periodic=(bc == PERIODIC))
+    a = orc.solve(rho, 1.0 / n, bc, bc_value=0.2 if bc == FIXED else 0.0, tol=1e-10)
+    b = orc.solve(rho, 1.0 / n, bc, bc_value=0.2 if bc == FIXED else 0.0, tol=1e-10,
+                  coarse_literal=True)
+    assert np.array_equal(a.phi, b.phi) and np.array_equal(a.hist, b.hist)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_literal_coarse_rule_converges_to_the_dense_solution(orc, n):
+    """The coarse rule changes only how fast the cycle converges, not the
+    discrete problem of the finest level: iterated to the rounding floor, the
+    literal reading reaches the same zero-mean solution as a dense solve."""
+    rng = np.random.default_rng(40 + n)
+    h = 1.0 / n
+    rho = rng.standard_normal((n, n, n))
+    A, _ = dense_system(n, h, ZEROGRAD)
+    f = rho.ravel() - rho.mean()
+    M = np.zeros((n ** 3 + 1, n ** 3 + 1))
+    M[:-1, :-1] = A
+    M[:-1, -1] = 1.0
+    M[-1, :-1] = 1.0
+    ref = np.linalg.solve(M, np.append(f, 0.0))[:-1]
+    r = orc.solve(rho, h, ZEROGRAD, tol=0.0, stall_ratio=1.0, max_cycles=400, hist_cap=512,
+                  coarse_literal=True)
+    assert r.ok, (r.status, r.hist[-5:])
+    assert emax(r.phi.ravel(), ref) < 1e-12
+
+
+def test_literal_coarse_rule_converges_slowly(orc):
+    """Zero fixed corrections cannot represent the smooth modes of a
+    zero-gradient defect near the walls, so the factor per V(1,1) cycle is far
+    above the homogeneous rule's and grows with N; it stays below 1."""
+    cfs = []
+    for n in (16, 32):
+        rho = inputs.gaussian_blobs(n, 8, seed=5, periodic=False)
+        r = orc.solve(rho, 1.0 / n, ZEROGRAD, tol=1e-8, stall_ratio=1.0, max_cycles=600,
+                      hist_cap=700, coarse_literal=True)
+        assert r.ok, (n, r.status, r.hist[-3:])
+        hst = r.hist
+        cfs.append((hst[-1] / hst[-11]) ** 0.1)
+        hom = orc.solve(rho, 1.0 / n, ZEROGRAD, tol=1e-8)
+        assert hom.ok and len(hom.hist) < len(hst) // 4
+    assert 0.5 < cfs[0] < cfs[1] < 1.0, cfs
+
+
+# --------------------------------------------------------------------------
 # Operators (Sec. 2.3.1 and 2.3.2).
 
 def test_restriction_preserves_sum_and_constants(orc):
