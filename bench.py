@@ -65,7 +65,7 @@ def peaks():
 KERNEL_SOURCES = {
     "fused_up": ["mg_fused.cuh", "mg_fused.cu", "mg_internal.h"],
     "fused_down": ["mg_fused.cuh", "mg_fused.cu", "mg_internal.h"],
-    "outer_residual": ["mg_fixed.cu", "mg_device.cuh", "mg_internal.h"],
+    "outer_residual": ["mg_fixed.cu", "mg_convert.cuh", "mg_device.cuh", "mg_internal.h"],
 }
 
 
