@@ -52,8 +52,15 @@ typedef enum {
  * centres; fixed and open ghosts are 2 b - (adjacent active cell), so that the
  * value on the domain surface equals b (a constant for FIXED, the multipole
  * potential of App. A for OPEN).  Coarse correction levels use the
- * homogeneous counterpart (periodic, zero fixed, zero gradient). */
-typedef enum { MG_BC_PERIODIC = 0, MG_BC_FIXED = 1, MG_BC_ZEROGRAD = 2, MG_BC_OPEN = 3 } mg_bc;
+ * homogeneous counterpart (periodic, zero fixed, zero gradient).  MIXED is a
+ * rule per face, made by mg_create_faces only. */
+typedef enum {
+  MG_BC_PERIODIC = 0,
+  MG_BC_FIXED = 1,
+  MG_BC_ZEROGRAD = 2,
+  MG_BC_OPEN = 3,
+  MG_BC_MIXED = 4
+} mg_bc;
 
 /* Arithmetic of a solve.  FP64: every step in double.  MIXED: an FP64
  * defect-correction loop (outer residual, correction update, source,
@@ -99,16 +106,37 @@ typedef struct mg_ctx mg_ctx;
 /* Fill *opts with the defaults listed above. */
 void mg_opts_init(mg_opts *opts);
 
-/* Create a solver for an nx*ny*nz grid of spacing dx with boundary kind bc.
- * Each dimension must be a power of two >= 2; this version requires
- * nx == ny == nz (the coarsest level is then one cell, Sec. 2.3.2).  The
- * level hierarchy (N_l = N / 2^(L-1-l), L = log2 N + 1 levels, Sec. 3.2.1) and
- * all scratch are allocated on the current device here.  opts may be NULL
- * for defaults; it is copied.  On success *ctx owns the device memory until
- * mg_destroy.  Errors: MG_ERR_ARG (sizes, kinds, options), MG_ERR_OOM,
- * MG_ERR_CUDA. */
+/* Create a solver for an nx*ny*nz grid of spacing dx with boundary kind bc
+ * (periodic, fixed, zero gradient or open).  Each dimension must be a power
+ * of two >= 2 with nx a longest side.  Levels are halved until the shortest
+ * side has one cell (Sec. 3.2.1): for a cube the coarsest level is one cell,
+ * solved exactly; for a box it has several, smoothed by N_0,max Gauss-Seidel
+ * sweeps (Sec. 2.3.2).  The level hierarchy and all scratch are allocated on
+ * the current device here.  opts may be NULL for defaults; it is copied.  On
+ * success *ctx owns the device memory until mg_destroy.  Errors: MG_ERR_ARG
+ * (sizes, kinds, options), MG_ERR_OOM, MG_ERR_CUDA. */
 mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts *opts,
                     mg_ctx **ctx);
+
+/* Create a solver whose six faces have rules of their own (Sec. 2.3.6 lets
+ * the rules differ between boundaries).  face_bc[q], face_value[q] for the
+ * faces q = 0..5 = x-, x+, y-, y+, z-, z+ (host arrays of 6):
+ *   MG_BC_PERIODIC   both faces of that axis must be periodic;
+ *   MG_BC_FIXED      phi on the face is face_value[q];
+ *   MG_BC_ZEROGRAD   zero normal gradient.
+ * face_value may be NULL for all zeros; it is read on fixed faces only.  Any
+ * fixed face sets the zero point of phi; without one the means of f and phi
+ * are removed, as for periodic grids.  Coarse correction levels use each
+ * face's homogeneous rule (opts->coarse_literal: zero fixed on zero-gradient
+ * faces too).  Six equal rules (and, if fixed, equal values) give the
+ * context mg_create gives for that rule; otherwise the context's rule is
+ * MG_BC_MIXED, whose levels run the per-level kernels with the face rules in
+ * their ghost synthesis: the fused FP32 legs (they take one homogeneous rule
+ * per grid) serve only levels whose correction rule is uniform, and MG_MIXED
+ * forms its outer residual in FP64 (the fixed-point step takes one rule per
+ * grid).  Other arguments and errors as mg_create. */
+mg_status mg_create_faces(int nx, int ny, int nz, double dx, const mg_bc *face_bc,
+                          const double *face_value, const mg_opts *opts, mg_ctx **ctx);
 
 /* mg_solve, then the gravitational acceleration at cell centres (Sec. 3.2.3):
  * per axis the average of the two face accelerations -(phi_{i+1} - phi_i)/h

@@ -8,7 +8,9 @@ never does.  It shares no code with the CUDA path.
 
 Arrays are numpy float64, C-contiguous, shaped (nz, ny, nx) with x fastest.
 Boundary kinds: 0 periodic, 1 fixed value, 2 zero gradient, 3 open
-(multipole), 4 given face values (finest level only; tests of the dense solve).
+(multipole), 4 given face values (finest level only; tests of the dense solve),
+5 (PER_FACE) a rule per face (periodic in pairs, fixed b_face or zero gradient), passed as
+``faces=mixed_rule(kinds, values)``.
 """
 from __future__ import annotations
 
@@ -26,8 +28,15 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PERIODIC, FIXED, ZEROGRAD, OPEN, FACES = 0, 1, 2, 3, 4
+PERIODIC, FIXED, ZEROGRAD, OPEN, FACES, PER_FACE = 0, 1, 2, 3, 4, 5
 CORRECTION, FAS = 0, 1
+
+
+def mixed_rule(kinds, values=(0.0,) * 6):
+    """Descriptor of a rule per face (x-, x+, y-, y+, z-, z+): six kinds, then
+    six values b_face (read on fixed faces)."""
+    assert len(kinds) == 6 and len(values) == 6
+    return np.array(list(kinds) + list(values), dtype=np.float64)
 STATUS = {0: "ok", 1: "arg", 2: "oom", 4: "not_converged", 5: "diverged"}
 
 
@@ -66,7 +75,7 @@ def lib():
             L.orc_op_coarsest.restype = i
             L.orc_op_coarsest.argtypes = [i, i, i, d, i, d, p, p, p]
             L.orc_op_vcycle.restype = i
-            L.orc_op_vcycle.argtypes = [i, i, i, d, i, d, d, i, i, i, i, p, p]
+            L.orc_op_vcycle.argtypes = [i, i, i, d, i, d, p, d, i, i, i, i, p, p]
             L.orc_op_gravity.argtypes = [i, i, i, d, i, d, p, p, p]
             L.orc_op_gravity.restype = i
             L.orc_ylm.restype = d
@@ -192,12 +201,13 @@ def coarsest(f, h, bc=PERIODIC, *, bc_value=0.0, faces=None):
     return u
 
 
-def vcycle(u, f, h, bc=PERIODIC, *, bc_value=0.0, omega=1.15, pre=1, post=1, cycle=CORRECTION,
-           coarse_literal=False):
+def vcycle(u, f, h, bc=PERIODIC, *, bc_value=0.0, faces=None, omega=1.15, pre=1, post=1,
+           cycle=CORRECTION, coarse_literal=False):
     u = _f64(u).copy()
     f = _f64(f)
     nz, ny, nx = u.shape
-    st = lib().orc_op_vcycle(nx, ny, nz, h, bc, bc_value, omega, pre, post, cycle,
+    fa = None if faces is None else _f64(faces)
+    st = lib().orc_op_vcycle(nx, ny, nz, h, bc, bc_value, _ptr(fa), omega, pre, post, cycle,
                              int(coarse_literal), _ptr(u), _ptr(f))
     assert st == 0
     return u

@@ -60,8 +60,12 @@ enum {
   ORC_ERR_DIVERGED = 5
 };
 
-/* Boundary kinds, Sec. 2.3.6. */
-enum { BC_PERIODIC = 0, BC_FIXED = 1, BC_ZEROGRAD = 2, BC_OPEN = 3, BC_FACES = 4 };
+/* Boundary kinds, Sec. 2.3.6.  BC_MIXED: a rule of its own on each face
+ * (periodic on both faces of an axis, fixed b_face or zero gradient), given to
+ * the entry points as a 12-double descriptor in place of the face arrays: the
+ * six kinds (x-, x+, y-, y+, z-, z+) followed by the six values b_face (read
+ * on fixed faces only). */
+enum { BC_PERIODIC = 0, BC_FIXED = 1, BC_ZEROGRAD = 2, BC_OPEN = 3, BC_FACES = 4, BC_MIXED = 5 };
 
 /* Coarse-grid schemes. */
 enum { CYCLE_CORRECTION = 0, CYCLE_FAS = 1 };
@@ -70,7 +74,34 @@ typedef struct {
   int kind;
   double value;          /* BC_FIXED: the boundary value b on every face    */
   const double *face[6]; /* BC_OPEN / BC_FACES: value on the domain surface */
+  int fk[6];             /* BC_MIXED: the kind of each face                 */
+  double fv[6];          /* BC_MIXED: b on each fixed face                  */
 } Bc;
+
+/* Read a BC_MIXED descriptor into b; a periodic face needs a periodic
+ * opposite face, and only periodic, fixed and zero-gradient faces exist. */
+static int mixed_from(const double *desc, Bc *b) {
+  if (!desc) return 1;
+  b->kind = BC_MIXED;
+  for (int q = 0; q < 6; ++q) {
+    const double k = desc[q];
+    if (k != (double)BC_PERIODIC && k != (double)BC_FIXED && k != (double)BC_ZEROGRAD) return 1;
+    b->fk[q] = (int)k;
+    b->fv[q] = desc[6 + q];
+  }
+  for (int a = 0; a < 3; ++a)
+    if ((b->fk[2 * a] == BC_PERIODIC) != (b->fk[2 * a + 1] == BC_PERIODIC)) return 1;
+  return 0;
+}
+
+/* Whether a rule fixes the zero point of the potential (Sec. 2.3.6): some
+ * face carries a value. */
+static int sets_zero_point(const Bc *bc) {
+  if (bc->kind != BC_MIXED) return !(bc->kind == BC_PERIODIC || bc->kind == BC_ZEROGRAD);
+  for (int q = 0; q < 6; ++q)
+    if (bc->fk[q] == BC_FIXED) return 1;
+  return 0;
+}
 
 typedef struct {
   int nx, ny, nz;
@@ -101,6 +132,7 @@ static size_t fidx(int face, int nx, int ny, int a, int b) {
 
 static double face_value(const Bc *bc, int face, size_t idx) {
   if (bc->kind == BC_FIXED) return bc->value;
+  if (bc->kind == BC_MIXED) return bc->fv[face];
   return bc->face[face][idx];
 }
 
@@ -109,7 +141,7 @@ static double face_value(const Bc *bc, int face, size_t idx) {
  * adjacent active cell -- the value on the domain surface -- equals the
  * boundary value b, i.e. ghost = 2 b - active. */
 static double ghost_of(const Bc *bc, int face, size_t fi, double adjacent, double wrapped) {
-  switch (bc->kind) {
+  switch (bc->kind == BC_MIXED ? bc->fk[face] : bc->kind) {
     case BC_PERIODIC: return wrapped;
     case BC_ZEROGRAD: return adjacent;
     default: return 2.0 * face_value(bc, face, fi) - adjacent;
@@ -145,7 +177,10 @@ static void fill_ghosts(const Level *L, double *a, const Bc *bc) {
 static Bc homogeneous(const Bc *bc) {
   Bc z;
   memset(&z, 0, sizeof z);
-  if (bc->kind == BC_PERIODIC || bc->kind == BC_ZEROGRAD) {
+  if (bc->kind == BC_MIXED) {
+    z.kind = BC_MIXED;
+    for (int q = 0; q < 6; ++q) z.fk[q] = bc->fk[q]; /* fixed faces get b = 0 */
+  } else if (bc->kind == BC_PERIODIC || bc->kind == BC_ZEROGRAD) {
     z.kind = bc->kind;
   } else {
     z.kind = BC_FIXED;
@@ -164,6 +199,9 @@ static Bc correction_rule(const Bc *bc, int literal) {
     z.kind = BC_FIXED;
     z.value = 0.0;
   }
+  if (literal && z.kind == BC_MIXED)
+    for (int q = 0; q < 6; ++q)
+      if (z.fk[q] == BC_ZEROGRAD) z.fk[q] = BC_FIXED;
   return z;
 }
 
@@ -291,7 +329,16 @@ static void coarsest(Level *L, const Bc *bc) {
   const double h2 = L->h * L->h;
   if (nx * ny * nz == 1) {
     size_t c = pidx(1, 1, 1, 1, 1);
-    if (bc->kind == BC_PERIODIC || bc->kind == BC_ZEROGRAD) {
+    if (bc->kind == BC_MIXED) {
+      /* A periodic or zero-gradient ghost is u itself, a fixed one 2 b - u:
+       * with a fixed faces, sum(ghosts) - 6u = 2 sum(b) - 2 a u = h^2 f.
+       * Without a fixed face it is singular, as below. */
+      int a = 0;
+      double sb = 0.0;
+      for (int q = 0; q < 6; ++q)
+        if (bc->fk[q] == BC_FIXED) { ++a; sb += bc->fv[q]; }
+      if (a > 0) L->u[c] = (2.0 * sb - h2 * L->f[c]) / (2.0 * a);
+    } else if (bc->kind == BC_PERIODIC || bc->kind == BC_ZEROGRAD) {
       /* Every ghost equals u itself: the 1-cell system is singular (its
        * right-hand side is 0 once the mean is removed) and any value solves
        * it; the starting value is kept, which is 0 for a correction. */
@@ -612,7 +659,10 @@ static int hier_set_bc(Hier *H, int kind, double value, const double *Q, int lma
     memset(b, 0, sizeof *b);
     b->kind = kind;
     b->value = value;
-    if (kind == BC_OPEN || kind == BC_FACES) {
+    if (kind == BC_MIXED) {
+      /* the same face kinds and values on every level (FMG) */
+      if (mixed_from(finest_faces, b)) return ORC_ERR_ARG;
+    } else if (kind == BC_OPEN || kind == BC_FACES) {
       H->faces[l] = calloc(faces_total(L->nx, L->ny, L->nz), sizeof(double));
       if (!H->faces[l]) return ORC_ERR_OOM;
       if (kind == BC_OPEN) {
@@ -642,7 +692,7 @@ int orc_solve(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
               double stall_ratio, double tol, double four_pi_G, const double *rho, double *phi,
               double *hist, int hist_cap, int *n_hist, double *origin_out, double *Q_out) {
   if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || h <= 0.0) return ORC_ERR_ARG;
-  if (bc_kind < 0 || bc_kind > BC_FACES || pre < 0 || post < 0 || max_cycles < 0) return ORC_ERR_ARG;
+  if (bc_kind < 0 || bc_kind > BC_MIXED || pre < 0 || post < 0 || max_cycles < 0) return ORC_ERR_ARG;
   if (lmax < 0 || lmax > 4 || hist_cap < 1) return ORC_ERR_ARG;
   if (bc_kind == BC_FACES && (mode_fmg || cycle == CYCLE_FAS)) return ORC_ERR_ARG;
   Hier H;
@@ -667,7 +717,7 @@ int orc_solve(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i)
         F->f[pidx(nx, ny, i + 1, j + 1, k + 1)] = four_pi_G * rho[((size_t)k * ny + j) * nx + i];
-  int mean_free = (bc_kind == BC_PERIODIC || bc_kind == BC_ZEROGRAD);
+  int mean_free = !sets_zero_point(&H.bcs[0]);
   if (mean_free) {
     double m = mean_active(F, F->f);
     for (int k = 1; k <= nz; ++k)
@@ -744,7 +794,9 @@ static int one_level(OneLevel *o, int nx, int ny, int nz, double h, int bc_kind,
   if (!o->L.u || !o->L.f || !o->L.d) return ORC_ERR_OOM;
   o->bc.kind = bc_kind;
   o->bc.value = bc_value;
-  if (bc_kind == BC_OPEN || bc_kind == BC_FACES) {
+  if (bc_kind == BC_MIXED) {
+    if (mixed_from(faces, &o->bc)) return ORC_ERR_ARG;
+  } else if (bc_kind == BC_OPEN || bc_kind == BC_FACES) {
     o->faces = malloc(faces_total(nx, ny, nz) * sizeof(double));
     if (!o->faces) return ORC_ERR_OOM;
     memcpy(o->faces, faces, faces_total(nx, ny, nz) * sizeof(double));
@@ -777,7 +829,8 @@ int orc_op_smooth(int nx, int ny, int nz, double h, int bc_kind, double bc_value
                   const double *faces, double omega, int steps, int colours, double *u,
                   const double *f) {
   OneLevel o;
-  if (one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces) != ORC_OK) { one_free(&o); return ORC_ERR_OOM; }
+  int e = one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces);
+  if (e != ORC_OK) { one_free(&o); return e; }
   load(&o.L, o.L.u, u);
   load(&o.L, o.L.f, f);
   for (int s = 0; s < steps; ++s) {
@@ -792,7 +845,8 @@ int orc_op_smooth(int nx, int ny, int nz, double h, int bc_kind, double bc_value
 int orc_op_defect(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
                   const double *faces, const double *u, const double *f, double *d) {
   OneLevel o;
-  if (one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces) != ORC_OK) { one_free(&o); return ORC_ERR_OOM; }
+  int e = one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces);
+  if (e != ORC_OK) { one_free(&o); return e; }
   load(&o.L, o.L.u, u);
   load(&o.L, o.L.f, f);
   defect(&o.L, &o.bc, o.L.d);
@@ -821,10 +875,9 @@ int orc_op_restrict(int nx, int ny, int nz, const double *uf, double *uc) {
 int orc_op_prolong(int nx, int ny, int nz, int bc_kind, double bc_value, const double *coarse_faces,
                    int high_order, int add, const double *uc, double *uf) {
   OneLevel F, C;
-  if (one_level(&F, nx, ny, nz, 1.0, BC_PERIODIC, 0.0, NULL) != ORC_OK ||
-      one_level(&C, nx / 2, ny / 2, nz / 2, 2.0, bc_kind, bc_value, coarse_faces) != ORC_OK) {
-    one_free(&F); one_free(&C); return ORC_ERR_OOM;
-  }
+  int e = one_level(&F, nx, ny, nz, 1.0, BC_PERIODIC, 0.0, NULL);
+  if (e == ORC_OK) e = one_level(&C, nx / 2, ny / 2, nz / 2, 2.0, bc_kind, bc_value, coarse_faces);
+  if (e != ORC_OK) { one_free(&F); one_free(&C); return e; }
   load(&C.L, C.L.u, uc);
   load(&F.L, F.L.u, uf);
   fill_ghosts(&C.L, C.L.u, &C.bc);
@@ -838,7 +891,8 @@ int orc_op_prolong(int nx, int ny, int nz, int bc_kind, double bc_value, const d
 int orc_op_coarsest(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
                     const double *faces, const double *f, double *u) {
   OneLevel o;
-  if (one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces) != ORC_OK) { one_free(&o); return ORC_ERR_OOM; }
+  int e = one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces);
+  if (e != ORC_OK) { one_free(&o); return e; }
   load(&o.L, o.L.f, f);
   coarsest(&o.L, &o.bc);
   store(&o.L, o.L.u, u);
@@ -847,14 +901,15 @@ int orc_op_coarsest(int nx, int ny, int nz, double h, int bc_kind, double bc_val
 }
 
 /* One V-cycle of Algorithm 1 (cycle = 0) or Algorithm 3 (cycle = 1) on the
- * finest level of an nx*ny*nz grid, given u and f (f is used as is). */
-int orc_op_vcycle(int nx, int ny, int nz, double h, int bc_kind, double bc_value, double omega,
-                  int pre, int post, int cycle, int coarse_literal, double *u,
-                  const double *f) {
+ * finest level of an nx*ny*nz grid, given u and f (f is used as is); `mixed`
+ * is the BC_MIXED descriptor (else unused). */
+int orc_op_vcycle(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
+                  const double *mixed, double omega, int pre, int post, int cycle,
+                  int coarse_literal, double *u, const double *f) {
   if (bc_kind == BC_OPEN || bc_kind == BC_FACES) return ORC_ERR_ARG;
   Hier H;
   int st = hier_build(&H, nx, ny, nz, h);
-  if (st == ORC_OK) st = hier_set_bc(&H, bc_kind, bc_value, NULL, 0, 0.0, NULL, NULL);
+  if (st == ORC_OK) st = hier_set_bc(&H, bc_kind, bc_value, NULL, 0, 0.0, NULL, mixed);
   if (st != ORC_OK) { hier_free(&H); return st; }
   Level *F = &H.lev[H.nlev - 1];
   load(F, F->u, u);
@@ -876,7 +931,8 @@ int orc_op_vcycle(int nx, int ny, int nz, double h, int bc_kind, double bc_value
 int orc_op_gravity(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
                    const double *faces, const double *phi, double *g) {
   OneLevel o;
-  if (one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces) != ORC_OK) { one_free(&o); return ORC_ERR_OOM; }
+  int e = one_level(&o, nx, ny, nz, h, bc_kind, bc_value, faces);
+  if (e != ORC_OK) { one_free(&o); return e; }
   load(&o.L, o.L.u, phi);
   fill_ghosts(&o.L, o.L.u, &o.bc);
   const double *u = o.L.u;

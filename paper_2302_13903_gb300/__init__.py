@@ -15,14 +15,14 @@ import numpy as np
 
 from . import _build
 
-PERIODIC, FIXED, ZEROGRAD, OPEN = 0, 1, 2, 3
+PERIODIC, FIXED, ZEROGRAD, OPEN, PER_FACE = 0, 1, 2, 3, 4  # PER_FACE: made by mg_create_faces
 FP64, MIXED = 0, 1
 STATUS = {0: "MG_OK", 1: "MG_ERR_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR_CUDA",
           4: "MG_ERR_NOT_CONVERGED", 5: "MG_ERR_DIVERGED", 6: "MG_ERR_TIMEOUT", 7: "MG_ERR_BUSY"}
 
 # Every symbol include/mg.h declares (checked by the ABI test).
 EXPORTS = [
-    "mg_opts_init", "mg_create", "mg_solve", "mg_solve_host", "mg_destroy",
+    "mg_opts_init", "mg_create", "mg_create_faces", "mg_solve", "mg_solve_host", "mg_destroy",
     "mg_ctx_device_bytes", "mg_ctx_last_launches", "mg_status_str", "mg_last_error",
     "mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict", "mg_op_prolong",
     "mg_op_coarsest", "mg_op_multipole_moments", "mg_op_open_faces", "mg_faces_count",
@@ -110,6 +110,9 @@ def lib():
             L.mg_opts_init.restype = None
             L.mg_create.argtypes = [i, i, i, d, i, ctypes.POINTER(Opts), ctypes.POINTER(p)]
             L.mg_create.restype = i
+            L.mg_create_faces.argtypes = [i, i, i, d, p, p, ctypes.POINTER(Opts),
+                                          ctypes.POINTER(p)]
+            L.mg_create_faces.restype = i
             L.mg_solve.argtypes = [p, p, d, d, p, p, i, ctypes.POINTER(i), p]
             L.mg_solve.restype = i
             L.mg_solve_host.argtypes = [p, p, d, d, p, p, i, ctypes.POINTER(i), p]
@@ -234,16 +237,28 @@ def _dptr(t, dtype=None):
 
 
 class Solver:
-    """One grid configuration: ``mg_create`` on construction, ``mg_destroy`` on close."""
+    """One grid configuration: ``mg_create`` (or ``mg_create_faces``) on
+    construction, ``mg_destroy`` on close."""
 
-    def __init__(self, n, dx, bc=PERIODIC, **opts):
-        """n: cells per side, or (nx, ny, nz) for a box (arrays are (nz, ny, nx))."""
+    def __init__(self, n, dx, bc=PERIODIC, face_values=None, **opts):
+        """n: cells per side, or (nx, ny, nz) for a box (arrays are (nz, ny, nx)).
+        bc: one rule, or six (x-, x+, y-, y+, z-, z+) with face_values the fixed
+        faces' values (default 0)."""
         dims = (n, n, n) if isinstance(n, int) else tuple(int(v) for v in n)
         self.dims = dims
         self.n, self.dx, self.bc = min(dims), dx, bc
         self.opts = default_opts(**opts)
         h = ctypes.c_void_p()
-        _check(lib().mg_create(*dims, dx, bc, ctypes.byref(self.opts), ctypes.byref(h)))
+        if isinstance(bc, (int, np.integer)):
+            _check(lib().mg_create(*dims, dx, int(bc), ctypes.byref(self.opts), ctypes.byref(h)))
+        else:
+            kinds = np.ascontiguousarray(bc, dtype=np.int32)
+            vals = np.zeros(6) if face_values is None else np.ascontiguousarray(face_values,
+                                                                                  dtype=np.float64)
+            if kinds.shape != (6,) or vals.shape != (6,):
+                raise ValueError("a rule per face needs six kinds and six values")
+            _check(lib().mg_create_faces(*dims, dx, kinds.ctypes.data, vals.ctypes.data,
+                                         ctypes.byref(self.opts), ctypes.byref(h)))
         self.ctx = h
 
     def close(self):

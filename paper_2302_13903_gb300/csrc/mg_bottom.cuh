@@ -235,7 +235,8 @@ __device__ void smooth_level(const BottomArgs<T>& a, int l, const Bc& bc, int st
 // One V-cycle on levels top .. 0 with rule bc_top on level `top`.
 template <typename T>
 __device__ void vcycle(const BottomArgs<T>& a, int top, const Bc& bc_top, bool zero_guess) {
-  if (bc_top.kind == a.hom.kind && bc_top.value == 0.0 && bc_top.kind != BC_OPEN) {
+  if (bc_top.kind == a.hom.kind && bc_top.value == 0.0 && bc_top.kind != BC_OPEN &&
+      bc_top.kind != BC_MIXED) {
     if (a.hom.kind == BC_PERIODIC) h_vcycle<T, BC_PERIODIC>(a, top, zero_guess);
     else if (a.hom.kind == BC_ZEROGRAD) h_vcycle<T, BC_ZEROGRAD>(a, top, zero_guess);
     else h_vcycle<T, BC_FIXED>(a, top, zero_guess);

@@ -30,6 +30,7 @@ __host__ __device__ inline size_t at(const Grid& g, int i, int j, int k) {
 // Value on a face point; `a`, `b` are padded tangential indices (0..n+1).
 __device__ inline double face_value(const Bc& bc, const Grid& g, int face, int a, int b) {
   if (bc.kind == BC_FIXED) return bc.value;
+  if (bc.kind == BC_MIXED && !bc.faces) return 0.0;
   size_t off;
   size_t fx = (size_t)(g.ny + 2) * (g.nz + 2), fy = (size_t)(g.nx + 2) * (g.nz + 2),
          fz = (size_t)(g.nx + 2) * (g.ny + 2);
@@ -44,24 +45,31 @@ __device__ inline double face_value(const Bc& bc, const Grid& g, int face, int a
 template <typename T>
 __device__ __noinline__ T ghost(const T* u, int i, int j, int k, const Grid g,
                                 const Bc bc) {
-  const bool affine = (bc.kind == BC_FIXED || bc.kind == BC_OPEN);
-  const bool wrap = (bc.kind == BC_PERIODIC);
   int i2 = i, j2 = j, k2 = k;
   T az = 1, cz = 0, ay = 1, cy = 0, ax = 1, cx = 0;
   if ((unsigned)k >= (unsigned)g.nz) {
-    const int hi = k >= g.nz;
-    k2 = wrap ? (hi ? 0 : g.nz - 1) : (hi ? g.nz - 1 : 0);
-    if (affine) { az = -1; cz = (T)(2.0 * face_value(bc, g, 4 + hi, i + 1, j + 1)); }
+    const int hi = k >= g.nz, kind = face_kind(bc, 4 + hi);
+    k2 = kind == BC_PERIODIC ? (hi ? 0 : g.nz - 1) : (hi ? g.nz - 1 : 0);
+    if (kind == BC_FIXED || kind == BC_OPEN) {
+      az = -1;
+      cz = (T)(2.0 * face_value(bc, g, 4 + hi, i + 1, j + 1));
+    }
   }
   if ((unsigned)j >= (unsigned)g.ny) {
-    const int hi = j >= g.ny;
-    j2 = wrap ? (hi ? 0 : g.ny - 1) : (hi ? g.ny - 1 : 0);
-    if (affine) { ay = -1; cy = (T)(2.0 * face_value(bc, g, 2 + hi, i + 1, k2 + 1)); }
+    const int hi = j >= g.ny, kind = face_kind(bc, 2 + hi);
+    j2 = kind == BC_PERIODIC ? (hi ? 0 : g.ny - 1) : (hi ? g.ny - 1 : 0);
+    if (kind == BC_FIXED || kind == BC_OPEN) {
+      ay = -1;
+      cy = (T)(2.0 * face_value(bc, g, 2 + hi, i + 1, k2 + 1));
+    }
   }
   if ((unsigned)i >= (unsigned)g.nx) {
-    const int hi = i >= g.nx;
-    i2 = wrap ? (hi ? 0 : g.nx - 1) : (hi ? g.nx - 1 : 0);
-    if (affine) { ax = -1; cx = (T)(2.0 * face_value(bc, g, 0 + hi, j2 + 1, k2 + 1)); }
+    const int hi = i >= g.nx, kind = face_kind(bc, hi);
+    i2 = kind == BC_PERIODIC ? (hi ? 0 : g.nx - 1) : (hi ? g.nx - 1 : 0);
+    if (kind == BC_FIXED || kind == BC_OPEN) {
+      ax = -1;
+      cx = (T)(2.0 * face_value(bc, g, 0 + hi, j2 + 1, k2 + 1));
+    }
   }
   T v = u[at(g, i2, j2, k2)];
   v = ax * v + cx;
@@ -260,19 +268,27 @@ __device__ __forceinline__ void prolong_range(const T* uc, T* uf, Grid gf, Bc bc
   }
 }
 
-// COARSEST on a single cell: the six ghosts are 2 b_face - u (fixed / open)
-// or u itself (periodic / zero gradient, singular: 0).
+// COARSEST on a single cell: a ghost is 2 b_face - u on a fixed / open face
+// and u itself on a periodic / zero-gradient one, so with a such faces
+// sum(ghosts) - 6u = 2 sum(b) - 2 a u = h^2 f; with none it is singular.
 template <typename T>
 __device__ __forceinline__ void coarsest_one(const T* f, T* u, double h, Bc bc,
                                              bool keep = false) {
-  if (bc.kind == BC_PERIODIC || bc.kind == BC_ZEROGRAD) {
+  const Grid g{1, 1, 1};
+  int a = 0;
+  double sb = 0.0;
+  for (int face = 0; face < 6; ++face) {
+    const int kind = face_kind(bc, face);
+    if (kind == BC_FIXED || kind == BC_OPEN) {
+      ++a;
+      sb += face_value(bc, g, face, 1, 1);
+    }
+  }
+  if (a == 0) {
     if (!keep) u[0] = T(0);  // singular: any value solves it; keep the start (FAS) or 0
     return;
   }
-  const Grid g{1, 1, 1};
-  double sb = 0.0;
-  for (int face = 0; face < 6; ++face) sb += face_value(bc, g, face, 1, 1);
-  u[0] = (T)((2.0 * sb - h * h * (double)f[0]) / 12.0);
+  u[0] = (T)((2.0 * sb - h * h * (double)f[0]) / (2.0 * a));
 }
 
 }  // namespace dev

@@ -11,7 +11,7 @@
 
 namespace mg {
 
-enum BcKind : int { BC_PERIODIC = 0, BC_FIXED = 1, BC_ZEROGRAD = 2, BC_OPEN = 3 };
+enum BcKind : int { BC_PERIODIC = 0, BC_FIXED = 1, BC_ZEROGRAD = 2, BC_OPEN = 3, BC_MIXED = 4 };
 
 // Cells per side of one level.
 struct Grid {
@@ -21,17 +21,34 @@ struct Grid {
 
 // Boundary rule of one level as a kernel sees it (Sec. 2.3.6).  OPEN uses the
 // level's face array (layout of mg.h); FIXED uses `value`; the homogeneous
-// counterpart of FIXED/OPEN is FIXED with value 0.
+// counterpart of FIXED/OPEN is FIXED with value 0.  MIXED has a rule per face:
+// bits 2q..2q+1 of `fk` hold the kind of face q (x-, x+, y-, y+, z-, z+:
+// periodic, fixed or zero gradient) and the fixed faces' values are read from
+// the face array, or are 0 where it is null (the homogeneous rule).
 struct Bc {
   int kind;
   double value;
   const double* faces;
+  int fk;
 };
 
+__host__ __device__ inline int face_kind(const Bc& b, int face) {
+  return b.kind == BC_MIXED ? (b.fk >> (2 * face)) & 3 : b.kind;
+}
+
+// A MIXED rule whose six faces have one kind is that kind's rule (its fixed
+// faces then hold 0: only homogeneous rules are collapsed).
+inline Bc collapse_homogeneous(Bc h) {
+  if (h.kind != BC_MIXED) return h;
+  for (int q = 1; q < 6; ++q)
+    if (face_kind(h, q) != face_kind(h, 0)) return h;
+  return Bc{face_kind(h, 0), 0.0, nullptr, 0};
+}
+
 inline Bc homogeneous(const Bc& b) {
-  Bc h{b.kind, 0.0, nullptr};
+  Bc h{b.kind, 0.0, nullptr, b.fk};
   if (b.kind == BC_FIXED || b.kind == BC_OPEN) h.kind = BC_FIXED;
-  return h;
+  return collapse_homogeneous(h);
 }
 
 inline size_t faces_count(const Grid& g) {

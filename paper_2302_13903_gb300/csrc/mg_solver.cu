@@ -39,12 +39,15 @@ struct mg_ctx {
   int L = 0;            // number of levels; level L-1 is the finest
   double h = 0.0;       // finest spacing
   int bc_kind = 0;
+  // MG_BC_MIXED: the kind of face q in bits 2q..2q+1 and the fixed faces' values
+  int face_mask = 0;
+  double face_b[6] = {};
   mg_opts opts{};
   int device = 0;
   // FP64 hierarchy (u64[L-1] is the caller's phi during a solve).
   double* u64[kMaxLevels] = {};
   double* f64[kMaxLevels] = {};
-  double* faces[kMaxLevels] = {};  // open boundary values per level
+  double* faces[kMaxLevels] = {};  // open / fixed-face boundary values per level
   double* ur64[kMaxLevels] = {};   // FAS: restricted potential per coarse level
   // FP32 hierarchy (mixed precision); u32b is the second buffer of levels the
   // fused kernels handle (they read one buffer and write the other).
@@ -146,9 +149,21 @@ T* dalloc(mg_ctx* c, size_t count) {
   return static_cast<T*>(p);
 }
 
+// Whether no face fixes the zero point of phi (Sec. 2.3.6): then the means of
+// f and phi are removed.
+bool mean_free(const mg_ctx* c) {
+  if (c->bc_kind == MG_BC_MIXED) {
+    for (int q = 0; q < 6; ++q)
+      if (((c->face_mask >> (2 * q)) & 3) == MG_BC_FIXED) return false;
+    return true;
+  }
+  return c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD;
+}
+
 // The device arrays of a context (counted only, when c->dry).
 void alloc_hierarchy(mg_ctx* c) {
   const mg_bc bc = (mg_bc)c->bc_kind;
+  const bool face_arrays = bc == MG_BC_OPEN || bc == MG_BC_MIXED;
   const mg_opts& o = c->opts;
   const int L = c->L;
   const int F = L - 1;
@@ -158,20 +173,23 @@ void alloc_hierarchy(mg_ctx* c) {
       if (l < F) c->u64[l] = dalloc<double>(c, cells);
       if (l < F && o.fas) c->ur64[l] = dalloc<double>(c, cells);
       c->f64[l] = dalloc<double>(c, cells);
-      if (bc == MG_BC_OPEN) c->faces[l] = dalloc<double>(c, mg::faces_count(level_grid(c, l)));
+      if (face_arrays) c->faces[l] = dalloc<double>(c, mg::faces_count(level_grid(c, l)));
     } else {
       c->u32[l] = dalloc<float>(c, cells);
       c->f32[l] = dalloc<float>(c, cells);
-      if (mg::fused_ok(level_grid(c, l), mg::homogeneous(Bc{(int)bc, 0.0, nullptr})))
+      if (mg::fused_ok(level_grid(c, l), mg::homogeneous(Bc{(int)bc, 0.0, nullptr, c->face_mask})))
         c->u32b[l] = dalloc<float>(c, cells);
     }
   }
   if (o.prec == MG_MIXED) {
     c->f64[F] = dalloc<double>(c, level_grid(c, F).cells());
-    if (bc == MG_BC_OPEN) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
+    if (face_arrays) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
   }
   c->partials_cap = mg::kPartials;
-  if (o.prec == MG_MIXED && o.outer_fixed && mg::fx_step_ok(level_grid(c, F))) {
+  // the fixed-point outer step synthesises one rule per grid: a rule per face
+  // takes the FP64 outer residual
+  if (o.prec == MG_MIXED && o.outer_fixed && bc != MG_BC_MIXED &&
+      mg::fx_step_ok(level_grid(c, F))) {
     c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
     const int nb = mg::fx_step_blocks(level_grid(c, F), 0);
     if (nb > c->partials_cap) c->partials_cap = nb;
@@ -183,8 +201,27 @@ void alloc_hierarchy(mg_ctx* c) {
 }
 
 Bc physical_bc(const mg_ctx* c, int l) {
-  Bc b{c->bc_kind, c->opts.fixed_value, c->faces[l]};
+  Bc b{c->bc_kind, c->opts.fixed_value, c->faces[l], c->face_mask};
   return b;
+}
+
+// Fill the face arrays of a rule per face with each face's value (levels
+// that have one; constant over the face and the same on every level).
+void fill_mixed_faces(mg_ctx* c) {
+  for (int l = 0; l < c->L; ++l) {
+    if (!c->faces[l]) continue;
+    const Grid g = level_grid(c, l);
+    const size_t fx = (size_t)(g.ny + 2) * (g.nz + 2), fy = (size_t)(g.nx + 2) * (g.nz + 2),
+                 fz = (size_t)(g.nx + 2) * (g.ny + 2);
+    const size_t len[6] = {fx, fx, fy, fy, fz, fz};
+    size_t off = 0;
+    for (int q = 0; q < 6; ++q) {
+      check(c, mg::launch_fill<double>(c->faces[l] + off, (long long)len[q], c->face_b[q], nullptr),
+            "face values");
+      off += len[q];
+    }
+  }
+  check(c, cudaStreamSynchronize(nullptr), "sync");
 }
 
 // Brackets one finest-level launch with events when timing is on.
@@ -376,7 +413,9 @@ void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool ze
   const Grid g = level_grid(c, l);
   const double h = level_h(c, l);
   if constexpr (std::is_same<T, float>::value) {
-    if (c->u32b[l] && mg::fused_ok(g, bc_top)) {
+    // the fused up leg synthesises the coarse correction's ghosts with the
+    // level's own rule, so it serves levels whose coarse rule is the same
+    if (c->u32b[l] && mg::fused_ok(g, bc_top) && hom.kind == bc_top.kind) {
       vcycle_fused(c, l, bc_top, hom, zero_guess, s);
       return;
     }
@@ -506,7 +545,7 @@ double prepare_source(mg_ctx* c, const double* rho, double four_pi_G, double* f_
     KTimer t(c, MG_K_SOURCE, true, s);
     check(c, mg::launch_source(rho, f_fin, N, four_pi_G, c->partials, s), "source");
   }
-  if (c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD)
+  if (mean_free(c))
     check(c, mg::launch_subtract_mean(f_fin, N, c->partials, nb, c->scal + 40, s), "subtract_mean");
   check(c, mg::launch_sum<double>(f_fin, N, 1, c->partials, s), "sum f^2");
   check(c, mg::launch_finish_sum(c->partials, nb, c->scal + 0, s), "finish f^2");
@@ -526,7 +565,7 @@ double prepare_source(mg_ctx* c, const double* rho, double four_pi_G, double* f_
 }
 
 void remove_mean(mg_ctx* c, double* u, cudaStream_t s) {
-  if (c->bc_kind != MG_BC_PERIODIC && c->bc_kind != MG_BC_ZEROGRAD) return;
+  if (!mean_free(c)) return;
   const long long N = level_grid(c, c->L - 1).cells();
   check(c, mg::launch_sum<double>(u, N, 0, c->partials, s), "sum phi");
   check(c, mg::launch_subtract_mean(u, N, c->partials, mg::reduce_blocks(N), c->scal + 40, s),
@@ -547,11 +586,18 @@ double defect_rms(mg_ctx* c, const double* u, const double* f, const Bc& bc, cud
 }
 
 // The rule of the coarse correction levels below a level with rule `top`:
-// its homogeneous counterpart, or with coarse_literal zero fixed values for a
-// zero-gradient rule too (Sec. 2.3.6 taken word for word).
+// its homogeneous counterpart, or with coarse_literal zero fixed values on
+// zero-gradient faces too (Sec. 2.3.6 taken word for word).
 Bc correction_bc(const mg_ctx* c, const Bc& top) {
-  const Bc z = mg::homogeneous(top);
-  if (c->opts.coarse_literal && z.kind == mg::BC_ZEROGRAD) return Bc{mg::BC_FIXED, 0.0, nullptr};
+  Bc z = mg::homogeneous(top);
+  if (!c->opts.coarse_literal) return z;
+  if (z.kind == mg::BC_ZEROGRAD) return Bc{mg::BC_FIXED, 0.0, nullptr};
+  if (z.kind == mg::BC_MIXED) {
+    for (int q = 0; q < 6; ++q)
+      if (mg::face_kind(z, q) == mg::BC_ZEROGRAD)
+        z.fk = (z.fk & ~(3 << (2 * q))) | (mg::BC_FIXED << (2 * q));
+    z = mg::collapse_homogeneous(z);
+  }
   return z;
 }
 
@@ -672,9 +718,14 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   const Bc hom = mg::homogeneous(bc);
   const Bc coarse = correction_bc(c, bc);
   const bool fx = c->opts.outer_fixed != 0 && c->fxbuf != nullptr;
-  const bool has_mean = c->bc_kind == MG_BC_PERIODIC || c->bc_kind == MG_BC_ZEROGRAD;
-  const bool zero_values = bc.kind == mg::BC_PERIODIC || bc.kind == mg::BC_ZEROGRAD ||
-                           (bc.kind == mg::BC_FIXED && bc.value == 0.0);
+  const bool has_mean = mean_free(c);
+  bool zero_values = bc.kind == mg::BC_PERIODIC || bc.kind == mg::BC_ZEROGRAD ||
+                     (bc.kind == mg::BC_FIXED && bc.value == 0.0);
+  if (bc.kind == mg::BC_MIXED) {
+    zero_values = true;
+    for (int q = 0; q < 6; ++q)
+      if (mg::face_kind(bc, q) == mg::BC_FIXED && c->face_b[q] != 0.0) zero_values = false;
+  }
   // From phi = 0 with a rule whose boundary values are 0, L phi = 0 and the
   // first residual is f itself.  On that path (with the fixed-point outer
   // loop) f is never stored as doubles: one pass over rho gives its sum (the
@@ -967,8 +1018,8 @@ float time_launches(mg_ctx* c, cudaStream_t s, int reps, void* flush, size_t flu
 void autotune(mg_ctx* c, cudaStream_t s) {
   cudaDeviceProp prop;
   check(c, cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
-  const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr});
-  const int periodic = c->bc_kind == MG_BC_PERIODIC ? 1 : 0;
+  const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr, c->face_mask});
+  const int periodic = hom.kind == mg::BC_PERIODIC ? 1 : 0;
   const double om = c->opts.omega;
   const int F = c->L - 1;
   const int reps = 5;
@@ -1169,8 +1220,11 @@ mg_status mg_destroy(mg_ctx* c) {
   return MG_OK;
 }
 
-mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* opts,
-                    mg_ctx** out) {
+namespace {
+
+// mg_create and mg_create_faces; face_mask / face_b describe a MIXED rule.
+mg_status create_ctx(int nx, int ny, int nz, double dx, mg_bc bc, int face_mask,
+                     const double* face_b, const mg_opts* opts, mg_ctx** out) {
   if (!out) {
     g_err = "mg_create: ctx is NULL";
     return MG_ERR_ARG;
@@ -1179,7 +1233,7 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
   mg_opts o;
   if (opts) o = *opts;
   else mg_opts_init(&o);
-  if (!dims_ok(nx, ny, nz) || !(dx > 0.0) || (int)bc < 0 || (int)bc > 3 ||
+  if (!dims_ok(nx, ny, nz) || !(dx > 0.0) || (int)bc < 0 || (int)bc > 4 ||
       validate_opts(o) != MG_OK) {
     g_err = "mg_create: invalid argument (powers of two >= 2 with nx the longest side, dx > 0, "
             "bc, opts)";
@@ -1192,6 +1246,10 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
     c->nz = nz;
     c->h = dx;
     c->bc_kind = (int)bc;
+    if (bc == MG_BC_MIXED) {
+      c->face_mask = face_mask;
+      for (int q = 0; q < 6; ++q) c->face_b[q] = face_b[q];
+    }
     c->opts = o;
     const int m = std::min(nx, std::min(ny, nz));
     int L = 1;
@@ -1201,6 +1259,7 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
     check(c, cudaGetDevice(&c->device), "cudaGetDevice");
     if (bc == MG_BC_OPEN) check(c, mg::prepare_multipole(), "multipole tables");
     alloc_hierarchy(c);
+    if (bc == MG_BC_MIXED) fill_mixed_faces(c);
     check(c, cudaMallocHost(&c->pinned, 64 * sizeof(double)), "cudaMallocHost");
   } catch (const Fail& f) {
     mg_destroy(c);
@@ -1208,6 +1267,57 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* 
   }
   *out = c;
   return MG_OK;
+}
+
+}  // namespace
+
+mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts* opts,
+                    mg_ctx** out) {
+  if (bc == MG_BC_MIXED) {
+    g_err = "mg_create: a rule per face is made by mg_create_faces";
+    if (out) *out = nullptr;
+    return MG_ERR_ARG;
+  }
+  return create_ctx(nx, ny, nz, dx, bc, 0, nullptr, opts, out);
+}
+
+mg_status mg_create_faces(int nx, int ny, int nz, double dx, const mg_bc* face_bc,
+                          const double* face_value, const mg_opts* opts, mg_ctx** out) {
+  if (out) *out = nullptr;
+  if (!face_bc || !out) {
+    g_err = "mg_create_faces: face_bc and ctx must not be NULL";
+    return MG_ERR_ARG;
+  }
+  double b[6] = {};
+  int mask = 0;
+  for (int q = 0; q < 6; ++q) {
+    const mg_bc k = face_bc[q];
+    if (k != MG_BC_PERIODIC && k != MG_BC_FIXED && k != MG_BC_ZEROGRAD) {
+      g_err = "mg_create_faces: a face is periodic, fixed or zero gradient";
+      return MG_ERR_ARG;
+    }
+    b[q] = (k == MG_BC_FIXED && face_value) ? face_value[q] : 0.0;
+    if (!std::isfinite(b[q])) {
+      g_err = "mg_create_faces: face values must be finite";
+      return MG_ERR_ARG;
+    }
+    mask |= (int)k << (2 * q);
+  }
+  for (int a = 0; a < 3; ++a)
+    if ((face_bc[2 * a] == MG_BC_PERIODIC) != (face_bc[2 * a + 1] == MG_BC_PERIODIC)) {
+      g_err = "mg_create_faces: periodic faces come in pairs";
+      return MG_ERR_ARG;
+    }
+  bool same = true;
+  for (int q = 1; q < 6; ++q) same = same && face_bc[q] == face_bc[0] && b[q] == b[0];
+  if (same) {  // one rule on every face: that rule's own context
+    mg_opts o;
+    if (opts) o = *opts;
+    else mg_opts_init(&o);
+    if (face_bc[0] == MG_BC_FIXED) o.fixed_value = b[0];
+    return create_ctx(nx, ny, nz, dx, face_bc[0], 0, nullptr, &o, out);
+  }
+  return create_ctx(nx, ny, nz, dx, MG_BC_MIXED, mask, b, opts, out);
 }
 
 mg_status mg_required_bytes(int nx, int ny, int nz, mg_bc bc, const mg_opts* opts,

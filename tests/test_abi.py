@@ -126,6 +126,17 @@ def test_argument_validation_needs_no_gpu():
     assert L.mg_create(8, 8, 8, 0.1, 0, ctypes.byref(bad), ctypes.byref(h)) == 1
     bad = mg.default_opts(coarse_literal=2)
     assert L.mg_create(8, 8, 8, 0.1, 2, ctypes.byref(bad), ctypes.byref(h)) == 1
+    # a rule per face: six kinds of periodic (in pairs), fixed or zero gradient,
+    # finite values; MG_BC_MIXED is not a kind mg_create takes
+    kinds = lambda *k: (ctypes.c_int * 6)(*k)
+    vals = (ctypes.c_double * 6)(0, 0, 0, 0, 0.5, float("nan"))
+    P, F, Z, OP = mg.PERIODIC, mg.FIXED, mg.ZEROGRAD, mg.OPEN
+    for k, v in [(kinds(P, F, Z, Z, F, F), None), (kinds(OP, OP, Z, Z, F, F), None),
+                 (kinds(P, P, Z, Z, F, F), vals), (kinds(P, P, Z, Z, 5, F), None)]:
+        assert L.mg_create_faces(8, 8, 8, 0.1, k, v, ctypes.byref(o), ctypes.byref(h)) == 1
+        assert not h.value
+    assert L.mg_create_faces(8, 8, 8, 0.1, None, None, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert L.mg_create(8, 8, 8, 0.1, mg.PER_FACE, ctypes.byref(o), ctypes.byref(h)) == 1
     # the batched solve keeps the homogeneous coarse rules
     lit = mg.default_opts(prec=mg.MIXED, coarse_literal=1)
     dims = (ctypes.c_int * 3)(16, 16, 16)

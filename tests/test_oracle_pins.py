@@ -155,6 +155,147 @@ def test_open_boundary_solve_equals_dense_solve_with_multipole_faces(orc):
 
 
 # --------------------------------------------------------------------------
+# A rule per face (Sec. 2.3.6: the rules may differ between boundaries; a
+# fixed value on any face sets the zero point, otherwise the means of f and
+# phi are removed).
+
+def dense_system_per_face(n, h, kinds, values):
+    """The 7-point operator with each face's own ghost elimination: periodic
+    wraps, zero gradient adds the cell itself, fixed b adds 2b - u."""
+    N = n ** 3
+    A = np.zeros((N, N))
+    g = np.zeros(N)
+    idx = lambda i, j, k: (k * n + j) * n + i
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                c = idx(i, j, k)
+                A[c, c] -= 6 / h ** 2
+                for axis in range(3):
+                    for side in (-1, 1):
+                        p = [i, j, k]
+                        p[axis] += side
+                        face = 2 * axis + (0 if side < 0 else 1)
+                        if 0 <= p[axis] < n:
+                            A[c, idx(*p)] += 1 / h ** 2
+                        elif kinds[face] == PERIODIC:
+                            p[axis] %= n
+                            A[c, idx(*p)] += 1 / h ** 2
+                        elif kinds[face] == ZEROGRAD:
+                            A[c, c] += 1 / h ** 2
+                        else:
+                            A[c, c] -= 1 / h ** 2
+                            g[c] += 2 * values[face] / h ** 2
+    return A, g
+
+
+MIXED_CASES = [
+    ((PERIODIC, PERIODIC, ZEROGRAD, ZEROGRAD, FIXED, FIXED), (0, 0, 0, 0, 0.3, -0.2)),
+    ((FIXED, ZEROGRAD, PERIODIC, PERIODIC, ZEROGRAD, ZEROGRAD), (0.5, 0, 0, 0, 0, 0)),
+    ((ZEROGRAD, FIXED, FIXED, ZEROGRAD, FIXED, ZEROGRAD), (0, -0.4, 0.1, 0, 0.7, 0)),
+    ((PERIODIC, PERIODIC, ZEROGRAD, ZEROGRAD, ZEROGRAD, ZEROGRAD), (0,) * 6),  # no zero point
+]
+
+
+@pytest.mark.parametrize("case", range(len(MIXED_CASES)))
+@pytest.mark.parametrize("n", [4, 8])
+def test_per_face_rules_converge_to_the_dense_solve(orc, case, n):
+    kinds, values = MIXED_CASES[case]
+    rng = np.random.default_rng(60 + 7 * case + n)
+    h = 1.0 / n
+    rho = rng.standard_normal((n, n, n))
+    A, g = dense_system_per_face(n, h, kinds, values)
+    f = rho.ravel().copy()
+    if FIXED not in kinds:
+        f -= f.mean()
+        M = np.zeros((n ** 3 + 1, n ** 3 + 1))
+        M[:-1, :-1] = A
+        M[:-1, -1] = 1.0
+        M[-1, :-1] = 1.0
+        ref = np.linalg.solve(M, np.append(f - g, 0.0))[:-1]
+    else:
+        ref = np.linalg.solve(A, f - g)
+    for cycle in (orc.CORRECTION, orc.FAS):
+        r = orc.solve(rho, h, orc.PER_FACE, faces=orc.mixed_rule(kinds, values), tol=0.0,
+                      max_cycles=80, cycle=cycle)
+        assert r.ok, (cycle, r.status, r.hist)
+        assert emax(r.phi.ravel(), ref) < 1e-12, cycle
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_per_face_coarsest_is_exact(orc, n):
+    """COARSEST on one or eight cells with the ghosts eliminated face by face
+    (a periodic or zero-gradient ghost is the cell itself) equals the dense
+    solve; without a fixed face the one-cell system is singular and stays 0."""
+    h = 0.5
+    kinds, values = MIXED_CASES[2]
+    f = np.random.default_rng(3).standard_normal((n, n, n))
+    A, g = dense_system_per_face(n, h, kinds, values)
+    ref = np.linalg.solve(A, f.ravel() - g)
+    if n == 1:
+        u = orc.coarsest(f, h, orc.PER_FACE, faces=orc.mixed_rule(kinds, values))
+    else:  # N_0,max Gauss-Seidel sweeps do not solve exactly: iterate V-cycles instead
+        u = np.zeros_like(f)
+        for _ in range(60):
+            u = orc.vcycle(u, f, h, orc.PER_FACE, faces=orc.mixed_rule(kinds, values))
+    assert emax(u.ravel(), ref) < 1e-12
+    kinds0, values0 = MIXED_CASES[3]
+    u0 = orc.coarsest(np.ones((1, 1, 1)), h, orc.PER_FACE, faces=orc.mixed_rule(kinds0, values0))
+    assert u0[0, 0, 0] == 0.0
+
+
+def test_per_face_mixed_eigenmode_is_exact(orc):
+    """sin(2 pi x) cos(pi y) sin(pi z) with x periodic, y zero gradient and z
+    zero fixed is an eigenvector of that operator: lambda is the sum of the
+    one-dimensional eigenvalues -(4/h^2) sin^2(pi h), -(4/h^2) sin^2(pi h / 2)
+    and -(4/h^2) sin^2(pi h / 2)."""
+    n = 32
+    h = 1.0 / n
+    x, y, z = grid(n)
+    f = np.sin(2 * np.pi * x) * np.cos(np.pi * y) * np.sin(np.pi * z)
+    lam = -(4 / h ** 2) * (np.sin(np.pi * h) ** 2 + 2 * np.sin(np.pi * h / 2) ** 2)
+    kinds = (PERIODIC, PERIODIC, ZEROGRAD, ZEROGRAD, FIXED, FIXED)
+    r = orc.solve(f, h, orc.PER_FACE, faces=orc.mixed_rule(kinds), tol=1e-12, max_cycles=60)
+    assert r.ok
+    assert emax(r.phi, f / lam) < 1e-10
+
+
+def test_per_face_linear_potential_is_exact(orc):
+    """With no source, fixed values a and b on the x faces and zero gradient
+    elsewhere the discrete solution is the straight line between them: the
+    7-point operator and the ghost 2b - u are exact for linear functions."""
+    n = 16
+    h = 1.0 / n
+    a, b = 0.25, -1.5
+    x, _, _ = grid(n)
+    kinds = (FIXED, FIXED, ZEROGRAD, ZEROGRAD, ZEROGRAD, ZEROGRAD)
+    r = orc.solve(np.zeros((n, n, n)), h, orc.PER_FACE, faces=orc.mixed_rule(kinds, (a, b, 0, 0, 0, 0)),
+                  tol=1e-13, max_cycles=80)
+    assert r.ok, r.hist
+    want = np.broadcast_to(a + (b - a) * x, (n, n, n))
+    assert np.abs(r.phi - want).max() < 1e-12
+
+
+def test_per_face_uniform_descriptor_is_the_uniform_rule(orc):
+    n = 16
+    rho = inputs.gaussian_blobs(n, 4, seed=8, periodic=False)
+    for kind, val in ((PERIODIC, 0.0), (FIXED, 0.3), (ZEROGRAD, 0.0)):
+        a = orc.solve(rho, 1.0 / n, kind, bc_value=val, tol=1e-10)
+        b = orc.solve(rho, 1.0 / n, orc.PER_FACE, faces=orc.mixed_rule([kind] * 6, [val] * 6),
+                      tol=1e-10)
+        assert np.array_equal(a.phi, b.phi) and np.array_equal(a.hist, b.hist)
+
+
+def test_per_face_descriptor_is_checked(orc):
+    n = 4
+    bad = [(PERIODIC, FIXED, ZEROGRAD, ZEROGRAD, FIXED, FIXED),  # periodic needs its pair
+           (OPEN, OPEN, ZEROGRAD, ZEROGRAD, FIXED, FIXED)]  # open faces are all-or-nothing
+    for kinds in bad:
+        r = orc.solve(np.ones((n, n, n)), 0.25, orc.PER_FACE, faces=orc.mixed_rule(kinds))
+        assert r.status == 1
+
+
+# --------------------------------------------------------------------------
 # Convergence behaviour the paper prints (Sec. 4.1.1).
 
 @pytest.mark.parametrize("bc", [PERIODIC, FIXED, ZEROGRAD])
