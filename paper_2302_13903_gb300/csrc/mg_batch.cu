@@ -582,25 +582,25 @@ __device__ __forceinline__ void tile_leg(bool down, bool per, const GridDev& g, 
     const bool zg = (l < g.L - 1) || zero_finest;
     if (zg) {
       if (per)
-        fused::fused_tile<fused::kDown, true, true, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, true, 7, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, true, false, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, true, 0, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     } else {
       if (per)
-        fused::fused_tile<fused::kDown, false, true, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, false, 7, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, false, false, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, false, 0, TX, 16, 4, false, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     }
   } else {
     if (per)
-      fused::fused_tile<fused::kUp, false, true, TX, 16, 4, false, kThreads>(
+      fused::fused_tile<fused::kUp, false, 7, TX, 16, 4, false, kThreads>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
     else
-      fused::fused_tile<fused::kUp, false, false, TX, 16, 4, false, kThreads>(
+      fused::fused_tile<fused::kUp, false, 0, TX, 16, 4, false, kThreads>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
   }
 }
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
           const double hl = g.h * (double)(1 << (g.L - 1 - l));
           fused::FusedParams fp;
           fp.nx = fp.ny = fp.nz = P.n;
-          fp.s = g.bc == BC_ZEROGRAD ? 1.f : -1.f;
+          fp.sx0 = fp.sx1 = fp.sy0 = fp.sy1 = fp.sz0 = fp.sz1 = g.bc == BC_ZEROGRAD ? 1.f : -1.f;
           fp.cu = (float)(1.0 - c.omega);
           fp.cs = (float)(c.omega / 6.0);
           fp.cf = (float)(-c.omega * hl * hl / 6.0);

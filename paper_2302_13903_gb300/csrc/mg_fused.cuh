@@ -34,10 +34,13 @@
 // alignment, 4 in y to keep row pairs) and must see the values from before
 // the step.
 //
-// Boundaries: periodic halo cells are real cells at wrapped indices and are
-// updated like any other; for the non-periodic rules a neighbour outside the
-// level is s * (the cell itself), s = -1 (zero fixed) or +1 (zero gradient) --
-// the ghost value of Sec. 2.3.6 at the moment it is read.
+// Boundaries: along a periodic axis (bit a of the compile-time mask PM) halo
+// cells are real cells at wrapped indices and are updated like any other;
+// across a non-periodic face a neighbour outside the level is s * (the cell
+// itself), with the face's own s = -1 (zero fixed) or +1 (zero gradient) --
+// the ghost value of Sec. 2.3.6 at the moment it is read.  PM = 7 is the
+// periodic rule, 0 the zero-fixed / zero-gradient ones (one s on every face
+// or one per face), 3 a slab periodic in x and y.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -51,7 +54,8 @@ namespace fused {
 
 struct FusedParams {
   int nx, ny, nz;
-  float s;           // -1 zero fixed, +1 zero gradient (non-periodic rules)
+  // ghost sign of each non-periodic face: -1 zero fixed, +1 zero gradient
+  float sx0, sx1, sy0, sy1, sz0, sz1;
   float cu, cs, cf;  // SOR: u <- cu u + cs sum_nb + cf f
   float inv_h2;
   int cz;            // planes per CTA (multiple of 8, or nz)
@@ -60,6 +64,12 @@ struct FusedParams {
 enum Mode : int { kPlain = 0, kDown = 1, kUp = 2 };
 
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Periodic axes of a mask PM.
+template <int PM>
+struct Per {
+  static constexpr bool X = (PM & 1) != 0, Y = (PM & 2) != 0, Z = (PM & 4) != 0;
+};
 
 // ---------------------------------------------------------------------------
 // Packed helpers.  A row of four cells is kept as e = (c0, c2), o = (c1, c3).
@@ -111,7 +121,7 @@ __device__ __forceinline__ float2 defect2(float2 self, float2 xm, float2 xp, flo
   return __ffma2_rn(make_float2(-p.inv_h2, -p.inv_h2), lap, f);
 }
 
-// Boundary flags of a thread's patch for the non-periodic rules.
+// Boundary flags of a thread's patch at non-periodic faces.
 struct Flags {
   bool xlo, xhi, ylo, yhi;
 };
@@ -133,17 +143,31 @@ __device__ __forceinline__ void set_part(Row& r, float2 v) {
 // x neighbours of one row's e cells (E) or o cells (!E); `sidev` is the
 // neighbouring thread's cell next to them: its c3 on the left for e, its c0 on
 // the right for o.
-template <bool PER, bool E>
+template <int PM, bool E>
 __device__ __forceinline__ void x_nb(const Row& r, float sidev, float2 self, float2& xm,
                                      float2& xp, const FusedParams& p, const Flags& fl) {
   if (E) {
     xm = f2(sidev, r.o.x);
     xp = r.o;
-    if (!PER && fl.xlo) xm.x = p.s * self.x;
+    if (!Per<PM>::X && fl.xlo) xm.x = p.sx0 * self.x;
   } else {
     xm = r.e;
     xp = f2(r.e.y, sidev);
-    if (!PER && fl.xhi) xp.y = p.s * self.y;
+    if (!Per<PM>::X && fl.xhi) xp.y = p.sx1 * self.y;
+  }
+}
+
+// The y / z neighbours of a row's cells with the ghosts of non-periodic faces
+// applied (yout: the neighbours in the adjacent row pair, on the low side for
+// row a, ROWB = false, on the high side for row b).
+template <int PM, bool ROWB>
+__device__ __forceinline__ void yz_ghosts(float2 self, float2& yout, float2& zmv, float2& zpv,
+                                          const FusedParams& p, const Flags& fl, bool zlo,
+                                          bool zhi) {
+  if (!Per<PM>::Y) yout = sub_if(ROWB ? fl.yhi : fl.ylo, ROWB ? p.sy1 : p.sy0, self, yout);
+  if (!Per<PM>::Z) {
+    zmv = sub_if(zlo, p.sz0, self, zmv);
+    zpv = sub_if(zhi, p.sz1, self, zpv);
   }
 }
 
@@ -152,34 +176,33 @@ __device__ __forceinline__ void x_nb(const Row& r, float sidev, float2 self, flo
 // the patch's other row; sidev as in x_nb.  DEF: *d receives the updated
 // cells' defects from the update's own neighbour sum (plus, for the
 // non-periodic rules, the change of their ghost neighbours s u).
-template <bool PER, bool E, bool ROWB, bool DEF>
+template <int PM, bool E, bool ROWB, bool DEF>
 __device__ __forceinline__ void sor_row(Row& r, const Row& other, float2 yout, float sidev,
                                         const Row& rzm, const Row& rzp, const Row& rf,
                                         const FusedParams& p, const Flags& fl, bool zlo, bool zhi,
                                         float2* d) {
   const float2 self = part<E>(r);
   float2 xm, xp;
-  x_nb<PER, E>(r, sidev, self, xm, xp, p, fl);
+  x_nb<PM, E>(r, sidev, self, xm, xp, p, fl);
   const float2 yin = part<E>(other);
   float2 zmv = part<E>(rzm), zpv = part<E>(rzp);
-  if (!PER) {
-    yout = sub_if(ROWB ? fl.yhi : fl.ylo, p.s, self, yout);
-    zmv = sub_if(zlo, p.s, self, zmv);
-    zpv = sub_if(zhi, p.s, self, zpv);
-  }
+  yz_ghosts<PM, ROWB>(self, yout, zmv, zpv, p, fl, zlo, zhi);
   float2 sum;
   const float2 un = ROWB ? sor2(self, xm, xp, yin, yout, zmv, zpv, part<E>(rf), p, sum)
                          : sor2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p, sum);
   set_part<E>(r, un);
   if (DEF) {
     float2 dd = defect_from_sum(un, sum, part<E>(rf), p);
-    if (!PER) {
+    if (PM != 7) {
       // each ghost neighbour s u moved with u: its share of the finished
       // sweep's sum is s (un - self) more than the update used
-      const float base = (float)((ROWB ? fl.yhi : fl.ylo) + zlo + zhi);
-      const float k = -p.s * p.inv_h2;
-      const float2 kng = make_float2(k * (base + ((E && fl.xlo) ? 1.f : 0.f)),
-                                     k * (base + ((!E && fl.xhi) ? 1.f : 0.f)));
+      float sg = 0.f;
+      if (!Per<PM>::Y && (ROWB ? fl.yhi : fl.ylo)) sg += ROWB ? p.sy1 : p.sy0;
+      if (!Per<PM>::Z && zlo) sg += p.sz0;
+      if (!Per<PM>::Z && zhi) sg += p.sz1;
+      const float sgx = sg + ((!Per<PM>::X && E && fl.xlo) ? p.sx0 : 0.f);
+      const float sgy = sg + ((!Per<PM>::X && !E && fl.xhi) ? p.sx1 : 0.f);
+      const float2 kng = make_float2(-p.inv_h2 * sgx, -p.inv_h2 * sgy);
       dd = __ffma2_rn(kng, add2(un, make_float2(-self.x, -self.y)), dd);
     }
     *d = dd;
@@ -187,21 +210,17 @@ __device__ __forceinline__ void sor_row(Row& r, const Row& other, float2 yout, f
 }
 
 // Defect of one row's E cells (arguments as in sor_row).
-template <bool PER, bool E, bool ROWB>
+template <int PM, bool E, bool ROWB>
 __device__ __forceinline__ float2 defect_row(const Row& r, const Row& other, float2 yout,
                                              float sidev, const Row& rzm, const Row& rzp,
                                              const Row& rf, const FusedParams& p,
                                              const Flags& fl, bool zlo, bool zhi) {
   const float2 self = part<E>(r);
   float2 xm, xp;
-  x_nb<PER, E>(r, sidev, self, xm, xp, p, fl);
+  x_nb<PM, E>(r, sidev, self, xm, xp, p, fl);
   const float2 yin = part<E>(other);
   float2 zmv = part<E>(rzm), zpv = part<E>(rzp);
-  if (!PER) {
-    yout = sub_if(ROWB ? fl.yhi : fl.ylo, p.s, self, yout);
-    zmv = sub_if(zlo, p.s, self, zmv);
-    zpv = sub_if(zhi, p.s, self, zpv);
-  }
+  yz_ghosts<PM, ROWB>(self, yout, zmv, zpv, p, fl, zlo, zhi);
   return ROWB ? defect2(self, xm, xp, yin, yout, zmv, zpv, part<E>(rf), p)
               : defect2(self, xm, xp, yout, yin, zmv, zpv, part<E>(rf), p);
 }
@@ -222,7 +241,7 @@ __device__ __forceinline__ float side_of(const float2* SP, int idx, int offL, in
 // the other colour's cells of this plane in the pair plane SP (offsets in
 // float2); zm, zp: the patch in the planes below / above.  DEF: dsum receives
 // the updated cells' defects summed over both rows (sor_row).
-template <bool PER, bool AE, bool DEF = false>
+template <int PM, bool AE, bool DEF = false>
 __device__ __forceinline__ void sor_pairs(Patch& u, const float2* __restrict__ SP, int pa, int pb,
                                           int offL, int offR, int offU, int offD, const Patch& zm,
                                           const Patch& zp, const Patch& f, const FusedParams& p,
@@ -230,25 +249,25 @@ __device__ __forceinline__ void sor_pairs(Patch& u, const float2* __restrict__ S
                                           float2* dsum = nullptr) {
   constexpr bool BE = !AE;
   float2 da, db;
-  sor_row<PER, AE, false, DEF>(u.a, u.b, SP[pa + offU], side_of(SP, pa, offL, offR, AE), zm.a,
-                               zp.a, f.a, p, fl, zlo, zhi, &da);
-  sor_row<PER, BE, true, DEF>(u.b, u.a, SP[pb + offD], side_of(SP, pb, offL, offR, BE), zm.b,
-                              zp.b, f.b, p, fl, zlo, zhi, &db);
+  sor_row<PM, AE, false, DEF>(u.a, u.b, SP[pa + offU], side_of(SP, pa, offL, offR, AE), zm.a,
+                              zp.a, f.a, p, fl, zlo, zhi, &da);
+  sor_row<PM, BE, true, DEF>(u.b, u.a, SP[pb + offD], side_of(SP, pb, offL, offR, BE), zm.b,
+                             zp.b, f.b, p, fl, zlo, zhi, &db);
   if (DEF) *dsum = add2(da, db);
 }
 
 // Defect of the red cells of a patch (row a's e cells if AE, row b's of the
 // other parity) from a pair plane of the final black cells, summed over both
 // rows.
-template <bool PER, bool AE>
+template <int PM, bool AE>
 __device__ __forceinline__ float2 defect_red(const Patch& u, const float2* __restrict__ SP, int pa,
                                              int pb, int RS2, const Patch& zm, const Patch& zp,
                                              const Patch& f, const FusedParams& p,
                                              const Flags& fl, bool zlo, bool zhi) {
-  const float2 da = defect_row<PER, AE, false>(u.a, u.b, SP[pa - RS2], side_of(SP, pa, -1, 1, AE),
-                                               zm.a, zp.a, f.a, p, fl, zlo, zhi);
-  const float2 db = defect_row<PER, !AE, true>(u.b, u.a, SP[pb + RS2], side_of(SP, pb, -1, 1, !AE),
-                                               zm.b, zp.b, f.b, p, fl, zlo, zhi);
+  const float2 da = defect_row<PM, AE, false>(u.a, u.b, SP[pa - RS2], side_of(SP, pa, -1, 1, AE),
+                                              zm.a, zp.a, f.a, p, fl, zlo, zhi);
+  const float2 db = defect_row<PM, !AE, true>(u.b, u.a, SP[pb + RS2], side_of(SP, pb, -1, 1, !AE),
+                                              zm.b, zp.b, f.b, p, fl, zlo, zhi);
   return add2(da, db);
 }
 
@@ -270,55 +289,56 @@ __device__ __forceinline__ void cp_async_wait() {
 // four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  The up leg
 // stages the coarse cells under its tile in shared memory, one plane at a
 // time: CX columns from x0/2 - 4 and CY rows from y0/2 - HY/2 - 1, wrapped
-// (periodic) or zero-filled outside the level.  A thread's 3 x 4 block then
-// starts at tile row tp, column 1 + 2 tr; for the non-periodic rules its
-// indices are clamped to the level's edge cells and carry the ghost sign s
-// (CoarseIdx).  Patches outside the level read clamped indices; their values
-// are unused.
+// along periodic axes, zero-filled outside the level along the others.  A
+// thread's 3 x 4 block then starts at tile row tp, column 1 + 2 tr; along a
+// non-periodic axis its indices are clamped to the level's edge cells and
+// carry that face's ghost sign s (CoarseIdx).  Patches outside the level read
+// clamped indices; their values are unused.
 struct Coarse12 {
   float c[3][4];
 };
 
-template <bool PER>
 struct CoarseIdx {
-  int col[4];  // tile column (non-periodic rules)
+  int col[4];  // tile column
   int row[3];  // tile row
   float sx[4], sy[3];  // ghost signs (1 inside)
 };
 
-template <bool PER>
-__device__ __forceinline__ CoarseIdx<PER> coarse_idx(const FusedParams& p, int gx4, int gyA,
-                                                     int cx0, int cy0) {
+// Along a periodic axis the tile index is the plain one (the staged tile is
+// wrapped) and the sign 1.
+template <int PM>
+__device__ __forceinline__ CoarseIdx coarse_idx(const FusedParams& p, int gx4, int gyA, int cx0,
+                                                int cy0) {
   const int cnx = p.nx >> 1, cny = p.ny >> 1;
   const int X0 = gx4 >> 1, Y = gyA >> 1;
-  CoarseIdx<PER> ci;
+  CoarseIdx ci;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int Xc = X0 - 1 + a;
-    ci.sx[a] = (Xc < 0 || Xc >= cnx) ? p.s : 1.f;
-    ci.col[a] = (Xc < 0 ? 0 : (Xc >= cnx ? cnx - 1 : Xc)) - cx0;
+    ci.sx[a] = Per<PM>::X ? 1.f : (Xc < 0 ? p.sx0 : (Xc >= cnx ? p.sx1 : 1.f));
+    ci.col[a] = (Per<PM>::X ? Xc : (Xc < 0 ? 0 : (Xc >= cnx ? cnx - 1 : Xc))) - cx0;
   }
 #pragma unroll
   for (int yy = 0; yy < 3; ++yy) {
     const int Yc = Y - 1 + yy;
-    ci.sy[yy] = (Yc < 0 || Yc >= cny) ? p.s : 1.f;
-    ci.row[yy] = (Yc < 0 ? 0 : (Yc >= cny ? cny - 1 : Yc)) - cy0;
+    ci.sy[yy] = Per<PM>::Y ? 1.f : (Yc < 0 ? p.sy0 : (Yc >= cny ? p.sy1 : 1.f));
+    ci.row[yy] = (Per<PM>::Y ? Yc : (Yc < 0 ? 0 : (Yc >= cny ? cny - 1 : Yc))) - cy0;
   }
   return ci;
 }
 
 // The 3 x 4 coarse values of a staged plane S (sz: the ghost sign of a plane
-// outside a non-periodic level), ghosts applied.
-template <bool PER, int CX>
-__device__ __forceinline__ Coarse12 xy_read(const float* S, const CoarseIdx<PER>& ci, int tr,
-                                            int tp, float sz) {
+// outside a level with z walls, else 1), ghosts applied.
+template <int PM, int CX>
+__device__ __forceinline__ Coarse12 xy_read(const float* S, const CoarseIdx& ci, int tr, int tp,
+                                            float sz) {
   Coarse12 r;
-  if (PER) {
+  if (Per<PM>::X && Per<PM>::Y) {
     const float* b = S + tp * CX + 1 + 2 * tr;
 #pragma unroll
     for (int yy = 0; yy < 3; ++yy)
 #pragma unroll
-      for (int a = 0; a < 4; ++a) r.c[yy][a] = b[yy * CX + a];
+      for (int a = 0; a < 4; ++a) r.c[yy][a] = Per<PM>::Z ? b[yy * CX + a] : sz * b[yy * CX + a];
   } else {
 #pragma unroll
     for (int yy = 0; yy < 3; ++yy)
@@ -395,7 +415,7 @@ struct Shape {
 // (0: exactly NT); threads tid >= Shape::NT of a larger CTA take part in the
 // barriers only.  Element offsets are 32-bit: levels have fewer than 2^32
 // cells (fused_ok).
-template <int MODE, bool ZERO, bool PER, int TX, int TY, int HYO = 0, bool PAD = true,
+template <int MODE, bool ZERO, int PM, int TX, int TY, int HYO = 0, bool PAD = true,
           int NTB = 0>
 __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, const float* f,
                                            const float* ec, float* fc,
@@ -424,15 +444,16 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   const int z1 = min(z0 + p.cz, p.nz);
   const int gx4 = x0 - 4 + 4 * tr;   // x of the patch's first cell (may be outside)
   const int gyA = y0 - HY + 2 * tp;  // even row of the patch (may be outside)
-  const bool in_col = (gx4 >= 0 && gx4 < p.nx) && (gyA >= 0 && gyA < p.ny);
-  const int gx4w = PER ? wrap(gx4, p.nx) : gx4;
-  const int gyAw = PER ? wrap(gyA, p.ny) : gyA;
-  const bool col_ok = PER || in_col;  // the patch holds real cells
+  constexpr bool PX = Per<PM>::X, PY = Per<PM>::Y, PZ = Per<PM>::Z;
+  const int gx4w = PX ? wrap(gx4, p.nx) : gx4;
+  const int gyAw = PY ? wrap(gyA, p.ny) : gyA;
+  // the patch holds real cells
+  const bool col_ok = (PX || (gx4 >= 0 && gx4 < p.nx)) && (PY || (gyA >= 0 && gyA < p.ny));
   Flags fl;
-  fl.xlo = !PER && gx4 == 0;
-  fl.xhi = !PER && gx4 + 3 == p.nx - 1;
-  fl.ylo = !PER && gyA == 0;
-  fl.yhi = !PER && gyA + 1 == p.ny - 1;
+  fl.xlo = !PX && gx4 == 0;
+  fl.xhi = !PX && gx4 + 3 == p.nx - 1;
+  fl.ylo = !PY && gyA == 0;
+  fl.yhi = !PY && gyA + 1 == p.ny - 1;
   const bool out = tr >= 1 && tr <= TX / 4 && tp >= HY / 2 && tp < HY / 2 + TY / 2;
   const unsigned plane = (unsigned)p.nx * (unsigned)p.ny;
   const unsigned offA = col_ok ? (unsigned)gyAw * p.nx + gx4w : 0u;  // row a; row b is nx further
@@ -449,15 +470,15 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     constexpr int SU = decltype(SUc)::value, SF = decltype(SFc)::value;
     if (act && qu <= q_last) {
       if (!ZERO) {
-        const bool in = col_ok && (PER || (qu >= 0 && qu < p.nz));
-        const unsigned o = (unsigned)(PER ? wrap(qu, p.nz) : (in ? qu : 0)) * plane + offA;
+        const bool in = col_ok && (PZ || (qu >= 0 && qu < p.nz));
+        const unsigned o = (unsigned)(PZ ? wrap(qu, p.nz) : (in ? qu : 0)) * plane + offA;
         float4* d = &s_u[SU * PL];
         cp_async16(&d[ia], u_in + o, in ? 16 : 0);
         cp_async16(&d[ib], u_in + (o + p.nx), in ? 16 : 0);
       }
       const int qf = qu - 1;
-      const bool inf = col_ok && (PER || (qf >= 0 && qf < p.nz));
-      const unsigned o = (unsigned)(PER ? wrap(qf, p.nz) : (inf ? qf : 0)) * plane + offA;
+      const bool inf = col_ok && (PZ || (qf >= 0 && qf < p.nz));
+      const unsigned o = (unsigned)(PZ ? wrap(qf, p.nz) : (inf ? qf : 0)) * plane + offA;
       float4* d = &s_f[SF * PL];
       cp_async16(&d[ia], f + o, inf ? 16 : 0);
       cp_async16(&d[ib], f + (o + p.nx), inf ? 16 : 0);
@@ -474,19 +495,19 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       const int i = t / CW, j = t - i * CW;
       int X = cx0 + 4 * j, Y = cy0 + i, K = Kc;
       bool in = true;
-      if (PER) {
-        X = wrap(X, cnx); Y = wrap(Y, cny); K = wrap(K, cnz);
-      } else {
-        in = X >= 0 && X < cnx && Y >= 0 && Y < cny;
-        K = K < 0 ? 0 : (K >= cnz ? cnz - 1 : K);
-        if (!in) { X = 0; Y = 0; }
-      }
+      if (PX) X = wrap(X, cnx);
+      else in = X >= 0 && X < cnx;
+      if (PY) Y = wrap(Y, cny);
+      else in = in && Y >= 0 && Y < cny;
+      if (PZ) K = wrap(K, cnz);
+      else K = K < 0 ? 0 : (K >= cnz ? cnz - 1 : K);
+      if (!in) { X = 0; Y = 0; }
       cp_async16(s_c + SL * S_::CX * S_::CY + i * S_::CX + 4 * j,
                  ec + (((unsigned)K * cny + Y) * cnx + X), in ? 16 : 0);
     }
   };
   auto plane_sign = [&](int Kc) {
-    return (!PER && (Kc < 0 || Kc >= (p.nz >> 1))) ? p.s : 1.f;
+    return PZ ? 1.f : (Kc < 0 ? p.sz0 : (Kc >= (p.nz >> 1) ? p.sz1 : 1.f));
   };
 
   Patch r1 = zero_patch(), r2 = r1, r3 = r1, r4 = r1, f2p = r1, f3p = r1;
@@ -501,9 +522,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   // slot (K+1) mod 2, whose copy was issued two steps earlier; plane K+2 is
   // then copied into slot K mod 2.
   Patch W[2];
-  CoarseIdx<PER> ci;
+  CoarseIdx ci;
   if (MODE == kUp) {
-    if (!PER) ci = coarse_idx<PER>(p, gx4, gyA, cx0, cy0);
+    if (!(PX && PY)) ci = coarse_idx<PM>(p, gx4, gyA, cx0, cy0);
     // q_first = z0 - 2 with z0 a multiple of 8: K0 = q_first / 2 is odd
     const int K0 = q_first >> 1;
     copy_coarse(std::integral_constant<int, 0>{}, K0 - 1);
@@ -511,8 +532,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    W[0] = xy_combine(xy_read<PER, S_::CX>(s_c, ci, tr, tp, plane_sign(K0 - 1)));
-    W[1] = xy_combine(xy_read<PER, S_::CX>(s_c + S_::CX * S_::CY, ci, tr, tp, plane_sign(K0)));
+    W[0] = xy_combine(xy_read<PM, S_::CX>(s_c, ci, tr, tp, plane_sign(K0 - 1)));
+    W[1] = xy_combine(xy_read<PM, S_::CX>(s_c + S_::CX * S_::CY, ci, tr, tp, plane_sign(K0)));
     __syncthreads();
     copy_coarse(std::integral_constant<int, 0>{}, K0 + 1);  // committed with plane q_first
   }
@@ -543,9 +564,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       constexpr int KP = (QP >> 1) & 1;  // parity of K = floor(q / 2)
       const int K = q >> 1;
       if (QP & 1)
-        W[1 - KP] = xy_combine(xy_read<PER, S_::CX>(s_c + (1 - KP) * S_::CX * S_::CY, ci, tr, tp,
-                                                     plane_sign(K + 1)));
-      if (col_ok && (PER || (q >= 0 && q < p.nz))) {
+        W[1 - KP] = xy_combine(xy_read<PM, S_::CX>(s_c + (1 - KP) * S_::CX * S_::CY, ci, tr, tp,
+                                                    plane_sign(K + 1)));
+      if (col_ok && (PZ || (q >= 0 && q < p.nz))) {
         const float2 w0 = make_float2(0.75f, 0.75f), w1 = make_float2(0.25f, 0.25f);
         const Patch& PK = W[KP];
         const Patch& PN = W[1 - KP];
@@ -566,7 +587,7 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     // e cells when the plane is even
     {
       const int pz = q - 1;
-      const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+      const bool zlo = !PZ && pz == 0, zhi = !PZ && pz == p.nz - 1;
       if (q > q_first) {
         if (ZERO) {
           // every neighbour of a red cell is still 0
@@ -579,7 +600,7 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
             r1.b.e = __fmul2_rn(cf2, f1.b.e);
           }
         } else {
-          sor_pairs<PER, ZP_RED == 0>(r1, &s_ub[ZP_RED * PL2], pa, pb, offL, offR, offU2, offD2,
+          sor_pairs<PM, ZP_RED == 0>(r1, &s_ub[ZP_RED * PL2], pa, pb, offL, offR, offU2, offD2,
                                       r2, r0, f1, p, fl, zlo, zhi);
         }
       }
@@ -591,10 +612,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     // [C] black half-step on plane q-2 (red values of planes q-3 .. q-1)
     {
       const int pz = q - 2;
-      const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+      const bool zlo = !PZ && pz == 0, zhi = !PZ && pz == p.nz - 1;
       float2 dblk = make_float2(0.f, 0.f);
       if (q > q_first + 1)
-        sor_pairs<PER, ZP_BLK != 0, SPLIT>(r2, &s_red[ZP_BLK * PL2], pa, pb, offL, offR, offU2,
+        sor_pairs<PM, ZP_BLK != 0, SPLIT>(r2, &s_red[ZP_BLK * PL2], pa, pb, offL, offR, offU2,
                                            offD2, r3, r1, f2p, p, fl, zlo, zhi, &dblk);
       if (SPLIT && act && out && pz >= z0 && pz < z1) {
         // black defects of plane q-2 open (even plane) or join its coarse plane's sum
@@ -617,9 +638,9 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     if (MODE == kDown) {
       const int pz = q - 3;
       if (act && pz >= z0 && pz < z1 && out) {
-        const bool zlo = !PER && pz == 0, zhi = !PER && pz == p.nz - 1;
+        const bool zlo = !PZ && pz == 0, zhi = !PZ && pz == p.nz - 1;
         constexpr int ZA = ((QP + 1) % 4) >> 1;  // parity of the coarse plane (q-3)/2
-        accz[ZA] = add2(accz[ZA], defect_red<PER, ZP_DEF == 0>(r3, &s_finp[ZP_DEF * PL2], pa, pb,
+        accz[ZA] = add2(accz[ZA], defect_red<PM, ZP_DEF == 0>(r3, &s_finp[ZP_DEF * PL2], pa, pb,
                                                                RS2, r4, r2, f3p, p, fl, zlo, zhi));
         if (ZP_DEF != 0) {
           const unsigned cnx = (unsigned)p.nx >> 1, cny = (unsigned)p.ny >> 1;
@@ -660,13 +681,13 @@ constexpr int fused_max_regs() {
   return TY == 16 ? (MODE == kUp ? 96 : 128) : 168;
 }
 
-template <int MODE, bool ZERO, bool PER, int TX, int TY>
+template <int MODE, bool ZERO, int PM, int TX, int TY>
 __global__ void __maxnreg__((fused_max_regs<MODE, TY>()))
     k_fused(const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
             const float* __restrict__ ec, float* __restrict__ fc, FusedParams p) {
   extern __shared__ float4 smem[];
-  fused_tile<MODE, ZERO, PER, TX, TY>(u_in, u_out, f, ec, fc, p, blockIdx.x, blockIdx.y, blockIdx.z,
-                                      smem);
+  fused_tile<MODE, ZERO, PM, TX, TY>(u_in, u_out, f, ec, fc, p, blockIdx.x, blockIdx.y, blockIdx.z,
+                                     smem);
 }
 
 }  // namespace fused

@@ -415,7 +415,7 @@ void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool ze
   if constexpr (std::is_same<T, float>::value) {
     // the fused up leg synthesises the coarse correction's ghosts with the
     // level's own rule, so it serves levels whose coarse rule is the same
-    if (c->u32b[l] && mg::fused_ok(g, bc_top) && hom.kind == bc_top.kind) {
+    if (c->u32b[l] && mg::fused_ok(g, bc_top) && hom.kind == bc_top.kind && hom.fk == bc_top.fk) {
       vcycle_fused(c, l, bc_top, hom, zero_guess, s);
       return;
     }
@@ -1019,7 +1019,11 @@ void autotune(mg_ctx* c, cudaStream_t s) {
   cudaDeviceProp prop;
   check(c, cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
   const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr, c->face_mask});
-  const int periodic = hom.kind == mg::BC_PERIODIC ? 1 : 0;
+  // the kernels' periodic axes: 1 all, 3 x and y (slab), 0 none
+  int periodic = hom.kind == mg::BC_PERIODIC ? 1 : 0;
+  if (hom.kind == mg::BC_MIXED && mg::face_kind(hom, 0) == mg::BC_PERIODIC &&
+      mg::face_kind(hom, 2) == mg::BC_PERIODIC)
+    periodic = 3;
   const double om = c->opts.omega;
   const int F = c->L - 1;
   const int reps = 5;
