@@ -251,12 +251,20 @@ __global__ void k_fx_correct(long long* __restrict__ phi, const float* __restric
   if (bad) atomicOr(flag, 1);
 }
 
+// The rule on the integer grid.  A MIXED rule (kinds per face in fk, as in
+// Bc) takes its fixed faces' values from the face array like OPEN, or 0
+// where there is none (the homogeneous rule).
 struct FxBc {
   int kind;
-  long long b2;          // FIXED: 2 round(b 2^S)
-  const double* faces;   // OPEN: boundary values (doubles), scaled by c2 = 2^(S+1)
+  int fk;                // MIXED: bits 2q..2q+1 the kind of face q
+  long long b2;          // FIXED: round(2 b 2^S)
+  const double* faces;   // OPEN / MIXED: boundary values (doubles), scaled by c2 = 2^(S+1)
   double c2;
 };
+
+__device__ __forceinline__ int fx_face_kind(const FxBc& bc, int face) {
+  return bc.kind == BC_MIXED ? (bc.fk >> (2 * face)) & 3 : bc.kind;
+}
 
 // One outer step on the integer grid, fused and z-marching:
 //   PHI' = PHI_in + round(e * c)          (the pending FP32 correction; e may be
@@ -273,11 +281,13 @@ struct FxBc {
 constexpr int FX_TX = 32, FX_TY = 16, FX_W = FX_TX + 2, FX_H = FX_TY + 2;
 constexpr int FX_HALO = 2 * FX_W + 2 * FX_TY;  // 100
 
+// The ghost across face (axis, hi) of a non-periodic axis.
 __device__ __forceinline__ long long fx_face_ghost(const FxBc& bc, const Grid& g, long long self,
                                                    int i, int j, int k, int axis, int hi) {
-  if (bc.kind == BC_ZEROGRAD) return self;
+  if (fx_face_kind(bc, 2 * axis + hi) == BC_ZEROGRAD) return self;
   long long b2 = bc.b2;
-  if (bc.kind == BC_OPEN) {
+  if (bc.kind == BC_MIXED && !bc.faces) b2 = 0;
+  if ((bc.kind == BC_OPEN || bc.kind == BC_MIXED) && bc.faces) {
     size_t off;
     const size_t fx = (size_t)(g.ny + 2) * (g.nz + 2), fy = (size_t)(g.nx + 2) * (g.nz + 2),
                  fz = (size_t)(g.nx + 2) * (g.ny + 2);
@@ -289,35 +299,21 @@ __device__ __forceinline__ long long fx_face_ghost(const FxBc& bc, const Grid& g
   return b2 - self;
 }
 
-// The rule on the integer grid for the finishing pass.
-struct FxBcLite {
-  int kind;
-  long long b2;          // FIXED: round(2 b 2^S)
-  const double* faces;   // OPEN: face values, times c2 = 2^(S+1)
-  double c2;
-};
-
 // Integer neighbour along `axis` (side hi) of cell (i, j, k) holding `self`:
 // the stored value inside the grid, else the rule's ghost.
-__device__ __forceinline__ long long fx_nb_lite(const long long* __restrict__ q,
-                                                const FxBcLite& bc, const Grid& g,
-                                                long long self, bool inside, long long o, int i,
-                                                int j, int k, int axis, int hi) {
+__device__ __forceinline__ long long fx_nb_lite(const long long* __restrict__ q, const FxBc& bc,
+                                                const Grid& g, long long self, bool inside,
+                                                long long o, int i, int j, int k, int axis,
+                                                int hi) {
   if (inside) return q[o];
-  if (bc.kind == BC_PERIODIC) {
+  if (fx_face_kind(bc, 2 * axis + hi) == BC_PERIODIC) {
     const long long sy = g.nx, sz = (long long)g.nx * g.ny;
     const long long t = ((long long)k * g.ny + j) * g.nx + i;
     if (axis == 0) return q[hi ? t - (g.nx - 1) : t + (g.nx - 1)];
     if (axis == 1) return q[hi ? t - (long long)(g.ny - 1) * sy : t + (long long)(g.ny - 1) * sy];
     return q[hi ? t - (long long)(g.nz - 1) * sz : t + (long long)(g.nz - 1) * sz];
   }
-  if (bc.kind == BC_ZEROGRAD) return self;
-  FxBc full;
-  full.kind = bc.kind;
-  full.b2 = bc.b2;
-  full.faces = bc.faces;
-  full.c2 = bc.c2;
-  return fx_face_ghost(full, g, self, i, j, k, axis, hi);
+  return fx_face_ghost(bc, g, self, i, j, k, axis, hi);
 }
 
 // PHI' at flat offset o.
@@ -364,7 +360,8 @@ struct FxRing {
 };
 constexpr size_t kFxSmem = sizeof(FxRing);
 
-template <bool PER, bool ZERO_IN>
+// PM: the periodic axes (bit 0 x, 1 y, 2 z).
+template <int PM, bool ZERO_IN>
 __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     k_fx_step(const long long* __restrict__ phi_in, long long* __restrict__ phi_out,
               const float* __restrict__ e, float c, const long long* __restrict__ F,
@@ -392,14 +389,13 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     else if (h < 2 * FX_W + FX_TY) { ha = 0; hb = h - 2 * FX_W + 1; }
     else { ha = FX_W - 1; hb = h - 2 * FX_W - FX_TY + 1; }
   }
+  constexpr bool PX = (PM & 1) != 0, PY = (PM & 2) != 0, PZ = (PM & 4) != 0;
   int hx = x0 - 1 + ha, hy = y0 - 1 + hb;
   bool h_in = halo;
-  if (PER) {
-    hx = hx < 0 ? hx + g.nx : (hx >= g.nx ? hx - g.nx : hx);
-    hy = hy < 0 ? hy + g.ny : (hy >= g.ny ? hy - g.ny : hy);
-  } else {
-    h_in = h_in && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
-  }
+  if (PX) hx = hx < 0 ? hx + g.nx : (hx >= g.nx ? hx - g.nx : hx);
+  else h_in = h_in && hx >= 0 && hx < g.nx;
+  if (PY) hy = hy < 0 ? hy + g.ny : (hy >= g.ny ? hy - g.ny : hy);
+  else h_in = h_in && hy >= 0 && hy < g.ny;
   const unsigned hcol = h_in ? (unsigned)hy * g.nx + hx : 0u;
   // Ring slot of plane q is (q - z0 + 1) mod 4; the z-march below is unrolled
   // by four, so every slot (and the plane buffer of P) is a compile-time
@@ -407,8 +403,8 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
   auto issue = [&](auto SLc, int q) {
     constexpr int sl = decltype(SLc)::value;
     if (q <= z1) {
-      const bool in = PER || (q >= 0 && q < g.nz);
-      const int qw = PER ? (q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q)) : (in ? q : 0);
+      const bool in = PZ || (q >= 0 && q < g.nz);
+      const int qw = PZ ? (q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q)) : (in ? q : 0);
       const unsigned o = (unsigned)qw * plane + col;
       if (!ZERO_IN) cp_async8(&ring.p[sl][tid], phi_in + o, in ? 8 : 0);
       cp_async4(&ring.e[sl][tid], e + o, in ? 4 : 0);
@@ -466,11 +462,15 @@ __global__ void __launch_bounds__(FX_TX* FX_TY, 3)
     long long xm = P[buf][ty + 1][tx], xp = P[buf][ty + 1][tx + 2];
     long long ym = P[buf][ty][tx + 1], yp = P[buf][ty + 2][tx + 1];
     long long zmv = zm, zpv = zp;
-    if (!PER) {
+    if (!PX) {
       if (i == 0) xm = fx_face_ghost(bc, g, self, i, j, z, 0, 0);
       if (i == g.nx - 1) xp = fx_face_ghost(bc, g, self, i, j, z, 0, 1);
+    }
+    if (!PY) {
       if (j == 0) ym = fx_face_ghost(bc, g, self, i, j, z, 1, 0);
       if (j == g.ny - 1) yp = fx_face_ghost(bc, g, self, i, j, z, 1, 1);
+    }
+    if (!PZ) {
       if (z == 0) zmv = fx_face_ghost(bc, g, self, i, j, z, 2, 0);
       if (z == g.nz - 1) zpv = fx_face_ghost(bc, g, self, i, j, z, 2, 1);
     }
@@ -578,7 +578,7 @@ __global__ void k_finish_fx_sum(const long long* __restrict__ psum, int nb, int 
 // -(PHI_{i+1} - PHI_{i-1}) rounded once and scaled by 2^-S / (2 h).
 // Writes phi (as doubles, into a different buffer than q) and g = [gx|gy|gz].
 __global__ void k_fx_finish_gravity(const long long* __restrict__ q, double* __restrict__ phi,
-                                    double* __restrict__ g, Grid gr, FxBcLite bc, int S,
+                                    double* __restrict__ g, Grid gr, FxBc bc, int S,
                                     double cg, const long long* __restrict__ mean) {
   const long long M = mean ? mean[0] : 0;
   const long long N = gr.cells();
@@ -735,16 +735,35 @@ int fx_step_blocks(Grid g, int cz) {
   return (int)(cols * ((g.nz + z - 1) / z));
 }
 
+namespace {
+
+FxBc fx_bc(const Bc& bc, double two_pow_S) {
+  FxBc b;
+  b.kind = bc.kind;
+  b.fk = bc.fk;
+  b.c2 = 2.0 * two_pow_S;
+  b.b2 = bc.kind == BC_FIXED ? (long long)std::llrint(bc.value * b.c2) : 0;
+  b.faces = bc.faces;
+  return b;
+}
+
+int fx_periodic_mask(const Bc& bc) {
+  int m = 0;
+  for (int a = 0; a < 3; ++a)
+    if (face_kind(bc, 2 * a) == BC_PERIODIC) m |= 1 << a;
+  return m;
+}
+
+}  // namespace
+
 cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const float* e, float c,
                            const long long* F, float* r32, Grid g, const Bc& bc, double two_pow_S,
                            float factor, double* partials, int nb_max, int* flag, int* nb_out,
                            cudaStream_t s, int cz_req, long long* psum) {
   // The ghost 2 b - phi on the fixed-point grid: 2 b 2^S rounded once.
-  FxBc b;
-  b.kind = bc.kind;
-  b.c2 = 2.0 * two_pow_S;
-  b.b2 = bc.kind == BC_FIXED ? (long long)std::llrint(bc.value * b.c2) : 0;
-  b.faces = bc.faces;
+  const FxBc b = fx_bc(bc, two_pow_S);
+  const int pm = fx_periodic_mask(bc);
+  if (pm != 0 && pm != 3 && pm != 7) return cudaErrorInvalidValue;
   if (cz_req != 0 && cz_req < kFxMinCz) return cudaErrorInvalidValue;
   const int cz = fx_step_cz(g, cz_req);
   dim3 grid(g.nx / FX_TX, g.ny / FX_TY, (g.nz + cz - 1) / cz);
@@ -752,21 +771,22 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   if (nb > nb_max) return cudaErrorInvalidValue;
   *nb_out = nb;
   ++g_launches;
-  const bool per = bc.kind == BC_PERIODIC, zero_in = phi_in == nullptr;
+  const bool zero_in = phi_in == nullptr;
   static std::atomic<int> configured[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev].load()) {
-    for (auto kf : {k_fx_step<true, true>, k_fx_step<true, false>, k_fx_step<false, true>,
-                    k_fx_step<false, false>}) {
+    for (auto kf : {k_fx_step<7, true>, k_fx_step<7, false>, k_fx_step<3, true>,
+                    k_fx_step<3, false>, k_fx_step<0, true>, k_fx_step<0, false>}) {
       const cudaError_t e2 =
           cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFxSmem);
       if (e2 != cudaSuccess) return e2;
     }
     configured[dev].store(1);
   }
-  auto kf = per ? (zero_in ? k_fx_step<true, true> : k_fx_step<true, false>)
-                : (zero_in ? k_fx_step<false, true> : k_fx_step<false, false>);
+  auto kf = pm == 7 ? (zero_in ? k_fx_step<7, true> : k_fx_step<7, false>)
+            : pm == 3 ? (zero_in ? k_fx_step<3, true> : k_fx_step<3, false>)
+                      : (zero_in ? k_fx_step<0, true> : k_fx_step<0, false>);
   kf<<<grid, FX_TX * FX_TY, kFxSmem, s>>>(phi_in, phi_out, e, c, F, r32, g, b, factor, cz,
                                           partials, psum, flag);
   return cudaGetLastError();
@@ -776,11 +796,7 @@ cudaError_t launch_fx_finish_gravity(const long long* q, double* phi, double* g,
                                      const Bc& bc, double h, int S, const long long* mean,
                                      cudaStream_t s) {
   const double two_pow_S = std::ldexp(1.0, S);
-  FxBcLite b;
-  b.kind = bc.kind;
-  b.c2 = 2.0 * two_pow_S;
-  b.b2 = bc.kind == BC_FIXED ? (long long)std::llrint(bc.value * b.c2) : 0;
-  b.faces = bc.faces;
+  const FxBc b = fx_bc(bc, two_pow_S);
   ++g_launches;
   k_fx_finish_gravity<<<grid_for(gr.cells()), kThreads, 0, s>>>(
       q, phi, g, gr, b, S, 1.0 / (2.0 * h * two_pow_S), mean);

@@ -186,10 +186,16 @@ void alloc_hierarchy(mg_ctx* c) {
     if (face_arrays) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
   }
   c->partials_cap = mg::kPartials;
-  // the fixed-point outer step synthesises one rule per grid: a rule per face
-  // takes the FP64 outer residual
-  if (o.prec == MG_MIXED && o.outer_fixed && bc != MG_BC_MIXED &&
-      mg::fx_step_ok(level_grid(c, F))) {
+  // the fixed-point outer step has kernels for no periodic axis, x and y, or
+  // all three; a rule per face with other periodic axes takes the FP64 outer
+  // residual
+  bool fx_rule = true;
+  if (bc == MG_BC_MIXED) {
+    const bool px = (c->face_mask & 3) == MG_BC_PERIODIC, py = ((c->face_mask >> 4) & 3) == MG_BC_PERIODIC,
+               pz = ((c->face_mask >> 8) & 3) == MG_BC_PERIODIC;
+    fx_rule = !pz && px == py;
+  }
+  if (o.prec == MG_MIXED && o.outer_fixed && fx_rule && mg::fx_step_ok(level_grid(c, F))) {
     c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
     const int nb = mg::fx_step_blocks(level_grid(c, F), 0);
     if (nb > c->partials_cap) c->partials_cap = nb;
