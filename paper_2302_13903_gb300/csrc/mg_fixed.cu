@@ -168,16 +168,31 @@ __global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
                             double2* __restrict__ copy) {
   ExactSum acc;
   unsigned long long m = 0;
-#pragma unroll 4
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
-       t += (long long)gridDim.x * blockDim.x) {
-    const double2 r = rho[t];
-    if (copy) copy[t] = r;
+  auto take = [&](const double2 r) {
     exact_add(acc, r.x);
     exact_add(acc, r.y);
     const unsigned long long a = abs_bits(r.x), b = abs_bits(r.y);
     m = a > m ? a : m;
     m = b > m ? b : m;
+  };
+  // four loads in flight before the (branchy) exact adds use them; the same
+  // order of values per thread as one at a time
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < n2; t += 4 * stride) {
+    double2 r[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] = rho[t + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (copy) copy[t + k * stride] = r[k];
+      take(r[k]);
+    }
+  }
+  for (; t < n2; t += stride) {
+    const double2 r = rho[t];
+    if (copy) copy[t] = r;
+    take(r);
   }
   const double bs = block_reduce<false>(exact_value(acc));
   const double bm = block_reduce<true>(__longlong_as_double((long long)m));
