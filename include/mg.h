@@ -434,10 +434,11 @@ typedef struct {
   mg_bc bc;
   double fixed_value;    /* boundary value b of MG_BC_FIXED */
   int lmax;              /* multipole order 0..4 of MG_BC_OPEN */
-  const double *rho;     /* FP64 device array, nx*ny*nz, caller-owned */
+  const double *rho;     /* FP64 array, nx*ny*nz, caller-owned: device memory, or */
+                         /* host memory (then phi is host memory too)            */
   double four_pi_G;
   double tol;            /* ||d||/||f|| target of this request */
-  double *phi;           /* FP64 device array written with the result */
+  double *phi;           /* FP64 array written with the result, in the same memory as rho */
 } mg_request;
 
 typedef struct {
@@ -465,8 +466,12 @@ mg_status mg_server_create(size_t hbm_budget_bytes, int slots, int max_queue,
                            const mg_opts *opts, mg_server **server);
 
 /* Queue one request; *ticket names it.  rho and phi must stay valid and phi
- * untouched by the caller until the request is done.  Errors: MG_ERR_ARG
- * (invalid request), MG_ERR_OOM (its hierarchy alone exceeds the budget),
+ * untouched by the caller until the request is done.  With host arrays the
+ * slot copies rho in and phi out on its own stream by the copy engines (the
+ * other slots keep computing meanwhile; page-locked buffers move fastest) and
+ * the request's hierarchy holds device copies of both (counted in the
+ * budget).  Errors: MG_ERR_ARG (invalid request, or rho and phi in different
+ * memories), MG_ERR_OOM (its hierarchy alone exceeds the budget),
  * MG_ERR_BUSY (the queue is full; nothing was queued). */
 mg_status mg_server_submit(mg_server *server, const mg_request *request, long long *ticket);
 

@@ -226,6 +226,13 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+def _any_ptr(t):
+    """Address of a contiguous float64 torch tensor on the device or the host."""
+    import torch
+    assert t.is_contiguous() and t.dtype == torch.float64, "expected contiguous float64"
+    return t.data_ptr()
+
+
 def _dptr(t, dtype=None):
     import torch
     if t is None:
@@ -612,12 +619,13 @@ class Server:
 
     def submit(self, rho, phi, dx=None, bc=PERIODIC, four_pi_G=1.0, tol=1e-10, lmax=4,
                fixed_value=0.0):
-        """rho, phi: CUDA float64 (n, n, n) tensors kept alive until done.
+        """rho, phi: float64 (n, n, n) tensors kept alive until done, both on the
+        device or both in host memory (pinned host tensors move fastest).
         Returns the ticket, or raises MGError (MG_ERR_BUSY when the queue is full)."""
         import torch
         n = rho.shape[0]
         q = Request(n, n, n, 1.0 / n if dx is None else dx, bc, fixed_value, lmax,
-                    _dptr(rho, torch.float64), four_pi_G, tol, _dptr(phi, torch.float64))
+                    _any_ptr(rho), four_pi_G, tol, _any_ptr(phi))
         t = ctypes.c_longlong(0)
         st = lib().mg_server_submit(self.ptr, ctypes.byref(q), ctypes.byref(t))
         if st != 0:

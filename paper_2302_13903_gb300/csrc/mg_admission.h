@@ -24,9 +24,10 @@ namespace admission {
 struct Key {
   int n = 0, bc = 0, lmax = 0;
   double dx = 0.0, fixed_value = 0.0;
+  bool host = false;  // requests with host buffers: the hierarchy holds device copies too
   bool operator==(const Key& o) const {
     return n == o.n && bc == o.bc && lmax == o.lmax && dx == o.dx &&
-           fixed_value == o.fixed_value;
+           fixed_value == o.fixed_value && host == o.host;
   }
 };
 

@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <string>
 
+#include "../../include/mg.h"
+
 namespace mg {
 
 enum BcKind : int { BC_PERIODIC = 0, BC_FIXED = 1, BC_ZEROGRAD = 2, BC_OPEN = 3, BC_MIXED = 4 };
@@ -55,6 +57,15 @@ inline size_t faces_count(const Grid& g) {
   return 2 * (size_t)(g.ny + 2) * (g.nz + 2) + 2 * (size_t)(g.nx + 2) * (g.nz + 2) +
          2 * (size_t)(g.nx + 2) * (g.ny + 2);
 }
+
+// mg_solve with rho and phi in host memory moved by copies on `s` (the copy
+// engines) into the context's own device arrays and back, so that the SMs stay
+// free for solves on other streams while the bytes cross the host link (the
+// serving loop); mg_solve_host instead lets the solve's first and last passes
+// read and write page-locked host memory themselves.
+mg_status solve_host_copies(mg_ctx* c, const double* rho, double four_pi_G, double tol,
+                            double* phi, double* hist, int hist_cap, int* n_hist,
+                            cudaStream_t s);
 
 // Launch counter (per thread: a context is not thread-safe, so the driver
 // resets and reads it around one solve on one thread).

@@ -10,7 +10,9 @@
 // its convergence scalars every outer iteration), the others keep launching,
 // so the kernels of different requests overlap on the device.  Every result
 // is the one the same request gives alone: each hierarchy is used by one
-// request at a time, and a solve is deterministic given its inputs.
+// request at a time, and a solve is deterministic given its inputs.  A
+// request with host buffers has its rho and phi moved by the copy engines on
+// its slot's stream, so its transfers overlap the other slots' solves.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -26,6 +28,7 @@
 
 #include "../../include/mg.h"
 #include "mg_admission.h"
+#include "mg_internal.h"
 
 namespace {
 
@@ -57,6 +60,17 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 }
 
 bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+
+// 0: device (or managed) memory, 1: host memory, page-locked or not; -1: unknown.
+int memory_space(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
+  return 1;
+}
 
 }  // namespace
 
@@ -134,8 +148,12 @@ void run_worker(mg_server* S) {
       else S->pool.drop(dec.id);
       lk.unlock();
     }
+    if (st == MG_OK && dec.act == Act::CREATE) mg_ctx_autotune(ctx, stream);  // shapes, cached
     int nh = 0;
-    if (st == MG_OK)
+    if (st == MG_OK && r->key.host)
+      st = mg::solve_host_copies(ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi,
+                                 r->hist, kHistCap, &nh, stream);
+    else if (st == MG_OK)
       st = mg_solve(ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi, r->hist, kHistCap,
                     &nh, stream);
     const Clock::time_point t_done = Clock::now();
@@ -234,6 +252,16 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
     S->err = "mg_server_submit: invalid request";
     return MG_ERR_ARG;
   }
+  // rho and phi both in device memory, or both in host memory (page-locked
+  // or not); then the hierarchy also keeps device copies of the two arrays
+  const int rs = memory_space(q->rho), ps = memory_space(q->phi);
+  if (rs < 0 || rs != ps) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->err = "mg_server_submit: rho and phi must both be device arrays or both host arrays";
+    return MG_ERR_ARG;
+  }
+  const bool host = rs == 1;
+  if (host) need += 2 * sizeof(double) * (size_t)q->nx * q->ny * q->nz;
   Request* r = new Request;
   r->req = *q;
   r->key.n = q->nx;
@@ -241,6 +269,7 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
   r->key.lmax = q->bc == MG_BC_OPEN ? q->lmax : 0;
   r->key.dx = q->dx;
   r->key.fixed_value = q->bc == MG_BC_FIXED ? q->fixed_value : 0.0;
+  r->key.host = host;
   r->need = need;
   std::lock_guard<std::mutex> lk(S->mu);
   if (need > S->pool.budget()) {

@@ -1455,6 +1455,37 @@ size_t mg_faces_count(int nx, int ny, int nz) { return mg::faces_count(Grid{nx, 
 
 }  // extern "C"
 
+namespace mg {
+
+mg_status solve_host_copies(mg_ctx* c, const double* rho, double four_pi_G, double tol,
+                            double* phi, double* hist, int hist_cap, int* n_hist,
+                            cudaStream_t s) {
+  if (!c || !rho || !phi) return MG_ERR_ARG;
+  const size_t bytes = (size_t)level_grid(c, c->L - 1).cells() * sizeof(double);
+  try {
+    check(c, cudaSetDevice(c->device), "cudaSetDevice");
+    if (!c->rho_dev_own) c->rho_dev_own = dalloc<double>(c, bytes / sizeof(double));
+    if (!c->phi_dev_own) c->phi_dev_own = dalloc<double>(c, bytes / sizeof(double));
+    check(c, cudaMemcpyAsync(c->rho_dev_own, rho, bytes, cudaMemcpyHostToDevice, s), "H2D rho");
+    if (!c->opts.mode_fmg)
+      check(c, cudaMemcpyAsync(c->phi_dev_own, phi, bytes, cudaMemcpyHostToDevice, s), "H2D phi");
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  const mg_status st =
+      mg_solve(c, c->rho_dev_own, four_pi_G, tol, c->phi_dev_own, hist, hist_cap, n_hist, s);
+  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+  try {
+    check(c, cudaMemcpyAsync(phi, c->phi_dev_own, bytes, cudaMemcpyDeviceToHost, s), "D2H phi");
+    check(c, cudaStreamSynchronize(s), "sync");
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  return st;
+}
+
+}  // namespace mg
+
 namespace {
 
 bool op_args_ok(int prec, int nx, int ny, int nz, int bc, const double* faces) {

@@ -108,3 +108,35 @@ def test_server_refusals_and_ticket_lifecycle():
             s.poll(taken[0][0])
         for _, p in taken[1:]:
             assert torch.equal(p, taken[0][1])
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_server_host_buffers_equal_device_buffers(pinned):
+    """Requests with host rho and phi (copied in and out by the slot's stream)
+    give the bits of the same requests on device arrays, several at once."""
+    mix = [(64, mg.PERIODIC, 0, 1e-10), (32, mg.OPEN, 4, 1e-9), (64, mg.FIXED, 0, 1e-10),
+           (32, mg.ZEROGRAD, 0, 1e-10)]
+    rhos = sources(mix, seed=31)
+    dev = [solve_alone(r, n, bc, lmax, tol) for r, (n, bc, lmax, tol) in zip(rhos, mix)]
+    host_rho = [r.cpu() for r in rhos]
+    if pinned:
+        host_rho = [r.pin_memory() for r in host_rho]
+    phis = [torch.full_like(r, float("nan")) for r in host_rho]
+    if pinned:
+        phis = [p.pin_memory() for p in phis]
+    with mg.Server(1 << 34, slots=3, max_queue=16) as s:
+        tickets = [s.submit(r, p, bc=bc, tol=tol, lmax=lmax)
+                   for r, p, (n, bc, lmax, tol) in zip(host_rho, phis, mix)]
+        results = [s.wait(t, 120) for t in tickets]
+    for k, ((res, hist), (pd, hd)) in enumerate(zip(results, dev)):
+        assert res.done and res.status == 0, (k, res.status)
+        assert torch.equal(phis[k], pd.cpu()), k
+        assert np.array_equal(hist, hd), k
+
+
+def test_server_refuses_mixed_memory():
+    rho = torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda")
+    phi = torch.zeros((16, 16, 16), dtype=torch.float64)
+    with mg.Server(1 << 30, slots=1) as s:
+        with pytest.raises(mg.MGError):
+            s.submit(rho, phi)
