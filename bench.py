@@ -69,6 +69,24 @@ KERNEL_SOURCES = {
 }
 
 
+NOMINAL_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of the part, for context
+
+
+def mixed_solve_bytes_per_cell(outer: int, inner: int) -> float:
+    """Algorithmic bytes per finest cell of one mixed solve: per outer iteration
+    `inner` FP32 V(1,1) cycles (the first from a zero correction: its down leg
+    reads f only, 2w + w/8; the others 3w + w/8; every up leg 3w + w/8; coarse
+    levels add 1/7 of the zero-start legs' bytes) and one fixed-point outer step
+    (32 B); plus the passes around the loop: rho read three times (mean and
+    maximum, first residual, integer h^2 f), r32 and the integer f written, e
+    read once for its maximum, phi converted back (read and write): 56 B."""
+    w = 4.0
+    leg0, leg = 2 * w + w / 8, 3 * w + w / 8
+    finest = (leg0 + leg) + (inner - 1) * (2 * leg)
+    coarse = inner * (leg0 + leg) / 7.0
+    return outer * (finest + coarse + 32.0) + 56.0
+
+
 def src_sha(kernel: str = None) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2302_13903_gb300", "csrc")
@@ -334,7 +352,7 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512)
@@ -396,18 +414,19 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     launches = 0
-    ev0.record(stream)
-    for _ in range(args.steps):
+    evs[0].record(stream)
+    for q in range(args.steps):
         _, hist, st = solver.solve(rho, 1.0, TOL, phi=phi, stream=stream)
         assert st == 0, (st, hist)
         launches += solver.last_launches
-    ev1.record(stream)
+        evs[q + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[q].elapsed_time(evs[q + 1]) for q in range(args.steps)]
     # the same K solves again with CUDA events around every finest-level
     # launch (kernel durations for the roofline; the launches go one by one)
     solver.set_timing(True)
@@ -435,7 +454,19 @@ def main():
     traffic = ncu_traffic(dom, prec_tag, n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom}_{prec_tag}",
-                "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg}
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    # the whole solve against the same roofline, and its V-cycle rate
+    whole = None
+    if prec == mg.MIXED:
+        inner = 1 + solver.opts.inner_cycles
+        b_cell = mixed_solve_bytes_per_cell(cycles, inner)
+        whole = {"algorithmic_bytes_per_cell": b_cell,
+                 "achieved_gbs": b_cell * n ** 3 / (ms_per_step * 1e-3) / 1e9,
+                 "v_cycles": cycles * inner,
+                 "cell_v_cycles_per_s": n ** 3 * cycles * inner / (ms_per_step * 1e-3)}
+        whole["frac"] = whole["achieved_gbs"] / peak
+        whole["frac_of_nominal"] = whole["achieved_gbs"] / NOMINAL_HBM_GBS
 
     # end to end through the host API: pinned host rho/phi, copies inside the timed region
     e2e = None
@@ -527,7 +558,8 @@ def main():
         torch.cuda.synchronize()
         t64 = a.elapsed_time(b) / args.fp64_steps
         fp64 = {"value": n ** 3 / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
-                "cycles": len(h64), "status": st}
+                "cycles": len(h64), "status": st,
+                "cell_v_cycles_per_s_after_fmg": n ** 3 * (len(h64) - 1) / (t64 * 1e-3)}
         s64.close()
     else:
         solver.close()
@@ -560,6 +592,8 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "ms_per_step_median": statistics.median(step_ms),
+            "whole_solve_roofline": whole,
             "gpu_launches": launches,
             "clocks": clk,
             "residual_checks_per_solve": cycles,
