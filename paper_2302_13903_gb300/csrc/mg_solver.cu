@@ -1470,15 +1470,20 @@ mg_status solve_host_copies(mg_ctx* c, const double* rho, double four_pi_G, doub
     if (!c->opts.mode_fmg)
       check(c, cudaMemcpyAsync(c->phi_dev_own, phi, bytes, cudaMemcpyHostToDevice, s), "H2D phi");
   } catch (const Fail& f) {
+    cudaStreamSynchronize(s);
     return f.st;
   }
   const mg_status st =
       mg_solve(c, c->rho_dev_own, four_pi_G, tol, c->phi_dev_own, hist, hist_cap, n_hist, s);
-  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) {
+    cudaStreamSynchronize(s);  // nothing of this request stays in flight on the context
+    return st;
+  }
   try {
     check(c, cudaMemcpyAsync(phi, c->phi_dev_own, bytes, cudaMemcpyDeviceToHost, s), "D2H phi");
     check(c, cudaStreamSynchronize(s), "sync");
   } catch (const Fail& f) {
+    cudaStreamSynchronize(s);
     return f.st;
   }
   return st;
