@@ -185,9 +185,21 @@ def oracle_solve_timed(n: int, threads: int):
 def cpu_baseline(n_sample: int):
     threads = os.cpu_count() or 1
     dt, cycles = oracle_solve_timed(n_sample, threads)
+    # the same recipe on one core, at half the size (an eighth of the cells)
+    n1 = max(n_sample // 2, 8)
+    dt1, cycles1 = oracle_solve_timed(n1, 1)
+    oracle_threads(threads)
     return {"value": n_sample ** 3 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"one oracle solve of the same recipe at {n_sample}^3 (64 blobs, seed {SEED}), "
-                      f"FMG + V(1,1) to 1e-10 ({cycles} residual checks), {dt:.2f} s wall"}
+                      f"FMG + V(1,1) to 1e-10 ({cycles} residual checks), {dt:.2f} s wall",
+            "single_core": {"value": n1 ** 3 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"one oracle solve at {n1}^3 ({cycles1} residual checks), "
+                                      f"{dt1:.2f} s"}}
+
+
+def oracle_threads(threads: int):
+    import oracle
+    oracle.set_num_threads(threads)
 
 
 def run_reference(args, ws, rank):
