@@ -165,3 +165,35 @@ def test_host_buffers_with_face_rules():
         host, hh, st = s.solve_host(rho.copy(), 1.0, 1e-10)
     assert st == 0
     assert np.array_equal(np.asarray(host), dev.cpu().numpy()) and np.array_equal(hd, hh)
+
+
+@pytest.mark.parametrize("case", ["slab", "box"])
+@pytest.mark.parametrize("pre,post", [(2, 2), (0, 2), (2, 0)])
+def test_mixed_smoothing_counts_with_face_rules(case, pre, post):
+    """V(M,N) variants run the fused legs' extra smoothing kernel (and the
+    per-level kernels where a leg has no smoothing step) with the face rules;
+    the outer loop still reaches the oracle's converged solution."""
+    n = 64
+    rho = source((n, n, n), case, seed=5 + pre + 3 * post)
+    ref = oracle_solve(rho, case, tol=0.0, max_cycles=80)
+    phi, hist, st = gpu_solve(rho, case, 1e-10, prec=mg.MIXED, pre=pre, post=post,
+                              max_cycles=60)
+    assert st == 0 and hist[-1] < 1e-10, (st, hist)
+    assert emax(phi, ref.phi) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
+def test_initial_guess_with_face_rules(prec):
+    """MGI mode (Sec. 2.3.7): phi_dev holds the initial guess; a perturbed
+    converged solution converges back to it."""
+    n, case = 64, "slab"
+    kinds, values = CASES[case]
+    rho = source((n, n, n), case, seed=61)
+    ref = oracle_solve(rho, case, tol=0.0, max_cycles=80)
+    guess = ref.phi + 1e-3 * np.sin(np.arange(n ** 3).reshape(n, n, n))
+    with mg.Solver(n, 1.0 / n, list(kinds), face_values=list(values), prec=prec,
+                   mode_fmg=0) as s:
+        phi = torch.from_numpy(np.ascontiguousarray(guess)).cuda()
+        phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-10, phi=phi)
+    assert st == 0 and hist[-1] < 1e-10, (st, hist)
+    assert emax(phi.cpu().numpy(), ref.phi) <= 1e-9
