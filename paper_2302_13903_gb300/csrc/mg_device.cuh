@@ -268,6 +268,72 @@ __device__ __forceinline__ void prolong_range(const T* uc, T* uf, Grid gf, Bc bc
   }
 }
 
+// The same prolongation over z-chunks of coarse columns: thread work item t
+// is coarse column (I, J) = t mod (nx_c ny_c) and chunk t / (nx_c ny_c) of cz
+// coarse planes.  The (x, y) interpolation of each coarse plane is formed
+// once and kept in registers for the three pairs of fine planes that use it;
+// every fine value takes the same operations in the same order as in
+// prolong_range (x, then y, then z), so the results are the same bits.
+template <typename T, bool HIGH>
+__device__ __forceinline__ void xy_interp(const T* uc, const Grid& gc, const Bc& bc, int I, int J,
+                                          int K, T out[2][2]) {
+  T c[3][3];
+  if (I > 0 && I < gc.nx - 1 && J > 0 && J < gc.ny - 1 && K >= 0 && K < gc.nz) {
+    const size_t sy = (size_t)gc.nx, o = at(gc, I, J, K);
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) c[cy][cx] = uc[o + (cy - 1) * sy + (cx - 1)];
+  } else {
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) c[cy][cx] = fetch(uc, I + cx - 1, J + cy - 1, K, gc, bc);
+  }
+  T vx[3][2];
+#pragma unroll
+  for (int cy = 0; cy < 3; ++cy)
+    interp1<T, HIGH>(c[cy][0], c[cy][1], c[cy][2], vx[cy][0], vx[cy][1]);
+#pragma unroll
+  for (int px = 0; px < 2; ++px)
+    interp1<T, HIGH>(vx[0][px], vx[1][px], vx[2][px], out[0][px], out[1][px]);
+}
+
+template <typename T, bool HIGH>
+__device__ __forceinline__ void prolong_zchunk(const T* uc, T* uf, const Grid& gf, const Bc& bc,
+                                               int add, long long t, int cz) {
+  const Grid gc{gf.nx / 2, gf.ny / 2, gf.nz / 2};
+  const long long cols = (long long)gc.nx * gc.ny;
+  const int ch = (int)(t / cols);
+  const int col = (int)(t - (long long)ch * cols);
+  const int J = col / gc.nx, I = col - J * gc.nx;
+  const int K0 = ch * cz, K1 = min(K0 + cz, gc.nz);
+  T pm[2][2], p0[2][2], pp[2][2];
+  xy_interp<T, HIGH>(uc, gc, bc, I, J, K0 - 1, pm);
+  xy_interp<T, HIGH>(uc, gc, bc, I, J, K0, p0);
+  const size_t plane = (size_t)gf.nx * gf.ny;
+  for (int K = K0; K < K1; ++K) {
+    xy_interp<T, HIGH>(uc, gc, bc, I, J, K + 1, pp);
+#pragma unroll
+    for (int py = 0; py < 2; ++py)
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        T lo, hi;
+        interp1<T, HIGH>(pm[py][px], p0[py][px], pp[py][px], lo, hi);
+        const size_t q0 = at(gf, 2 * I + px, 2 * J + py, 2 * K), q1 = q0 + plane;
+        uf[q0] = add ? uf[q0] + lo : lo;
+        uf[q1] = add ? uf[q1] + hi : hi;
+      }
+#pragma unroll
+    for (int py = 0; py < 2; ++py)
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        pm[py][px] = p0[py][px];
+        p0[py][px] = pp[py][px];
+      }
+  }
+}
+
 // COARSEST on a single cell: a ghost is 2 b_face - u on a fixed / open face
 // and u itself on a periodic / zero-gradient one, so with a such faces
 // sum(ghosts) - 6u = 2 sum(b) - 2 a u = h^2 f; with none it is singular.

@@ -103,9 +103,10 @@ __global__ void k_restrict(const T* uf, T* uc, Grid gf) {
 }
 
 template <typename T, bool HIGH>
-__global__ void k_prolong(const T* uc, T* uf, Grid gf, Bc bc, int add) {
-  dev::prolong_range<T, HIGH>(uc, uf, gf, bc, add, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                              (long long)gridDim.x * blockDim.x);
+__global__ void k_prolong(const T* uc, T* uf, Grid gf, Bc bc, int add, int cz, long long items) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < items;
+       t += (long long)gridDim.x * blockDim.x)
+    dev::prolong_zchunk<T, HIGH>(uc, uf, gf, bc, add, t, cz);
 }
 
 template <typename T>
@@ -297,11 +298,17 @@ template <typename T>
 cudaError_t launch_prolong(const T* uc, T* uf, Grid gf, Bc bc_coarse, int high_order, int add,
                            cudaStream_t s) {
   ++g_launches;
-  const long long work = gf.cells() / 8;
+  // z-chunks of coarse columns: 8 planes each while that leaves about 2^18
+  // work items (enough threads for the device), fewer on small levels
+  const long long cols = (long long)(gf.nx / 2) * (gf.ny / 2);
+  const int cnz = gf.nz / 2;
+  int cz = 8;
+  while (cz > 1 && cols * ((cnz + cz - 1) / cz) < (1LL << 18)) cz /= 2;
+  const long long items = cols * ((cnz + cz - 1) / cz);
   if (high_order)
-    k_prolong<T, true><<<grid_for(work), kThreads, 0, s>>>(uc, uf, gf, bc_coarse, add);
+    k_prolong<T, true><<<grid_for(items), kThreads, 0, s>>>(uc, uf, gf, bc_coarse, add, cz, items);
   else
-    k_prolong<T, false><<<grid_for(work), kThreads, 0, s>>>(uc, uf, gf, bc_coarse, add);
+    k_prolong<T, false><<<grid_for(items), kThreads, 0, s>>>(uc, uf, gf, bc_coarse, add, cz, items);
   return cudaGetLastError();
 }
 
