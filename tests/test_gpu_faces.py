@@ -197,3 +197,16 @@ def test_initial_guess_with_face_rules(prec):
         phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-10, phi=phi)
     assert st == 0 and hist[-1] < 1e-10, (st, hist)
     assert emax(phi.cpu().numpy(), ref.phi) <= 1e-9
+
+
+@pytest.mark.parametrize("case", ["slab", "box", "wall"])
+def test_mixed_box_with_face_rules(case):
+    """A 64 x 64 x 32 box (x, y, z): its finest level runs the fused legs with
+    the face rules on a grid shorter in z; the coarsest level has several cells."""
+    shape = (32, 64, 64)  # (nz, ny, nx)
+    rho = source(shape, case, seed=91)
+    ref = oracle_solve(rho, case, tol=0.0, max_cycles=80)
+    assert ref.ok
+    phi, hist, st = gpu_solve(rho, case, 1e-10, prec=mg.MIXED, max_cycles=60)
+    assert st == 0 and hist[-1] < 1e-10, (st, hist)
+    assert emax(phi, ref.phi) <= 1e-9
