@@ -719,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
           a.fmg = 0;
           bottom::set_coefficients(a);
           const bool zg = (top < g.L - 1) || (P.cycle == 0 && c.inner_zero);
-          bottom::vcycle(a, top, a.hom, zg);
+          bottom::vcycle<float, false>(a, top, a.hom, zg);
           break;
         }
         case PH_DOWN:

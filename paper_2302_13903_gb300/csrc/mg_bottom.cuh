@@ -48,26 +48,35 @@ __host__ __device__ inline void set_coefficients(BottomArgs<T>& a) {
 // shifts, and a neighbour outside the level is the periodic wrap, the cell
 // itself (zero gradient) or minus the cell (zero fixed) -- the ghost of
 // Sec. 2.3.6 for a zero boundary value, with no branch to a general routine.
+// KIND is one rule for every face, or BC_MIXED: each face's kind from the
+// mask fk of the homogeneous rule (bits 2q..2q+1 for face q).
+
+template <int KIND>
+__device__ __forceinline__ int hkind(int fk, int face) {
+  return KIND == BC_MIXED ? (fk >> (2 * face)) & 3 : KIND;
+}
 
 template <typename T, int KIND>
 __device__ __forceinline__ T hnb(const T* u, int c, bool inside, int off_in, int off_wrap,
-                                 T self) {
+                                 T self, int fk, int face) {
   if (inside) return u[c + off_in];
-  if (KIND == BC_PERIODIC) return u[c + off_wrap];
-  return KIND == BC_ZEROGRAD ? self : -self;
+  const int kind = hkind<KIND>(fk, face);
+  if (kind == BC_PERIODIC) return u[c + off_wrap];
+  return kind == BC_ZEROGRAD ? self : -self;
 }
 
 // Sum of the six neighbours of cell c = (i, j, k), in the order x-, x+, y-,
 // y+, z-, z+.
 template <typename T, int KIND>
-__device__ __forceinline__ T hsum(const T* u, int c, int i, int j, int k, int n, T self) {
+__device__ __forceinline__ T hsum(const T* u, int c, int i, int j, int k, int n, T self,
+                                  int fk) {
   const int sy = n, sz = n * n, w = n - 1;
-  T s = hnb<T, KIND>(u, c, i > 0, -1, w, self);
-  s += hnb<T, KIND>(u, c, i < w, 1, -w, self);
-  s += hnb<T, KIND>(u, c, j > 0, -sy, w * sy, self);
-  s += hnb<T, KIND>(u, c, j < w, sy, -w * sy, self);
-  s += hnb<T, KIND>(u, c, k > 0, -sz, w * sz, self);
-  s += hnb<T, KIND>(u, c, k < w, sz, -w * sz, self);
+  T s = hnb<T, KIND>(u, c, i > 0, -1, w, self, fk, 0);
+  s += hnb<T, KIND>(u, c, i < w, 1, -w, self, fk, 1);
+  s += hnb<T, KIND>(u, c, j > 0, -sy, w * sy, self, fk, 2);
+  s += hnb<T, KIND>(u, c, j < w, sy, -w * sy, self, fk, 3);
+  s += hnb<T, KIND>(u, c, k > 0, -sz, w * sz, self, fk, 4);
+  s += hnb<T, KIND>(u, c, k < w, sz, -w * sz, self, fk, 5);
   return s;
 }
 
@@ -94,7 +103,7 @@ __device__ void h_smooth(const BottomArgs<T>& a, int l, int steps, bool zero_gue
         const int i = 2 * (t & ((n >> 1) - 1)) + ((j + k) & 1);
         const int c = (r << lg) + i;
         const T self = u[c];
-        u[c] = cu * self + cs * hsum<T, KIND>(u, c, i, j, k, n, self) + cf * f[c];
+        u[c] = cu * self + cs * hsum<T, KIND>(u, c, i, j, k, n, self, a.hom.fk) + cf * f[c];
       }
     }
     __syncthreads();
@@ -103,7 +112,7 @@ __device__ void h_smooth(const BottomArgs<T>& a, int l, int steps, bool zero_gue
       const int i = 2 * (t & ((n >> 1) - 1)) + ((j + k + 1) & 1);
       const int c = (r << lg) + i;
       const T self = u[c];
-      u[c] = cu * self + cs * hsum<T, KIND>(u, c, i, j, k, n, self) + cf * f[c];
+      u[c] = cu * self + cs * hsum<T, KIND>(u, c, i, j, k, n, self, a.hom.fk) + cf * f[c];
     }
     __syncthreads();
   }
@@ -126,28 +135,30 @@ __device__ void h_defect_restrict(const BottomArgs<T>& a, int l) {
           const int i = 2 * I + ax, j = 2 * J + by, k = 2 * K + cz;
           const int c = (k * n + j) * n + i;
           const T self = u[c];
-          acc += f[c] - (hsum<T, KIND>(u, c, i, j, k, n, self) - T(6) * self) * ih2;
+          acc += f[c] - (hsum<T, KIND>(u, c, i, j, k, n, self, a.hom.fk) - T(6) * self) * ih2;
         }
     fc[t] = acc * T(0.125);
   }
 }
 
 // Coarse value at (I, J, K) with up to one cell outside on each axis: wrap,
-// or the nearest cell times +1 (zero gradient) / -1 per axis left (zero fixed).
+// or the nearest cell times +1 (zero gradient) / -1 per axis left (zero fixed),
+// by the rule of the face that was crossed.
 template <typename T, int KIND>
-__device__ __forceinline__ T hcoarse(const T* uc, int I, int J, int K, int nc) {
+__device__ __forceinline__ T hcoarse(const T* uc, int I, int J, int K, int nc, int fk) {
   T sg = T(1);
-  auto fix = [&](int& q) {
+  auto fix = [&](int& q, int axis) {
     if (q >= 0 && q < nc) return;
-    if (KIND == BC_PERIODIC) q = q < 0 ? q + nc : q - nc;
+    const int kind = hkind<KIND>(fk, 2 * axis + (q < 0 ? 0 : 1));
+    if (kind == BC_PERIODIC) q = q < 0 ? q + nc : q - nc;
     else {
       q = q < 0 ? 0 : nc - 1;
-      if (KIND != BC_ZEROGRAD) sg = -sg;
+      if (kind != BC_ZEROGRAD) sg = -sg;
     }
   };
-  fix(I);
-  fix(J);
-  fix(K);
+  fix(I, 0);
+  fix(J, 1);
+  fix(K, 2);
   return sg * uc[(K * nc + J) * nc + I];
 }
 
@@ -166,7 +177,7 @@ __device__ void h_prolong_add(const BottomArgs<T>& a, int l) {
       for (int cy = 0; cy < 3; ++cy)
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx)
-          c[cz][cy][cx] = hcoarse<T, KIND>(uc, I + cx - 1, J + cy - 1, K + cz - 1, nc);
+          c[cz][cy][cx] = hcoarse<T, KIND>(uc, I + cx - 1, J + cy - 1, K + cz - 1, nc, a.hom.fk);
     T vx[3][3][2];
 #pragma unroll
     for (int cz = 0; cz < 3; ++cz)
@@ -232,14 +243,21 @@ __device__ void smooth_level(const BottomArgs<T>& a, int l, const Bc& bc, int st
   }
 }
 
-// One V-cycle on levels top .. 0 with rule bc_top on level `top`.
-template <typename T>
+// One V-cycle on levels top .. 0 with rule bc_top on level `top`.  PER_FACE:
+// whether a rule per face (homogeneous, the same on every level) takes the
+// fast cycle too (the batched solver has one rule per grid).
+template <typename T, bool PER_FACE = true>
 __device__ void vcycle(const BottomArgs<T>& a, int top, const Bc& bc_top, bool zero_guess) {
   if (bc_top.kind == a.hom.kind && bc_top.value == 0.0 && bc_top.kind != BC_OPEN &&
       bc_top.kind != BC_MIXED) {
     if (a.hom.kind == BC_PERIODIC) h_vcycle<T, BC_PERIODIC>(a, top, zero_guess);
     else if (a.hom.kind == BC_ZEROGRAD) h_vcycle<T, BC_ZEROGRAD>(a, top, zero_guess);
     else h_vcycle<T, BC_FIXED>(a, top, zero_guess);
+    return;
+  }
+  if (PER_FACE && bc_top.kind == BC_MIXED && a.hom.kind == BC_MIXED && !bc_top.faces &&
+      !a.hom.faces && bc_top.fk == a.hom.fk) {
+    h_vcycle<T, BC_MIXED>(a, top, zero_guess);
     return;
   }
   for (int l = top; l >= 1; --l) {
