@@ -130,11 +130,10 @@ mg_status mg_create(int nx, int ny, int nz, double dx, mg_bc bc, const mg_opts *
  * face's homogeneous rule (opts->coarse_literal: zero fixed on zero-gradient
  * faces too).  Six equal rules (and, if fixed, equal values) give the
  * context mg_create gives for that rule; otherwise the context's rule is
- * MG_BC_MIXED.  Its levels run with the face rules in their ghost synthesis;
- * the fused FP32 legs and MG_MIXED's exact fixed-point outer step have
- * kernels for grids periodic along no axis or along x and y only (a slab with
- * walls in z); other combinations run the per-level FP32 kernels and the FP64
- * outer residual.  Other arguments and errors as mg_create. */
+ * MG_BC_MIXED.  Its levels run with the face rules in their ghost synthesis
+ * (the fused FP32 legs, the single-CTA coarse levels and MG_MIXED's exact
+ * fixed-point outer step for any combination of periodic axes).  Other
+ * arguments and errors as mg_create. */
 mg_status mg_create_faces(int nx, int ny, int nz, double dx, const mg_bc *face_bc,
                           const double *face_value, const mg_opts *opts, mg_ctx **ctx);
 

@@ -778,7 +778,6 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   // The ghost 2 b - phi on the fixed-point grid: 2 b 2^S rounded once.
   const FxBc b = fx_bc(bc, two_pow_S);
   const int pm = fx_periodic_mask(bc);
-  if (pm != 0 && pm != 3 && pm != 7) return cudaErrorInvalidValue;
   if (cz_req != 0 && cz_req < kFxMinCz) return cudaErrorInvalidValue;
   const int cz = fx_step_cz(g, cz_req);
   dim3 grid(g.nx / FX_TX, g.ny / FX_TY, (g.nz + cz - 1) / cz);
@@ -790,18 +789,24 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   static std::atomic<int> configured[64];
   int dev = 0;
   cudaGetDevice(&dev);
+  // the step's kernels by periodic-axis mask (0..7) and zero start
+  using Kf = void (*)(const long long*, long long*, const float*, float, const long long*,
+                      float*, Grid, FxBc, float, int, double*, long long*, int*);
+  static const Kf kfs[8][2] = {
+      {k_fx_step<0, false>, k_fx_step<0, true>}, {k_fx_step<1, false>, k_fx_step<1, true>},
+      {k_fx_step<2, false>, k_fx_step<2, true>}, {k_fx_step<3, false>, k_fx_step<3, true>},
+      {k_fx_step<4, false>, k_fx_step<4, true>}, {k_fx_step<5, false>, k_fx_step<5, true>},
+      {k_fx_step<6, false>, k_fx_step<6, true>}, {k_fx_step<7, false>, k_fx_step<7, true>}};
   if (dev >= 0 && dev < 64 && !configured[dev].load()) {
-    for (auto kf : {k_fx_step<7, true>, k_fx_step<7, false>, k_fx_step<3, true>,
-                    k_fx_step<3, false>, k_fx_step<0, true>, k_fx_step<0, false>}) {
-      const cudaError_t e2 =
-          cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFxSmem);
-      if (e2 != cudaSuccess) return e2;
-    }
+    for (const auto& pair : kfs)
+      for (Kf kf : pair) {
+        const cudaError_t e2 =
+            cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFxSmem);
+        if (e2 != cudaSuccess) return e2;
+      }
     configured[dev].store(1);
   }
-  auto kf = pm == 7 ? (zero_in ? k_fx_step<7, true> : k_fx_step<7, false>)
-            : pm == 3 ? (zero_in ? k_fx_step<3, true> : k_fx_step<3, false>)
-                      : (zero_in ? k_fx_step<0, true> : k_fx_step<0, false>);
+  const Kf kf = kfs[pm][zero_in ? 1 : 0];
   kf<<<grid, FX_TX * FX_TY, kFxSmem, s>>>(phi_in, phi_out, e, c, F, r32, g, b, factor, cz,
                                           partials, psum, flag);
   return cudaGetLastError();

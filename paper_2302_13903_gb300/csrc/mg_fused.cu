@@ -2,55 +2,11 @@
 // programs themselves are in mg_fused.cuh).
 #include <cuda_runtime.h>
 
-#include <atomic>
-
-#include "mg_fused.cuh"
-#include "mg_internal.h"
+#include "mg_fused_launch.cuh"
 
 namespace mg {
 namespace fused {
 namespace {
-
-template <int MODE, bool ZERO, int PM, int TX, int TY>
-cudaError_t launch_t(const float* ui, float* uo, const float* f, const float* ec, float* fc,
-                     const FusedParams& p, cudaStream_t s) {
-  using S_ = Shape<MODE, TX, TY>;
-  static std::atomic<int> configured[64];  // zero-initialised (static storage)
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !configured[dev].load()) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused<MODE, ZERO, PM, TX, TY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S_::SMEM);
-    if (e != cudaSuccess) return e;
-    configured[dev].store(1);
-  }
-  dim3 grid(p.nx / TX, p.ny / TY, (p.nz + p.cz - 1) / p.cz);
-  ++g_launches;
-  k_fused<MODE, ZERO, PM, TX, TY><<<grid, S_::NT, S_::SMEM, s>>>(ui, uo, f, ec, fc, p);
-  return cudaGetLastError();
-}
-
-// Built-in shape: tiles of 64 x 16 for levels >= 64 cells wide, 32 x 16 for
-// 32 (32 rows when asked); the z-chunk is the largest of 64, 32, 16, 8 planes that still gives two
-// CTAs per SM.  A nonzero cfg field (checked by fused_cfg_ok) replaces it.
-template <int MODE, bool ZERO, int PM>
-cudaError_t dispatch_t(const float* ui, float* uo, const float* f, const float* ec, float* fc,
-                       FusedParams p, TileCfg cfg, cudaStream_t s) {
-  const long long sms = 152;
-  const int tx = cfg.tx ? cfg.tx : (p.nx >= 64 ? 64 : 32), ty = cfg.ty ? cfg.ty : 16;
-  const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
-  int cz = 64;
-  while (cz > 8 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
-  if (cfg.cz) cz = cfg.cz;
-  p.cz = cz < p.nz ? cz : p.nz;
-  if (ty == 32) {
-    if (tx == 64) return launch_t<MODE, ZERO, PM, 64, 32>(ui, uo, f, ec, fc, p, s);
-    return launch_t<MODE, ZERO, PM, 32, 32>(ui, uo, f, ec, fc, p, s);
-  }
-  if (tx == 64) return launch_t<MODE, ZERO, PM, 64, 16>(ui, uo, f, ec, fc, p, s);
-  return launch_t<MODE, ZERO, PM, 32, 16>(ui, uo, f, ec, fc, p, s);
-}
 
 // Periodic axes of a rule: bit 0 x, 1 y, 2 z.
 int periodic_mask(const Bc& bc) {
@@ -60,17 +16,17 @@ int periodic_mask(const Bc& bc) {
   return m;
 }
 
-// The masks with kernels: none, the x-y slab, all.
-bool mask_built(int pm) { return pm == 0 || pm == 3 || pm == 7; }
-
 template <int MODE, bool ZERO>
 cudaError_t dispatch(const float* ui, float* uo, const float* f, const float* ec, float* fc,
                      FusedParams p, const Bc& bc, TileCfg cfg, cudaStream_t s) {
-  switch (periodic_mask(bc)) {
+  const int pm = periodic_mask(bc);
+  switch (pm) {
     case 7: return dispatch_t<MODE, ZERO, 7>(ui, uo, f, ec, fc, p, cfg, s);
     case 3: return dispatch_t<MODE, ZERO, 3>(ui, uo, f, ec, fc, p, cfg, s);
     case 0: return dispatch_t<MODE, ZERO, 0>(ui, uo, f, ec, fc, p, cfg, s);
-    default: return cudaErrorInvalidValue;
+    case 5:
+    case 6: return dispatch_mask_56(pm, MODE, ZERO, ui, uo, f, ec, fc, p, cfg, s);
+    default: return dispatch_mask_124(pm, MODE, ZERO, ui, uo, f, ec, fc, p, cfg, s);
   }
 }
 
@@ -100,8 +56,8 @@ using fused::params;
 
 bool fused_ok(Grid g, const Bc& bc) {
   // homogeneous: no open face, fixed faces at 0 (a MIXED rule without face
-  // values); periodic axes none, x and y, or all
-  bool hom = bc.kind != BC_OPEN && fused::mask_built(fused::periodic_mask(bc));
+  // values); any periodic axes
+  bool hom = bc.kind != BC_OPEN;
   if (bc.kind == BC_FIXED) hom = hom && bc.value == 0.0;
   if (bc.kind == BC_MIXED) hom = hom && bc.faces == nullptr;
   // widths the 64- or 32-wide tiles divide, rows in 16s, planes in chunks of 8;

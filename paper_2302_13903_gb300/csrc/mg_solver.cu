@@ -186,16 +186,7 @@ void alloc_hierarchy(mg_ctx* c) {
     if (face_arrays) c->faces[F] = dalloc<double>(c, mg::faces_count(level_grid(c, F)));
   }
   c->partials_cap = mg::kPartials;
-  // the fixed-point outer step has kernels for no periodic axis, x and y, or
-  // all three; a rule per face with other periodic axes takes the FP64 outer
-  // residual
-  bool fx_rule = true;
-  if (bc == MG_BC_MIXED) {
-    const bool px = (c->face_mask & 3) == MG_BC_PERIODIC, py = ((c->face_mask >> 4) & 3) == MG_BC_PERIODIC,
-               pz = ((c->face_mask >> 8) & 3) == MG_BC_PERIODIC;
-    fx_rule = !pz && px == py;
-  }
-  if (o.prec == MG_MIXED && o.outer_fixed && fx_rule && mg::fx_step_ok(level_grid(c, F))) {
+  if (o.prec == MG_MIXED && o.outer_fixed && mg::fx_step_ok(level_grid(c, F))) {
     c->fxbuf = dalloc<long long>(c, level_grid(c, F).cells());
     const int nb = mg::fx_step_blocks(level_grid(c, F), 0);
     if (nb > c->partials_cap) c->partials_cap = nb;
@@ -1025,11 +1016,14 @@ void autotune(mg_ctx* c, cudaStream_t s) {
   cudaDeviceProp prop;
   check(c, cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
   const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr, c->face_mask});
-  // the kernels' periodic axes: 1 all, 3 x and y (slab), 0 none
+  // the kernels' periodic axes: 1 all (one rule), 0 none (one rule), 8 + the
+  // periodic-axis mask for a rule per face
   int periodic = hom.kind == mg::BC_PERIODIC ? 1 : 0;
-  if (hom.kind == mg::BC_MIXED && mg::face_kind(hom, 0) == mg::BC_PERIODIC &&
-      mg::face_kind(hom, 2) == mg::BC_PERIODIC)
-    periodic = 3;
+  if (hom.kind == mg::BC_MIXED) {
+    periodic = 8;
+    for (int a = 0; a < 3; ++a)
+      if (mg::face_kind(hom, 2 * a) == mg::BC_PERIODIC) periodic += 1 << a;
+  }
   const double om = c->opts.omega;
   const int F = c->L - 1;
   const int reps = 5;
