@@ -86,6 +86,11 @@ def lib():
             L.orc_multipole_potential.argtypes = [p, i, d, p, d, d, d]
             L.orc_open_faces.restype = None
             L.orc_open_faces.argtypes = [i, i, i, d, p, i, d, p, p]
+            L.orc_open_level_faces.restype = i
+            L.orc_open_level_faces.argtypes = [i, i, i, d, p, i, i, p, d, i, p]
+            L.orc_op_fx_step.restype = i
+            L.orc_op_fx_step.argtypes = [i, i, i, p, p, d, p, p, ctypes.c_float, p, p,
+                                         ctypes.c_float, p]
             L.orc_num_threads.restype = i
             L.orc_set_num_threads.argtypes = [i]
             _lib = L
@@ -238,6 +243,40 @@ def open_faces(nx, ny, nz, h, Q, lmax, G, origin):
     out = np.zeros(faces_size(nx, ny, nz))
     lib().orc_open_faces(nx, ny, nz, h, _ptr(Q), lmax, G, _ptr(org), _ptr(out))
     return out
+
+
+def open_level_faces(rho, h, level, lmax=4, use_com=True, origin=(0.0, 0.0, 0.0),
+                     four_pi_G=1.0):
+    """Face values of level `level` (0 = coarsest) of an open-boundary solve of
+    rho, as the solve sets them up (orc_open_level_faces)."""
+    rho = _f64(rho)
+    nz, ny, nx = rho.shape
+    nlev = int(min(nx, ny, nz)).bit_length()  # levels down to a shortest side of 1
+    shift = nlev - 1 - level
+    out = np.zeros(faces_size(nx >> shift, ny >> shift, nz >> shift))
+    org = _f64(origin)
+    st = lib().orc_open_level_faces(nx, ny, nz, h, _ptr(rho), lmax, int(use_com), _ptr(org),
+                                    four_pi_G, level, _ptr(out))
+    assert st == 0, st
+    return out
+
+
+def fx_step(phi_in, e, c, F, kinds, values, two_pow_S, factor):
+    """The exact integer defect of the fixed-point outer loop (orc_op_fx_step):
+    returns (phi' int64, r float32).  phi_in may be None (zero); e float32 or
+    None; F int64; kinds / values per face (x-, x+, y-, y+, z-, z+)."""
+    F = np.ascontiguousarray(F, dtype=np.int64)
+    nz, ny, nx = F.shape
+    pin = None if phi_in is None else np.ascontiguousarray(phi_in, dtype=np.int64)
+    e32 = None if e is None else np.ascontiguousarray(e, dtype=np.float32)
+    k = np.ascontiguousarray(kinds, dtype=np.int32)
+    b = _f64(values)
+    out = np.empty_like(F)
+    r = np.empty(F.shape, dtype=np.float32)
+    st = lib().orc_op_fx_step(nx, ny, nz, _ptr(k), _ptr(b), float(two_pow_S), _ptr(pin), _ptr(e32),
+                              float(c), _ptr(F), _ptr(out), float(factor), _ptr(r))
+    assert st == 0
+    return out, r
 
 
 def num_threads():

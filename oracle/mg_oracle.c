@@ -679,6 +679,45 @@ static int hier_set_bc(Hier *H, int kind, double value, const double *Q, int lma
   return ORC_OK;
 }
 
+/* The hierarchy of a solve with its physical rule on every level: for open
+ * boundaries the moments of rho (App. A) and each level's face values. */
+static int hier_with_rules(Hier *H, int nx, int ny, int nz, double h, int bc_kind,
+                           double bc_value, const double *given_faces, int lmax, int use_com,
+                           const double *origin_in, double four_pi_G, const double *rho,
+                           double *origin_out, double *Q_out) {
+  int st = hier_build(H, nx, ny, nz, h);
+  if (st != ORC_OK) return st;
+  const double pi = 3.14159265358979323846;
+  double origin[3] = {0.0, 0.0, 0.0};
+  double Q[25];
+  memset(Q, 0, sizeof Q);
+  if (origin_in) memcpy(origin, origin_in, sizeof origin);
+  if (bc_kind == BC_OPEN) orc_multipole_moments(nx, ny, nz, h, rho, lmax, use_com, origin, Q);
+  if (origin_out) memcpy(origin_out, origin, sizeof origin);
+  if (Q_out) memcpy(Q_out, Q, sizeof Q);
+  return hier_set_bc(H, bc_kind, bc_value, Q, lmax, four_pi_G / (4.0 * pi), origin, given_faces);
+}
+
+/* The face values an open-boundary solve of rho gives level `level` (0 the
+ * coarsest) of its hierarchy, exactly as orc_solve sets them up for the FMG
+ * ladder (Sec. 2.3.6: each level's own face points).  faces receives
+ * faces_total of that level. */
+int orc_open_level_faces(int nx, int ny, int nz, double h, const double *rho, int lmax,
+                         int use_com, const double *origin_in, double four_pi_G, int level,
+                         double *faces) {
+  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || h <= 0.0) return ORC_ERR_ARG;
+  Hier H;
+  int st = hier_with_rules(&H, nx, ny, nz, h, BC_OPEN, 0.0, NULL, lmax, use_com, origin_in,
+                           four_pi_G, rho, NULL, NULL);
+  if (st == ORC_OK && (level < 0 || level >= H.nlev)) st = ORC_ERR_ARG;
+  if (st == ORC_OK) {
+    const Level *L = &H.lev[level];
+    memcpy(faces, H.faces[level], faces_total(L->nx, L->ny, L->nz) * sizeof(double));
+  }
+  hier_free(&H);
+  return st;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Whole solve (Sec. 2.3.7): f = 4 pi G rho (mean removed where no boundary
  * fixes the zero point, Sec. 2.3.6), FMG or a given initial guess, then
@@ -696,20 +735,10 @@ int orc_solve(int nx, int ny, int nz, double h, int bc_kind, double bc_value,
   if (lmax < 0 || lmax > 4 || hist_cap < 1) return ORC_ERR_ARG;
   if (bc_kind == BC_FACES && (mode_fmg || cycle == CYCLE_FAS)) return ORC_ERR_ARG;
   Hier H;
-  int st = hier_build(&H, nx, ny, nz, h);
+  int st = hier_with_rules(&H, nx, ny, nz, h, bc_kind, bc_value, given_faces, lmax, use_com,
+                           origin_in, four_pi_G, rho, origin_out, Q_out);
   if (st != ORC_OK) { hier_free(&H); return st; }
   Level *F = &H.lev[H.nlev - 1];
-  const double pi = 3.14159265358979323846;
-
-  double origin[3] = {0.0, 0.0, 0.0};
-  double Q[25];
-  memset(Q, 0, sizeof Q);
-  if (origin_in) memcpy(origin, origin_in, sizeof origin);
-  if (bc_kind == BC_OPEN) orc_multipole_moments(nx, ny, nz, h, rho, lmax, use_com, origin, Q);
-  if (origin_out) memcpy(origin_out, origin, sizeof origin);
-  if (Q_out) memcpy(Q_out, Q, sizeof Q);
-  st = hier_set_bc(&H, bc_kind, bc_value, Q, lmax, four_pi_G / (4.0 * pi), origin, given_faces);
-  if (st != ORC_OK) { hier_free(&H); return st; }
   Bc hom = correction_rule(&H.bcs[0], coarse_literal);
 
   /* f = 4 pi G rho */
@@ -953,6 +982,60 @@ int orc_op_gravity(int nx, int ny, int nz, double h, int bc_kind, double bc_valu
         g[2 * N + t] = 0.5 * (zl + zr);
       }
   one_free(&o);
+  return ORC_OK;
+}
+
+/* The defect of Eq. (defect) on the integer grid of the mixed-precision
+ * outer loop (not in the paper: its defect-correction form keeps phi and h^2 f
+ * as 64-bit integers scaled by 2^S, so that the defect is exact):
+ *   P' = P + round(e c)          e c the FP32 product, rounded to the nearest
+ *                                integer (ties to even); P = 0 when p_in is NULL
+ *   R  = F - (sum of the six neighbours of P' - 6 P')   exactly, in integers
+ *   r  = fl32(R) * factor        (FP32)
+ * Neighbours outside the grid follow Sec. 2.3.6 face by face (kinds[q] for
+ * q = x-, x+, y-, y+, z-, z+): periodic wraps, zero gradient is the cell
+ * itself, fixed b_q is B_q - P' with B_q = round(2 b_q 2^S).  Where floating
+ * point decides an integer, both the rounding of e c and of 2 b_q 2^S, this
+ * takes the same decision in the same precision as the CUDA kernel it checks.
+ * Arrays are (nz, ny, nx) without ghosts; p_out receives P'. */
+int orc_op_fx_step(int nx, int ny, int nz, const int *kinds, const double *b, double two_pow_S,
+                   const long long *p_in, const float *e, float c, const long long *F,
+                   long long *p_out, float factor, float *r) {
+  const size_t N = (size_t)nx * ny * nz;
+  long long B[6];
+  for (int q = 0; q < 6; ++q) B[q] = llrint(b[q] * (2.0 * two_pow_S));
+  for (size_t t = 0; t < N; ++t) {
+    const float ec = e ? e[t] * c : 0.0f;
+    p_out[t] = (p_in ? p_in[t] : 0) + llrintf(ec);
+  }
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t t = ((size_t)k * ny + j) * nx + i;
+        const long long self = p_out[t];
+        const int idx[3] = {i, j, k}, n[3] = {nx, ny, nz};
+        long long sum = 0;
+        for (int a = 0; a < 3; ++a)
+          for (int side = 0; side < 2; ++side) {
+            const int q = 2 * a + side;
+            int m[3] = {i, j, k};
+            m[a] = idx[a] + (side ? 1 : -1);
+            long long v;
+            if (m[a] >= 0 && m[a] < n[a]) {
+              v = p_out[((size_t)m[2] * ny + m[1]) * nx + m[0]];
+            } else if (kinds[q] == BC_PERIODIC) {
+              m[a] = side ? 0 : n[a] - 1;
+              v = p_out[((size_t)m[2] * ny + m[1]) * nx + m[0]];
+            } else if (kinds[q] == BC_ZEROGRAD) {
+              v = self;
+            } else {
+              v = B[q] - self;
+            }
+            sum += v;
+          }
+        const long long R = F[t] - (sum - 6 * self);
+        r[t] = (float)R * factor;
+      }
   return ORC_OK;
 }
 

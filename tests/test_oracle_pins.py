@@ -812,3 +812,135 @@ def test_jeans_box_periodic_mode_is_exact(orc):
     r = orc.solve(rho, h, PERIODIC, tol=0.0, max_cycles=60)
     assert r.ok and len(r.hist) < 60
     assert emax(r.phi, rho / lam) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# The FMG ladder under non-periodic rules (Algorithm 2 with the physical rule
+# on every level, Sec. 2.3.6): one sweep must already be near the truncation
+# error, which a rule applied wrongly on the coarse FMG levels (a dropped
+# boundary value, the wrong rule, open-boundary values at the wrong points)
+# would spoil.
+
+def test_fmg_sweep_fixed_rule_with_boundary_value(orc):
+    """Fixed b = 0.7: phi = b + s / lambda_c for f = s = sin(pi x) sin(2 pi y)
+    sin(3 pi z), the continuum solution.  One FMG sweep is within 2x of the
+    converged error against it (which is the truncation error), at 32^3 and
+    64^3."""
+    k, b = (1, 2, 3), 0.7
+    for n in (32, 64):
+        h = 1.0 / n
+        x, y, z = grid(n)
+        s = np.sin(np.pi * k[0] * x) * np.sin(np.pi * k[1] * y) * np.sin(np.pi * k[2] * z)
+        exact = b + s / (-(math.pi ** 2) * sum(kk * kk for kk in k))
+        one = orc.solve(s, h, FIXED, bc_value=b, tol=0.0, max_cycles=0)
+        conv = orc.solve(s, h, FIXED, bc_value=b, tol=0.0, max_cycles=60)
+        assert len(one.hist) == 1 and conv.ok
+        e1, ec = np.abs(one.phi - exact).max(), np.abs(conv.phi - exact).max()
+        assert ec < 2e-4 / (n / 32) ** 2  # second order
+        assert e1 < 2.0 * ec, (n, e1, ec)
+
+
+def test_fmg_sweep_zero_gradient_rule(orc):
+    """Zero gradient, f = cos(2 pi x) cos(pi y) cos(3 pi z): the continuum
+    solution is f / lambda_c.  The zero-gradient cycle contracts by about 0.29
+    (against 0.1 for periodic), so one FMG sweep lands a few times above the
+    truncation error (2.5x at 32^3, 3.7x at 64^3) and FMG plus one V-cycle
+    within 1.1x of it."""
+    for n, bound in ((32, 3.0), (64, 4.5)):
+        h = 1.0 / n
+        x, y, z = grid(n)
+        c = np.cos(2 * np.pi * x) * np.cos(np.pi * y) * np.cos(3 * np.pi * z)
+        exact = c / (-(math.pi ** 2) * (4 + 1 + 9))
+        one = orc.solve(c, h, ZEROGRAD, tol=0.0, max_cycles=0)
+        two = orc.solve(c, h, ZEROGRAD, tol=0.0, max_cycles=1, stall_ratio=1e300)
+        conv = orc.solve(c, h, ZEROGRAD, tol=0.0, max_cycles=60)
+        e1, e2, ec = (np.abs(r.phi - exact).max() for r in (one, two, conv))
+        assert e1 < bound * ec, (n, e1, ec)
+        assert e2 < 1.1 * ec, (n, e2, ec)
+
+
+def test_fmg_sweep_open_uniform_sphere(orc):
+    """Open boundaries, the uniform sphere of the golden values against its
+    analytic potential: one FMG sweep within 2x of the converged error."""
+    s = GOLDEN["sphere_test"]
+    for n in (32, 64):
+        rho = inputs.uniform_sphere(n, s["R"], s["subcells_per_axis"])
+        exact = inputs.sphere_potential(n, s["R"], G=1.0)
+        one = orc.solve(rho, 1.0 / n, OPEN, four_pi_G=4 * math.pi, tol=0.0, max_cycles=0)
+        conv = orc.solve(rho, 1.0 / n, OPEN, four_pi_G=4 * math.pi, tol=1e-12)
+        e1, ec = np.abs(one.phi - exact).max(), np.abs(conv.phi - exact).max()
+        assert e1 < 2.0 * ec, (n, e1, ec)
+
+
+def _face_points(nx, ny, nz, H):
+    """Positions of every point of a faces array (x-, x+, y-, y+, z-, z+; the
+    documented layout, index 0 and n+1 the extended points) of a level of
+    nx*ny*nz cells of width H, centred on the origin."""
+    def centre(a, m):  # padded index a in 0..m+1 -> cell-centre coordinate
+        return (a - 0.5 - m / 2.0) * H
+    pts = []
+    for face in range(6):
+        axis, hi = divmod(face, 2)
+        n = (nx, ny, nz)
+        wall = (0.5 if hi else -0.5) * n[axis] * H
+        others = [a for a in range(3) if a != axis]  # (first, second) index axes
+        ma, mb = n[others[0]], n[others[1]]
+        for bidx in range(mb + 2):
+            for aidx in range(ma + 2):
+                p = [0.0, 0.0, 0.0]
+                p[axis] = wall
+                p[others[0]] = centre(aidx, ma)
+                p[others[1]] = centre(bidx, mb)
+                pts.append(p)
+    return np.array(pts)
+
+
+def test_open_faces_of_every_level_at_its_own_face_points(orc):
+    """A single massive cell: its expansion about the centre of mass is the
+    monopole alone, so the boundary value at any point p is -G M / |p - c|
+    (App. A at l = 0; G = 1 here).  Each level of the FMG hierarchy carries
+    that value at its own face points, which move between levels (Sec.
+    2.3.6); computed here from the geometry, not from the oracle's faces."""
+    n, h = 32, 1.0 / 32
+    rho = np.zeros((n, n, n))
+    i, j, k = 5, 20, 9
+    rho[k, j, i] = 3.0
+    M = 3.0 * h ** 3
+    c = np.array([(i + 0.5 - n / 2) * h, (j + 0.5 - n / 2) * h, (k + 0.5 - n / 2) * h])
+    for level in range(6):
+        m = n >> (5 - level)
+        got = orc.open_level_faces(rho, h, level, lmax=4, four_pi_G=4 * math.pi)
+        p = _face_points(m, m, m, h * (n // m))
+        want = -M / np.linalg.norm(p - c, axis=1)
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), level
+
+
+def test_fx_step_integer_defect(orc):
+    """The exact integer defect of the mixed outer loop against the FP64 defect
+    of Eq. (defect) (orc.defect, pinned above) on values where FP64 is exact:
+    with 2^S = 1 and h = 1, R = F - (sum_nb P' - 6 P') is f - L u for u = P',
+    f = F, fixed faces b_q = B_q / 2."""
+    rng = np.random.default_rng(3)
+    shape = (8, 16, 32)
+    kinds = [orc.FIXED, orc.ZEROGRAD, orc.PERIODIC, orc.PERIODIC, orc.ZEROGRAD, orc.FIXED]
+    b = [1.5, 0.0, 0.0, 0.0, 0.0, -2.5]
+    phi = rng.integers(-1000, 1000, size=shape)
+    F = rng.integers(-1000, 1000, size=shape)
+    e = rng.integers(-50, 50, size=shape).astype(np.float32) * np.float32(0.25)
+    out, r = orc.fx_step(phi, e, 4.0, F, kinds, b, 1.0, 1.0)
+    assert np.array_equal(out, phi + (e * np.float32(4.0)).astype(np.int64))
+    d = orc.defect(out.astype(np.float64), F.astype(np.float64), 1.0, orc.PER_FACE,
+                   faces=orc.mixed_rule(kinds, b))
+    assert np.array_equal(r.astype(np.float64), d)
+
+
+def test_fx_step_rounding(orc):
+    """round(e c) rounds half to even (2.5 -> 2, 3.5 -> 4, -2.5 -> -2); with
+    P = 0 and no correction the residual is F itself, scaled in FP32."""
+    F = np.zeros((2, 2, 2), dtype=np.int64)
+    e = np.array([2.5, 3.5, -2.5, -3.5, 0.49999997, 1.5, 0.5, -0.5], np.float32).reshape(2, 2, 2)
+    out, _ = orc.fx_step(None, e, 1.0, F, [orc.PERIODIC] * 6, [0.0] * 6, 1.0, 1.0)
+    assert out.ravel().tolist() == [2, 4, -2, -4, 0, 2, 0, 0]
+    F = np.arange(8, dtype=np.int64).reshape(2, 2, 2) * (2 ** 40 + 3)
+    _, r = orc.fx_step(None, None, 1.0, F, [orc.ZEROGRAD] * 6, [0.0] * 6, 1.0, 0.5)
+    assert np.array_equal(r, F.astype(np.float32) * np.float32(0.5))
