@@ -29,6 +29,7 @@
 #include "../../include/mg.h"
 #include "mg_admission.h"
 #include "mg_internal.h"
+#include "mg_tickets.h"
 
 namespace {
 
@@ -50,8 +51,11 @@ struct Request {
   size_t need = 0;
   Clock::time_point t_submit, t_start, t_done;
   bool done = false;
+  int waiters = 0;       // threads in mg_server_wait on this ticket
+  bool retired = false;  // the ticket no longer resolves (mg_tickets.h)
   mg_status status = MG_OK;
   int n_hist = 0;
+  double copy_ms[2] = {};  // host arrays: device time of the copies in and out
   double hist[kHistCap] = {};
 };
 
@@ -83,7 +87,7 @@ struct mg_server {
   std::condition_variable cv_work, cv_done;
   Pool pool{0};
   std::deque<Request*> queue;
-  std::unordered_map<long long, Request*> reqs;
+  mg::tickets::Book<Request> reqs;
   long long next_ticket = 1;
   long long submitted = 0, completed = 0, rejected = 0, cells_completed = 0;
   int running = 0;
@@ -152,7 +156,7 @@ void run_worker(mg_server* S) {
     int nh = 0;
     if (st == MG_OK && r->key.host)
       st = mg::solve_host_copies(ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi,
-                                 r->hist, kHistCap, &nh, stream);
+                                 r->hist, kHistCap, &nh, stream, r->copy_ms);
     else if (st == MG_OK)
       st = mg_solve(ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi, r->hist, kHistCap,
                     &nh, stream);
@@ -186,6 +190,8 @@ void fill_result(const Request* r, mg_result* res, double* hist, int hist_cap) {
   res->queue_ms = ms_between(r->t_submit, r->t_start);
   res->solve_ms = ms_between(r->t_start, r->t_done);
   res->total_ms = ms_between(r->t_submit, r->t_done);
+  res->h2d_ms = r->copy_ms[0];
+  res->d2h_ms = r->copy_ms[1];
 }
 
 }  // namespace
@@ -286,7 +292,7 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
   }
   r->ticket = S->next_ticket++;
   r->t_submit = Clock::now();
-  S->reqs[r->ticket] = r;
+  S->reqs.add(r->ticket, r);
   S->queue.push_back(r);
   ++S->submitted;
   ++S->gen;
@@ -299,15 +305,11 @@ mg_status mg_server_poll(mg_server* S, long long ticket, mg_result* res, double*
                          int hist_cap) {
   if (!S || !res) return MG_ERR_ARG;
   std::lock_guard<std::mutex> lk(S->mu);
-  auto it = S->reqs.find(ticket);
-  if (it == S->reqs.end()) {
-    S->err = "mg_server_poll: unknown ticket";
+  const mg::tickets::Got got =
+      S->reqs.poll(ticket, [&](const Request& r) { fill_result(&r, res, hist, hist_cap); });
+  if (got == mg::tickets::Got::UNKNOWN) {
+    S->err = "mg_server_poll: unknown or retired ticket";
     return MG_ERR_ARG;
-  }
-  fill_result(it->second, res, hist, hist_cap);
-  if (it->second->done) {
-    delete it->second;
-    S->reqs.erase(it);
   }
   return MG_OK;
 }
@@ -316,21 +318,14 @@ mg_status mg_server_wait(mg_server* S, long long ticket, double timeout_s, mg_re
                          double* hist, int hist_cap) {
   if (!S || !res || !(timeout_s >= 0.0)) return MG_ERR_ARG;
   std::unique_lock<std::mutex> lk(S->mu);
-  auto it = S->reqs.find(ticket);
-  if (it == S->reqs.end()) {
-    S->err = "mg_server_wait: unknown ticket";
+  const mg::tickets::Got got = S->reqs.wait(
+      ticket, lk, S->cv_done, timeout_s,
+      [&](const Request& r) { fill_result(&r, res, hist, hist_cap); });
+  if (got == mg::tickets::Got::UNKNOWN) {
+    S->err = "mg_server_wait: unknown or retired ticket";
     return MG_ERR_ARG;
   }
-  Request* r = it->second;
-  const auto limit = std::chrono::duration<double>(timeout_s);
-  if (!S->cv_done.wait_for(lk, limit, [&] { return r->done; })) {
-    fill_result(r, res, hist, hist_cap);
-    return MG_ERR_TIMEOUT;
-  }
-  fill_result(r, res, hist, hist_cap);
-  delete r;
-  S->reqs.erase(ticket);
-  return MG_OK;
+  return got == mg::tickets::Got::DONE ? MG_OK : MG_ERR_TIMEOUT;
 }
 
 mg_status mg_server_get_stats(mg_server* S, mg_server_stats* out) {
@@ -362,13 +357,18 @@ mg_status mg_server_destroy(mg_server* S) {
   S->cv_work.notify_all();
   for (std::thread& t : S->workers) t.join();
   for (void* c : S->pool.drain_idle()) mg_destroy(static_cast<mg_ctx*>(c));
-  for (auto& kv : S->reqs) delete kv.second;
+  S->reqs.clear();
   delete S;
   return MG_OK;
 }
 
 const char* mg_server_last_error(const mg_server* S) {
-  return S ? S->err.c_str() : g_server_err.c_str();
+  if (!S) return g_server_err.c_str();
+  // submit and poll write S->err from other threads: hand out this thread's copy
+  thread_local std::string copy;
+  std::lock_guard<std::mutex> lk(const_cast<mg_server*>(S)->mu);
+  copy = S->err;
+  return copy.c_str();
 }
 
 }  // extern "C"
