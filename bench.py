@@ -44,11 +44,17 @@ def algorithmic_bytes_per_cell(kernel: str, w: int, fixed_point: bool = True) ->
         "correct": 20.0,                # FP64 u, FP32 e -> FP64 u
         "source": 16.0,                 # FP64 rho -> FP64 f
         "fused_down": 3.0 * w + w / 8.0,  # read u, f; write u, coarse f
+        "fused_down0": 2.0 * w + w / 8.0,  # from a zero start: read f; write u, coarse f
         "fused_up": 3.0 * w + w / 8.0,    # read u, coarse e, f; write u
+        # the up leg of one V-cycle and the down leg of the next in one pass:
+        # read u, f, coarse e; write u, coarse f
+        "fused_updown": 3.0 * w + w / 4.0,
+        "gravity": 32.0,                  # int64 phi in; FP64 phi and 3 FP64 g out (fixed point)
     }[kernel]
 
 
-FP32_CLASSES = {"sor", "defect_restrict", "prolong", "fmg_prolong", "fused_down", "fused_up"}
+FP32_CLASSES = {"sor", "defect_restrict", "prolong", "fmg_prolong", "fused_down", "fused_down0",
+                "fused_up", "fused_updown"}
 
 
 def peaks():
@@ -65,6 +71,7 @@ def peaks():
 KERNEL_SOURCES = {
     "fused_up": ["mg_fused.cuh", "mg_fused_launch.cuh", "mg_fused.cu", "mg_internal.h"],
     "fused_down": ["mg_fused.cuh", "mg_fused_launch.cuh", "mg_fused.cu", "mg_internal.h"],
+    "fused_down0": ["mg_fused.cuh", "mg_fused_launch.cuh", "mg_fused.cu", "mg_internal.h"],
     "outer_residual": ["mg_fixed.cu", "mg_convert.cuh", "mg_device.cuh", "mg_internal.h"],
 }
 
@@ -72,17 +79,22 @@ KERNEL_SOURCES = {
 NOMINAL_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of the part, for context
 
 
-def mixed_solve_bytes_per_cell(outer: int, inner: int) -> float:
+def mixed_solve_bytes_per_cell(outer: int, inner: int, paired: bool = True) -> float:
     """Algorithmic bytes per finest cell of one mixed solve: per outer iteration
     `inner` FP32 V(1,1) cycles (the first from a zero correction: its down leg
     reads f only, 2w + w/8; the others 3w + w/8; every up leg 3w + w/8; coarse
     levels add 1/7 of the zero-start legs' bytes) and one fixed-point outer step
     (32 B); plus the passes around the loop: rho read three times (mean and
     maximum, first residual, integer h^2 f), r32 and the integer f written, e
-    read once for its maximum, phi converted back (read and write): 56 B."""
+    read once for its maximum, phi converted back (read and write): 56 B.
+    paired: on the finest level the up leg of each cycle but the last and the
+    down leg of the next are one pass (3w + w/4)."""
     w = 4.0
-    leg0, leg = 2 * w + w / 8, 3 * w + w / 8
-    finest = (leg0 + leg) + (inner - 1) * (2 * leg)
+    leg0, leg, ud = 2 * w + w / 8, 3 * w + w / 8, 3 * w + w / 4
+    if paired:
+        finest = leg0 + (inner - 1) * ud + leg
+    else:
+        finest = (leg0 + leg) + (inner - 1) * (2 * leg)
     coarse = inner * (leg0 + leg) / 7.0
     return outer * (finest + coarse + 32.0) + 56.0
 
@@ -160,6 +172,46 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def near_cpus(gpu_index: int) -> dict:
+    """The GPU's PCI address, its local CPUs and NUMA node (sysfs), for placing
+    page-locked host buffers next to it."""
+    out = {}
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=30).stdout.strip()
+        dom, rest = bus.lower().split(":", 1)
+        path = f"/sys/bus/pci/devices/{dom[-4:]}:{rest}"
+        out["pci"] = f"{dom[-4:]}:{rest}"
+        out["numa_node"] = int(open(os.path.join(path, "numa_node")).read().strip())
+        cpus = set()
+        for part in open(os.path.join(path, "local_cpulist")).read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        out["local_cpus"] = sorted(cpus)
+        out["local_cpus_text"] = open(os.path.join(path, "local_cpulist")).read().strip()
+    except Exception as e:  # not fatal: the buffers are then placed by the default policy
+        out["error"] = str(e)[:200]
+    return out
+
+
+def pages_by_node(ptr: int) -> dict:
+    """Pages per NUMA node of the mapping that holds address ptr
+    (/proc/self/numa_maps)."""
+    best, line_best = -1, None
+    try:
+        for line in open("/proc/self/numa_maps"):
+            start = int(line.split()[0], 16)
+            if start <= ptr and start > best:
+                best, line_best = start, line
+    except Exception:
+        return {}
+    if line_best is None:
+        return {}
+    return {f[1:].split("=")[0]: int(f.split("=")[1]) for f in line_best.split()
+            if f.startswith("N") and "=" in f}
 
 
 def dist_env():
@@ -376,6 +428,8 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=256, help="oracle sample size")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--legs-steps", type=int, default=3,
+                    help="timed solves with separate finest-level legs (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed batched solves (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of arrivals per serving rate (0: skip)")
@@ -455,34 +509,77 @@ def main():
     ktimes = solver.kernel_times()
     solver.set_timing(False)
 
-    # roofline of the dominant kernel class (finest-level launches)
-    dom = max(ktimes, key=lambda k: ktimes[k][0])
-    tot_ms, nl = ktimes[dom]
-    w = 4 if (prec == mg.MIXED and dom in FP32_CLASSES) else 8
-    alg = algorithmic_bytes_per_cell(dom, w) * n ** 3
-    achieved = alg / (tot_ms / nl * 1e-3) / 1e9
+    # roofline of every finest-level launch class, each credited with its own
+    # algorithmic bytes per launch; the dominant class (by device time) is the
+    # headline roofline
     peak, peak_kind = peaks()
-    prec_tag = "f32" if w == 4 else "f64"
+    by_class = {}
+    for k, (tot_ms, nl) in ktimes.items():
+        if nl == 0:
+            continue
+        w = 4 if (prec == mg.MIXED and k in FP32_CLASSES) else 8
+        alg = algorithmic_bytes_per_cell(k, w) * n ** 3
+        ach = alg / (tot_ms / nl * 1e-3) / 1e9
+        by_class[k] = {"launches_per_solve": nl / args.steps, "ms_per_launch": tot_ms / nl,
+                       "algorithmic_bytes_per_launch": alg, "achieved_gbs": ach,
+                       "frac": ach / peak, "dtype": "f32" if w == 4 else "f64"}
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    d = by_class[dom]
+    prec_tag = d["dtype"]
     traffic = ncu_traffic(dom, prec_tag, n)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom}_{prec_tag}",
-                "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg,
-                "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": d["frac"], "traffic": traffic, "kernel": f"{dom}_{prec_tag}",
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"],
+                "frac_of_nominal": d["achieved_gbs"] / NOMINAL_HBM_GBS,
+                "by_class": by_class}
     # the whole solve against the same roofline, and its V-cycle rate
     whole = None
     if prec == mg.MIXED:
         inner = 1 + solver.opts.inner_cycles
-        b_cell = mixed_solve_bytes_per_cell(cycles, inner)
-        whole = {"algorithmic_bytes_per_cell": b_cell,
+        paired = ktimes.get("fused_updown", (0, 0))[1] > 0
+        b_cell = mixed_solve_bytes_per_cell(cycles, inner, paired)
+        whole = {"algorithmic_bytes_per_cell": b_cell, "paired_legs": paired,
                  "achieved_gbs": b_cell * n ** 3 / (ms_per_step * 1e-3) / 1e9,
                  "v_cycles": cycles * inner,
                  "cell_v_cycles_per_s": n ** 3 * cycles * inner / (ms_per_step * 1e-3)}
         whole["frac"] = whole["achieved_gbs"] / peak
         whole["frac_of_nominal"] = whole["achieved_gbs"] / NOMINAL_HBM_GBS
 
+    # the same solve with every finest-level leg as its own pass (no fused
+    # up-down pass): what the temporal blocking saves
+    legs = None
+    if args.legs_steps > 0 and prec == mg.MIXED:
+        with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=prec, leg_pairs=2) as s2:
+            if not args.no_tune:
+                s2.autotune(stream)
+            for _ in range(2):
+                s2.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.legs_steps):
+                _, h2, st2 = s2.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tl = a.elapsed_time(b) / args.legs_steps
+        legs = {"ms_per_solve": tl, "value": n ** 3 / (tl * 1e-3), "unit": UNIT, "status": st2,
+                "what": "the same solve with the up and down legs of consecutive finest-level "
+                        "V-cycles as separate passes (opts.leg_pairs = 2)"}
+
     # end to end through the host API: pinned host rho/phi, copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
+        # page-locked buffers on the memory node next to this GPU: allocate them
+        # from a thread bound to the GPU's local CPUs (first touch places pages)
+        numa = near_cpus(local)
+        saved_aff = None
+        if numa.get("local_cpus"):
+            try:
+                saved_aff = os.sched_getaffinity(0)
+                os.sched_setaffinity(0, numa["local_cpus"])
+            except OSError:
+                saved_aff = None
         rho_h = rho.cpu().pin_memory()
         phi_h = torch.zeros_like(rho_h).pin_memory()
         solver.solve_host(rho_h, 1.0, TOL, phi=phi_h, stream=stream)
@@ -508,6 +605,9 @@ def main():
         inflight = args.e2e_inflight
         k_req = inflight * args.e2e_steps
         phis_h = [torch.zeros_like(rho_h).pin_memory() for _ in range(inflight)]
+        numa["rho_pages_by_node"] = pages_by_node(rho_h.data_ptr())
+        numa["phi_pages_by_node"] = pages_by_node(phis_h[0].data_ptr())
+        copies = []  # (h2d ms, d2h ms, solve ms) of every timed request
         free, _ = torch.cuda.mem_get_info()
         with mg.Server(free // 2, slots=inflight, max_queue=4 * inflight, prec=mg.MIXED) as srv:
             for tk in [srv.submit(rho_h, p, tol=TOL) for p in phis_h]:  # hierarchies, shapes
@@ -520,19 +620,32 @@ def main():
                 if q >= inflight:
                     res, _ = srv.wait(tickets[q - inflight], 600)
                     assert res.done and res.status == 0
+                    copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms))
                 tickets.append(srv.submit(rho_h, phis_h[q % inflight], tol=TOL))
             for tk in tickets[-inflight:]:
                 res, _ = srv.wait(tk, 600)
                 assert res.done and res.status == 0
+                copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms))
             dt2 = time.perf_counter() - t0
+        if saved_aff is not None:
+            os.sched_setaffinity(0, saved_aff)
         if ws > 1:
             t = torch.tensor([dt2], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             dt2 = float(t.item())
+        h2d = statistics.median(c[0] for c in copies)
+        d2h = statistics.median(c[1] for c in copies)
         e2e = {"value": ws * n ** 3 * k_req / dt2, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "via": f"mg_server with pinned host rho / phi, {inflight} requests in flight "
                       f"({k_req} solves timed, copies on the slots' streams)",
+               "copies": {"h2d_ms_median": h2d, "d2h_ms_median": d2h,
+                          "h2d_gbs": nbytes / (h2d * 1e-3) / 1e9,
+                          "d2h_gbs": nbytes / (d2h * 1e-3) / 1e9,
+                          "solve_ms_median": statistics.median(c[2] for c in copies),
+                          "what": "per request, device time of the slot's copies (events on its "
+                                  "stream; concurrent with other slots' solves and copies)"},
+               "numa": numa,
                "sequential": sequential}
         del rho_h, phi_h, phis_h
 
@@ -612,6 +725,7 @@ def main():
             "final_ratio": float(hist[-1]),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items() if v[1]},
             "fp64_path": fp64,
+            "separate_legs": legs,
             "with_gravity": grav,
             "open_sphere": open_sphere,
             "per_face": per_face,

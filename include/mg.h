@@ -98,7 +98,13 @@ typedef struct {
                       /*    0.9 per V-cycle on 16^3-32^3 grids against 0.15), so    */
                       /*    give stall_ratio >= 1 and room in max_cycles.  Not in    */
                       /*    mg_batch_create.  Default 0                              */
-  int reserved[5];    /* must be zero                                               */
+  int leg_pairs;      /* MIXED: the up leg of each inner V-cycle on the finest     */
+                      /*    level and the down leg of the next (Algorithm 1, steps   */
+                      /*    5-7 then 1-3) as one fused pass, two SMOOTH steps per    */
+                      /*    pass over HBM, or as two passes; same bits either way.   */
+                      /*    0 (default): two passes, unless mg_ctx_autotune timed    */
+                      /*    the fused pass faster; 1: always fused; 2: never         */
+  int reserved[4];    /* must be zero                                               */
 } mg_opts;
 
 typedef struct mg_ctx mg_ctx;
@@ -203,7 +209,10 @@ typedef enum {
   MG_K_FUSED_DOWN = 8,      /* FP32 fused SMOOTH + defect + restriction           */
   MG_K_FUSED_UP = 9,        /* FP32 fused prolongation + correction + SMOOTH      */
   MG_K_GRAVITY = 10,        /* acceleration g = -grad phi (mg_solve_gravity)       */
-  MG_K_COUNT = 11
+  MG_K_FUSED_DOWN0 = 11,    /* MG_K_FUSED_DOWN from a zero start (reads f only)   */
+  MG_K_FUSED_UPDOWN = 12,   /* FP32 up leg of one V-cycle and down leg of the     */
+                            /* next in one pass (two SMOOTH steps)                */
+  MG_K_COUNT = 13
 } mg_kernel;
 
 /* Enable (on = 1) or disable per-kernel timing: every finest-level launch of
@@ -296,6 +305,46 @@ mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double ome
                           const float *u_in_dev, float *u_out_dev, const float *f_dev,
                           const float *ec_dev, void *stream);
 
+/* The fused FP32 kernels of the two legs above, called directly (no
+ * fallback to the per-step kernels), with a rule per face and an explicit
+ * launch shape, so that every compiled variant can be checked on its own.
+ * leg 0: down (steps 1-3 of Algorithm 1: u_out = SMOOTH(u_in, or 0 when
+ * zero_guess), fc = restriction of f - L u_out); leg 1: up (steps 5-7:
+ * u_out = SMOOTH(u_in + trilinear(ec))); leg 2: the up leg of one V-cycle and
+ * the down leg of the next in one pass (steps 5-7, then 1-3 of the next cycle:
+ * u_out = SMOOTH(SMOOTH(u_in + trilinear(ec))), fc = restriction of
+ * f - L u_out; tx 0 or 64, nx a multiple of 64, nz >= 16).  face_bc[6] (host) gives each face's
+ * homogeneous rule (x-, x+, y-, y+, z-, z+): MG_BC_PERIODIC on both faces of an
+ * axis, MG_BC_FIXED (value 0) or MG_BC_ZEROGRAD.  tx (0, 32 or 64 cells), ty
+ * (0, 16 or 32 rows) and cz (0 or a multiple of 8 planes) choose the CTA tile
+ * and z-chunk; 0 takes the built-in choice.  Arrays as in mg_op_vcycle_down
+ * and mg_op_vcycle_up.  Errors: MG_ERR_ARG for bad arguments and for grids or
+ * shapes the fused kernels do not take (sides below 32, nx not a multiple of
+ * the tile width, ny of the tile height, nz of 8). */
+mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int *face_bc,
+                          double omega, int zero_guess, int tx, int ty, int cz,
+                          const float *u_in_dev, float *u_out_dev, const float *f_dev,
+                          const float *ec_dev, float *fc_dev, void *stream);
+
+/* The fixed-point outer step of MG_MIXED (not in the paper: the exact form
+ * of the FP64 defect correction, with phi and h^2 f held as 64-bit integers
+ * P and F scaled by 2^S):
+ *   P' = P + round(e * c)   (e * c the FP32 product rounded to the nearest
+ *                            integer, ties to even; phi_in_dev NULL: P = 0;
+ *                            e_dev must not be NULL)
+ *   R  = F - (sum of the six neighbours of P' - 6 P')   exactly (Eq. defect)
+ *   r32 = fl32(R) * factor.
+ * phi_out_dev receives P', r32_dev the residual.  face_bc[6] as in
+ * mg_op_fused_leg; a fixed face's neighbour is B - P' with B = round(2 b 2^S),
+ * b from faces_dev (the faces layout above, FP64; NULL: b = 0); two_pow_S =
+ * 2^S.  cz: planes per CTA (0 built-in, else >= 4).  int64 arrays
+ * nx*ny*nz; nx a multiple of 32 and ny of 16.  Synchronises `stream`.
+ * Errors: MG_ERR_ARG, MG_ERR_CUDA. */
+mg_status mg_op_fx_step(int nx, int ny, int nz, const int *face_bc, const double *faces_dev,
+                        double two_pow_S, int cz, const long long *phi_in_dev, const float *e_dev,
+                        float c, const long long *F_dev, long long *phi_out_dev, float factor,
+                        float *r32_dev, void *stream);
+
 /* Multipole moments of rho_dev (FP64, nx*ny*nz, spacing h) for App. A:
  * Q_host receives (lmax+1)^2 moments ordered l*l + (m + l) (25 slots are
  * written, zero above lmax); origin_host is the expansion origin on input
@@ -386,6 +435,13 @@ int mg_batch_graph(const mg_batch *batch);
  * Synchronises the device.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
 mg_status mg_batch_phase_ms(mg_batch *batch, double *ms_by_type, int n_types);
 
+/* Limit of one wait at the persistent kernel's grid-wide barriers, in GPU
+ * clock cycles (default 4e9, about 2 s at 2 GHz); a wait that runs out makes
+ * every block return and mg_batch_solve report MG_ERR_TIMEOUT, leaving the
+ * batch usable.  Takes effect at the next mg_batch_solve, which captures its
+ * CUDA graph again.  Errors: MG_ERR_ARG (cycles < 0). */
+mg_status mg_batch_set_barrier_limit(mg_batch *batch, long long cycles);
+
 const char *mg_batch_last_error(const mg_batch *batch);
 
 /* Number of doubles in a faces array of an nx*ny*nz level. */
@@ -405,10 +461,9 @@ size_t mg_faces_count(int nx, int ny, int nz);
 mg_status mg_ctx_autotune(mg_ctx *ctx, void *stream);
 
 /* The shape (tile width tx, height ty, planes cz) chosen for a kernel class on
- * a level (MG_K_FUSED_DOWN,
- * MG_K_FUSED_UP, MG_K_SOR for extra fused smoothing steps, MG_K_OUTER_RESIDUAL
- * for the fixed-point step on the finest level); 0 means the built-in
- * choice. */
+ * a level (MG_K_FUSED_DOWN, MG_K_FUSED_UP, MG_K_FUSED_UPDOWN, MG_K_SOR for
+ * extra fused smoothing steps, MG_K_OUTER_RESIDUAL for the fixed-point step on
+ * the finest level); 0 means the built-in choice. */
 mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, int *ty,
                              int *cz);
 
@@ -448,6 +503,8 @@ typedef struct {
   double queue_ms;       /* submission -> a slot took it */
   double solve_ms;       /* slot took it -> result in phi (stream synchronised) */
   double total_ms;       /* submission -> result: the request's latency */
+  double h2d_ms;         /* host arrays: device time of the copy of rho in (else 0) */
+  double d2h_ms;         /* host arrays: device time of the copy of phi out (else 0) */
 } mg_result;
 
 typedef struct {
@@ -475,13 +532,18 @@ mg_status mg_server_create(size_t hbm_budget_bytes, int slots, int max_queue,
 mg_status mg_server_submit(mg_server *server, const mg_request *request, long long *ticket);
 
 /* State of a ticket without waiting.  Once it reports done = 1 the ticket
- * is retired (a later poll returns MG_ERR_ARG).  hist (host, hist_cap
- * entries, may be NULL) receives the residual history as mg_solve's. */
+ * is retired: a later poll or wait of it returns MG_ERR_ARG.  hist (host,
+ * hist_cap entries, may be NULL) receives the residual history as
+ * mg_solve's. */
 mg_status mg_server_poll(mg_server *server, long long ticket, mg_result *result, double *hist,
                          int hist_cap);
 
 /* Wait up to timeout_s seconds for a ticket; retires it when done.  Returns
- * MG_ERR_TIMEOUT (ticket kept, result->done = 0) when time ran out. */
+ * MG_ERR_TIMEOUT (ticket kept, result->done = 0) when time ran out.  Several
+ * threads may wait on one ticket (and others poll it) at once: every thread
+ * already waiting when the request finishes receives its result, even if a
+ * poll retired the ticket meanwhile; calls made after the retirement return
+ * MG_ERR_ARG. */
 mg_status mg_server_wait(mg_server *server, long long ticket, double timeout_s,
                          mg_result *result, double *hist, int hist_cap);
 

@@ -33,9 +33,11 @@ EXPORTS = [
     "mg_ctx_tile_config", "mg_batch_phase_ms", "mg_solve_gravity", "mg_op_gravity",
     "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
     "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error", "mg_op_convert",
+    "mg_op_fused_leg", "mg_op_fx_step", "mg_batch_set_barrier_limit",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
-           "correct", "source", "fused_down", "fused_up", "gravity"]
+           "correct", "source", "fused_down", "fused_up", "gravity", "fused_down0",
+           "fused_updown"]
 
 
 class Opts(ctypes.Structure):
@@ -46,7 +48,7 @@ class Opts(ctypes.Structure):
         ("origin", ctypes.c_double * 3), ("stall_ratio", ctypes.c_double),
         ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("outer_fixed", ctypes.c_int), ("fas", ctypes.c_int), ("coarse_literal", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("leg_pairs", ctypes.c_int), ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -63,7 +65,7 @@ class Result(ctypes.Structure):
     _fields_ = [
         ("done", ctypes.c_int), ("status", ctypes.c_int), ("n_hist", ctypes.c_int),
         ("reserved", ctypes.c_int), ("queue_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-        ("total_ms", ctypes.c_double),
+        ("total_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double),
     ]
 
 
@@ -145,6 +147,11 @@ def lib():
             L.mg_op_vcycle_down.restype = i
             L.mg_op_vcycle_up.argtypes = [i, i, i, d, i, d, p, p, p, p, p]
             L.mg_op_vcycle_up.restype = i
+            L.mg_op_fused_leg.argtypes = [i, i, i, i, d, p, d, i, i, i, i, p, p, p, p, p, p]
+            L.mg_op_fused_leg.restype = i
+            L.mg_op_fx_step.argtypes = [i, i, i, p, p, d, i, p, p, ctypes.c_float, p, p,
+                                        ctypes.c_float, p, p]
+            L.mg_op_fx_step.restype = i
             L.mg_op_multipole_moments_noalloc.argtypes = [i, i, i, d, p, i, i, p, p, p]
             L.mg_op_multipole_moments_noalloc.restype = i
             for name in ("mg_op_smooth", "mg_op_defect", "mg_op_defect_restrict", "mg_op_restrict",
@@ -167,6 +174,8 @@ def lib():
             L.mg_batch_phase_ms.restype = i
             L.mg_batch_graph.argtypes = [p]
             L.mg_batch_graph.restype = i
+            L.mg_batch_set_barrier_limit.argtypes = [p, ctypes.c_longlong]
+            L.mg_batch_set_barrier_limit.restype = i
             L.mg_batch_last_error.argtypes = [p]
             L.mg_batch_last_error.restype = ctypes.c_char_p
             L.mg_faces_count.argtypes = [i, i, i]
@@ -301,11 +310,11 @@ class Solver:
         _check(lib().mg_ctx_autotune(self.ctx, _stream_ptr(stream)), self.ctx)
 
     def tile_configs(self):
-        """{"fused_down" | "fused_up" | "sor" | "outer_residual": {level: (tx, ty, cz)}}
-        (0: built-in)."""
+        """{"fused_down" | "fused_up" | "fused_updown" | "sor" | "outer_residual":
+        {level: (tx, ty, cz)}} (0: built-in)."""
         out = {}
         levels = self.n.bit_length()
-        for name in ("fused_down", "fused_up", "sor", "outer_residual"):
+        for name in ("fused_down", "fused_up", "fused_updown", "sor", "outer_residual"):
             k = KERNELS.index(name)
             per = {}
             for l in range(levels):
@@ -492,6 +501,46 @@ def op_vcycle_up(u, f, ec, h, bc=PERIODIC, omega=1.15, stream=None):
     return uo
 
 
+def _face_kinds(kinds):
+    k = (ctypes.c_int * 6)(*[int(x) for x in kinds])
+    return k
+
+
+def op_fused_leg(leg, u, f, h, kinds, omega=1.15, zero_guess=False, ec=None, tile=(0, 0, 0),
+                 stream=None):
+    """The fused FP32 kernels themselves (mg_op_fused_leg): leg 0 down returns
+    (u_out, fc); leg 1 up returns u_out; leg 2 (up then down) returns (u_out,
+    fc).  kinds: six face rules; tile = (tx, ty, cz), zeros for the built-in
+    shape."""
+    import torch
+    nz, ny, nx = f.shape
+    uo = torch.empty_like(f)
+    fc = None
+    if leg != 1:
+        fc = torch.empty((nz // 2, ny // 2, nx // 2), dtype=f.dtype, device=f.device)
+    tx, ty, cz = tile
+    _check(lib().mg_op_fused_leg(
+        leg, nx, ny, nz, h, _face_kinds(kinds), omega, int(zero_guess), tx, ty, cz,
+        None if (zero_guess or u is None) else _dptr(u, torch.float32), _dptr(uo),
+        _dptr(f, torch.float32), None if ec is None else _dptr(ec, torch.float32),
+        None if fc is None else _dptr(fc), _stream_ptr(stream)))
+    return uo if leg == 1 else (uo, fc)
+
+
+def op_fx_step(phi_in, e, c, F, kinds, two_pow_S, factor, faces=None, cz=0, stream=None):
+    """The fixed-point outer step (mg_op_fx_step): returns (phi' int64, r32)."""
+    import torch
+    nz, ny, nx = F.shape
+    out = torch.empty_like(F)
+    r = torch.empty(F.shape, dtype=torch.float32, device=F.device)
+    _check(lib().mg_op_fx_step(
+        nx, ny, nz, _face_kinds(kinds), _faces_ptr(faces), float(two_pow_S), cz,
+        None if phi_in is None else _dptr(phi_in, torch.int64),
+        None if e is None else _dptr(e, torch.float32), float(c), _dptr(F, torch.int64),
+        _dptr(out), float(factor), _dptr(r), _stream_ptr(stream)))
+    return out, r
+
+
 def op_multipole_moments(rho, h, lmax=4, use_com=True, origin=(0.0, 0.0, 0.0), stream=None):
     import torch
     nz, ny, nx = rho.shape
@@ -577,6 +626,13 @@ class Batch:
         if st in (3, 6):
             raise MGError(st, lib().mg_batch_last_error(self.ptr).decode())
         return st, [hist[g, : nh[g]].copy() for g in range(n)], sts
+
+    def set_barrier_limit(self, cycles):
+        """Clock cycles one grid-wide barrier wait may take before the solve
+        gives up with MG_ERR_TIMEOUT (default 4e9)."""
+        st = lib().mg_batch_set_barrier_limit(self.ptr, int(cycles))
+        if st != 0:
+            raise MGError(st, lib().mg_batch_last_error(self.ptr).decode())
 
     def close(self):
         if getattr(self, "ptr", None):

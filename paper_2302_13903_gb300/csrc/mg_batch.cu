@@ -126,6 +126,7 @@ struct Ctl {
   double omega;
   int max_cycles, inner_zero;
   double stall_ratio;
+  long long bar_cycles;  // a barrier wait gives up after this many clock cycles
 };
 
 __device__ bool grid_barrier(const Ctl& c) {
@@ -141,7 +142,7 @@ __device__ bool grid_barrier(const Ctl& c) {
     } else {
       const long long t0 = clock64();
       while (*gen == g0) {
-        if (clock64() - t0 > kBarrierCycles) {
+        if (clock64() - t0 > c.bar_cycles) {
           atomicOr(c.err, 1);
           break;
         }
@@ -794,6 +795,7 @@ struct mg_batch {
   std::vector<void*> allocs;
   size_t bytes = 0;
   std::string err;
+  long long bar_cycles = kBarrierCycles;  // limit of one grid-wide barrier wait
 };
 
 namespace {
@@ -925,6 +927,7 @@ cudaError_t enqueue_solve(mg_batch* b, cudaStream_t s) {
   c.max_cycles = b->opts.max_cycles;
   c.inner_zero = b->opts.inner_fmg ? 0 : 1;
   c.stall_ratio = b->opts.stall_ratio;
+  c.bar_cycles = b->bar_cycles;
   if (e == cudaSuccess) {
     void* args[] = {&c};
     e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->blocks), dim3(kThreads), args,
@@ -1179,6 +1182,21 @@ mg_status mg_batch_phase_ms(mg_batch* b, double* ms_by_type, int n_types) {
     if (ty < n_types) ms_by_type[ty] += (double)(t[(size_t)ph] - last) * 1e-6;
     last = t[(size_t)ph];
   }
+  return MG_OK;
+}
+
+mg_status mg_batch_set_barrier_limit(mg_batch* b, long long cycles) {
+  if (!b || cycles < 0) {
+    g_batch_err = "mg_batch_set_barrier_limit: invalid argument";
+    return MG_ERR_ARG;
+  }
+  b->bar_cycles = cycles;
+  // the limit is a kernel argument: the captured solve is captured again
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->graph_tried = false;
   return MG_OK;
 }
 

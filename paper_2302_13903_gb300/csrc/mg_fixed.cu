@@ -28,7 +28,7 @@ constexpr int kThreads = 256;
 int grid_for(long long work) {
   long long b = (work + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  if (b > 152LL * 64) b = 152LL * 64;
+  if (b > sm_count() * 64LL) b = sm_count() * 64LL;
   return (int)b;
 }
 
@@ -282,7 +282,7 @@ __device__ __forceinline__ int fx_face_kind(const FxBc& bc, int face) {
 }
 
 // One outer step on the integer grid, fused and z-marching:
-//   PHI' = PHI_in + round(e * c)          (the pending FP32 correction; e may be
+//   PHI' = PHI_in + round(e * c)          (the pending FP32 correction, never
 //                                           null; ZERO_IN: PHI_in is all zero)
 //   R    = F - (sum_nb PHI' - 6 PHI')      (exact)
 //   r32  = R * factor, partial sums of r32^2 (and of PHI' when psum is given),
@@ -329,16 +329,6 @@ __device__ __forceinline__ long long fx_nb_lite(const long long* __restrict__ q,
     return q[hi ? t - (long long)(g.nz - 1) * sz : t + (long long)(g.nz - 1) * sz];
   }
   return fx_face_ghost(bc, g, self, i, j, k, axis, hi);
-}
-
-// PHI' at flat offset o.
-template <bool ZERO_IN>
-__device__ __forceinline__ long long fx_corrected(const long long* __restrict__ phi_in,
-                                                  const float* __restrict__ e, float c,
-                                                  size_t o) {
-  long long v = ZERO_IN ? 0 : phi_in[o];
-  if (e) v += __float2ll_rn(e[o] * c);
-  return v;
 }
 
 // Asynchronous global -> shared copies of 8 or 4 bytes (src_bytes 0 fills
@@ -736,7 +726,7 @@ int fx_step_cz(Grid g, int cz) {
   const long long cols = (long long)(g.nx / FX_TX) * (g.ny / FX_TY);
   if (cz <= 0) {
     cz = 64;
-    while (cz > kFxMinCz && cols * ((g.nz + cz - 1) / cz) < 4 * 152) cz /= 2;
+    while (cz > kFxMinCz && cols * ((g.nz + cz - 1) / cz) < 4LL * sm_count()) cz /= 2;
   }
   if (cz > 128) cz = 128;
   return cz > g.nz ? g.nz : cz;
@@ -779,6 +769,7 @@ cudaError_t launch_fx_step(const long long* phi_in, long long* phi_out, const fl
   const FxBc b = fx_bc(bc, two_pow_S);
   const int pm = fx_periodic_mask(bc);
   if (cz_req != 0 && cz_req < kFxMinCz) return cudaErrorInvalidValue;
+  if (!e || !F || !phi_out || !r32 || !partials || !flag) return cudaErrorInvalidValue;
   const int cz = fx_step_cz(g, cz_req);
   dim3 grid(g.nx / FX_TX, g.ny / FX_TY, (g.nz + cz - 1) / cz);
   const int nb = (int)(grid.x * grid.y * grid.z);

@@ -328,13 +328,14 @@ __device__ __forceinline__ CoarseIdx coarse_idx(const FusedParams& p, int gx4, i
 }
 
 // The 3 x 4 coarse values of a staged plane S (sz: the ghost sign of a plane
-// outside a level with z walls, else 1), ghosts applied.
-template <int PM, int CX>
+// outside a level with z walls, else 1), ghosts applied.  C0: the tile column
+// of thread tr = 0's first coarse cell.
+template <int PM, int CX, int C0 = 1>
 __device__ __forceinline__ Coarse12 xy_read(const float* S, const CoarseIdx& ci, int tr, int tp,
                                             float sz) {
   Coarse12 r;
   if (Per<PM>::X && Per<PM>::Y) {
-    const float* b = S + tp * CX + 1 + 2 * tr;
+    const float* b = S + tp * CX + C0 + 2 * tr;
 #pragma unroll
     for (int yy = 0; yy < 3; ++yy)
 #pragma unroll

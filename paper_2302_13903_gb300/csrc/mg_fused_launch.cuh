@@ -41,7 +41,7 @@ inline cudaError_t launch_t(const float* ui, float* uo, const float* f, const fl
 template <int MODE, bool ZERO, int PM>
 inline cudaError_t dispatch_t(const float* ui, float* uo, const float* f, const float* ec, float* fc,
                        FusedParams p, TileCfg cfg, cudaStream_t s) {
-  const long long sms = 152;
+  const long long sms = sm_count();
   const int tx = cfg.tx ? cfg.tx : (p.nx >= 64 ? 64 : 32), ty = cfg.ty ? cfg.ty : 16;
   const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
   int cz = 64;

@@ -63,9 +63,18 @@ inline size_t faces_count(const Grid& g) {
 // free for solves on other streams while the bytes cross the host link (the
 // serving loop); mg_solve_host instead lets the solve's first and last passes
 // read and write page-locked host memory themselves.
+// copy_ms (may be null) receives the device time of the host-to-device copy
+// of rho and of the device-to-host copy of phi, from events on `s`.
 mg_status solve_host_copies(mg_ctx* c, const double* rho, double four_pi_G, double tol,
                             double* phi, double* hist, int hist_cap, int* n_hist,
-                            cudaStream_t s);
+                            cudaStream_t s, double* copy_ms = nullptr);
+
+// Record the message mg_last_error(NULL) returns on this thread (entry points
+// that have no context report their failures through it).
+void set_last_error(const std::string& msg);
+
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
 
 // Launch counter (per thread: a context is not thread-safe, so the driver
 // resets and reads it around one solve on one thread).
@@ -180,6 +189,16 @@ cudaError_t launch_fused_smooth(const float* u_in, float* u_out, const float* f,
                                 Bc bc, double omega, bool zero_guess, cudaStream_t s,
                                 TileCfg cfg = TileCfg{});
 
+// The up leg of one V-cycle and the down leg of the next on the same level in
+// one pass (Algorithm 1, steps 5-7 then 1-3): u_out = SMOOTH(SMOOTH(u_in +
+// trilinear(ec))), fc = restriction of f - L u_out.  Levels with nx a multiple
+// of 64, ny of 16 and nz >= 16 that fused_ok takes (updown_ok).
+bool updown_ok(Grid g, const Bc& bc);
+bool updown_cfg_ok(Grid g, TileCfg cfg);
+cudaError_t launch_fused_updown(const float* u_in, float* u_out, const float* f, const float* ec,
+                                float* fc, Grid g, double h, Bc bc, double omega, cudaStream_t s,
+                                TileCfg cfg = TileCfg{});
+
 // ---------------------------------------------------------------------------
 // Exact 64-bit fixed-point outer residual (mg_fixed.cu).
 
@@ -210,7 +229,7 @@ cudaError_t launch_rho_to_fx(const double* rho, long long* q, long long n, doubl
 // PHI += round(e * c); *flag |= 1 if |PHI| passes 2^60.
 cudaError_t launch_fx_correct(long long* phi, const float* e, long long n, float c, int* flag,
                               cudaStream_t s);
-// Fused outer step: PHI_out = PHI_in + round(e * c) (e may be null; phi_in
+// Fused outer step: PHI_out = PHI_in + round(e * c) (e must not be null; phi_in
 // null means PHI_in = 0), then r32 = (F - (sum_nb PHI_out - 6 PHI_out)) *
 // factor exactly in integers, one partial sum of r32^2 per block in partials
 // (count in *nb_out, at most nb_max) and, when psum is given, the exact sum of

@@ -13,6 +13,7 @@
 // bodies in mg_device.cuh, and deterministic two-stage reductions.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "mg_device.cuh"
@@ -50,7 +51,7 @@ __device__ __forceinline__ double block_sum(double v) {
 int grid_for(long long work) {
   long long b = (work + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  if (b > 152LL * 64) b = 152LL * 64;
+  if (b > sm_count() * 64LL) b = sm_count() * 64LL;
   return (int)b;
 }
 
@@ -243,6 +244,24 @@ __global__ void k_gravity(const double* __restrict__ u, double* __restrict__ g, 
 }
 
 }  // namespace
+
+int sm_count() {
+  static std::atomic<int> cached[64];  // zero-initialised (static storage)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  int n = cached[dev].load();
+  if (n == 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cached[dev].store(n);
+  }
+  return n;
+}
 
 int reduce_blocks(long long n) {
   long long b = (n + kThreads * 4 - 1) / (kThreads * 4);

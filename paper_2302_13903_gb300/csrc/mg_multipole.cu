@@ -344,7 +344,7 @@ cudaError_t launch_open_faces(Grid g, double h, const double* qo, int lmax, doub
   if (e != cudaSuccess) return e;
   const long long total = (long long)faces_count(g);
   long long nb = (total + kThreads - 1) / kThreads;
-  if (nb > 152 * 16) nb = 152 * 16;
+  if (nb > sm_count() * 16LL) nb = sm_count() * 16LL;
   ++g_launches;
   k_open_faces<<<(int)nb, kThreads, 0, s>>>(g, h, qo, lmax, G, faces);
   return cudaGetLastError();

@@ -35,8 +35,6 @@ __device__ __align__(256) double g_moment_scratch[kStaticDoubles];
 std::mutex g_mu;
 double* g_addr[64] = {};
 
-thread_local std::string g_noalloc_err;
-
 // Device address of the scratch array on the current device, looked up once
 // per device (with that device current) and cached.
 cudaError_t scratch_address(double** out) {
@@ -55,11 +53,17 @@ cudaError_t scratch_address(double** out) {
   return cudaSuccess;
 }
 
+// Failures are reported through mg_last_error(NULL), like the other entry
+// points without a context, and on stderr.
+mg_status fail(mg_status st, const std::string& msg) {
+  mg::set_last_error(msg);
+  std::fprintf(stderr, "%s\n", msg.c_str());
+  return st;
+}
+
 mg_status fail_cuda(cudaError_t e, const char* what) {
-  g_noalloc_err = std::string("mg_op_multipole_moments_noalloc: ") + what + ": " +
-                  cudaGetErrorString(e);
-  std::fprintf(stderr, "%s\n", g_noalloc_err.c_str());
-  return MG_ERR_CUDA;
+  return fail(MG_ERR_CUDA, std::string("mg_op_multipole_moments_noalloc: ") + what + ": " +
+                               cudaGetErrorString(e));
 }
 
 }  // namespace
@@ -69,19 +73,15 @@ extern "C" mg_status mg_op_multipole_moments_noalloc(int nx, int ny, int nz, dou
                                                      double* origin_host, double* Q_host,
                                                      void* stream) {
   if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !rho_dev || !origin_host || !Q_host ||
-      lmax < 0 || lmax > 4) {
-    std::fprintf(stderr, "mg_op_multipole_moments_noalloc: invalid argument\n");
-    return MG_ERR_ARG;
-  }
+      lmax < 0 || lmax > 4)
+    return fail(MG_ERR_ARG, "mg_op_multipole_moments_noalloc: invalid argument");
   const long long rows = (long long)ny * nz;
   const long long nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
-  if (nb > kStaticBlocks) {
-    std::fprintf(stderr,
-                 "mg_op_multipole_moments_noalloc: grid has %lld rows (ny*nz); the fixed scratch "
-                 "holds at most %d rows -- use mg_op_multipole_moments instead\n",
-                 rows, kStaticBlocks * kRowsPerBlock);
-    return MG_ERR_ARG;
-  }
+  if (nb > kStaticBlocks)
+    return fail(MG_ERR_ARG, "mg_op_multipole_moments_noalloc: grid has " +
+                                std::to_string(rows) + " rows (ny*nz); the fixed scratch holds at "
+                                "most " + std::to_string(kStaticBlocks * kRowsPerBlock) +
+                                " rows -- use mg_op_multipole_moments instead");
   cudaStream_t s = (cudaStream_t)stream;
   double* scratch = nullptr;
   cudaError_t e = mg::prepare_multipole();  // constant tables, once per device

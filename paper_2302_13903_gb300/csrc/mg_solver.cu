@@ -81,7 +81,8 @@ struct mg_ctx {
   long long kernel_n[MG_K_COUNT] = {};
   // Launch shapes of the fused legs per level and of the fixed-point outer
   // step (zeros: built-in choice), set by mg_ctx_autotune.
-  mg::TileCfg cfg_down[kMaxLevels] = {}, cfg_up[kMaxLevels] = {}, cfg_smooth[kMaxLevels] = {};
+  mg::TileCfg cfg_down[kMaxLevels] = {}, cfg_up[kMaxLevels] = {}, cfg_smooth[kMaxLevels] = {},
+              cfg_ud[kMaxLevels] = {};
   int fx_cz = 0;
   // The mixed path's inner FP32 solve (the same launches on the same buffers
   // every outer iteration) as a CUDA graph, captured on its second run and
@@ -89,6 +90,9 @@ struct mg_ctx {
   cudaGraphExec_t inner_exec = nullptr;
   long long inner_launches = 0;  // kernels in the graph
   int inner_runs = 0;
+  // the autotuner timed the finest level's fused up-down pass faster than the
+  // two legs it replaces (opts.leg_pairs = 0 then fuses them)
+  bool pairs_faster = false;
 };
 
 namespace {
@@ -115,6 +119,12 @@ bool dims_ok(int nx, int ny, int nz) {
 struct Fail {
   mg_status st;
 };
+
+}  // namespace
+
+void mg::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 void check(mg_ctx* c, cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
@@ -364,7 +374,7 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
     zg = false;
   }
   if (pre >= 1) {  // 1-3
-    KTimer t(c, MG_K_FUSED_DOWN, fin, s);
+    KTimer t(c, zg ? MG_K_FUSED_DOWN0 : MG_K_FUSED_DOWN, fin, s);
     check(c, mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
                                    om, zg, s, c->cfg_down[l]),
           "fused down");
@@ -402,6 +412,67 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
     KTimer t(c, MG_K_PROLONG, fin, s);
     check(c, mg::launch_prolong<float>(c->u32[l - 1], c->u32[l], g, hom, 0, 1, s), "prolong");
   }
+}
+
+// Steps 4.1-4.2 of Algorithm 1 below an FP32 level l: the coarse correction
+// from the restricted defect in f32[l-1], into u32[l-1] (from zero).
+void coarse_correction(mg_ctx* c, int l, const Bc& hom, cudaStream_t s) {
+  Pyr<float> P = pyr<float>(c);
+  if (l - 1 == 0)
+    coarsest_solve<float>(c, P.u[0], P.f[0], hom, false, s);
+  else if (l - 1 <= bottom_top(c))
+    launch_bottom_levels<float>(c, P.u, P.f, l - 1, nullptr, hom, false, s);
+  else
+    vcycle<float>(c, P, l - 1, hom, hom, true, s);
+}
+
+// Whether `cycles` V(1,1) cycles on FP32 level l from a zero start can run as
+// pairs: the first down leg, then the up leg of each cycle fused with the down
+// leg of the next (temporal blocking of the smoother), then the last up leg.
+bool pairs_ok(const mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, int cycles) {
+  const Grid g = level_grid(c, l);
+  return cycles >= 2 && c->opts.pre == 1 && c->opts.post == 1 && c->u32b[l] &&
+         mg::fused_ok(g, bc_top) && hom.kind == bc_top.kind && hom.fk == bc_top.fk &&
+         mg::updown_ok(g, bc_top);
+}
+
+bool use_pairs(const mg_ctx* c) {
+  return c->opts.leg_pairs == 1 || (c->opts.leg_pairs == 0 && c->pairs_faster);
+}
+
+// `cycles` V(1,1) cycles (Algorithm 1) on FP32 level l from a zero correction,
+// with every up leg but the last fused with the next cycle's down leg: one
+// pass reads u, f and the coarse correction and writes u and the next coarse
+// right-hand side, where two passes would move u and f twice.
+void vcycles_paired(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, int cycles,
+                    cudaStream_t s) {
+  const Grid g = level_grid(c, l);
+  const double h = level_h(c, l), om = c->opts.omega;
+  const bool fin = (l == c->L - 1);
+  auto swap_level = [&]() { std::swap(c->u32[l], c->u32b[l]); };
+  {
+    KTimer t(c, MG_K_FUSED_DOWN0, fin, s);
+    check(c, mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
+                                   om, true, s, c->cfg_down[l]),
+          "fused down");
+    swap_level();
+  }
+  coarse_correction(c, l, hom, s);
+  for (int k = 1; k < cycles; ++k) {
+    {
+      KTimer t(c, MG_K_FUSED_UPDOWN, fin, s);
+      check(c, mg::launch_fused_updown(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1],
+                                       c->f32[l - 1], g, h, bc_top, om, s, c->cfg_ud[l]),
+            "fused up-down");
+      swap_level();
+    }
+    coarse_correction(c, l, hom, s);
+  }
+  KTimer t(c, MG_K_FUSED_UP, fin, s);
+  check(c, mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc_top, om,
+                               s, c->cfg_up[l]),
+        "fused up");
+  swap_level();
 }
 
 template <typename T>
@@ -652,6 +723,9 @@ void inner_solve_launches(mg_ctx* c, const Bc& hom, const Bc& coarse, cudaStream
   for (int l = 0; l < c->L; ++l) bcs[l] = hom;
   if (c->opts.inner_fmg) {
     fmg<float>(c, P, bcs, coarse, s);
+  } else if (use_pairs(c) && pairs_ok(c, F, hom, coarse, 1 + c->opts.inner_cycles)) {
+    vcycles_paired(c, F, hom, coarse, 1 + c->opts.inner_cycles, s);
+    return;
   } else {
     vcycle<float>(c, P, F, hom, coarse, true, s);
   }
@@ -933,6 +1007,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (o.outer_fixed != 0 && o.outer_fixed != 1) return MG_ERR_ARG;
   if (o.fas != 0 && (o.fas != 1 || o.prec != MG_FP64)) return MG_ERR_ARG;
   if (o.coarse_literal != 0 && o.coarse_literal != 1) return MG_ERR_ARG;
+  if (o.leg_pairs < 0 || o.leg_pairs > 2) return MG_ERR_ARG;
   if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;
@@ -946,7 +1021,14 @@ mg_status validate_opts(const mg_opts& o) {
 // wins.  Results are kept per process, keyed by device and problem shape, so
 // every context of that shape launches identically (and gives identical
 // bits); with MG_TUNE_CACHE naming a file they also persist across runs.
-enum TuneKind { TUNE_DOWN = 0, TUNE_UP = 1, TUNE_SMOOTH = 2, TUNE_FX = 3 };
+enum TuneKind {
+  TUNE_DOWN = 0,
+  TUNE_UP = 1,
+  TUNE_SMOOTH = 2,
+  TUNE_FX = 3,
+  TUNE_UD = 4,      // shape of the fused up-down pass
+  TUNE_UD_WIN = 5   // cz = 1 when that pass beat the two legs it replaces
+};
 
 struct TuneKey {
   int sms, major, minor, kind, nx, ny, nz, periodic;
@@ -1090,6 +1172,57 @@ void autotune(mg_ctx* c, cudaStream_t s) {
         }
         (kind == TUNE_DOWN ? c->cfg_down : kind == TUNE_UP ? c->cfg_up : c->cfg_smooth)[l] = best;
       }
+      // the fused up-down pass of the finest level's inner cycles
+      if (l == F && c->opts.leg_pairs != 2 && pairs_ok(c, l, hom, hom, 2)) {
+        const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, TUNE_UD, g.nx, g.ny,
+                          g.nz, periodic};
+        mg::TileCfg best;
+        auto hit = g_tune.find(key);
+        if (hit != g_tune.end()) {
+          best = hit->second;
+        } else {
+          float best_ms = 1e30f;
+          for (int ty : {16, 32})
+            for (int cz : {16, 32, 64, 128}) {
+              const mg::TileCfg cand{64, cz, ty};
+              if (cz > g.nz || !mg::updown_cfg_ok(g, cand)) continue;
+              const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+                return mg::launch_fused_updown(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1],
+                                               c->f32[l - 1], g, h, hom, om, s, cand);
+              });
+              if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+              }
+            }
+          tune_store_locked(key, best);
+        }
+        c->cfg_ud[l] = best;
+        // fuse the legs only where the fused pass is the faster (its halo
+        // recomputation can cost more than the bytes it saves)
+        const TuneKey wkey{prop.multiProcessorCount, prop.major, prop.minor, TUNE_UD_WIN, g.nx,
+                           g.ny, g.nz, periodic};
+        auto whit = g_tune.find(wkey);
+        if (whit != g_tune.end()) {
+          c->pairs_faster = whit->second.cz == 1;
+        } else {
+          const float ud_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+            return mg::launch_fused_updown(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1],
+                                           c->f32[l - 1], g, h, hom, om, s, best);
+          });
+          const float legs_ms =
+              time_launches(c, s, reps, flush, flush_bytes, [&]() {
+                return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g,
+                                             h, hom, om, false, s, c->cfg_down[l]);
+              }) +
+              time_launches(c, s, reps, flush, flush_bytes, [&]() {
+                return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h,
+                                           hom, om, s, c->cfg_up[l]);
+              });
+          c->pairs_faster = ud_ms < legs_ms;
+          tune_store_locked(wkey, mg::TileCfg{0, c->pairs_faster ? 1 : 0, 0});
+        }
+      }
     }
   }
   const Grid g = level_grid(c, F);
@@ -1196,7 +1329,8 @@ mg_status mg_ctx_autotune(mg_ctx* c, void* stream) {
 mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, int* ty, int* cz) {
   if (!c || !tx || !ty || !cz || level < 0 || level >= c->L) return MG_ERR_ARG;
   mg::TileCfg v;
-  if (kernel == MG_K_FUSED_DOWN) v = c->cfg_down[level];
+  if (kernel == MG_K_FUSED_DOWN || kernel == MG_K_FUSED_DOWN0) v = c->cfg_down[level];
+  else if (kernel == MG_K_FUSED_UPDOWN) v = c->cfg_ud[level];
   else if (kernel == MG_K_FUSED_UP) v = c->cfg_up[level];
   else if (kernel == MG_K_SOR) v = c->cfg_smooth[level];
   else if (kernel == MG_K_OUTER_RESIDUAL) v = mg::TileCfg{0, level == c->L - 1 ? c->fx_cz : 0};
@@ -1453,14 +1587,27 @@ namespace mg {
 
 mg_status solve_host_copies(mg_ctx* c, const double* rho, double four_pi_G, double tol,
                             double* phi, double* hist, int hist_cap, int* n_hist,
-                            cudaStream_t s) {
+                            cudaStream_t s, double* copy_ms) {
   if (!c || !rho || !phi) return MG_ERR_ARG;
   const size_t bytes = (size_t)level_grid(c, c->L - 1).cells() * sizeof(double);
+  // events around the two copies (timed only when asked)
+  cudaEvent_t ev[4] = {};
+  struct Events {
+    cudaEvent_t* e;
+    ~Events() {
+      for (int k = 0; k < 4; ++k)
+        if (e[k]) cudaEventDestroy(e[k]);
+    }
+  } events{ev};
   try {
     check(c, cudaSetDevice(c->device), "cudaSetDevice");
+    if (copy_ms)
+      for (cudaEvent_t& e : ev) check(c, cudaEventCreate(&e), "cudaEventCreate");
     if (!c->rho_dev_own) c->rho_dev_own = dalloc<double>(c, bytes / sizeof(double));
     if (!c->phi_dev_own) c->phi_dev_own = dalloc<double>(c, bytes / sizeof(double));
+    if (copy_ms) check(c, cudaEventRecord(ev[0], s), "record");
     check(c, cudaMemcpyAsync(c->rho_dev_own, rho, bytes, cudaMemcpyHostToDevice, s), "H2D rho");
+    if (copy_ms) check(c, cudaEventRecord(ev[1], s), "record");
     if (!c->opts.mode_fmg)
       check(c, cudaMemcpyAsync(c->phi_dev_own, phi, bytes, cudaMemcpyHostToDevice, s), "H2D phi");
   } catch (const Fail& f) {
@@ -1474,8 +1621,17 @@ mg_status solve_host_copies(mg_ctx* c, const double* rho, double four_pi_G, doub
     return st;
   }
   try {
+    if (copy_ms) check(c, cudaEventRecord(ev[2], s), "record");
     check(c, cudaMemcpyAsync(phi, c->phi_dev_own, bytes, cudaMemcpyDeviceToHost, s), "D2H phi");
+    if (copy_ms) check(c, cudaEventRecord(ev[3], s), "record");
     check(c, cudaStreamSynchronize(s), "sync");
+    if (copy_ms) {
+      float a = 0.f, b = 0.f;
+      check(c, cudaEventElapsedTime(&a, ev[0], ev[1]), "elapsed");
+      check(c, cudaEventElapsedTime(&b, ev[2], ev[3]), "elapsed");
+      copy_ms[0] = a;
+      copy_ms[1] = b;
+    }
   } catch (const Fail& f) {
     cudaStreamSynchronize(s);
     return f.st;
@@ -1680,6 +1836,86 @@ mg_status mg_op_convert(int kind, long long n, const void* in, void* out, void* 
     return MG_ERR_ARG;
   }
   return op_result(mg::launch_convert(kind, n, in, out, (cudaStream_t)stream), "convert");
+}
+
+// A rule per face read from six kinds (periodic in pairs, fixed, zero
+// gradient); false when the kinds are not such a rule.
+static bool face_rule(const int* kinds, Bc* out) {
+  if (!kinds) return false;
+  int fk = 0;
+  for (int q = 0; q < 6; ++q) {
+    if (kinds[q] != MG_BC_PERIODIC && kinds[q] != MG_BC_FIXED && kinds[q] != MG_BC_ZEROGRAD)
+      return false;
+    fk |= kinds[q] << (2 * q);
+  }
+  for (int a = 0; a < 3; ++a)
+    if ((kinds[2 * a] == MG_BC_PERIODIC) != (kinds[2 * a + 1] == MG_BC_PERIODIC)) return false;
+  *out = Bc{mg::BC_MIXED, 0.0, nullptr, fk};
+  return true;
+}
+
+mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* face_bc,
+                          double omega, int zero_guess, int tx, int ty, int cz,
+                          const float* u_in, float* u_out, const float* f, const float* ec,
+                          float* fc, void* stream) {
+  Bc b{};
+  const Grid g{nx, ny, nz};
+  const mg::TileCfg cfg{tx, cz, ty};
+  bool ok = leg >= 0 && leg <= 2 && face_rule(face_bc, &b) && h > 0.0 && omega > 0.0 &&
+            omega < 2.0 && u_out && f && (u_in || (leg == 0 && zero_guess)) && u_in != u_out &&
+            (leg == 1 || fc != nullptr) && (leg == 0 || ec != nullptr) &&
+            (leg == 0 || !zero_guess);
+  if (ok) {
+    b = mg::collapse_homogeneous(b);
+    ok = mg::fused_ok(g, b) && mg::fused_cfg_ok(g, cfg) && (tx == 0 || tx == 32 || tx == 64) &&
+         (ty == 0 || ty == 16 || ty == 32) && cz >= 0;
+    if (leg == 2) ok = mg::updown_ok(g, b) && mg::updown_cfg_ok(g, cfg);
+  }
+  if (!ok) {
+    g_err = "mg_op_fused_leg: invalid argument, or a grid or shape the fused kernels do not take";
+    return MG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (leg == 0)
+    e = mg::launch_fused_down(u_in, u_out, f, fc, g, h, b, omega, zero_guess != 0, s, cfg);
+  else if (leg == 1)
+    e = mg::launch_fused_up(u_in, u_out, f, ec, g, h, b, omega, s, cfg);
+  else
+    e = mg::launch_fused_updown(u_in, u_out, f, ec, fc, g, h, b, omega, s, cfg);
+  return op_result(e, "fused_leg");
+}
+
+mg_status mg_op_fx_step(int nx, int ny, int nz, const int* face_bc, const double* faces_dev,
+                        double two_pow_S, int cz, const long long* phi_in, const float* e,
+                        float c, const long long* F, long long* phi_out, float factor, float* r32,
+                        void* stream) {
+  Bc b{};
+  const Grid g{nx, ny, nz};
+  bool ok = face_rule(face_bc, &b) && mg::fx_step_ok(g) && nx >= 2 && ny >= 2 && nz >= 2 &&
+            e && phi_out && F && r32 && phi_in != phi_out && (cz == 0 || cz >= mg::kFxMinCz) &&
+            std::isfinite(two_pow_S) && two_pow_S > 0.0;
+  if (!ok) {
+    g_err = "mg_op_fx_step: invalid argument, or a grid the fixed-point step does not take";
+    return MG_ERR_ARG;
+  }
+  b.faces = faces_dev;
+  if (!faces_dev) b = mg::collapse_homogeneous(b);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = mg::fx_step_blocks(g, cz);
+  double* partials = nullptr;
+  int* flag = nullptr;
+  cudaError_t err = cudaMalloc(&partials, sizeof(double) * (size_t)nb);
+  if (err == cudaSuccess) err = cudaMalloc(&flag, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  int nb_out = 0;
+  if (err == cudaSuccess)
+    err = mg::launch_fx_step(phi_in, phi_out, e, c, F, r32, g, b, two_pow_S, factor, partials, nb,
+                             flag, &nb_out, s, cz);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(partials);
+  cudaFree(flag);
+  return op_result(err, "fx_step");
 }
 
 mg_status mg_op_multipole_moments(int nx, int ny, int nz, double h, const double* rho, int lmax,

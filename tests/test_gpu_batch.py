@@ -77,3 +77,38 @@ def test_batch_rejects_unsupported_options():
         mg.Batch([8], [0.1], [mg.PERIODIC], prec=mg.FP64)
     with pytest.raises(mg.MGError):
         mg.Batch([12], [0.1], [mg.PERIODIC])
+
+
+def test_barrier_limit_runs_out_and_the_batch_recovers():
+    """A grid-wide barrier wait of at most one clock cycle cannot see every
+    block arrive: the waiting blocks give up, set the error flag and return,
+    so the solve ends with MG_ERR_TIMEOUT instead of hanging.  With the
+    default limit back, the same batch solves again and gives the bits of a
+    batch that never timed out."""
+    specs = [(16, mg.PERIODIC), (32, mg.FIXED), (16, mg.ZEROGRAD), (32, mg.PERIODIC)]
+    rhos, fixed = make_case(specs, seed=7)
+    sizes = [n for n, _ in specs]
+    rd = [torch.from_numpy(r).cuda() for r in rhos]
+    args = (sizes, [1.0 / n for n in sizes], [bc for _, bc in specs], fixed)
+    with mg.Batch(*args) as ref_b:
+        ref_phi = [torch.zeros_like(r) for r in rd]
+        st, ref_h, _ = ref_b.solve(rd, ref_phi, 1.0, 1e-10)
+        assert st == 0
+    with mg.Batch(*args) as b:
+        phis = [torch.zeros_like(r) for r in rd]
+        b.set_barrier_limit(1)
+        timeouts = 0
+        for _ in range(3):
+            try:
+                b.solve(rd, phis, 1.0, 1e-10)
+            except mg.MGError as e:
+                assert e.status == 6, e  # MG_ERR_TIMEOUT, never a CUDA error
+                timeouts += 1
+        assert timeouts >= 1
+        with pytest.raises(mg.MGError):
+            b.set_barrier_limit(-1)
+        b.set_barrier_limit(4_000_000_000)
+        st, h, _ = b.solve(rd, phis, 1.0, 1e-10)
+        assert st == 0 and b.graph
+        for p, q, ha, hb in zip(phis, ref_phi, h, ref_h):
+            assert torch.equal(p, q) and np.array_equal(ha, hb)

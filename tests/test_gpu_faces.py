@@ -28,6 +28,10 @@ CASES = {
     "box": ((Z, F, F, Z, F, Z), (0, -0.4, 0.1, 0, 0.7, 0)),
     "channel": ((P, P, Z, Z, Z, Z), (0,) * 6),  # no zero point: means removed
     "zero_walls": ((P, P, F, F, F, F), (0,) * 6),  # homogeneous: fast source path off too
+    # z periodic with walls across x or y: periodic-axis masks 4, 5 and 6
+    "z_pipe": ((F, F, Z, Z, P, P), (0.2, -0.1, 0, 0, 0, 0)),  # periodic in z only
+    "xz_sheet": ((P, P, F, Z, P, P), (0, 0, 0.4, 0, 0, 0)),  # periodic in x and z
+    "yz_sheet": ((Z, F, P, P, P, P), (0, -0.3, 0, 0, 0, 0)),  # periodic in y and z
 }
 
 

@@ -263,6 +263,8 @@ def test_autotuned_shapes_keep_the_result(bc, n):
         width = n >> (n.bit_length() - 1 - l)
         assert tx in (32, 64) and width % tx == 0 and cz in (8, 16, 32, 64) and cz <= width
         assert ty in (16, 32) and width % ty == 0
+    for l, (tx, ty, cz) in cfg["fused_updown"].items():  # the finest level's paired cycles
+        assert l == n.bit_length() - 1 and tx == 64 and ty in (16, 32) and cz in (16, 32, 64, 128)
     assert list(cfg["outer_residual"]) == [n.bit_length() - 1]
     assert cfg["outer_residual"][n.bit_length() - 1][2] in (4, 8, 16, 32, 64)
     assert torch.equal(p0, p1)
@@ -438,3 +440,46 @@ def test_non_cubic_shape_rules():
         mg.Solver((8, 16, 16), 0.1, mg.PERIODIC)
     with pytest.raises(mg.MGError):
         mg.Solver((12, 8, 8), 0.1, mg.PERIODIC)
+
+
+@pytest.mark.parametrize("bc,n", [(mg.PERIODIC, 64), (mg.FIXED, 128), (mg.ZEROGRAD, 64),
+                                  (mg.OPEN, 64)])
+def test_paired_legs_give_the_same_bits(bc, n):
+    """The finest level's inner V-cycles with each up leg fused to the next
+    cycle's down leg (one pass, two SMOOTH steps) run the same per-cell
+    arithmetic as the two legs apart: the same phi and residual history, bit
+    for bit."""
+    rho, fpg = source(n, bc, seed=31)
+    a = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED, leg_pairs=1)
+    b = gpu_solve(rho, bc, fpg, 1e-10, prec=mg.MIXED, leg_pairs=2)
+    assert a[2] == b[2] == 0
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert a[3] < b[3]  # fewer launches: one pass per pair of legs
+
+
+@pytest.fixture(scope="module")
+def headline_reference():
+    """The oracle's converged solution of the 512^3 periodic workload (64
+    Gaussian blobs, seed 20230227): the FP64 solve iterated to its rounding
+    floor on the host cores."""
+    n = 512
+    rho = inputs.gaussian_blobs(n, 64, seed=20230227)
+    ref = orc.solve(rho, 1.0 / n, mg.PERIODIC, tol=0.0, max_cycles=40)
+    assert ref.ok, ref.hist
+    return rho, ref
+
+
+def test_headline_512_mixed_after_autotune_matches_converged_oracle(headline_reference):
+    """The configuration the throughput is quoted on, in the launch shapes the
+    bench times: 512^3 periodic blobs, mixed precision to 1e-10 after
+    autotune(), element by element against the converged FP64 oracle."""
+    rho, ref = headline_reference
+    n = rho.shape[0]
+    rd = torch.from_numpy(rho).cuda()
+    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED) as s:
+        s.autotune()
+        phi, hist, st = s.solve(rd, 1.0, 1e-10)
+        tiles = s.tile_configs()
+    assert st == 0 and hist[-1] < 1e-10, (st, hist)
+    assert n.bit_length() - 1 in tiles["fused_down"]  # tuned shapes on the finest level
+    assert emax(phi.cpu().numpy(), ref.phi) <= 1e-9
