@@ -318,6 +318,79 @@ def run_open_sphere(args, stream):
     return out
 
 
+def run_sinusoid(args, stream):
+    """The 64^3 periodic sinusoid rho = sin 2 pi x sin 2 pi y sin 2 pi z with
+    4 pi G = 1 (Sec. 4.1.1 test), FMG + V(1,1) to 1e-10, FP64 and mixed:
+    latency of one solve, and the error against the exact discrete solution
+    f / lambda, lambda = -(12 / h^2) sin^2(pi h)."""
+    import numpy as np
+    import torch
+
+    import paper_2302_13903_gb300 as mg
+    from paper_2302_13903_gb300 import inputs
+    n = 64
+    h = 1.0 / n
+    rho_h = inputs.sinusoid(n)
+    exact = rho_h / (-(12.0 / h ** 2) * math.sin(math.pi * h) ** 2)
+    rho = torch.from_numpy(rho_h).cuda()
+    phi = torch.zeros_like(rho)
+    out = {"workload": "64^3 periodic sinusoid, 4 pi G = 1, FMG + V(1,1) to 1e-10"}
+    for name, prec in (("fp64", mg.FP64), ("mixed", mg.MIXED)):
+        with mg.Solver(n, h, mg.PERIODIC, prec=prec) as s:
+            for _ in range(3):
+                _, hist, st = s.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(args.sin_steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                _, hist, st = s.solve(rho, 1.0, TOL, phi=phi, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+        p = phi.cpu().numpy()
+        ms = statistics.median(ts)
+        out[name] = {"ms_per_solve_median": ms, "ms_p99": sorted(ts)[int(0.99 * (len(ts) - 1))],
+                     "value": n ** 3 / (ms * 1e-3), "unit": UNIT, "status": st,
+                     "residual_checks": len(hist), "final_ratio": float(hist[-1]),
+                     "max_rel_error_vs_exact_discrete":
+                         float(np.abs(p - exact).max() / np.abs(exact).max())}
+    return out
+
+
+def batch_roofline(specs, hists, phase_ms, inner_cycles, peak):
+    """Algorithmic bytes of the batched solve's fused down and up phases (every
+    level of 32^3 and up; levels below run in the single-CTA bottom phase),
+    from each grid's own count of outer iterations, against their device
+    time.  FP32 levels (w = 4): down leg 3w + w/8 (2w + w/8 from a zero
+    start), up leg 3w + w/8."""
+    w = 4.0
+    down = up = 0.0
+    for spec, hist in zip(specs, hists):
+        n, outer = spec["n"], len(hist)
+        levels = []
+        m = n
+        while m >= 32:
+            levels.append(m)
+            m //= 2
+        if not levels:
+            continue
+        cycles = outer * (1 + inner_cycles)
+        fin = levels[0] ** 3
+        down += outer * ((2 * w + w / 8) + inner_cycles * (3 * w + w / 8)) * fin
+        up += cycles * (3 * w + w / 8) * fin
+        for m in levels[1:]:
+            down += cycles * (2 * w + w / 8) * m ** 3
+            up += cycles * (3 * w + w / 8) * m ** 3
+    out = {}
+    for name, b in (("down", down), ("up", up)):
+        ms = phase_ms.get(name, 0.0)
+        if ms > 0:
+            gbs = b / (ms * 1e-3) / 1e9
+            out[name] = {"algorithmic_bytes": b, "ms": ms, "achieved_gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 def run_per_face(args, stream):
     """512^3 slab: periodic in x and y, phi = 0 on both z faces (a rule per
     face, Sec. 2.3.6), the headline's 64 blobs, to 1e-10 in FP64 and in mixed
@@ -379,8 +452,11 @@ def run_batched(args, ws, rank, stream):
         cells = b.cells
         graph = b.graph
         phases = {k: round(v, 3) for k, v in b.phase_ms().items() if v > 0}
+        inner_cycles = b.opts.inner_cycles
     total = sum(s["n"] ** 3 for s in specs)
-    return {"grids": len(specs), "cells": total, "ms_per_solve": ms,
+    peak, _ = peaks()
+    roof = batch_roofline(mine, hists, phases, inner_cycles, peak)
+    return {"grids": len(specs), "cells": total, "ms_per_solve": ms, "roofline": roof,
             "value": total / (ms * 1e-3), "unit": UNIT, "graph": graph,
             "converged": int(sum(1 for x in sts if x == 0)), "of": len(sts),
             "max_outer_iterations": max(len(h) for h in hists), "rank_cells": cells,
@@ -431,10 +507,12 @@ def main():
     ap.add_argument("--legs-steps", type=int, default=3,
                     help="timed solves with separate finest-level legs (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed batched solves (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds of arrivals per serving rate (0: skip)")
     ap.add_argument("--face-steps", type=int, default=3,
                     help="timed solves of the per-face slab (0: skip)")
+    ap.add_argument("--sin-steps", type=int, default=20,
+                    help="timed solves of the 64^3 sinusoid per precision (0: skip)")
     ap.add_argument("--open-steps", type=int, default=3,
                     help="timed solves of the 256^3 open-boundary sphere per precision (0: skip)")
     args = ap.parse_args()
@@ -690,6 +768,7 @@ def main():
         solver.close()
 
     open_sphere = run_open_sphere(args, stream) if args.open_steps > 0 else None
+    sinusoid = run_sinusoid(args, stream) if args.sin_steps > 0 else None
     per_face = run_per_face(args, stream) if args.face_steps > 0 else None
     batched = run_batched(args, ws, rank, stream) if args.batch_steps > 0 else None
     serving = run_serving(args) if args.serve_seconds > 0 and ws == 1 else None
@@ -728,6 +807,7 @@ def main():
             "separate_legs": legs,
             "with_gravity": grav,
             "open_sphere": open_sphere,
+            "sinusoid_64": sinusoid,
             "per_face": per_face,
             "batched": batched,
             "serving": serving,

@@ -402,7 +402,10 @@ mg_status mg_batch_create(int n, const int *dims, const double *dx, const mg_bc 
                           const double *fixed_values, const mg_opts *opts, mg_batch **batch);
 
 /* Solve every grid: rho_dev[g], phi_dev[g] are the FP64 device arrays of grid
- * g, four_pi_G[g] and tol[g] its constants (host arrays of n).  One persistent
+ * g, four_pi_G[g] and tol[g] its constants (host arrays of n).  rho_dev[g] =
+ * NULL leaves slot g out of this solve (phi_dev[g] is not touched, status[g]
+ * = MG_OK, n_hist[g] = 0); at least one grid must be given.  A grid's result
+ * does not depend on the other slots.  One persistent
  * cooperative kernel runs every phase of every grid; the first call captures
  * the upload of the per-grid arguments, the kernel and the download of the
  * results as a CUDA graph (so make it outside any capture of your own) and
@@ -434,6 +437,12 @@ int mg_batch_graph(const mg_batch *batch);
  * removal.
  * Synchronises the device.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
 mg_status mg_batch_phase_ms(mg_batch *batch, double *ms_by_type, int n_types);
+
+/* CTAs of the persistent launch: 0 (default) as many as fit on the device at
+ * once, else at most that many (fewer CTAs leave SMs to other streams' work,
+ * for a batch of small grids).  Takes effect at the next mg_batch_solve,
+ * which captures its CUDA graph again.  Errors: MG_ERR_ARG (blocks < 0). */
+mg_status mg_batch_set_blocks(mg_batch *batch, int blocks);
 
 /* Limit of one wait at the persistent kernel's grid-wide barriers, in GPU
  * clock cycles (default 4e9, about 2 s at 2 GHz); a wait that runs out makes
@@ -477,8 +486,15 @@ mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, 
  * waiting one up to 64 times, then the waiting one holds the next free slot.
  * Hierarchies stay resident between requests of the same key (cells, dx,
  * rule, fixed value, lmax).  Requests on different slots run concurrently on
- * the device; each result equals the result of the same request alone.  The
- * server is internally synchronised: any thread may submit, poll and wait.
+ * the device; each result equals the result of the same request alone.
+ * Continuous batching: requests of at most 64^3 cells with a periodic, fixed
+ * or zero-gradient rule (when the options allow mg_batch_create's solve) are
+ * served by batched hierarchies of up to 16 grids of one shape and rule (as
+ * many as the budget holds): the slot that takes one also takes the queued
+ * requests of that shape and rule and solves them in one persistent launch
+ * (mg_batch_solve), whatever their tolerances; a grid's result there does not
+ * depend on the others.  The server is internally synchronised: any thread
+ * may submit, poll and wait.
  * --------------------------------------------------------------------------- */
 typedef struct mg_server mg_server;
 
@@ -503,12 +519,13 @@ typedef struct {
   double queue_ms;       /* submission -> a slot took it */
   double solve_ms;       /* slot took it -> result in phi (stream synchronised) */
   double total_ms;       /* submission -> result: the request's latency */
-  double h2d_ms;         /* host arrays: device time of the copy of rho in (else 0) */
-  double d2h_ms;         /* host arrays: device time of the copy of phi out (else 0) */
+  double h2d_ms;         /* host arrays on a single hierarchy: device time of the  */
+  double d2h_ms;         /* copies of rho in and phi out (0 otherwise)              */
 } mg_result;
 
 typedef struct {
   long long submitted, completed, rejected, evictions, created, cells_completed;
+  long long batched;     /* requests solved in one batched launch with others */
   size_t budget_bytes, resident_bytes, peak_bytes; /* hierarchy bytes as mg_required_bytes */
   int queued, running, slots, resident;
 } mg_server_stats;

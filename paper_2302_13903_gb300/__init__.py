@@ -33,7 +33,7 @@ EXPORTS = [
     "mg_ctx_tile_config", "mg_batch_phase_ms", "mg_solve_gravity", "mg_op_gravity",
     "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
     "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error", "mg_op_convert",
-    "mg_op_fused_leg", "mg_op_fx_step", "mg_batch_set_barrier_limit",
+    "mg_op_fused_leg", "mg_op_fx_step", "mg_batch_set_barrier_limit", "mg_batch_set_blocks",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
            "correct", "source", "fused_down", "fused_up", "gravity", "fused_down0",
@@ -74,8 +74,8 @@ class ServerStats(ctypes.Structure):
         ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
         ("rejected", ctypes.c_longlong), ("evictions", ctypes.c_longlong),
         ("created", ctypes.c_longlong), ("cells_completed", ctypes.c_longlong),
-        ("budget_bytes", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t),
-        ("peak_bytes", ctypes.c_size_t), ("queued", ctypes.c_int), ("running", ctypes.c_int),
+        ("batched", ctypes.c_longlong), ("budget_bytes", ctypes.c_size_t),
+        ("resident_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("queued", ctypes.c_int), ("running", ctypes.c_int),
         ("slots", ctypes.c_int), ("resident", ctypes.c_int),
     ]
 
@@ -176,6 +176,8 @@ def lib():
             L.mg_batch_graph.restype = i
             L.mg_batch_set_barrier_limit.argtypes = [p, ctypes.c_longlong]
             L.mg_batch_set_barrier_limit.restype = i
+            L.mg_batch_set_blocks.argtypes = [p, i]
+            L.mg_batch_set_blocks.restype = i
             L.mg_batch_last_error.argtypes = [p]
             L.mg_batch_last_error.restype = ctypes.c_char_p
             L.mg_faces_count.argtypes = [i, i, i]
@@ -613,8 +615,9 @@ class Batch:
         """rhos, phis: lists of CUDA float64 tensors.  Returns (status, hists, statuses)."""
         import torch
         n = self.n
-        rp = np.array([_dptr(r, torch.float64) for r in rhos], dtype=np.uint64)
-        pp = np.array([_dptr(q, torch.float64) for q in phis], dtype=np.uint64)
+        # None in rhos leaves that slot out of this solve
+        rp = np.array([0 if r is None else _dptr(r, torch.float64) for r in rhos], dtype=np.uint64)
+        pp = np.array([0 if q is None else _dptr(q, torch.float64) for q in phis], dtype=np.uint64)
         fpg = np.broadcast_to(np.asarray(four_pi_G, dtype=np.float64), (n,)).copy()
         tl = np.broadcast_to(np.asarray(tol, dtype=np.float64), (n,)).copy()
         hist = np.zeros((n, hist_cap))
@@ -626,6 +629,12 @@ class Batch:
         if st in (3, 6):
             raise MGError(st, lib().mg_batch_last_error(self.ptr).decode())
         return st, [hist[g, : nh[g]].copy() for g in range(n)], sts
+
+    def set_blocks(self, blocks):
+        """CTAs of the persistent launch (0: all that fit)."""
+        st = lib().mg_batch_set_blocks(self.ptr, int(blocks))
+        if st != 0:
+            raise MGError(st, lib().mg_batch_last_error(self.ptr).decode())
 
     def set_barrier_limit(self, cycles):
         """Clock cycles one grid-wide barrier wait may take before the solve

@@ -25,9 +25,10 @@ struct Key {
   int n = 0, bc = 0, lmax = 0;
   double dx = 0.0, fixed_value = 0.0;
   bool host = false;  // requests with host buffers: the hierarchy holds device copies too
+  int slots = 0;      // > 0: a batched hierarchy of that many grids of this shape
   bool operator==(const Key& o) const {
     return n == o.n && bc == o.bc && lmax == o.lmax && dx == o.dx &&
-           fixed_value == o.fixed_value && host == o.host;
+           fixed_value == o.fixed_value && host == o.host && slots == o.slots;
   }
 };
 

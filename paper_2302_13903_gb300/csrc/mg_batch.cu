@@ -66,6 +66,7 @@ struct GridDev {
   // state
   double mean, fnorm, rn, scale, prev, d0;
   int stalls, active, status, nh, cycles;
+  int skip;  // this grid has no request in this solve: every phase passes it by
   // fixed-point outer loop: phi and h^2 f as integers scaled by two_S
   double maxf, two_S;
   int S;            // two_S = 2^S
@@ -621,7 +622,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
       const Item I = c.items[P.first + it];
       GridDev& g = c.grids[I.grid];
       const bool has_mean = g.bc == BC_PERIODIC || g.bc == BC_ZEROGRAD;
-      const bool run = P.type == PH_PSUM ? has_mean : (P.type > PH_PSUM || g.active);
+      const bool run =
+          !g.skip && (P.type == PH_PSUM ? has_mean : (P.type > PH_PSUM || g.active));
       if (!run) continue;
       switch (P.type) {
         case PH_SRC: chunk_item<PH_SRC>(c, g, I.a); break;
@@ -785,7 +787,7 @@ struct mg_batch {
   std::vector<Phase> host_phases;
   int* h_err = nullptr;
   int nphases = 0, nitems = 0, nchunks = 0, ntiles = 0, hist_cap = 64;
-  int blocks = 0;
+  int blocks = 0, max_blocks = 0;  // CTAs of the persistent launch; all that fit at once
   long long cells = 0;
   // the per-solve work captured once as a CUDA graph and replayed
   bool graph_tried = false;
@@ -1067,7 +1069,7 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
     free_batch(b);
     return MG_ERR_OOM;
   }
-  b->blocks = per_sm * sms;
+  b->blocks = b->max_blocks = per_sm * sms;
   *out = b;
   return MG_OK;
 }
@@ -1080,16 +1082,25 @@ mg_status mg_batch_solve(mg_batch* b, const double* const* rho, const double* fo
     return MG_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  int used = 0;
   for (int g = 0; g < b->ngrids; ++g) {
-    if (!rho[g] || !phi[g] || !(tol[g] >= 0.0)) {
+    if (!rho[g]) continue;  // a slot without a grid this time
+    ++used;
+    if (!phi[g] || !(tol[g] >= 0.0)) {
       g_batch_err = "mg_batch_solve: invalid per-grid argument";
       return MG_ERR_ARG;
     }
+  }
+  if (used == 0) {
+    g_batch_err = "mg_batch_solve: no grid to solve";
+    return MG_ERR_ARG;
+  }
+  for (int g = 0; g < b->ngrids; ++g) {
     GridDev d = b->host_grids[g];
     d.rho = rho[g];
-    d.phi = phi[g];
-    d.fpg = four_pi_G[g];
-    d.tol = tol[g];
+    d.phi = rho[g] ? phi[g] : nullptr;
+    d.fpg = rho[g] ? four_pi_G[g] : 0.0;
+    d.tol = rho[g] ? tol[g] : 0.0;
     d.mean = 0.0;
     d.fnorm = d.rn = 0.0;
     d.scale = 1.0;
@@ -1108,6 +1119,11 @@ mg_status mg_batch_solve(mg_batch* b, const double* const* rho, const double* fo
     d.in_fx = 0;
     d.fxbad = 0;
     d.cur = 0;
+    d.skip = rho[g] ? 0 : 1;
+    if (d.skip) {
+      d.active = 0;
+      d.status = MG_OK;
+    }
     b->h_grids[g] = d;
   }
   cudaError_t e = cudaSuccess;
@@ -1182,6 +1198,21 @@ mg_status mg_batch_phase_ms(mg_batch* b, double* ms_by_type, int n_types) {
     if (ty < n_types) ms_by_type[ty] += (double)(t[(size_t)ph] - last) * 1e-6;
     last = t[(size_t)ph];
   }
+  return MG_OK;
+}
+
+mg_status mg_batch_set_blocks(mg_batch* b, int blocks) {
+  if (!b || blocks < 0) {
+    g_batch_err = "mg_batch_set_blocks: invalid argument";
+    return MG_ERR_ARG;
+  }
+  const int cap = b->max_blocks;
+  b->blocks = blocks == 0 || blocks > cap ? cap : blocks;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->graph_tried = false;
   return MG_OK;
 }
 

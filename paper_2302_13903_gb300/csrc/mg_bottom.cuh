@@ -292,16 +292,23 @@ __host__ __device__ inline int cells_upto(const BottomArgs<T>& a) {
 // of shared memory, not of L2.  f[top] is copied in, and u[top] when its start
 // value is used (load_u); u[top] is copied back out.  Lower levels are
 // scratch of the cycle (their f comes from restriction, their u starts at 0).
+// The copy of the arguments with the shared-memory pointers lives in shared
+// memory too: its per-level arrays are indexed by a run-time level, which in
+// a thread's own copy would put them in local memory.
 template <typename T, typename Body>
 __device__ void in_shared(const BottomArgs<T>& a, T* smem, bool load_u, Body body) {
-  BottomArgs<T> b = a;
-  const int total = cells_upto(a);
-  int off = 0;
-  for (int l = 0; l <= a.top; ++l) {
-    b.u[l] = smem + off;
-    b.f[l] = smem + total + off;
-    off += a.n[l] * a.n[l] * a.n[l];
+  __shared__ BottomArgs<T> b;
+  if (threadIdx.x == 0) {
+    b = a;
+    const int total = cells_upto(a);
+    int off = 0;
+    for (int l = 0; l <= a.top; ++l) {
+      b.u[l] = smem + off;
+      b.f[l] = smem + total + off;
+      off += a.n[l] * a.n[l] * a.n[l];
+    }
   }
+  __syncthreads();
   const int top = a.top, ct = a.n[top] * a.n[top] * a.n[top];
   for (int t = threadIdx.x; t < ct; t += blockDim.x) {
     b.f[top][t] = a.f[top][t];

@@ -41,6 +41,13 @@ using mg::admission::Pool;
 
 constexpr int kHistCap = 64;
 constexpr int kMaxBypass = 64;
+// Requests of at most kBatchMaxN^3 cells with a periodic, fixed or
+// zero-gradient rule on device arrays go through batched hierarchies of
+// kBatchSlots grids: a slot that takes one also takes the queued requests of
+// the same shape and rule (up to kBatchSlots in all) and solves them in one
+// persistent launch.
+constexpr int kBatchMaxN = 64;
+constexpr int kBatchSlots = 16;
 
 thread_local std::string g_server_err;
 
@@ -58,6 +65,24 @@ struct Request {
   double copy_ms[2] = {};  // host arrays: device time of the copies in and out
   double hist[kHistCap] = {};
 };
+
+// A resident hierarchy of the pool: a solver context, or a batch of
+// kBatchSlots grids of one shape (Key::slots > 0).
+struct Hier {
+  mg_ctx* ctx = nullptr;
+  mg_batch* batch = nullptr;
+  // a batch serving host arrays: each slot's device copies of rho and phi
+  std::vector<double*> dev;
+};
+
+void destroy_hier(void* p) {
+  Hier* h = static_cast<Hier*>(p);
+  if (!h) return;
+  if (h->batch) mg_batch_destroy(h->batch);
+  if (h->ctx) mg_destroy(h->ctx);
+  for (double* d : h->dev) cudaFree(d);
+  delete h;
+}
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
@@ -90,6 +115,7 @@ struct mg_server {
   mg::tickets::Book<Request> reqs;
   long long next_ticket = 1;
   long long submitted = 0, completed = 0, rejected = 0, cells_completed = 0;
+  long long batched = 0;  // requests solved in a batched launch with others
   int running = 0;
   int head_bypassed = 0;
   unsigned long long gen = 0;  // bumped on every submission and completion
@@ -100,6 +126,99 @@ struct mg_server {
 
 namespace {
 
+// Whether the server's options allow the batched solve (mg_batch_create's
+// conditions).
+bool batch_opts_ok(const mg_opts& o) {
+  return o.prec == MG_MIXED && o.pre == 1 && o.post == 1 && o.mode_fmg == 1 &&
+         o.inner_fmg == 0 && o.max_cycles <= 64 && o.inner_cycles <= 16 && o.coarse_literal == 0;
+}
+
+// Create the hierarchy of a CREATE decision for request r.
+mg_status create_hier(mg_server* S, const Request* r, cudaStream_t stream, Hier** out) {
+  Hier* h = new Hier;
+  mg_opts o = S->opts;
+  o.lmax = r->req.lmax;
+  o.fixed_value = r->req.fixed_value;
+  mg_status st;
+  if (r->key.slots > 0) {
+    const int k = r->key.slots;
+    std::vector<int> dims(3 * (size_t)k, r->req.nx);
+    std::vector<double> dx((size_t)k, r->req.dx), fv((size_t)k, r->req.fixed_value);
+    std::vector<mg_bc> bcs((size_t)k, r->req.bc);
+    st = mg_batch_create(k, dims.data(), dx.data(), bcs.data(), fv.data(), &o, &h->batch);
+    // one CTA per SM: the small grids need no more, and the other slots'
+    // solves keep room on every SM
+    if (st == MG_OK) st = mg_batch_set_blocks(h->batch, mg::sm_count());
+    if (st == MG_OK && r->key.host) {  // device copies of each slot's rho and phi
+      const size_t bytes = sizeof(double) * (size_t)r->req.nx * r->req.ny * r->req.nz;
+      for (int g = 0; g < 2 * k && st == MG_OK; ++g) {
+        double* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) {
+          cudaGetLastError();
+          st = MG_ERR_OOM;
+        } else {
+          h->dev.push_back(d);
+        }
+      }
+    }
+  } else {
+    st = mg_create(r->req.nx, r->req.ny, r->req.nz, r->req.dx, r->req.bc, &o, &h->ctx);
+    if (st == MG_OK) mg_ctx_autotune(h->ctx, stream);  // shapes, cached per process
+  }
+  if (st != MG_OK) {
+    destroy_hier(h);
+    h = nullptr;
+  }
+  *out = h;
+  return st;
+}
+
+// One batched solve of the requests in `group` (same key) on hierarchy h.
+// Host arrays are copied in and out on the slot's stream around the launch.
+void solve_group(Hier* h, std::vector<Request*>& group, cudaStream_t stream) {
+  const int k = (int)group.size();
+  const int slots = group[0]->key.slots;
+  const bool host = group[0]->key.host;
+  const size_t bytes =
+      sizeof(double) * (size_t)group[0]->req.nx * group[0]->req.ny * group[0]->req.nz;
+  cudaError_t ce = cudaSuccess;
+  std::vector<const double*> rho((size_t)slots, nullptr);
+  std::vector<double*> phi((size_t)slots, nullptr);
+  std::vector<double> fpg((size_t)slots, 0.0), tol((size_t)slots, 0.0);
+  std::vector<double> hist((size_t)slots * kHistCap, 0.0);
+  std::vector<int> nh((size_t)slots, 0);
+  std::vector<mg_status> sts((size_t)slots, MG_OK);
+  for (int g = 0; g < k; ++g) {
+    const Request* r = group[(size_t)g];
+    rho[(size_t)g] = host ? h->dev[2 * (size_t)g] : r->req.rho;
+    phi[(size_t)g] = host ? h->dev[2 * (size_t)g + 1] : r->req.phi;
+    fpg[(size_t)g] = r->req.four_pi_G;
+    tol[(size_t)g] = r->req.tol;
+    if (host && ce == cudaSuccess)
+      ce = cudaMemcpyAsync(h->dev[2 * (size_t)g], r->req.rho, bytes, cudaMemcpyHostToDevice,
+                           stream);
+  }
+  mg_status st = ce == cudaSuccess
+                     ? mg_batch_solve(h->batch, rho.data(), fpg.data(), tol.data(), phi.data(),
+                                      hist.data(), kHistCap, nh.data(), sts.data(), stream)
+                     : MG_ERR_CUDA;
+  if (host && (st == MG_OK || st == MG_ERR_NOT_CONVERGED || st == MG_ERR_DIVERGED)) {
+    for (int g = 0; g < k && ce == cudaSuccess; ++g)
+      ce = cudaMemcpyAsync(group[(size_t)g]->req.phi, h->dev[2 * (size_t)g + 1], bytes,
+                           cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) st = MG_ERR_CUDA;
+  }
+  if (ce != cudaSuccess) cudaGetLastError();
+  const bool whole = st == MG_ERR_ARG || st == MG_ERR_CUDA || st == MG_ERR_TIMEOUT;
+  for (int g = 0; g < k; ++g) {
+    Request* r = group[(size_t)g];
+    r->status = whole ? st : sts[(size_t)g];
+    r->n_hist = whole ? 0 : nh[(size_t)g];
+    for (int q = 0; q < r->n_hist; ++q) r->hist[q] = hist[(size_t)g * kHistCap + q];
+  }
+}
+
 void run_worker(mg_server* S) {
   cudaSetDevice(S->device);
   cudaStream_t stream = nullptr;
@@ -109,6 +228,7 @@ void run_worker(mg_server* S) {
   }
   std::unique_lock<std::mutex> lk(S->mu);
   unsigned long long seen = ~0ULL;
+  std::vector<Request*> group;
   for (;;) {
     if (S->queue.empty() || seen == S->gen) {
       if (S->stop && S->queue.empty()) break;
@@ -129,48 +249,68 @@ void run_worker(mg_server* S) {
           return false;
         });
     if (at < 0) continue;  // nothing fits now: wait for a completion
-    Request* r = S->queue[(size_t)at];
+    group.clear();
+    group.push_back(S->queue[(size_t)at]);
     S->queue.erase(S->queue.begin() + at);
-    ++S->running;
-    r->t_start = Clock::now();
+    if (group[0]->key.slots > 0) {
+      // continuous batching: the queued requests of the same shape and rule
+      // join this launch, in arrival order
+      for (size_t i = 0; i < S->queue.size() && (int)group.size() < group[0]->key.slots;) {
+        if (S->queue[i]->key == group[0]->key) {
+          group.push_back(S->queue[i]);
+          S->queue.erase(S->queue.begin() + (long)i);
+        } else {
+          ++i;
+        }
+      }
+    }
+    const Clock::time_point t_start = Clock::now();
+    for (Request* r : group) r->t_start = t_start;
+    S->running += (int)group.size();
     if (!S->queue.empty()) {  // the pool changed: let the other slots look again
       ++S->gen;
       S->cv_work.notify_all();
     }
     lk.unlock();
 
-    for (void* old : dec.evict) mg_destroy(static_cast<mg_ctx*>(old));
-    mg_ctx* ctx = static_cast<mg_ctx*>(dec.ctx);
+    for (void* old : dec.evict) destroy_hier(old);
+    Hier* h = static_cast<Hier*>(dec.ctx);
+    Request* r = group[0];
     mg_status st = MG_OK;
     if (dec.act == Act::CREATE) {
-      mg_opts o = S->opts;
-      o.lmax = r->req.lmax;
-      o.fixed_value = r->req.fixed_value;
-      st = mg_create(r->req.nx, r->req.ny, r->req.nz, r->req.dx, r->req.bc, &o, &ctx);
+      st = create_hier(S, r, stream, &h);
       lk.lock();
-      if (st == MG_OK) S->pool.set_ctx(dec.id, ctx);
+      if (st == MG_OK) S->pool.set_ctx(dec.id, h);
       else S->pool.drop(dec.id);
       lk.unlock();
     }
-    if (st == MG_OK && dec.act == Act::CREATE) mg_ctx_autotune(ctx, stream);  // shapes, cached
-    int nh = 0;
-    if (st == MG_OK && r->key.host)
-      st = mg::solve_host_copies(ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi,
-                                 r->hist, kHistCap, &nh, stream, r->copy_ms);
-    else if (st == MG_OK)
-      st = mg_solve(ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi, r->hist, kHistCap,
-                    &nh, stream);
+    if (st != MG_OK) {
+      for (Request* q : group) q->status = st;
+    } else if (h->batch) {
+      solve_group(h, group, stream);
+    } else {
+      int nh = 0;
+      if (r->key.host)
+        st = mg::solve_host_copies(h->ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi,
+                                   r->hist, kHistCap, &nh, stream, r->copy_ms);
+      else
+        st = mg_solve(h->ctx, r->req.rho, r->req.four_pi_G, r->req.tol, r->req.phi, r->hist,
+                      kHistCap, &nh, stream);
+      r->status = st;
+      r->n_hist = nh;
+    }
     const Clock::time_point t_done = Clock::now();
 
     lk.lock();
-    if (ctx) S->pool.release(ctx);
-    r->t_done = t_done;
-    r->status = st;
-    r->n_hist = nh;
-    r->done = true;
-    --S->running;
-    ++S->completed;
-    S->cells_completed += (long long)r->req.nx * r->req.ny * r->req.nz;
+    if (h) S->pool.release(h);
+    for (Request* q : group) {
+      q->t_done = t_done;
+      q->done = true;
+      ++S->completed;
+      S->cells_completed += (long long)q->req.nx * q->req.ny * q->req.nz;
+    }
+    S->running -= (int)group.size();
+    if (group.size() > 1) S->batched += (long long)group.size();
     ++S->gen;
     S->cv_work.notify_all();
     S->cv_done.notify_all();
@@ -276,6 +416,18 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
   r->key.dx = q->dx;
   r->key.fixed_value = q->bc == MG_BC_FIXED ? q->fixed_value : 0.0;
   r->key.host = host;
+  // small requests with a periodic, fixed or zero-gradient rule: a batched
+  // hierarchy of up to kBatchSlots grids, as many as the budget holds (its
+  // bytes: that many single hierarchies); the slot count of a shape is fixed
+  // by the budget, and a grid's result does not depend on it
+  if (q->nx <= kBatchMaxN && q->bc != MG_BC_OPEN && batch_opts_ok(S->opts) && need > 0) {
+    size_t k = S->pool.budget() / need;
+    if (k > (size_t)kBatchSlots) k = kBatchSlots;
+    if (k >= 1) {
+      r->key.slots = (int)k;
+      need *= k;
+    }
+  }
   r->need = need;
   std::lock_guard<std::mutex> lk(S->mu);
   if (need > S->pool.budget()) {
@@ -338,6 +490,7 @@ mg_status mg_server_get_stats(mg_server* S, mg_server_stats* out) {
   out->evictions = S->pool.evictions();
   out->created = S->pool.created();
   out->cells_completed = S->cells_completed;
+  out->batched = S->batched;
   out->budget_bytes = S->pool.budget();
   out->resident_bytes = S->pool.resident_bytes();
   out->peak_bytes = S->pool.peak_bytes();
@@ -356,7 +509,7 @@ mg_status mg_server_destroy(mg_server* S) {
   }
   S->cv_work.notify_all();
   for (std::thread& t : S->workers) t.join();
-  for (void* c : S->pool.drain_idle()) mg_destroy(static_cast<mg_ctx*>(c));
+  for (void* c : S->pool.drain_idle()) destroy_hier(c);
   S->reqs.clear();
   delete S;
   return MG_OK;

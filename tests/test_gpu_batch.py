@@ -112,3 +112,35 @@ def test_barrier_limit_runs_out_and_the_batch_recovers():
         assert st == 0 and b.graph
         for p, q, ha, hb in zip(phis, ref_phi, h, ref_h):
             assert torch.equal(p, q) and np.array_equal(ha, hb)
+
+
+def test_batch_slots_left_out_and_fewer_ctas():
+    """Slots without a grid in a solve (rho = None) are passed by: the other
+    grids give the bits they give with every slot used, also on fewer CTAs,
+    and the empty slots' phi stays untouched."""
+    specs = [(32, mg.PERIODIC), (64, mg.FIXED), (32, mg.ZEROGRAD), (16, mg.PERIODIC)]
+    rhos, fixed = make_case(specs, seed=9)
+    sizes = [n for n, _ in specs]
+    rd = [torch.from_numpy(r).cuda() for r in rhos]
+    with mg.Batch(sizes, [1.0 / n for n in sizes], [bc for _, bc in specs], fixed) as b:
+        full = [torch.zeros_like(r) for r in rd]
+        st, hf, _ = b.solve(rd, full, 1.0, 1e-10)
+        assert st == 0
+        part = [torch.full_like(r, 7.0) for r in rd]
+        use = [True, False, True, False]
+        st, hp, sts = b.solve([r if u else None for r, u in zip(rd, use)],
+                              [p if u else None for p, u in zip(part, use)], 1.0, 1e-10)
+        assert st == 0 and list(sts) == [0, 0, 0, 0]
+        for g, u in enumerate(use):
+            if u:
+                assert torch.equal(part[g], full[g]) and np.array_equal(hp[g], hf[g])
+            else:
+                assert len(hp[g]) == 0
+        b.set_blocks(8)
+        few = [torch.zeros_like(r) for r in rd]
+        st, h8, _ = b.solve(rd, few, 1.0, 1e-10)
+        assert st == 0 and b.graph
+        for g in range(len(specs)):
+            assert torch.equal(few[g], full[g]) and np.array_equal(h8[g], hf[g])
+        st, _, _ = b.solve([None] * 4, [None] * 4, 1.0, 1e-10)
+        assert st == 1  # MG_ERR_ARG: no grid to solve

@@ -172,3 +172,33 @@ def test_server_requests_overlap_on_the_device():
     # run intervals [queue_ms, total_ms] from (nearly) one submission instant
     spans = sorted((r.queue_ms, r.total_ms) for r in results)
     assert any(b[0] + spread_ms < a[1] for a, b in zip(spans, spans[1:]))
+
+
+def test_small_requests_are_batched_and_match_alone_and_oracle():
+    """Continuous batching: a burst of small requests of one shape and rule
+    queued behind a busy slot runs as one batched launch (the server counts
+    them); each result equals the same request alone, and a fixed-rule one
+    the oracle's converged solution within 1e-9."""
+    n = 32
+    mix = [(n, mg.FIXED, 0, tol) for tol in (1e-10, 1e-8, 1e-6, 1e-10, 1e-9, 1e-10)]
+    rhos = sources(mix, seed=70)
+    alone = [solve_alone(r, nn, bc, lmax, tol) for r, (nn, bc, lmax, tol) in zip(rhos, mix)]
+    big = inputs.serving_source(dict(n=128, bc=mg.PERIODIC, seed=3, n_blobs=2), "cuda")
+    with mg.Server(1 << 34, slots=1, max_queue=64) as s:
+        s.wait(s.submit(rhos[0], torch.zeros_like(rhos[0]), bc=mg.FIXED, tol=1e-10), 120)
+        hold = s.submit(big, torch.zeros_like(big), tol=1e-10)  # keeps the one slot busy
+        phis = [torch.full_like(r, float("nan")) for r in rhos]
+        tickets = [s.submit(r, p, bc=bc, tol=tol) for r, p, (_, bc, _, tol) in zip(rhos, phis, mix)]
+        results = [s.wait(t, 120) for t in tickets]
+        assert s.wait(hold, 120)[0].status == 0
+        st = s.stats()
+    assert st["batched"] >= 2
+    for k, ((res, hist), (pa, ha)) in enumerate(zip(results, alone)):
+        assert res.done and res.status == 0, (k, res.status)
+        assert hist[-1] < mix[k][3]
+        assert torch.equal(phis[k], pa), k
+        assert np.array_equal(hist, ha), k
+    rho = rhos[0].cpu().numpy()
+    ref = orc.solve(rho, 1.0 / n, orc.FIXED, tol=0.0, max_cycles=80)
+    err = float(np.abs(phis[0].cpu().numpy() - ref.phi).max() / np.abs(ref.phi).max())
+    assert err <= 1e-9, err
