@@ -484,9 +484,22 @@ def run_serving(args):
             rec, busy, wall = serving.run_stream(srv, stream, pool)
             out.append(serving.summarize(rec, busy, wall, rate, args.serve_seconds))
         stats = srv.stats()
+    # the same streams at two rates with the small requests merged into batched
+    # launches (opts.batch_small = 1)
+    batched = []
+    with mg.Server(free // 2, slots=8, max_queue=128, batch_small=1) as srv:
+        serving.run_stream(srv, inputs.serving_stream(200, 0.5, seed=1), pool)
+        for rate in (300, 3000):
+            stream = inputs.serving_stream(rate, args.serve_seconds)
+            rec, busy, wall = serving.run_stream(srv, stream, pool)
+            batched.append(serving.summarize(rec, busy, wall, rate, args.serve_seconds))
+        bstats = srv.stats()
     return {"rates": out, "slots": 8, "max_queue": 128, "budget_bytes": stats["budget_bytes"],
             "peak_resident_bytes": stats["peak_bytes"], "evictions": stats["evictions"],
-            "latency": "submission to result in the caller's phi (server clock)"}
+            "latency": "submission to result in the caller's phi (server clock)",
+            "with_batch_small": {"rates": batched, "batched_requests": bstats["batched"],
+                                 "what": "requests of at most 64^3 cells merged into "
+                                         "persistent batched launches (opts.batch_small = 1)"}}
 
 
 def main():
@@ -693,17 +706,25 @@ def main():
             barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            tickets = []
-            for q in range(k_req):
-                if q >= inflight:
-                    res, _ = srv.wait(tickets[q - inflight], 600)
-                    assert res.done and res.status == 0
-                    copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms))
-                tickets.append(srv.submit(rho_h, phis_h[q % inflight], tol=TOL))
-            for tk in tickets[-inflight:]:
-                res, _ = srv.wait(tk, 600)
-                assert res.done and res.status == 0
-                copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms))
+            # keep `inflight` requests outstanding: as soon as any one is done
+            # (polled in turn), the next is submitted with its phi buffer
+            outstanding = {srv.submit(rho_h, phis_h[q], tol=TOL): q for q in range(inflight)}
+            submitted = inflight
+            while outstanding:
+                done = []
+                for tk, q in outstanding.items():
+                    res, _ = srv.poll(tk)
+                    if res.done:
+                        assert res.status == 0
+                        copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms))
+                        done.append((tk, q))
+                for tk, q in done:
+                    del outstanding[tk]
+                    if submitted < k_req:
+                        outstanding[srv.submit(rho_h, phis_h[q], tol=TOL)] = q
+                        submitted += 1
+                if not done:
+                    time.sleep(2e-4)
             dt2 = time.perf_counter() - t0
         if saved_aff is not None:
             os.sched_setaffinity(0, saved_aff)

@@ -104,7 +104,12 @@ typedef struct {
                       /*    pass over HBM, or as two passes; same bits either way.   */
                       /*    0 (default): two passes, unless mg_ctx_autotune timed    */
                       /*    the fused pass faster; 1: always fused; 2: never         */
-  int reserved[4];    /* must be zero                                               */
+  int batch_small;    /* serving loop only: 1 serves requests of at most 64^3 cells  */
+                      /*    with a periodic, fixed or zero-gradient rule by batched  */
+                      /*    hierarchies (continuous batching into one persistent     */
+                      /*    launch, see mg_server_create); 0 (default): one solve    */
+                      /*    per request                                              */
+  int reserved[3];    /* must be zero                                               */
 } mg_opts;
 
 typedef struct mg_ctx mg_ctx;
@@ -487,9 +492,9 @@ mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, 
  * Hierarchies stay resident between requests of the same key (cells, dx,
  * rule, fixed value, lmax).  Requests on different slots run concurrently on
  * the device; each result equals the result of the same request alone.
- * Continuous batching: requests of at most 64^3 cells with a periodic, fixed
- * or zero-gradient rule (when the options allow mg_batch_create's solve) are
- * served by batched hierarchies of up to 16 grids of one shape and rule (as
+ * With opts->batch_small = 1, requests of at most 64^3 cells with a periodic,
+ * fixed or zero-gradient rule (when the options allow mg_batch_create's solve)
+ * are served by batched hierarchies of up to 16 grids of one shape and rule (as
  * many as the budget holds): the slot that takes one also takes the queued
  * requests of that shape and rule and solves them in one persistent launch
  * (mg_batch_solve), whatever their tolerances; a grid's result there does not

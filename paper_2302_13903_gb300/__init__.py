@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
         ("origin", ctypes.c_double * 3), ("stall_ratio", ctypes.c_double),
         ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("outer_fixed", ctypes.c_int), ("fas", ctypes.c_int), ("coarse_literal", ctypes.c_int),
-        ("leg_pairs", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+        ("leg_pairs", ctypes.c_int), ("batch_small", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 

@@ -129,7 +129,7 @@ namespace {
 // Whether the server's options allow the batched solve (mg_batch_create's
 // conditions).
 bool batch_opts_ok(const mg_opts& o) {
-  return o.prec == MG_MIXED && o.pre == 1 && o.post == 1 && o.mode_fmg == 1 &&
+  return o.batch_small == 1 && o.prec == MG_MIXED && o.pre == 1 && o.post == 1 && o.mode_fmg == 1 &&
          o.inner_fmg == 0 && o.max_cycles <= 64 && o.inner_cycles <= 16 && o.coarse_literal == 0;
 }
 

@@ -1008,6 +1008,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (o.fas != 0 && (o.fas != 1 || o.prec != MG_FP64)) return MG_ERR_ARG;
   if (o.coarse_literal != 0 && o.coarse_literal != 1) return MG_ERR_ARG;
   if (o.leg_pairs < 0 || o.leg_pairs > 2) return MG_ERR_ARG;
+  if (o.batch_small != 0 && o.batch_small != 1) return MG_ERR_ARG;
   if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;

@@ -23,8 +23,8 @@ def sources(mix, seed=11):
             for k, (n, bc, _, _) in enumerate(mix)]
 
 
-def solve_alone(rho, n, bc, lmax, tol):
-    with mg.Server(1 << 34, slots=1, max_queue=4) as s:
+def solve_alone(rho, n, bc, lmax, tol, **opts):
+    with mg.Server(1 << 34, slots=1, max_queue=4, **opts) as s:
         phi = torch.zeros_like(rho)
         res, hist = s.wait(s.submit(rho, phi, bc=bc, tol=tol, lmax=lmax), 120)
         assert res.done and res.status in (0, 4)
@@ -45,6 +45,23 @@ def test_server_mix_equals_alone():
         assert res.done and res.status == 0, (k, res.status)
         assert hist[-1] < MIX[k][3]
         assert 0.0 <= res.queue_ms <= res.total_ms and res.solve_ms > 0.0
+        assert torch.equal(phis[k], pa), k
+        assert np.array_equal(hist, ha), k
+
+
+def test_server_mix_with_batching_equals_alone():
+    """The same mix with small requests served by batched hierarchies
+    (batch_small = 1): every result still equals the request alone."""
+    rhos = sources(MIX, seed=13)
+    alone = [solve_alone(r, n, bc, lmax, tol, batch_small=1)
+             for r, (n, bc, lmax, tol) in zip(rhos, MIX)]
+    with mg.Server(1 << 34, slots=4, max_queue=64, batch_small=1) as s:
+        phis = [torch.full_like(r, float("nan")) for r in rhos]
+        tickets = [s.submit(r, p, bc=bc, tol=tol, lmax=lmax)
+                   for r, p, (n, bc, lmax, tol) in zip(rhos, phis, MIX)]
+        results = [s.wait(t, 120) for t in tickets]
+    for k, ((res, hist), (pa, ha)) in enumerate(zip(results, alone)):
+        assert res.done and res.status == 0, (k, res.status)
         assert torch.equal(phis[k], pa), k
         assert np.array_equal(hist, ha), k
 
@@ -182,9 +199,10 @@ def test_small_requests_are_batched_and_match_alone_and_oracle():
     n = 32
     mix = [(n, mg.FIXED, 0, tol) for tol in (1e-10, 1e-8, 1e-6, 1e-10, 1e-9, 1e-10)]
     rhos = sources(mix, seed=70)
-    alone = [solve_alone(r, nn, bc, lmax, tol) for r, (nn, bc, lmax, tol) in zip(rhos, mix)]
+    alone = [solve_alone(r, nn, bc, lmax, tol, batch_small=1)
+             for r, (nn, bc, lmax, tol) in zip(rhos, mix)]
     big = inputs.serving_source(dict(n=128, bc=mg.PERIODIC, seed=3, n_blobs=2), "cuda")
-    with mg.Server(1 << 34, slots=1, max_queue=64) as s:
+    with mg.Server(1 << 34, slots=1, max_queue=64, batch_small=1) as s:
         s.wait(s.submit(rhos[0], torch.zeros_like(rhos[0]), bc=mg.FIXED, tol=1e-10), 120)
         hold = s.submit(big, torch.zeros_like(big), tol=1e-10)  # keeps the one slot busy
         phis = [torch.full_like(r, float("nan")) for r in rhos]

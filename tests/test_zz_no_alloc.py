@@ -74,43 +74,61 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
 
 
 CHILD = r"""
-import ctypes, json, sys
+import ctypes, glob, json, os, sys
 sys.path.insert(0, sys.argv[1])
 import numpy as np
 import paper_2302_13903_gb300 as mg
-L = mg.lib()            # the library (and its device code) before the context exists
-import torch
-torch.cuda.init()
-rho = torch.rand((32, 64, 64), dtype=torch.float64, device="cuda") + 0.5
+L = mg.lib()
+# A CUDA runtime of its own for allocating the input and reading free memory,
+# so that no other library's device code is loaded into this process.
+cands = sorted(glob.glob(os.path.join(sys.argv[2], "lib64", "libcudart.so*")))
+if not cands:
+    print(json.dumps({"skip": "no libcudart.so under " + sys.argv[2]}))
+    sys.exit(0)
+rt = ctypes.CDLL(cands[0])
+vp, sz = ctypes.c_void_p, ctypes.c_size_t
+assert rt.cudaSetDevice(0) == 0
+def dalloc(a):
+    p = vp()
+    assert rt.cudaMalloc(ctypes.byref(p), sz(a.nbytes)) == 0
+    assert rt.cudaMemcpy(p, a.ctypes.data_as(vp), sz(a.nbytes), 1) == 0  # host to device
+    return p
+def free_bytes():
+    f, t = sz(), sz()
+    assert rt.cudaDeviceSynchronize() == 0
+    assert rt.cudaMemGetInfo(ctypes.byref(f), ctypes.byref(t)) == 0
+    return f.value
+rho = dalloc(np.random.default_rng(1).random((32, 64, 64)) + 0.5)
+tiny, tiny_c = dalloc(np.zeros(8)), dalloc(np.zeros(1))
 # The library carries its own CUDA runtime, whose first call loads the
 # library's device code (with CUDA_MODULE_LOADING=EAGER all of it, the fixed
 # scratch included): make that first call through another entry point.
-mg.op_restrict(torch.zeros((2, 2, 2), dtype=torch.float64, device="cuda"))
-torch.cuda.synchronize()
-free = [torch.cuda.mem_get_info()[0]]
+assert L.mg_op_restrict(0, 2, 2, 2, tiny, tiny_c, None) == 0
+free = [free_bytes()]
 for _ in range(3):
     Q = np.zeros(25); org = np.zeros(3)
-    st = L.mg_op_multipole_moments_noalloc(64, 64, 32, 1.0 / 64, rho.data_ptr(), 4, 1,
-                                           org.ctypes.data_as(ctypes.c_void_p),
-                                           Q.ctypes.data_as(ctypes.c_void_p), None)
+    st = L.mg_op_multipole_moments_noalloc(64, 64, 32, 1.0 / 64, rho, 4, 1,
+                                           org.ctypes.data_as(vp), Q.ctypes.data_as(vp), None)
     assert st == 0, st
-    torch.cuda.synchronize()
-    free.append(torch.cuda.mem_get_info()[0])
+    free.append(free_bytes())
 print(json.dumps({"free": free, "Q00": Q[0]}))
 """
 
 
 def test_noalloc_first_call_leaves_free_memory_unchanged():
-    """In a fresh process whose library device code is already loaded
-    (CUDA_MODULE_LOADING=EAGER and one call of another entry point, so that
-    loading the module, which holds the fixed scratch, is not counted), the
-    first call of the no-allocation entry point -- which also does its
-    per-device set-up -- and the calls after it change the device's free
-    memory by nothing."""
+    """In a fresh process that loads no other library's device code, once
+    the library's own device code is loaded (CUDA_MODULE_LOADING=EAGER and one
+    call of another entry point, so that loading the module, which holds the
+    fixed scratch, is not counted), the first call of the no-allocation entry
+    point -- which also does its per-device set-up -- and the calls after it
+    change the device's free memory by nothing."""
     env = dict(os.environ, CUDA_MODULE_LOADING="EAGER")
-    out = subprocess.run([sys.executable, "-c", CHILD, ROOT], capture_output=True, text=True,
-                         env=env, timeout=300)
+    cuda_home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    out = subprocess.run([sys.executable, "-c", CHILD, ROOT, cuda_home], capture_output=True,
+                         text=True, env=env, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     rec = json.loads(out.stdout.strip().splitlines()[-1])
+    if "skip" in rec:
+        pytest.skip(rec["skip"])
     assert len(set(rec["free"])) == 1, rec["free"]
     assert rec["Q00"] > 0.0
