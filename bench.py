@@ -512,7 +512,7 @@ def main():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64-path solves (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=8)
-    ap.add_argument("--e2e-inflight", type=int, default=4,
+    ap.add_argument("--e2e-inflight", type=int, default=2,
                     help="requests in flight in the served end-to-end measurement")
     ap.add_argument("--cpu-n", type=int, default=256, help="oracle sample size")
     ap.add_argument("--no-cpu", action="store_true")
@@ -716,7 +716,8 @@ def main():
                     res, _ = srv.poll(tk)
                     if res.done:
                         assert res.status == 0
-                        copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms))
+                        copies.append((res.h2d_ms, res.d2h_ms, res.solve_ms, res.queue_ms,
+                                       res.total_ms))
                         done.append((tk, q))
                 for tk, q in done:
                     del outstanding[tk]
@@ -742,6 +743,9 @@ def main():
                           "h2d_gbs": nbytes / (h2d * 1e-3) / 1e9,
                           "d2h_gbs": nbytes / (d2h * 1e-3) / 1e9,
                           "solve_ms_median": statistics.median(c[2] for c in copies),
+                          "queue_ms_median": statistics.median(c[3] for c in copies),
+                          "total_ms_median": statistics.median(c[4] for c in copies),
+                          "slot_busy_fraction": sum(c[2] for c in copies) / (inflight * dt2 * 1e3),
                           "what": "per request, device time of the slot's copies (events on its "
                                   "stream; concurrent with other slots' solves and copies)"},
                "numa": numa,

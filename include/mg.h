@@ -318,7 +318,8 @@ mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double ome
  * u_out = SMOOTH(u_in + trilinear(ec))); leg 2: the up leg of one V-cycle and
  * the down leg of the next in one pass (steps 5-7, then 1-3 of the next cycle:
  * u_out = SMOOTH(SMOOTH(u_in + trilinear(ec))), fc = restriction of
- * f - L u_out; tx 0 or 64, nx a multiple of 64, nz >= 16).  face_bc[6] (host) gives each face's
+ * f - L u_out; tx 0 or 64, nx a multiple of 64, nz >= 16).  face_bc[6] (host)
+ * gives each face's
  * homogeneous rule (x-, x+, y-, y+, z-, z+): MG_BC_PERIODIC on both faces of an
  * axis, MG_BC_FIXED (value 0) or MG_BC_ZEROGRAD.  tx (0, 32 or 64 cells), ty
  * (0, 16 or 32 rows) and cz (0 or a multiple of 8 planes) choose the CTA tile
@@ -514,6 +515,12 @@ typedef struct {
   double four_pi_G;
   double tol;            /* ||d||/||f|| target of this request */
   double *phi;           /* FP64 array written with the result, in the same memory as rho */
+  int per_face;          /* 1: a rule per face (Sec. 2.3.6) from the two arrays below,  */
+                         /*    as in mg_create_faces (bc and fixed_value are ignored);  */
+                         /*    0 (zero-initialised requests): the one rule bc           */
+  mg_bc face_bc[6];      /* x-, x+, y-, y+, z-, z+: periodic (in pairs), fixed or zero  */
+                         /*    gradient                                                  */
+  double face_value[6];  /* b on each fixed face                                         */
 } mg_request;
 
 typedef struct {

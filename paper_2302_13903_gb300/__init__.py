@@ -58,7 +58,8 @@ class Request(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_double),
         ("bc", ctypes.c_int), ("fixed_value", ctypes.c_double), ("lmax", ctypes.c_int),
         ("rho", ctypes.c_void_p), ("four_pi_G", ctypes.c_double), ("tol", ctypes.c_double),
-        ("phi", ctypes.c_void_p),
+        ("phi", ctypes.c_void_p), ("per_face", ctypes.c_int), ("face_bc", ctypes.c_int * 6),
+        ("face_value", ctypes.c_double * 6),
     ]
 
 
@@ -684,14 +685,22 @@ class Server:
         self.ptr = h
 
     def submit(self, rho, phi, dx=None, bc=PERIODIC, four_pi_G=1.0, tol=1e-10, lmax=4,
-               fixed_value=0.0):
+               fixed_value=0.0, face_values=None):
         """rho, phi: float64 (n, n, n) tensors kept alive until done, both on the
-        device or both in host memory (pinned host tensors move fastest).
-        Returns the ticket, or raises MGError (MG_ERR_BUSY when the queue is full)."""
+        device or both in host memory (pinned host tensors move fastest).  bc
+        may be a list of six face rules (x-, x+, y-, y+, z-, z+), with
+        face_values the fixed faces' values.  Returns the ticket, or raises
+        MGError (MG_ERR_BUSY when the queue is full)."""
         import torch
         n = rho.shape[0]
-        q = Request(n, n, n, 1.0 / n if dx is None else dx, bc, fixed_value, lmax,
+        q = Request(n, n, n, 1.0 / n if dx is None else dx, 0, fixed_value, lmax,
                     _any_ptr(rho), four_pi_G, tol, _any_ptr(phi))
+        if isinstance(bc, (list, tuple)):
+            q.per_face = 1
+            q.face_bc = (ctypes.c_int * 6)(*[int(k) for k in bc])
+            q.face_value = (ctypes.c_double * 6)(*(face_values or [0.0] * 6))
+        else:
+            q.bc = bc
         t = ctypes.c_longlong(0)
         st = lib().mg_server_submit(self.ptr, ctypes.byref(q), ctypes.byref(t))
         if st != 0:

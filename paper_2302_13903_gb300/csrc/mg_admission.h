@@ -26,9 +26,15 @@ struct Key {
   double dx = 0.0, fixed_value = 0.0;
   bool host = false;  // requests with host buffers: the hierarchy holds device copies too
   int slots = 0;      // > 0: a batched hierarchy of that many grids of this shape
+  int fk = 0;         // a rule per face (bc = 4): the kind of face q in bits 2q..2q+1
+  double fv[6] = {};  // ... and the values of its fixed faces
   bool operator==(const Key& o) const {
-    return n == o.n && bc == o.bc && lmax == o.lmax && dx == o.dx &&
-           fixed_value == o.fixed_value && host == o.host && slots == o.slots;
+    if (!(n == o.n && bc == o.bc && lmax == o.lmax && dx == o.dx &&
+          fixed_value == o.fixed_value && host == o.host && slots == o.slots && fk == o.fk))
+      return false;
+    for (int q = 0; q < 6; ++q)
+      if (fv[q] != o.fv[q]) return false;
+    return true;
   }
 };
 

@@ -42,15 +42,19 @@
 namespace mg {
 namespace batch {
 
-constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4, false>::NT;  // 216
-constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4, false>::SMEM;
-static_assert(fused::Shape<fused::kUp, 64, 16, 4, false>::SMEM <= kSmem &&
-                  fused::Shape<fused::kUp, 32, 16, 4, false>::SMEM <= kSmem,
+// The tile programs pad their shared rows (bank-conflict-free, as the
+// single-grid kernels) at a cost of 9 KB per CTA of the shared memory the
+// other phases could use as L1.
+constexpr bool kPad = true;
+constexpr int kThreads = fused::Shape<fused::kDown, 64, 16, 4, kPad>::NT;  // 216
+constexpr size_t kSmem = fused::Shape<fused::kDown, 64, 16, 4, kPad>::SMEM;
+static_assert(fused::Shape<fused::kUp, 64, 16, 4, kPad>::SMEM <= kSmem &&
+                  fused::Shape<fused::kUp, 32, 16, 4, kPad>::SMEM <= kSmem,
               "an up-leg tile needs more shared memory than the CTA has");
 constexpr int kMaxL = 16;
 constexpr int kChunk = 32768;   // cells per chunk item
 constexpr int kFusedMinN = 32;  // levels of at least 32^3 use the fused tiles
-constexpr int kCz = 32;         // z-chunk of fused tiles
+constexpr int kCz = 64;         // z-chunk of fused tiles
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct GridDev {
@@ -584,25 +588,25 @@ __device__ __forceinline__ void tile_leg(bool down, bool per, const GridDev& g, 
     const bool zg = (l < g.L - 1) || zero_finest;
     if (zg) {
       if (per)
-        fused::fused_tile<fused::kDown, true, 7, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, true, 7, TX, 16, 4, kPad, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, true, 0, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, true, 0, TX, 16, 4, kPad, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     } else {
       if (per)
-        fused::fused_tile<fused::kDown, false, 7, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, false, 7, TX, 16, 4, kPad, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
       else
-        fused::fused_tile<fused::kDown, false, 0, TX, 16, 4, false, kThreads>(
+        fused::fused_tile<fused::kDown, false, 0, TX, 16, 4, kPad, kThreads>(
             g.u32[l], g.u32b[l], g.f32[l], nullptr, g.f32[l - 1], fp, I.a, I.b, I.c, smem);
     }
   } else {
     if (per)
-      fused::fused_tile<fused::kUp, false, 7, TX, 16, 4, false, kThreads>(
+      fused::fused_tile<fused::kUp, false, 7, TX, 16, 4, kPad, kThreads>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
     else
-      fused::fused_tile<fused::kUp, false, 0, TX, 16, 4, false, kThreads>(
+      fused::fused_tile<fused::kUp, false, 0, TX, 16, 4, kPad, kThreads>(
           g.u32b[l], g.u32[l], g.f32[l], g.u32[l - 1], nullptr, fp, I.a, I.b, I.c, smem);
   }
 }
@@ -704,23 +708,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(Ctl c) {
           }
           break;
         case PH_BOTTOM: {
-          bottom::BottomArgs<float> a;
+          // the arguments in shared memory: their per-level arrays are indexed
+          // by a run-time level, which in each thread's own copy would put
+          // them in local memory
+          __shared__ bottom::BottomArgs<float> a;
           const int top = level_of(g, min(g.n, kFusedMinN / 2));
-          for (int l = 0; l < kBottomLevels; ++l) {
-            const bool used = l <= top;
-            a.u[l] = used ? g.u32[l] : nullptr;
-            a.f[l] = used ? g.f32[l] : nullptr;
-            a.n[l] = used ? (g.n >> (g.L - 1 - l)) : 0;
-            a.h[l] = used ? g.h * (double)(1 << (g.L - 1 - l)) : 0.0;
-            a.bc[l] = hom_bc(g);
+          if (threadIdx.x == 0) {
+            for (int l = 0; l < kBottomLevels; ++l) {
+              const bool used = l <= top;
+              a.u[l] = used ? g.u32[l] : nullptr;
+              a.f[l] = used ? g.f32[l] : nullptr;
+              a.n[l] = used ? (g.n >> (g.L - 1 - l)) : 0;
+              a.h[l] = used ? g.h * (double)(1 << (g.L - 1 - l)) : 0.0;
+              a.bc[l] = hom_bc(g);
+            }
+            a.hom = hom_bc(g);
+            a.omega = c.omega;
+            a.pre = 1;
+            a.post = 1;
+            a.top = top;
+            a.fmg = 0;
+            bottom::set_coefficients(a);
           }
-          a.hom = hom_bc(g);
-          a.omega = c.omega;
-          a.pre = 1;
-          a.post = 1;
-          a.top = top;
-          a.fmg = 0;
-          bottom::set_coefficients(a);
+          __syncthreads();
           const bool zg = (top < g.L - 1) || (P.cycle == 0 && c.inner_zero);
           bottom::vcycle<float, false>(a, top, a.hom, zg);
           break;

@@ -162,7 +162,11 @@ mg_status create_hier(mg_server* S, const Request* r, cudaStream_t stream, Hier*
       }
     }
   } else {
-    st = mg_create(r->req.nx, r->req.ny, r->req.nz, r->req.dx, r->req.bc, &o, &h->ctx);
+    if (r->req.per_face)
+      st = mg_create_faces(r->req.nx, r->req.ny, r->req.nz, r->req.dx, r->req.face_bc,
+                           r->req.face_value, &o, &h->ctx);
+    else
+      st = mg_create(r->req.nx, r->req.ny, r->req.nz, r->req.dx, r->req.bc, &o, &h->ctx);
     if (st == MG_OK) mg_ctx_autotune(h->ctx, stream);  // shapes, cached per process
   }
   if (st != MG_OK) {
@@ -382,9 +386,22 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
     return MG_ERR_ARG;
   }
   *ticket = 0;
+  bool faces_ok = q->per_face == 0 || q->per_face == 1;
+  int fk = 0;
+  if (q->per_face == 1) {
+    for (int f = 0; f < 6; ++f) {
+      const mg_bc k = q->face_bc[f];
+      faces_ok = faces_ok && (k == MG_BC_PERIODIC || k == MG_BC_FIXED || k == MG_BC_ZEROGRAD) &&
+                 std::isfinite(q->face_value[f]);
+      fk |= ((int)k & 3) << (2 * f);
+    }
+    for (int a = 0; a < 3; ++a)
+      faces_ok = faces_ok && ((q->face_bc[2 * a] == MG_BC_PERIODIC) ==
+                              (q->face_bc[2 * a + 1] == MG_BC_PERIODIC));
+  }
   if (!pow2(q->nx) || q->nx != q->ny || q->nx != q->nz || !(q->dx > 0.0) || !q->rho ||
-      !q->phi || !(q->tol >= 0.0) || !std::isfinite(q->four_pi_G) || (int)q->bc < 0 ||
-      (int)q->bc > 3 || q->lmax < 0 || q->lmax > 4) {
+      !q->phi || !(q->tol >= 0.0) || !std::isfinite(q->four_pi_G) || !faces_ok ||
+      (!q->per_face && ((int)q->bc < 0 || (int)q->bc > 3)) || q->lmax < 0 || q->lmax > 4) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->err = "mg_server_submit: invalid request";
     return MG_ERR_ARG;
@@ -393,7 +410,10 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
   o.lmax = q->lmax;
   o.fixed_value = q->fixed_value;
   size_t need = 0;
-  if (mg_required_bytes(q->nx, q->ny, q->nz, q->bc, &o, &need) != MG_OK) {
+  // a rule per face: the bytes of a fixed-rule hierarchy plus the face arrays
+  // of its levels (at most 4/3 of the finest level's)
+  const mg_bc need_bc = q->per_face ? MG_BC_FIXED : q->bc;
+  if (mg_required_bytes(q->nx, q->ny, q->nz, need_bc, &o, &need) != MG_OK) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->err = "mg_server_submit: invalid request";
     return MG_ERR_ARG;
@@ -408,19 +428,26 @@ mg_status mg_server_submit(mg_server* S, const mg_request* q, long long* ticket)
   }
   const bool host = rs == 1;
   if (host) need += 2 * sizeof(double) * (size_t)q->nx * q->ny * q->nz;
+  if (q->per_face) need += 4 * sizeof(double) * 6 * (size_t)(q->nx + 2) * (q->nx + 2) / 3;
   Request* r = new Request;
   r->req = *q;
   r->key.n = q->nx;
-  r->key.bc = (int)q->bc;
-  r->key.lmax = q->bc == MG_BC_OPEN ? q->lmax : 0;
+  r->key.bc = q->per_face ? (int)MG_BC_MIXED : (int)q->bc;
+  r->key.lmax = !q->per_face && q->bc == MG_BC_OPEN ? q->lmax : 0;
   r->key.dx = q->dx;
-  r->key.fixed_value = q->bc == MG_BC_FIXED ? q->fixed_value : 0.0;
+  r->key.fixed_value = !q->per_face && q->bc == MG_BC_FIXED ? q->fixed_value : 0.0;
   r->key.host = host;
+  if (q->per_face) {
+    r->key.fk = fk;
+    for (int f = 0; f < 6; ++f)
+      r->key.fv[f] = q->face_bc[f] == MG_BC_FIXED ? q->face_value[f] : 0.0;
+  }
   // small requests with a periodic, fixed or zero-gradient rule: a batched
   // hierarchy of up to kBatchSlots grids, as many as the budget holds (its
   // bytes: that many single hierarchies); the slot count of a shape is fixed
   // by the budget, and a grid's result does not depend on it
-  if (q->nx <= kBatchMaxN && q->bc != MG_BC_OPEN && batch_opts_ok(S->opts) && need > 0) {
+  if (!q->per_face && q->nx <= kBatchMaxN && q->bc != MG_BC_OPEN && batch_opts_ok(S->opts) &&
+      need > 0) {
     size_t k = S->pool.budget() / need;
     if (k > (size_t)kBatchSlots) k = kBatchSlots;
     if (k >= 1) {

@@ -1862,10 +1862,10 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
   Bc b{};
   const Grid g{nx, ny, nz};
   const mg::TileCfg cfg{tx, cz, ty};
+  const bool down = leg == 0;
   bool ok = leg >= 0 && leg <= 2 && face_rule(face_bc, &b) && h > 0.0 && omega > 0.0 &&
-            omega < 2.0 && u_out && f && (u_in || (leg == 0 && zero_guess)) && u_in != u_out &&
-            (leg == 1 || fc != nullptr) && (leg == 0 || ec != nullptr) &&
-            (leg == 0 || !zero_guess);
+            omega < 2.0 && u_out && f && (u_in || (down && zero_guess)) && u_in != u_out &&
+            (leg == 1 || fc != nullptr) && (down || ec != nullptr) && (down || !zero_guess);
   if (ok) {
     b = mg::collapse_homogeneous(b);
     ok = mg::fused_ok(g, b) && mg::fused_cfg_ok(g, cfg) && (tx == 0 || tx == 32 || tx == 64) &&

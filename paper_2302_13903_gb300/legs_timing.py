@@ -6,10 +6,11 @@ python -m paper_2302_13903_gb300.legs_timing LEGS [REPS] [NZ NY NX]
 LEGS is a comma-separated list of down (SMOOTH + defect + restriction, 64 x 32
 tiles, 64 planes per CTA), down0 (the same from a zero start), up
 (prolongation + correction + SMOOTH, 64 x 16 tiles), ud16 / ud32 (the up leg
-of one V-cycle fused with the down leg of the next, 16- or 32-row tiles), all
-periodic; fx (the fixed-point outer step, 64 planes per CTA).  Each leg runs twice untimed, then REPS times (default 10) between
-CUDA events; one line per leg gives the milliseconds per launch.  The default
-box is 256 x 256 x 512 cells (nz, ny, nx): 128 MiB per FP32 array.
+of one V-cycle fused with the down leg of the next, 16- or 32-row tiles), fx
+(the fixed-point outer step, 64 planes per CTA), all periodic.  Each leg runs
+twice untimed, then REPS times (default 10) between CUDA events; one line per
+leg gives the milliseconds per launch.  The default box is 256 x 256 x 512
+cells (nz, ny, nx): 128 MiB per FP32 array.
 """
 from __future__ import annotations
 

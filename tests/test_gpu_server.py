@@ -220,3 +220,38 @@ def test_small_requests_are_batched_and_match_alone_and_oracle():
     ref = orc.solve(rho, 1.0 / n, orc.FIXED, tol=0.0, max_cycles=80)
     err = float(np.abs(phis[0].cpu().numpy() - ref.phi).max() / np.abs(ref.phi).max())
     assert err <= 1e-9, err
+
+
+def test_server_rule_per_face_requests():
+    """Requests with a rule per face (Sec. 2.3.6) next to uniform ones: each
+    gives the bits of mg_create_faces' solve of the same grid, and the oracle's
+    converged solution within 1e-9."""
+    P, F, Z = mg.PERIODIC, mg.FIXED, mg.ZEROGRAD
+    faces = [((P, P, P, P, F, F), (0, 0, 0, 0, 0.3, -0.2)), ((Z, F, F, Z, P, P), (0, 0.4, 0.1, 0, 0, 0))]
+    n = 64
+    rhos = [torch.from_numpy(inputs.gaussian_blobs(n, 6, seed=80 + k, periodic=False,
+                                                   remove_mean=False)).cuda() for k in range(2)]
+    ref = []
+    for rho, (kinds, vals) in zip(rhos, faces):
+        with mg.Solver(n, 1.0 / n, list(kinds), face_values=list(vals), prec=mg.MIXED) as s:
+            s.autotune()
+            phi, hist, st = s.solve(rho, 1.0, 1e-10)
+            ref.append((phi, hist))
+    uni = inputs.serving_source(dict(n=n, bc=P, seed=9, n_blobs=3), "cuda")
+    with mg.Server(1 << 34, slots=3, max_queue=16) as srv:
+        phis = [torch.zeros_like(r) for r in rhos]
+        tickets = [srv.submit(r, p, bc=list(k), face_values=list(v), tol=1e-10)
+                   for r, p, (k, v) in zip(rhos, phis, faces)]
+        t_uni = srv.submit(uni, torch.zeros_like(uni), tol=1e-10)
+        results = [srv.wait(t, 120) for t in tickets]
+        assert srv.wait(t_uni, 120)[0].status == 0
+        with pytest.raises(mg.MGError):  # periodic faces come in pairs
+            srv.submit(uni, torch.zeros_like(uni), bc=[P, F, P, P, P, P])
+    for k, ((res, hist), (pr, hr)) in enumerate(zip(results, ref)):
+        assert res.done and res.status == 0, (k, res.status)
+        assert torch.equal(phis[k], pr) and np.array_equal(hist, hr), k
+        kinds, vals = faces[k]
+        o = orc.solve(rhos[k].cpu().numpy(), 1.0 / n, orc.PER_FACE,
+                      faces=orc.mixed_rule(kinds, vals), tol=0.0, max_cycles=80)
+        err = float(np.abs(phis[k].cpu().numpy() - o.phi).max() / np.abs(o.phi).max())
+        assert err <= 1e-9, (k, err)
