@@ -72,6 +72,9 @@ KERNEL_SOURCES = {
     "fused_up": ["mg_fused.cuh", "mg_fused_launch.cuh", "mg_fused.cu", "mg_internal.h"],
     "fused_down": ["mg_fused.cuh", "mg_fused_launch.cuh", "mg_fused.cu", "mg_internal.h"],
     "fused_down0": ["mg_fused.cuh", "mg_fused_launch.cuh", "mg_fused.cu", "mg_internal.h"],
+    # the down legs with tensor copies
+    "fused_down_tma": ["mg_fused.cuh", "mg_fused_tma.cu", "mg_internal.h"],
+    "fused_down0_tma": ["mg_fused.cuh", "mg_fused_tma.cu", "mg_internal.h"],
     "outer_residual": ["mg_fixed.cu", "mg_convert.cuh", "mg_device.cuh", "mg_internal.h"],
 }
 
@@ -560,6 +563,7 @@ def main():
     if not args.no_tune:
         solver.autotune(stream)
     tiles = solver.tile_configs()
+    tcopies = solver.tensor_copies()
     hist = None
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -604,6 +608,13 @@ def main():
     # algorithmic bytes per launch; the dominant class (by device time) is the
     # headline roofline
     peak, peak_kind = peaks()
+    fin = n.bit_length() - 1
+
+    def variant(k):  # the finest down legs' kernel: tensor copies or per-thread copies
+        if k in ("fused_down", "fused_down0") and tcopies.get(fin, (0, 0))[k == "fused_down0"]:
+            return k + "_tma"
+        return k
+
     by_class = {}
     for k, (tot_ms, nl) in ktimes.items():
         if nl == 0:
@@ -613,13 +624,15 @@ def main():
         ach = alg / (tot_ms / nl * 1e-3) / 1e9
         by_class[k] = {"launches_per_solve": nl / args.steps, "ms_per_launch": tot_ms / nl,
                        "algorithmic_bytes_per_launch": alg, "achieved_gbs": ach,
-                       "frac": ach / peak, "dtype": "f32" if w == 4 else "f64"}
+                       "frac": ach / peak, "dtype": "f32" if w == 4 else "f64",
+                       "kernel": variant(k),
+                       "traffic": ncu_traffic(variant(k), "f32" if w == 4 else "f64", n)}
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     d = by_class[dom]
     prec_tag = d["dtype"]
-    traffic = ncu_traffic(dom, prec_tag, n)
+    traffic = d["traffic"]
     roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                "frac": d["frac"], "traffic": traffic, "kernel": f"{dom}_{prec_tag}",
+                "frac": d["frac"], "traffic": traffic, "kernel": f"{variant(dom)}_{prec_tag}",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"],
                 "frac_of_nominal": d["achieved_gbs"] / NOMINAL_HBM_GBS,
@@ -817,6 +830,9 @@ def main():
                        "parallelism": f"replicas x{ws}",
                        "tile_configs": {k: {str(l): list(v) for l, v in d.items()}
                                         for k, d in tiles.items() if d},
+                       # levels whose down leg (nonzero start, zero start) takes
+                       # its planes by tensor copies
+                       "tensor_copies": {str(l): list(v) for l, v in tcopies.items()},
                        "l2": "inputs larger than L2 (1 GiB per FP64 field), no flush"},
             "roofline": roofline,
             "cpu_baseline": cpu,

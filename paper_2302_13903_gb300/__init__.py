@@ -34,6 +34,7 @@ EXPORTS = [
     "mg_server_create", "mg_server_submit", "mg_server_poll", "mg_server_wait",
     "mg_server_get_stats", "mg_server_destroy", "mg_server_last_error", "mg_op_convert",
     "mg_op_fused_leg", "mg_op_fx_step", "mg_batch_set_barrier_limit", "mg_batch_set_blocks",
+    "mg_ctx_tensor_copies",
 ]
 KERNELS = ["sor", "defect_restrict", "prolong", "fmg_prolong", "defect_norm", "outer_residual",
            "correct", "source", "fused_down", "fused_up", "gravity", "fused_down0",
@@ -49,7 +50,7 @@ class Opts(ctypes.Structure):
         ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("outer_fixed", ctypes.c_int), ("fas", ctypes.c_int), ("coarse_literal", ctypes.c_int),
         ("leg_pairs", ctypes.c_int), ("batch_small", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("tensor_copies", ctypes.c_int), ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -184,6 +185,8 @@ def lib():
             L.mg_batch_last_error.restype = ctypes.c_char_p
             L.mg_faces_count.argtypes = [i, i, i]
             L.mg_faces_count.restype = sz
+            L.mg_ctx_tensor_copies.argtypes = [p, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            L.mg_ctx_tensor_copies.restype = i
             L.mg_ctx_autotune.argtypes = [p, p]
             L.mg_ctx_autotune.restype = i
             L.mg_ctx_tile_config.argtypes = [p, i, i, ctypes.POINTER(i), ctypes.POINTER(i),
@@ -312,6 +315,18 @@ class Solver:
     def autotune(self, stream=None):
         """Time the candidate launch shapes of the hot kernels and keep the fastest."""
         _check(lib().mg_ctx_autotune(self.ctx, _stream_ptr(stream)), self.ctx)
+
+    def tensor_copies(self):
+        """{level: (down, down0)} for the levels whose down leg (from a
+        nonzero start, from zero) takes its planes by tensor copies."""
+        out = {}
+        for l in range(self.n.bit_length()):
+            a, b = ctypes.c_int(0), ctypes.c_int(0)
+            _check(lib().mg_ctx_tensor_copies(self.ctx, l, ctypes.byref(a), ctypes.byref(b)),
+                   self.ctx)
+            if a.value or b.value:
+                out[l] = (a.value, b.value)
+        return out
 
     def tile_configs(self):
         """{"fused_down" | "fused_up" | "fused_updown" | "sor" | "outer_residual":
@@ -520,7 +535,7 @@ def op_fused_leg(leg, u, f, h, kinds, omega=1.15, zero_guess=False, ec=None, til
     nz, ny, nx = f.shape
     uo = torch.empty_like(f)
     fc = None
-    if leg != 1:
+    if leg != 1:  # 3: the down leg with tensor copies
         fc = torch.empty((nz // 2, ny // 2, nx // 2), dtype=f.dtype, device=f.device)
     tx, ty, cz = tile
     _check(lib().mg_op_fused_leg(

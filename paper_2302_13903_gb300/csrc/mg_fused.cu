@@ -30,20 +30,6 @@ cudaError_t dispatch(const float* ui, float* uo, const float* f, const float* ec
   }
 }
 
-FusedParams params(Grid g, double h, const Bc& bc, double omega) {
-  FusedParams p;
-  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
-  float sg[6];
-  for (int q = 0; q < 6; ++q) sg[q] = face_kind(bc, q) == BC_ZEROGRAD ? 1.f : -1.f;
-  p.sx0 = sg[0]; p.sx1 = sg[1]; p.sy0 = sg[2]; p.sy1 = sg[3]; p.sz0 = sg[4]; p.sz1 = sg[5];
-  p.cu = (float)(1.0 - omega);
-  p.cs = (float)(omega / 6.0);
-  p.cf = (float)(-omega * h * h / 6.0);
-  p.inv_h2 = (float)(1.0 / (h * h));
-  p.cz = 8;
-  return p;
-}
-
 }  // namespace
 }  // namespace fused
 

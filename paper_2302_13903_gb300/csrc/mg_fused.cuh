@@ -61,6 +61,33 @@ struct FusedParams {
   int cz;            // planes per CTA (multiple of 8, or nz)
 };
 
+// The kernels' constants for level g (spacing h, SOR factor omega, face
+// rules bc); cz is set by the launch.
+inline FusedParams params(Grid g, double h, const Bc& bc, double omega) {
+  FusedParams p;
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
+  float sg[6];
+  for (int q = 0; q < 6; ++q) sg[q] = face_kind(bc, q) == BC_ZEROGRAD ? 1.f : -1.f;
+  p.sx0 = sg[0]; p.sx1 = sg[1]; p.sy0 = sg[2]; p.sy1 = sg[3]; p.sz0 = sg[4]; p.sz1 = sg[5];
+  p.cu = (float)(1.0 - omega);
+  p.cs = (float)(omega / 6.0);
+  p.cf = (float)(-omega * h * h / 6.0);
+  p.inv_h2 = (float)(1.0 / (h * h));
+  p.cz = 8;
+  return p;
+}
+
+// Planes per CTA: cz_cfg when nonzero, else the largest of 64, 32, 16, 8 that
+// still gives two CTAs per SM on tiles of tx x ty; at most nz.
+inline int chunk_planes(const FusedParams& p, int tx, int ty, int cz_cfg) {
+  const long long sms = sm_count();
+  const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
+  int cz = 64;
+  while (cz > 8 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
+  if (cz_cfg) cz = cz_cfg;
+  return cz < p.nz ? cz : p.nz;
+}
+
 enum Mode : int { kPlain = 0, kDown = 1, kUp = 2 };
 
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
@@ -284,6 +311,55 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Tensor-memory-accelerator copies of whole plane tiles (one thread issues,
+// an mbarrier in shared memory counts the bytes that land).
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier; gives up after 2^22 tries (each
+// suspends the thread for at most a few microseconds), raising *err, so that a
+// copy that never lands cannot hang the GPU.
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
+  for (int k = 0; k < (1 << 22); ++k)
+    if (mbar_try_wait(bar, parity)) return;
+  if (err) *reinterpret_cast<volatile int*>(err) = 1;  // a flag: a plain store suffices
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const void* tmap, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(tmap),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 // (x, y) part of the trilinear prolongation of one coarse plane at a patch:
 // rows gyA (even: coarse rows Y-1, Y) and gyA+1 (odd: Y, Y+1), Y = gyA/2;
 // four fine x cells from coarse x X0-1 .. X0+2, X0 = gx4/2.  The up leg
@@ -416,12 +492,18 @@ struct Shape {
 // (0: exactly NT); threads tid >= Shape::NT of a larger CTA take part in the
 // barriers only.  Element offsets are 32-bit: levels have fewer than 2^32
 // cells (fused_ok).
+// TMA: tiles whose window lies inside the level (and, along a periodic axis,
+// needs no wrap) take their planes of u and f by one tensor copy each, issued
+// by one thread, from the tensor maps tmu and tmf (boxes of 4 RS columns by
+// RR rows by one plane: a ring slot); the others by cp.async.  A copy that
+// does not land in time raises *err.
 template <int MODE, bool ZERO, int PM, int TX, int TY, int HYO = 0, bool PAD = true,
-          int NTB = 0>
+          int NTB = 0, bool TMA = false, int PF = 0>
 __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, const float* f,
                                            const float* ec, float* fc,
                                            const FusedParams& p, int bx, int by, int bz,
-                                           float4* smem) {
+                                           float4* smem, const void* tmu = nullptr,
+                                           const void* tmf = nullptr, int* err = nullptr) {
   using S_ = Shape<MODE, TX, TY, HYO, PAD>;
   constexpr int HZ = S_::HZ, HY = S_::HY, RT = S_::RT, RS = S_::RS, RP = S_::RP, PL = S_::PL;
   float4* s_u = smem;                     // [4][PL] planes of u (async copies)
@@ -465,10 +547,42 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   const int offL = tr > 0 ? -1 : 0, offR = tr < RT - 1 ? 1 : 0;
   const int q_first = z0 - HZ, q_last = z1 - 1 + HZ;
 
+  // TMA tiles: their window [x0 - 4, x0 + TX + 4) x [y0 - HY, y0 + TY + HY)
+  // inside the level (the box's extra padding columns may leave it: they are
+  // zero-filled and never read); mbarrier b counts the copies of plane b mod 4
+  __shared__ unsigned long long tma_bar[TMA ? 4 : 1];
+  const bool tma_tile = TMA && x0 - 4 >= 0 && x0 + TX + 4 <= p.nx && y0 - HY >= 0 &&
+                        y0 + TY + HY <= p.ny;
+  if (TMA && tma_tile) {
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < 4; ++b) mbar_init(&tma_bar[b], 1);
+      fence_proxy_async();
+    }
+    __syncthreads();
+  }
   // Copies of plane qu of u into ring slot SU and plane qu - 1 of f into
   // slot SF (the slots are compile-time: qu mod 4 is fixed by the step).
   auto issue = [&](auto SUc, auto SFc, int qu) {
     constexpr int SU = decltype(SUc)::value, SF = decltype(SFc)::value;
+    if (TMA && PF > 0 && threadIdx.x == 0 && qu + PF <= q_last) {
+      const int qp = qu + PF;
+      const int zp = PZ ? wrap(qp, p.nz) : qp, zpf = PZ ? wrap(qp - 1, p.nz) : qp - 1;
+      const int px = max(x0 - 4, 0), py = max(y0 - HY, 0);
+      if (!ZERO) tma_prefetch_3d(tmu, px, py, zp);
+      tma_prefetch_3d(tmf, px, py, zpf);
+    }
+    if (TMA && tma_tile) {
+      if (threadIdx.x == 0 && qu <= q_last) {
+        unsigned long long* bar = &tma_bar[SU];
+        const int qf = qu - 1;
+        const int zu = PZ ? wrap(qu, p.nz) : qu, zf = PZ ? wrap(qf, p.nz) : qf;
+        fence_proxy_async();  // earlier reads of the slots come before the copies
+        mbar_expect_tx(bar, (ZERO ? 1u : 2u) * (unsigned)(PL * 16));
+        if (!ZERO) tma_load_3d(&s_u[SU * PL], tmu, x0 - 4, y0 - HY, zu, bar);
+        tma_load_3d(&s_f[SF * PL], tmf, x0 - 4, y0 - HY, zf, bar);
+      }
+      return;
+    }
     if (act && qu <= q_last) {
       if (!ZERO) {
         const bool in = col_ok && (PZ || (qu >= 0 && qu < p.nz));
@@ -548,7 +662,10 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     constexpr int ZP_RED = (QP + 3) % 2;  // parity of plane q-1
     constexpr int ZP_BLK = (QP + 2) % 2;  // parity of plane q-2
     constexpr int ZP_DEF = (QP + 1) % 2;  // parity of plane q-3
-    cp_async_wait<1>();  // this thread's copies of plane q have landed
+    if (TMA && tma_tile)
+      mbar_wait(&tma_bar[QP], (unsigned)(((q - q_first) >> 2) & 1), err);  // plane q's copies
+    else
+      cp_async_wait<1>();  // this thread's copies of plane q have landed
     __syncthreads();     // ... and everyone's; the previous step is finished
     issue(std::integral_constant<int, (QP + 2) % 4>{}, std::integral_constant<int, (QP + 1) % 4>{},
           q + 2);

@@ -41,13 +41,8 @@ inline cudaError_t launch_t(const float* ui, float* uo, const float* f, const fl
 template <int MODE, bool ZERO, int PM>
 inline cudaError_t dispatch_t(const float* ui, float* uo, const float* f, const float* ec, float* fc,
                        FusedParams p, TileCfg cfg, cudaStream_t s) {
-  const long long sms = sm_count();
   const int tx = cfg.tx ? cfg.tx : (p.nx >= 64 ? 64 : 32), ty = cfg.ty ? cfg.ty : 16;
-  const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
-  int cz = 64;
-  while (cz > 8 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
-  if (cfg.cz) cz = cfg.cz;
-  p.cz = cz < p.nz ? cz : p.nz;
+  p.cz = chunk_planes(p, tx, ty, cfg.cz);
   if (ty == 32) {
     if (tx == 64) return launch_t<MODE, ZERO, PM, 64, 32>(ui, uo, f, ec, fc, p, s);
     return launch_t<MODE, ZERO, PM, 32, 32>(ui, uo, f, ec, fc, p, s);

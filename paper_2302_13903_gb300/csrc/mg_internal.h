@@ -199,6 +199,17 @@ cudaError_t launch_fused_updown(const float* u_in, float* u_out, const float* f,
                                 float* fc, Grid g, double h, Bc bc, double omega, cudaStream_t s,
                                 TileCfg cfg = TileCfg{});
 
+// The periodic down leg with 64 x 32 tiles whose planes arrive by tensor copies
+// (mg_fused_tma.cu); *err (device-visible) is set to 1 if a copy does not
+// land in time.
+bool down_tma_ok(Grid g, const Bc& bc);
+cudaError_t launch_fused_down_tma(const float* u_in, float* u_out, const float* f, float* fc,
+                                  Grid g, double h, double omega, bool zero_guess, int cz,
+                                  int* err, cudaStream_t s);
+// A host-mapped flag (one per process, host and device share its address)
+// for the leg-3 calls of mg_op_fused_leg; null if it cannot be had.
+int* down_tma_op_flag();
+
 // ---------------------------------------------------------------------------
 // Exact 64-bit fixed-point outer residual (mg_fixed.cu).
 

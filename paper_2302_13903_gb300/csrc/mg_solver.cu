@@ -55,7 +55,7 @@ struct mg_ctx {
   float* u32b[kMaxLevels] = {};
   float* f32[kMaxLevels] = {};
   double* partials = nullptr;  // reduction partials
-  int* iflag = nullptr;        // device flag (fixed-point overflow)
+  int* iflag = nullptr;        // device flags: [0] fixed-point overflow, [1] tensor copy late
   long long* fxbuf = nullptr;  // second integer buffer of the fixed-point outer loop
   int partials_cap = 0;        // doubles in `partials`
   double* scal = nullptr;      // device scalars: [0] |f|^2 sum, [1] |d|^2 sum, [2..31] multipole
@@ -93,6 +93,9 @@ struct mg_ctx {
   // the autotuner timed the finest level's fused up-down pass faster than the
   // two legs it replaces (opts.leg_pairs = 0 then fuses them)
   bool pairs_faster = false;
+  // per level: the down leg (from a nonzero start / from zero) brings its
+  // planes in by tensor copies (opts.tensor_copies and the autotuner)
+  bool tma_down[kMaxLevels] = {}, tma_down0[kMaxLevels] = {};
 };
 
 namespace {
@@ -357,6 +360,25 @@ void vcycle(mg_ctx* c, Pyr<T> P, int l, const Bc& bc_top, const Bc& hom, bool ze
 
 // The same cycle on an FP32 level handled by the fused kernels: one kernel
 // per leg, ping-ponging between the level's two buffers.
+// Whether level l's down leg takes its planes by tensor copies: opts 1 where
+// the kernel applies, 0 where the autotuner timed it faster, 2 never.
+bool tma_level(const mg_ctx* c, int l, const Bc& bc, bool zero_guess) {
+  if (c->opts.tensor_copies == 2 || !mg::down_tma_ok(level_grid(c, l), bc)) return false;
+  return c->opts.tensor_copies == 1 || (zero_guess ? c->tma_down0[l] : c->tma_down[l]);
+}
+
+// Steps 1-3 of Algorithm 1 on FP32 level l in one pass, into u32b[l] and
+// f32[l-1] (the caller swaps the level's buffers).
+cudaError_t launch_down(mg_ctx* c, int l, const Bc& bc, bool zero_guess, cudaStream_t s) {
+  const Grid g = level_grid(c, l);
+  const double h = level_h(c, l), om = c->opts.omega;
+  if (tma_level(c, l, bc, zero_guess))
+    return mg::launch_fused_down_tma(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, om,
+                                     zero_guess, c->cfg_down[l].cz, c->iflag + 1, s);
+  return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc, om,
+                               zero_guess, s, c->cfg_down[l]);
+}
+
 void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_guess,
                   cudaStream_t s) {
   const Grid g = level_grid(c, l);
@@ -375,9 +397,7 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
   }
   if (pre >= 1) {  // 1-3
     KTimer t(c, zg ? MG_K_FUSED_DOWN0 : MG_K_FUSED_DOWN, fin, s);
-    check(c, mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
-                                   om, zg, s, c->cfg_down[l]),
-          "fused down");
+    check(c, launch_down(c, l, bc_top, zg, s), "fused down");
     swap_level();
   } else {
     if (zg) check(c, mg::launch_fill<float>(c->u32[l], g.cells(), 0.f, s), "fill");
@@ -452,9 +472,7 @@ void vcycles_paired(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, int cycle
   auto swap_level = [&]() { std::swap(c->u32[l], c->u32b[l]); };
   {
     KTimer t(c, MG_K_FUSED_DOWN0, fin, s);
-    check(c, mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc_top,
-                                   om, true, s, c->cfg_down[l]),
-          "fused down");
+    check(c, launch_down(c, l, bc_top, true, s), "fused down");
     swap_level();
   }
   coarse_correction(c, l, hom, s);
@@ -994,6 +1012,21 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       check(c, mg::launch_gravity(phi, gacc, g, c->h, bc, s), "gravity");
     }
   }
+  bool tma = false;
+  for (int l = 1; l < c->L; ++l)
+    tma = tma || tma_level(c, l, hom, false) || tma_level(c, l, hom, true);
+  if (tma) {  // a down leg whose tensor copies did not land in time raised iflag[1]
+    int late = 0;
+    check(c, cudaMemcpyAsync(c->pinned + 61, c->iflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s),
+          "read flag");
+    check(c, cudaStreamSynchronize(s), "sync");
+    std::memcpy(&late, c->pinned + 61, sizeof(int));
+    if (late) {
+      check(c, cudaMemsetAsync(c->iflag + 1, 0, sizeof(int), s), "clear flag");
+      c->err = "fused down leg: a tensor copy did not land in time";
+      st = MG_ERR_TIMEOUT;
+    }
+  }
   *n_hist = n;
   return (mg_status)st;
 }
@@ -1009,6 +1042,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (o.coarse_literal != 0 && o.coarse_literal != 1) return MG_ERR_ARG;
   if (o.leg_pairs < 0 || o.leg_pairs > 2) return MG_ERR_ARG;
   if (o.batch_small != 0 && o.batch_small != 1) return MG_ERR_ARG;
+  if (o.tensor_copies < 0 || o.tensor_copies > 2) return MG_ERR_ARG;
   if (!(o.stall_ratio > 0.0)) return MG_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return MG_ERR_ARG;
@@ -1028,7 +1062,8 @@ enum TuneKind {
   TUNE_SMOOTH = 2,
   TUNE_FX = 3,
   TUNE_UD = 4,      // shape of the fused up-down pass
-  TUNE_UD_WIN = 5   // cz = 1 when that pass beat the two legs it replaces
+  TUNE_UD_WIN = 5,  // cz = 1 when that pass beat the two legs it replaces
+  TUNE_TMA = 6      // tx = 1 / cz = 1: the down leg with tensor copies won from zero / not
 };
 
 struct TuneKey {
@@ -1172,6 +1207,32 @@ void autotune(mg_ctx* c, cudaStream_t s) {
           tune_store_locked(key, best);
         }
         (kind == TUNE_DOWN ? c->cfg_down : kind == TUNE_UP ? c->cfg_up : c->cfg_smooth)[l] = best;
+      }
+      // the down leg with tensor copies against the per-thread copies, from a
+      // zero start and from a nonzero one
+      if (c->opts.tensor_copies == 0 && mg::down_tma_ok(g, hom)) {
+        const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, TUNE_TMA, g.nx, g.ny,
+                          g.nz, periodic};
+        mg::TileCfg v{0, 0, 0};
+        auto hit = g_tune.find(key);
+        if (hit != g_tune.end()) {
+          v = hit->second;
+        } else {
+          for (const bool zg : {true, false}) {
+            const float plain_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+              return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h,
+                                           hom, om, zg, s, c->cfg_down[l]);
+            });
+            const float tma_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+              return mg::launch_fused_down_tma(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g,
+                                               h, om, zg, c->cfg_down[l].cz, c->iflag + 1, s);
+            });
+            (zg ? v.tx : v.cz) = tma_ms < plain_ms ? 1 : 0;
+          }
+          tune_store_locked(key, v);
+        }
+        c->tma_down0[l] = v.tx == 1;
+        c->tma_down[l] = v.cz == 1;
       }
       // the fused up-down pass of the finest level's inner cycles
       if (l == F && c->opts.leg_pairs != 2 && pairs_ok(c, l, hom, hom, 2)) {
@@ -1342,6 +1403,15 @@ mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, in
   return MG_OK;
 }
 
+mg_status mg_ctx_tensor_copies(const mg_ctx* c, int level, int* down, int* down0) {
+  if (!c || !down || !down0 || level < 0 || level >= c->L) return MG_ERR_ARG;
+  const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr, c->face_mask});
+  const bool fp32 = c->opts.prec == MG_MIXED && level > 0 && c->u32b[level];
+  *down = fp32 && tma_level(c, level, hom, false) ? 1 : 0;
+  *down0 = fp32 && tma_level(c, level, hom, true) ? 1 : 0;
+  return MG_OK;
+}
+
 mg_status mg_ctx_kernel_time(const mg_ctx* c, int k, double* total_ms, long long* launches) {
   if (!c || k < 0 || k >= MG_K_COUNT || !total_ms || !launches) return MG_ERR_ARG;
   *total_ms = c->kernel_ms[k];
@@ -1398,6 +1468,7 @@ mg_status create_ctx(int nx, int ny, int nz, double dx, mg_bc bc, int face_mask,
     check(c, cudaGetDevice(&c->device), "cudaGetDevice");
     if (bc == MG_BC_OPEN) check(c, mg::prepare_multipole(), "multipole tables");
     alloc_hierarchy(c);
+    check(c, cudaMemset(c->iflag, 0, 4 * sizeof(int)), "clear flags");
     if (bc == MG_BC_MIXED) fill_mixed_faces(c);
     check(c, cudaMallocHost(&c->pinned, 64 * sizeof(double)), "cudaMallocHost");
   } catch (const Fail& f) {
@@ -1862,8 +1933,8 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
   Bc b{};
   const Grid g{nx, ny, nz};
   const mg::TileCfg cfg{tx, cz, ty};
-  const bool down = leg == 0;
-  bool ok = leg >= 0 && leg <= 2 && face_rule(face_bc, &b) && h > 0.0 && omega > 0.0 &&
+  const bool down = leg == 0 || leg == 3;
+  bool ok = leg >= 0 && leg <= 3 && face_rule(face_bc, &b) && h > 0.0 && omega > 0.0 &&
             omega < 2.0 && u_out && f && (u_in || (down && zero_guess)) && u_in != u_out &&
             (leg == 1 || fc != nullptr) && (down || ec != nullptr) && (down || !zero_guess);
   if (ok) {
@@ -1871,6 +1942,7 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
     ok = mg::fused_ok(g, b) && mg::fused_cfg_ok(g, cfg) && (tx == 0 || tx == 32 || tx == 64) &&
          (ty == 0 || ty == 16 || ty == 32) && cz >= 0;
     if (leg == 2) ok = mg::updown_ok(g, b) && mg::updown_cfg_ok(g, cfg);
+    if (leg == 3) ok = ok && mg::down_tma_ok(g, b) && (tx == 0 || tx == 64) && (ty == 0 || ty == 32);
   }
   if (!ok) {
     g_err = "mg_op_fused_leg: invalid argument, or a grid or shape the fused kernels do not take";
@@ -1882,8 +1954,19 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
     e = mg::launch_fused_down(u_in, u_out, f, fc, g, h, b, omega, zero_guess != 0, s, cfg);
   else if (leg == 1)
     e = mg::launch_fused_up(u_in, u_out, f, ec, g, h, b, omega, s, cfg);
-  else
+  else if (leg == 2)
     e = mg::launch_fused_updown(u_in, u_out, f, ec, fc, g, h, b, omega, s, cfg);
+  else {
+    volatile int* late = mg::down_tma_op_flag();
+    if (!late) return op_result(cudaErrorMemoryAllocation, "fused_leg");
+    if (*late) {  // raised by an earlier call's kernel, finished by now
+      *late = 0;
+      g_err = "mg_op_fused_leg: a tensor copy of an earlier leg-3 call did not land in time";
+      return MG_ERR_TIMEOUT;
+    }
+    e = mg::launch_fused_down_tma(u_in, u_out, f, fc, g, h, omega, zero_guess != 0, cz,
+                                  const_cast<int*>(late), s);
+  }
   return op_result(e, "fused_leg");
 }
 

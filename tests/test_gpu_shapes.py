@@ -112,6 +112,22 @@ def test_fused_up_then_down_every_shape_and_mask(grid, mask):
         assert err < 2e-6, (tile, err)
 
 
+@pytest.mark.parametrize("zero", [False, True], ids=["down", "down_from_zero"])
+def test_fused_down_with_tensor_copies_matches_plain_down_leg(zero):
+    """Leg 3: the periodic down leg whose tiles inside the level take their
+    planes by tensor copies; the tiles at the level's edges keep per-thread
+    copies.  Same arithmetic: bit for bit the plain down leg's results."""
+    rng = np.random.default_rng(33)
+    nz, ny, nx = 48, 128, 256  # 2 x 2 of the 4 x 4 tiles lie inside the level
+    u, f = (torch.from_numpy(rng.standard_normal((nz, ny, nx)).astype(np.float32)).cuda()
+            for _ in range(2))
+    for cz in (8, 16, 0):
+        a = mg.op_fused_leg(0, u, f, 1.0 / nx, [P] * 6, zero_guess=zero, tile=(64, 32, cz))
+        b = mg.op_fused_leg(3, u, f, 1.0 / nx, [P] * 6, zero_guess=zero, tile=(64, 32, cz))
+        torch.cuda.synchronize()
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), cz
+
+
 def test_fused_leg_rejects_shapes_it_does_not_take():
     f = torch.zeros((64, 48, 64), device="cuda")  # 48 rows: 16-row tiles only
     mg.op_fused_leg(0, f, f, 1.0, [P] * 6, tile=(64, 16, 8))  # taken

@@ -457,6 +457,53 @@ def test_paired_legs_give_the_same_bits(bc, n):
     assert a[3] < b[3]  # fewer launches: one pass per pair of legs
 
 
+def test_tensor_copies_give_the_same_bits():
+    """The down leg with its planes brought in by tensor copies
+    (opts.tensor_copies = 1) runs the same per-cell arithmetic as with
+    per-thread copies (2), and so does whatever the autotuner picks (0): the
+    same phi and residual history, bit for bit (the tuned run's history up
+    to the summation order of its norm).  Tensor copies apply to the
+    periodic levels at least 64 cells wide with rows in 32s."""
+    n = 128
+    rho, fpg = source(n, mg.PERIODIC, seed=37)
+    a = gpu_solve(rho, mg.PERIODIC, fpg, 1e-10, prec=mg.MIXED, tensor_copies=1)
+    b = gpu_solve(rho, mg.PERIODIC, fpg, 1e-10, prec=mg.MIXED, tensor_copies=2)
+    assert a[2] == b[2] == 0
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED, tensor_copies=1) as s:
+        assert s.tensor_copies() == {6: (1, 1), 7: (1, 1)}  # the 64^3 and 128^3 levels
+    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED, tensor_copies=2) as s:
+        assert s.tensor_copies() == {}
+    with mg.Solver(n, 1.0 / n, mg.FIXED, prec=mg.MIXED, tensor_copies=1) as s:
+        assert s.tensor_copies() == {}  # periodic levels only
+    with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED) as s:
+        s.autotune()
+        assert set(s.tensor_copies()) <= {6, 7}
+        phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), fpg, 1e-10)
+        assert st == 0
+        # the tuned shapes sum the residual norm's FP32 partials in another order
+        assert np.array_equal(phi.cpu().numpy(), b[0])
+        assert np.allclose(hist, b[1], rtol=64 * 2.0 ** -24, atol=0.0)
+
+
+def test_tensor_copies_on_a_box():
+    """A 256 x 128 x 64 periodic box: the same bits with and without tensor
+    copies, on every level they apply to."""
+    rng = np.random.default_rng(41)
+    rho = rng.standard_normal((64, 128, 256))
+    rho -= rho.mean()
+    out = []
+    for tc in (1, 2):
+        with mg.Solver((256, 128, 64), 1.0 / 256, mg.PERIODIC, prec=mg.MIXED,
+                       tensor_copies=tc) as s:
+            if tc == 1:
+                assert 6 in s.tensor_copies() and 5 in s.tensor_copies()
+            phi, hist, st = s.solve(torch.from_numpy(rho).cuda(), 1.0, 1e-9)
+            assert st == 0
+            out.append((phi.cpu().numpy(), hist))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 @pytest.fixture(scope="module")
 def headline_reference():
     """The oracle's converged solution of the 512^3 periodic workload (64
