@@ -75,6 +75,7 @@ KERNEL_SOURCES = {
     # the down legs with tensor copies
     "fused_down_tma": ["mg_fused.cuh", "mg_fused_tma.cu", "mg_internal.h"],
     "fused_down0_tma": ["mg_fused.cuh", "mg_fused_tma.cu", "mg_internal.h"],
+    "fused_up_tma": ["mg_fused.cuh", "mg_fused_tma.cu", "mg_internal.h"],
     "outer_residual": ["mg_fixed.cu", "mg_convert.cuh", "mg_device.cuh", "mg_internal.h"],
 }
 
@@ -610,8 +611,9 @@ def main():
     peak, peak_kind = peaks()
     fin = n.bit_length() - 1
 
-    def variant(k):  # the finest down legs' kernel: tensor copies or per-thread copies
-        if k in ("fused_down", "fused_down0") and tcopies.get(fin, (0, 0))[k == "fused_down0"]:
+    def variant(k):  # the finest legs' kernel: tensor copies or per-thread copies
+        which = {"fused_down": 0, "fused_down0": 1, "fused_up": 2}.get(k)
+        if which is not None and tcopies.get(fin, (0, 0, 0))[which]:
             return k + "_tma"
         return k
 
@@ -830,8 +832,8 @@ def main():
                        "parallelism": f"replicas x{ws}",
                        "tile_configs": {k: {str(l): list(v) for l, v in d.items()}
                                         for k, d in tiles.items() if d},
-                       # levels whose down leg (nonzero start, zero start) takes
-                       # its planes by tensor copies
+                       # levels whose down leg (nonzero start, zero start) and
+                       # up leg take their planes by tensor copies
                        "tensor_copies": {str(l): list(v) for l, v in tcopies.items()},
                        "l2": "inputs larger than L2 (1 GiB per FP64 field), no flush"},
             "roofline": roofline,

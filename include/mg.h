@@ -109,13 +109,14 @@ typedef struct {
                       /*    hierarchies (continuous batching into one persistent     */
                       /*    launch, see mg_server_create); 0 (default): one solve    */
                       /*    per request                                              */
-  int tensor_copies;  /* MIXED, periodic levels of at least 64 x 32 cells: the     */
-                      /*    down leg's planes of u and f brought into shared memory  */
-                      /*    by tensor copies (cp.async.bulk.tensor, one thread per   */
-                      /*    CTA) instead of per-thread asynchronous copies; same     */
+  int tensor_copies;  /* MIXED, periodic levels at least 64 cells wide: the fused  */
+                      /*    legs' planes of u and f brought into shared memory by    */
+                      /*    tensor copies (cp.async.bulk.tensor, one thread per CTA) */
+                      /*    instead of per-thread asynchronous copies (down leg:     */
+                      /*    rows in 32s, 64 x 32 tiles; up leg: 64 x 16 tiles); same */
                       /*    bits either way.  0 (default): per-thread copies, unless */
-                      /*    mg_ctx_autotune timed the tensor copies faster on that   */
-                      /*    level; 1: always (where they apply); 2: never            */
+                      /*    mg_ctx_autotune timed the tensor copies faster for that  */
+                      /*    leg and level; 1: always (where they apply); 2: never    */
   int reserved[2];    /* must be zero                                               */
 } mg_opts;
 
@@ -329,9 +330,11 @@ mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double ome
  * the planes of u_in and f brought into shared memory by tensor copies
  * (cp.async.bulk.tensor) on the tiles whose window does not wrap (all faces
  * periodic, tx 0 or 64, ty 0 or 32, nx a multiple of 64, ny of 32; same bits
- * as leg 0).  A leg-3 kernel that waits too long for a copy sets a
- * process-wide flag; the next leg-3 call that finds it set clears it and
- * returns MG_ERR_TIMEOUT.  face_bc[6] (host) gives each face's
+ * as leg 0); leg 4: leg 1 with the planes of u_in and f brought in the same
+ * way (tx 0 or 64, ty 0 or 16, nx a multiple of 64; same bits as leg 1).  A
+ * leg-3 or leg-4 kernel that waits too long for a copy sets a process-wide
+ * flag; the next such call that finds it set clears it and returns
+ * MG_ERR_TIMEOUT.  face_bc[6] (host) gives each face's
  * homogeneous rule (x-, x+, y-, y+, z-, z+): MG_BC_PERIODIC on both faces of an
  * axis, MG_BC_FIXED (value 0) or MG_BC_ZEROGRAD.  tx (0, 32 or 64 cells), ty
  * (0, 16 or 32 rows) and cz (0 or a multiple of 8 planes) choose the CTA tile
@@ -494,12 +497,13 @@ mg_status mg_ctx_autotune(mg_ctx *ctx, void *stream);
 mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, int *ty,
                              int *cz);
 
-/* Whether the down leg of a level of the mixed path (Algorithm 1, steps 1-3 in
- * one pass) brings its planes into shared memory by tensor copies, from a
- * nonzero start (*down) and from zero (*down0): 1 or 0, as fixed by
- * opts.tensor_copies and mg_ctx_autotune.  Errors: MG_ERR_ARG (null pointer,
- * level outside 0..L-1). */
-mg_status mg_ctx_tensor_copies(const mg_ctx *ctx, int level, int *down, int *down0);
+/* Whether the fused legs of a level of the mixed path bring their planes into
+ * shared memory by tensor copies: the down leg (Algorithm 1, steps 1-3 in one
+ * pass) from a nonzero start (*down) and from zero (*down0), and the up leg
+ * (steps 5-7, *up): 1 or 0, as fixed by opts.tensor_copies and
+ * mg_ctx_autotune.  Errors: MG_ERR_ARG (null pointer, level outside
+ * 0..L-1). */
+mg_status mg_ctx_tensor_copies(const mg_ctx *ctx, int level, int *down, int *down0, int *up);
 
 /* ---------------------------------------------------------------------------
  * Serving loop.  Requests (solves of any supported size and boundary rule)

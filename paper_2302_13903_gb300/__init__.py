@@ -185,7 +185,8 @@ def lib():
             L.mg_batch_last_error.restype = ctypes.c_char_p
             L.mg_faces_count.argtypes = [i, i, i]
             L.mg_faces_count.restype = sz
-            L.mg_ctx_tensor_copies.argtypes = [p, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            L.mg_ctx_tensor_copies.argtypes = [p, i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                               ctypes.POINTER(i)]
             L.mg_ctx_tensor_copies.restype = i
             L.mg_ctx_autotune.argtypes = [p, p]
             L.mg_ctx_autotune.restype = i
@@ -317,15 +318,16 @@ class Solver:
         _check(lib().mg_ctx_autotune(self.ctx, _stream_ptr(stream)), self.ctx)
 
     def tensor_copies(self):
-        """{level: (down, down0)} for the levels whose down leg (from a
-        nonzero start, from zero) takes its planes by tensor copies."""
+        """{level: (down, down0, up)} for the levels where the down leg (from
+        a nonzero start, from zero) or the up leg takes its planes by tensor
+        copies."""
         out = {}
         for l in range(self.n.bit_length()):
-            a, b = ctypes.c_int(0), ctypes.c_int(0)
-            _check(lib().mg_ctx_tensor_copies(self.ctx, l, ctypes.byref(a), ctypes.byref(b)),
-                   self.ctx)
-            if a.value or b.value:
-                out[l] = (a.value, b.value)
+            a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+            _check(lib().mg_ctx_tensor_copies(self.ctx, l, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(c)), self.ctx)
+            if a.value or b.value or c.value:
+                out[l] = (a.value, b.value, c.value)
         return out
 
     def tile_configs(self):
@@ -535,7 +537,7 @@ def op_fused_leg(leg, u, f, h, kinds, omega=1.15, zero_guess=False, ec=None, til
     nz, ny, nx = f.shape
     uo = torch.empty_like(f)
     fc = None
-    if leg != 1:  # 3: the down leg with tensor copies
+    if leg not in (1, 4):  # 3 / 4: the down / up leg with tensor copies
         fc = torch.empty((nz // 2, ny // 2, nx // 2), dtype=f.dtype, device=f.device)
     tx, ty, cz = tile
     _check(lib().mg_op_fused_leg(
@@ -543,7 +545,7 @@ def op_fused_leg(leg, u, f, h, kinds, omega=1.15, zero_guess=False, ec=None, til
         None if (zero_guess or u is None) else _dptr(u, torch.float32), _dptr(uo),
         _dptr(f, torch.float32), None if ec is None else _dptr(ec, torch.float32),
         None if fc is None else _dptr(fc), _stream_ptr(stream)))
-    return uo if leg == 1 else (uo, fc)
+    return uo if leg in (1, 4) else (uo, fc)
 
 
 def op_fx_step(phi_in, e, c, F, kinds, two_pow_S, factor, faces=None, cz=0, stream=None):

@@ -485,6 +485,10 @@ struct Shape {
   static constexpr int NUB = 2;  // pair planes of the u planes' black cells
   static constexpr size_t SMEM =
       (size_t)(NU + NF) * PL * 16 + (size_t)(NRED + NUB + NFIN) * PL2 * 8 + (size_t)NC * 4;
+  // with tensor copies every ring slot starts on a 128-byte boundary: slots
+  // PLS float4 apart, and SMEM_TMA bytes in all
+  static constexpr int PLS = (PL + 7) / 8 * 8;
+  static constexpr size_t SMEM_TMA = SMEM + (size_t)(NU + NF) * (PLS - PL) * 16;
 };
 
 // The program of one CTA on one tile (bx, by) and z-chunk bz; `smem` holds
@@ -506,10 +510,11 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
                                            const void* tmf = nullptr, int* err = nullptr) {
   using S_ = Shape<MODE, TX, TY, HYO, PAD>;
   constexpr int HZ = S_::HZ, HY = S_::HY, RT = S_::RT, RS = S_::RS, RP = S_::RP, PL = S_::PL;
-  float4* s_u = smem;                     // [4][PL] planes of u (async copies)
-  float4* s_f = s_u + S_::NU * PL;        // [4][PL] planes of f (async copies)
+  constexpr int PLS = TMA ? S_::PLS : PL;  // float4 between ring slots
+  float4* s_u = smem;                     // [4][PLS] planes of u (async copies)
+  float4* s_f = s_u + S_::NU * PLS;       // [4][PLS] planes of f (async copies)
   // [2][PL2] pair planes of the red cells after the red half-step
-  float2* s_red = reinterpret_cast<float2*>(s_f + S_::NF * PL);
+  float2* s_red = reinterpret_cast<float2*>(s_f + S_::NF * PLS);
   // [2][PL2] pair planes of the black cells of u (with the correction, on the
   // up leg) as loaded: the red half-step's neighbours
   float2* s_ub = s_red + S_::NRED * S_::PL2;
@@ -578,8 +583,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
         const int zu = PZ ? wrap(qu, p.nz) : qu, zf = PZ ? wrap(qf, p.nz) : qf;
         fence_proxy_async();  // earlier reads of the slots come before the copies
         mbar_expect_tx(bar, (ZERO ? 1u : 2u) * (unsigned)(PL * 16));
-        if (!ZERO) tma_load_3d(&s_u[SU * PL], tmu, x0 - 4, y0 - HY, zu, bar);
-        tma_load_3d(&s_f[SF * PL], tmf, x0 - 4, y0 - HY, zf, bar);
+        if (!ZERO) tma_load_3d(&s_u[SU * PLS], tmu, x0 - 4, y0 - HY, zu, bar);
+        tma_load_3d(&s_f[SF * PLS], tmf, x0 - 4, y0 - HY, zf, bar);
       }
       return;
     }
@@ -587,14 +592,14 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       if (!ZERO) {
         const bool in = col_ok && (PZ || (qu >= 0 && qu < p.nz));
         const unsigned o = (unsigned)(PZ ? wrap(qu, p.nz) : (in ? qu : 0)) * plane + offA;
-        float4* d = &s_u[SU * PL];
+        float4* d = &s_u[SU * PLS];
         cp_async16(&d[ia], u_in + o, in ? 16 : 0);
         cp_async16(&d[ib], u_in + (o + p.nx), in ? 16 : 0);
       }
       const int qf = qu - 1;
       const bool inf = col_ok && (PZ || (qf >= 0 && qf < p.nz));
       const unsigned o = (unsigned)(PZ ? wrap(qf, p.nz) : (inf ? qf : 0)) * plane + offA;
-      float4* d = &s_f[SF * PL];
+      float4* d = &s_f[SF * PLS];
       cp_async16(&d[ia], f + o, inf ? 16 : 0);
       cp_async16(&d[ib], f + (o + p.nx), inf ? 16 : 0);
     }
@@ -662,10 +667,12 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     constexpr int ZP_RED = (QP + 3) % 2;  // parity of plane q-1
     constexpr int ZP_BLK = (QP + 2) % 2;  // parity of plane q-2
     constexpr int ZP_DEF = (QP + 1) % 2;  // parity of plane q-3
-    if (TMA && tma_tile)
+    if (TMA && tma_tile) {
       mbar_wait(&tma_bar[QP], (unsigned)(((q - q_first) >> 2) & 1), err);  // plane q's copies
-    else
+      if (MODE == kUp) cp_async_wait<1>();  // and this thread's copies of the coarse plane
+    } else {
       cp_async_wait<1>();  // this thread's copies of plane q have landed
+    }
     __syncthreads();     // ... and everyone's; the previous step is finished
     issue(std::integral_constant<int, (QP + 2) % 4>{}, std::integral_constant<int, (QP + 1) % 4>{},
           q + 2);
@@ -675,8 +682,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     // [A] plane q of u (old values), plus the prolonged correction (up leg)
     Patch r0 = zero_patch();
     if (!ZERO) {
-      r0.a = unpack(s_u[SL_U * PL + ia]);
-      r0.b = unpack(s_u[SL_U * PL + ib]);
+      r0.a = unpack(s_u[SL_U * PLS + ia]);
+      r0.b = unpack(s_u[SL_U * PLS + ib]);
     }
     if (MODE == kUp) {
       constexpr int KP = (QP >> 1) & 1;  // parity of K = floor(q / 2)
@@ -699,8 +706,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
       s_ub[(QP & 1) * PL2 + pb] = part<(QP & 1) == 0>(r0.b);
     }
     Patch f1;
-    f1.a = unpack(s_f[SL_FM1 * PL + ia]);
-    f1.b = unpack(s_f[SL_FM1 * PL + ib]);
+    f1.a = unpack(s_f[SL_FM1 * PLS + ia]);
+    f1.b = unpack(s_f[SL_FM1 * PLS + ib]);
     // [B] red half-step on plane q-1: the red cells of the even row are its
     // e cells when the plane is even
     {

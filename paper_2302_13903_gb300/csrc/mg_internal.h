@@ -206,6 +206,11 @@ bool down_tma_ok(Grid g, const Bc& bc);
 cudaError_t launch_fused_down_tma(const float* u_in, float* u_out, const float* f, float* fc,
                                   Grid g, double h, double omega, bool zero_guess, int cz,
                                   int* err, cudaStream_t s);
+// The periodic up leg with 64 x 16 tiles whose planes of u and f arrive by
+// tensor copies (mg_fused_tma.cu); *err as for the down leg.
+bool up_tma_ok(Grid g, const Bc& bc);
+cudaError_t launch_fused_up_tma(const float* u_in, float* u_out, const float* f, const float* ec,
+                                Grid g, double h, double omega, int cz, int* err, cudaStream_t s);
 // A host-mapped flag (one per process, host and device share its address)
 // for the leg-3 calls of mg_op_fused_leg; null if it cannot be had.
 int* down_tma_op_flag();

@@ -93,9 +93,9 @@ struct mg_ctx {
   // the autotuner timed the finest level's fused up-down pass faster than the
   // two legs it replaces (opts.leg_pairs = 0 then fuses them)
   bool pairs_faster = false;
-  // per level: the down leg (from a nonzero start / from zero) brings its
-  // planes in by tensor copies (opts.tensor_copies and the autotuner)
-  bool tma_down[kMaxLevels] = {}, tma_down0[kMaxLevels] = {};
+  // per level: the down leg (from a nonzero start / from zero) and the up leg
+  // bring their planes in by tensor copies (opts.tensor_copies, autotuner)
+  bool tma_down[kMaxLevels] = {}, tma_down0[kMaxLevels] = {}, tma_up[kMaxLevels] = {};
 };
 
 namespace {
@@ -367,6 +367,24 @@ bool tma_level(const mg_ctx* c, int l, const Bc& bc, bool zero_guess) {
   return c->opts.tensor_copies == 1 || (zero_guess ? c->tma_down0[l] : c->tma_down[l]);
 }
 
+// The same for the up leg.
+bool tma_up_level(const mg_ctx* c, int l, const Bc& bc) {
+  if (c->opts.tensor_copies == 2 || !mg::up_tma_ok(level_grid(c, l), bc)) return false;
+  return c->opts.tensor_copies == 1 || c->tma_up[l];
+}
+
+// Steps 5-7 of Algorithm 1 on FP32 level l in one pass: u32[l] plus the
+// prolonged correction u32[l-1], smoothed into u32b[l].
+cudaError_t launch_up(mg_ctx* c, int l, const Bc& bc, cudaStream_t s) {
+  const Grid g = level_grid(c, l);
+  const double h = level_h(c, l), om = c->opts.omega;
+  if (tma_up_level(c, l, bc))
+    return mg::launch_fused_up_tma(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, om,
+                                   c->cfg_up[l].cz, c->iflag + 1, s);
+  return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc, om, s,
+                             c->cfg_up[l]);
+}
+
 // Steps 1-3 of Algorithm 1 on FP32 level l in one pass, into u32b[l] and
 // f32[l-1] (the caller swaps the level's buffers).
 cudaError_t launch_down(mg_ctx* c, int l, const Bc& bc, bool zero_guess, cudaStream_t s) {
@@ -416,9 +434,7 @@ void vcycle_fused(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, bool zero_g
   if (post >= 1) {  // 5-7
     {
       KTimer t(c, MG_K_FUSED_UP, fin, s);
-      check(c, mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc_top,
-                                   om, s, c->cfg_up[l]),
-            "fused up");
+      check(c, launch_up(c, l, bc_top, s), "fused up");
       swap_level();
     }
     for (int q = 1; q < post; ++q) {
@@ -487,9 +503,7 @@ void vcycles_paired(mg_ctx* c, int l, const Bc& bc_top, const Bc& hom, int cycle
     coarse_correction(c, l, hom, s);
   }
   KTimer t(c, MG_K_FUSED_UP, fin, s);
-  check(c, mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc_top, om,
-                               s, c->cfg_up[l]),
-        "fused up");
+  check(c, launch_up(c, l, bc_top, s), "fused up");
   swap_level();
 }
 
@@ -1014,7 +1028,8 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   }
   bool tma = false;
   for (int l = 1; l < c->L; ++l)
-    tma = tma || tma_level(c, l, hom, false) || tma_level(c, l, hom, true);
+    tma = tma || tma_level(c, l, hom, false) || tma_level(c, l, hom, true) ||
+          tma_up_level(c, l, hom);
   if (tma) {  // a down leg whose tensor copies did not land in time raised iflag[1]
     int late = 0;
     check(c, cudaMemcpyAsync(c->pinned + 61, c->iflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s),
@@ -1063,7 +1078,8 @@ enum TuneKind {
   TUNE_FX = 3,
   TUNE_UD = 4,      // shape of the fused up-down pass
   TUNE_UD_WIN = 5,  // cz = 1 when that pass beat the two legs it replaces
-  TUNE_TMA = 6      // tx = 1 / cz = 1: the down leg with tensor copies won from zero / not
+  TUNE_TMA = 7      // tx / cz / ty = 1: tensor copies won for the down leg from zero / the
+                    // down leg from a nonzero start / the up leg
 };
 
 struct TuneKey {
@@ -1229,10 +1245,22 @@ void autotune(mg_ctx* c, cudaStream_t s) {
             });
             (zg ? v.tx : v.cz) = tma_ms < plain_ms ? 1 : 0;
           }
+          if (mg::up_tma_ok(g, hom)) {
+            const float plain_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+              return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h,
+                                         hom, om, s, c->cfg_up[l]);
+            });
+            const float tma_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+              return mg::launch_fused_up_tma(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g,
+                                             h, om, c->cfg_up[l].cz, c->iflag + 1, s);
+            });
+            v.ty = tma_ms < plain_ms ? 1 : 0;
+          }
           tune_store_locked(key, v);
         }
         c->tma_down0[l] = v.tx == 1;
         c->tma_down[l] = v.cz == 1;
+        c->tma_up[l] = v.ty == 1;
       }
       // the fused up-down pass of the finest level's inner cycles
       if (l == F && c->opts.leg_pairs != 2 && pairs_ok(c, l, hom, hom, 2)) {
@@ -1403,12 +1431,13 @@ mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, in
   return MG_OK;
 }
 
-mg_status mg_ctx_tensor_copies(const mg_ctx* c, int level, int* down, int* down0) {
-  if (!c || !down || !down0 || level < 0 || level >= c->L) return MG_ERR_ARG;
+mg_status mg_ctx_tensor_copies(const mg_ctx* c, int level, int* down, int* down0, int* up) {
+  if (!c || !down || !down0 || !up || level < 0 || level >= c->L) return MG_ERR_ARG;
   const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr, c->face_mask});
   const bool fp32 = c->opts.prec == MG_MIXED && level > 0 && c->u32b[level];
   *down = fp32 && tma_level(c, level, hom, false) ? 1 : 0;
   *down0 = fp32 && tma_level(c, level, hom, true) ? 1 : 0;
+  *up = fp32 && tma_up_level(c, level, hom) ? 1 : 0;
   return MG_OK;
 }
 
@@ -1934,15 +1963,16 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
   const Grid g{nx, ny, nz};
   const mg::TileCfg cfg{tx, cz, ty};
   const bool down = leg == 0 || leg == 3;
-  bool ok = leg >= 0 && leg <= 3 && face_rule(face_bc, &b) && h > 0.0 && omega > 0.0 &&
+  bool ok = leg >= 0 && leg <= 4 && face_rule(face_bc, &b) && h > 0.0 && omega > 0.0 &&
             omega < 2.0 && u_out && f && (u_in || (down && zero_guess)) && u_in != u_out &&
-            (leg == 1 || fc != nullptr) && (down || ec != nullptr) && (down || !zero_guess);
+            (leg == 1 || leg == 4 || fc != nullptr) && (down || ec != nullptr) && (down || !zero_guess);
   if (ok) {
     b = mg::collapse_homogeneous(b);
     ok = mg::fused_ok(g, b) && mg::fused_cfg_ok(g, cfg) && (tx == 0 || tx == 32 || tx == 64) &&
          (ty == 0 || ty == 16 || ty == 32) && cz >= 0;
     if (leg == 2) ok = mg::updown_ok(g, b) && mg::updown_cfg_ok(g, cfg);
     if (leg == 3) ok = ok && mg::down_tma_ok(g, b) && (tx == 0 || tx == 64) && (ty == 0 || ty == 32);
+    if (leg == 4) ok = ok && mg::up_tma_ok(g, b) && (tx == 0 || tx == 64) && (ty == 0 || ty == 16);
   }
   if (!ok) {
     g_err = "mg_op_fused_leg: invalid argument, or a grid or shape the fused kernels do not take";
@@ -1956,7 +1986,7 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
     e = mg::launch_fused_up(u_in, u_out, f, ec, g, h, b, omega, s, cfg);
   else if (leg == 2)
     e = mg::launch_fused_updown(u_in, u_out, f, ec, fc, g, h, b, omega, s, cfg);
-  else {
+  else {  // 3, 4: the down and up legs with tensor copies
     volatile int* late = mg::down_tma_op_flag();
     if (!late) return op_result(cudaErrorMemoryAllocation, "fused_leg");
     if (*late) {  // raised by an earlier call's kernel, finished by now
@@ -1964,8 +1994,11 @@ mg_status mg_op_fused_leg(int leg, int nx, int ny, int nz, double h, const int* 
       g_err = "mg_op_fused_leg: a tensor copy of an earlier leg-3 call did not land in time";
       return MG_ERR_TIMEOUT;
     }
-    e = mg::launch_fused_down_tma(u_in, u_out, f, fc, g, h, omega, zero_guess != 0, cz,
-                                  const_cast<int*>(late), s);
+    if (leg == 3)
+      e = mg::launch_fused_down_tma(u_in, u_out, f, fc, g, h, omega, zero_guess != 0, cz,
+                                    const_cast<int*>(late), s);
+    else
+      e = mg::launch_fused_up_tma(u_in, u_out, f, ec, g, h, omega, cz, const_cast<int*>(late), s);
   }
   return op_result(e, "fused_leg");
 }

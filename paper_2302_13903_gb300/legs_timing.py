@@ -5,7 +5,7 @@ python -m paper_2302_13903_gb300.legs_timing LEGS [REPS] [NZ NY NX]
 
 LEGS is a comma-separated list of down (SMOOTH + defect + restriction, 64 x 32
 tiles, 64 planes per CTA), down0 (the same from a zero start), tma / tma0 (down
-/ down0 with the planes brought in by tensor copies), up
+/ down0 with the planes brought in by tensor copies), upt (up, the same way), up
 (prolongation + correction + SMOOTH, 64 x 16 tiles), ud16 / ud32 (the up leg
 of one V-cycle fused with the down leg of the next, 16- or 32-row tiles), fx
 (the fixed-point outer step, 64 planes per CTA), all periodic.  Each leg runs
@@ -21,7 +21,7 @@ import torch
 
 from . import PERIODIC, op_fused_leg, op_fx_step
 
-SHAPES = {"down": (64, 32, 64), "down0": (64, 32, 64), "tma": (64, 32, 64), "tma0": (64, 32, 64), "up": (64, 16, 64),
+SHAPES = {"down": (64, 32, 64), "down0": (64, 32, 64), "tma": (64, 32, 64), "tma0": (64, 32, 64), "upt": (64, 16, 64), "up": (64, 16, 64),
           "ud16": (64, 16, 128), "ud32": (64, 32, 64), "fx": (32, 16, 64)}
 
 
@@ -51,6 +51,8 @@ def main(argv):
             return op_fused_leg(3, u, f, h, kinds, zero_guess=(leg == "tma0"), tile=tile)
         if leg == "up":
             return op_fused_leg(1, u, f, h, kinds, ec=ec, tile=tile)
+        if leg == "upt":
+            return op_fused_leg(4, u, f, h, kinds, ec=ec, tile=tile)
         return op_fused_leg(2, u, f, h, kinds, ec=ec, tile=tile)
 
     for leg in legs:

@@ -128,6 +128,22 @@ def test_fused_down_with_tensor_copies_matches_plain_down_leg(zero):
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), cz
 
 
+def test_fused_up_with_tensor_copies_matches_plain_up_leg():
+    """Leg 4: the periodic up leg whose tiles inside the level take their
+    planes of u and f by tensor copies: bit for bit leg 1's results."""
+    rng = np.random.default_rng(34)
+    nz, ny, nx = 48, 64, 256  # 2 x 2 of the 4 x 4 tiles lie inside the level
+    u, f = (torch.from_numpy(rng.standard_normal((nz, ny, nx)).astype(np.float32)).cuda()
+            for _ in range(2))
+    ec = torch.from_numpy(rng.standard_normal((nz // 2, ny // 2, nx // 2)).astype(np.float32))
+    ec = ec.cuda()
+    for cz in (8, 16, 0):
+        a = mg.op_fused_leg(1, u, f, 1.0 / nx, [P] * 6, ec=ec, tile=(64, 16, cz))
+        b = mg.op_fused_leg(4, u, f, 1.0 / nx, [P] * 6, ec=ec, tile=(64, 16, cz))
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), cz
+
+
 def test_fused_leg_rejects_shapes_it_does_not_take():
     f = torch.zeros((64, 48, 64), device="cuda")  # 48 rows: 16-row tiles only
     mg.op_fused_leg(0, f, f, 1.0, [P] * 6, tile=(64, 16, 8))  # taken

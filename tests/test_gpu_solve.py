@@ -458,12 +458,13 @@ def test_paired_legs_give_the_same_bits(bc, n):
 
 
 def test_tensor_copies_give_the_same_bits():
-    """The down leg with its planes brought in by tensor copies
-    (opts.tensor_copies = 1) runs the same per-cell arithmetic as with
+    """The fused legs with their planes brought in by tensor copies
+    (opts.tensor_copies = 1) run the same per-cell arithmetic as with
     per-thread copies (2), and so does whatever the autotuner picks (0): the
     same phi and residual history, bit for bit (the tuned run's history up
     to the summation order of its norm).  Tensor copies apply to the
-    periodic levels at least 64 cells wide with rows in 32s."""
+    periodic levels at least 64 cells wide (the down leg's with rows in
+    32s)."""
     n = 128
     rho, fpg = source(n, mg.PERIODIC, seed=37)
     a = gpu_solve(rho, mg.PERIODIC, fpg, 1e-10, prec=mg.MIXED, tensor_copies=1)
@@ -471,7 +472,7 @@ def test_tensor_copies_give_the_same_bits():
     assert a[2] == b[2] == 0
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED, tensor_copies=1) as s:
-        assert s.tensor_copies() == {6: (1, 1), 7: (1, 1)}  # the 64^3 and 128^3 levels
+        assert s.tensor_copies() == {6: (1, 1, 1), 7: (1, 1, 1)}  # the 64^3 and 128^3 levels
     with mg.Solver(n, 1.0 / n, mg.PERIODIC, prec=mg.MIXED, tensor_copies=2) as s:
         assert s.tensor_copies() == {}
     with mg.Solver(n, 1.0 / n, mg.FIXED, prec=mg.MIXED, tensor_copies=1) as s:
