@@ -42,7 +42,9 @@ def algorithmic_bytes_per_cell(kernel: str, w: int, fixed_point: bool = True) ->
         # the plain FP64 residual: FP64 u, f in, FP32 r out
         "outer_residual": 32.0 if fixed_point else 20.0,
         "correct": 20.0,                # FP64 u, FP32 e -> FP64 u
-        "source": 16.0,                 # FP64 rho -> FP64 f
+        # FP64 rho -> FP64 f; on the mixed path's fixed-point start only the
+        # pass over rho for its sum and maximum (read rho)
+        "source": 8.0 if fixed_point else 16.0,
         "fused_down": 3.0 * w + w / 8.0,  # read u, f; write u, coarse f
         "fused_down0": 2.0 * w + w / 8.0,  # from a zero start: read f; write u, coarse f
         "fused_up": 3.0 * w + w / 8.0,    # read u, coarse e, f; write u
@@ -622,7 +624,7 @@ def main():
         if nl == 0:
             continue
         w = 4 if (prec == mg.MIXED and k in FP32_CLASSES) else 8
-        alg = algorithmic_bytes_per_cell(k, w) * n ** 3
+        alg = algorithmic_bytes_per_cell(k, w, fixed_point=(prec == mg.MIXED)) * n ** 3
         ach = alg / (tot_ms / nl * 1e-3) / 1e9
         by_class[k] = {"launches_per_solve": nl / args.steps, "ms_per_launch": tot_ms / nl,
                        "algorithmic_bytes_per_launch": alg, "achieved_gbs": ach,
