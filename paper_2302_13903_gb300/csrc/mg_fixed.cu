@@ -660,35 +660,10 @@ cudaError_t launch_convert(int kind, long long n, const void* in, void* out, cud
   return cudaGetLastError();
 }
 
-// Blocks of k_rho_stats: one full wave (its registers allow fewer resident
-// blocks per SM than the other passes, and a second, partial wave would leave
-// most SMs idle), at most reduce_blocks(n2).
-int rho_stats_blocks(long long n2) {
-  static std::atomic<int> per_sm[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    return reduce_blocks(n2);
-  }
-  int k = per_sm[dev].load();
-  if (k == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_rho_stats, kThreads, 0) !=
-            cudaSuccess ||
-        k < 1) {
-      cudaGetLastError();
-      k = 4;
-    }
-    per_sm[dev].store(k);
-  }
-  const long long full = (long long)k * sm_count();
-  const int nb = reduce_blocks(n2);
-  return nb < full ? nb : (int)full;
-}
-
 cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, double* out,
                              cudaStream_t s) {
   if (n % 2) return cudaErrorInvalidValue;
-  const int nb = rho_stats_blocks(n / 2);
+  const int nb = reduce_blocks(n / 2);
   // at most 2^14 values per thread in the exact sums (2^32 cells, 34 GB of rho)
   if (n > (long long)nb * kThreads * 16384) return cudaErrorInvalidValue;
   ++g_launches;
@@ -702,7 +677,7 @@ cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, d
 cudaError_t launch_rho_stats_copy(const double* host_rho, double* dev, long long n,
                                   double* partials, double* out, cudaStream_t s) {
   if (n % 2) return cudaErrorInvalidValue;
-  const int nb = rho_stats_blocks(n / 2);
+  const int nb = reduce_blocks(n / 2);
   if (n > (long long)nb * kThreads * 16384) return cudaErrorInvalidValue;
   ++g_launches;
   k_rho_stats<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(host_rho), n / 2, partials,
