@@ -365,9 +365,18 @@ struct FxRing {
 };
 constexpr size_t kFxSmem = sizeof(FxRing);
 
+// CTAs per SM the step's registers are sized for: three (at most 40
+// registers), except for the masks whose ghosts need more (0: no periodic
+// axis, 1: only x, 2: only y), which spilled at 40 and run 11 % faster at two
+// CTAs per SM without spills (256 x 256 x 512 box).
+template <int PM>
+constexpr int fx_min_blocks() {
+  return (PM == 0 || PM == 1 || PM == 2) ? 2 : 3;
+}
+
 // PM: the periodic axes (bit 0 x, 1 y, 2 z).
 template <int PM, bool ZERO_IN>
-__global__ void __launch_bounds__(FX_TX* FX_TY, 3)
+__global__ void __launch_bounds__(FX_TX* FX_TY, fx_min_blocks<PM>())
     k_fx_step(const long long* __restrict__ phi_in, long long* __restrict__ phi_out,
               const float* __restrict__ e, float c, const long long* __restrict__ F,
               float* __restrict__ r32, Grid g, FxBc bc, float factor, int cz,

@@ -800,14 +800,17 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
 // Register caps.  The register file is split among the four schedulers, so
 // two 7-warp CTAs (down leg, 16-row tiles) fit on an SM at <= 128 registers
 // and three 6-warp CTAs (up leg) at <= 96; the 32-row tiles take one CTA per
-// SM (their shared memory alone decides).
-template <int MODE, int TY>
+// SM (their shared memory alone decides).  The up leg with a non-periodic face
+// needs more than 96 registers: it takes 128 and two CTAs per SM, which
+// measured 28-33 % faster than spilling at three (mask 0, 1, 4 on a
+// 256 x 256 x 512 box) and no slower for mask 3.
+template <int MODE, int TY, int PM = 7>
 constexpr int fused_max_regs() {
-  return TY == 16 ? (MODE == kUp ? 96 : 128) : 168;
+  return TY == 16 ? (MODE == kUp ? (PM == 7 ? 96 : 128) : 128) : 168;
 }
 
 template <int MODE, bool ZERO, int PM, int TX, int TY>
-__global__ void __maxnreg__((fused_max_regs<MODE, TY>()))
+__global__ void __maxnreg__((fused_max_regs<MODE, TY, PM>()))
     k_fused(const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
             const float* __restrict__ ec, float* __restrict__ fc, FusedParams p) {
   extern __shared__ float4 smem[];
