@@ -116,10 +116,10 @@ struct ExactSum {
 
 __device__ __forceinline__ void exact_add(ExactSum& a, double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned uh = (unsigned)(u >> 32), ul = (unsigned)u;
+  const int e = (int)((uh >> 20) & 0x7ff);
   if (e == 0) return;
-  const unsigned long long m = (u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-  const int k = e - 1075;  // x = +-m 2^k
+  const int k = e - 1075;  // x = +-m 2^k, m = mh 2^32 + ul
   if (k - a.B > 60) {  // a new largest exponent: A >>= d (arithmetic), B += d
     const int d = k - 60 - a.B;
     if (d >= 128) {
@@ -135,22 +135,30 @@ __device__ __forceinline__ void exact_add(ExactSum& a, double x) {
     a.B = k - 60;
   }
   const int sh = k - a.B;  // <= 60
-  unsigned long long tlo = 0, thi = 0;
+  unsigned long long tlo, thi;
   if (sh >= 0) {
-    tlo = m << sh;
-    thi = sh > 11 ? m >> (64 - sh) : 0;  // m < 2^53: bits reach the high word from sh = 12
+    // m << sh as four 32-bit words: shift by sh mod 32 with funnel shifts,
+    // then up one word when sh >= 32 (m < 2^53, sh <= 60: 113 bits at most)
+    const unsigned mh = (uh & 0xFFFFFu) | 0x100000u;
+    const unsigned r = (unsigned)sh & 31u;
+    const unsigned x0 = ul << r, x1 = __funnelshift_l(ul, mh, r), x2 = __funnelshift_l(mh, 0u, r);
+    const bool up = sh >= 32;
+    tlo = ((unsigned long long)(up ? x0 : x1) << 32) | (up ? 0u : x0);
+    thi = ((unsigned long long)(up ? x2 : 0u) << 32) | (up ? x1 : x2);
   } else if (sh > -64) {
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
     tlo = m >> -sh;
-  }
-  if (u >> 63) {
-    const unsigned long long lo = a.lo - tlo;
-    a.hi = a.hi - (long long)thi - (lo > a.lo ? 1 : 0);
-    a.lo = lo;
+    thi = 0;
   } else {
-    const unsigned long long lo = a.lo + tlo;
-    a.hi = a.hi + (long long)thi + (lo < tlo ? 1 : 0);
-    a.lo = lo;
+    return;
   }
+  // A -= T or A += T with the carry chained through the two words
+  unsigned long long hi = (unsigned long long)a.hi;
+  if (uh >> 31)
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(hi) : "l"(tlo), "l"(thi));
+  else
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(hi) : "l"(tlo), "l"(thi));
+  a.hi = (long long)hi;
 }
 
 // The thread's sum as a double (rounded in the conversions of its two words).
