@@ -58,13 +58,44 @@ __device__ __forceinline__ double block_reduce(double v) {
 }
 
 // max |a| in the array's own precision (no FP64 work for FP32 data)
-template <typename T>
+// VEC (FP32, 16-byte aligned): four values per 16-byte load, four loads in
+// flight per thread.
+template <typename T, bool VEC = false>
 __global__ void k_absmax(const T* __restrict__ a, long long n, double* __restrict__ partials) {
   T m = T(0);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const T v = a[t] < T(0) ? -a[t] : a[t];
+  auto take = [&](T x) {
+    const T v = x < T(0) ? -x : x;
     m = v > m ? v : m;
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if constexpr (VEC) {
+    const long long n4 = n >> 2;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    for (; t + 3 * stride < n4; t += 4 * stride) {
+      float4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = a4[t + k * stride];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        take(v[k].x);
+        take(v[k].y);
+        take(v[k].z);
+        take(v[k].w);
+      }
+    }
+    for (; t < n4; t += stride) {
+      const float4 v = a4[t];
+      take(v.x);
+      take(v.y);
+      take(v.z);
+      take(v.w);
+    }
+    for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += stride)
+      take(a[i]);
+  } else {
+    for (; t < n; t += stride) take(a[t]);
   }
   const double r = block_reduce<true>((double)m);
   if (threadIdx.x == 0) partials[blockIdx.x] = r;
@@ -87,12 +118,47 @@ __global__ void k_f64_to_fx(double* a, long long n, double mu, double c) {
 
 // out[t] = (q[t] - M) 2^-S as a double (out may alias q), M = *mean (the
 // integers' rounded mean) when given, else 0.  Integer arithmetic only.
+// out[i] = op(in[i]) over n 8-byte elements.  PAIRS: both arrays are 16-byte
+// aligned, so a thread moves two elements per 16-byte load and store, with
+// four such loads in flight before their results are stored (each element is
+// read before it is written, so in == out is allowed).
+template <bool PAIRS, typename Op>
+__device__ __forceinline__ void stream8(const unsigned long long* in, unsigned long long* out,
+                                        long long n, Op op) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if constexpr (!PAIRS) {
+    for (; t < n; t += stride) out[t] = op(in[t]);
+    return;
+  }
+  const long long n2 = n >> 1;
+  const ulonglong2* in2 = reinterpret_cast<const ulonglong2*>(in);
+  ulonglong2* out2 = reinterpret_cast<ulonglong2*>(out);
+  for (; t + 3 * stride < n2; t += 4 * stride) {
+    ulonglong2 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = in2[t + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out2[t + k * stride] = make_ulonglong2(op(v[k].x), op(v[k].y));
+  }
+  for (; t < n2; t += stride) {
+    const ulonglong2 v = in2[t];
+    out2[t] = make_ulonglong2(op(v.x), op(v.y));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[n - 1] = op(in[n - 1]);
+}
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <bool PAIRS>
 __global__ void k_fx_to_f64(const long long* q, double* out, long long n, int S,
                             const long long* __restrict__ mean) {
   const long long M = mean ? mean[0] : 0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    out[t] = cvt::ll2d_pow2_rn(q[t] - M, S);
+  stream8<PAIRS>(reinterpret_cast<const unsigned long long*>(q),
+                 reinterpret_cast<unsigned long long*>(out), n, [&](unsigned long long v) {
+                   return (unsigned long long)__double_as_longlong(
+                       cvt::ll2d_pow2_rn((long long)v - M, S));
+                 });
 }
 
 // |x| as an unsigned integer: for non-negative doubles (and floats) the order
@@ -238,11 +304,13 @@ __global__ void k_rho_to_r32(const double2* __restrict__ rho, float2* __restrict
 }
 
 // In place into the integer array q: round(a rho - b) (the fixed-point h^2 f).
+template <bool PAIRS>
 __global__ void k_rho_to_fx(const double* __restrict__ rho, long long* __restrict__ q, long long n,
                             double a, double b) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    q[t] = cvt::d2ll_rn(fma(a, rho[t], -b));
+  stream8<PAIRS>(reinterpret_cast<const unsigned long long*>(rho),
+                 reinterpret_cast<unsigned long long*>(q), n, [&](unsigned long long v) {
+                   return (unsigned long long)cvt::d2ll_rn(fma(a, __longlong_as_double(v), -b));
+                 });
 }
 
 __global__ void k_finish_sum_max(const double* __restrict__ sum, const double* __restrict__ mx,
@@ -630,7 +698,10 @@ template <typename T>
 cudaError_t launch_absmax(const T* a, long long n, double* partials, double* out, cudaStream_t s) {
   const int nb = reduce_blocks(n);
   ++g_launches;
-  k_absmax<T><<<nb, kThreads, 0, s>>>(a, n, partials);
+  if (sizeof(T) == 4 && aligned16(a))
+    k_absmax<T, sizeof(T) == 4><<<nb, kThreads, 0, s>>>(a, n, partials);
+  else
+    k_absmax<T><<<nb, kThreads, 0, s>>>(a, n, partials);
   ++g_launches;
   k_finish_max<<<1, kThreads, 0, s>>>(partials, nb, out);
   return cudaGetLastError();
@@ -647,7 +718,10 @@ cudaError_t launch_f64_to_fx(double* a, long long n, double mu, double c, cudaSt
 cudaError_t launch_fx_to_f64(const long long* q, double* out, long long n, int S,
                              const long long* mean, cudaStream_t s) {
   ++g_launches;
-  k_fx_to_f64<<<grid_for(n), kThreads, 0, s>>>(q, out, n, S, mean);
+  if (aligned16(q) && aligned16(out))
+    k_fx_to_f64<true><<<grid_for(n / 8), kThreads, 0, s>>>(q, out, n, S, mean);
+  else
+    k_fx_to_f64<false><<<grid_for(n), kThreads, 0, s>>>(q, out, n, S, mean);
   return cudaGetLastError();
 }
 
@@ -720,7 +794,10 @@ cudaError_t launch_rho_to_r32(const double* rho, float* r32, long long n, double
 cudaError_t launch_rho_to_fx(const double* rho, long long* q, long long n, double a, double b,
                              cudaStream_t s) {
   ++g_launches;
-  k_rho_to_fx<<<grid_for(n), kThreads, 0, s>>>(rho, q, n, a, b);
+  if (aligned16(rho) && aligned16(q))
+    k_rho_to_fx<true><<<grid_for(n / 8), kThreads, 0, s>>>(rho, q, n, a, b);
+  else
+    k_rho_to_fx<false><<<grid_for(n), kThreads, 0, s>>>(rho, q, n, a, b);
   return cudaGetLastError();
 }
 
