@@ -491,9 +491,11 @@ size_t mg_faces_count(int nx, int ny, int nz);
 mg_status mg_ctx_autotune(mg_ctx *ctx, void *stream);
 
 /* The shape (tile width tx, height ty, planes cz) chosen for a kernel class on
- * a level (MG_K_FUSED_DOWN, MG_K_FUSED_UP, MG_K_FUSED_UPDOWN, MG_K_SOR for
- * extra fused smoothing steps, MG_K_OUTER_RESIDUAL for the fixed-point step on
- * the finest level); 0 means the built-in choice. */
+ * a level (MG_K_FUSED_DOWN, MG_K_FUSED_DOWN0, MG_K_FUSED_UP, MG_K_FUSED_UPDOWN,
+ * MG_K_SOR for extra fused smoothing steps, MG_K_OUTER_RESIDUAL for the
+ * fixed-point step on the finest level); 0 means the built-in choice.  Where a
+ * leg takes its planes by tensor copies (mg_ctx_tensor_copies) the shape is
+ * that variant's (64 x 32 down, 64 x 16 up). */
 mg_status mg_ctx_tile_config(const mg_ctx *ctx, int level, int kernel, int *tx, int *ty,
                              int *cz);
 

@@ -96,6 +96,8 @@ struct mg_ctx {
   // per level: the down leg (from a nonzero start / from zero) and the up leg
   // bring their planes in by tensor copies (opts.tensor_copies, autotuner)
   bool tma_down[kMaxLevels] = {}, tma_down0[kMaxLevels] = {}, tma_up[kMaxLevels] = {};
+  // their planes per CTA (0: built-in choice)
+  int tma_cz_down[kMaxLevels] = {}, tma_cz_down0[kMaxLevels] = {}, tma_cz_up[kMaxLevels] = {};
 };
 
 namespace {
@@ -380,7 +382,7 @@ cudaError_t launch_up(mg_ctx* c, int l, const Bc& bc, cudaStream_t s) {
   const double h = level_h(c, l), om = c->opts.omega;
   if (tma_up_level(c, l, bc))
     return mg::launch_fused_up_tma(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, om,
-                                   c->cfg_up[l].cz, c->iflag + 1, s);
+                                   c->tma_cz_up[l], c->iflag + 1, s);
   return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h, bc, om, s,
                              c->cfg_up[l]);
 }
@@ -392,7 +394,9 @@ cudaError_t launch_down(mg_ctx* c, int l, const Bc& bc, bool zero_guess, cudaStr
   const double h = level_h(c, l), om = c->opts.omega;
   if (tma_level(c, l, bc, zero_guess))
     return mg::launch_fused_down_tma(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, om,
-                                     zero_guess, c->cfg_down[l].cz, c->iflag + 1, s);
+                                     zero_guess,
+                                     zero_guess ? c->tma_cz_down0[l] : c->tma_cz_down[l],
+                                     c->iflag + 1, s);
   return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h, bc, om,
                                zero_guess, s, c->cfg_down[l]);
 }
@@ -1078,8 +1082,9 @@ enum TuneKind {
   TUNE_FX = 3,
   TUNE_UD = 4,      // shape of the fused up-down pass
   TUNE_UD_WIN = 5,  // cz = 1 when that pass beat the two legs it replaces
-  TUNE_TMA = 7      // tx / cz / ty = 1: tensor copies won for the down leg from zero / the
+  TUNE_TMA = 7,     // tx / cz / ty = 1: tensor copies won for the down leg from zero / the
                     // down leg from a nonzero start / the up leg
+  TUNE_TMA_CZ = 8   // tx / cz / ty: those three legs' planes per CTA with tensor copies
 };
 
 struct TuneKey {
@@ -1198,10 +1203,12 @@ void autotune(mg_ctx* c, cudaStream_t s) {
           best = hit->second;
         } else {
           float best_ms = 1e30f;
-          for (int cand_i = 0; cand_i < 16; ++cand_i) {
+          for (int cand_i = 0; cand_i < 32; ++cand_i) {
             {
               const int tx = (cand_i & 1) ? 64 : 32, ty = (cand_i & 2) ? 32 : 16;
-              const int cz = 8 << (cand_i >> 2);  // 8, 16, 32, 64
+              // 8, 16, ..., 64 planes: the chunks that are not powers of two
+              // even out the last wave of CTAs on some grids
+              const int cz = 8 * (1 + (cand_i >> 2));
               const mg::TileCfg cand{tx, cz, ty};
               if (cz > g.nz || !mg::fused_cfg_ok(g, cand)) continue;
               const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
@@ -1224,43 +1231,86 @@ void autotune(mg_ctx* c, cudaStream_t s) {
         }
         (kind == TUNE_DOWN ? c->cfg_down : kind == TUNE_UP ? c->cfg_up : c->cfg_smooth)[l] = best;
       }
-      // the down leg with tensor copies against the per-thread copies, from a
-      // zero start and from a nonzero one
+      // the legs with tensor copies against the per-thread copies: each
+      // variant's best z-chunk, then the two winners timed in alternation
+      // (three rounds), since they are often within a few per cent
       if (c->opts.tensor_copies == 0 && mg::down_tma_ok(g, hom)) {
         const TuneKey key{prop.multiProcessorCount, prop.major, prop.minor, TUNE_TMA, g.nx, g.ny,
                           g.nz, periodic};
-        mg::TileCfg v{0, 0, 0};
+        const TuneKey czkey{prop.multiProcessorCount, prop.major, prop.minor, TUNE_TMA_CZ, g.nx,
+                            g.ny, g.nz, periodic};
+        mg::TileCfg v{0, 0, 0}, w{0, 0, 0};
         auto hit = g_tune.find(key);
-        if (hit != g_tune.end()) {
+        auto czhit = g_tune.find(czkey);
+        if (hit != g_tune.end() && czhit != g_tune.end()) {
           v = hit->second;
+          w = czhit->second;
         } else {
+          auto best_cz = [&](int ty, auto run) {
+            float best = 1e30f;
+            int bcz = 0;
+            for (int cz = 8; cz <= 64; cz += 8) {
+              if (cz > g.nz || !mg::fused_cfg_ok(g, mg::TileCfg{64, cz, ty})) continue;
+              const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() { return run(cz); });
+              if (ms < best) {
+                best = ms;
+                bcz = cz;
+              }
+            }
+            return bcz;
+          };
+          auto second_faster = [&](auto run_a, auto run_b) {
+            float a = 0.f, b = 0.f;
+            for (int r = 0; r < 3; ++r) {
+              a += time_launches(c, s, reps, flush, flush_bytes, run_a);
+              b += time_launches(c, s, reps, flush, flush_bytes, run_b);
+            }
+            return b < a;
+          };
           for (const bool zg : {true, false}) {
-            const float plain_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
-              return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g, h,
-                                           hom, om, zg, s, c->cfg_down[l]);
-            });
-            const float tma_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+            const int cz = best_cz(32, [&](int z) {
               return mg::launch_fused_down_tma(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g,
-                                               h, om, zg, c->cfg_down[l].cz, c->iflag + 1, s);
+                                               h, om, zg, z, c->iflag + 1, s);
             });
-            (zg ? v.tx : v.cz) = tma_ms < plain_ms ? 1 : 0;
+            const bool win = second_faster(
+                [&]() {
+                  return mg::launch_fused_down(c->u32[l], c->u32b[l], c->f32[l], c->f32[l - 1], g,
+                                               h, hom, om, zg, s, c->cfg_down[l]);
+                },
+                [&]() {
+                  return mg::launch_fused_down_tma(c->u32[l], c->u32b[l], c->f32[l],
+                                                   c->f32[l - 1], g, h, om, zg, cz, c->iflag + 1,
+                                                   s);
+                });
+            (zg ? v.tx : v.cz) = win ? 1 : 0;
+            (zg ? w.tx : w.cz) = cz;
           }
           if (mg::up_tma_ok(g, hom)) {
-            const float plain_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
-              return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g, h,
-                                         hom, om, s, c->cfg_up[l]);
-            });
-            const float tma_ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {
+            const int cz = best_cz(16, [&](int z) {
               return mg::launch_fused_up_tma(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g,
-                                             h, om, c->cfg_up[l].cz, c->iflag + 1, s);
+                                             h, om, z, c->iflag + 1, s);
             });
-            v.ty = tma_ms < plain_ms ? 1 : 0;
+            const bool win = second_faster(
+                [&]() {
+                  return mg::launch_fused_up(c->u32[l], c->u32b[l], c->f32[l], c->u32[l - 1], g,
+                                             h, hom, om, s, c->cfg_up[l]);
+                },
+                [&]() {
+                  return mg::launch_fused_up_tma(c->u32[l], c->u32b[l], c->f32[l],
+                                                 c->u32[l - 1], g, h, om, cz, c->iflag + 1, s);
+                });
+            v.ty = win ? 1 : 0;
+            w.ty = cz;
           }
           tune_store_locked(key, v);
+          tune_store_locked(czkey, w);
         }
         c->tma_down0[l] = v.tx == 1;
         c->tma_down[l] = v.cz == 1;
         c->tma_up[l] = v.ty == 1;
+        c->tma_cz_down0[l] = w.tx;
+        c->tma_cz_down[l] = w.cz;
+        c->tma_cz_up[l] = w.ty;
       }
       // the fused up-down pass of the finest level's inner cycles
       if (l == F && c->opts.leg_pairs != 2 && pairs_ok(c, l, hom, hom, 2)) {
@@ -1419,7 +1469,15 @@ mg_status mg_ctx_autotune(mg_ctx* c, void* stream) {
 mg_status mg_ctx_tile_config(const mg_ctx* c, int level, int kernel, int* tx, int* ty, int* cz) {
   if (!c || !tx || !ty || !cz || level < 0 || level >= c->L) return MG_ERR_ARG;
   mg::TileCfg v;
-  if (kernel == MG_K_FUSED_DOWN || kernel == MG_K_FUSED_DOWN0) v = c->cfg_down[level];
+  const Bc hom = mg::homogeneous(Bc{c->bc_kind, c->opts.fixed_value, nullptr, c->face_mask});
+  const bool fp32 = c->opts.prec == MG_MIXED && level > 0 && c->u32b[level];
+  if (fp32 && kernel == MG_K_FUSED_DOWN && tma_level(c, level, hom, false))
+    v = mg::TileCfg{64, c->tma_cz_down[level], 32};  // the leg with tensor copies
+  else if (fp32 && kernel == MG_K_FUSED_DOWN0 && tma_level(c, level, hom, true))
+    v = mg::TileCfg{64, c->tma_cz_down0[level], 32};
+  else if (fp32 && kernel == MG_K_FUSED_UP && tma_up_level(c, level, hom))
+    v = mg::TileCfg{64, c->tma_cz_up[level], 16};
+  else if (kernel == MG_K_FUSED_DOWN || kernel == MG_K_FUSED_DOWN0) v = c->cfg_down[level];
   else if (kernel == MG_K_FUSED_UPDOWN) v = c->cfg_ud[level];
   else if (kernel == MG_K_FUSED_UP) v = c->cfg_up[level];
   else if (kernel == MG_K_SOR) v = c->cfg_smooth[level];
