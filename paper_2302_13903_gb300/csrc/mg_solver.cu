@@ -989,6 +989,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
     st = rule.decide(r, it + 1, c->opts.max_cycles, n, hist_cap);
     if (st >= 0) break;
   }
+  int late = 0;  // iflag[1]
   if (in_fx) {
     // phi = (PHI - M) 2^-S, M the integers' mean (periodic / zero gradient)
     // rounded to an integer, from the last step's exact integer sums
@@ -1014,12 +1015,14 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       check(c, mg::launch_fx_to_f64(cur, out, N, S, mean, s), "fixed point -> phi");
       c->host_phi_written = c->host_phi != nullptr;
     }
-    int flag = 0;
-    check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s),
-          "read flag");
+    // both flags in one read: [0] overflow, [1] a tensor copy that was late
+    int flags[2] = {0, 0};
+    check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s),
+          "read flags");
     check(c, cudaStreamSynchronize(s), "sync");
-    std::memcpy(&flag, c->pinned + 60, sizeof(int));
-    if (flag) {
+    std::memcpy(flags, c->pinned + 60, 2 * sizeof(int));
+    late = flags[1];
+    if (flags[0]) {
       c->err = "fixed-point outer loop: |phi| passed 2^60 (the solve diverged)";
       st = MG_ERR_DIVERGED;
     }
@@ -1034,15 +1037,16 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   for (int l = 1; l < c->L; ++l)
     tma = tma || tma_level(c, l, hom, false) || tma_level(c, l, hom, true) ||
           tma_up_level(c, l, hom);
-  if (tma) {  // a down leg whose tensor copies did not land in time raised iflag[1]
-    int late = 0;
+  if (tma && !in_fx) {  // not read with the overflow flag above
     check(c, cudaMemcpyAsync(c->pinned + 61, c->iflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s),
           "read flag");
     check(c, cudaStreamSynchronize(s), "sync");
     std::memcpy(&late, c->pinned + 61, sizeof(int));
+  }
+  if (tma) {  // a leg whose tensor copies did not land in time raised iflag[1]
     if (late) {
       check(c, cudaMemsetAsync(c->iflag + 1, 0, sizeof(int), s), "clear flag");
-      c->err = "fused down leg: a tensor copy did not land in time";
+      c->err = "fused leg: a tensor copy did not land in time";
       st = MG_ERR_TIMEOUT;
     }
   }
