@@ -336,12 +336,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 // Wait for phase `parity` of the barrier; gives up after 2^22 tries (each
-// suspends the thread for at most a few microseconds), raising *err, so that a
-// copy that never lands cannot hang the GPU.
-__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
+// suspends the thread for at most a few microseconds), raising *err and
+// returning false, so that a copy that never lands cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
   for (int k = 0; k < (1 << 22); ++k)
-    if (mbar_try_wait(bar, parity)) return;
+    if (mbar_try_wait(bar, parity)) return true;
   if (err) *reinterpret_cast<volatile int*>(err) = 1;  // a flag: a plain store suffices
+  return false;
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
                                             unsigned long long* bar) {
@@ -500,7 +501,7 @@ struct Shape {
 // needs no wrap) take their planes of u and f by one tensor copy each, issued
 // by one thread, from the tensor maps tmu and tmf (boxes of 4 RS columns by
 // RR rows by one plane: a ring slot); the others by cp.async.  A copy that
-// does not land in time raises *err.
+// does not land in time raises *err, and the CTA stops its z-march.
 template <int MODE, bool ZERO, int PM, int TX, int TY, int HYO = 0, bool PAD = true,
           int NTB = 0, bool TMA = false, int PF = 0>
 __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, const float* f,
@@ -556,6 +557,8 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   // inside the level (the box's extra padding columns may leave it: they are
   // zero-filled and never read); mbarrier b counts the copies of plane b mod 4
   __shared__ unsigned long long tma_bar[TMA ? 4 : 1];
+  bool stop = false;  // a tensor copy did not land in time (the same in every thread)
+  int q_stop = 0;     // the plane whose copies were late
   const bool tma_tile = TMA && x0 - 4 >= 0 && x0 + TX + 4 <= p.nx && y0 - HY >= 0 &&
                         y0 + TY + HY <= p.ny;
   if (TMA && tma_tile) {
@@ -668,12 +671,18 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
     constexpr int ZP_BLK = (QP + 2) % 2;  // parity of plane q-2
     constexpr int ZP_DEF = (QP + 1) % 2;  // parity of plane q-3
     if (TMA && tma_tile) {
-      mbar_wait(&tma_bar[QP], (unsigned)(((q - q_first) >> 2) & 1), err);  // plane q's copies
+      // plane q's copies; a wait that ran out stops the whole CTA (uniformly)
+      const bool late = !mbar_wait(&tma_bar[QP], (unsigned)(((q - q_first) >> 2) & 1), err);
       if (MODE == kUp) cp_async_wait<1>();  // and this thread's copies of the coarse plane
+      if (__syncthreads_or(late)) {
+        stop = true;
+        q_stop = q;
+        return;
+      }
     } else {
       cp_async_wait<1>();  // this thread's copies of plane q have landed
+      __syncthreads();     // ... and everyone's; the previous step is finished
     }
-    __syncthreads();     // ... and everyone's; the previous step is finished
     issue(std::integral_constant<int, (QP + 2) % 4>{}, std::integral_constant<int, (QP + 1) % 4>{},
           q + 2);
     if (MODE == kUp && (QP & 1) && q + 2 <= q_last)  // q = 2K+1: plane K+2 into slot K mod 2
@@ -787,12 +796,19 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   cp_async_commit();
   for (int q = q_first; q <= q_last; q += 4) {
     step(std::integral_constant<int, 0>{}, q);
-    if (q + 1 > q_last) break;
+    if (stop || q + 1 > q_last) break;
     step(std::integral_constant<int, 1>{}, q + 1);
-    if (q + 2 > q_last) break;
+    if (stop || q + 2 > q_last) break;
     step(std::integral_constant<int, 2>{}, q + 2);
-    if (q + 3 > q_last) break;
+    if (stop || q + 3 > q_last) break;
     step(std::integral_constant<int, 3>{}, q + 3);
+    if (stop) break;
+  }
+  if (TMA && stop && threadIdx.x == 0) {
+    // give the copies still in flight (planes q_stop and q_stop + 1) a
+    // bounded time to land before the CTA's shared memory is released
+    for (int q = q_stop; q <= q_stop + 1 && q <= q_last; ++q)
+      mbar_wait(&tma_bar[q & 3], (unsigned)(((q - q_first) >> 2) & 1), nullptr);
   }
   cp_async_wait<0>();
 }
