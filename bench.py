@@ -29,7 +29,7 @@ TOL = 1e-10
 SEED = 20230227
 
 # Algorithmic bytes per finest cell of one launch of each kernel class, by
-# the width w of the level precision (see the design notes): the least data
+# the width w of the level precision: the least data
 # that launch must move.
 def algorithmic_bytes_per_cell(kernel: str, w: int, fixed_point: bool = True) -> float:
     return {
