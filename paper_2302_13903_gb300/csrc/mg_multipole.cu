@@ -206,40 +206,54 @@ __device__ double binom(int n, int k) {
   return r;
 }
 
-// One block: reduce partials per monomial in block order, then (thread 0)
-// centre of mass, shifted moments and Q_lm.
+// One block: reduce partials per monomial in block order, then the centre of
+// mass (thread 0), the moments about it (one monomial per thread) and Q_lm
+// (thread 0).
 __global__ void k_moments_finish(const double* __restrict__ partials, int nb, double h, int lmax,
                                  int use_com, double ox, double oy, double oz,
                                  double* __restrict__ out) {
   __shared__ double M[kMono];
+  __shared__ double Cs[kMono];
+  __shared__ double P[3][5];  // (-o)^p per axis, p = 0..4
   for (int m = threadIdx.x; m < kMono; m += blockDim.x) {
     double t = 0.0;
     for (int b = 0; b < nb; ++b) t += partials[(size_t)b * kMono + m];
     M[m] = t;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const double dv = h * h * h;
   // M[0] = sum rho, M[1..3] = sum rho x, y, z (indices of (1,0,0), (0,1,0), (0,0,1))
-  double o[3] = {ox, oy, oz};
-  if (use_com && M[0] != 0.0) {
-    o[0] = M[1] / M[0];
-    o[1] = M[2] / M[0];
-    o[2] = M[3] / M[0];
+  if (threadIdx.x == 0) {
+    double o[3] = {ox, oy, oz};
+    if (use_com && M[0] != 0.0) {
+      o[0] = M[1] / M[0];
+      o[1] = M[2] / M[0];
+      o[2] = M[3] / M[0];
+    }
+    for (int d = 0; d < 3; ++d) {
+      P[d][0] = 1.0;
+      for (int p = 1; p < 5; ++p) P[d][p] = P[d][p - 1] * -o[d];
+      out[25 + d] = o[d];
+    }
   }
-  double C[kMono];
-  for (int q = 0; q < kMono; ++q) {
+  __syncthreads();
+  // moments about o: C_q = sum over r <= q of the binomial shifts (one
+  // monomial per thread)
+  for (int q = threadIdx.x; q < kMono; q += blockDim.x) {
     const int a = c_mono[q][0], b = c_mono[q][1], c = c_mono[q][2];
     double acc = 0.0;
     for (int r = 0; r < kMono; ++r) {
       const int a2 = c_mono[r][0], b2 = c_mono[r][1], c2 = c_mono[r][2];
       if (a2 > a || b2 > b || c2 > c) continue;
-      const double w = binom(a, a2) * binom(b, b2) * binom(c, c2) * pow(-o[0], a - a2) *
-                       pow(-o[1], b - b2) * pow(-o[2], c - c2);
+      const double w = binom(a, a2) * binom(b, b2) * binom(c, c2) * P[0][a - a2] *
+                       P[1][b - b2] * P[2][c - c2];
       acc += w * M[r];
     }
-    C[q] = acc;
+    Cs[q] = acc;
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double dv = h * h * h;
+  const double* C = Cs;
   const double pi = 3.14159265358979323846;
   double Q[kTerms];
   for (int q = 0; q < kTerms; ++q) Q[q] = 0.0;
@@ -250,9 +264,6 @@ __global__ void k_moments_finish(const double* __restrict__ partials, int nb, do
       Q[q] = (l <= lmax) ? Q[q] * dv * sqrt(4.0 * pi / (2.0 * l + 1.0)) : 0.0;
     }
   for (int q = 0; q < kTerms; ++q) out[q] = Q[q];
-  out[25] = o[0];
-  out[26] = o[1];
-  out[27] = o[2];
   out[28] = M[0] * dv;
 }
 
