@@ -168,18 +168,46 @@ __global__ void k_raw_moments(const double* __restrict__ rho, Grid g, double h,
   int a0 = c_mono[m0][0], b0 = c_mono[m0][1], e0 = c_mono[m0][2];
   int a1 = 0, b1 = 0, e1 = 0;
   if (m1 < kMono) { a1 = c_mono[m1][0]; b1 = c_mono[m1][1]; e1 = c_mono[m1][2]; }
+  // rows of at most 256 cells: the powers of x of this lane's (at most 8)
+  // columns are the same in every row and are formed once, so a cell costs one
+  // add and four independent multiply-adds
+  const bool narrow = g.nx <= 256;
+  double xs[8][4];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double x = ((double)(lane + 32 * c) + 0.5 - 0.5 * g.nx) * h;
+    xs[c][0] = x;
+    xs[c][1] = x * x;
+    xs[c][2] = xs[c][1] * x;
+    xs[c][3] = xs[c][2] * x;
+  }
   for (long long row = gw; row < rows; row += nw) {
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
     const double* r = rho + (size_t)row * g.nx;
     double s[5] = {0, 0, 0, 0, 0};
-    for (int i = lane; i < g.nx; i += 32) {
-      const double x = ((double)i + 0.5 - 0.5 * g.nx) * h;
-      double t = r[i];
-      s[0] += t; t *= x;
-      s[1] += t; t *= x;
-      s[2] += t; t *= x;
-      s[3] += t; t *= x;
-      s[4] += t;
+    if (narrow) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int i = lane + 32 * c;
+        if (i < g.nx) {
+          const double t = r[i];
+          s[0] += t;
+          s[1] = fma(t, xs[c][0], s[1]);
+          s[2] = fma(t, xs[c][1], s[2]);
+          s[3] = fma(t, xs[c][2], s[3]);
+          s[4] = fma(t, xs[c][3], s[4]);
+        }
+      }
+    } else {
+      for (int i = lane; i < g.nx; i += 32) {
+        const double x = ((double)i + 0.5 - 0.5 * g.nx) * h;
+        double t = r[i];
+        s[0] += t; t *= x;
+        s[1] += t; t *= x;
+        s[2] += t; t *= x;
+        s[3] += t; t *= x;
+        s[4] += t;
+      }
     }
     for (int p = 0; p < 5; ++p)
       for (int o = 16; o > 0; o >>= 1) s[p] += __shfl_xor_sync(0xffffffffu, s[p], o);
@@ -267,13 +295,27 @@ __global__ void k_moments_finish(const double* __restrict__ partials, int nb, do
   out[28] = M[0] * dv;
 }
 
-// Potential of the expansion at every face point of a level.
+// Potential of the expansion at every face point of a level.  The block first
+// folds the moments into the coefficient of each monomial of the potential's
+// degree-l parts (P_l = sqrt(4 pi / (2l + 1)) sum_m Q_lm r^l Y_lm, homogeneous
+// of degree l), so that a point costs the 35 monomials at compile-time
+// indices and one reciprocal square root: phi = -G sum_l P_l / r^(2l+1).
 __global__ void k_open_faces(Grid g, double h, const double* __restrict__ qo, int lmax, double G,
                              double* __restrict__ faces) {
+  __shared__ double A[kMono];
+  const double pi = 3.14159265358979323846;
+  for (int q = threadIdx.x; q < kMono; q += blockDim.x) {
+    const int l = c_mono[q][0] + c_mono[q][1] + c_mono[q][2];
+    double a = 0.0;
+    for (int t = 0; t < c_nterm; ++t)
+      if (c_term_mono[t] == q) a += qo[c_term_lm[t]] * c_term_coef[t];
+    A[q] = l <= lmax ? a * sqrt(4.0 * pi / (2.0 * l + 1.0)) : 0.0;
+  }
+  __syncthreads();
   const long long fx = (long long)(g.ny + 2) * (g.nz + 2), fy = (long long)(g.nx + 2) * (g.nz + 2),
                   fz = (long long)(g.nx + 2) * (g.ny + 2);
   const long long total = 2 * (fx + fy + fz);
-  const double pi = 3.14159265358979323846;
+  const double ox = qo[25], oy = qo[26], oz = qo[27];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     long long q = t;
@@ -291,23 +333,30 @@ __global__ void k_open_faces(Grid g, double h, const double* __restrict__ qo, in
     } else {
       x = ((double)a - 0.5 - 0.5 * g.nx) * h; y = ((double)b - 0.5 - 0.5 * g.ny) * h; z = side * g.nz * h;
     }
-    x -= qo[25]; y -= qo[26]; z -= qo[27];
-    const double r2 = x * x + y * y + z * z, r = sqrt(r2);
+    x -= ox; y -= oy; z -= oz;
+    const double r2 = x * x + y * y + z * z;
     double xp[5], yp[5], zp[5];
     xp[0] = yp[0] = zp[0] = 1.0;
+#pragma unroll
     for (int p = 1; p < 5; ++p) { xp[p] = xp[p - 1] * x; yp[p] = yp[p - 1] * y; zp[p] = zp[p - 1] * z; }
-    double R[kTerms];
-    for (int s = 0; s < kTerms; ++s) R[s] = 0.0;
-    for (int s = 0; s < c_nterm; ++s) {
-      const int m = c_term_mono[s];
-      R[c_term_lm[s]] += c_term_coef[s] * xp[c_mono[m][0]] * yp[c_mono[m][1]] * zp[c_mono[m][2]];
-    }
-    double phi = 0.0, rl = r;  // r^(2l+1)
-    for (int l = 0; l <= lmax; ++l) {
-      double sl = 0.0;
-      for (int m = -l; m <= l; ++m) sl += qo[l * l + m + l] * R[l * l + m + l];
-      phi += sqrt(4.0 * pi / (2.0 * l + 1.0)) * sl / rl;
-      rl *= r2;
+    // the monomials in the order of c_mono: degree, then a, then b descending
+    double P[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int m = 0;
+#pragma unroll
+    for (int d = 0; d <= 4; ++d)
+#pragma unroll
+      for (int ea = d; ea >= 0; --ea)
+#pragma unroll
+        for (int eb = d - ea; eb >= 0; --eb) {
+          P[d] += A[m] * (xp[ea] * yp[eb] * zp[d - ea - eb]);
+          ++m;
+        }
+    const double ir = 1.0 / sqrt(r2), ir2 = ir * ir;
+    double phi = 0.0, w = ir;  // 1 / r^(2l+1)
+#pragma unroll
+    for (int l = 0; l <= 4; ++l) {
+      phi += P[l] * w;
+      w *= ir2;
     }
     faces[t] = -G * phi;
   }
