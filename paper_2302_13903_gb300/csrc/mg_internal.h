@@ -295,5 +295,10 @@ cudaError_t launch_moments_finish(const double* partials, int nb, double h, int 
 // in `qo` (layout of launch_moments_finish's output).
 cudaError_t launch_open_faces(Grid g, double h, const double* qo, int lmax, double G,
                               double* faces, cudaStream_t s);
+// A start value for phi under the open rule at every cell of level g: the
+// monopole and dipole of the expansion in qo (as launch_open_faces reads it),
+// -G (P_0 / r + P_1 / r^3) with r at least 1/8 of the shortest side.
+cudaError_t launch_open_guess(double* phi, Grid g, double h, const double* qo, double G,
+                              cudaStream_t s);
 
 }  // namespace mg

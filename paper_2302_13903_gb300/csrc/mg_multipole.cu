@@ -16,6 +16,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "mg_device.cuh"
 #include "mg_internal.h"
 
 namespace mg {
@@ -362,9 +363,57 @@ __global__ void k_open_faces(Grid g, double h, const double* __restrict__ qo, in
   }
 }
 
+// A start value for phi under the open rule: the expansion's monopole and
+// dipole, -G (P_0 / r + P_1 / r^3), at every cell, with r at least rmin (the
+// expansion is singular at its origin).  It matches the face potentials up to
+// the quadrupole and higher terms, so the first residual has no boundary
+// layer; its accuracy inside does not matter (the outer loop corrects it
+// exactly), and FP32 arithmetic suffices.
+__global__ void k_open_guess(double* __restrict__ phi, Grid g, double h,
+                             const double* __restrict__ qo, double G, float rmin) {
+  __shared__ float A[4];  // coefficients of 1, x, y, z (the first four monomials)
+  const double pi = 3.14159265358979323846;
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x, l = q == 0 ? 0 : 1;
+    double a = 0.0;
+    for (int t = 0; t < c_nterm; ++t)
+      if (c_term_mono[t] == q) a += qo[c_term_lm[t]] * c_term_coef[t];
+    A[q] = (float)(-G * a * sqrt(4.0 * pi / (2.0 * l + 1.0)));
+  }
+  __syncthreads();
+  const float ox = (float)qo[25], oy = (float)qo[26], oz = (float)qo[27], hf = (float)h;
+  const float cx = 0.5f * g.nx, cy = 0.5f * g.ny, cz = 0.5f * g.nz;
+  const long long total = g.cells();
+  const dev::Split sp(g.nx, g.ny);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    sp(t, i, j, k);
+    const float x = ((float)i + 0.5f - cx) * hf - ox, y = ((float)j + 0.5f - cy) * hf - oy,
+                z = ((float)k + 0.5f - cz) * hf - oz;
+    const float r = fmaxf(sqrtf(x * x + y * y + z * z), rmin), ir = 1.0f / r;
+    phi[t] = (double)((A[0] + (A[1] * x + A[2] * y + A[3] * z) * ir * ir) * ir);
+  }
+}
+
 }  // namespace
 
 cudaError_t prepare_multipole() { return upload_tables(); }
+
+cudaError_t launch_open_guess(double* phi, Grid g, double h, const double* qo, double G,
+                              cudaStream_t s) {
+  cudaError_t e = upload_tables();
+  if (e != cudaSuccess) return e;
+  ++g_launches;
+  long long nb = (g.cells() + kThreads - 1) / kThreads;
+  if (nb > sm_count() * 16LL) nb = sm_count() * 16LL;
+  // r at least 1/8 of the shortest side: inside that the start value is flat
+  // (a larger value there would only coarsen the fixed-point scale chosen from
+  // max |phi|)
+  const int nmin = g.nx < g.ny ? (g.nx < g.nz ? g.nx : g.nz) : (g.ny < g.nz ? g.ny : g.nz);
+  k_open_guess<<<(int)nb, kThreads, 0, s>>>(phi, g, h, qo, G, (float)(0.125 * nmin * h));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_raw_moments(const double* rho, Grid g, double h, double* partials, int* nb_out,
                                cudaStream_t s) {

@@ -841,6 +841,8 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   // the scale 2^S is known.  Few FP64 operations per cell: on this GPU they,
   // not the bytes, would bound these passes.
   const bool fast = fx && c->opts.mode_fmg && zero_values;
+  // open rule from an FMG start: begin from the expansion's monopole and dipole
+  const bool open_guess = c->bc_kind == MG_BC_OPEN && c->opts.mode_fmg != 0;
   if (c->host_rho && !fast)
     check(c, cudaMemcpyAsync(const_cast<double*>(rho), c->host_rho, sizeof(double) * N,
                              cudaMemcpyHostToDevice, s),
@@ -879,7 +881,14 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
     }
   } else {
     fnorm = prepare_source(c, rho, four_pi_G, f, false, s);
-    if (c->opts.mode_fmg) check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
+    if (open_guess) {
+      // the expansion's monopole and dipole as the start: the first residual
+      // then has no boundary layer from the face potentials
+      const double G = four_pi_G / (4.0 * 3.14159265358979323846);
+      check(c, mg::launch_open_guess(phi, g, c->h, c->scal + 2, G, s), "open start");
+    } else if (c->opts.mode_fmg) {
+      check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
+    }
     // r = f - L phi, scaled into FP32 so that its RMS is about 1.
     scale = fnorm > 0.0 ? 1.0 / fnorm : 1.0;
     if (c->opts.mode_fmg && zero_values) {
@@ -938,7 +947,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
         check(c, mg::launch_absmax<float>(c->u32[F], N, c->partials, c->scal + 50, s), "max |e|");
         if (mf < 0.0)
           check(c, mg::launch_absmax<double>(f, N, c->partials, c->scal + 51, s), "max |f|");
-        phi_zero = c->opts.mode_fmg != 0;
+        phi_zero = c->opts.mode_fmg != 0 && !open_guess;
         if (!phi_zero)
           check(c, mg::launch_absmax<double>(phi, N, c->partials, c->scal + 52, s), "max |phi|");
         else
