@@ -134,6 +134,9 @@ cudaError_t launch_sub(double* u, const double* ur, long long n, cudaStream_t s)
 // g = -grad phi at cell centres (Sec. 3.2.3), g = [gx | gy | gz] (3 N doubles).
 cudaError_t launch_gravity(const double* u, double* g, Grid gr, double h, Bc bc, cudaStream_t s);
 
+// u += v (n cells).
+cudaError_t launch_add_const(double* u, long long n, double v, cudaStream_t s);
+
 // Mixed precision outer step (FP64 in, FP32 out): r32 = scale * (f - L_h u),
 // partial sums of (f - L_h u)^2 in FP64.
 cudaError_t launch_outer_residual(const double* u, const double* f, float* r32, Grid g, double h,

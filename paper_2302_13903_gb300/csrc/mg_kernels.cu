@@ -122,6 +122,12 @@ __global__ void k_fill(T* __restrict__ u, long long n, T v) {
     u[t] = v;
 }
 
+__global__ void k_add_const(double* __restrict__ u, long long n, double v) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    u[t] += v;
+}
+
 __global__ void k_source(const double* __restrict__ rho, double* __restrict__ f, long long n,
                          double four_pi_G, double* __restrict__ partials) {
   double acc = 0.0;
@@ -398,6 +404,12 @@ cudaError_t launch_outer_residual(const double* u, const double* f, float* r32, 
   ++g_launches;
   k_outer_residual<<<reduce_blocks(g.cells()), kThreads, 0, s>>>(u, f, r32, g, bc, 1.0 / (h * h),
                                                                  scale, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_const(double* u, long long n, double v, cudaStream_t s) {
+  ++g_launches;
+  k_add_const<<<grid_for(n), kThreads, 0, s>>>(u, n, v);
   return cudaGetLastError();
 }
 

@@ -821,7 +821,14 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   const long long N = g.cells();
   const int nb = mg::reduce_blocks(N);
   double* f = c->f64[F];
-  const Bc bc = physical_bc(c, F);
+  Bc bc = physical_bc(c, F);
+  // one fixed value b on every face, from an FMG start: solve for phi - b,
+  // whose faces are zero-fixed (L_h of a constant is zero with the ghosts
+  // 2b - phi, cell by cell), and add b at the end -- the zero-value path, and
+  // no bits of the fixed-point scale spent on the offset
+  const double b_shift =
+      (bc.kind == mg::BC_FIXED && bc.value != 0.0 && c->opts.mode_fmg != 0) ? bc.value : 0.0;
+  if (b_shift != 0.0) bc.value = 0.0;
   const Bc hom = mg::homogeneous(bc);
   const Bc coarse = correction_bc(c, bc);
   const bool fx = c->opts.outer_fixed != 0 && c->fxbuf != nullptr;
@@ -843,6 +850,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
   const bool fast = fx && c->opts.mode_fmg && zero_values;
   // open rule from an FMG start: begin from the expansion's monopole and dipole
   const bool open_guess = c->bc_kind == MG_BC_OPEN && c->opts.mode_fmg != 0;
+
   if (c->host_rho && !fast)
     check(c, cudaMemcpyAsync(const_cast<double*>(rho), c->host_rho, sizeof(double) * N,
                              cudaMemcpyHostToDevice, s),
@@ -1023,7 +1031,9 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       double* out = c->host_phi ? c->host_phi : phi;
       check(c, mg::launch_fx_to_f64(cur, out, N, S, mean, s), "fixed point -> phi");
       c->host_phi_written = c->host_phi != nullptr;
+      if (b_shift != 0.0) check(c, mg::launch_add_const(out, N, b_shift, s), "phi + b");
     }
+    if (gacc && b_shift != 0.0) check(c, mg::launch_add_const(phi, N, b_shift, s), "phi + b");
     // both flags in one read: [0] overflow, [1] a tensor copy that was late
     int flags[2] = {0, 0};
     check(c, cudaMemcpyAsync(c->pinned + 60, c->iflag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s),
@@ -1041,6 +1051,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       KTimer t(c, MG_K_GRAVITY, true, s);
       check(c, mg::launch_gravity(phi, gacc, g, c->h, bc, s), "gravity");
     }
+    if (b_shift != 0.0) check(c, mg::launch_add_const(phi, N, b_shift, s), "phi + b");
   }
   bool tma = false;
   for (int l = 1; l < c->L; ++l)

@@ -112,6 +112,29 @@ def test_mixed_matches_converged_oracle(bc, n, outer_fixed):
     assert emax(phi, ref.phi) <= 1e-9
 
 
+@pytest.mark.parametrize("b", [-3.0, 10.0])
+@pytest.mark.parametrize("gravity", [False, True])
+def test_mixed_fixed_value_offset(b, gravity):
+    """A fixed value b on every face (Sec. 2.3.6): the mixed path solves for
+    phi - b, whose faces are zero-fixed, and adds b back.  Against the oracle's
+    converged solution with the same b, also where b dwarfs the potential the
+    source makes (10) -- the offset takes no bits of the fixed-point scale --
+    and through the solve that also writes g = -grad phi."""
+    n = 64
+    rho, fpg = source(n, mg.FIXED, seed=13)
+    ref = orc.solve(rho, 1.0 / n, mg.FIXED, bc_value=b, four_pi_G=fpg, tol=0.0, max_cycles=80)
+    with mg.Solver(n, 1.0 / n, mg.FIXED, prec=mg.MIXED, fixed_value=b) as s:
+        rd = torch.from_numpy(rho).cuda()
+        if gravity:
+            phi, g, hist, st = s.solve_gravity(rd, fpg, 1e-10)
+            g0 = s.solve_gravity(rd, fpg, 1e-10)[1]  # the same again: deterministic
+            assert torch.equal(g, g0)
+        else:
+            phi, hist, st = s.solve(rd, fpg, 1e-10)
+    assert st == 0 and hist[-1] < 1e-10, (st, hist)
+    assert emax(phi.cpu().numpy(), ref.phi) <= 1e-9
+
+
 @pytest.mark.parametrize("inner_fmg,inner_cycles", [(1, 1), (1, 3), (0, 1), (0, 5)])
 @pytest.mark.parametrize("bc", [mg.PERIODIC, mg.ZEROGRAD])
 def test_mixed_inner_schedules(inner_fmg, inner_cycles, bc):
