@@ -519,7 +519,7 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64-path solves (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--e2e-inflight", type=int, default=3,
                     help="requests in flight in the served end-to-end measurement")
     ap.add_argument("--cpu-n", type=int, default=256, help="oracle sample size")
