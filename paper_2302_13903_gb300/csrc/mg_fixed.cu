@@ -282,9 +282,12 @@ __global__ void k_rho_stats(const double2* __restrict__ rho, long long n2,
 // fixed-point step recomputes); per-block partial sums of r32^2 (FP32 per
 // thread) and maxima of |r32|.  No FP64 arithmetic: rho reaches FP32 by the
 // integer conversion.
+// From the device: a and b (as doubles holding FP32 values) in ab[0], ab[1]
+// when ab is given, else the arguments.
 __global__ void k_rho_to_r32(const double2* __restrict__ rho, float2* __restrict__ r32,
-                             long long n2, float a, float b, double* __restrict__ sum,
-                             double* __restrict__ mx) {
+                             long long n2, float a_arg, float b_arg, const double* __restrict__ ab,
+                             double* __restrict__ sum, double* __restrict__ mx) {
+  const float a = ab ? (float)ab[0] : a_arg, b = ab ? (float)ab[1] : b_arg;
   float acc = 0.f, m = 0.f;
 #pragma unroll 4
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
@@ -778,14 +781,38 @@ cudaError_t launch_rho_stats_copy(const double* host_rho, double* dev, long long
   return cudaGetLastError();
 }
 
+// The source's scale on the device, from the sums of launch_rho_stats in
+// st[0] (sum rho) and st[1] (max |rho|): out[0] = mu (the mean of f, or 0),
+// out[1] = scale = 1 / (|4 pi G| max|rho| + |mu|), out[2], out[3] = the FP32
+// a = 4 pi G scale and b = mu scale of launch_rho_to_r32 -- each one IEEE
+// operation in the order the host would take them.
+__global__ void k_source_scale(const double* __restrict__ st, long long n, double four_pi_G,
+                               int has_mean, double* __restrict__ out) {
+  const double mu = has_mean ? __dmul_rn(four_pi_G, __ddiv_rn(st[0], (double)n)) : 0.0;
+  const double bound = __dadd_rn(__dmul_rn(fabs(four_pi_G), st[1]), fabs(mu));
+  const double scale = bound > 0.0 ? __ddiv_rn(1.0, bound) : 1.0;
+  out[0] = mu;
+  out[1] = scale;
+  out[2] = (double)__double2float_rn(__dmul_rn(four_pi_G, scale));
+  out[3] = (double)__double2float_rn(__dmul_rn(mu, scale));
+}
+
+cudaError_t launch_source_scale(const double* st, long long n, double four_pi_G, bool has_mean,
+                                double* out, cudaStream_t s) {
+  ++g_launches;
+  k_source_scale<<<1, 1, 0, s>>>(st, n, four_pi_G, has_mean ? 1 : 0, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rho_to_r32(const double* rho, float* r32, long long n, double a, double b,
-                              double* partials, double* out, cudaStream_t s) {
+                              double* partials, double* out, cudaStream_t s,
+                              const double* ab_dev) {
   if (n % 2) return cudaErrorInvalidValue;
   const int nb = reduce_blocks(n / 2);
   ++g_launches;
   k_rho_to_r32<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(rho),
                                        reinterpret_cast<float2*>(r32), n / 2, (float)a, (float)b,
-                                       partials, partials + nb);
+                                       ab_dev, partials, partials + nb);
   ++g_launches;
   k_finish_sum_max<<<1, kThreads, 0, s>>>(partials, partials + nb, nb, out);
   return cudaGetLastError();

@@ -239,9 +239,16 @@ cudaError_t launch_rho_stats_copy(const double* host_rho, double* dev, long long
                                   double* partials, double* out, cudaStream_t s);
 cudaError_t launch_rho_stats(const double* rho, long long n, double* partials, double* out,
                              cudaStream_t s);
-// r32 = fl32(a rho - b); out[0] = sum r32^2, out[1] = max |r32|.
+// out[0..3] = mu, scale, a, b of the source from the launch_rho_stats sums in
+// st (on the device, so that no host round trip sits between the passes).
+cudaError_t launch_source_scale(const double* st, long long n, double four_pi_G, bool has_mean,
+                                double* out, cudaStream_t s);
+// r32 = fl32(a rho - b); out[0] = sum r32^2, out[1] = max |r32|.  ab_dev: a
+// and b from the device (launch_source_scale's out + 2) instead of the
+// arguments.
 cudaError_t launch_rho_to_r32(const double* rho, float* r32, long long n, double a, double b,
-                              double* partials, double* out, cudaStream_t s);
+                              double* partials, double* out, cudaStream_t s,
+                              const double* ab_dev = nullptr);
 // q = round(a rho - b) as int64.
 cudaError_t launch_rho_to_fx(const double* rho, long long* q, long long n, double a, double b,
                              cudaStream_t s);

@@ -868,25 +868,15 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       else
         check(c, mg::launch_rho_stats(rho, N, c->partials, c->scal + 0, s), "source stats");
     }
-    check(c, cudaMemcpyAsync(c->pinned, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
-          "read source stats");
-    check(c, cudaStreamSynchronize(s), "sync");
-    mu = has_mean ? four_pi_G * (c->pinned[0] / (double)N) : 0.0;
-    const double bound = std::fabs(four_pi_G) * c->pinned[1] + std::fabs(mu);  // >= max|f - mean|
-    scale = bound > 0.0 ? 1.0 / bound : 1.0;
-    check(c, mg::launch_rho_to_r32(rho, c->f32[F], N, four_pi_G * scale, mu * scale, c->partials,
-                                   c->scal + 0, s),
+    // mu and the scale (1 / bound on |f - mean|) on the device: the host
+    // learns them, with the first residual's norm and maximum, in the first
+    // outer iteration's read (no round trip before the first inner solve)
+    check(c, mg::launch_source_scale(c->scal + 0, N, four_pi_G, has_mean, c->scal + 32, s),
+          "source scale");
+    check(c, mg::launch_rho_to_r32(rho, c->f32[F], N, 0.0, 0.0, c->partials, c->scal + 0, s,
+                                   c->scal + 34),
           "r = f - mean");
-    check(c, cudaMemcpyAsync(c->pinned, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
-          "read norm");
-    check(c, cudaStreamSynchronize(s), "sync");
-    fnorm = std::sqrt(c->pinned[0] / (double)N) / scale;
-    mf = c->pinned[1] / scale;
-    rn = fnorm;
-    if (fnorm == 0.0) {
-      fnorm = 1.0;
-      check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
-    }
+    fnorm = scale = rn = -1.0;  // known after the first inner solve
   } else {
     fnorm = prepare_source(c, rho, four_pi_G, f, false, s);
     if (open_guess) {
@@ -936,6 +926,27 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       break;
     }
     inner_solve(c, hom, coarse, s);
+    if (fast && it == 0) {
+      // one read for the source's scalars, the first residual's norm and
+      // maximum, and max |e| after the first inner solve
+      check(c, mg::launch_absmax<float>(c->u32[F], N, c->partials, c->scal + 50, s), "max |e|");
+      check(c, cudaMemsetAsync(c->scal + 52, 0, sizeof(double), s), "zero");
+      check(c, cudaMemcpyAsync(c->pinned, c->scal, 64 * sizeof(double), cudaMemcpyDeviceToHost,
+                               s),
+            "read scalars");
+      check(c, cudaStreamSynchronize(s), "sync");
+      mu = c->pinned[32];
+      scale = c->pinned[33];
+      fnorm = std::sqrt(c->pinned[0] / (double)N) / scale;
+      mf = c->pinned[1] / scale;
+      rn = fnorm;
+      if (fnorm == 0.0) {  // zero source: phi = 0 (the inner solve ran on zeros)
+        check(c, mg::launch_fill<double>(phi, N, 0.0, s), "zero phi");
+        hist[n++] = 0.0;
+        st = MG_OK;
+        break;
+      }
+    }
     const double old_scale = scale;
     scale = 1.0 / rn;  // the next residual is scaled by the current one's size
     if (!fx) {
@@ -952,19 +963,23 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       if (it == 0) {
         // S such that |phi| < 2^55 and |h^2 f| < 2^58 on the integer grid;
         // phi after this step is at most max|phi_0| + max|e| / scale.
-        check(c, mg::launch_absmax<float>(c->u32[F], N, c->partials, c->scal + 50, s), "max |e|");
-        if (mf < 0.0)
-          check(c, mg::launch_absmax<double>(f, N, c->partials, c->scal + 51, s), "max |f|");
         phi_zero = c->opts.mode_fmg != 0 && !open_guess;
-        if (!phi_zero)
-          check(c, mg::launch_absmax<double>(phi, N, c->partials, c->scal + 52, s), "max |phi|");
-        else
-          check(c, cudaMemsetAsync(c->scal + 52, 0, sizeof(double), s), "zero");
-        check(c, cudaMemcpyAsync(c->pinned + 50, c->scal + 50, 3 * sizeof(double),
-                                 cudaMemcpyDeviceToHost, s),
-              "read max");
+        if (!fast) {  // (the fast path read these with its scalars)
+          check(c, mg::launch_absmax<float>(c->u32[F], N, c->partials, c->scal + 50, s),
+                "max |e|");
+          if (mf < 0.0)
+            check(c, mg::launch_absmax<double>(f, N, c->partials, c->scal + 51, s), "max |f|");
+          if (!phi_zero)
+            check(c, mg::launch_absmax<double>(phi, N, c->partials, c->scal + 52, s),
+                  "max |phi|");
+          else
+            check(c, cudaMemsetAsync(c->scal + 52, 0, sizeof(double), s), "zero");
+          check(c, cudaMemcpyAsync(c->pinned + 50, c->scal + 50, 3 * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s),
+                "read max");
+          check(c, cudaStreamSynchronize(s), "sync");
+        }
         check(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), s), "clear flag");
-        check(c, cudaStreamSynchronize(s), "sync");
         const double mphi = c->pinned[52] + c->pinned[50] / old_scale;
         const double mfh = (mf >= 0.0 ? mf : c->pinned[51]) * c->h * c->h;
         double lim = 0.0;
