@@ -261,6 +261,41 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
     ar = fmaf(xs, xs, ar);
     return xs;
   };
+  if (TYPE == PH_TOFX || TYPE == PH_PSUB) {
+    // pure streams: four 16-byte loads in flight per thread before their
+    // stores (each element is read before it is written, so PHI may be phi)
+    const double a = fpg * c2, b = mean * c2;
+    auto tofx = [&](double2 v) {
+      return make_longlong2(cvt::d2ll_rn(fma(a, v.x, -b)), cvt::d2ll_rn(fma(a, v.y, -b)));
+    };
+    auto psub = [&](longlong2 v) {
+      return fx ? make_double2(cvt::ll2d_pow2_rn(v.x - g.imean, g.S),
+                               cvt::ll2d_pow2_rn(v.y - g.imean, g.S))
+                : make_double2(0.0, 0.0);
+    };
+    const int stride = blockDim.x, e2 = hi >> 1;
+    int t2 = (lo >> 1) + threadIdx.x;
+    for (; t2 + 3 * stride < e2; t2 += 4 * stride) {
+      if (TYPE == PH_TOFX) {
+        double2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = rho2[t2 + q * stride];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) reinterpret_cast<longlong2*>(FX)[t2 + q * stride] = tofx(v[q]);
+      } else {
+        longlong2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const longlong2*>(PHI)[t2 + q * stride];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(phi)[t2 + q * stride] = psub(v[q]);
+      }
+    }
+    for (; t2 < e2; t2 += stride) {
+      if (TYPE == PH_TOFX) reinterpret_cast<longlong2*>(FX)[t2] = tofx(rho2[t2]);
+      else reinterpret_cast<double2*>(phi)[t2] = psub(reinterpret_cast<const longlong2*>(PHI)[t2]);
+    }
+    return;
+  }
 #pragma unroll 8
   for (int t2 = (lo >> 1) + threadIdx.x; t2 < (hi >> 1); t2 += blockDim.x) {
     const int t = 2 * t2;  // cells t, t + 1 (lo, hi and N are even)
