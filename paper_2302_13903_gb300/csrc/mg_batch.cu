@@ -296,9 +296,33 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
     }
     return;
   }
-#pragma unroll 8
-  for (int t2 = (lo >> 1) + threadIdx.x; t2 < (hi >> 1); t2 += blockDim.x) {
+  // the first residual: each thread's cells in the same order as one at a
+  // time, with four 16-byte loads in flight ahead of their use
+  const int stride = blockDim.x, e2 = hi >> 1;
+  auto r0_pair = [&](int t2, double2 v) {
     const int t = 2 * t2;  // cells t, t + 1 (lo, hi and N are even)
+    const float x0 = r0_cell(t, v.x), x1 = r0_cell(t + 1, v.y);
+    reinterpret_cast<float2*>(r32)[t2] = make_float2(x0, x1);
+    if (++nf == 4) {  // FP32 sums over at most 8 cells, then added in FP64
+      acc += af;
+      acc2 += ar;
+      af = ar = 0.f;
+      nf = 0;
+    }
+  };
+  if (TYPE == PH_R0) {
+    int t2 = (lo >> 1) + threadIdx.x;
+    for (; t2 + 3 * stride < e2; t2 += 4 * stride) {
+      double2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = rho2[t2 + q * stride];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r0_pair(t2 + q * stride, v[q]);
+    }
+    for (; t2 < e2; t2 += stride) r0_pair(t2, rho2[t2]);
+  }
+#pragma unroll 8
+  for (int t2 = (lo >> 1) + threadIdx.x; TYPE != PH_R0 && t2 < e2; t2 += stride) {
     if (TYPE == PH_SRC) {
       const double2 v = rho2[t2];
       acc += v.x + v.y;
@@ -306,37 +330,13 @@ __device__ void chunk_item(const Ctl& c, GridDev& g, int chunk) {
       const unsigned long long b1 = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffULL;
       mb = b0 > mb ? b0 : mb;
       mb = b1 > mb ? b1 : mb;
-    } else if (TYPE == PH_R0) {
-      const double2 v = rho2[t2];
-      const float x0 = r0_cell(t, v.x), x1 = r0_cell(t + 1, v.y);
-      reinterpret_cast<float2*>(r32)[t2] = make_float2(x0, x1);
-      if (++nf == 4) {  // FP32 sums over at most 8 cells, then added in FP64
-        acc += af;
-        acc2 += ar;
-        af = ar = 0.f;
-        nf = 0;
-      }
     } else if (TYPE == PH_EMAX) {
       const float2 v = reinterpret_cast<const float2*>(e32)[t2];
       mx = fmax(mx, (double)fmaxf(fabsf(v.x), fabsf(v.y)));
-    } else if (TYPE == PH_TOFX) {
-      const double2 v = rho2[t2];
-      const double a = fpg * c2, b = mean * c2;
-      reinterpret_cast<longlong2*>(FX)[t2] =
-          make_longlong2(cvt::d2ll_rn(fma(a, v.x, -b)), cvt::d2ll_rn(fma(a, v.y, -b)));
     } else if (TYPE == PH_PSUM) {
       const longlong2 v = reinterpret_cast<const longlong2*>(PHI)[t2];
       s_hi += (v.x >> 32) + (v.y >> 32);
       s_lo += (v.x & 0xffffffffLL) + (v.y & 0xffffffffLL);
-    } else if (TYPE == PH_PSUB) {
-      // a grid that never reached the fixed-point loop has phi = 0 exactly
-      double2 out = make_double2(0.0, 0.0);
-      if (fx) {  // (PHI - M) 2^-S, M the rounded integer mean: integer arithmetic only
-        const longlong2 v = reinterpret_cast<const longlong2*>(PHI)[t2];
-        out = make_double2(cvt::ll2d_pow2_rn(v.x - g.imean, g.S),
-                           cvt::ll2d_pow2_rn(v.y - g.imean, g.S));
-      }
-      reinterpret_cast<double2*>(phi)[t2] = out;
     }
   }
   if (TYPE == PH_R0) {
