@@ -117,7 +117,13 @@ typedef struct {
                       /*    bits either way.  0 (default): per-thread copies, unless */
                       /*    mg_ctx_autotune timed the tensor copies faster for that  */
                       /*    leg and level; 1: always (where they apply); 2: never    */
-  int reserved[2];    /* must be zero                                               */
+  int first_cycles;   /* MIXED: V-cycles (counting the FMG start when inner_fmg = 1) */
+                      /*    of the first outer iteration's inner solve, 1..65; 0    */
+                      /*    (default): 1 + inner_cycles like the others.  The first  */
+                      /*    inner solve corrects the whole source: its residual      */
+                      /*    levels off where FP32 rounding of the correction sets    */
+                      /*    the floor, and cycles past that point change little     */
+  int reserved[1];    /* must be zero                                               */
 } mg_opts;
 
 typedef struct mg_ctx mg_ctx;
@@ -417,7 +423,8 @@ typedef struct mg_batch mg_batch;
  * fixed point, as in mg_solve -- around FP32 V(1,1) cycles): opts->prec must
  * be MG_MIXED, pre = post = 1, mode_fmg = 1 (phi starts at 0), inner_fmg = 0;
  * max_cycles (outer iterations, <= 64) and inner_cycles (V-cycles per outer
- * iteration after the one from a zero correction, 0..16) are shared.  All
+ * iteration after the one from a zero correction, 0..16; first_cycles, 0..17,
+ * for the first outer iteration) are shared.  All
  * level storage is allocated here.  Errors: MG_ERR_ARG, MG_ERR_OOM. */
 mg_status mg_batch_create(int n, const int *dims, const double *dx, const mg_bc *bcs,
                           const double *fixed_values, const mg_opts *opts, mg_batch **batch);

@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
         ("inner_fmg", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("outer_fixed", ctypes.c_int), ("fas", ctypes.c_int), ("coarse_literal", ctypes.c_int),
         ("leg_pairs", ctypes.c_int), ("batch_small", ctypes.c_int),
-        ("tensor_copies", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+        ("tensor_copies", ctypes.c_int), ("first_cycles", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 

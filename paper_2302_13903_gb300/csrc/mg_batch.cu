@@ -921,9 +921,11 @@ void build_phases(mg_batch* b, std::vector<Phase>& phases, std::vector<Item>& it
   add_grid_phase(PH_MEANFIN, 0);
   add_chunk_phase(PH_R0);
   add_grid_phase(PH_R0FIN, 0);
-  // one V-cycle from a zero correction, then inner_cycles more (as mg_solve)
-  const int inner = 1 + b->opts.inner_cycles;
+  // one V-cycle from a zero correction, then inner_cycles more (as mg_solve;
+  // first_cycles in all in the first outer iteration when given)
   for (int o = 0; o < b->opts.max_cycles; ++o) {
+    const int inner =
+        (o == 0 && b->opts.first_cycles > 0) ? b->opts.first_cycles : 1 + b->opts.inner_cycles;
     for (int k = 0; k < inner; ++k) {
       for (int n = nmax; n >= kFusedMinN; n >>= 1) add_tile_phase(PH_DOWN, n, k);
       add_grid_phase(PH_BOTTOM, k);
@@ -1006,10 +1008,10 @@ mg_status mg_batch_create(int n, const int* dims, const double* dx, const mg_bc*
   else mg_opts_init(&o);
   if (o.prec != MG_MIXED || o.pre != 1 || o.post != 1 || !o.mode_fmg || o.inner_fmg ||
       o.max_cycles < 1 || o.max_cycles > 64 || o.inner_cycles < 0 || o.inner_cycles > 16 ||
-      o.coarse_literal) {
+      o.first_cycles < 0 || o.first_cycles > 17 || o.coarse_literal) {
     g_batch_err = "mg_batch_create: the batched solve runs MG_MIXED, V(1,1), FMG mode, inner "
-                  "V-cycles from a zero correction (inner_fmg = 0), 1..64 outer iterations, "
-                  "homogeneous coarse rules (coarse_literal = 0)";
+                  "V-cycles from a zero correction (inner_fmg = 0), 1..64 outer iterations "
+                  "of at most 17 V-cycles, homogeneous coarse rules (coarse_literal = 0)";
     return MG_ERR_ARG;
   }
   for (int g = 0; g < n; ++g) {

@@ -130,7 +130,8 @@ namespace {
 // conditions).
 bool batch_opts_ok(const mg_opts& o) {
   return o.batch_small == 1 && o.prec == MG_MIXED && o.pre == 1 && o.post == 1 && o.mode_fmg == 1 &&
-         o.inner_fmg == 0 && o.max_cycles <= 64 && o.inner_cycles <= 16 && o.coarse_literal == 0;
+         o.inner_fmg == 0 && o.max_cycles <= 64 && o.inner_cycles <= 16 && o.first_cycles <= 17 &&
+         o.coarse_literal == 0;
 }
 
 // Create the hierarchy of a CREATE decision for request r.

@@ -87,9 +87,13 @@ struct mg_ctx {
   // The mixed path's inner FP32 solve (the same launches on the same buffers
   // every outer iteration) as a CUDA graph, captured on its second run and
   // replayed from then on; dropped when the launch shapes change.
-  cudaGraphExec_t inner_exec = nullptr;
-  long long inner_launches = 0;  // kernels in the graph
-  int inner_runs = 0;
+  // Two graphs: [0] for 1 + inner_cycles V-cycles, [1] for the first outer
+  // iteration's first_cycles when they differ.
+  struct InnerGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;  // kernels in the graph
+    int runs = 0;
+  } inner[2];
   // the autotuner timed the finest level's fused up-down pass faster than the
   // two legs it replaces (opts.leg_pairs = 0 then fuses them)
   bool pairs_faster = false;
@@ -752,66 +756,77 @@ mg_status solve_fp64(mg_ctx* c, const double* rho, double four_pi_G, double tol,
 // FP32 multigrid solve of L e = r into u32[L-1], with r already in f32[L-1]:
 // rule `hom` (the homogeneous rule of the finest level) for e itself and in
 // FMG, `coarse` for the corrections of e on the levels below.
-void inner_solve_launches(mg_ctx* c, const Bc& hom, const Bc& coarse, cudaStream_t s) {
+void inner_solve_launches(mg_ctx* c, const Bc& hom, const Bc& coarse, int cycles,
+                          cudaStream_t s) {
   const int F = c->L - 1;
   Pyr<float> P = pyr<float>(c);
   Bc bcs[kMaxLevels];
   for (int l = 0; l < c->L; ++l) bcs[l] = hom;
   if (c->opts.inner_fmg) {
     fmg<float>(c, P, bcs, coarse, s);
-  } else if (use_pairs(c) && pairs_ok(c, F, hom, coarse, 1 + c->opts.inner_cycles)) {
-    vcycles_paired(c, F, hom, coarse, 1 + c->opts.inner_cycles, s);
+  } else if (use_pairs(c) && pairs_ok(c, F, hom, coarse, cycles)) {
+    vcycles_paired(c, F, hom, coarse, cycles, s);
     return;
   } else {
     vcycle<float>(c, P, F, hom, coarse, true, s);
   }
-  for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, P, F, hom, coarse, false, s);
+  for (int q = 1; q < cycles; ++q) vcycle<float>(c, P, F, hom, coarse, false, s);
 }
 
 void drop_inner_graph(mg_ctx* c) {
-  if (c->inner_exec) cudaGraphExecDestroy(c->inner_exec);
-  c->inner_exec = nullptr;
-  c->inner_runs = 0;
+  for (auto& ig : c->inner) {
+    if (ig.exec) cudaGraphExecDestroy(ig.exec);
+    ig.exec = nullptr;
+    ig.runs = 0;
+  }
 }
 
-// The inner solve, from its second run on as one CUDA graph launch (not while
-// per-kernel timing is on, on the legacy default stream, or inside a capture
-// the caller started).  The launches are the same every outer iteration: the
-// same kernels, shapes and buffers.
-void inner_solve(mg_ctx* c, const Bc& hom, const Bc& coarse, cudaStream_t s) {
-  if (c->inner_exec && !c->timing) {
-    check(c, cudaGraphLaunch(c->inner_exec, s), "inner solve graph");
-    mg::g_launches += c->inner_launches;
+// V-cycles (or FMG and the V-cycles after it) of the inner solve of outer
+// iteration `it`.
+int inner_count(const mg_ctx* c, int it) {
+  return (it == 0 && c->opts.first_cycles > 0) ? c->opts.first_cycles : 1 + c->opts.inner_cycles;
+}
+
+// The inner solve of `cycles` V-cycles, from its second run with that count
+// on as one CUDA graph launch (not while per-kernel timing is on, on the
+// legacy default stream, or inside a capture the caller started).  The
+// launches are the same every outer iteration: the same kernels, shapes and
+// buffers.
+void inner_solve(mg_ctx* c, const Bc& hom, const Bc& coarse, int cycles, cudaStream_t s) {
+  mg_ctx::InnerGraph& ig = c->inner[cycles == 1 + c->opts.inner_cycles ? 0 : 1];
+  if (ig.exec && !c->timing) {
+    check(c, cudaGraphLaunch(ig.exec, s), "inner solve graph");
+    mg::g_launches += ig.launches;
     return;
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  const bool capture = !c->timing && c->inner_runs >= 1 && s != nullptr &&
+  const bool capture = !c->timing && ig.runs >= 1 && s != nullptr &&
                        cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
                        cs == cudaStreamCaptureStatusNone;
-  ++c->inner_runs;
+  ++ig.runs;
   if (!capture) {
-    inner_solve_launches(c, hom, coarse, s);
+    inner_solve_launches(c, hom, coarse, cycles, s);
     return;
   }
   check(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   const long long before = mg::g_launches;
   cudaGraph_t graph = nullptr;
   try {
-    inner_solve_launches(c, hom, coarse, s);
+    inner_solve_launches(c, hom, coarse, cycles, s);
   } catch (const Fail&) {
     cudaStreamEndCapture(s, &graph);
     if (graph) cudaGraphDestroy(graph);
     throw;
   }
   check(c, cudaStreamEndCapture(s, &graph), "end capture");
-  const cudaError_t e = cudaGraphInstantiate(&c->inner_exec, graph, 0);
+  const cudaError_t e = cudaGraphInstantiate(&ig.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    c->inner_exec = nullptr;
+    ig.exec = nullptr;
     check(c, e, "instantiate inner solve graph");
   }
-  c->inner_launches = mg::g_launches - before;
-  check(c, cudaGraphLaunch(c->inner_exec, s), "inner solve graph");
+  ig.launches = mg::g_launches - before;
+  check(c, cudaGraphLaunch(ig.exec, s), "inner solve graph");
 }
 
 mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol, double* phi,
@@ -925,7 +940,7 @@ mg_status solve_mixed(mg_ctx* c, const double* rho, double four_pi_G, double tol
       st = MG_OK;
       break;
     }
-    inner_solve(c, hom, coarse, s);
+    inner_solve(c, hom, coarse, inner_count(c, it), s);
     if (fast && it == 0) {
       // one read for the source's scalars, the first residual's norm and
       // maximum, and max |e| after the first inner solve
@@ -1095,6 +1110,7 @@ mg_status validate_opts(const mg_opts& o) {
   if (!(o.omega > 0.0 && o.omega < 2.0)) return MG_ERR_ARG;
   if (o.max_cycles < 0 || o.lmax < 0 || o.lmax > 4) return MG_ERR_ARG;
   if (o.inner_cycles < 0 || o.inner_cycles > 64) return MG_ERR_ARG;
+  if (o.first_cycles < 0 || o.first_cycles > 65) return MG_ERR_ARG;
   if (o.outer_fixed != 0 && o.outer_fixed != 1) return MG_ERR_ARG;
   if (o.fas != 0 && (o.fas != 1 || o.prec != MG_FP64)) return MG_ERR_ARG;
   if (o.coarse_literal != 0 && o.coarse_literal != 1) return MG_ERR_ARG;

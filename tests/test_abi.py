@@ -46,7 +46,8 @@ def test_default_options_layout():
     assert o.stall_ratio == 0.9 and o.inner_fmg == 0 and o.inner_cycles == 3
     assert o.outer_fixed == 1 and o.fas == 0
     assert o.coarse_literal == 0
-    assert list(o.reserved) == [0] * 2 and o.batch_small == 0 and o.tensor_copies == 0
+    assert list(o.reserved) == [0] and o.batch_small == 0 and o.tensor_copies == 0
+    assert o.first_cycles == 0
     assert o.leg_pairs == 0
 
 

@@ -149,6 +149,52 @@ def test_mixed_inner_schedules(inner_fmg, inner_cycles, bc):
     assert emax(phi, ref.phi) <= 1e-9
 
 
+@pytest.mark.parametrize("bc", [mg.PERIODIC, mg.ZEROGRAD, mg.OPEN])
+def test_first_outer_iteration_cycles(bc):
+    """first_cycles changes only the first outer iteration's inner solve: one
+    V-cycle there leaves a larger first residual, the later iterations keep
+    1 + inner_cycles, and the solve still reaches the oracle's converged
+    solution; first_cycles = 1 + inner_cycles is the default schedule, bit for
+    bit, through both inner-solve graphs (a second solve replays them)."""
+    n = 64 if bc != mg.OPEN else 32
+    rho, fpg = source(n, bc, seed=41)
+    ref = orc.solve(rho, 1.0 / n, bc, four_pi_G=fpg, tol=0.0, max_cycles=80)
+    rd = torch.from_numpy(rho).cuda()
+    runs = {}
+    for first in (0, 4, 1):
+        with mg.Solver(n, 1.0 / n, bc, prec=mg.MIXED, first_cycles=first) as s:
+            s.solve(rd, fpg, 1e-10)
+            phi, hist, st = s.solve(rd, fpg, 1e-10)
+        assert st == 0 and hist[-1] < 1e-10, (first, hist)
+        assert emax(phi.cpu().numpy(), ref.phi) <= 1e-9
+        runs[first] = (phi, hist)
+    assert torch.equal(runs[4][0], runs[0][0]) and np.array_equal(runs[4][1], runs[0][1])
+    assert runs[1][1][0] > 10 * runs[0][1][0]
+    with pytest.raises(mg.MGError):
+        mg.Solver(8, 1.0 / 8, bc, prec=mg.MIXED, first_cycles=66)
+
+
+def test_batch_first_outer_iteration_cycles():
+    """The batched solve takes first_cycles for its first outer iteration as
+    mg_solve does (the first residual grows with one V-cycle there) and still
+    converges; more than 17 is refused."""
+    n = 32
+    rho = inputs.gaussian_blobs(n, 4, seed=43)
+    ref = orc.solve(rho, 1.0 / n, mg.PERIODIC, tol=0.0, max_cycles=80)
+    rd = torch.from_numpy(rho).cuda()
+    hists = {}
+    for first in (0, 1):
+        with mg.Batch([n], [1.0 / n], [mg.PERIODIC], first_cycles=first) as b:
+            pd = torch.zeros_like(rd)
+            st, h, _ = b.solve([rd], [pd], 1.0, 1e-10)
+        assert st == 0 and h[0][-1] < 1e-10, (first, h)
+        assert emax(pd.cpu().numpy(), ref.phi) <= 1e-9
+        hists[first] = h[0]
+    assert hists[1][0] > 10 * hists[0][0]
+    with pytest.raises(mg.MGError):
+        mg.Batch([n], [1.0 / n], [mg.PERIODIC], first_cycles=18)
+
+
 @pytest.mark.parametrize("prec", [mg.FP64, mg.MIXED])
 def test_mgi_initial_guess(prec):
     n = 16
