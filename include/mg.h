@@ -343,7 +343,8 @@ mg_status mg_op_vcycle_up(int nx, int ny, int nz, double h, mg_bc bc, double ome
  * MG_ERR_TIMEOUT.  face_bc[6] (host) gives each face's
  * homogeneous rule (x-, x+, y-, y+, z-, z+): MG_BC_PERIODIC on both faces of an
  * axis, MG_BC_FIXED (value 0) or MG_BC_ZEROGRAD.  tx (0, 32 or 64 cells), ty
- * (0, 16 or 32 rows) and cz (0 or a multiple of 8 planes) choose the CTA tile
+ * (0, 16 or 32 rows) and cz (0 or a multiple of 4 planes; of 8 for leg 2)
+ * choose the CTA tile
  * and z-chunk; 0 takes the built-in choice.  Arrays as in mg_op_vcycle_down
  * and mg_op_vcycle_up.  Errors: MG_ERR_ARG for bad arguments and for grids or
  * shapes the fused kernels do not take (sides below 32, nx not a multiple of

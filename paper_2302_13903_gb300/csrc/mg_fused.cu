@@ -46,7 +46,7 @@ bool fused_ok(Grid g, const Bc& bc) {
   bool hom = bc.kind != BC_OPEN;
   if (bc.kind == BC_FIXED) hom = hom && bc.value == 0.0;
   if (bc.kind == BC_MIXED) hom = hom && bc.faces == nullptr;
-  // widths the 64- or 32-wide tiles divide, rows in 16s, planes in chunks of 8;
+  // widths the 64- or 32-wide tiles divide, rows in 16s, planes in 8s;
   // element offsets of 32 bits
   return hom && g.nx >= 32 && g.ny >= 32 && g.nz >= 32 && g.nx % 32 == 0 && g.ny % 16 == 0 &&
          g.nz % 8 == 0 && (g.nx < 64 || g.nx % 64 == 0) && g.cells() < (1LL << 32);
@@ -55,7 +55,7 @@ bool fused_ok(Grid g, const Bc& bc) {
 bool fused_cfg_ok(Grid g, TileCfg cfg) {
   const bool tx_ok = cfg.tx == 0 || (cfg.tx == 32 && g.nx % 32 == 0) ||
                      (cfg.tx == 64 && g.nx % 64 == 0);
-  const bool cz_ok = cfg.cz == 0 || (cfg.cz >= 8 && cfg.cz % 8 == 0 && cfg.cz <= 1024);
+  const bool cz_ok = cfg.cz == 0 || (cfg.cz >= 4 && cfg.cz % 4 == 0 && cfg.cz <= 1024);
   const bool ty_ok = cfg.ty == 0 || cfg.ty == 16 || (cfg.ty == 32 && g.ny % 32 == 0);
   return tx_ok && cz_ok && ty_ok;
 }

@@ -58,7 +58,7 @@ struct FusedParams {
   float sx0, sx1, sy0, sy1, sz0, sz1;
   float cu, cs, cf;  // SOR: u <- cu u + cs sum_nb + cf f
   float inv_h2;
-  int cz;            // planes per CTA (multiple of 8, or nz)
+  int cz;            // planes per CTA (multiple of 4, or nz)
 };
 
 // The kernels' constants for level g (spacing h, SOR factor omega, face
@@ -648,7 +648,7 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   CoarseIdx ci;
   if (MODE == kUp) {
     if (!(PX && PY)) ci = coarse_idx<PM>(p, gx4, gyA, cx0, cy0);
-    // q_first = z0 - 2 with z0 a multiple of 8: K0 = q_first / 2 is odd
+    // q_first = z0 - 2 with z0 a multiple of 4: K0 = q_first / 2 is odd
     const int K0 = q_first >> 1;
     copy_coarse(std::integral_constant<int, 0>{}, K0 - 1);
     copy_coarse(std::integral_constant<int, 1>{}, K0);
@@ -662,7 +662,7 @@ __device__ __forceinline__ void fused_tile(const float* u_in, float* u_out, cons
   }
 
   // One plane step.  J = (q - q_first) mod 4 fixes the ring slots and the
-  // colours at compile time: q_first = z0 - HZ with z0 a multiple of 8.
+  // colours at compile time: q_first = z0 - HZ with z0 a multiple of 4.
   auto step = [&](auto Jc, int q) {
     constexpr int J = decltype(Jc)::value;
     constexpr int QP = ((J - HZ) % 4 + 4) % 4;  // q mod 4

@@ -1258,12 +1258,14 @@ void autotune(mg_ctx* c, cudaStream_t s) {
           best = hit->second;
         } else {
           float best_ms = 1e30f;
-          for (int cand_i = 0; cand_i < 32; ++cand_i) {
+          for (int cand_i = 0; cand_i < 36; ++cand_i) {
             {
               const int tx = (cand_i & 1) ? 64 : 32, ty = (cand_i & 2) ? 32 : 16;
               // 8, 16, ..., 64 planes: the chunks that are not powers of two
-              // even out the last wave of CTAs on some grids
-              const int cz = 8 * (1 + (cand_i >> 2));
+              // even out the last wave of CTAs on some grids; 4 planes halve
+              // the chain of plane steps of a CTA on the small levels, where
+              // that chain, not the bytes, sets a launch's time
+              const int cz = cand_i < 32 ? 8 * (1 + (cand_i >> 2)) : 4;
               const mg::TileCfg cand{tx, cz, ty};
               if (cz > g.nz || !mg::fused_cfg_ok(g, cand)) continue;
               const float ms = time_launches(c, s, reps, flush, flush_bytes, [&]() {

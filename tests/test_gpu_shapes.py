@@ -2,8 +2,8 @@
 step, called directly through the C ABI (mg_op_fused_leg, mg_op_fx_step),
 against the oracle's operators: each periodic-axis mask 0-7 (a rule per face,
 Sec. 2.3.6) times each launch shape the autotuner may choose (tiles of 32 or
-64 cells by 16 or 32 rows, z-chunks of 8 to 64 planes, including a chunk that
-leaves a ragged last one), on a 128^3 cube and a 256 x 128 x 128 box.
+64 cells by 16 or 32 rows, z-chunks of 4 to 64 planes, including chunks that
+leave a ragged last one), on a 128^3 cube and a 256 x 128 x 128 box.
 
 Tolerance of the FP32 legs: 2e-6 of the largest output (a few FP32 ulp of at
 most 27 terms; the oracle runs in FP64 on the same FP32 inputs).  The
@@ -23,7 +23,8 @@ P, F, Z = mg.PERIODIC, mg.FIXED, mg.ZEROGRAD
 # non-periodic faces of each axis get two different rules (per-face signs)
 WALLS = [(F, Z), (Z, F), (F, Z)]
 GRIDS = {"cube128": (128, 128, 128), "box256": (128, 128, 256)}  # (nz, ny, nx)
-SHAPES = [(tx, ty, cz) for tx in (32, 64) for ty in (16, 32) for cz in (8, 24, 64)] + [(0, 0, 0)]
+SHAPES = [(tx, ty, cz) for tx in (32, 64) for ty in (16, 32) for cz in (4, 8, 12, 24, 64)]
+SHAPES += [(0, 0, 0)]
 _REF = {}
 
 
@@ -121,7 +122,7 @@ def test_fused_down_with_tensor_copies_matches_plain_down_leg(zero):
     nz, ny, nx = 48, 128, 256  # 2 x 2 of the 4 x 4 tiles lie inside the level
     u, f = (torch.from_numpy(rng.standard_normal((nz, ny, nx)).astype(np.float32)).cuda()
             for _ in range(2))
-    for cz in (8, 16, 0):
+    for cz in (4, 8, 16, 0):
         a = mg.op_fused_leg(0, u, f, 1.0 / nx, [P] * 6, zero_guess=zero, tile=(64, 32, cz))
         b = mg.op_fused_leg(3, u, f, 1.0 / nx, [P] * 6, zero_guess=zero, tile=(64, 32, cz))
         torch.cuda.synchronize()
@@ -137,7 +138,7 @@ def test_fused_up_with_tensor_copies_matches_plain_up_leg():
             for _ in range(2))
     ec = torch.from_numpy(rng.standard_normal((nz // 2, ny // 2, nx // 2)).astype(np.float32))
     ec = ec.cuda()
-    for cz in (8, 16, 0):
+    for cz in (4, 8, 16, 0):
         a = mg.op_fused_leg(1, u, f, 1.0 / nx, [P] * 6, ec=ec, tile=(64, 16, cz))
         b = mg.op_fused_leg(4, u, f, 1.0 / nx, [P] * 6, ec=ec, tile=(64, 16, cz))
         torch.cuda.synchronize()
@@ -147,7 +148,7 @@ def test_fused_up_with_tensor_copies_matches_plain_up_leg():
 def test_fused_leg_rejects_shapes_it_does_not_take():
     f = torch.zeros((64, 48, 64), device="cuda")  # 48 rows: 16-row tiles only
     mg.op_fused_leg(0, f, f, 1.0, [P] * 6, tile=(64, 16, 8))  # taken
-    for tile in [(32, 32, 0), (48, 16, 0), (32, 16, 12)]:
+    for tile in [(32, 32, 0), (48, 16, 0), (32, 16, 6), (32, 16, 2)]:
         with pytest.raises(mg.MGError):
             mg.op_fused_leg(0, f, f, 1.0, [P] * 6, tile=tile)
     with pytest.raises(mg.MGError):  # periodic faces come in pairs
@@ -160,6 +161,8 @@ def test_fused_leg_rejects_shapes_it_does_not_take():
         mg.op_fused_leg(2, f, f, 1.0, [P] * 6, ec=e, tile=(32, 16, 8))
     with pytest.raises(mg.MGError):  # ... and 32-row tiles need rows in 32s
         mg.op_fused_leg(2, f, f, 1.0, [P] * 6, ec=e, tile=(64, 32, 8))
+    with pytest.raises(mg.MGError):  # ... and z-chunks in 8s
+        mg.op_fused_leg(2, f, f, 1.0, [P] * 6, ec=e, tile=(64, 16, 4))
     u2, fc2 = mg.op_fused_leg(2, f, f, 1.0, [P] * 6, ec=e, tile=(64, 16, 16))  # taken
 
 

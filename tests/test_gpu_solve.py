@@ -330,7 +330,8 @@ def test_autotuned_shapes_keep_the_result(bc, n):
     assert sorted(cfg["fused_down"]) == sorted(cfg["fused_up"]) == fused_levels
     for l, (tx, ty, cz) in list(cfg["fused_down"].items()) + list(cfg["fused_up"].items()):
         width = n >> (n.bit_length() - 1 - l)
-        assert tx in (32, 64) and width % tx == 0 and cz in range(8, 65, 8) and cz <= width
+        assert tx in (32, 64) and width % tx == 0 and cz in [4] + list(range(8, 65, 8))
+        assert cz <= width
         assert ty in (16, 32) and width % ty == 0
     for l, (tx, ty, cz) in cfg["fused_updown"].items():  # the finest level's paired cycles
         assert l == n.bit_length() - 1 and tx == 64 and ty in (16, 32) and cz in (16, 32, 64, 128)
