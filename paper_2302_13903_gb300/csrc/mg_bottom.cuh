@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mg_device.cuh"
 #include "mg_internal.h"
 
@@ -310,14 +312,54 @@ __device__ void in_shared(const BottomArgs<T>& a, T* smem, bool load_u, Body bod
   }
   __syncthreads();
   const int top = a.top, ct = a.n[top] * a.n[top] * a.n[top];
-  for (int t = threadIdx.x; t < ct; t += blockDim.x) {
-    b.f[top][t] = a.f[top][t];
-    if (load_u) b.u[top][t] = a.u[top][t];
-  }
+  // 16-byte global accesses where the arrays allow, a thread's loads all
+  // issued before its shared stores (the copies are a chain of L2 round
+  // trips otherwise); the shared copies are 4- or 8-byte aligned only
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int V = 16 / sizeof(T);
+  const bool vec = ct % V == 0 &&
+                   ((reinterpret_cast<unsigned long long>(a.f[top]) |
+                     reinterpret_cast<unsigned long long>(a.u[top])) & 15) == 0;
+  auto copy_in = [&](const T* src, T* dst) {
+    if (!vec) {
+      for (int t = threadIdx.x; t < ct; t += blockDim.x) dst[t] = src[t];
+      return;
+    }
+    constexpr int K = 4;
+    const Vec* s4 = reinterpret_cast<const Vec*>(src);
+    for (int t0 = threadIdx.x; t0 < ct / V; t0 += K * blockDim.x) {
+      Vec r[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (t0 + k * (int)blockDim.x < ct / V) r[k] = s4[t0 + k * blockDim.x];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int t = t0 + k * blockDim.x;
+        if (t < ct / V) {
+          const T* rv = reinterpret_cast<const T*>(&r[k]);
+#pragma unroll
+          for (int j = 0; j < V; ++j) dst[V * t + j] = rv[j];
+        }
+      }
+    }
+  };
+  copy_in(a.f[top], b.f[top]);
+  if (load_u) copy_in(a.u[top], b.u[top]);
   __syncthreads();
   body(b);
   __syncthreads();
-  for (int t = threadIdx.x; t < ct; t += blockDim.x) a.u[top][t] = b.u[top][t];
+  if (vec) {
+    Vec* d4 = reinterpret_cast<Vec*>(a.u[top]);
+    for (int t = threadIdx.x; t < ct / V; t += blockDim.x) {
+      Vec r;
+      T* rv = reinterpret_cast<T*>(&r);
+#pragma unroll
+      for (int j = 0; j < V; ++j) rv[j] = b.u[top][V * t + j];
+      d4[t] = r;
+    }
+  } else {
+    for (int t = threadIdx.x; t < ct; t += blockDim.x) a.u[top][t] = b.u[top][t];
+  }
   __syncthreads();
 }
 

@@ -77,13 +77,13 @@ inline FusedParams params(Grid g, double h, const Bc& bc, double omega) {
   return p;
 }
 
-// Planes per CTA: cz_cfg when nonzero, else the largest of 64, 32, 16, 8 that
-// still gives two CTAs per SM on tiles of tx x ty; at most nz.
+// Planes per CTA: cz_cfg when nonzero, else the largest of 64, 32, 16, 8, 4
+// that still gives two CTAs per SM on tiles of tx x ty; at most nz.
 inline int chunk_planes(const FusedParams& p, int tx, int ty, int cz_cfg) {
   const long long sms = sm_count();
   const long long cols = (long long)(p.nx / tx) * (p.ny / ty);
   int cz = 64;
-  while (cz > 8 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
+  while (cz > 4 && cols * ((p.nz + cz - 1) / cz) < 2 * sms) cz /= 2;
   if (cz_cfg) cz = cz_cfg;
   return cz < p.nz ? cz : p.nz;
 }
